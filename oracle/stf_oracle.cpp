@@ -1,0 +1,718 @@
+// FP64 CPU oracle for stochastic texture filtering -- TEST INFRASTRUCTURE ONLY.
+//
+// Plain, slow, obviously-correct restatement of what the paper's method computes
+// (Pharr, Wronski, Salvi, Fajardo 2024, "Filtering After Shading With Stochastic
+// Texture Filtering").  Only tests/, the smoke check and bench.py's CPU-baseline leg
+// may load this library; the CUDA product path never does, and the two share no code.
+//
+// Structure of one lookup (2-D):
+//   * screen-space jitter of the lookup point inside the pixel footprint (Sec. 4.2.1,
+//     Fig. 6), the stochastic MIP level (Sec. 4.2.1; supplement "Real-time anisotropic
+//     filtering", and the stochastic lerp of supplement Sec. "Linear Filters"),
+//   * separable filter weights from the 1-D kernels of supplement Sec. "Filter Kernels"
+//     (tent, Keys cubic, cubic B-spline) and Mitchell-Netravali BC(1/3,1/3),
+//   * the estimators: filter-before-shading (Eq. filter-before-shading), exact
+//     filter-after-shading (Eq. filtering-after-shading), single-tap stochastic
+//     estimator (Eq. stochastic-sum with CDF inversion, Sec. 2.2 "Sampling arrays") and
+//     positivization (Sec. 2.2 "Positivization").
+//
+// Precision.  Everything that *decides an integer* (which MIP level, which texel) is
+// evaluated in FP32 exactly as the paper's listings do (they are float code), with a
+// fixed operation order and no fused multiply-add.  Every *value* (filter weights used
+// for sums, shading, transmittance, averages) is FP64.  For every decision the oracle
+// also takes the same decision from FP64 quantities and reports the distance of the
+// uniform to the nearest FP64 CDF boundary, so that tests can check that FP32 and FP64
+// decisions differ only next to a boundary.
+//
+// Parity status of each function: see the pins in tests/test_oracle_*.py.
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw 2011), keyed by
+// (seed, query/pixel id, sample, stream); the uniform is the top 24 bits * 2^-24.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <algorithm>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ------------------------------------------------------------------ enums (API values)
+enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
+enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
+enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
+enum { FLAG_STRATIFIED = 1u };
+enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
+enum { ADDR_WRAP = 0, ADDR_CLAMP = 1 };
+const uint32_t NO_PICK = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------ Philox4x32-10
+void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;   // round multipliers
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;   // Weyl key increments
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * x0, p1 = (uint64_t)M1 * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void draw(uint64_t seed, uint64_t id, uint32_t sample, uint32_t stream, uint32_t out[4]) {
+    uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), sample, stream};
+    uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    philox4x32_10(c, k, out);
+}
+
+// uniform in [0,1) on the 2^-24 grid; exactly representable in float and double
+inline float unif(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
+
+// ------------------------------------------------------------------ 1-D kernels, FP64
+// supplement "Filter Kernels": tent K1, Keys cubic K3(a), cubic B-spline K_bs;
+// Mitchell & Netravali (1988) BC family (cited beside K3 in the supplement).
+double k_tent(double d) { d = std::fabs(d); return d < 1.0 ? 1.0 - d : 0.0; }
+double k_bspline(double d) {
+    d = std::fabs(d);
+    if (d <= 1.0) return (4.0 - 3.0 * d * d * (2.0 - d)) / 6.0;
+    if (d <= 2.0) { double e = 2.0 - d; return e * e * e / 6.0; }
+    return 0.0;
+}
+double k_keys(double a, double d) {
+    d = std::fabs(d);
+    if (d < 1.0) return (a + 2.0) * d * d * d - (a + 3.0) * d * d + 1.0;
+    if (d < 2.0) return a * d * d * d - 5.0 * a * d * d + 8.0 * a * d - 4.0 * a;
+    return 0.0;
+}
+double k_bc(double B, double C, double d) {
+    d = std::fabs(d);
+    if (d < 1.0)
+        return ((12.0 - 9.0 * B - 6.0 * C) * d * d * d + (-18.0 + 12.0 * B + 6.0 * C) * d * d +
+                (6.0 - 2.0 * B)) / 6.0;
+    if (d < 2.0)
+        return ((-B - 6.0 * C) * d * d * d + (6.0 * B + 30.0 * C) * d * d +
+                (-12.0 * B - 48.0 * C) * d + (8.0 * B + 24.0 * C)) / 6.0;
+    return 0.0;
+}
+double kernel64(int f, double d) {
+    switch (f) {
+        case F_LINEAR: return k_tent(d);
+        case F_BSPLINE: return k_bspline(d);
+        case F_CATMULL_ROM: return k_keys(-0.5, d);
+        case F_MITCHELL: return k_bc(1.0 / 3.0, 1.0 / 3.0, d);
+    }
+    return 0.0;
+}
+int ntaps(int f) { return f == F_LINEAR ? 2 : 4; }
+int first_tap(int f) { return f == F_LINEAR ? 0 : -1; }   // offset of tap 0 from floor(p)
+bool signed_filter(int f) { return f == F_CATMULL_ROM || f == F_MITCHELL; }
+
+// ------------------------------------------------------------------ FP32 decision weights
+// Per-axis weights in float, written as the paper's listings compute them (the B-spline
+// polynomials of the bicubic/tricubic listings; the cubic kernels evaluated at the four
+// tap distances 1+t, t, 1-t, 2-t).  Used only to take decisions.
+float k32_cubic(int f, float d) {
+    float c3, c2, c0, q3, q2, q1, q0;
+    if (f == F_CATMULL_ROM) {
+        c3 = 1.5f; c2 = -2.5f; c0 = 1.0f; q3 = -0.5f; q2 = 2.5f; q1 = -4.0f; q0 = 2.0f;
+    } else {   // Mitchell B = C = 1/3
+        c3 = 7.0f / 6.0f; c2 = -2.0f; c0 = 8.0f / 9.0f;
+        q3 = -7.0f / 18.0f; q2 = 2.0f; q1 = -10.0f / 3.0f; q0 = 16.0f / 9.0f;
+    }
+    if (d < 1.0f) { float a = c3 * d; a = a + c2; a = a * d; a = a * d; return a + c0; }
+    if (d < 2.0f) { float a = q3 * d; a = a + q2; a = a * d; a = a + q1; a = a * d; return a + q0; }
+    return 0.0f;
+}
+int weights32(int f, float t, float w[4]) {
+    if (f == F_LINEAR) { w[0] = 1.0f - t; w[1] = t; return 2; }
+    if (f == F_BSPLINE) {
+        const float s = 1.0f / 6.0f;
+        float t2 = t * t, t3 = t * t2;
+        float a;
+        a = -t3; a = a + 3.0f * t2; a = a - 3.0f * t; a = a + 1.0f; w[0] = s * a;
+        a = (3.0f * t) * t2; a = a - 6.0f * t2; a = a + 4.0f; w[1] = s * a;
+        a = (-3.0f * t) * t2; a = a + 3.0f * t2; a = a + 3.0f * t; a = a + 1.0f; w[2] = s * a;
+        w[3] = s * t3;
+        return 4;
+    }
+    w[0] = k32_cubic(f, 1.0f + t); w[1] = k32_cubic(f, t);
+    w[2] = k32_cubic(f, 1.0f - t); w[3] = k32_cubic(f, 2.0f - t);
+    return 4;
+}
+
+// CDF inversion ("Sampling arrays"): first k with xi * S < prefix_k, S = sum |w|,
+// restricted to taps of a sign class (cls = 0 all, +1 w > 0, -1 w < 0).
+int pick32(const float* w, int n, float xi, int cls, float* total) {
+    float C[4], acc = 0.0f;
+    for (int k = 0; k < n; ++k) {
+        bool in = cls == 0 || (cls > 0 ? w[k] > 0.0f : w[k] < 0.0f);
+        acc = acc + (in ? std::fabs(w[k]) : 0.0f);
+        C[k] = acc;
+    }
+    if (total) *total = acc;
+    float target = xi * acc;
+    for (int k = 0; k < n; ++k) if (target < C[k]) return k;
+    return n - 1;
+}
+// Same decision from FP64 weights; also the distance of xi to the nearest interior
+// boundary of the FP64 CDF.
+int pick64(const double* w, int n, double xi, int cls, double* bdist) {
+    double S = 0.0, C[4];
+    for (int k = 0; k < n; ++k) {
+        bool in = cls == 0 || (cls > 0 ? w[k] > 0.0 : w[k] < 0.0);
+        S += in ? std::fabs(w[k]) : 0.0;
+        C[k] = S;
+    }
+    int pick = n - 1;
+    bool found = false;
+    double bd = 1e30;
+    for (int k = 0; k < n; ++k) {
+        double ck = S > 0 ? C[k] / S : 1.0;
+        if (k < n - 1) bd = std::min(bd, std::fabs(xi - ck));
+        if (!found && xi < ck) { pick = k; found = true; }
+    }
+    if (bdist) *bdist = std::min(*bdist, bd);
+    return pick;
+}
+
+// ------------------------------------------------------------------ shading, FP64
+// GGX (Trowbridge-Reitz) microfacet specular + Lambert diffuse, times the cosine
+// factor: f_hat = [rho/pi + D G2 F / (4 nl nv)] nl.  The paper evaluates a Disney BRDF
+// through this f_hat (Sec. 3); this restatement fixes l, v and F0 (see the design notes).
+const double PI = 3.14159265358979323846;
+struct V3 { double x, y, z; };
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+inline V3 normalize(V3 a) { double l = std::sqrt(dot(a, a)); return {a.x / l, a.y / l, a.z / l}; }
+// fixed light and view directions, given as FP32 constants
+const V3 LDIR = {(double)0.48f, (double)0.36f, (double)0.80f};
+const V3 VDIR = {(double)-0.28f, (double)0.0f, (double)0.96f};
+const double F0_DIELECTRIC = (double)0.04f;
+const double ALPHA_MIN = (double)0.05f, ALPHA_MAX = 1.0;
+
+double ggx_D(double a2, double nh, double s2) {     // s2 = |n x h|^2 = 1 - nh^2
+    double q = a2 * nh * nh + s2;
+    return a2 / (PI * q * q);
+}
+double smith_lambda(double a2, double tan2) { return 0.5 * (std::sqrt(1.0 + a2 * tan2) - 1.0); }
+
+void ggx_eval(V3 n, V3 l, V3 v, double alpha, const double rho[3], double F0, double out[3]) {
+    double nl = dot(n, l), nv = dot(n, v);
+    if (!(nl > 0.0) || !(nv > 0.0)) { out[0] = out[1] = out[2] = 0.0; return; }
+    double a = std::min(std::max(alpha, ALPHA_MIN), ALPHA_MAX), a2 = a * a;
+    V3 h = normalize({l.x + v.x, l.y + v.y, l.z + v.z});
+    V3 nxh = cross(n, h), nxl = cross(n, l), nxv = cross(n, v);
+    double D = ggx_D(a2, dot(n, h), dot(nxh, nxh));
+    double G = 1.0 / (1.0 + smith_lambda(a2, dot(nxl, nxl) / (nl * nl)) +
+                      smith_lambda(a2, dot(nxv, nxv) / (nv * nv)));
+    double vh = dot(v, h), m = 1.0 - vh;
+    double F = F0 + (1.0 - F0) * m * m * m * m * m;
+    double spec = D * G * F / (4.0 * nv);   // (D G F / (4 nl nv)) * nl
+    for (int c = 0; c < 3; ++c) out[c] = rho[c] * nl / PI + spec;
+}
+
+// decoded material sample
+struct Mat { double rho[3]; double rough; V3 n; };
+
+void shade(int mode, const Mat& m, double out[3]) {
+    if (mode == S_LINEAR) { for (int c = 0; c < 3; ++c) out[c] = m.rho[c]; return; }
+    ggx_eval(m.n, LDIR, VDIR, m.rough, m.rho, F0_DIELECTRIC, out);
+}
+
+// ------------------------------------------------------------------ textures
+struct Tex {
+    int format, levels, address;
+    int width[16], height[16];
+    const void* data[16];
+    const uint8_t* normal[16];
+};
+
+int wrapi(int i, int n, int addr) {
+    if (addr == ADDR_CLAMP) return std::min(std::max(i, 0), n - 1);
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+Mat fetch(const Tex& T, int lvl, int ix, int iy) {
+    Mat m;
+    size_t o = (size_t)iy * T.width[lvl] + ix;
+    if (T.format == FMT_RGBA32F) {
+        const float* p = (const float*)T.data[lvl] + 4 * o;
+        m.rho[0] = p[0]; m.rho[1] = p[1]; m.rho[2] = p[2]; m.rough = p[3];
+    } else {
+        const uint8_t* p = (const uint8_t*)T.data[lvl] + 4 * o;
+        for (int c = 0; c < 3; ++c) m.rho[c] = p[c] / 255.0;
+        m.rough = 0.05 + 0.95 * (p[3] / 255.0);
+    }
+    if (T.normal[lvl]) {
+        const uint8_t* q = T.normal[lvl] + 2 * o;
+        double x = 2.0 * q[0] / 255.0 - 1.0, y = 2.0 * q[1] / 255.0 - 1.0;
+        double z = std::sqrt(std::max(0.0, 1.0 - x * x - y * y));
+        m.n = normalize({x, y, z});
+    } else {
+        m.n = {0.0, 0.0, 1.0};
+    }
+    return m;
+}
+inline uint32_t pack2d(int lvl, int ix, int iy) {
+    return ((uint32_t)lvl << 28) | ((uint32_t)iy << 14) | (uint32_t)ix;
+}
+
+struct Queries {
+    uint64_t n;
+    const float *u, *v, *dudx, *dvdx, *dudy, *dvdy;   // derivs nullable (all or none)
+};
+
+// LOD from the screen-space derivatives: minor ellipse axis, anisotropy capped at 64
+// (Sec. 4.2.1; supplement listing "computeLodAniso"), clamped to [0, L-1].
+// FP32 as in the listing (decision precision), plus the FP64 value for boundary checks.
+void lod(const Tex& T, const Queries& Q, uint64_t q, float* lam32, double* lam64) {
+    if (!Q.dudx || T.levels <= 1) { *lam32 = 0.0f; *lam64 = 0.0; return; }
+    float W = (float)T.width[0], H = (float)T.height[0];
+    float ax = Q.dudx[q] * W, ay = Q.dvdx[q] * H, bx = Q.dudy[q] * W, by = Q.dvdy[q] * H;
+    float la = ax * ax; la = la + ay * ay;
+    float lb = bx * bx; lb = lb + by * by;
+    float mn = la, mx = lb;
+    if (mn > mx) { mn = lb; mx = la; }
+    float minl = std::sqrt(mn), maxl = std::sqrt(mx);
+    if (minl > 0.0f && minl * 64.0f < maxl) minl = maxl * (1.0f / 64.0f);
+    float l = std::log2(minl);
+    l = std::fmin(std::fmax(l, 0.0f), (float)(T.levels - 1));
+    *lam32 = l;
+    double A = (double)Q.dudx[q] * W, B = (double)Q.dvdx[q] * H;
+    double C = (double)Q.dudy[q] * W, D = (double)Q.dvdy[q] * H;
+    double a2 = A * A + B * B, b2 = C * C + D * D;
+    double mn64 = std::sqrt(std::min(a2, b2)), mx64 = std::sqrt(std::max(a2, b2));
+    if (mn64 > 0.0 && mn64 * 64.0 < mx64) mn64 = mx64 / 64.0;
+    double l64 = std::log2(mn64);
+    *lam64 = std::fmin(std::fmax(l64, 0.0), (double)(T.levels - 1));
+}
+
+struct Out {
+    double* rgb;        // n*3
+    uint32_t* picks;    // n*spp*2 or null (FP32 decisions)
+    uint32_t* picks64;  // n*spp*2 or null (FP64 decisions)
+    double* bdist;      // n or null: min distance of any uniform to an FP64 boundary
+};
+
+// per level: FP32 texel position and tap geometry on one axis
+struct Axis { int i0; float t; double pos; };
+Axis axis_at(float x, int res) {
+    float p = x * (float)res;
+    p = p - 0.5f;
+    float fl = std::floor(p);
+    return {(int)fl, p - fl, (double)p};
+}
+
+void run_query(const Tex& T, const Queries& Q, uint64_t q, int filter, int mode, int smode,
+               uint32_t spp, uint64_t seed, uint32_t flags, Out& O) {
+    float lam32; double lam64;
+    lod(T, Q, q, &lam32, &lam64);
+    int l0 = (int)std::floor(lam32);
+    float fr = lam32 - (float)l0;
+    int l0_64 = (int)std::floor(lam64);
+    double fr64 = lam64 - l0_64;
+    double bd = 1e30;
+    if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs(lam64 - std::nearbyint(lam64)));
+    int nt = ntaps(filter), ft = first_tap(filter);
+    bool sgn = signed_filter(filter);
+    double acc[3] = {0, 0, 0};
+    int kside = 1;
+    if (flags & FLAG_STRATIFIED) { kside = (int)std::lround(std::sqrt((double)spp)); }
+
+    for (uint32_t s = 0; s < spp; ++s) {
+        uint32_t r0[4], r1[4], r2[4];
+        draw(seed, q, s, 0, r0);
+        draw(seed, q, s, 1, r1);
+        draw(seed, q, s, 2, r2);
+        // screen-space jitter inside the pixel footprint (FP32, fixed order)
+        float x = Q.u[q], y = Q.v[q];
+        if (Q.dudx) {
+            float jx, jy;
+            if (flags & FLAG_STRATIFIED) {
+                jx = ((float)(s % kside) + 0.5f) / (float)kside - 0.5f;
+                jy = ((float)(s / kside) + 0.5f) / (float)kside - 0.5f;
+            } else {
+                jx = unif(r0[0]) - 0.5f;
+                jy = unif(r0[1]) - 0.5f;
+            }
+            float a = jx * Q.dudx[q], b = jy * Q.dudy[q];
+            x = x + a; x = x + b;
+            float c = jx * Q.dvdx[q], d = jy * Q.dvdy[q];
+            y = y + c; y = y + d;
+        }
+        uint32_t* pk = O.picks ? O.picks + (q * spp + s) * 2 : nullptr;
+        uint32_t* pk64 = O.picks64 ? O.picks64 + (q * spp + s) * 2 : nullptr;
+        if (pk) pk[0] = pk[1] = NO_PICK;
+        if (pk64) pk64[0] = pk64[1] = NO_PICK;
+        double est[3] = {0, 0, 0};
+
+        if (mode == M_NTAP_BEFORE || mode == M_NTAP_AFTER) {
+            // exact sum over both MIP levels and the full 2-D tap grid, FP64 weights
+            double wl[2] = {1.0 - (double)fr, (double)fr};
+            Mat fm{}; fm.n = {0, 0, 0};
+            double fsum[3] = {0, 0, 0};
+            for (int li = 0; li < 2; ++li) {
+                int lvl = l0 + li;
+                if (wl[li] == 0.0 || lvl >= T.levels) continue;
+                int W = T.width[lvl], H = T.height[lvl];
+                Axis ax = axis_at(x, W), ay = axis_at(y, H);
+                for (int j = 0; j < nt; ++j) {
+                    int iy = ay.i0 + ft + j;
+                    double wy = kernel64(filter, ay.pos - (double)iy);
+                    for (int i = 0; i < nt; ++i) {
+                        int ix = ax.i0 + ft + i;
+                        double w = wl[li] * kernel64(filter, ax.pos - (double)ix) * wy;
+                        if (w == 0.0) continue;
+                        Mat m = fetch(T, lvl, wrapi(ix, W, T.address), wrapi(iy, H, T.address));
+                        if (mode == M_NTAP_BEFORE) {
+                            for (int c = 0; c < 3; ++c) fm.rho[c] += w * m.rho[c];
+                            fm.rough += w * m.rough;
+                            fm.n.x += w * m.n.x; fm.n.y += w * m.n.y; fm.n.z += w * m.n.z;
+                        } else {
+                            double o[3];
+                            shade(smode, m, o);
+                            for (int c = 0; c < 3; ++c) fsum[c] += w * o[c];
+                        }
+                    }
+                }
+            }
+            if (mode == M_NTAP_BEFORE) {
+                double ln = std::sqrt(dot(fm.n, fm.n));
+                fm.n = ln > 0 ? V3{fm.n.x / ln, fm.n.y / ln, fm.n.z / ln} : V3{0, 0, 1};
+                shade(smode, fm, est);
+            } else {
+                for (int c = 0; c < 3; ++c) est[c] = fsum[c];
+            }
+        } else {
+            // stochastic MIP level: floor(lambda) + [xi < frac(lambda)] (stochastic lerp)
+            float xl = unif(r0[2]);
+            int lvl = l0 + ((xl < fr) ? 1 : 0);
+            int lvl64 = l0_64 + (((double)xl < fr64) ? 1 : 0);
+            if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs((double)xl - fr64));
+            lvl = std::min(lvl, T.levels - 1);
+            lvl64 = std::min(lvl64, T.levels - 1);
+            int W = T.width[lvl], H = T.height[lvl];
+            Axis ax = axis_at(x, W), ay = axis_at(y, H);
+            float wx[4], wy[4];
+            weights32(filter, ax.t, wx);
+            weights32(filter, ay.t, wy);
+            double wx64[4], wy64[4];
+            for (int k = 0; k < nt; ++k) {
+                wx64[k] = kernel64(filter, ax.pos - (double)(ax.i0 + ft + k));
+                wy64[k] = kernel64(filter, ay.pos - (double)(ay.i0 + ft + k));
+            }
+            // FP64 decisions are evaluated at the FP64 level when it agrees; otherwise the
+            // query is a counted boundary case and only the FP32 picks are reported.
+            auto texel = [&](int lv, int kx, int ky) {
+                int ix = wrapi(ax.i0 + ft + kx, W, T.address), iy = wrapi(ay.i0 + ft + ky, H, T.address);
+                return std::make_pair(ix, iy);
+            };
+            if (mode == M_STOCHASTIC) {
+                float Sx, Sy;
+                int kx = pick32(wx, nt, unif(r0[3]), 0, &Sx);
+                int ky = pick32(wy, nt, unif(r1[0]), 0, &Sy);
+                int kx64 = pick64(wx64, nt, unif(r0[3]), 0, &bd);
+                int ky64 = pick64(wy64, nt, unif(r1[0]), 0, &bd);
+                auto t = texel(lvl, kx, ky);
+                Mat m = fetch(T, lvl, t.first, t.second);
+                double o[3];
+                shade(smode, m, o);
+                double Wt = 1.0;
+                if (sgn) {
+                    double sx = 0, sy = 0;
+                    for (int k = 0; k < nt; ++k) { sx += std::fabs(wx64[k]); sy += std::fabs(wy64[k]); }
+                    Wt = sx * sy * ((wx64[kx] < 0) != (wy64[ky] < 0) ? -1.0 : 1.0);
+                }
+                for (int c = 0; c < 3; ++c) est[c] = Wt * o[c];
+                if (pk) pk[0] = pack2d(lvl, t.first, t.second);
+                if (pk64) {
+                    auto t64 = texel(lvl64, kx64, ky64);
+                    pk64[0] = lvl64 == lvl ? pack2d(lvl64, t64.first, t64.second) : NO_PICK - 1;
+                }
+            } else {   // positivization: one sample from each sign set (Sec. 2.2)
+                float Px, Nx, Py, Ny;
+                pick32(wx, nt, 0.0f, +1, &Px); pick32(wx, nt, 0.0f, -1, &Nx);
+                pick32(wy, nt, 0.0f, +1, &Py); pick32(wy, nt, 0.0f, -1, &Ny);
+                float Wp = Px * Py; Wp = Wp + Nx * Ny;
+                float Wn = Px * Ny; Wn = Wn + Nx * Py;
+                double Px64 = 0, Nx64 = 0, Py64 = 0, Ny64 = 0;
+                for (int k = 0; k < nt; ++k) {
+                    (wx64[k] > 0 ? Px64 : Nx64) += std::fabs(wx64[k]);
+                    (wy64[k] > 0 ? Py64 : Ny64) += std::fabs(wy64[k]);
+                }
+                double Wp64 = Px64 * Py64 + Nx64 * Ny64, Wn64 = Px64 * Ny64 + Nx64 * Py64;
+                // positive set: class (+,+) with probability Px Py / W+, else (-,-)
+                float xc = unif(r1[1]);
+                int cx = (xc * Wp < Px * Py) ? +1 : -1;
+                int cx64 = ((double)xc < Px64 * Py64 / Wp64) ? +1 : -1;
+                if (Nx64 * Ny64 > 0) bd = std::min(bd, std::fabs((double)xc - Px64 * Py64 / Wp64));
+                int kx = pick32(wx, nt, unif(r0[3]), cx, nullptr);
+                int ky = pick32(wy, nt, unif(r1[0]), cx, nullptr);
+                int kx64 = pick64(wx64, nt, unif(r0[3]), cx64, &bd);
+                int ky64 = pick64(wy64, nt, unif(r1[0]), cx64, &bd);
+                auto tp = texel(lvl, kx, ky);
+                double o[3];
+                shade(smode, fetch(T, lvl, tp.first, tp.second), o);
+                for (int c = 0; c < 3; ++c) est[c] = Wp64 * o[c];
+                if (pk) pk[0] = pack2d(lvl, tp.first, tp.second);
+                if (pk64) {
+                    auto t64 = texel(lvl64, kx64, ky64);
+                    pk64[0] = lvl64 == lvl ? pack2d(lvl64, t64.first, t64.second) : NO_PICK - 1;
+                }
+                // negative set: class (+,-) with probability Px Ny / W-, else (-,+)
+                if (Wn > 0.0f) {
+                    float xn = unif(r2[0]);
+                    int nx_cls = (xn * Wn < Px * Ny) ? +1 : -1;
+                    int nx64 = ((double)xn < Px64 * Ny64 / Wn64) ? +1 : -1;
+                    if (Px64 * Ny64 > 0 && Nx64 * Py64 > 0)
+                        bd = std::min(bd, std::fabs((double)xn - Px64 * Ny64 / Wn64));
+                    int qx = pick32(wx, nt, unif(r1[2]), nx_cls, nullptr);
+                    int qy = pick32(wy, nt, unif(r1[3]), -nx_cls, nullptr);
+                    int qx64 = pick64(wx64, nt, unif(r1[2]), nx64, &bd);
+                    int qy64 = pick64(wy64, nt, unif(r1[3]), -nx64, &bd);
+                    auto tn = texel(lvl, qx, qy);
+                    shade(smode, fetch(T, lvl, tn.first, tn.second), o);
+                    for (int c = 0; c < 3; ++c) est[c] -= Wn64 * o[c];
+                    if (pk) pk[1] = pack2d(lvl, tn.first, tn.second);
+                    if (pk64) {
+                        auto t64 = texel(lvl64, qx64, qy64);
+                        pk64[1] = lvl64 == lvl ? pack2d(lvl64, t64.first, t64.second) : NO_PICK - 1;
+                    }
+                }
+            }
+        }
+        for (int c = 0; c < 3; ++c) acc[c] += est[c];
+    }
+    for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c] / (double)spp;
+    if (O.bdist) O.bdist[q] = bd;
+}
+
+// ------------------------------------------------------------------ volume march
+// FP16 -> double, exact (IEEE 754 binary16)
+double half_to_double(uint16_t h) {
+    int e = (h >> 10) & 0x1F, m = h & 0x3FF;
+    double s = (h & 0x8000) ? -1.0 : 1.0;
+    if (e == 0) return s * std::ldexp((double)m, -24);
+    if (e == 31) return m ? NAN : s * INFINITY;
+    return s * std::ldexp((double)(m | 0x400), e - 25);
+}
+
+struct Vol { int nx, ny, nz; const uint16_t* data; float sigma_scale; };
+
+inline uint32_t pack3d(int x, int y, int z) { return ((uint32_t)z << 20) | ((uint32_t)y << 10) | (uint32_t)x; }
+
+// One pixel sample of the 128-step (or `steps`) ray march through the unit cube with
+// per-step transmittance exp(-sigma dt) (Sec. 5 "Offline rendering": density filtered by
+// trilinear or tricubic B-spline, stochastically or with all taps).
+double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint32_t steps,
+                    int filter, int mode, uint64_t seed, uint32_t flags, uint32_t spp,
+                    uint64_t pix, uint32_t s, uint32_t* picks, double* bd) {
+    uint32_t px = (uint32_t)(pix % W), py = (uint32_t)(pix / W);
+    float jx, jy;
+    if (flags & FLAG_STRATIFIED) {
+        int k = (int)std::lround(std::sqrt((double)spp));
+        jx = ((float)(s % k) + 0.5f) / (float)k;
+        jy = ((float)(s / k) + 0.5f) / (float)k;
+    } else {
+        uint32_t r[4];
+        draw(seed, pix, s, 0, r);
+        jx = unif(r[0]); jy = unif(r[1]);
+    }
+    float sx = (float)px + jx; sx = sx * (2.0f / (float)W); sx = sx - 1.0f;
+    float sy = (float)py + jy; sy = sy * (2.0f / (float)H); sy = 1.0f - sy;
+    const float *e = cam, *f = cam + 3, *r = cam + 6, *u = cam + 9;
+    float d[3];
+    for (int a = 0; a < 3; ++a) { float t = sx * r[a]; t = f[a] + t; float t2 = sy * u[a]; d[a] = t + t2; }
+    float l2 = d[0] * d[0]; l2 = l2 + d[1] * d[1]; l2 = l2 + d[2] * d[2];
+    float inv = 1.0f / std::sqrt(l2);
+    for (int a = 0; a < 3; ++a) d[a] = d[a] * inv;
+    float tmin = 0.0f, tmax = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            float id = 1.0f / d[a];
+            float t1 = (0.0f - e[a]) * id, t2 = (1.0f - e[a]) * id;
+            tmin = std::fmax(tmin, std::fmin(t1, t2));
+            tmax = std::fmin(tmax, std::fmax(t1, t2));
+        } else if (e[a] < 0.0f || e[a] > 1.0f) {
+            tmax = -1.0f;
+        }
+    }
+    if (!(tmin < tmax)) {
+        if (picks) for (uint32_t k = 0; k < steps; ++k) picks[k] = NO_PICK;
+        return 1.0;
+    }
+    float dt = (tmax - tmin) / (float)steps;
+    const int res[3] = {V.nx, V.ny, V.nz};
+    int nt = ntaps(filter), ft = first_tap(filter);
+    double sig = (double)V.sigma_scale, dt64 = (double)dt;
+    double sum_sigma = 0.0, prod = 1.0;
+    for (uint32_t k = 0; k < steps; ++k) {
+        float tk = (float)k + 0.5f; tk = tk * dt; tk = tmin + tk;
+        Axis ax[3];
+        for (int a = 0; a < 3; ++a) {
+            float p = tk * d[a]; p = e[a] + p;
+            ax[a] = axis_at(p, res[a]);
+        }
+        auto vox = [&](int ix, int iy, int iz) {
+            ix = wrapi(ix, V.nx, ADDR_CLAMP); iy = wrapi(iy, V.ny, ADDR_CLAMP); iz = wrapi(iz, V.nz, ADDR_CLAMP);
+            return half_to_double(V.data[((size_t)iz * V.ny + iy) * V.nx + ix]);
+        };
+        if (mode == M_STOCHASTIC) {
+            uint32_t rr[4];
+            draw(seed, pix, s, k + 1, rr);
+            int kk[3];
+            for (int a = 0; a < 3; ++a) {
+                float w[4];
+                double w64[4];
+                weights32(filter, ax[a].t, w);
+                for (int j = 0; j < nt; ++j) w64[j] = kernel64(filter, ax[a].pos - (double)(ax[a].i0 + ft + j));
+                kk[a] = pick32(w, nt, unif(rr[a]), 0, nullptr);
+                pick64(w64, nt, unif(rr[a]), 0, bd);
+            }
+            int ix = ax[0].i0 + ft + kk[0], iy = ax[1].i0 + ft + kk[1], iz = ax[2].i0 + ft + kk[2];
+            sum_sigma += sig * vox(ix, iy, iz);
+            if (picks)
+                picks[k] = pack3d(wrapi(ix, V.nx, ADDR_CLAMP), wrapi(iy, V.ny, ADDR_CLAMP), wrapi(iz, V.nz, ADDR_CLAMP));
+        } else {
+            double fsig = 0.0, favg = 0.0;
+            for (int c = 0; c < nt; ++c) {
+                int iz = ax[2].i0 + ft + c;
+                double wz = kernel64(filter, ax[2].pos - (double)iz);
+                for (int b = 0; b < nt; ++b) {
+                    int iy = ax[1].i0 + ft + b;
+                    double wy = kernel64(filter, ax[1].pos - (double)iy);
+                    for (int a = 0; a < nt; ++a) {
+                        int ix = ax[0].i0 + ft + a;
+                        double w = kernel64(filter, ax[0].pos - (double)ix) * wy * wz;
+                        if (w == 0.0) continue;
+                        double sv = sig * vox(ix, iy, iz);
+                        fsig += w * sv;
+                        favg += w * std::exp(-sv * dt64);
+                    }
+                }
+            }
+            sum_sigma += fsig;
+            prod *= favg;
+            if (picks) picks[k] = NO_PICK;
+        }
+    }
+    if (mode == M_NTAP_AFTER) return prod;
+    return std::exp(-sum_sigma * dt64);
+}
+
+template <class F>
+void parallel_for(uint64_t n, int nthreads, F fn) {
+    if (nthreads <= 1 || n < 64) { for (uint64_t i = 0; i < n; ++i) fn(i); return; }
+    std::vector<std::thread> th;
+    uint64_t chunk = (n + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; ++t) {
+        uint64_t b = t * chunk, e = std::min(n, b + chunk);
+        if (b >= e) break;
+        th.emplace_back([=]() { for (uint64_t i = b; i < e; ++i) fn(i); });
+    }
+    for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+// ===================================================================== C entry points
+extern "C" {
+
+typedef struct {
+    int format, levels, address;
+    int width[16], height[16];
+    const void* data[16];
+    const uint8_t* normal[16];
+} orc_texture;
+
+void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
+
+double orc_kernel(int filter, double d) { return kernel64(filter, d); }
+double orc_kernel_bc(double B, double Cc, double d) { return k_bc(B, Cc, d); }
+double orc_kernel_keys(double a, double d) { return k_keys(a, d); }
+
+int orc_weights32(int filter, float t, float* w) { return weights32(filter, t, w); }
+
+// FP32 CDF pick (cls 0 = all taps, +1 positive taps, -1 negative taps)
+int orc_pick32(const float* w, int n, float xi, int cls) { return pick32(w, n, xi, cls, nullptr); }
+
+// FP64 CDF pick over an arbitrary array of up to 64 non-negative weights
+int orc_pick_array(const double* w, int n, double xi) {
+    double S = 0; for (int k = 0; k < n; ++k) S += std::fabs(w[k]);
+    double acc = 0;
+    for (int k = 0; k < n; ++k) { acc += std::fabs(w[k]); if (xi < acc / S) return k; }
+    return n - 1;
+}
+
+// general GGX + Lambert evaluation (f_hat including the cosine factor)
+void orc_ggx_eval(const double* n, const double* l, const double* v, double alpha,
+                  const double* rho, double F0, double* out) {
+    ggx_eval({n[0], n[1], n[2]}, {l[0], l[1], l[2]}, {v[0], v[1], v[2]}, alpha, rho, F0, out);
+}
+double orc_ggx_D(double alpha, double nh) { double a2 = alpha * alpha; return ggx_D(a2, nh, 1.0 - nh * nh); }
+double orc_smith_lambda(double alpha, double tan2) { return smith_lambda(alpha * alpha, tan2); }
+
+// the fixed-direction shade used by the texture path: rho[n*3], rough[n], nrm[n*3]
+void orc_shade_batch(uint64_t n, int smode, const double* rho, const double* rough,
+                     const double* nrm, double* out) {
+    for (uint64_t i = 0; i < n; ++i) {
+        Mat m;
+        for (int c = 0; c < 3; ++c) m.rho[c] = rho[3 * i + c];
+        m.rough = rough[i];
+        m.n = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+        shade(smode, m, out + 3 * i);
+    }
+}
+
+// decoded texel (for tests): rho[3], rough, n[3]
+void orc_fetch(const orc_texture* t, int lvl, int ix, int iy, double* out7) {
+    Tex T; std::memcpy(&T, t, sizeof(Tex));
+    Mat m = fetch(T, lvl, ix, iy);
+    out7[0] = m.rho[0]; out7[1] = m.rho[1]; out7[2] = m.rho[2]; out7[3] = m.rough;
+    out7[4] = m.n.x; out7[5] = m.n.y; out7[6] = m.n.z;
+}
+
+int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const float* v,
+                     const float* dudx, const float* dvdx, const float* dudy, const float* dvdy,
+                     int filter, int mode, int smode, uint32_t spp, uint64_t seed, uint32_t flags,
+                     double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist, int nthreads) {
+    if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 3 || mode < 0 || mode > 3) return 1;
+    if (tex->levels < 1 || tex->levels > 16) return 1;
+    if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
+    if (flags & FLAG_STRATIFIED) {
+        long k = std::lround(std::sqrt((double)spp));
+        if ((uint32_t)(k * k) != spp) return 1;
+    }
+    Tex T; std::memcpy(&T, tex, sizeof(Tex));
+    Queries Q{n, u, v, dudx, dvdx, dudy, dvdy};
+    Out O{rgb, picks, picks64, bdist};
+    parallel_for(n, nthreads, [&](uint64_t q) { run_query(T, Q, q, filter, mode, smode, spp, seed, flags, O); });
+    return 0;
+}
+
+int orc_march(int nx, int ny, int nz, const uint16_t* data, float sigma_scale, const float* cam,
+              uint32_t W, uint32_t H, uint32_t steps, int filter, int mode, uint32_t spp,
+              uint64_t seed, uint32_t flags, uint64_t pix_begin, uint64_t pix_count,
+              double* T, uint32_t* picks, double* bdist, int nthreads) {
+    if (!data || !cam || !T || spp == 0 || steps == 0) return 1;
+    if (!(filter == F_LINEAR || filter == F_BSPLINE) || mode == M_POSITIVIZED) return 1;
+    Vol V{nx, ny, nz, data, sigma_scale};
+    parallel_for(pix_count, nthreads, [&](uint64_t i) {
+        uint64_t pix = pix_begin + i;
+        double acc = 0.0, bd = 1e30;
+        for (uint32_t s = 0; s < spp; ++s) {
+            uint32_t* pk = picks ? picks + (i * spp + s) * steps : nullptr;
+            acc += march_sample(V, cam, W, H, steps, filter, mode, seed, flags, spp, pix, s, pk, &bd);
+        }
+        T[i] = acc / spp;
+        if (bdist) bdist[i] = bd;
+    });
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+"""Seeded synthetic inputs for stochastic texture filtering.
+
+This module is shared by the FP64 oracle (``oracle/``), the CUDA library's tests and
+``bench.py``.  It holds data recipes only -- fBm textures, box-filtered MIP chains,
+normal maps, query streams, a density volume and a camera -- and none of the
+filtering, sampling or shading arithmetic of the method.  Every array is a pure
+function of its seed (numpy PCG64 plus an integer lattice hash), so that the CPU and
+GPU sides see identical bytes.
+
+The paper's workloads are real assets (the Disney Cloud, Sec. 5 "Offline rendering";
+ambientCG materials, Sec. 5); these synthetic stand-ins reproduce their shapes and
+statistics:
+
+* ``texture_rgba32f``   -- 2-D RGBA FP32 texture, RGB ~ U[0,1), A = roughness in [0.05, 1].
+* ``material_rgba8``    -- fBm albedo+roughness RGBA8 and an RG8 tangent-space normal map
+                           derived from an fBm height, each with a full box-filtered MIP chain.
+* ``queries_uniform``   -- uv on the 2^-24 grid, optional isotropic screen-space
+                           derivatives whose LOD is uniform over a range of MIP levels.
+* ``volume_cloud``      -- fBm density cloud, thresholded so that a given fraction of
+                           voxels is exactly zero, stored as FP16.
+* ``camera_pinhole``    -- pinhole camera basis for the volume march.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+U32 = np.uint32
+
+
+# ---------------------------------------------------------------------------------
+# integer lattice hash (Wellons' "lowbias32" mixer) -- deterministic on any machine
+# ---------------------------------------------------------------------------------
+def _mix32(x: np.ndarray) -> np.ndarray:
+    x = x.astype(np.uint32, copy=True)
+    x ^= x >> U32(16)
+    x *= U32(0x7FEB352D)
+    x ^= x >> U32(15)
+    x *= U32(0x846CA68B)
+    x ^= x >> U32(16)
+    return x
+
+
+def _lattice(shape, seed: int, octave: int) -> np.ndarray:
+    """Uniform [0,1) values on an integer lattice, keyed by (seed, octave, index)."""
+    n = int(np.prod(shape))
+    idx = np.arange(n, dtype=np.uint64)
+    h = _mix32((idx & np.uint64(0xFFFFFFFF)).astype(np.uint32) ^ _mix32(np.array(
+        [seed * 0x9E3779B1 + octave * 0x85EBCA77], dtype=np.uint64).astype(np.uint32)))
+    h = _mix32(h ^ U32((seed * 31 + octave * 7919 + 12345) & 0xFFFFFFFF))
+    return (h.astype(np.float64) * (1.0 / 4294967296.0)).reshape(shape)
+
+
+def _interp_axis(arr: np.ndarray, axis: int, period: int, size: int, dtype) -> np.ndarray:
+    """Periodic smoothstep interpolation of a lattice axis of length ``period`` up to ``size``."""
+    s = (np.arange(size, dtype=np.float64) + 0.5) * (period / size)
+    i0 = np.floor(s).astype(np.int64)
+    f = s - i0
+    f = f * f * (3.0 - 2.0 * f)
+    i0 %= period
+    i1 = (i0 + 1) % period
+    a0 = np.take(arr, i0, axis=axis)
+    a1 = np.take(arr, i1, axis=axis)
+    shp = [1] * arr.ndim
+    shp[axis] = size
+    f = f.reshape(shp).astype(dtype)
+    return (a0 * (1 - f) + a1 * f).astype(dtype)
+
+
+def fbm2d(size: int, octaves: int, base: int, seed: int, gain: float = 0.5) -> np.ndarray:
+    """Periodic 2-D value-noise fBm in [0,1], lacunarity 2 (float64, shape (size, size))."""
+    out = np.zeros((size, size), dtype=np.float64)
+    amp, norm = 1.0, 0.0
+    for o in range(octaves):
+        p = min(base << o, size)
+        lat = _lattice((p, p), seed, o)
+        r = _interp_axis(lat, 1, p, size, np.float64)   # (p, size)
+        r = _interp_axis(r, 0, p, size, np.float64)     # (size, size)
+        out += amp * r
+        norm += amp
+        amp *= gain
+    return out / norm
+
+
+def fbm3d(size: int, octaves: int, base: int, seed: int, gain: float = 0.5) -> np.ndarray:
+    """Periodic 3-D value-noise fBm in [0,1] (float32, shape (size, size, size) as z, y, x)."""
+    out = np.zeros((size, size, size), dtype=np.float32)
+    amp, norm = 1.0, 0.0
+    for o in range(octaves):
+        p = min(base << o, size)
+        lat = _lattice((p, p, p), seed, o).astype(np.float32)
+        r = _interp_axis(lat, 2, p, size, np.float32)
+        r = _interp_axis(r, 1, p, size, np.float32)
+        for z0 in range(0, size, 64):                  # bounded temporaries along z
+            s = (np.arange(z0, min(size, z0 + 64), dtype=np.float64) + 0.5) * (p / size)
+            i0 = np.floor(s).astype(np.int64)
+            f = s - i0
+            f = (f * f * (3.0 - 2.0 * f)).astype(np.float32)[:, None, None]
+            i0 %= p
+            zz = r[i0] * (1 - f) + r[(i0 + 1) % p] * f
+            out[z0:z0 + zz.shape[0]] += np.float32(amp) * zz
+        norm += amp
+        amp *= gain
+    out /= np.float32(norm)
+    return out
+
+
+def _rne_u8(x: np.ndarray) -> np.ndarray:
+    return np.clip(np.rint(x), 0, 255).astype(np.uint8)
+
+
+def box_mips_u8(level0: np.ndarray) -> list[np.ndarray]:
+    """Full box-filtered MIP chain of a (H, W, C) uint8 image, round-half-even averages."""
+    levels = [level0]
+    cur = level0.astype(np.float64)
+    while cur.shape[0] > 1 or cur.shape[1] > 1:
+        h, w = cur.shape[:2]
+        if h > 1:
+            cur = 0.5 * (cur[0::2] + cur[1::2])
+        if w > 1:
+            cur = 0.5 * (cur[:, 0::2] + cur[:, 1::2])
+        q = _rne_u8(cur)
+        levels.append(q)
+        cur = q.astype(np.float64)
+    return levels
+
+
+# ---------------------------------------------------------------------------------
+# 2-D textures
+# ---------------------------------------------------------------------------------
+def texture_rgba32f(size: int = 256, seed: int = 101) -> np.ndarray:
+    """(size, size, 4) float32: RGB ~ U[0,1), A = 0.05 + 0.95 U[0,1) (roughness)."""
+    rng = np.random.default_rng(seed)
+    t = rng.random((size, size, 4), dtype=np.float64)
+    t[..., 3] = 0.05 + 0.95 * t[..., 3]
+    return t.astype(np.float32)
+
+
+@dataclass
+class Material:
+    albedo_rough: list      # per level (H, W, 4) uint8: albedo RGB, roughness byte
+    normal: list            # per level (H, W, 2) uint8: tangent-space normal XY
+    height: np.ndarray      # (H, W) float64 fBm height at level 0 (kept for neural targets)
+
+
+def material_rgba8(size: int = 4096, seed: int = 102, octaves: int = 8,
+                   base: int = 8, mips: bool = True) -> Material:
+    """fBm albedo+roughness (RGBA8) and normal map (RG8) with full MIP chains."""
+    height = fbm2d(size, octaves, base, seed * 17 + 1)
+    cr = fbm2d(size, octaves, base, seed * 17 + 2)
+    cg = fbm2d(size, octaves, base, seed * 17 + 3)
+    ro = fbm2d(size, octaves, base, seed * 17 + 4)
+    ar = np.empty((size, size, 4), dtype=np.uint8)
+    # warm stone-like palette; contrast stretched around the fBm mean of ~0.5
+    ar[..., 0] = _rne_u8(255 * np.clip(0.55 + 1.6 * (height - 0.5) + 0.4 * (cr - 0.5), 0, 1))
+    ar[..., 1] = _rne_u8(255 * np.clip(0.45 + 1.6 * (height - 0.5) + 0.4 * (cg - 0.5), 0, 1))
+    ar[..., 2] = _rne_u8(255 * np.clip(0.35 + 1.2 * (height - 0.5), 0, 1))
+    ar[..., 3] = _rne_u8(255 * np.clip(0.5 + 2.5 * (ro - 0.5), 0, 1))
+    # normal from the height's periodic central differences, slope std fixed at 0.35
+    gx = 0.5 * (np.roll(height, -1, axis=1) - np.roll(height, 1, axis=1))
+    gy = 0.5 * (np.roll(height, -1, axis=0) - np.roll(height, 1, axis=0))
+    k = 0.35 / max(1e-12, float(np.sqrt(0.5 * (gx.var() + gy.var()))))
+    nx, ny, nz = -k * gx, -k * gy, np.ones_like(gx)
+    inv = 1.0 / np.sqrt(nx * nx + ny * ny + nz * nz)
+    nrm = np.empty((size, size, 2), dtype=np.uint8)
+    nrm[..., 0] = _rne_u8((nx * inv * 0.5 + 0.5) * 255)
+    nrm[..., 1] = _rne_u8((ny * inv * 0.5 + 0.5) * 255)
+    if mips:
+        return Material(box_mips_u8(ar), box_mips_u8(nrm), height)
+    return Material([ar], [nrm], height)
+
+
+# ---------------------------------------------------------------------------------
+# queries
+# ---------------------------------------------------------------------------------
+@dataclass
+class Queries:
+    u: np.ndarray
+    v: np.ndarray
+    dudx: np.ndarray | None = None
+    dvdx: np.ndarray | None = None
+    dudy: np.ndarray | None = None
+    dvdy: np.ndarray | None = None
+
+    @property
+    def n(self) -> int:
+        return int(self.u.shape[0])
+
+    def has_derivs(self) -> bool:
+        return self.dudx is not None
+
+    def subset(self, idx) -> "Queries":
+        f = (lambda a: None if a is None else np.ascontiguousarray(a[idx]))
+        return Queries(f(self.u), f(self.v), f(self.dudx), f(self.dvdx), f(self.dudy), f(self.dvdy))
+
+
+def queries_uniform(n: int, seed: int, res: int | None = None, lod_range: float = 0.0,
+                    const_derivs: tuple | None = None) -> Queries:
+    """uv uniform on the 2^-24 grid.
+
+    ``lod_range > 0``: isotropic derivatives with |ddx| = |ddy| = 2^lam / res,
+    lam ~ U[0, lod_range), random rotation.  ``const_derivs=(dudx, dvdx, dudy, dvdy)``:
+    the same derivatives for every query.  Neither: no derivatives.
+    """
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, 1 << 24, size=(2, n), dtype=np.int64)
+    u = (k[0].astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    v = (k[1].astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    if lod_range > 0:
+        assert res is not None
+        lam = lod_range * rng.random(n)
+        th = 2 * math.pi * rng.random(n)
+        ln = np.exp2(lam) / res
+        c, s = np.cos(th) * ln, np.sin(th) * ln
+        return Queries(u, v, c.astype(np.float32), s.astype(np.float32),
+                       (-s).astype(np.float32), c.astype(np.float32))
+    if const_derivs is not None:
+        d = [np.full(n, x, dtype=np.float32) for x in const_derivs]
+        return Queries(u, v, *d)
+    return Queries(u, v)
+
+
+# ---------------------------------------------------------------------------------
+# volume and camera
+# ---------------------------------------------------------------------------------
+def volume_cloud(size: int = 512, seed: int = 103, zero_frac: float = 0.9,
+                 octaves: int = 6, base: int = 4) -> np.ndarray:
+    """(size,size,size) float16 density (z, y, x), ``zero_frac`` of voxels exactly 0, max 1."""
+    d = fbm3d(size, octaves, base, seed)
+    c = (np.arange(size, dtype=np.float32) + 0.5) / size - 0.5
+    r2 = c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2
+    env = np.clip(1.0 - np.sqrt(r2) / np.float32(0.48), 0.0, 1.0).astype(np.float32)
+    d *= np.sqrt(env)
+    del r2, env
+    flat = d.reshape(-1)
+    kth = int(zero_frac * flat.size)
+    thr = np.partition(flat.copy(), kth)[kth] if kth < flat.size else flat.max()
+    mx = float(flat.max())
+    out = np.where(d > thr, (d - thr) / np.float32(max(mx - thr, 1e-12)), np.float32(0))
+    return out.astype(np.float16)
+
+
+@dataclass
+class Camera:
+    eye: tuple
+    fwd: tuple
+    right: tuple     # screen +x direction scaled by tan(vfov/2) * aspect
+    up: tuple        # screen +y direction scaled by tan(vfov/2)
+
+    def as_array(self) -> np.ndarray:
+        return np.array([*self.eye, *self.fwd, *self.right, *self.up], dtype=np.float32)
+
+
+def camera_pinhole(width: int, height: int, eye=(0.5, 0.5, -1.2), look=(0.5, 0.5, 0.5),
+                   up=(0.0, 1.0, 0.0), vfov_deg: float = 45.0) -> Camera:
+    e, l, u = (np.asarray(x, dtype=np.float64) for x in (eye, look, up))
+    f = l - e
+    f /= np.linalg.norm(f)
+    r = np.cross(u, f)
+    r /= np.linalg.norm(r)
+    uu = np.cross(f, r)
+    th = math.tan(math.radians(vfov_deg) * 0.5)
+    asp = width / height
+    f32 = lambda a: tuple(float(np.float32(x)) for x in a)
+    return Camera(f32(e), f32(f), f32(r * th * asp), f32(uu * th))
