@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark: shaded texture lookups/s of stochastic 1-tap filtering vs N-tap filtering.
+
+Workload (the 2-D mipmapped material): a 4096^2 RGBA8 albedo+roughness texture and an
+RG8 normal map (fBm, full 13-level MIP chains), 2^24 queries per GPU with uv uniform and
+isotropic screen-space derivatives whose LOD is uniform over 8 MIP levels.  One step =
+the stochastic filter+shade (GGX + Lambert) of every query at 8 spp with each of the three
+filters (trilinear, bicubic B-spline, Mitchell BC(1/3,1/3) with sign-carried negative
+lobes): 3 x 2^24 x 8 shaded lookups.  Inputs (384 MiB of queries, 171 MiB of texels) are
+larger than L2, so no flush is needed between steps.
+
+value   = shaded lookups/s over all ranks (kernel time, inputs resident in HBM)
+e2e     = the same step through stf_filter_shade_host from pinned host buffers
+equal_rmse / volume = N-tap comparators and the equal-RMSE speedups (rank 0, N = 1)
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import stf_synth as synth  # noqa: E402
+
+TEX_RES = 4096
+LOD_RANGE = 8.0
+SPP = 8
+FILTERS = ("linear", "bspline", "mitchell")
+METRIC = "shaded texture lookups/s, stochastic 1-tap vs N-tap, at equal RMSE vs FP64"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self) -> dict:
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ helpers
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured", "sm_max_mhz": d.get("sm_max_mhz", 2032.0)}
+    return {"hbm_gbs": 6400.0, "src": "fallback", "sm_max_mhz": 2032.0}
+
+
+def make_queries(n: int, rank: int):
+    return synth.queries_uniform(n, 1 + rank, res=TEX_RES, lod_range=LOD_RANGE)
+
+
+def cpu_baseline(material, seconds: float = 12.0) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (host cores)."""
+    import oracle
+    otex = oracle.Texture(material.albedo_rough, material.normal)
+    cores = oracle.nthreads_default()
+    n = 1 << 10
+    while True:
+        q = make_queries(n, 0)
+        t0 = time.perf_counter()
+        for f in FILTERS:
+            oracle.filter_shade(otex, q, f, "stochastic", "ggx", SPP, 1, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= (1 << 22):
+            break
+        n = min(1 << 22, int(n * max(2.0, seconds / 4 / max(dt, 1e-3))))
+        n = 1 << int(math.log2(n))
+    units = n * SPP * len(FILTERS)
+    return {"value": units / dt, "unit": "lookups/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} queries x {SPP} spp x {len(FILTERS)} filters (stochastic, FP64 oracle), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2407_06107_b300 as stf
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    material = synth.material_rgba8(TEX_RES, 102)
+    tex = ctx.create_texture(material.albedo_rough, material.normal)
+    nq = args.queries
+    q = make_queries(nq, rank)
+    id_base = rank * nq
+    t = lambda a: torch.from_numpy(a).to(dev)
+    u, v = t(q.u), t(q.v)
+    d = [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]
+    out = [torch.empty(nq, dtype=torch.float32, device=dev) for _ in range(3)]
+    stream = torch.cuda.current_stream(dev)
+
+    def launch(f, mode="stochastic", spp=SPP, n=None, outp=None):
+        if n is None:
+            ctx.filter_shade(tex, u, v, d, f, mode, "ggx", spp, 1, 0, id_base=id_base, out=outp or out)
+        else:
+            ctx.filter_shade(tex, u[:n], v[:n], [x[:n] for x in d], f, mode, "ggx", spp, 1, 0,
+                             id_base=id_base, out=outp)
+
+    for _ in range(args.warmup):
+        for f in FILTERS:
+            launch(f)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(FILTERS) + 1)] for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            for i, f in enumerate(FILTERS):
+                launch(f)
+                ev[k][i + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(len(FILTERS))] for k in range(args.steps)])
+    ms_total = float(ev[0][0].elapsed_time(ev[-1][-1]))
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    units_step = nq * SPP * len(FILTERS)
+    value = world * units_step * args.steps / (ms_total / 1e3)
+    clocks = clk.summary()
+
+    # ---- end to end: pinned host buffers through stf_filter_shade_host
+    hq = [torch.from_numpy(a).pin_memory() for a in (q.u, q.v, q.dudx, q.dvdx, q.dudy, q.dvdy)]
+    hout = [torch.empty(nq, dtype=torch.float32).pin_memory() for _ in range(3)]
+
+    def e2e_step():
+        for f in FILTERS:
+            ctx.filter_shade_host(tex, hq[0], hq[1], hq[2:], f, "stochastic", "ggx", SPP, 1, 0,
+                                  id_base=id_base, out=hout)
+    e2e_step()
+    torch.cuda.synchronize()
+    ke = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / ke
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * units_step / e2e_s, "unit": "lookups/s",
+           "h2d_bytes_per_step": len(FILTERS) * nq * 24, "d2h_bytes_per_step": len(FILTERS) * nq * 12}
+
+    # ---- roofline of the dominant kernel
+    mean = per.mean(0)
+    dom = int(np.argmax(mean))
+    pk = peaks()
+    units_launch = nq * SPP
+    alg_bytes = units_launch * 8 + nq * (24 + 12)    # one 8-B texel per lookup + query in / rgb out
+    achieved = alg_bytes / (mean[dom] / 1e3) / 1e9
+    traffic = load_traffic(FILTERS[dom], "stochastic")
+    roof = {"kernel": f"k_filter_shade<{FILTERS[dom]}, stochastic>", "bound": "hbm", "achieved": achieved,
+            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"],
+            "traffic": traffic, "ms_per_launch": float(mean[dom])}
+
+    line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2-D mipmapped material: 4096^2 RGBA8+RG8 fBm with MIPs, 2^24 queries/GPU, "
+                                   "LOD uniform over 8 levels, stochastic trilinear+bicubic B-spline+Mitchell, 8 spp, GGX",
+                       "queries_per_gpu": nq, "spp": SPP, "filters": list(FILTERS), "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"query-sharded x{world}"},
+            "ms_per_launch": {f: float(mean[i]) for i, f in enumerate(FILTERS)},
+            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * len(FILTERS), "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
+        line["volume"] = volume_block(ctx, dev, args)
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(material)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def load_traffic(filter_name: str, mode: str):
+    """dram bytes per launch from the committed ncu summary, if it covers this kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d.get(f"{filter_name}/{mode}")
+
+
+def _time_launch(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
+    """RMSE vs the exact filter-after reference (stratified 16x16 over the pixel footprint,
+    computed by the exact N-tap filter-after kernel, itself checked against the FP64 oracle
+    in the tests), for the bicubic B-spline; then the equal-RMSE speedup over N-tap
+    filter-before at 8 spp."""
+    import torch
+    res = {}
+    sub = lambda x: x[:nsub]
+    ds = [sub(x) for x in d]
+    mk = lambda: [torch.empty(nsub, dtype=torch.float32, device=dev) for _ in range(3)]
+    for filt in ("bspline", "mitchell"):
+        ref = mk()
+        ctx.filter_shade(tex, sub(u), sub(v), ds, filt, "ntap_after", "ggx", 256, 1, 1, out=ref)
+        R = torch.stack(ref, 1).double()
+
+        def rmse(mode, spp, seed=7):
+            o = mk()
+            ctx.filter_shade(tex, sub(u), sub(v), ds, filt, mode, "ggx", spp, seed, 0, out=o)
+            return float(((torch.stack(o, 1).double() - R) ** 2).mean().sqrt())
+        r_before = rmse("ntap_before", 8)
+        r_after = rmse("ntap_after", 8)
+        curve = {s: rmse("stochastic", s) for s in (1, 2, 4, 8, 16, 32, 64)}
+        s_star = next((s for s in sorted(curve) if curve[s] <= r_before), None)
+        nfull = u.shape[0]
+        outf = [torch.empty(nfull, dtype=torch.float32, device=dev) for _ in range(3)]
+        t_before = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "ntap_before", "ggx", 8, 1, 0, out=outf))
+        t_s8 = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", 8, 1, 0, out=outf))
+        t_star = (_time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", s_star, 1, 0, out=outf))
+                  if s_star else None)
+        res[filt] = {
+            "rmse_ntap_before_8spp": r_before, "rmse_ntap_after_8spp": r_after,
+            "rmse_stochastic": {str(k): v for k, v in curve.items()},
+            "mse_increase_stochastic_vs_after_8spp": curve[8] ** 2 / r_after ** 2 - 1.0,
+            "ntap_taps": 32, "ms_ntap_before_8spp": t_before, "ms_stochastic_8spp": t_s8,
+            "ntap_before_lookups_per_s": nfull * 8 / (t_before / 1e3),
+            "stochastic_lookups_per_s": nfull * 8 / (t_s8 / 1e3),
+            "equal_spp_speedup": t_before / t_s8, "s_star": s_star,
+            "equal_rmse_speedup": (t_before / t_star) if t_star else None,
+        }
+    return res
+
+
+def volume_block(ctx, dev, args):
+    """512^3 FP16 cloud at 1920x1080, 128 steps: tricubic (64-tap) and trilinear (8-tap)
+    N-tap filter-before vs stochastic 1-tap, equal-RMSE vs the exact filter-after reference."""
+    import torch
+    W, H, steps = 1920, 1080, 128
+    vol = synth.volume_cloud(512, 103)
+    vh = ctx.create_volume(vol, 20.0)
+    cam = synth.camera_pinhole(W, H).as_array()
+    n = W * H
+    band_begin, band = (H // 2 - 32) * W, 64 * W       # 64 central rows for the RMSE
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    sub = torch.empty(band, dtype=torch.float32, device=dev)
+    res = {}
+    for filt, taps in (("bspline", 64), ("linear", 8)):
+        ref = torch.empty(band, dtype=torch.float32, device=dev)
+        # exact filter-after reference, 4x4 stratified sub-pixel jitter
+        ctx.march_volume(vh, cam, W, H, steps, filt, "ntap_after", spp=16, seed=1, flags=1,
+                         pix_begin=band_begin, pix_count=band, out=ref)
+        R = ref.double()
+
+        def rmse(mode, spp):
+            ctx.march_volume(vh, cam, W, H, steps, filt, mode, spp=spp, seed=5, pix_begin=band_begin,
+                             pix_count=band, out=sub)
+            return float(((sub.double() - R) ** 2).mean().sqrt())
+        r_before = rmse("ntap_before", 8)
+        curve = {s: rmse("stochastic", s) for s in (1, 2, 4, 8, 16)}
+        s_star = next((s for s in sorted(curve) if curve[s] <= r_before), None)
+        t_before = _time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "ntap_before", spp=8, seed=5, out=out), 2)
+        t_s8 = _time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "stochastic", spp=8, seed=5, out=out), 2)
+        t_star = (_time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "stochastic", spp=s_star, seed=5, out=out), 2)
+                  if s_star else None)
+        res[filt] = {"taps": taps, "rmse_ntap_before_8spp": r_before,
+                     "rmse_stochastic": {str(k): v for k, v in curve.items()}, "s_star": s_star,
+                     "ms_ntap_before_8spp": t_before, "ms_stochastic_8spp": t_s8,
+                     "ntap_step_lookups_per_s": n * 8 * steps / (t_before / 1e3),
+                     "stochastic_step_lookups_per_s": n * 8 * steps / (t_s8 / 1e3),
+                     "equal_spp_speedup": t_before / t_s8,
+                     "equal_rmse_speedup": (t_before / t_star) if t_star else None}
+    ctx.destroy_volume(vh)
+    return res
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    material = synth.material_rgba8(TEX_RES, 102)
+    otex = oracle.Texture(material.albedo_rough, material.normal)
+    cores = oracle.nthreads_default()
+    n = args.ref_queries
+    q = make_queries(n, 0)
+
+    def step():
+        for f in FILTERS:
+            oracle.filter_shade(otex, q, f, "stochastic", "ggx", SPP, 1, nthreads=cores)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    units = n * SPP * len(FILTERS)
+    v = units / dt
+    sample = f"{n} queries x {SPP} spp x {len(FILTERS)} filters per step (FP64 oracle, stochastic)"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "lookups/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2-D mipmapped material: 4096^2 RGBA8+RG8 fBm with MIPs, LOD uniform over 8 levels, "
+                                   "stochastic trilinear+bicubic B-spline+Mitchell, 8 spp, GGX",
+                       "queries_per_step": n, "spp": SPP, "filters": list(FILTERS)},
+            "cpu_baseline": {"value": v, "unit": "lookups/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "lookups/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--queries", type=int, default=1 << 24)
+    ap.add_argument("--ref-queries", type=int, default=1 << 13)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

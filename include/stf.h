@@ -1,0 +1,175 @@
+/* stf.h -- C ABI of libstf: stochastic texture filtering (filter-after-shading) on B300.
+ *
+ * Method: Pharr, Wronski, Salvi, Fajardo, "Filtering After Shading With Stochastic
+ * Texture Filtering" (2024).  For every query the library either
+ *   - importance-samples ONE texel from a separable filter and shades it (the
+ *     stochastic estimator of Eq. stochastic-sum applied to Eq. filtering-after-shading,
+ *     Sec. 4 "Stochastic Texture Filtering", Sec. 4.1 FRS), or
+ *   - evaluates the conventional N-tap filter-before-shading sum
+ *     (Eq. filter-before-shading), or
+ *   - evaluates the exact N-tap filter-after-shading sum (Eq. filtering-after-shading).
+ *
+ * Conventions for every entry point
+ *   - No exception crosses the ABI; every call returns an stf_status.  Host-side argument
+ *     validation is synchronous: on error nothing is enqueued and outputs are untouched.
+ *   - Work is enqueued asynchronously on the context's CUDA stream.  Device-detected
+ *     problems (NaN inputs, out-of-range table ids) set bits of a device status word,
+ *     read and cleared by stf_get_device_status().
+ *   - Ownership: the caller owns query, derivative and output buffers (device pointers,
+ *     e.g. torch tensors, 4-byte aligned; 16-byte alignment enables vector loads).  The
+ *     library owns textures and volumes: it COPIES the data in at creation and frees it at
+ *     destruction.
+ *   - A context is not thread-safe; use one per host thread.
+ *   - Query ids are 64-bit (they key the Philox counter): the id of query i of a call is
+ *     queries->id_base + i, so that shards of one batch draw the same numbers as the whole.
+ */
+#ifndef STF_H
+#define STF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stf_ctx_s* stf_ctx;
+typedef uint64_t stf_tex;   /* texture handle, 0 is never valid */
+typedef uint64_t stf_vol;   /* volume handle, 0 is never valid */
+
+typedef enum {
+    STF_OK = 0,
+    STF_ERR_INVALID_ARG = 1,    /* null pointer, size/enum out of range, misalignment    */
+    STF_ERR_BAD_HANDLE = 2,     /* unknown or destroyed texture / volume handle          */
+    STF_ERR_OOM = 3,            /* device allocation failed                              */
+    STF_ERR_CUDA = 4,           /* a CUDA runtime call failed (see stf_last_error)       */
+    STF_ERR_UNSUPPORTED = 5,    /* valid but unsupported combination (e.g. positivized
+                                   with a non-negative filter)                          */
+    STF_ERR_DEVICE_STATUS = 6,  /* the device status word had bits set                  */
+    STF_ERR_TIMEOUT = 7         /* a bounded device wait gave up                         */
+} stf_status;
+
+typedef enum {
+    STF_FMT_RGBA32F = 0,  /* RGB albedo, A = roughness (GGX alpha), 16 B/texel            */
+    STF_FMT_RGBA8 = 1,    /* UNORM albedo RGB, A byte -> roughness 0.05 + 0.95 a/255       */
+    STF_FMT_RG8 = 2,      /* tangent-space normal XY (UNORM, z reconstructed)              */
+    STF_FMT_R16F = 3      /* FP16 density (volumes)                                       */
+} stf_format;
+
+/* 1-D reconstruction kernels, applied separably (supplement "Filter Kernels").
+ * With MIP levels and derivatives, every filter also blends the two nearest levels
+ * linearly (trilinear for STF_FILTER_LINEAR). */
+typedef enum {
+    STF_FILTER_LINEAR = 0,       /* tent K1: bilinear / trilinear, 2 taps per axis        */
+    STF_FILTER_BSPLINE = 1,      /* cubic B-spline K_bs, 4 taps per axis                  */
+    STF_FILTER_CATMULL_ROM = 2,  /* Keys cubic K3 with a = -1/2, 4 taps, negative lobes   */
+    STF_FILTER_MITCHELL = 3      /* Mitchell-Netravali BC(1/3,1/3), 4 taps, neg. lobes    */
+} stf_filter;
+
+typedef enum {
+    STF_MODE_NTAP_BEFORE = 0,           /* shade(sum_i w_i t_i)             Eq. filter-before-shading */
+    STF_MODE_NTAP_AFTER = 1,            /* sum_i w_i shade(t_i) (exact)     Eq. filtering-after-shading */
+    STF_MODE_STOCHASTIC = 2,            /* one texel drawn ~|w|, times sign * sum|w|  Eq. stochastic-sum */
+    STF_MODE_STOCHASTIC_POSITIVIZED = 3 /* one texel from each sign set (Sec. 2.2 positivization) */
+} stf_mode;
+
+typedef enum {
+    STF_SHADE_GGX_LAMBERT = 0,  /* f_hat = [rho/pi + D G F/(4 nl nv)] nl, fixed l, v      */
+    STF_SHADE_LINEAR = 1        /* identity on albedo (affine shade, Sec. 3)               */
+} stf_shade;
+
+typedef enum { STF_ADDRESS_WRAP = 0, STF_ADDRESS_CLAMP = 1 } stf_address;
+
+/* flags */
+#define STF_FLAG_STRATIFIED 1u  /* jitter on a sqrt(spp) x sqrt(spp) grid (spp must be a square) */
+
+/* device status bits */
+#define STF_DEV_NAN_INPUT 1u
+#define STF_DEV_BAD_INDEX 2u
+
+#define STF_MAX_LEVELS 16
+
+typedef struct {
+    uint32_t width, height;        /* level 0 size, 1 .. 16384                              */
+    uint32_t num_levels;           /* 1 .. 16; level l is max(1, w >> l) x max(1, h >> l)   */
+    stf_format format;             /* STF_FMT_RGBA32F or STF_FMT_RGBA8                       */
+    stf_address address;
+    const void* const* level_data; /* num_levels pointers, row-major (y then x), tightly packed */
+    const void* const* normal_data;/* nullable; num_levels RG8 pointers (RGBA8 only)        */
+    int data_on_device;            /* 0: host pointers; 1: device pointers                  */
+} stf_texture_desc;
+
+typedef struct {
+    uint64_t n;          /* number of queries (0 is a valid no-op)                          */
+    uint64_t id_base;    /* Philox id of query 0                                            */
+    const float* u;      /* [n] texture coordinates, any real value (wrapped / clamped)     */
+    const float* v;      /* [n]                                                             */
+} stf_queries;
+
+typedef struct {         /* screen-space derivatives of (u, v), [n] each                    */
+    const float* dudx;
+    const float* dvdx;
+    const float* dudy;
+    const float* dvdy;
+} stf_derivs;
+
+typedef struct {
+    float* r;            /* [n] mean shaded value over spp, SoA                             */
+    float* g;
+    float* b;
+    uint32_t* picks;     /* nullable: [n][spp][2] selected texels (lvl<<28 | iy<<14 | ix),
+                            slot 1 = negative sample of positivization, 0xFFFFFFFF = none   */
+} stf_output;
+
+/* ---- context --------------------------------------------------------------------------- */
+/* device: CUDA ordinal; cuda_stream: cudaStream_t or NULL for the legacy default stream. */
+stf_status stf_create(int device, void* cuda_stream, stf_ctx* out);
+stf_status stf_destroy(stf_ctx ctx);
+stf_status stf_set_stream(stf_ctx ctx, void* cuda_stream);
+stf_status stf_synchronize(stf_ctx ctx);
+/* Reads and clears the device status word (synchronises the stream).  Returns
+ * STF_ERR_DEVICE_STATUS if any bit was set. */
+stf_status stf_get_device_status(stf_ctx ctx, uint32_t* flags);
+const char* stf_status_string(stf_status s);
+const char* stf_last_error(stf_ctx ctx);
+
+/* ---- textures (Eq. texture-definition: texels on a uniform grid, Sec. 2.1) ------------ */
+stf_status stf_create_texture(stf_ctx ctx, const stf_texture_desc* desc, stf_tex* out);
+stf_status stf_destroy_texture(stf_ctx ctx, stf_tex tex);
+
+/* ---- 2-D filter + shade ---------------------------------------------------------------- */
+/* For every query: spp samples, each = screen-space jitter inside the derivative
+ * footprint (Sec. 4.2.1), stochastic MIP level (or linear blend for N-tap modes), the
+ * filter in `mode`, shade; out = mean over samples.  derivs == NULL: no jitter, level 0.
+ * spp >= 1; positivized mode needs a signed filter (else STF_ERR_UNSUPPORTED). */
+stf_status stf_filter_shade(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
+                            stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
+                            uint64_t seed, uint32_t flags, const stf_output* out);
+
+/* Same computation from HOST buffers (u, v, derivs, r, g, b, picks all host memory):
+ * copies the inputs to library-owned device staging memory, runs, copies the results back
+ * and synchronises.  Pinned host memory gives full PCIe bandwidth. */
+stf_status stf_filter_shade_host(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
+                                 stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
+                                 uint64_t seed, uint32_t flags, const stf_output* out);
+
+/* ---- 3-D volume march (Sec. 5 "Offline rendering", transmittance exp(-sigma dt)) ------- */
+/* data: nz*ny*nx FP16 densities (x fastest); sigma = sigma_scale * density. */
+stf_status stf_create_volume(stf_ctx ctx, uint32_t nx, uint32_t ny, uint32_t nz, stf_format format,
+                             float sigma_scale, const void* data, int data_on_device, stf_vol* out);
+stf_status stf_destroy_volume(stf_ctx ctx, stf_vol vol);
+
+/* cam: 12 floats = eye[3], forward[3], right[3] (scaled by tan(fov/2)*aspect), up[3]
+ * (scaled by tan(fov/2)).  Pixels pix_begin .. pix_begin+pix_count-1 of a width x height
+ * image (row-major); out_T[pix_count] = mean transmittance over spp.  filter: LINEAR
+ * (trilinear, 8 taps) or BSPLINE (tricubic, 64 taps); mode: NTAP_BEFORE, NTAP_AFTER or
+ * STOCHASTIC.  out_picks nullable: [pix_count][spp][steps] voxels (z<<20 | y<<10 | x). */
+stf_status stf_march_volume(stf_ctx ctx, stf_vol vol, const float* cam, uint32_t width,
+                            uint32_t height, uint32_t steps, stf_filter filter, stf_mode mode,
+                            uint32_t spp, uint64_t seed, uint32_t flags, uint64_t pix_begin,
+                            uint64_t pix_count, float* out_T, uint32_t* out_picks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STF_H */

@@ -74,11 +74,11 @@ def lib():
         L.orc_smith_lambda.restype = C.c_double
         L.orc_shade_batch.argtypes = [C.c_uint64, C.c_int, P, P, P, P]
         L.orc_fetch.argtypes = [C.POINTER(_Tex), C.c_int, C.c_int, C.c_int, P]
-        L.orc_filter_shade.argtypes = [C.POINTER(_Tex), C.c_uint64] + [P] * 6 + [
+        L.orc_filter_shade.argtypes = [C.POINTER(_Tex), C.c_uint64] + [P] * 7 + [
             C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, C.c_int]
         L.orc_march.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_float, P, C.c_uint32, C.c_uint32,
                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
-                                C.c_uint64, C.c_uint64, P, P, P, C.c_int]
+                                C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
         _lib = L
     return _lib
 
@@ -195,7 +195,8 @@ class FilterResult:
 
 def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", spp: int = 1,
                  seed: int = 1, flags: int = 0, want_picks: bool = False,
-                 nthreads: int | None = None) -> FilterResult:
+                 nthreads: int | None = None, ids=None) -> FilterResult:
+    """Evaluate queries q; the Philox id of query i is ids[i] (default: i)."""
     n = q.n
     rgb = np.zeros((n, 3))
     picks = np.zeros((n, spp, 2), dtype=np.uint32) if want_picks else None
@@ -204,7 +205,8 @@ def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", sp
     t = tex._struct()
     arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None
             for a in (q.u, q.v, q.dudx, q.dvdx, q.dudy, q.dvdy)]
-    rc = lib().orc_filter_shade(C.byref(t), n, *[_p(a) for a in arrs], FILTERS[filter], MODES[mode],
+    ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint64)
+    rc = lib().orc_filter_shade(C.byref(t), n, *[_p(a) for a in arrs], _p(ids), FILTERS[filter], MODES[mode],
                                 SHADES[shade], spp, seed, flags, _p(rgb), _p(picks), _p(picks64),
                                 _p(bd), nthreads or nthreads_default())
     if rc != 0:
@@ -222,17 +224,22 @@ class MarchResult:
 def march(vol: np.ndarray, sigma_scale: float, cam: np.ndarray, width: int, height: int,
           steps: int, filter: str, mode: str, spp: int, seed: int, flags: int = 0,
           pix_begin: int = 0, pix_count: int | None = None, want_picks: bool = False,
-          nthreads: int | None = None) -> MarchResult:
+          nthreads: int | None = None, pix_ids=None) -> MarchResult:
+    """Pixels pix_begin.. (or the explicit list pix_ids) of a width x height image."""
     vol = np.ascontiguousarray(vol, dtype=np.float16)
     nz, ny, nx = vol.shape
-    cnt = width * height - pix_begin if pix_count is None else pix_count
+    if pix_ids is not None:
+        pix_ids = np.ascontiguousarray(pix_ids, dtype=np.uint64)
+        cnt = len(pix_ids)
+    else:
+        cnt = width * height - pix_begin if pix_count is None else pix_count
     T = np.zeros(cnt)
     bd = np.zeros(cnt)
     picks = np.zeros((cnt, spp, steps), dtype=np.uint32) if want_picks else None
     cam = np.ascontiguousarray(cam, dtype=np.float32)
     rc = lib().orc_march(nx, ny, nz, _p(vol.view(np.uint16)), float(sigma_scale), _p(cam), width,
                          height, steps, FILTERS[filter], MODES[mode], spp, seed, flags, pix_begin,
-                         cnt, _p(T), _p(picks), _p(bd), nthreads or nthreads_default())
+                         cnt, _p(pix_ids), _p(T), _p(picks), _p(bd), nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("oracle: invalid march arguments")
     return MarchResult(T, picks, bd)

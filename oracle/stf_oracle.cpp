@@ -308,7 +308,7 @@ Axis axis_at(float x, int res) {
     return {(int)fl, p - fl, (double)p};
 }
 
-void run_query(const Tex& T, const Queries& Q, uint64_t q, int filter, int mode, int smode,
+void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filter, int mode, int smode,
                uint32_t spp, uint64_t seed, uint32_t flags, Out& O) {
     float lam32; double lam64;
     lod(T, Q, q, &lam32, &lam64);
@@ -326,9 +326,9 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, int filter, int mode,
 
     for (uint32_t s = 0; s < spp; ++s) {
         uint32_t r0[4], r1[4], r2[4];
-        draw(seed, q, s, 0, r0);
-        draw(seed, q, s, 1, r1);
-        draw(seed, q, s, 2, r2);
+        draw(seed, id, s, 0, r0);
+        draw(seed, id, s, 1, r1);
+        draw(seed, id, s, 2, r2);
         // screen-space jitter inside the pixel footprint (FP32, fixed order)
         float x = Q.u[q], y = Q.v[q];
         if (Q.dudx) {
@@ -679,8 +679,9 @@ void orc_fetch(const orc_texture* t, int lvl, int ix, int iy, double* out7) {
 
 int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const float* v,
                      const float* dudx, const float* dvdx, const float* dudy, const float* dvdy,
-                     int filter, int mode, int smode, uint32_t spp, uint64_t seed, uint32_t flags,
-                     double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist, int nthreads) {
+                     const uint64_t* ids, int filter, int mode, int smode, uint32_t spp, uint64_t seed,
+                     uint32_t flags, double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist,
+                     int nthreads) {
     if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 3 || mode < 0 || mode > 3) return 1;
     if (tex->levels < 1 || tex->levels > 16) return 1;
     if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
@@ -691,19 +692,21 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
     Tex T; std::memcpy(&T, tex, sizeof(Tex));
     Queries Q{n, u, v, dudx, dvdx, dudy, dvdy};
     Out O{rgb, picks, picks64, bdist};
-    parallel_for(n, nthreads, [&](uint64_t q) { run_query(T, Q, q, filter, mode, smode, spp, seed, flags, O); });
+    parallel_for(n, nthreads, [&](uint64_t q) {
+        run_query(T, Q, q, ids ? ids[q] : q, filter, mode, smode, spp, seed, flags, O);
+    });
     return 0;
 }
 
 int orc_march(int nx, int ny, int nz, const uint16_t* data, float sigma_scale, const float* cam,
               uint32_t W, uint32_t H, uint32_t steps, int filter, int mode, uint32_t spp,
               uint64_t seed, uint32_t flags, uint64_t pix_begin, uint64_t pix_count,
-              double* T, uint32_t* picks, double* bdist, int nthreads) {
+              const uint64_t* pix_ids, double* T, uint32_t* picks, double* bdist, int nthreads) {
     if (!data || !cam || !T || spp == 0 || steps == 0) return 1;
     if (!(filter == F_LINEAR || filter == F_BSPLINE) || mode == M_POSITIVIZED) return 1;
     Vol V{nx, ny, nz, data, sigma_scale};
     parallel_for(pix_count, nthreads, [&](uint64_t i) {
-        uint64_t pix = pix_begin + i;
+        uint64_t pix = pix_ids ? pix_ids[i] : pix_begin + i;
         double acc = 0.0, bd = 1e30;
         for (uint32_t s = 0; s < spp; ++s) {
             uint32_t* pk = picks ? picks + (i * spp + s) * steps : nullptr;

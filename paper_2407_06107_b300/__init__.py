@@ -1,0 +1,234 @@
+"""Python binding of libstf -- stochastic texture filtering on B300 (sm_103a).
+
+Argument marshalling only: every step of the hot path runs in the CUDA kernels of
+``csrc/`` behind the C ABI of ``include/stf.h``.  torch is used for device memory and
+streams.  There is no CPU fallback: if ``libstf.so`` has not been built, or no CUDA device
+is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstf.so")
+
+FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3}
+MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
+SHADES = {"ggx": 0, "linear": 1}
+FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F = 0, 1, 2, 3
+FLAG_STRATIFIED = 1
+DEV_NAN_INPUT, DEV_BAD_INDEX = 1, 2
+NO_PICK = 0xFFFFFFFF
+
+STATUS = {0: "STF_OK", 1: "STF_ERR_INVALID_ARG", 2: "STF_ERR_BAD_HANDLE", 3: "STF_ERR_OOM",
+          4: "STF_ERR_CUDA", 5: "STF_ERR_UNSUPPORTED", 6: "STF_ERR_DEVICE_STATUS", 7: "STF_ERR_TIMEOUT"}
+
+
+class StfError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _TextureDesc(C.Structure):
+    _fields_ = [("width", C.c_uint32), ("height", C.c_uint32), ("num_levels", C.c_uint32),
+                ("format", C.c_int), ("address", C.c_int), ("level_data", C.POINTER(C.c_void_p)),
+                ("normal_data", C.POINTER(C.c_void_p)), ("data_on_device", C.c_int)]
+
+
+class _Queries(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("id_base", C.c_uint64), ("u", C.c_void_p), ("v", C.c_void_p)]
+
+
+class _Derivs(C.Structure):
+    _fields_ = [("dudx", C.c_void_p), ("dvdx", C.c_void_p), ("dudy", C.c_void_p), ("dvdy", C.c_void_p)]
+
+
+class _Output(C.Structure):
+    _fields_ = [("r", C.c_void_p), ("g", C.c_void_p), ("b", C.c_void_p), ("picks", C.c_void_p)]
+
+
+# every entry point declared in include/stf.h, with its ctypes signature
+_P, _U32, _U64, _I, _F = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int, C.c_float
+SIGNATURES = {
+    "stf_create": ([_I, _P, C.POINTER(_P)], _I),
+    "stf_destroy": ([_P], _I),
+    "stf_set_stream": ([_P, _P], _I),
+    "stf_synchronize": ([_P], _I),
+    "stf_get_device_status": ([_P, C.POINTER(_U32)], _I),
+    "stf_status_string": ([_I], C.c_char_p),
+    "stf_last_error": ([_P], C.c_char_p),
+    "stf_create_texture": ([_P, C.POINTER(_TextureDesc), C.POINTER(_U64)], _I),
+    "stf_destroy_texture": ([_P, _U64], _I),
+    "stf_filter_shade": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32, _U64,
+                          _U32, C.POINTER(_Output)], _I),
+    "stf_filter_shade_host": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
+                               _U64, _U32, C.POINTER(_Output)], _I),
+    "stf_create_volume": ([_P, _U32, _U32, _U32, _I, _F, _P, _I, C.POINTER(_U64)], _I),
+    "stf_destroy_volume": ([_P, _U64], _I),
+    "stf_march_volume": ([_P, _U64, _P, _U32, _U32, _U32, _I, _I, _U32, _U64, _U32, _U64, _U64, _P, _P], _I),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libstf.so (raises if it was never built -- there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not built: run __graft_entry__.build() or "
+                               "python paper_2407_06107_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes, fn.restype = args, res
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+class Context:
+    """One libstf context on one CUDA device, bound to a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        self._check(lib().stf_create(device, C.c_void_p(stream.cuda_stream), C.byref(h)), None)
+        self.h = h
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, st: int, h=None):
+        if st != 0:
+            msg = lib().stf_last_error(h if h is not None else getattr(self, "h", None)) or b""
+            raise StfError(st, msg.decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().stf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        self._check(lib().stf_synchronize(self.h), self.h)
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(lib().stf_set_stream(self.h, C.c_void_p(stream.cuda_stream)), self.h)
+
+    def device_status(self) -> int:
+        f = C.c_uint32(0)
+        st = lib().stf_get_device_status(self.h, C.byref(f))
+        if st not in (0, 6):
+            self._check(st, self.h)
+        return int(f.value)
+
+    # -------------------------------------------------------------- resources
+    def create_texture(self, levels, normal=None, address: str = "wrap") -> int:
+        """levels: list of (H, W, 4) float32 or uint8 arrays (numpy host or torch cuda)."""
+        on_dev = not isinstance(levels[0], np.ndarray)
+        keep = [lv if on_dev else np.ascontiguousarray(lv) for lv in levels]
+        fmt = FMT_RGBA32F if (str(keep[0].dtype).endswith("float32")) else FMT_RGBA8
+        arr = (C.c_void_p * len(keep))(*[_ptr(x) for x in keep])
+        narr = None
+        if normal is not None:
+            nk = [nm if on_dev else np.ascontiguousarray(nm) for nm in normal]
+            keep += nk
+            narr = (C.c_void_p * len(nk))(*[_ptr(x) for x in nk])
+        d = _TextureDesc(int(keep[0].shape[1]), int(keep[0].shape[0]), len(levels), fmt,
+                         0 if address == "wrap" else 1, arr, narr, 1 if on_dev else 0)
+        out = C.c_uint64(0)
+        self._check(lib().stf_create_texture(self.h, C.byref(d), C.byref(out)), self.h)
+        return int(out.value)
+
+    def destroy_texture(self, tex: int):
+        self._check(lib().stf_destroy_texture(self.h, tex), self.h)
+
+    def create_volume(self, data, sigma_scale: float) -> int:
+        """data: (nz, ny, nx) float16, numpy host or torch cuda."""
+        on_dev = not isinstance(data, np.ndarray)
+        if not on_dev:
+            data = np.ascontiguousarray(data, dtype=np.float16)
+        nz, ny, nx = data.shape
+        out = C.c_uint64(0)
+        self._check(lib().stf_create_volume(self.h, nx, ny, nz, FMT_R16F, float(sigma_scale),
+                                            C.c_void_p(_ptr(data)), 1 if on_dev else 0, C.byref(out)), self.h)
+        return int(out.value)
+
+    def destroy_volume(self, vol: int):
+        self._check(lib().stf_destroy_volume(self.h, vol), self.h)
+
+    # -------------------------------------------------------------- hot path
+    def _args(self, u, v, derivs, out, picks, n, id_base):
+        q = _Queries(n, id_base, _ptr(u), _ptr(v))
+        d = None
+        if derivs is not None:
+            d = _Derivs(*[_ptr(x) for x in derivs])
+        o = _Output(_ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(picks))
+        return q, d, o
+
+    def filter_shade(self, tex: int, u, v, derivs=None, filter: str = "bspline", mode: str = "stochastic",
+                     shade: str = "ggx", spp: int = 1, seed: int = 1, flags: int = 0, id_base: int = 0,
+                     out=None, want_picks: bool = False):
+        """u, v, derivs (dudx, dvdx, dudy, dvdy): float32 cuda tensors.  Returns (r, g, b, picks)."""
+        torch = self.torch
+        n = int(u.shape[0])
+        if out is None:
+            out = [torch.empty(n, dtype=torch.float32, device=u.device) for _ in range(3)]
+        picks = torch.empty((n, spp, 2), dtype=torch.int32, device=u.device) if want_picks else None
+        q, d, o = self._args(u, v, derivs, out, picks, n, id_base)
+        st = lib().stf_filter_shade(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
+                                    FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2], picks
+
+    def filter_shade_host(self, tex: int, u, v, derivs=None, filter: str = "bspline", mode: str = "stochastic",
+                          shade: str = "ggx", spp: int = 1, seed: int = 1, flags: int = 0, id_base: int = 0,
+                          out=None, want_picks: bool = False):
+        """Host (CPU, ideally pinned) float32 tensors or numpy arrays in and out."""
+        n = int(u.shape[0])
+        if out is None:
+            out = [np.empty(n, dtype=np.float32) for _ in range(3)]
+        picks = np.empty((n, spp, 2), dtype=np.uint32) if want_picks else None
+        q, d, o = self._args(u, v, derivs, out, picks, n, id_base)
+        st = lib().stf_filter_shade_host(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
+                                         FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2], picks
+
+    def march_volume(self, vol: int, cam, width: int, height: int, steps: int = 128,
+                     filter: str = "bspline", mode: str = "stochastic", spp: int = 1, seed: int = 1,
+                     flags: int = 0, pix_begin: int = 0, pix_count: int | None = None, out=None,
+                     want_picks: bool = False):
+        torch = self.torch
+        cnt = width * height - pix_begin if pix_count is None else pix_count
+        if out is None:
+            out = torch.empty(cnt, dtype=torch.float32, device=f"cuda:{self.device}")
+        picks = (torch.empty((cnt, spp, steps), dtype=torch.int32, device=f"cuda:{self.device}")
+                 if want_picks else None)
+        camv = (C.c_float * 12)(*[float(x) for x in np.asarray(cam, dtype=np.float32)])
+        st = lib().stf_march_volume(self.h, vol, camv, width, height, steps, FILTERS[filter], MODES[mode],
+                                    spp, seed, flags, pix_begin, cnt, C.c_void_p(_ptr(out)),
+                                    C.c_void_p(_ptr(picks)) if picks is not None else None)
+        self._check(st, self.h)
+        return out, picks

@@ -1,0 +1,276 @@
+// 2-D texture filter + shade kernels (sm_103a).
+//
+// One thread owns one query and loops over its spp samples.  Per sample:
+//   Philox -> screen-space jitter (Sec. 4.2.1) -> stochastic MIP level (stochastic lerp,
+//   supplement "Linear Filters") -> per-axis weights in registers -> per-axis CDF pick
+//   (Sec. 2.2 "Sampling arrays"; separable FRS, Sec. 4.1) -> ONE texel fetch -> decode ->
+//   GGX + Lambert shade -> accumulate sign * W * f_hat (Eq. stochastic-sum).
+// The N-tap modes instead visit every tap of both MIP levels: filter-before sums the
+// decoded texels and shades once (Eq. filter-before-shading); filter-after shades every
+// tap (Eq. filtering-after-shading).
+#include "stf_kernels.h"
+#include "stf_device.cuh"
+
+namespace stf {
+
+struct FetchCtx {
+    const unsigned char* base;
+    int fmt, levels, has_normal;
+    uint64_t off[16];
+    int w[16], h[16];
+};
+
+__device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, int iy) {
+    const size_t idx = (size_t)iy * (size_t)T.w[lvl] + (size_t)ix;
+    if (T.fmt == FMT_RGBA32F) {
+        const float4* p = reinterpret_cast<const float4*>(T.base + T.off[lvl]);
+        return decode_rgba32f(__ldg(p + idx));
+    }
+    const uint2* p = reinterpret_cast<const uint2*>(T.base + T.off[lvl]);
+    return decode_rgba8(__ldg(p + idx), T.has_normal != 0);
+}
+
+__device__ __forceinline__ uint32_t pack_pick(int lvl, int ix, int iy) {
+    return ((uint32_t)lvl << 28) | ((uint32_t)iy << 14) | (uint32_t)ix;
+}
+
+// LOD from the derivative footprint: log2 of the minor axis in level-0 texels with the
+// anisotropy capped at 64 (supplement listing computeLodAniso), clamped to [0, L-1].
+__device__ __forceinline__ float lod_aniso(float dudx, float dvdx, float dudy, float dvdy,
+                                           float W, float H, int levels) {
+    const float ax = __fmul_rn(dudx, W), ay = __fmul_rn(dvdx, H);
+    const float bx = __fmul_rn(dudy, W), by = __fmul_rn(dvdy, H);
+    const float la = __fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay));
+    const float lb = __fadd_rn(__fmul_rn(bx, bx), __fmul_rn(by, by));
+    float mn = la, mx = lb;
+    if (mn > mx) { mn = lb; mx = la; }
+    float minl = sqrtf(mn);
+    const float maxl = sqrtf(mx);
+    if (minl > 0.0f && __fmul_rn(minl, 64.0f) < maxl) minl = __fmul_rn(maxl, 1.0f / 64.0f);
+    const float l = log2f(minl);
+    return fminf(fmaxf(l, 0.0f), (float)(levels - 1));
+}
+
+template <int FILTER, int MODE>
+__global__ void __launch_bounds__(256)
+k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
+    constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const float inv_spp = 1.0f / (float)a.spp;
+    const int kside = a.kside;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const float u = a.u[q], v = a.v[q];
+        float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f;
+        float lam = 0.0f;
+        if (a.has_derivs) {
+            dudx = a.dudx[q]; dvdx = a.dvdx[q]; dudy = a.dudy[q]; dvdy = a.dvdy[q];
+            if (T.levels > 1) lam = lod_aniso(dudx, dvdx, dudy, dvdy, (float)T.w[0], (float)T.h[0], T.levels);
+        }
+        if (isnan(u) || isnan(v) || isnan(dudx) || isnan(dvdx) || isnan(dudy) || isnan(dvdy))
+            atomicOr(a.status, DEV_NAN_INPUT);
+        const int l0 = (int)floorf(lam);
+        const float fr = __fsub_rn(lam, (float)l0);
+        const uint64_t id = a.id_base + q;
+        const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+        float3 acc = make_float3(0.f, 0.f, 0.f);
+
+        for (uint32_t s = 0; s < a.spp; ++s) {
+            const uint4 r0 = philox(id_lo, id_hi, s, 0u, k0, k1);
+            float x = u, y = v;
+            if (a.has_derivs) {
+                float jx, jy;
+                if (a.flags & FLAG_STRATIFIED) {
+                    jx = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s % kside), 0.5f), (float)kside), 0.5f);
+                    jy = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s / kside), 0.5f), (float)kside), 0.5f);
+                } else {
+                    jx = __fsub_rn(unif(r0.x), 0.5f);
+                    jy = __fsub_rn(unif(r0.y), 0.5f);
+                }
+                x = __fadd_rn(__fadd_rn(x, __fmul_rn(jx, dudx)), __fmul_rn(jy, dudy));
+                y = __fadd_rn(__fadd_rn(y, __fmul_rn(jx, dvdx)), __fmul_rn(jy, dvdy));
+            }
+            float3 est;
+            if (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) {
+                const uint4 r1 = philox(id_lo, id_hi, s, 1u, k0, k1);
+                int lvl = l0 + ((unif(r0.z) < fr) ? 1 : 0);
+                lvl = min(lvl, T.levels - 1);
+                const int W = T.w[lvl], H = T.h[lvl];
+                const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+                float wx[4], wy[4];
+                axis_weights<FILTER>(ax.t, wx);
+                axis_weights<FILTER>(ay.t, wy);
+                if (MODE == M_STOCHASTIC) {
+                    float Sx, Sy;
+                    const int kx = cdf_pick<NT>(wx, unif(r0.w), 0, &Sx);
+                    const int ky = cdf_pick<NT>(wy, unif(r1.x), 0, &Sy);
+                    const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
+                    const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
+                    float Wt = 1.0f;
+                    if (is_signed(FILTER)) {
+                        Wt = Sx * Sy;
+                        if ((wx[kx] < 0.0f) != (wy[ky] < 0.0f)) Wt = -Wt;
+                    }
+                    est = make_float3(Wt * f.x, Wt * f.y, Wt * f.z);
+                    if (a.picks) {
+                        uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                        pk[0] = pack_pick(lvl, ix, iy);
+                        pk[1] = NO_PICK;
+                    }
+                } else {
+                    // positivization: one sample from each sign set, separable (Sec. 2.2)
+                    float Px, Nx, Py, Ny;
+                    cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
+                    cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
+                    const float Wp = __fadd_rn(__fmul_rn(Px, Py), __fmul_rn(Nx, Ny));
+                    const float Wn = __fadd_rn(__fmul_rn(Px, Ny), __fmul_rn(Nx, Py));
+                    const int cp = (__fmul_rn(unif(r1.y), Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
+                    const int kx = cdf_pick<NT>(wx, unif(r0.w), cp, nullptr);
+                    const int ky = cdf_pick<NT>(wy, unif(r1.x), cp, nullptr);
+                    const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
+                    const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
+                    est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
+                    uint32_t negpick = NO_PICK;
+                    if (Wn > 0.0f) {
+                        const uint4 r2 = philox(id_lo, id_hi, s, 2u, k0, k1);
+                        const int cn = (__fmul_rn(unif(r2.x), Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
+                        const int qx = cdf_pick<NT>(wx, unif(r1.z), cn, nullptr);
+                        const int qy = cdf_pick<NT>(wy, unif(r1.w), -cn, nullptr);
+                        const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
+                        const float3 g = shade(a.shade, fetch(T, lvl, jx, jy), SC);
+                        est.x = fmaf(-Wn, g.x, est.x);
+                        est.y = fmaf(-Wn, g.y, est.y);
+                        est.z = fmaf(-Wn, g.z, est.z);
+                        negpick = pack_pick(lvl, jx, jy);
+                    }
+                    if (a.picks) {
+                        uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                        pk[0] = pack_pick(lvl, ix, iy);
+                        pk[1] = negpick;
+                    }
+                }
+            } else {
+                // N-tap: every tap of levels floor(lam) and floor(lam)+1
+                Material fm;
+                fm.rho = make_float3(0.f, 0.f, 0.f);
+                fm.rough = 0.f;
+                fm.n = make_float3(0.f, 0.f, 0.f);
+                float3 fsum = make_float3(0.f, 0.f, 0.f);
+#pragma unroll 1
+                for (int li = 0; li < 2; ++li) {
+                    const int lvl = l0 + li;
+                    const float wl = li == 0 ? __fsub_rn(1.0f, fr) : fr;
+                    if (wl == 0.0f || lvl >= T.levels) continue;
+                    const int W = T.w[lvl], H = T.h[lvl];
+                    const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+                    float wx[4], wy[4];
+                    axis_weights<FILTER>(ax.t, wx);
+                    axis_weights<FILTER>(ay.t, wy);
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) {
+                        const int iy = wrap_index(ay.i0 + T0 + j, H);
+                        const float wyl = wl * wy[j];
+#pragma unroll
+                        for (int i = 0; i < NT; ++i) {
+                            const float w = wyl * wx[i];
+                            if (w == 0.0f) continue;
+                            const int ix = wrap_index(ax.i0 + T0 + i, W);
+                            const Material m = fetch(T, lvl, ix, iy);
+                            if (MODE == M_NTAP_BEFORE) {
+                                fm.rho.x = fmaf(w, m.rho.x, fm.rho.x);
+                                fm.rho.y = fmaf(w, m.rho.y, fm.rho.y);
+                                fm.rho.z = fmaf(w, m.rho.z, fm.rho.z);
+                                fm.rough = fmaf(w, m.rough, fm.rough);
+                                fm.n.x = fmaf(w, m.n.x, fm.n.x);
+                                fm.n.y = fmaf(w, m.n.y, fm.n.y);
+                                fm.n.z = fmaf(w, m.n.z, fm.n.z);
+                            } else {
+                                const float3 f = shade(a.shade, m, SC);
+                                fsum.x = fmaf(w, f.x, fsum.x);
+                                fsum.y = fmaf(w, f.y, fsum.y);
+                                fsum.z = fmaf(w, f.z, fsum.z);
+                            }
+                        }
+                    }
+                }
+                if (MODE == M_NTAP_BEFORE) {
+                    const float ln2 = dot3(fm.n, fm.n);
+                    if (ln2 > 0.0f) {
+                        const float inv = 1.0f / sqrtf(ln2);
+                        fm.n = make_float3(fm.n.x * inv, fm.n.y * inv, fm.n.z * inv);
+                    } else {
+                        fm.n = make_float3(0.f, 0.f, 1.f);
+                    }
+                    est = shade(a.shade, fm, SC);
+                } else {
+                    est = fsum;
+                }
+                if (a.picks) {
+                    uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                    pk[0] = NO_PICK;
+                    pk[1] = NO_PICK;
+                }
+            }
+            acc.x += est.x; acc.y += est.y; acc.z += est.z;
+        }
+        a.r[q] = acc.x * inv_spp;
+        a.g[q] = acc.y * inv_spp;
+        a.b[q] = acc.z * inv_spp;
+    }
+}
+
+template <int FILTER, int MODE>
+static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
+                             int grid, cudaStream_t st) {
+    k_filter_shade<FILTER, MODE><<<grid, 256, 0, st>>>(a, T, SC);
+    return cudaGetLastError();
+}
+
+template <int FILTER>
+static cudaError_t launch_f(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
+                            int grid, cudaStream_t st) {
+    switch (a.mode) {
+        case M_NTAP_BEFORE: return launch_fm<FILTER, M_NTAP_BEFORE>(a, T, SC, grid, st);
+        case M_NTAP_AFTER: return launch_fm<FILTER, M_NTAP_AFTER>(a, T, SC, grid, st);
+        case M_STOCHASTIC: return launch_fm<FILTER, M_STOCHASTIC>(a, T, SC, grid, st);
+        case M_POSITIVIZED:
+            if constexpr (is_signed(FILTER)) return launch_fm<FILTER, M_POSITIVIZED>(a, T, SC, grid, st);
+            return cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
+}
+
+ShadeConst make_shade_const() {
+    // l = (0.48, 0.36, 0.80), v = (-0.28, 0, 0.96): unit vectors in exact arithmetic
+    ShadeConst C;
+    C.l = make_float3(0.48f, 0.36f, 0.80f);
+    C.v = make_float3(-0.28f, 0.0f, 0.96f);
+    const double hx = 0.48 - 0.28, hy = 0.36, hz = 0.80 + 0.96;
+    const double hl = std::sqrt(hx * hx + hy * hy + hz * hz);
+    C.h = make_float3((float)(hx / hl), (float)(hy / hl), (float)(hz / hl));
+    const double vh = (-0.28 * hx + 0.96 * hz) / hl, m = 1.0 - vh;
+    C.F = (float)(0.04 + 0.96 * m * m * m * m * m);
+    return C;
+}
+
+cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int num_sms, cudaStream_t st) {
+    FetchCtx T;
+    T.base = static_cast<const unsigned char*>(tv.base);
+    T.fmt = tv.fmt;
+    T.levels = tv.levels;
+    T.has_normal = tv.has_normal;
+    for (int i = 0; i < 16; ++i) { T.off[i] = tv.off[i]; T.w[i] = tv.w[i]; T.h[i] = tv.h[i]; }
+    const ShadeConst SC = make_shade_const();
+    const uint64_t blocks_needed = (a.n + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms * 8;
+    const int grid = (int)(blocks_needed < cap ? (blocks_needed ? blocks_needed : 1) : cap);
+    switch (a.filter) {
+        case F_LINEAR: return launch_f<F_LINEAR>(a, T, SC, grid, st);
+        case F_BSPLINE: return launch_f<F_BSPLINE>(a, T, SC, grid, st);
+        case F_CATMULL_ROM: return launch_f<F_CATMULL_ROM>(a, T, SC, grid, st);
+        case F_MITCHELL: return launch_f<F_MITCHELL>(a, T, SC, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stf

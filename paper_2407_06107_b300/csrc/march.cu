@@ -1,0 +1,159 @@
+// Volume ray march kernels (sm_103a): trilinear (8 taps) / tricubic B-spline (64 taps)
+// density reconstruction, per-step transmittance exp(-sigma dt), stochastic 1-tap vs
+// N-tap (Sec. 5 "Offline rendering"; FRS for the 3-D B-spline, Sec. 4.1, and the
+// tricubic listing of the supplement).
+//
+// One thread owns one pixel and all its samples.  Ray setup and sample positions are
+// FP32 with a fixed operation order (they decide which voxel is picked).  Estimators:
+//   stochastic : T = exp(-dt * sigma_scale * sum_k d_pick,k), the densities summed in
+//                exact 2^-24 fixed point, so one expf per ray carries the only rounding;
+//   N-tap after: T = prod_k sum_i w_i exp(-sigma_i dt), an FMA-compensated product of
+//                1 - sum_i w_i (1 - exp(-sigma_i dt)) (exactly 1 in empty space);
+//   N-tap before: T = exp(-dt sum_k sum_i w_i sigma_i), compensated summation over k.
+#include "stf_kernels.h"
+#include "stf_device.cuh"
+
+namespace stf {
+
+__device__ __forceinline__ float vox(const MarchArgs& a, int x, int y, int z) {
+    x = clamp_index(x, a.nx); y = clamp_index(y, a.ny); z = clamp_index(z, a.nz);
+    return __half2float(a.vox[((size_t)z * a.ny + y) * a.nx + x]);
+}
+
+template <int FILTER, int MODE>
+__global__ void __launch_bounds__(128) k_march(MarchArgs a) {
+    constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const float res[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.pix_count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t pix = a.pix_begin + i;
+        const uint32_t px = (uint32_t)(pix % a.width), py = (uint32_t)(pix / a.width);
+        const uint32_t id_lo = (uint32_t)pix, id_hi = (uint32_t)(pix >> 32);
+        float acc = 0.0f;
+        for (uint32_t s = 0; s < a.spp; ++s) {
+            uint32_t* pk = a.picks ? a.picks + (i * a.spp + s) * a.steps : nullptr;
+            float jx, jy;
+            if (a.flags & FLAG_STRATIFIED) {
+                jx = __fdiv_rn(__fadd_rn((float)(s % a.kside), 0.5f), (float)a.kside);
+                jy = __fdiv_rn(__fadd_rn((float)(s / a.kside), 0.5f), (float)a.kside);
+            } else {
+                const uint4 r = philox(id_lo, id_hi, s, 0u, k0, k1);
+                jx = unif(r.x); jy = unif(r.y);
+            }
+            float sx = __fsub_rn(__fmul_rn(__fadd_rn((float)px, jx), __fdiv_rn(2.0f, (float)a.width)), 1.0f);
+            float sy = __fsub_rn(1.0f, __fmul_rn(__fadd_rn((float)py, jy), __fdiv_rn(2.0f, (float)a.height)));
+            float d[3], e[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                e[c] = a.cam[c];
+                d[c] = __fadd_rn(__fadd_rn(a.cam[3 + c], __fmul_rn(sx, a.cam[6 + c])), __fmul_rn(sy, a.cam[9 + c]));
+            }
+            const float l2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+            const float inv = __fdiv_rn(1.0f, __fsqrt_rn(l2));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d[c] = __fmul_rn(d[c], inv);
+            float tmin = 0.0f, tmax = __int_as_float(0x7f800000);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (d[c] != 0.0f) {
+                    const float id = __fdiv_rn(1.0f, d[c]);
+                    const float t1 = __fmul_rn(__fsub_rn(0.0f, e[c]), id), t2 = __fmul_rn(__fsub_rn(1.0f, e[c]), id);
+                    tmin = fmaxf(tmin, fminf(t1, t2));
+                    tmax = fminf(tmax, fmaxf(t1, t2));
+                } else if (e[c] < 0.0f || e[c] > 1.0f) {
+                    tmax = -1.0f;
+                }
+            }
+            if (!(tmin < tmax)) {
+                acc += 1.0f;
+                if (pk) for (uint32_t k = 0; k < a.steps; ++k) pk[k] = NO_PICK;
+                continue;
+            }
+            const float dt = __fdiv_rn(__fsub_rn(tmax, tmin), (float)a.steps);
+            uint64_t fixed_sum = 0;                 // stochastic: sum of d * 2^24 (exact)
+            float Ssum = 0.0f, Scomp = 0.0f;        // before: compensated sum of filtered sigma/scale
+            float P = 1.0f, Pe = 0.0f;              // after: compensated product
+            const float sdt = a.sigma_scale * dt;
+            for (uint32_t k = 0; k < a.steps; ++k) {
+                const float tk = __fadd_rn(tmin, __fmul_rn(__fadd_rn((float)k, 0.5f), dt));
+                AxisPos ap[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ap[c] = axis_pos(__fadd_rn(e[c], __fmul_rn(tk, d[c])), res[c]);
+                float w[3][4];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) axis_weights<FILTER>(ap[c].t, w[c]);
+                if (MODE == M_STOCHASTIC) {
+                    const uint4 r = philox(id_lo, id_hi, s, k + 1u, k0, k1);
+                    const int kx = cdf_pick<NT>(w[0], unif(r.x), 0, nullptr);
+                    const int ky = cdf_pick<NT>(w[1], unif(r.y), 0, nullptr);
+                    const int kz = cdf_pick<NT>(w[2], unif(r.z), 0, nullptr);
+                    const int ix = clamp_index(ap[0].i0 + T0 + kx, a.nx);
+                    const int iy = clamp_index(ap[1].i0 + T0 + ky, a.ny);
+                    const int iz = clamp_index(ap[2].i0 + T0 + kz, a.nz);
+                    const float dv = __half2float(a.vox[((size_t)iz * a.ny + iy) * a.nx + ix]);
+                    fixed_sum += (uint64_t)(dv * 16777216.0f);
+                    if (pk) pk[k] = ((uint32_t)iz << 20) | ((uint32_t)iy << 10) | (uint32_t)ix;
+                } else {
+                    float fsig = 0.0f, fab = 0.0f;   // sum w d, sum w (1 - exp(-sigma dt))
+#pragma unroll
+                    for (int cz = 0; cz < NT; ++cz) {
+#pragma unroll
+                        for (int cy = 0; cy < NT; ++cy) {
+                            const float wyz = w[2][cz] * w[1][cy];
+#pragma unroll
+                            for (int cx = 0; cx < NT; ++cx) {
+                                const float ww = wyz * w[0][cx];
+                                const float dv = vox(a, ap[0].i0 + T0 + cx, ap[1].i0 + T0 + cy, ap[2].i0 + T0 + cz);
+                                if (MODE == M_NTAP_BEFORE) {
+                                    fsig = fmaf(ww, dv, fsig);
+                                } else if (dv != 0.0f) {
+                                    fab = fmaf(ww, -expm1f(-sdt * dv), fab);
+                                }
+                            }
+                        }
+                    }
+                    if (MODE == M_NTAP_BEFORE) {
+                        const float t = Ssum + fsig;   // Neumaier compensated summation
+                        Scomp += (fabsf(Ssum) >= fabsf(fsig)) ? (Ssum - t) + fsig : (fsig - t) + Ssum;
+                        Ssum = t;
+                    } else if (fab != 0.0f) {
+                        const float f = 1.0f - fab;
+                        const float p = P * f;
+                        Pe = fmaf(Pe, f, fmaf(P, f, -p));   // exact error of P*f, carried
+                        P = p;
+                    }
+                    if (pk) pk[k] = NO_PICK;
+                }
+            }
+            float T;
+            if (MODE == M_STOCHASTIC) T = expf(-sdt * ((float)fixed_sum * 5.9604644775390625e-8f));
+            else if (MODE == M_NTAP_BEFORE) T = expf(-sdt * (Ssum + Scomp));
+            else T = P + Pe;
+            acc += T;
+        }
+        a.T[i] = acc / (float)a.spp;
+    }
+}
+
+template <int FILTER>
+static cudaError_t launch_f(const MarchArgs& a, int grid, cudaStream_t st) {
+    switch (a.mode) {
+        case M_NTAP_BEFORE: k_march<FILTER, M_NTAP_BEFORE><<<grid, 128, 0, st>>>(a); break;
+        case M_NTAP_AFTER: k_march<FILTER, M_NTAP_AFTER><<<grid, 128, 0, st>>>(a); break;
+        case M_STOCHASTIC: k_march<FILTER, M_STOCHASTIC><<<grid, 128, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    const uint64_t need = (a.pix_count + 127) / 128;
+    const uint64_t cap = (uint64_t)num_sms * 16;
+    const int grid = (int)(need < cap ? (need ? need : 1) : cap);
+    if (a.filter == F_LINEAR) return launch_f<F_LINEAR>(a, grid, st);
+    if (a.filter == F_BSPLINE) return launch_f<F_BSPLINE>(a, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stf

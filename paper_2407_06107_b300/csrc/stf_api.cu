@@ -1,0 +1,422 @@
+// C-ABI layer of libstf: contexts, handles, argument validation, uploads and launches.
+// See include/stf.h for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/stf.h"
+#include "stf_kernels.h"
+
+struct TexRec {
+    void* mem = nullptr;
+    stf::TexView view{};
+};
+struct VolRec {
+    void* mem = nullptr;
+    uint32_t nx = 0, ny = 0, nz = 0;
+    float sigma_scale = 1.0f;
+};
+
+struct stf_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 148;
+    uint32_t* d_status = nullptr;
+    std::string last_error;
+    uint64_t next_handle = 1;
+    std::unordered_map<uint64_t, TexRec> tex;
+    std::unordered_map<uint64_t, VolRec> vol;
+    void* stage = nullptr;          // device staging for the host-buffer entry points
+    size_t stage_bytes = 0;
+    int fault = 0;                  // host-side fault injection (STF_FAULT), 0 = off
+};
+
+namespace {
+
+enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2 };
+
+stf_status fail(stf_ctx c, stf_status s, const char* msg) {
+    if (c) c->last_error = msg;
+    return s;
+}
+stf_status cuda_fail(stf_ctx c, cudaError_t e, const char* where) {
+    if (c) c->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STF_ERR_OOM : STF_ERR_CUDA;
+}
+stf_status dev_alloc(stf_ctx c, void** p, size_t bytes) {
+    if (c->fault == FAULT_ALLOC) return fail(c, STF_ERR_OOM, "injected allocation failure (STF_FAULT=alloc)");
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(c, e, "cudaMalloc"); }
+    return STF_OK;
+}
+bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
+bool bad_enum_filter(int f) { return f < 0 || f > 3; }
+bool bad_enum_mode(int m) { return m < 0 || m > 3; }
+bool signed_filter(int f) { return f == STF_FILTER_CATMULL_ROM || f == STF_FILTER_MITCHELL; }
+int square_side(uint32_t spp) {
+    int k = (int)std::lround(std::sqrt((double)spp));
+    return (uint32_t)(k * k) == spp ? k : -1;
+}
+uint32_t level_dim(uint32_t d, uint32_t l) { uint32_t x = d >> l; return x ? x : 1u; }
+
+struct CurrentDevice {
+    int prev = -1;
+    explicit CurrentDevice(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~CurrentDevice() { int now = -1; cudaGetDevice(&now); if (prev >= 0 && now != prev) cudaSetDevice(prev); }
+};
+
+stf_status ensure_stage(stf_ctx c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return STF_OK;
+    if (c->stage) { cudaStreamSynchronize(c->stream); cudaFree(c->stage); c->stage = nullptr; c->stage_bytes = 0; }
+    stf_status s = dev_alloc(c, &c->stage, bytes);
+    if (s == STF_OK) c->stage_bytes = bytes;
+    return s;
+}
+
+stf_status validate_filter_call(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
+                                stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint32_t flags,
+                                const stf_output* out, TexRec** rec) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    auto it = c->tex.find(t);
+    if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle");
+    *rec = &it->second;
+    if (!q || !out) return fail(c, STF_ERR_INVALID_ARG, "queries and output must be non-null");
+    if (bad_enum_filter(f) || bad_enum_mode(m) || (sh != STF_SHADE_GGX_LAMBERT && sh != STF_SHADE_LINEAR))
+        return fail(c, STF_ERR_INVALID_ARG, "filter, mode or shade out of range");
+    if (m == STF_MODE_STOCHASTIC_POSITIVIZED && !signed_filter(f))
+        return fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
+    if (spp == 0) return fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
+    if (flags & ~(uint32_t)STF_FLAG_STRATIFIED) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0)
+        return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
+    if (q->n == 0) return STF_OK;
+    if (q->n > (1ull << 40)) return fail(c, STF_ERR_INVALID_ARG, "too many queries");
+    if (out->picks && q->n * (uint64_t)spp > (1ull << 40)) return fail(c, STF_ERR_INVALID_ARG, "pick buffer too large");
+    const void* ptrs[5] = {q->u, q->v, out->r, out->g, out->b};
+    for (const void* p : ptrs)
+        if (!p || !aligned4(p)) return fail(c, STF_ERR_INVALID_ARG, "query/output pointers must be non-null and 4-byte aligned");
+    if (d) {
+        const void* dp[4] = {d->dudx, d->dvdx, d->dudy, d->dvdy};
+        for (const void* p : dp)
+            if (!p || !aligned4(p)) return fail(c, STF_ERR_INVALID_ARG, "derivative pointers must be all non-null and 4-byte aligned");
+    }
+    if (out->picks && !aligned4(out->picks)) return fail(c, STF_ERR_INVALID_ARG, "picks must be 4-byte aligned");
+    return STF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stf_status_string(stf_status s) {
+    switch (s) {
+        case STF_OK: return "STF_OK";
+        case STF_ERR_INVALID_ARG: return "STF_ERR_INVALID_ARG";
+        case STF_ERR_BAD_HANDLE: return "STF_ERR_BAD_HANDLE";
+        case STF_ERR_OOM: return "STF_ERR_OOM";
+        case STF_ERR_CUDA: return "STF_ERR_CUDA";
+        case STF_ERR_UNSUPPORTED: return "STF_ERR_UNSUPPORTED";
+        case STF_ERR_DEVICE_STATUS: return "STF_ERR_DEVICE_STATUS";
+        case STF_ERR_TIMEOUT: return "STF_ERR_TIMEOUT";
+    }
+    return "STF_ERR_UNKNOWN";
+}
+
+const char* stf_last_error(stf_ctx c) { return c ? c->last_error.c_str() : "null context"; }
+
+stf_status stf_create(int device, void* cuda_stream, stf_ctx* out) {
+    if (!out) return STF_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) { cudaGetLastError(); return STF_ERR_CUDA; }
+    if (device < 0 || device >= ndev) return STF_ERR_INVALID_ARG;
+    stf_ctx c = new stf_ctx_s();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (const char* f = std::getenv("STF_FAULT")) {
+        if (!std::strcmp(f, "alloc")) c->fault = FAULT_ALLOC;
+        else if (!std::strcmp(f, "launch")) c->fault = FAULT_LAUNCH;
+    }
+    CurrentDevice cd(device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    stf_status s = dev_alloc(c, (void**)&c->d_status, sizeof(uint32_t));
+    if (s != STF_OK) { delete c; return s; }
+    cudaMemset(c->d_status, 0, sizeof(uint32_t));
+    *out = c;
+    return STF_OK;
+}
+
+stf_status stf_destroy(stf_ctx c) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    CurrentDevice cd(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->tex) cudaFree(kv.second.mem);
+    for (auto& kv : c->vol) cudaFree(kv.second.mem);
+    if (c->stage) cudaFree(c->stage);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return STF_OK;
+}
+
+stf_status stf_set_stream(stf_ctx c, void* stream) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    c->stream = (cudaStream_t)stream;
+    return STF_OK;
+}
+
+stf_status stf_synchronize(stf_ctx c) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    CurrentDevice cd(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "cudaStreamSynchronize");
+}
+
+stf_status stf_get_device_status(stf_ctx c, uint32_t* flags) {
+    if (!c || !flags) return STF_ERR_INVALID_ARG;
+    CurrentDevice cd(c->device);
+    uint32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device status read");
+    *flags = h;
+    return h ? STF_ERR_DEVICE_STATUS : STF_OK;
+}
+
+// ------------------------------------------------------------------------------ textures
+stf_status stf_create_texture(stf_ctx c, const stf_texture_desc* d, stf_tex* out) {
+    if (!c || !d || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
+    *out = 0;
+    if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
+        return fail(c, STF_ERR_INVALID_ARG, "texture size must be 1..16384");
+    if (d->num_levels < 1 || d->num_levels > STF_MAX_LEVELS) return fail(c, STF_ERR_INVALID_ARG, "num_levels must be 1..16");
+    if (d->format != STF_FMT_RGBA32F && d->format != STF_FMT_RGBA8)
+        return fail(c, STF_ERR_INVALID_ARG, "2-D textures are RGBA32F or RGBA8");
+    if (d->address != STF_ADDRESS_WRAP) return fail(c, STF_ERR_UNSUPPORTED, "2-D textures use wrap addressing");
+    if (!d->level_data) return fail(c, STF_ERR_INVALID_ARG, "level_data is null");
+    if (d->normal_data && d->format != STF_FMT_RGBA8) return fail(c, STF_ERR_INVALID_ARG, "normal maps accompany RGBA8 textures");
+    for (uint32_t l = 0; l < d->num_levels; ++l) {
+        if (!d->level_data[l]) return fail(c, STF_ERR_INVALID_ARG, "null level pointer");
+        if (d->normal_data && !d->normal_data[l]) return fail(c, STF_ERR_INVALID_ARG, "null normal level pointer");
+        if (d->data_on_device && d->format == STF_FMT_RGBA8 &&
+            (((uintptr_t)d->level_data[l] & 3u) || (d->normal_data && ((uintptr_t)d->normal_data[l] & 1u))))
+            return fail(c, STF_ERR_INVALID_ARG, "device RGBA8 levels must be 4-byte and RG8 levels 2-byte aligned");
+    }
+    CurrentDevice cd(c->device);
+    const size_t texel = d->format == STF_FMT_RGBA32F ? 16 : 8;
+    TexRec rec;
+    rec.view.fmt = d->format == STF_FMT_RGBA32F ? 0 : 1;
+    rec.view.levels = (int)d->num_levels;
+    rec.view.has_normal = d->normal_data ? 1 : 0;
+    rec.view.address = 0;
+    size_t total = 0, max_level = 0;
+    for (uint32_t l = 0; l < d->num_levels; ++l) {
+        const uint32_t w = level_dim(d->width, l), h = level_dim(d->height, l);
+        rec.view.w[l] = (int)w; rec.view.h[l] = (int)h;
+        rec.view.off[l] = total;
+        const size_t b = (size_t)w * h * texel;
+        total += (b + 255) & ~(size_t)255;
+        max_level = std::max(max_level, (size_t)w * h);
+    }
+    for (uint32_t l = d->num_levels; l < STF_MAX_LEVELS; ++l) { rec.view.w[l] = rec.view.h[l] = 1; rec.view.off[l] = 0; }
+    stf_status s = dev_alloc(c, &rec.mem, total);
+    if (s != STF_OK) return s;
+    rec.view.base = rec.mem;
+    const cudaMemcpyKind kind = d->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaSuccess;
+    void* tmp = nullptr;
+    if (rec.view.fmt == 1 && !d->data_on_device) {
+        s = dev_alloc(c, &tmp, max_level * 6);
+        if (s != STF_OK) { cudaFree(rec.mem); return s; }
+    }
+    for (uint32_t l = 0; l < d->num_levels && e == cudaSuccess; ++l) {
+        const size_t n = (size_t)rec.view.w[l] * rec.view.h[l];
+        char* dst = (char*)rec.mem + rec.view.off[l];
+        if (rec.view.fmt == 0) {
+            e = cudaMemcpyAsync(dst, d->level_data[l], n * 16, kind, c->stream);
+        } else {
+            const void* rgba = d->level_data[l];
+            const void* rg = d->normal_data ? d->normal_data[l] : nullptr;
+            if (!d->data_on_device) {
+                e = cudaMemcpyAsync(tmp, rgba, n * 4, cudaMemcpyHostToDevice, c->stream);
+                if (e == cudaSuccess && rg) e = cudaMemcpyAsync((char*)tmp + n * 4, rg, n * 2, cudaMemcpyHostToDevice, c->stream);
+                rgba = tmp;
+                rg = rg ? (const char*)tmp + n * 4 : nullptr;
+            }
+            if (e == cudaSuccess) e = stf::launch_pack_rgba8(rgba, rg, dst, n, c->stream);
+            if (e == cudaSuccess && !d->data_on_device) e = cudaStreamSynchronize(c->stream);   // tmp reuse
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) { cudaFree(rec.mem); return cuda_fail(c, e, "texture upload"); }
+    const uint64_t h = c->next_handle++;
+    c->tex[h] = rec;
+    *out = h;
+    return STF_OK;
+}
+
+stf_status stf_destroy_texture(stf_ctx c, stf_tex t) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    auto it = c->tex.find(t);
+    if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle");
+    CurrentDevice cd(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(it->second.mem);
+    c->tex.erase(it);
+    return STF_OK;
+}
+
+// ------------------------------------------------------------------------- filter + shade
+static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries* q, const stf_derivs* d,
+                                 stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                                 uint32_t flags, const stf_output* out) {
+    if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
+    stf::FilterShadeArgs a{};
+    a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v;
+    a.has_derivs = d ? 1 : 0;
+    if (d) { a.dudx = d->dudx; a.dvdx = d->dvdx; a.dudy = d->dudy; a.dvdy = d->dvdy; }
+    a.filter = f; a.mode = m; a.shade = sh; a.spp = spp; a.flags = flags;
+    a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
+    a.seed = seed; a.r = out->r; a.g = out->g; a.b = out->b; a.picks = out->picks;
+    a.status = c->d_status;
+    cudaError_t e = stf::launch_filter_shade(a, rec.view, c->num_sms, c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "filter_shade launch");
+}
+
+stf_status stf_filter_shade(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
+                            stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                            uint32_t flags, const stf_output* out) {
+    TexRec* rec = nullptr;
+    stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, &rec);
+    if (s != STF_OK || q->n == 0) return s;
+    CurrentDevice cd(c->device);
+    return enqueue_filter(c, *rec, q, d, f, m, sh, spp, seed, flags, out);
+}
+
+stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
+                                 stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                                 uint32_t flags, const stf_output* out) {
+    TexRec* rec = nullptr;
+    stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, &rec);
+    if (s != STF_OK || q->n == 0) return s;
+    CurrentDevice cd(c->device);
+    const uint64_t n = q->n;
+    const size_t fb = ((n * 4 + 255) / 256) * 256;
+    const int nin = d ? 6 : 2;
+    const size_t pick_b = out->picks ? n * (size_t)spp * 2 * 4 : 0;
+    s = ensure_stage(c, fb * (nin + 3) + pick_b);
+    if (s != STF_OK) return s;
+    char* base = (char*)c->stage;
+    float* dv[6];
+    const float* hv[6] = {q->u, q->v, d ? d->dudx : nullptr, d ? d->dvdx : nullptr, d ? d->dudy : nullptr, d ? d->dvdy : nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nin && e == cudaSuccess; ++i) {
+        dv[i] = (float*)(base + fb * i);
+        e = cudaMemcpyAsync(dv[i], hv[i], n * 4, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "host->device copy");
+    stf_queries dq{n, q->id_base, dv[0], dv[1]};
+    stf_derivs dd{};
+    if (d) dd = stf_derivs{dv[2], dv[3], dv[4], dv[5]};
+    stf_output dout{(float*)(base + fb * nin), (float*)(base + fb * (nin + 1)), (float*)(base + fb * (nin + 2)),
+                    out->picks ? (uint32_t*)(base + fb * (nin + 3)) : nullptr};
+    s = enqueue_filter(c, *rec, &dq, d ? &dd : nullptr, f, m, sh, spp, seed, flags, &dout);
+    if (s != STF_OK) return s;
+    e = cudaMemcpyAsync(out->r, dout.r, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->g, dout.g, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->b, dout.b, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && out->picks) e = cudaMemcpyAsync(out->picks, dout.picks, pick_b, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "device->host copy");
+}
+
+// --------------------------------------------------------------------------------- volume
+stf_status stf_create_volume(stf_ctx c, uint32_t nx, uint32_t ny, uint32_t nz, stf_format fmt,
+                             float sigma_scale, const void* data, int on_device, stf_vol* out) {
+    if (!c || !data || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
+    *out = 0;
+    if (fmt != STF_FMT_R16F) return fail(c, STF_ERR_INVALID_ARG, "volumes are R16F");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024)
+        return fail(c, STF_ERR_INVALID_ARG, "volume size must be 1..1024 per axis");
+    if (!(sigma_scale >= 0.0f) || std::isinf(sigma_scale)) return fail(c, STF_ERR_INVALID_ARG, "sigma_scale must be finite and >= 0");
+    CurrentDevice cd(c->device);
+    VolRec rec;
+    rec.nx = nx; rec.ny = ny; rec.nz = nz; rec.sigma_scale = sigma_scale;
+    const size_t bytes = (size_t)nx * ny * nz * 2;
+    stf_status s = dev_alloc(c, &rec.mem, bytes);
+    if (s != STF_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(rec.mem, data, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { cudaFree(rec.mem); return cuda_fail(c, e, "volume upload"); }
+    const uint64_t h = c->next_handle++;
+    c->vol[h] = rec;
+    *out = h;
+    return STF_OK;
+}
+
+stf_status stf_destroy_volume(stf_ctx c, stf_vol v) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    auto it = c->vol.find(v);
+    if (it == c->vol.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown volume handle");
+    CurrentDevice cd(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(it->second.mem);
+    c->vol.erase(it);
+    return STF_OK;
+}
+
+stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t width, uint32_t height,
+                            uint32_t steps, stf_filter f, stf_mode m, uint32_t spp, uint64_t seed,
+                            uint32_t flags, uint64_t pix_begin, uint64_t pix_count, float* out_T,
+                            uint32_t* out_picks) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    auto it = c->vol.find(v);
+    if (it == c->vol.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown volume handle");
+    if (!cam) return fail(c, STF_ERR_INVALID_ARG, "camera is null");
+    if (f != STF_FILTER_LINEAR && f != STF_FILTER_BSPLINE) return fail(c, STF_ERR_UNSUPPORTED, "volumes use LINEAR or BSPLINE");
+    if (m != STF_MODE_NTAP_BEFORE && m != STF_MODE_NTAP_AFTER && m != STF_MODE_STOCHASTIC)
+        return fail(c, STF_ERR_UNSUPPORTED, "volume mode must be NTAP_BEFORE, NTAP_AFTER or STOCHASTIC");
+    if (width < 1 || height < 1 || steps < 1 || steps > 65535 || spp < 1) return fail(c, STF_ERR_INVALID_ARG, "bad image size, steps or spp");
+    if (flags & ~(uint32_t)STF_FLAG_STRATIFIED) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0) return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
+    if (pix_begin + pix_count > (uint64_t)width * height) return fail(c, STF_ERR_INVALID_ARG, "pixel range outside the image");
+    if (pix_count == 0) return STF_OK;
+    if (!out_T || !aligned4(out_T) || (out_picks && !aligned4(out_picks))) return fail(c, STF_ERR_INVALID_ARG, "bad output pointer");
+    if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
+    CurrentDevice cd(c->device);
+    stf::MarchArgs a{};
+    a.vox = (const __half*)it->second.mem;
+    a.nx = (int)it->second.nx; a.ny = (int)it->second.ny; a.nz = (int)it->second.nz;
+    a.sigma_scale = it->second.sigma_scale;
+    for (int i = 0; i < 12; ++i) a.cam[i] = cam[i];
+    a.width = width; a.height = height; a.steps = steps; a.spp = spp; a.flags = flags;
+    a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
+    a.filter = f; a.mode = m; a.seed = seed; a.pix_begin = pix_begin; a.pix_count = pix_count;
+    a.T = out_T; a.picks = out_picks; a.status = c->d_status;
+    cudaError_t e = stf::launch_march(a, c->num_sms, c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "march launch");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------ upload packing
+namespace stf {
+// RGBA8 albedo+roughness and RG8 normal -> one 8-byte texel, so that a stochastic lookup
+// touches a single 32-byte sector.
+__global__ void k_pack_rgba8(const uint32_t* rgba, const uint16_t* rg, uint2* out, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = make_uint2(rgba[i], rg ? (uint32_t)rg[i] : 0x8080u);
+}
+cudaError_t launch_pack_rgba8(const void* rgba, const void* rg, void* out, uint64_t n, cudaStream_t st) {
+    const uint64_t g = (n + 255) / 256;
+    k_pack_rgba8<<<(int)(g < 4096 ? (g ? g : 1) : 4096), 256, 0, st>>>((const uint32_t*)rgba, (const uint16_t*)rg, (uint2*)out, n);
+    return cudaGetLastError();
+}
+}  // namespace stf

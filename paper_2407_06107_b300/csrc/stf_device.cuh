@@ -1,0 +1,203 @@
+// Device-side building blocks of stochastic texture filtering (sm_103a).
+//
+// Decision arithmetic (positions, weights, CDFs) uses __fmul_rn / __fadd_rn so that the
+// compiler cannot contract it into FMAs: the selected texel is then a deterministic
+// function of the FP32 inputs, the precision of the paper's float listings.  Value
+// arithmetic (shading, sums) is free to use FMA.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+
+namespace stf {
+
+enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
+enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
+enum { SH_GGX = 0, SH_LINEAR = 1 };
+enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
+enum { FLAG_STRATIFIED = 1u };
+enum { DEV_NAN_INPUT = 1u, DEV_BAD_INDEX = 2u };
+constexpr uint32_t NO_PICK = 0xFFFFFFFFu;
+
+__host__ __device__ constexpr int ntaps(int f) { return f == F_LINEAR ? 2 : 4; }
+__host__ __device__ constexpr int tap0(int f) { return f == F_LINEAR ? 0 : -1; }
+__host__ __device__ constexpr bool is_signed(int f) { return f == F_CATMULL_ROM || f == F_MITCHELL; }
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC 2011).  ctr = (id_lo, id_hi, sample, stream), key = seed.
+__device__ __forceinline__ uint4 philox(uint32_t id_lo, uint32_t id_hi, uint32_t sample,
+                                        uint32_t stream, uint32_t k0, uint32_t k1) {
+    uint32_t x0 = id_lo, x1 = id_hi, x2 = sample, x3 = stream;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        x0 = hi1 ^ x1 ^ k0; x1 = lo1; x2 = hi0 ^ x3 ^ k1; x3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+// top 24 bits scaled by 2^-24: exact in FP32
+__device__ __forceinline__ float unif(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-8f; }
+
+// ---------------------------------------------------------------- FP32 decision weights
+// Per-axis weights for the taps at distances 1+t, t, 1-t, 2-t (cubic) or 1-t, t
+// (linear).  The B-spline uses the polynomials of the paper's bicubic listing; the cubic
+// kernels (Keys a=-1/2, Mitchell-Netravali BC(1/3,1/3)) are evaluated in Horner form.
+template <int F>
+__device__ __forceinline__ float k_cubic(float d) {
+    float c3, c2, c0, q3, q2, q1, q0;
+    if (F == F_CATMULL_ROM) {
+        c3 = 1.5f; c2 = -2.5f; c0 = 1.0f; q3 = -0.5f; q2 = 2.5f; q1 = -4.0f; q0 = 2.0f;
+    } else {
+        c3 = 7.0f / 6.0f; c2 = -2.0f; c0 = 8.0f / 9.0f;
+        q3 = -7.0f / 18.0f; q2 = 2.0f; q1 = -10.0f / 3.0f; q0 = 16.0f / 9.0f;
+    }
+    if (d < 1.0f) {
+        float a = __fmul_rn(c3, d);
+        a = __fadd_rn(a, c2);
+        a = __fmul_rn(a, d);
+        a = __fmul_rn(a, d);
+        return __fadd_rn(a, c0);
+    }
+    if (d < 2.0f) {
+        float a = __fmul_rn(q3, d);
+        a = __fadd_rn(a, q2);
+        a = __fmul_rn(a, d);
+        a = __fadd_rn(a, q1);
+        a = __fmul_rn(a, d);
+        return __fadd_rn(a, q0);
+    }
+    return 0.0f;
+}
+
+template <int F>
+__device__ __forceinline__ void axis_weights(float t, float w[4]) {
+    if (F == F_LINEAR) {
+        w[0] = __fsub_rn(1.0f, t);
+        w[1] = t;
+    } else if (F == F_BSPLINE) {
+        const float s = 1.0f / 6.0f;
+        const float t2 = __fmul_rn(t, t), t3 = __fmul_rn(t, t2);
+        float a = -t3;
+        a = __fadd_rn(a, __fmul_rn(3.0f, t2));
+        a = __fsub_rn(a, __fmul_rn(3.0f, t));
+        a = __fadd_rn(a, 1.0f);
+        w[0] = __fmul_rn(s, a);
+        a = __fmul_rn(__fmul_rn(3.0f, t), t2);
+        a = __fsub_rn(a, __fmul_rn(6.0f, t2));
+        a = __fadd_rn(a, 4.0f);
+        w[1] = __fmul_rn(s, a);
+        a = __fmul_rn(__fmul_rn(-3.0f, t), t2);
+        a = __fadd_rn(a, __fmul_rn(3.0f, t2));
+        a = __fadd_rn(a, __fmul_rn(3.0f, t));
+        a = __fadd_rn(a, 1.0f);
+        w[2] = __fmul_rn(s, a);
+        w[3] = __fmul_rn(s, t3);
+    } else {
+        w[0] = k_cubic<F>(__fadd_rn(1.0f, t));
+        w[1] = k_cubic<F>(t);
+        w[2] = k_cubic<F>(__fsub_rn(1.0f, t));
+        w[3] = k_cubic<F>(__fsub_rn(2.0f, t));
+    }
+}
+
+// CDF inversion over one axis: first k with xi*S < prefix_k, S = sum of |w| over the
+// taps of sign class CLS (0: all, +1: w > 0, -1: w < 0).  Returns the tap index.
+template <int N>
+__device__ __forceinline__ int cdf_pick(const float w[4], float xi, int cls, float* total) {
+    float c[N];
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const bool in = cls == 0 || (cls > 0 ? w[k] > 0.0f : w[k] < 0.0f);
+        acc = __fadd_rn(acc, in ? fabsf(w[k]) : 0.0f);
+        c[k] = acc;
+    }
+    if (total) *total = acc;
+    const float target = __fmul_rn(xi, acc);
+    int k = N - 1;
+#pragma unroll
+    for (int j = N - 2; j >= 0; --j) k = (target < c[j]) ? j : k;
+    return k;
+}
+
+// raster position on one axis: p = x*res - 1/2, i0 = floor(p), t = p - i0 (FP32)
+struct AxisPos { int i0; float t; };
+__device__ __forceinline__ AxisPos axis_pos(float x, float res) {
+    float p = __fsub_rn(__fmul_rn(x, res), 0.5f);
+    float fl = floorf(p);
+    return {(int)fl, __fsub_rn(p, fl)};
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+__device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0), n - 1); }
+
+// ---------------------------------------------------------------- shading (FP32)
+struct Material { float3 rho; float rough; float3 n; };
+
+// Fixed light / view directions (unit in exact arithmetic) and the derived half vector,
+// F(v.h) and 1/pi.  The half vector is FP32-rounded normalize(l+v).
+struct ShadeConst {
+    float3 l, v, h;
+    float F;   // Schlick Fresnel at v.h with F0 = 0.04
+};
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// f_hat = [rho/pi + D G2 F / (4 nl nv)] nl  (GGX, height-correlated Smith, Schlick)
+__device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst& C) {
+    const float nl = dot3(m.n, C.l), nv = dot3(m.n, C.v);
+    if (!(nl > 0.0f) || !(nv > 0.0f)) return make_float3(0.f, 0.f, 0.f);
+    const float a = fminf(fmaxf(m.rough, 0.05f), 1.0f), a2 = a * a;
+    const float3 nxh = cross3(m.n, C.h), nxl = cross3(m.n, C.l), nxv = cross3(m.n, C.v);
+    const float nh = dot3(m.n, C.h);
+    const float q = fmaf(a2 * nh, nh, dot3(nxh, nxh));
+    const float D = a2 / (3.14159265358979f * q * q);
+    // Lambda = (sqrt(1 + a2 tan^2) - 1)/2 written without cancellation: x / (2 (sqrt(1+x)+1))
+    const float xl = a2 * dot3(nxl, nxl) / (nl * nl), xv = a2 * dot3(nxv, nxv) / (nv * nv);
+    const float Ll = 0.5f * xl / (sqrtf(1.0f + xl) + 1.0f), Lv = 0.5f * xv / (sqrtf(1.0f + xv) + 1.0f);
+    const float G = 1.0f / (1.0f + Ll + Lv);
+    const float spec = D * G * C.F / (4.0f * nv);
+    const float kd = nl * 0.318309886183790672f;
+    return make_float3(fmaf(m.rho.x, kd, spec), fmaf(m.rho.y, kd, spec), fmaf(m.rho.z, kd, spec));
+}
+
+__device__ __forceinline__ float3 shade(int sh, const Material& m, const ShadeConst& C) {
+    if (sh == SH_LINEAR) return m.rho;
+    return shade_ggx(m, C);
+}
+
+// ---------------------------------------------------------------- texel decode
+// RGBA8 material texel packed with its RG8 normal into 8 bytes (uint2):
+//   x = albedo R | G<<8 | B<<16 | roughness byte<<24, y = normal X | Y<<8, has_normal flag
+__device__ __forceinline__ float3 decode_normal_rg8(uint32_t xy) {
+    const float X = (float)(int)(2u * (xy & 0xFFu)) - 255.0f;
+    const float Y = (float)(int)(2u * ((xy >> 8) & 0xFFu)) - 255.0f;
+    const float Z = sqrtf(fmaxf(0.0f, 65025.0f - X * X - Y * Y));   // exact integer radicand
+    const float inv = 1.0f / sqrtf(X * X + Y * Y + Z * Z);
+    return make_float3(X * inv, Y * inv, Z * inv);
+}
+__device__ __forceinline__ Material decode_rgba8(uint2 t, bool has_normal) {
+    Material m;
+    const float k = 1.0f / 255.0f;
+    m.rho = make_float3((float)(t.x & 0xFFu) / 255.0f, (float)((t.x >> 8) & 0xFFu) / 255.0f,
+                        (float)((t.x >> 16) & 0xFFu) / 255.0f);
+    m.rough = fmaf(0.95f, (float)(t.x >> 24) * k, 0.05f);
+    m.n = has_normal ? decode_normal_rg8(t.y) : make_float3(0.f, 0.f, 1.f);
+    return m;
+}
+__device__ __forceinline__ Material decode_rgba32f(float4 t) {
+    Material m;
+    m.rho = make_float3(t.x, t.y, t.z);
+    m.rough = t.w;
+    m.n = make_float3(0.f, 0.f, 1.f);
+    return m;
+}
+
+}  // namespace stf

@@ -1,0 +1,213 @@
+"""Parity of the CUDA 2-D filter+shade path (through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import stf_synth as synth
+from gpu_util import assert_values, compare_picks
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_06107_b300 as stf
+    c = stf.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(q):
+    f = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = None
+    if q.has_derivs():
+        d = [f(q.dudx), f(q.dvdx), f(q.dudy), f(q.dvdy)]
+    return f(q.u), f(q.v), d
+
+
+def _run(ctx, tex_h, q, filter, mode, spp, seed=1, shade="ggx", flags=0, picks=True, id_base=0):
+    u, v, d = _dev(q)
+    r, g, b, pk = ctx.filter_shade(tex_h, u, v, d, filter, mode, shade, spp, seed, flags,
+                                   id_base=id_base, want_picks=picks)
+    torch.cuda.synchronize()
+    rgb = torch.stack([r, g, b], 1).cpu().numpy().astype(np.float64)
+    return rgb, (pk.cpu().numpy().view(np.uint32) if pk is not None else None)
+
+
+def _check(ctx, tex_h, otex, q, filter, mode, spp, seed=1, shade="ggx", flags=0):
+    rgb, pk = _run(ctx, tex_h, q, filter, mode, spp, seed, shade, flags)
+    ref = oracle.filter_shade(otex, q, filter, mode, shade, spp, seed, flags, want_picks=True)
+    mism = compare_picks(pk, ref, q.n)
+    # positivized / signed estimators are differences of terms: scale the tolerance by the
+    # filter-after magnitude of the same query so cancellation is not mistaken for error
+    scale = None
+    if mode in ("positivized", "stochastic") and filter in ("mitchell", "catmull_rom"):
+        after = oracle.filter_shade(otex, q, filter, "ntap_after", shade, spp, seed, flags).rgb
+        scale = np.maximum(np.abs(ref.rgb), np.abs(after))
+    assert_values(rgb, ref.rgb, mism, scale=scale)
+    return rgb, ref
+
+
+# ---------------------------------------------------------------- config 1: RGBA32F bilinear
+@pytest.fixture(scope="module")
+def cfg1(ctx):
+    tex = synth.texture_rgba32f(256, 101)
+    q = synth.queries_uniform(65536, 1, const_derivs=(1 / 1024, 0.0, 0.0, 1 / 1024))
+    return ctx.create_texture([tex]), oracle.Texture([tex]), q
+
+
+@pytest.mark.parametrize("mode,spp", [("ntap_before", 1), ("stochastic", 1), ("stochastic", 16),
+                                      ("ntap_after", 4)])
+def test_config1_bilinear(ctx, cfg1, mode, spp):
+    h, otex, q = cfg1
+    _check(ctx, h, otex, q, "linear", mode, spp, seed=1)
+
+
+# ---------------------------------------------------------------- material with MIPs + normals
+@pytest.fixture(scope="module")
+def material(ctx):
+    m = synth.material_rgba8(256, 102, octaves=6, base=4)
+    q = synth.queries_uniform(6000, 3, res=256, lod_range=8.0)
+    return ctx.create_texture(m.albedo_rough, m.normal), oracle.Texture(m.albedo_rough, m.normal), q
+
+
+CASES = [(f, m) for f in ("linear", "bspline", "catmull_rom", "mitchell")
+         for m in ("ntap_before", "ntap_after", "stochastic", "positivized")
+         if not (m == "positivized" and f in ("linear", "bspline"))]
+
+
+@pytest.mark.parametrize("filter,mode", CASES)
+def test_material_filters(ctx, material, filter, mode):
+    h, otex, q = material
+    _check(ctx, h, otex, q, filter, mode, spp=3, seed=7)
+
+
+def test_material_linear_shade_and_stratified(ctx, material):
+    h, otex, q = material
+    _check(ctx, h, otex, q, "bspline", "ntap_after", spp=4, seed=5, shade="linear", flags=1)
+    _check(ctx, h, otex, q, "mitchell", "stochastic", spp=9, seed=5, flags=1)
+
+
+# ---------------------------------------------------------------- sizes and edge cases
+@pytest.mark.parametrize("n", [1, 7, 255, 257, 4097])
+def test_ragged_query_counts(ctx, material, n):
+    h, otex, q = material
+    _check(ctx, h, otex, q.subset(slice(0, n)), "bspline", "stochastic", spp=2, seed=11)
+
+
+def test_empty_batch_is_noop(ctx, material):
+    h, _, _ = material
+    e = torch.empty(0, device="cuda")
+    r, g, b, _ = ctx.filter_shade(h, e, e, None, "bspline", "stochastic", "ggx", 4, 1)
+    assert r.numel() == 0
+
+
+def test_npot_and_extreme_shapes(ctx):
+    # non-power-of-two, 1-texel and maximum-width textures (random texel bytes, every MIP
+    # level independent); uv far outside [0, 1) exercises wrap addressing
+    rng = np.random.default_rng(12)
+    for (hh, ww, lv) in [(37, 100, 1), (1, 1, 1), (2, 16384, 15), (16384, 1, 15), (300, 77, 9)]:
+        dims = [(max(1, hh >> i), max(1, ww >> i)) for i in range(lv)]
+        ar = [rng.integers(0, 256, (a, b, 4), dtype=np.uint8) for a, b in dims]
+        nm = [rng.integers(0, 256, (a, b, 2), dtype=np.uint8) for a, b in dims]
+        h = ctx.create_texture(ar, nm)
+        otex = oracle.Texture(ar, nm)
+        q = synth.queries_uniform(2000, 4, res=max(hh, ww), lod_range=float(lv))
+        q.u = (q.u * 7.0 - 3.0).astype(np.float32)
+        for f, mode in (("mitchell", "positivized"), ("bspline", "stochastic"), ("linear", "ntap_before"),
+                        ("catmull_rom", "ntap_after")):
+            _check(ctx, h, otex, q, f, mode, spp=2, seed=3)
+        ctx.destroy_texture(h)
+
+
+def test_id_base_shards_reproduce_whole(ctx, material):
+    # query ids key the Philox counter: two shards with id_base equal one launch
+    h, _, q = material
+    whole, _ = _run(ctx, h, q, "mitchell", "stochastic", 4, seed=21, picks=False)
+    a, _ = _run(ctx, h, q.subset(slice(0, 2500)), "mitchell", "stochastic", 4, seed=21, picks=False)
+    b, _ = _run(ctx, h, q.subset(slice(2500, None)), "mitchell", "stochastic", 4, seed=21, picks=False,
+                id_base=2500)
+    assert np.array_equal(np.concatenate([a, b]), whole)
+
+
+def test_nan_input_sets_device_status(ctx, material):
+    h, _, q = material
+    q2 = q.subset(slice(0, 64))
+    q2.u[5] = np.nan
+    ctx.device_status()
+    _run(ctx, h, q2, "linear", "stochastic", 1, picks=False)
+    import paper_2407_06107_b300 as stf
+    assert ctx.device_status() & stf.DEV_NAN_INPUT
+    assert ctx.device_status() == 0      # read clears
+
+
+def test_invalid_arguments(ctx, material):
+    import paper_2407_06107_b300 as stf
+    h, _, q = material
+    u, v, d = _dev(q.subset(slice(0, 16)))
+    with pytest.raises(stf.StfError) as e:
+        ctx.filter_shade(h, u, v, d, "bspline", "positivized", "ggx", 1, 1)
+    assert e.value.status == 5
+    with pytest.raises(stf.StfError) as e:
+        ctx.filter_shade(h, u, v, d, "bspline", "stochastic", "ggx", 0, 1)
+    assert e.value.status == 1
+    with pytest.raises(stf.StfError) as e:
+        ctx.filter_shade(h, u, v, d, "bspline", "stochastic", "ggx", 3, 1, flags=1)   # not square
+    assert e.value.status == 1
+    with pytest.raises(stf.StfError) as e:
+        ctx.filter_shade(h + 999, u, v, d, "bspline", "stochastic", "ggx", 1, 1)
+    assert e.value.status == 2
+
+
+def test_host_entry_point_matches_device(ctx, material):
+    h, _, q = material
+    dev, pk = _run(ctx, h, q, "mitchell", "positivized", 2, seed=8)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    r, g, b, pk2 = ctx.filter_shade_host(h, f(q.u), f(q.v), [f(q.dudx), f(q.dvdx), f(q.dudy), f(q.dvdy)],
+                                         "mitchell", "positivized", "ggx", 2, 8, want_picks=True)
+    assert np.array_equal(np.stack([r, g, b], 1).astype(np.float64), dev)
+    assert np.array_equal(pk2, pk)
+
+
+# ---------------------------------------------------------------- full size, sampled
+@pytest.mark.parametrize("filter", ["linear", "bspline", "mitchell"])
+def test_full_size_sampled(ctx, filter):
+    # the benchmark workload (4096^2 material with MIPs, 16M queries, 8 spp) in the
+    # launch configuration bench.py times; a seeded sample of queries is re-evaluated by
+    # the oracle with the same Philox ids
+    m = _full_material()
+    h = _full_handle(ctx, m)
+    q = synth.queries_uniform(1 << 24, 1, res=4096, lod_range=8.0)
+    u, v, d = _dev(q)
+    r, g, b, _ = ctx.filter_shade(h, u, v, d, filter, "stochastic", "ggx", 8, 1)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(99).choice(q.n, 3000, replace=False))
+    rgb = torch.stack([r, g, b], 1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    ref = oracle.filter_shade(oracle.Texture(m.albedo_rough, m.normal), q.subset(idx), filter,
+                              "stochastic", "ggx", 8, 1, ids=idx)
+    scale = None
+    if filter == "mitchell":
+        scale = np.maximum(np.abs(ref.rgb), oracle.filter_shade(
+            oracle.Texture(m.albedo_rough, m.normal), q.subset(idx), filter, "ntap_after", "ggx", 8, 1, ids=idx).rgb)
+    near = ref.bdist < 1e-6
+    assert near.sum() <= 3
+    assert_values(rgb, ref.rgb, near, scale=scale)
+
+
+_FULL = {}
+
+
+def _full_material():
+    if "m" not in _FULL:
+        _FULL["m"] = synth.material_rgba8(4096, 102)
+    return _FULL["m"]
+
+
+def _full_handle(ctx, m):
+    if "h" not in _FULL:
+        _FULL["h"] = ctx.create_texture(m.albedo_rough, m.normal)
+    return _FULL["h"]
