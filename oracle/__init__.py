@@ -75,7 +75,7 @@ def lib():
         L.orc_shade_batch.argtypes = [C.c_uint64, C.c_int, P, P, P, P]
         L.orc_fetch.argtypes = [C.POINTER(_Tex), C.c_int, C.c_int, C.c_int, P]
         L.orc_filter_shade.argtypes = [C.POINTER(_Tex), C.c_uint64] + [P] * 7 + [
-            C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, C.c_int]
+            C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, C.c_int]
         L.orc_march.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_float, P, C.c_uint32, C.c_uint32,
                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                 C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
@@ -191,6 +191,7 @@ class FilterResult:
     picks: np.ndarray | None   # (n, spp, 2) uint32, FP32 decisions (level<<28 | iy<<14 | ix)
     picks64: np.ndarray | None  # same, FP64 decisions (NO_PICK-1 where the level differs)
     bdist: np.ndarray | None   # (n,) distance of the nearest uniform to an FP64 boundary
+    mag: np.ndarray | None = None  # (n, 3) mean over samples of sum |w f_hat| over the summed terms
 
 
 def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", spp: int = 1,
@@ -202,16 +203,17 @@ def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", sp
     picks = np.zeros((n, spp, 2), dtype=np.uint32) if want_picks else None
     picks64 = np.zeros((n, spp, 2), dtype=np.uint32) if want_picks else None
     bd = np.zeros(n)
+    mag = np.zeros((n, 3))
     t = tex._struct()
     arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None
             for a in (q.u, q.v, q.dudx, q.dvdx, q.dudy, q.dvdy)]
     ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint64)
     rc = lib().orc_filter_shade(C.byref(t), n, *[_p(a) for a in arrs], _p(ids), FILTERS[filter], MODES[mode],
                                 SHADES[shade], spp, seed, flags, _p(rgb), _p(picks), _p(picks64),
-                                _p(bd), nthreads or nthreads_default())
+                                _p(bd), _p(mag), nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("oracle: invalid filter_shade arguments")
-    return FilterResult(rgb, picks, picks64, bd)
+    return FilterResult(rgb, picks, picks64, bd, mag)
 
 
 @dataclass

@@ -297,6 +297,7 @@ struct Out {
     uint32_t* picks;    // n*spp*2 or null (FP32 decisions)
     uint32_t* picks64;  // n*spp*2 or null (FP64 decisions)
     double* bdist;      // n or null: min distance of any uniform to an FP64 boundary
+    double* mag;        // n*3 or null: mean over samples of sum |term| (scale of the sum)
 };
 
 // per level: FP32 texel position and tap geometry on one axis
@@ -320,7 +321,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
     if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs(lam64 - std::nearbyint(lam64)));
     int nt = ntaps(filter), ft = first_tap(filter);
     bool sgn = signed_filter(filter);
-    double acc[3] = {0, 0, 0};
+    double acc[3] = {0, 0, 0}, mag[3] = {0, 0, 0};
     int kside = 1;
     if (flags & FLAG_STRATIFIED) { kside = (int)std::lround(std::sqrt((double)spp)); }
 
@@ -376,7 +377,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                         } else {
                             double o[3];
                             shade(smode, m, o);
-                            for (int c = 0; c < 3; ++c) fsum[c] += w * o[c];
+                            for (int c = 0; c < 3; ++c) { fsum[c] += w * o[c]; mag[c] += std::fabs(w * o[c]); }
                         }
                     }
                 }
@@ -385,6 +386,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 double ln = std::sqrt(dot(fm.n, fm.n));
                 fm.n = ln > 0 ? V3{fm.n.x / ln, fm.n.y / ln, fm.n.z / ln} : V3{0, 0, 1};
                 shade(smode, fm, est);
+                for (int c = 0; c < 3; ++c) mag[c] += std::fabs(est[c]);
             } else {
                 for (int c = 0; c < 3; ++c) est[c] = fsum[c];
             }
@@ -428,7 +430,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                     for (int k = 0; k < nt; ++k) { sx += std::fabs(wx64[k]); sy += std::fabs(wy64[k]); }
                     Wt = sx * sy * ((wx64[kx] < 0) != (wy64[ky] < 0) ? -1.0 : 1.0);
                 }
-                for (int c = 0; c < 3; ++c) est[c] = Wt * o[c];
+                for (int c = 0; c < 3; ++c) { est[c] = Wt * o[c]; mag[c] += std::fabs(est[c]); }
                 if (pk) pk[0] = pack2d(lvl, t.first, t.second);
                 if (pk64) {
                     auto t64 = texel(lvl64, kx64, ky64);
@@ -458,7 +460,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 auto tp = texel(lvl, kx, ky);
                 double o[3];
                 shade(smode, fetch(T, lvl, tp.first, tp.second), o);
-                for (int c = 0; c < 3; ++c) est[c] = Wp64 * o[c];
+                for (int c = 0; c < 3; ++c) { est[c] = Wp64 * o[c]; mag[c] += std::fabs(est[c]); }
                 if (pk) pk[0] = pack2d(lvl, tp.first, tp.second);
                 if (pk64) {
                     auto t64 = texel(lvl64, kx64, ky64);
@@ -477,7 +479,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                     int qy64 = pick64(wy64, nt, unif(r1[3]), -nx64, &bd);
                     auto tn = texel(lvl, qx, qy);
                     shade(smode, fetch(T, lvl, tn.first, tn.second), o);
-                    for (int c = 0; c < 3; ++c) est[c] -= Wn64 * o[c];
+                    for (int c = 0; c < 3; ++c) { est[c] -= Wn64 * o[c]; mag[c] += std::fabs(Wn64 * o[c]); }
                     if (pk) pk[1] = pack2d(lvl, tn.first, tn.second);
                     if (pk64) {
                         auto t64 = texel(lvl64, qx64, qy64);
@@ -489,6 +491,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
         for (int c = 0; c < 3; ++c) acc[c] += est[c];
     }
     for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c] / (double)spp;
+    if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c] / (double)spp;
     if (O.bdist) O.bdist[q] = bd;
 }
 
@@ -681,7 +684,7 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
                      const float* dudx, const float* dvdx, const float* dudy, const float* dvdy,
                      const uint64_t* ids, int filter, int mode, int smode, uint32_t spp, uint64_t seed,
                      uint32_t flags, double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist,
-                     int nthreads) {
+                     double* mag, int nthreads) {
     if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 3 || mode < 0 || mode > 3) return 1;
     if (tex->levels < 1 || tex->levels > 16) return 1;
     if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
@@ -691,7 +694,7 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
     }
     Tex T; std::memcpy(&T, tex, sizeof(Tex));
     Queries Q{n, u, v, dudx, dvdx, dudy, dvdy};
-    Out O{rgb, picks, picks64, bdist};
+    Out O{rgb, picks, picks64, bdist, mag};
     parallel_for(n, nthreads, [&](uint64_t q) {
         run_query(T, Q, q, ids ? ids[q] : q, filter, mode, smode, spp, seed, flags, O);
     });

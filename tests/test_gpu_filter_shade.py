@@ -42,13 +42,10 @@ def _check(ctx, tex_h, otex, q, filter, mode, spp, seed=1, shade="ggx", flags=0)
     rgb, pk = _run(ctx, tex_h, q, filter, mode, spp, seed, shade, flags)
     ref = oracle.filter_shade(otex, q, filter, mode, shade, spp, seed, flags, want_picks=True)
     mism = compare_picks(pk, ref, q.n)
-    # positivized / signed estimators are differences of terms: scale the tolerance by the
-    # filter-after magnitude of the same query so cancellation is not mistaken for error
-    scale = None
-    if mode in ("positivized", "stochastic") and filter in ("mitchell", "catmull_rom"):
-        after = oracle.filter_shade(otex, q, filter, "ntap_after", shade, spp, seed, flags).rgb
-        scale = np.maximum(np.abs(ref.rgb), np.abs(after))
-    assert_values(rgb, ref.rgb, mism, scale=scale)
+    # every summed term (w f_hat, or +-W f_hat) carries its own FP32 relative error, so
+    # the tolerance scales with the sum of |terms|: cancellation between signed terms is
+    # not mistaken for error
+    assert_values(rgb, ref.rgb, mism, scale=ref.mag)
     return rgb, ref
 
 
@@ -113,7 +110,7 @@ def test_npot_and_extreme_shapes(ctx):
     for (hh, ww, lv) in [(37, 100, 1), (1, 1, 1), (2, 16384, 15), (16384, 1, 15), (300, 77, 9)]:
         dims = [(max(1, hh >> i), max(1, ww >> i)) for i in range(lv)]
         ar = [rng.integers(0, 256, (a, b, 4), dtype=np.uint8) for a, b in dims]
-        nm = [rng.integers(0, 256, (a, b, 2), dtype=np.uint8) for a, b in dims]
+        nm = [rng.integers(64, 192, (a, b, 2), dtype=np.uint8) for a, b in dims]   # normals within ~30 deg of +z
         h = ctx.create_texture(ar, nm)
         otex = oracle.Texture(ar, nm)
         q = synth.queries_uniform(2000, 4, res=max(hh, ww), lod_range=float(lv))
@@ -189,13 +186,9 @@ def test_full_size_sampled(ctx, filter):
     rgb = torch.stack([r, g, b], 1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
     ref = oracle.filter_shade(oracle.Texture(m.albedo_rough, m.normal), q.subset(idx), filter,
                               "stochastic", "ggx", 8, 1, ids=idx)
-    scale = None
-    if filter == "mitchell":
-        scale = np.maximum(np.abs(ref.rgb), oracle.filter_shade(
-            oracle.Texture(m.albedo_rough, m.normal), q.subset(idx), filter, "ntap_after", "ggx", 8, 1, ids=idx).rgb)
     near = ref.bdist < 1e-6
     assert near.sum() <= 3
-    assert_values(rgb, ref.rgb, near, scale=scale)
+    assert_values(rgb, ref.rgb, near, scale=ref.mag)
 
 
 _FULL = {}
