@@ -380,6 +380,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_volume(args):
+    """Volume workload: 512^3 FP16 cloud, 128 steps, one march launch per step (single GPU)."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    W, H, steps = args.width, args.height, 128
+    vh = ctx.create_volume(synth.volume_cloud(512, 103), 20.0)
+    cam = synth.camera_pinhole(W, H).as_array()
+    out = torch.empty(W * H, dtype=torch.float32, device=dev)
+    go = lambda: ctx.march_volume(vh, cam, W, H, steps, args.vfilter, args.vmode, spp=SPP, seed=5, out=out)
+    for _ in range(args.warmup):
+        go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            go()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    units = W * H * SPP * steps
+    print(json.dumps({"metric": "ray-march step lookups/s", "value": units / (ms / 1e3), "unit": "lookups/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "config": {"workload": f"volume 512^3 FP16 cloud, {W}x{H}, 128 steps, "
+                                             f"{args.vfilter} {args.vmode}, {SPP} spp"},
+                      "clocks": clk.summary()}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,11 +424,18 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1 << 13)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="material", choices=["material", "volume"])
+    ap.add_argument("--vfilter", default="bspline", choices=["bspline", "linear"])
+    ap.add_argument("--vmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after"])
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "volume":
+        run_volume(args)
     else:
         run_ours(args)
 
