@@ -86,6 +86,7 @@ typedef enum { STF_ADDRESS_WRAP = 0, STF_ADDRESS_CLAMP = 1 } stf_address;
 /* device status bits */
 #define STF_DEV_NAN_INPUT 1u
 #define STF_DEV_BAD_INDEX 2u
+#define STF_DEV_TIMEOUT 4u      /* a bounded device wait gave up (tensor-core decode) */
 
 #define STF_MAX_LEVELS 16
 
@@ -168,6 +169,74 @@ stf_status stf_march_volume(stf_ctx ctx, stf_vol vol, const float* cam, uint32_t
                             uint32_t height, uint32_t steps, stf_filter filter, stf_mode mode,
                             uint32_t spp, uint64_t seed, uint32_t flags, uint64_t pix_begin,
                             uint64_t pix_count, float* out_T, uint32_t* out_picks);
+
+/* ---- learned form: neural texture ----------------------------------------------------
+ * A tex_res x tex_res texture of 8 channels (albedo RGB, roughness, normal XY, metalness,
+ * height; each byte/255) represented by 4 latent grids (8 channels each, grid_res[g]^2
+ * texels, sampled bilinearly with wrap at the texel centre) and an MLP 32 -> 64 (ReLU)
+ * -> 64 (ReLU) -> 8 with BF16 weights and FP32 accumulation.  The paper cites learned
+ * texture compression as an expensive-to-decode representation that stochastic filtering
+ * decodes once per lookup (Sec. 1, Sec. 5); the network itself is this library's.
+ * Training: MSE on texels drawn by Philox (ctr = (sample, step, 0, 0x4E54), key = seed),
+ * analytic backward, Adam (Kingma & Ba 2015). */
+typedef uint64_t stf_neural;
+
+typedef struct {
+    uint32_t tex_res;               /* decoded texture size, 1 .. 16384                     */
+    uint32_t grid_res[4];           /* latent grid sizes, 1 .. 4096                          */
+    const float* const* latent_init;/* 4 host arrays [grid_res^2][8] FP32                   */
+    const float* mlp_init;          /* host FP32 [6792] = W1[64x32] b1[64] W2[64x64] b2[64]
+                                       W3[8x64] b3[8], row-major [out][in]                  */
+    const uint8_t* targets;         /* host [tex_res^2][8] bytes, nullable (no training)     */
+} stf_neural_desc;
+
+typedef struct { float lr_latent, lr_mlp, beta1, beta2, eps; } stf_adam_params;
+
+typedef enum {
+    STF_LATENT_FP16 = 0,            /* inference latents FP16 (round to nearest even)        */
+    STF_LATENT_FP8_E4M3 = 1         /* FP8 E4M3 with a per-grid FP32 scale = max|l| / 448   */
+} stf_latent_format;
+
+typedef enum {                      /* stf_neural_get / stf_neural_set blocks                */
+    STF_NEURAL_LATENTS = 0,         /* FP32 master latents, all grids concatenated           */
+    STF_NEURAL_MLP = 1,             /* FP32 master MLP [6792]                                */
+    STF_NEURAL_GRAD_LATENTS = 2,    /* FP32 latent gradients                                 */
+    STF_NEURAL_GRAD_MLP = 3,        /* FP32 MLP gradients                                    */
+    STF_NEURAL_ADAM = 4,            /* FP32 Adam moments: m_lat, v_lat, m_mlp, v_mlp         */
+    STF_NEURAL_SCALES = 5,          /* FP32 [4] FP8 per-grid scales                          */
+    STF_NEURAL_STEP = 6             /* uint32 optimiser step counter                         */
+} stf_neural_block;
+
+stf_status stf_neural_create(stf_ctx ctx, const stf_neural_desc* desc, stf_neural* out);
+stf_status stf_neural_destroy(stf_ctx ctx, stf_neural net);
+/* `steps` optimiser steps of `batch` samples each (batch <= 2^24); losses: nullable host
+ * array [steps] receiving each step's mean squared error.  Re-quantises the inference
+ * form with the current latent format afterwards.  Synchronises the stream. */
+stf_status stf_neural_train(stf_ctx ctx, stf_neural net, uint32_t steps, uint32_t batch,
+                            const stf_adam_params* adam, uint64_t seed, float* losses);
+/* Gradients of one batch without an update (they replace the gradient blocks): the step
+ * index selects the Philox samples, or ex_ix/ex_iy (device int32 [batch], nullable)
+ * give the texels.  loss: host float. */
+stf_status stf_neural_grad(stf_ctx ctx, stf_neural net, uint32_t step, uint32_t batch, uint64_t seed,
+                           const int32_t* ex_ix, const int32_t* ex_iy, float* loss);
+/* Build the inference form (BF16 weights, FP16 or FP8 latents) from the FP32 masters. */
+stf_status stf_neural_quantize(stf_ctx ctx, stf_neural net, stf_latent_format fmt);
+/* Copy a block to / from host memory; bytes must equal the block size. Synchronous. */
+stf_status stf_neural_get(stf_ctx ctx, stf_neural net, stf_neural_block what, void* host, size_t bytes);
+stf_status stf_neural_set(stf_ctx ctx, stf_neural net, stf_neural_block what, const void* host, size_t bytes);
+/* Checkpoint: latents, MLP, Adam moments and step counter to / from a file. */
+stf_status stf_neural_save(stf_ctx ctx, stf_neural net, const char* path);
+stf_status stf_neural_load(stf_ctx ctx, stf_neural net, const char* path);
+/* Decode explicit texels on the tensor cores: ix, iy device int32 [n]; y device FP32 [n][8]. */
+stf_status stf_neural_decode(stf_ctx ctx, stf_neural net, uint64_t n, const int32_t* ix, const int32_t* iy,
+                             float* y);
+/* Filter + shade on the decoded texture (level 0, wrap): STOCHASTIC = one decode per
+ * sample (POSITIVIZED: two), NTAP_BEFORE = decode every tap, filter, shade once
+ * (decode-then-filter), NTAP_AFTER = decode and shade every tap.  Same queries, jitter,
+ * RNG and estimators as stf_filter_shade; flags must be 0; picks are not reported. */
+stf_status stf_neural_filter_shade(stf_ctx ctx, stf_neural net, const stf_queries* q, const stf_derivs* d,
+                                   stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
+                                   uint64_t seed, uint32_t flags, const stf_output* out);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,8 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "stf_oracle.cpp")
+SRCS = [os.path.join(HERE, f) for f in ("stf_oracle.cpp", "ntc_oracle.cpp")]
+DEPS = SRCS + [os.path.join(HERE, "oracle_internal.h")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3}
@@ -35,9 +36,9 @@ NO_PICK = 0xFFFFFFFF
 
 
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    if force or not os.path.exists(LIB) or any(os.path.getmtime(LIB) < os.path.getmtime(p) for p in DEPS):
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-pthread", SRC, "-o", LIB + ".tmp"]
+               "-shared", "-pthread", *SRCS, "-o", LIB + ".tmp"]
         subprocess.run(cmd, check=True)
         os.replace(LIB + ".tmp", LIB)
     return LIB
@@ -47,6 +48,15 @@ class _Tex(C.Structure):
     _fields_ = [("format", C.c_int), ("levels", C.c_int), ("address", C.c_int),
                 ("width", C.c_int * 16), ("height", C.c_int * 16),
                 ("data", C.c_void_p * 16), ("normal", C.c_void_p * 16)]
+
+
+class _Mlp(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+class _NeuralTex(C.Structure):
+    _fields_ = [("tex_res", C.c_int), ("res", C.c_int * 4), ("latent_fmt", C.c_int), ("grid", C.c_void_p * 4),
+                ("scale", C.c_float * 4), ("mlp", C.POINTER(_Mlp))]
 
 
 _lib = None
@@ -75,10 +85,21 @@ def lib():
         L.orc_shade_batch.argtypes = [C.c_uint64, C.c_int, P, P, P, P]
         L.orc_fetch.argtypes = [C.POINTER(_Tex), C.c_int, C.c_int, C.c_int, P]
         L.orc_filter_shade.argtypes = [C.POINTER(_Tex), C.c_uint64] + [P] * 7 + [
-            C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, C.c_int]
+            C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, P, C.c_int]
         L.orc_march.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_float, P, C.c_uint32, C.c_uint32,
                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                 C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
+        D = C.c_double
+        for nm in ("orc_round_bf16", "orc_round_fp16", "orc_round_e4m3"):
+            getattr(L, nm).argtypes = [D]
+            getattr(L, nm).restype = D
+        L.orc_e4m3_value.argtypes = [C.c_uint8]
+        L.orc_e4m3_value.restype = D
+        L.orc_ntc_features.argtypes = [C.POINTER(_NeuralTex), C.c_uint64, P, P, P]
+        L.orc_ntc_decode.argtypes = [C.POINTER(_NeuralTex), C.c_uint64, P, P, P, P]
+        L.orc_ntc_loss_grad.argtypes = [C.POINTER(_NeuralTex)] + [P] * 7 + [C.c_uint64, P, P, C.c_int] + [P] * 7
+        L.orc_ntc_loss_grad.restype = D
+        L.orc_adam.argtypes = [C.c_uint64, P, P, P, P, C.c_int, D, D, D, D]
         _lib = L
     return _lib
 
@@ -160,8 +181,16 @@ class Texture:
     normal: list | None = None   # (H, W, 2) uint8 per level, or None
     address: str = "wrap"
 
+    neural: "NeuralTexture | None" = None
+
     def _struct(self):
         t = _Tex()
+        if self.neural is not None:       # learned texture: one level decoded by the MLP
+            t.format, t.levels, t.address = 2, 1, 0
+            t.width[0] = t.height[0] = self.neural.tex_res
+            self._nt = self.neural._struct()
+            t.data[0] = C.cast(C.pointer(self._nt), C.c_void_p).value
+            return t
         fmt = 0 if self.levels[0].dtype == np.float32 else 1
         t.format, t.levels = fmt, len(self.levels)
         t.address = 0 if self.address == "wrap" else 1
@@ -192,6 +221,7 @@ class FilterResult:
     picks64: np.ndarray | None  # same, FP64 decisions (NO_PICK-1 where the level differs)
     bdist: np.ndarray | None   # (n,) distance of the nearest uniform to an FP64 boundary
     mag: np.ndarray | None = None  # (n, 3) mean over samples of sum |w f_hat| over the summed terms
+    rdist: np.ndarray | None = None  # (n,) learned texels: min relative distance to a BF16 rounding boundary
 
 
 def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", spp: int = 1,
@@ -204,16 +234,17 @@ def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", sp
     picks64 = np.zeros((n, spp, 2), dtype=np.uint32) if want_picks else None
     bd = np.zeros(n)
     mag = np.zeros((n, 3))
+    rdist = np.ones(n)
     t = tex._struct()
     arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None
             for a in (q.u, q.v, q.dudx, q.dvdx, q.dudy, q.dvdy)]
     ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint64)
     rc = lib().orc_filter_shade(C.byref(t), n, *[_p(a) for a in arrs], _p(ids), FILTERS[filter], MODES[mode],
                                 SHADES[shade], spp, seed, flags, _p(rgb), _p(picks), _p(picks64),
-                                _p(bd), _p(mag), nthreads or nthreads_default())
+                                _p(bd), _p(mag), _p(rdist), nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("oracle: invalid filter_shade arguments")
-    return FilterResult(rgb, picks, picks64, bd, mag)
+    return FilterResult(rgb, picks, picks64, bd, mag, rdist)
 
 
 @dataclass
@@ -245,3 +276,145 @@ def march(vol: np.ndarray, sigma_scale: float, cam: np.ndarray, width: int, heig
     if rc != 0:
         raise ValueError("oracle: invalid march arguments")
     return MarchResult(T, picks, bd)
+
+
+# ----------------------------------------------------------------------------- learned form
+def round_bf16(x) -> np.ndarray:
+    return np.array([lib().orc_round_bf16(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def round_fp16(x) -> np.ndarray:
+    return np.array([lib().orc_round_fp16(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def round_e4m3(x) -> np.ndarray:
+    return np.array([lib().orc_round_e4m3(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def e4m3_value(codes) -> np.ndarray:
+    return np.array([lib().orc_e4m3_value(int(c)) for c in np.ravel(codes)]).reshape(np.shape(codes))
+
+
+def _e4m3_codes(values: np.ndarray) -> np.ndarray:
+    """FP8 E4M3 codes of values that are already E4M3-representable (table lookup)."""
+    table = np.array([lib().orc_e4m3_value(c) for c in range(256)])
+    out = np.zeros(values.shape, dtype=np.uint8)
+    flat = values.ravel()
+    pos = {float(table[c]): c for c in range(256) if not np.isnan(table[c]) and (c & 0x80) == 0}
+    neg = {float(table[c]): c for c in range(128, 256) if not np.isnan(table[c])}
+    o = out.ravel()
+    for i, v in enumerate(flat):
+        o[i] = pos[float(v)] if (v > 0 or (v == 0 and not np.signbit(v))) else neg[float(v)]
+    return out
+
+
+@dataclass
+class NeuralTexture:
+    """Latents: 4 grids (R, R, 8) as float16 (fmt 'fp16'), float32 ('fp32'), or FP8
+    E4M3 codes (uint8, 'fp8') with per-grid scales.  MLP weights as float64 copies of the
+    values the decode uses (BF16-rounded for inference)."""
+    tex_res: int
+    grids: list
+    mlp: np.ndarray               # [6792] W1 b1 W2 b2 W3 b3
+    fmt: str = "fp16"
+    scales: tuple = (1.0, 1.0, 1.0, 1.0)
+
+    def _struct(self):
+        m = np.asarray(self.mlp, dtype=np.float64)
+        cut = np.cumsum([0, 2048, 64, 4096, 64, 512, 8])
+        self._parts = [np.ascontiguousarray(m[cut[i]:cut[i + 1]]) for i in range(6)]
+        self._mlp = _Mlp(*[p.ctypes.data for p in self._parts])
+        if self.fmt == "fp16":
+            gs = [np.ascontiguousarray(g, dtype=np.float16).view(np.uint16) for g in self.grids]
+            f = 0
+        elif self.fmt == "fp8":
+            gs = [np.ascontiguousarray(g, dtype=np.uint8) for g in self.grids]
+            f = 1
+        else:
+            gs = [np.ascontiguousarray(g, dtype=np.float32) for g in self.grids]
+            f = 2
+        self._grids = gs
+        s = _NeuralTex(self.tex_res, (C.c_int * 4)(*[g.shape[0] for g in gs]), f,
+                       (C.c_void_p * 4)(*[g.ctypes.data for g in gs]), (C.c_float * 4)(*self.scales),
+                       C.pointer(self._mlp))
+        return s
+
+    @staticmethod
+    def inference_form(tex_res: int, lat32, mlp32, fmt: str = "fp16") -> "NeuralTexture":
+        """The quantised inference form of FP32 master parameters, built by the oracle's
+        own codecs: BF16 weights (biases FP32), FP16 latents, or FP8 E4M3 latents with a
+        per-grid scale max|l| / 448 (FP32 arithmetic: scale = amax / 448, code =
+        E4M3(l * (1 / scale)))."""
+        m = np.asarray(mlp32, dtype=np.float32).astype(np.float64)
+        cut = np.cumsum([0, 2048, 64, 4096, 64, 512, 8])
+        w = m.copy()
+        for a, b in ((0, 1), (2, 3), (4, 5)):
+            w[cut[a]:cut[b]] = round_bf16(m[cut[a]:cut[b]].astype(np.float32))
+        if fmt == "fp16":
+            return NeuralTexture(tex_res, [np.asarray(g, np.float32).astype(np.float16) for g in lat32], w, "fp16")
+        scales, codes = [], []
+        for g in lat32:
+            g = np.asarray(g, dtype=np.float32)
+            amax = np.float32(np.max(np.abs(g)))
+            sc = np.float32(max(amax, np.float32(1e-30)) / np.float32(448.0))
+            inv = np.float32(np.float32(1.0) / sc)
+            vals = round_e4m3((g * inv).astype(np.float32))
+            codes.append(_e4m3_codes(vals))
+            scales.append(float(sc))
+        return NeuralTexture(tex_res, codes, w, "fp8", tuple(scales))
+
+
+def ntc_features(nt: NeuralTexture, ix, iy) -> np.ndarray:
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    out = np.zeros((len(ix), 32), dtype=np.float32)
+    s = nt._struct()
+    lib().orc_ntc_features(C.byref(s), len(ix), _p(ix), _p(iy), _p(out))
+    return out
+
+
+def ntc_decode(nt: NeuralTexture, ix, iy):
+    """(y [n, 8] float64, rdist [n]): decode and min relative distance to a BF16 boundary."""
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    y = np.zeros((len(ix), 8))
+    rd = np.zeros(len(ix))
+    s = nt._struct()
+    lib().orc_ntc_decode(C.byref(s), len(ix), _p(ix), _p(iy), _p(y), _p(rd))
+    return y, rd
+
+
+def ntc_loss_grad(tex_res: int, lat32, mlp32, targets, ix, iy, round_bf16: bool = True):
+    """Loss and gradients of one batch from FP32 master parameters."""
+    nt = NeuralTexture(tex_res, [np.asarray(g, np.float32) for g in lat32], np.zeros(6792), "fp32")
+    s = nt._struct()
+    m = np.ascontiguousarray(mlp32, dtype=np.float32)
+    cut = np.cumsum([0, 2048, 64, 4096, 64, 512, 8])
+    parts = [np.ascontiguousarray(m[cut[i]:cut[i + 1]]) for i in range(6)]
+    grads = [np.zeros(p.size) for p in parts]
+    dl = [np.zeros(np.asarray(g).size) for g in lat32]
+    dlp = (C.c_void_p * 4)(*[g.ctypes.data for g in dl])
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    tg = np.ascontiguousarray(targets, dtype=np.uint8)
+    loss = lib().orc_ntc_loss_grad(C.byref(s), *[_p(p) for p in parts], _p(tg), len(ix), _p(ix), _p(iy),
+                                   1 if round_bf16 else 0, *[_p(g) for g in grads], dlp)
+    return loss, np.concatenate(grads), np.concatenate(dl)
+
+
+def adam(p, g, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place FP64 Adam step on float64 arrays."""
+    lib().orc_adam(p.size, _p(p), _p(g), _p(m), _p(v), t, lr, beta1, beta2, eps)
+
+
+def ntc_sample_texels(step: int, batch: int, seed: int, tex_res: int):
+    """Training texels of one optimiser step: Philox(ctr = (k, step, 0, 0x4E54), key = seed),
+    ix = mulhi(word0, tex_res), iy = mulhi(word1, tex_res)."""
+    ix = np.zeros(batch, dtype=np.int32)
+    iy = np.zeros(batch, dtype=np.int32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for k in range(batch):
+        w = philox([k, step, 0, 0x4E54], key)
+        ix[k] = (int(w[0]) * tex_res) >> 32
+        iy[k] = (int(w[1]) * tex_res) >> 32
+    return ix, iy

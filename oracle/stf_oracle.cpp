@@ -35,6 +35,8 @@
 #include <thread>
 #include <vector>
 
+#include "oracle_internal.h"
+
 namespace {
 
 // ------------------------------------------------------------------ enums (API values)
@@ -42,7 +44,7 @@ enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
 enum { FLAG_STRATIFIED = 1u };
-enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
+enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_NEURAL = 2 };
 enum { ADDR_WRAP = 0, ADDR_CLAMP = 1 };
 const uint32_t NO_PICK = 0xFFFFFFFFu;
 
@@ -71,6 +73,22 @@ void draw(uint64_t seed, uint64_t id, uint32_t sample, uint32_t stream, uint32_t
 
 // uniform in [0,1) on the 2^-24 grid; exactly representable in float and double
 inline float unif(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
+
+// Five 24-bit uniforms from one Philox output: the high 24 bits of each word, and a fifth
+// assembled from the low bytes of words 0, 1 and 2 (bits no other uniform uses).
+void uniforms5(const uint32_t w[4], float u[5]) {
+    for (int i = 0; i < 4; ++i) u[i] = unif(w[i]);
+    uint32_t f = ((w[0] & 0xFFu) << 16) | ((w[1] & 0xFFu) << 8) | (w[2] & 0xFFu);
+    u[4] = (float)f * 5.9604644775390625e-8f;
+}
+
+// Six 21-bit uniforms from one Philox output (two volume march steps, three each).
+void uniforms6(const uint32_t w[4], float u[6]) {
+    const float k = 4.76837158203125e-7f;   // 2^-21
+    for (int i = 0; i < 4; ++i) u[i] = (float)(w[i] >> 11) * k;
+    u[4] = (float)((w[0] & 0x7FFu) | ((w[1] & 0x3FFu) << 11)) * k;
+    u[5] = (float)((w[2] & 0x7FFu) | ((w[3] & 0x3FFu) << 11)) * k;
+}
 
 // ------------------------------------------------------------------ 1-D kernels, FP64
 // supplement "Filter Kernels": tent K1, Keys cubic K3(a), cubic B-spline K_bs;
@@ -237,8 +255,29 @@ int wrapi(int i, int n, int addr) {
     return r < 0 ? r + n : r;
 }
 
-Mat fetch(const Tex& T, int lvl, int ix, int iy) {
+inline double clamp01(double x) { return std::min(std::max(x, 0.0), 1.0); }
+
+// Map the 8 decoded channels of a learned texel to the material: albedo RGB, roughness,
+// tangent-space normal XY (z reconstructed); channels 6 and 7 (metalness, height) are not
+// used by the shade.
+Mat material_from_channels(const double y[8]) {
     Mat m;
+    for (int c = 0; c < 3; ++c) m.rho[c] = clamp01(y[c]);
+    m.rough = 0.05 + 0.95 * clamp01(y[3]);
+    double x = 2.0 * clamp01(y[4]) - 1.0, yy = 2.0 * clamp01(y[5]) - 1.0;
+    double z = std::sqrt(std::max(0.0, 1.0 - x * x - yy * yy));
+    double l = std::sqrt(x * x + yy * yy + z * z);
+    m.n = l > 0 ? V3{x / l, yy / l, z / l} : V3{0.0, 0.0, 1.0};
+    return m;
+}
+
+Mat fetch(const Tex& T, int lvl, int ix, int iy, double* rdist = nullptr) {
+    Mat m;
+    if (T.format == FMT_NEURAL) {     // learned texel: one MLP decode
+        double y[8];
+        orc::neural_decode(*(const orc::NeuralTex*)T.data[0], ix, iy, y, rdist);
+        return material_from_channels(y);
+    }
     size_t o = (size_t)iy * T.width[lvl] + ix;
     if (T.format == FMT_RGBA32F) {
         const float* p = (const float*)T.data[lvl] + 4 * o;
@@ -298,6 +337,7 @@ struct Out {
     uint32_t* picks64;  // n*spp*2 or null (FP64 decisions)
     double* bdist;      // n or null: min distance of any uniform to an FP64 boundary
     double* mag;        // n*3 or null: mean over samples of sum |term| (scale of the sum)
+    double* rdist;      // n or null: min relative distance of a BF16 decision to a boundary
 };
 
 // per level: FP32 texel position and tap geometry on one axis
@@ -322,14 +362,19 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
     int nt = ntaps(filter), ft = first_tap(filter);
     bool sgn = signed_filter(filter);
     double acc[3] = {0, 0, 0}, mag[3] = {0, 0, 0};
+    double rd = 1.0;
     int kside = 1;
     if (flags & FLAG_STRATIFIED) { kside = (int)std::lround(std::sqrt((double)spp)); }
 
     for (uint32_t s = 0; s < spp; ++s) {
-        uint32_t r0[4], r1[4], r2[4];
+        // stream 0: (jitter x, jitter y, level, pick x, pick y); stream 1 (positivization):
+        // (positive class, negative pick x, negative pick y, negative class, -)
+        uint32_t r0[4], r1[4];
         draw(seed, id, s, 0, r0);
         draw(seed, id, s, 1, r1);
-        draw(seed, id, s, 2, r2);
+        float a[5], b[5];
+        uniforms5(r0, a);
+        uniforms5(r1, b);
         // screen-space jitter inside the pixel footprint (FP32, fixed order)
         float x = Q.u[q], y = Q.v[q];
         if (Q.dudx) {
@@ -338,8 +383,8 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 jx = ((float)(s % kside) + 0.5f) / (float)kside - 0.5f;
                 jy = ((float)(s / kside) + 0.5f) / (float)kside - 0.5f;
             } else {
-                jx = unif(r0[0]) - 0.5f;
-                jy = unif(r0[1]) - 0.5f;
+                jx = a[0] - 0.5f;
+                jy = a[1] - 0.5f;
             }
             float a = jx * Q.dudx[q], b = jy * Q.dudy[q];
             x = x + a; x = x + b;
@@ -369,7 +414,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                         int ix = ax.i0 + ft + i;
                         double w = wl[li] * kernel64(filter, ax.pos - (double)ix) * wy;
                         if (w == 0.0) continue;
-                        Mat m = fetch(T, lvl, wrapi(ix, W, T.address), wrapi(iy, H, T.address));
+                        Mat m = fetch(T, lvl, wrapi(ix, W, T.address), wrapi(iy, H, T.address), &rd);
                         if (mode == M_NTAP_BEFORE) {
                             for (int c = 0; c < 3; ++c) fm.rho[c] += w * m.rho[c];
                             fm.rough += w * m.rough;
@@ -392,7 +437,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
             }
         } else {
             // stochastic MIP level: floor(lambda) + [xi < frac(lambda)] (stochastic lerp)
-            float xl = unif(r0[2]);
+            float xl = a[2];
             int lvl = l0 + ((xl < fr) ? 1 : 0);
             int lvl64 = l0_64 + (((double)xl < fr64) ? 1 : 0);
             if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs((double)xl - fr64));
@@ -416,12 +461,12 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
             };
             if (mode == M_STOCHASTIC) {
                 float Sx, Sy;
-                int kx = pick32(wx, nt, unif(r0[3]), 0, &Sx);
-                int ky = pick32(wy, nt, unif(r1[0]), 0, &Sy);
-                int kx64 = pick64(wx64, nt, unif(r0[3]), 0, &bd);
-                int ky64 = pick64(wy64, nt, unif(r1[0]), 0, &bd);
+                int kx = pick32(wx, nt, a[3], 0, &Sx);
+                int ky = pick32(wy, nt, a[4], 0, &Sy);
+                int kx64 = pick64(wx64, nt, a[3], 0, &bd);
+                int ky64 = pick64(wy64, nt, a[4], 0, &bd);
                 auto t = texel(lvl, kx, ky);
-                Mat m = fetch(T, lvl, t.first, t.second);
+                Mat m = fetch(T, lvl, t.first, t.second, &rd);
                 double o[3];
                 shade(smode, m, o);
                 double Wt = 1.0;
@@ -449,17 +494,17 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 }
                 double Wp64 = Px64 * Py64 + Nx64 * Ny64, Wn64 = Px64 * Ny64 + Nx64 * Py64;
                 // positive set: class (+,+) with probability Px Py / W+, else (-,-)
-                float xc = unif(r1[1]);
+                float xc = b[0];
                 int cx = (xc * Wp < Px * Py) ? +1 : -1;
                 int cx64 = ((double)xc < Px64 * Py64 / Wp64) ? +1 : -1;
                 if (Nx64 * Ny64 > 0) bd = std::min(bd, std::fabs((double)xc - Px64 * Py64 / Wp64));
-                int kx = pick32(wx, nt, unif(r0[3]), cx, nullptr);
-                int ky = pick32(wy, nt, unif(r1[0]), cx, nullptr);
-                int kx64 = pick64(wx64, nt, unif(r0[3]), cx64, &bd);
-                int ky64 = pick64(wy64, nt, unif(r1[0]), cx64, &bd);
+                int kx = pick32(wx, nt, a[3], cx, nullptr);
+                int ky = pick32(wy, nt, a[4], cx, nullptr);
+                int kx64 = pick64(wx64, nt, a[3], cx64, &bd);
+                int ky64 = pick64(wy64, nt, a[4], cx64, &bd);
                 auto tp = texel(lvl, kx, ky);
                 double o[3];
-                shade(smode, fetch(T, lvl, tp.first, tp.second), o);
+                shade(smode, fetch(T, lvl, tp.first, tp.second, &rd), o);
                 for (int c = 0; c < 3; ++c) { est[c] = Wp64 * o[c]; mag[c] += std::fabs(est[c]); }
                 if (pk) pk[0] = pack2d(lvl, tp.first, tp.second);
                 if (pk64) {
@@ -468,17 +513,17 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 }
                 // negative set: class (+,-) with probability Px Ny / W-, else (-,+)
                 if (Wn > 0.0f) {
-                    float xn = unif(r2[0]);
+                    float xn = b[3];
                     int nx_cls = (xn * Wn < Px * Ny) ? +1 : -1;
                     int nx64 = ((double)xn < Px64 * Ny64 / Wn64) ? +1 : -1;
                     if (Px64 * Ny64 > 0 && Nx64 * Py64 > 0)
                         bd = std::min(bd, std::fabs((double)xn - Px64 * Ny64 / Wn64));
-                    int qx = pick32(wx, nt, unif(r1[2]), nx_cls, nullptr);
-                    int qy = pick32(wy, nt, unif(r1[3]), -nx_cls, nullptr);
-                    int qx64 = pick64(wx64, nt, unif(r1[2]), nx64, &bd);
-                    int qy64 = pick64(wy64, nt, unif(r1[3]), -nx64, &bd);
+                    int qx = pick32(wx, nt, b[1], nx_cls, nullptr);
+                    int qy = pick32(wy, nt, b[2], -nx_cls, nullptr);
+                    int qx64 = pick64(wx64, nt, b[1], nx64, &bd);
+                    int qy64 = pick64(wy64, nt, b[2], -nx64, &bd);
                     auto tn = texel(lvl, qx, qy);
-                    shade(smode, fetch(T, lvl, tn.first, tn.second), o);
+                    shade(smode, fetch(T, lvl, tn.first, tn.second, &rd), o);
                     for (int c = 0; c < 3; ++c) { est[c] -= Wn64 * o[c]; mag[c] += std::fabs(Wn64 * o[c]); }
                     if (pk) pk[1] = pack2d(lvl, tn.first, tn.second);
                     if (pk64) {
@@ -492,6 +537,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
     }
     for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c] / (double)spp;
     if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c] / (double)spp;
+    if (O.rdist) O.rdist[q] = rd;
     if (O.bdist) O.bdist[q] = bd;
 }
 
@@ -566,16 +612,20 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
             return half_to_double(V.data[((size_t)iz * V.ny + iy) * V.nx + ix]);
         };
         if (mode == M_STOCHASTIC) {
+            // steps 2p and 2p+1 share stream p+1: six 21-bit uniforms, three per step
             uint32_t rr[4];
-            draw(seed, pix, s, k + 1, rr);
+            float u6[6];
+            draw(seed, pix, s, (k >> 1) + 1, rr);
+            uniforms6(rr, u6);
+            const float* uk = u6 + 3 * (k & 1);
             int kk[3];
             for (int a = 0; a < 3; ++a) {
                 float w[4];
                 double w64[4];
                 weights32(filter, ax[a].t, w);
                 for (int j = 0; j < nt; ++j) w64[j] = kernel64(filter, ax[a].pos - (double)(ax[a].i0 + ft + j));
-                kk[a] = pick32(w, nt, unif(rr[a]), 0, nullptr);
-                pick64(w64, nt, unif(rr[a]), 0, bd);
+                kk[a] = pick32(w, nt, uk[a], 0, nullptr);
+                pick64(w64, nt, uk[a], 0, bd);
             }
             int ix = ax[0].i0 + ft + kk[0], iy = ax[1].i0 + ft + kk[1], iz = ax[2].i0 + ft + kk[2];
             sum_sigma += sig * vox(ix, iy, iz);
@@ -684,7 +734,7 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
                      const float* dudx, const float* dvdx, const float* dudy, const float* dvdy,
                      const uint64_t* ids, int filter, int mode, int smode, uint32_t spp, uint64_t seed,
                      uint32_t flags, double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist,
-                     double* mag, int nthreads) {
+                     double* mag, double* rdist, int nthreads) {
     if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 3 || mode < 0 || mode > 3) return 1;
     if (tex->levels < 1 || tex->levels > 16) return 1;
     if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
@@ -694,7 +744,7 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
     }
     Tex T; std::memcpy(&T, tex, sizeof(Tex));
     Queries Q{n, u, v, dudx, dvdx, dudy, dvdy};
-    Out O{rgb, picks, picks64, bdist, mag};
+    Out O{rgb, picks, picks64, bdist, mag, rdist};
     parallel_for(n, nthreads, [&](uint64_t q) {
         run_query(T, Q, q, ids ? ids[q] : q, filter, mode, smode, spp, seed, flags, O);
     });

@@ -51,6 +51,20 @@ class _Output(C.Structure):
     _fields_ = [("r", C.c_void_p), ("g", C.c_void_p), ("b", C.c_void_p), ("picks", C.c_void_p)]
 
 
+class _NeuralDesc(C.Structure):
+    _fields_ = [("tex_res", C.c_uint32), ("grid_res", C.c_uint32 * 4), ("latent_init", C.POINTER(C.c_void_p)),
+                ("mlp_init", C.c_void_p), ("targets", C.c_void_p)]
+
+
+class _Adam(C.Structure):
+    _fields_ = [("lr_latent", C.c_float), ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
+NEURAL_BLOCKS = {"latents": 0, "mlp": 1, "grad_latents": 2, "grad_mlp": 3, "adam": 4, "scales": 5, "step": 6}
+LATENT_FORMATS = {"fp16": 0, "fp8": 1}
+MLP_SIZE = 6792
+
 # every entry point declared in include/stf.h, with its ctypes signature
 _P, _U32, _U64, _I, _F = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int, C.c_float
 SIGNATURES = {
@@ -70,6 +84,18 @@ SIGNATURES = {
     "stf_create_volume": ([_P, _U32, _U32, _U32, _I, _F, _P, _I, C.POINTER(_U64)], _I),
     "stf_destroy_volume": ([_P, _U64], _I),
     "stf_march_volume": ([_P, _U64, _P, _U32, _U32, _U32, _I, _I, _U32, _U64, _U32, _U64, _U64, _P, _P], _I),
+    "stf_neural_create": ([_P, C.POINTER(_NeuralDesc), C.POINTER(_U64)], _I),
+    "stf_neural_destroy": ([_P, _U64], _I),
+    "stf_neural_train": ([_P, _U64, _U32, _U32, C.POINTER(_Adam), _U64, _P], _I),
+    "stf_neural_grad": ([_P, _U64, _U32, _U32, _U64, _P, _P, C.POINTER(C.c_float)], _I),
+    "stf_neural_quantize": ([_P, _U64, _I], _I),
+    "stf_neural_get": ([_P, _U64, _I, _P, C.c_size_t], _I),
+    "stf_neural_set": ([_P, _U64, _I, _P, C.c_size_t], _I),
+    "stf_neural_save": ([_P, _U64, C.c_char_p], _I),
+    "stf_neural_load": ([_P, _U64, C.c_char_p], _I),
+    "stf_neural_decode": ([_P, _U64, _U64, _P, _P, _P], _I),
+    "stf_neural_filter_shade": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32, _U64, _U32,
+                                 C.POINTER(_Output)], _I),
 }
 
 _lib = None
@@ -232,3 +258,77 @@ class Context:
                                     C.c_void_p(_ptr(picks)) if picks is not None else None)
         self._check(st, self.h)
         return out, picks
+
+    # -------------------------------------------------------------- learned form
+    def neural_create(self, tex_res: int, latents, mlp, targets=None) -> int:
+        """latents: 4 host float32 arrays (R, R, 8); mlp: float32 [6792]; targets: uint8
+        (tex_res, tex_res, 8) or None."""
+        lat = [np.ascontiguousarray(x, dtype=np.float32) for x in latents]
+        mlp = np.ascontiguousarray(mlp, dtype=np.float32)
+        assert mlp.size == MLP_SIZE
+        tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.uint8)
+        arr = (C.c_void_p * 4)(*[x.ctypes.data for x in lat])
+        d = _NeuralDesc(tex_res, (C.c_uint32 * 4)(*[x.shape[0] for x in lat]), arr, mlp.ctypes.data,
+                        None if tg is None else tg.ctypes.data)
+        out = C.c_uint64(0)
+        self._check(lib().stf_neural_create(self.h, C.byref(d), C.byref(out)), self.h)
+        return int(out.value)
+
+    def neural_destroy(self, net: int):
+        self._check(lib().stf_neural_destroy(self.h, net), self.h)
+
+    def neural_train(self, net: int, steps: int, batch: int, lr_latent: float = 1e-2, lr_mlp: float = 5e-3,
+                     seed: int = 1, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> np.ndarray:
+        losses = np.zeros(steps, dtype=np.float32)
+        ap = _Adam(lr_latent, lr_mlp, beta1, beta2, eps)
+        self._check(lib().stf_neural_train(self.h, net, steps, batch, C.byref(ap), seed,
+                                           losses.ctypes.data if steps else None), self.h)
+        return losses
+
+    def neural_grad(self, net: int, step: int, batch: int, seed: int = 1, ix=None, iy=None) -> float:
+        loss = C.c_float(0)
+        self._check(lib().stf_neural_grad(self.h, net, step, batch, seed, _ptr(ix), _ptr(iy), C.byref(loss)),
+                    self.h)
+        return float(loss.value)
+
+    def neural_quantize(self, net: int, fmt: str = "fp16"):
+        self._check(lib().stf_neural_quantize(self.h, net, LATENT_FORMATS[fmt]), self.h)
+
+    def _neural_block_size(self, net: int, what: str, lat_total: int) -> int:
+        return {"latents": lat_total, "grad_latents": lat_total, "mlp": MLP_SIZE, "grad_mlp": MLP_SIZE,
+                "adam": 2 * lat_total + 2 * MLP_SIZE, "scales": 4, "step": 1}[what]
+
+    def neural_get(self, net: int, what: str, lat_total: int) -> np.ndarray:
+        n = self._neural_block_size(net, what, lat_total)
+        out = np.zeros(n, dtype=np.uint32 if what == "step" else np.float32)
+        self._check(lib().stf_neural_get(self.h, net, NEURAL_BLOCKS[what], out.ctypes.data, out.nbytes), self.h)
+        return out
+
+    def neural_set(self, net: int, what: str, data: np.ndarray):
+        data = np.ascontiguousarray(data, dtype=np.uint32 if what == "step" else np.float32)
+        self._check(lib().stf_neural_set(self.h, net, NEURAL_BLOCKS[what], data.ctypes.data, data.nbytes), self.h)
+
+    def neural_save(self, net: int, path: str):
+        self._check(lib().stf_neural_save(self.h, net, path.encode()), self.h)
+
+    def neural_load(self, net: int, path: str):
+        self._check(lib().stf_neural_load(self.h, net, path.encode()), self.h)
+
+    def neural_decode(self, net: int, ix, iy):
+        """ix, iy: int32 cuda tensors [n] -> float32 cuda tensor [n, 8]."""
+        n = int(ix.shape[0])
+        y = self.torch.empty((n, 8), dtype=self.torch.float32, device=ix.device)
+        self._check(lib().stf_neural_decode(self.h, net, n, _ptr(ix), _ptr(iy), _ptr(y)), self.h)
+        return y
+
+    def neural_filter_shade(self, net: int, u, v, derivs=None, filter: str = "bspline", mode: str = "stochastic",
+                            shade: str = "ggx", spp: int = 1, seed: int = 1, id_base: int = 0, out=None):
+        torch = self.torch
+        n = int(u.shape[0])
+        if out is None:
+            out = [torch.empty(n, dtype=torch.float32, device=u.device) for _ in range(3)]
+        q, d, o = self._args(u, v, derivs, out, None, n, id_base)
+        st = lib().stf_neural_filter_shade(self.h, net, C.byref(q), C.byref(d) if d is not None else None,
+                                           FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, 0, C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2]

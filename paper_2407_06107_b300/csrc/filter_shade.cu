@@ -53,9 +53,8 @@ __device__ __forceinline__ float lod_aniso(float dudx, float dvdx, float dudy, f
 
 template <int FILTER, int MODE>
 __global__ void __launch_bounds__(256)
-k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
+k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC, RoundKeys K) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
-    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const float inv_spp = 1.0f / (float)a.spp;
     const int kside = a.kside;
     for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n;
@@ -76,7 +75,8 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
         float3 acc = make_float3(0.f, 0.f, 0.f);
 
         for (uint32_t s = 0; s < a.spp; ++s) {
-            const uint4 r0 = philox(id_lo, id_hi, s, 0u, k0, k1);
+            // stream 0: (jitter x, jitter y, level, pick x, pick y)
+            const U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
             float x = u, y = v;
             if (a.has_derivs) {
                 float jx, jy;
@@ -84,16 +84,15 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
                     jx = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s % kside), 0.5f), (float)kside), 0.5f);
                     jy = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s / kside), 0.5f), (float)kside), 0.5f);
                 } else {
-                    jx = __fsub_rn(unif(r0.x), 0.5f);
-                    jy = __fsub_rn(unif(r0.y), 0.5f);
+                    jx = __fsub_rn(A.u[0], 0.5f);
+                    jy = __fsub_rn(A.u[1], 0.5f);
                 }
                 x = __fadd_rn(__fadd_rn(x, __fmul_rn(jx, dudx)), __fmul_rn(jy, dudy));
                 y = __fadd_rn(__fadd_rn(y, __fmul_rn(jx, dvdx)), __fmul_rn(jy, dvdy));
             }
             float3 est;
             if (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) {
-                const uint4 r1 = philox(id_lo, id_hi, s, 1u, k0, k1);
-                int lvl = l0 + ((unif(r0.z) < fr) ? 1 : 0);
+                int lvl = l0 + ((A.u[2] < fr) ? 1 : 0);
                 lvl = min(lvl, T.levels - 1);
                 const int W = T.w[lvl], H = T.h[lvl];
                 const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
@@ -102,14 +101,21 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
                 axis_weights<FILTER>(ay.t, wy);
                 if (MODE == M_STOCHASTIC) {
                     float Sx, Sy;
-                    const int kx = cdf_pick<NT>(wx, unif(r0.w), 0, &Sx);
-                    const int ky = cdf_pick<NT>(wy, unif(r1.x), 0, &Sy);
+                    const int kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
+                    const int ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
                     const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
                     const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
                     float Wt = 1.0f;
                     if (is_signed(FILTER)) {
+                        // sign of the picked weight, selected without dynamic register indexing
+                        bool nx = false, ny = false;
+#pragma unroll
+                        for (int k = 0; k < NT; ++k) {
+                            nx = (k == kx) ? (wx[k] < 0.0f) : nx;
+                            ny = (k == ky) ? (wy[k] < 0.0f) : ny;
+                        }
                         Wt = Sx * Sy;
-                        if ((wx[kx] < 0.0f) != (wy[ky] < 0.0f)) Wt = -Wt;
+                        if (nx != ny) Wt = -Wt;
                     }
                     est = make_float3(Wt * f.x, Wt * f.y, Wt * f.z);
                     if (a.picks) {
@@ -124,18 +130,19 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
                     cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
                     const float Wp = __fadd_rn(__fmul_rn(Px, Py), __fmul_rn(Nx, Ny));
                     const float Wn = __fadd_rn(__fmul_rn(Px, Ny), __fmul_rn(Nx, Py));
-                    const int cp = (__fmul_rn(unif(r1.y), Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
-                    const int kx = cdf_pick<NT>(wx, unif(r0.w), cp, nullptr);
-                    const int ky = cdf_pick<NT>(wy, unif(r1.x), cp, nullptr);
+                    // stream 1: (positive class, negative pick x, negative pick y, negative class)
+                    const U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                    const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
+                    const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
+                    const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
                     const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
                     const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
                     est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
                     uint32_t negpick = NO_PICK;
                     if (Wn > 0.0f) {
-                        const uint4 r2 = philox(id_lo, id_hi, s, 2u, k0, k1);
-                        const int cn = (__fmul_rn(unif(r2.x), Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
-                        const int qx = cdf_pick<NT>(wx, unif(r1.z), cn, nullptr);
-                        const int qy = cdf_pick<NT>(wy, unif(r1.w), -cn, nullptr);
+                        const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
+                        const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
+                        const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
                         const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
                         const float3 g = shade(a.shade, fetch(T, lvl, jx, jy), SC);
                         est.x = fmaf(-Wn, g.x, est.x);
@@ -222,7 +229,7 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC) {
 template <int FILTER, int MODE>
 static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                              int grid, cudaStream_t st) {
-    k_filter_shade<FILTER, MODE><<<grid, 256, 0, st>>>(a, T, SC);
+    k_filter_shade<FILTER, MODE><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
     return cudaGetLastError();
 }
 

@@ -21,9 +21,8 @@ __device__ __forceinline__ float vox(const MarchArgs& a, int x, int y, int z) {
 }
 
 template <int FILTER, int MODE>
-__global__ void __launch_bounds__(128) k_march(MarchArgs a) {
+__global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
-    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const float res[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.pix_count;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -38,7 +37,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a) {
                 jx = __fdiv_rn(__fadd_rn((float)(s % a.kside), 0.5f), (float)a.kside);
                 jy = __fdiv_rn(__fadd_rn((float)(s / a.kside), 0.5f), (float)a.kside);
             } else {
-                const uint4 r = philox(id_lo, id_hi, s, 0u, k0, k1);
+                const uint4 r = philox(id_lo, id_hi, s, 0u, K);
                 jx = unif(r.x); jy = unif(r.y);
             }
             float sx = __fsub_rn(__fmul_rn(__fadd_rn((float)px, jx), __fdiv_rn(2.0f, (float)a.width)), 1.0f);
@@ -75,6 +74,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a) {
             float Ssum = 0.0f, Scomp = 0.0f;        // before: compensated sum of filtered sigma/scale
             float P = 1.0f, Pe = 0.0f;              // after: compensated product
             const float sdt = a.sigma_scale * dt;
+            uint4 rw = make_uint4(0u, 0u, 0u, 0u);
             for (uint32_t k = 0; k < a.steps; ++k) {
                 const float tk = __fadd_rn(tmin, __fmul_rn(__fadd_rn((float)k, 0.5f), dt));
                 AxisPos ap[3];
@@ -84,10 +84,13 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) axis_weights<FILTER>(ap[c].t, w[c]);
                 if (MODE == M_STOCHASTIC) {
-                    const uint4 r = philox(id_lo, id_hi, s, k + 1u, k0, k1);
-                    const int kx = cdf_pick<NT>(w[0], unif(r.x), 0, nullptr);
-                    const int ky = cdf_pick<NT>(w[1], unif(r.y), 0, nullptr);
-                    const int kz = cdf_pick<NT>(w[2], unif(r.z), 0, nullptr);
+                    // steps 2p and 2p+1 share stream p+1 (six 21-bit uniforms)
+                    if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
+                    float uk[3];
+                    uniforms3_of6(rw, (int)(k & 1u), uk);
+                    const int kx = cdf_pick<NT>(w[0], uk[0], 0, nullptr);
+                    const int ky = cdf_pick<NT>(w[1], uk[1], 0, nullptr);
+                    const int kz = cdf_pick<NT>(w[2], uk[2], 0, nullptr);
                     const int ix = clamp_index(ap[0].i0 + T0 + kx, a.nx);
                     const int iy = clamp_index(ap[1].i0 + T0 + ky, a.ny);
                     const int iz = clamp_index(ap[2].i0 + T0 + kz, a.nz);
@@ -139,9 +142,9 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a) {
 template <int FILTER>
 static cudaError_t launch_f(const MarchArgs& a, int grid, cudaStream_t st) {
     switch (a.mode) {
-        case M_NTAP_BEFORE: k_march<FILTER, M_NTAP_BEFORE><<<grid, 128, 0, st>>>(a); break;
-        case M_NTAP_AFTER: k_march<FILTER, M_NTAP_AFTER><<<grid, 128, 0, st>>>(a); break;
-        case M_STOCHASTIC: k_march<FILTER, M_STOCHASTIC><<<grid, 128, 0, st>>>(a); break;
+        case M_NTAP_BEFORE: k_march<FILTER, M_NTAP_BEFORE><<<grid, 128, 0, st>>>(a, expand_key(a.seed)); break;
+        case M_NTAP_AFTER: k_march<FILTER, M_NTAP_AFTER><<<grid, 128, 0, st>>>(a, expand_key(a.seed)); break;
+        case M_STOCHASTIC: k_march<FILTER, M_STOCHASTIC><<<grid, 128, 0, st>>>(a, expand_key(a.seed)); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

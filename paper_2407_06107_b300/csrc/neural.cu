@@ -1,0 +1,700 @@
+// Learned form: neural texture (4 FP16 / FP8 latent grids + MLP 32->64->64->8) trained by
+// hand-written forward/backward/Adam kernels and decoded on the 5th-generation tensor
+// cores (tcgen05.mma kind::f16, BF16 operands in shared memory, FP32 accumulators in
+// TMEM).  Stochastic filtering decodes the MLP once per lookup instead of once per filter
+// tap (Sec. 4: one texel per lookup inside the filter integral).
+//
+// Decode tile: 128 rows (one row = one texel decode).  Per tile:
+//   rows -> latent features (bilinear, FP32, fixed order) -> BF16 A tile (smem)
+//   MMA1 128x64x32 -> TMEM -> +b1, ReLU, BF16 -> A tile
+//   MMA2 128x64x64 -> TMEM -> +b2, ReLU, BF16 -> A tile
+//   MMA3 128x16x64 (8 outputs padded to N=16) -> TMEM -> +b3 -> shade / store.
+// Shared-memory operands use the no-swizzle K-major canonical layout: 8-row x 16-byte core
+// matrices; core matrices adjacent along K are 128 B apart (LBO), 8-row groups are
+// (K/8)*128 B apart (SBO).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "stf_device.cuh"
+#include "stf_kernels.h"
+
+namespace stf {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on an mbarrier phase: gives up after ~max_cycles SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_cycles) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > max_cycles) return false;
+    return true;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {   // whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {   // whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor, no swizzle, K-major
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+    return d;                 // base offset 0, relative LBO, layout SWIZZLE_NONE
+}
+// instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of element (row, k) in a K-major no-swizzle tile with K columns
+__host__ __device__ constexpr uint32_t kmaj_off(uint32_t row, uint32_t k, uint32_t K) {
+    return (row >> 3) * (K / 8) * 128u + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+}
+
+// ------------------------------------------------------------------ latent features
+// bilinear taps of grid g at the centre of texel (ix, iy): FP32 in the oracle's order
+struct LTap { int x0, y0, x1, y1; float w00, w10, w01, w11; };
+__device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, int iy) {
+    const float s = __fdiv_rn((float)N.res[g], (float)N.tex_res);
+    const float px = __fsub_rn(__fmul_rn(__fadd_rn((float)ix, 0.5f), s), 0.5f);
+    const float py = __fsub_rn(__fmul_rn(__fadd_rn((float)iy, 0.5f), s), 0.5f);
+    const float fx = floorf(px), fy = floorf(py);
+    const float tx = __fsub_rn(px, fx), ty = __fsub_rn(py, fy);
+    const float ux = __fsub_rn(1.0f, tx), uy = __fsub_rn(1.0f, ty);
+    LTap t;
+    t.x0 = wrap_index((int)fx, N.res[g]); t.y0 = wrap_index((int)fy, N.res[g]);
+    t.x1 = wrap_index((int)fx + 1, N.res[g]); t.y1 = wrap_index((int)fy + 1, N.res[g]);
+    t.w00 = __fmul_rn(ux, uy); t.w10 = __fmul_rn(tx, uy); t.w01 = __fmul_rn(ux, ty); t.w11 = __fmul_rn(tx, ty);
+    return t;
+}
+
+// 8 latent channels of one grid texel as floats (FP16, FP8 x scale, or FP32 master)
+__device__ __forceinline__ void load_latent8(const NeuralView& N, int fmt, int g, int x, int y, float v[8]) {
+    const size_t o = ((size_t)y * N.res[g] + x) * 8;
+    if (fmt == 0) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(N.lat16 + N.lat_off[g] + o));
+        const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { const float2 f = __half22float2(h[i]); v[2 * i] = f.x; v[2 * i + 1] = f.y; }
+    } else if (fmt == 1) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(N.lat8 + N.lat_off[g] + o));
+        const uint8_t* b = reinterpret_cast<const uint8_t*>(&q);
+        const float sc = N.scale[g];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            __nv_fp8_e4m3 e;
+            e.__x = b[i];
+            v[i] = __fmul_rn((float)e, sc);
+        }
+    } else {
+        const float4* p = reinterpret_cast<const float4*>(N.lat32 + N.lat_off[g] + o);
+        const float4 a = p[0], b = p[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+}
+
+__device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, int iy, float f[32]) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const LTap t = latent_taps(N, g, ix, iy);
+        float a[8], b[8], c[8], d[8];
+        load_latent8(N, fmt, g, t.x0, t.y0, a);
+        load_latent8(N, fmt, g, t.x1, t.y0, b);
+        load_latent8(N, fmt, g, t.x0, t.y1, c);
+        load_latent8(N, fmt, g, t.x1, t.y1, d);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v = __fmul_rn(t.w00, a[k]);
+            v = __fadd_rn(v, __fmul_rn(t.w10, b[k]));
+            v = __fadd_rn(v, __fmul_rn(t.w01, c[k]));
+            v = __fadd_rn(v, __fmul_rn(t.w11, d[k]));
+            f[8 * g + k] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// decoded channels -> material (albedo, roughness, tangent-space normal)
+__device__ __forceinline__ Material material_from_channels(const float y[8]) {
+    Material m;
+    m.rho = make_float3(__saturatef(y[0]), __saturatef(y[1]), __saturatef(y[2]));
+    m.rough = fmaf(0.95f, __saturatef(y[3]), 0.05f);
+    const float x = fmaf(2.0f, __saturatef(y[4]), -1.0f), yy = fmaf(2.0f, __saturatef(y[5]), -1.0f);
+    const float z2 = fmaxf(0.0f, 1.0f - x * x - yy * yy);
+    const float z = z2 > 0.0f ? z2 * rsqrtf(z2) : 0.0f;
+    const float l2 = x * x + yy * yy + z * z;
+    if (l2 > 0.0f) {
+        const float inv = rsqrtf(l2);
+        m.n = make_float3(x * inv, yy * inv, z * inv);
+    } else {
+        m.n = make_float3(0.f, 0.f, 1.f);
+    }
+    return m;
+}
+
+// ------------------------------------------------------------------ training (SIMT FP32)
+// One block = 128 samples.  Forward with BF16-rounded operands (as the tensor-core decode
+// computes), MSE loss, analytic backward; block partial gradients are atomically added.
+constexpr int TB = 128;
+
+struct TrainSmem {
+    float W1[64 * 32], W2[64 * 64], W3[8 * 64], b1[64], b2[64], b3[8];
+    float X[TB][33], H1[TB][65], H2[TB][65], DY[TB][9];
+    float red[TB / 32];
+};
+
+__global__ void __launch_bounds__(TB) k_ntc_train(NeuralView N, uint32_t step, uint32_t batch, RoundKeys K,
+                                                  float* loss_sum, uint32_t use_explicit, const int32_t* ex_ix,
+                                                  const int32_t* ex_iy) {
+    extern __shared__ __align__(16) uint8_t train_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_raw);
+    float (&W1)[64 * 32] = S.W1; float (&W2)[64 * 64] = S.W2; float (&W3)[8 * 64] = S.W3;
+    float (&b1)[64] = S.b1; float (&b2)[64] = S.b2; float (&b3)[8] = S.b3;
+    float (&X)[TB][33] = S.X; float (&H1)[TB][65] = S.H1; float (&H2)[TB][65] = S.H2; float (&DY)[TB][9] = S.DY;
+    float (&red)[TB / 32] = S.red;
+    const int t = threadIdx.x;
+    const float* P = N.mlp32;
+    for (int i = t; i < 64 * 32; i += TB) W1[i] = bf16r(P[i]);
+    for (int i = t; i < 64; i += TB) { b1[i] = P[2048 + i]; b2[i] = P[2048 + 64 + 4096 + i]; }
+    for (int i = t; i < 64 * 64; i += TB) W2[i] = bf16r(P[2048 + 64 + i]);
+    for (int i = t; i < 8 * 64; i += TB) W3[i] = bf16r(P[2048 + 64 + 4096 + 64 + i]);
+    if (t < 8) b3[t] = P[2048 + 64 + 4096 + 64 + 512 + t];
+    __syncthreads();
+
+    const uint32_t k = blockIdx.x * TB + t;
+    const bool live = k < batch;
+    int ix = 0, iy = 0;
+    if (live) {
+        if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
+        else {
+            const uint4 w = philox(k, step, 0u, 0x4E54u, K);
+            ix = (int)__umulhi(w.x, (uint32_t)N.tex_res);
+            iy = (int)__umulhi(w.y, (uint32_t)N.tex_res);
+        }
+    }
+    float loss = 0.0f;
+    {   // forward
+        float f[32];
+        features(N, 2, ix, iy, f);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) X[t][i] = bf16r(f[i]);
+        for (int o = 0; o < 64; ++o) {
+            float z = b1[o];
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) z = fmaf(W1[o * 32 + i], X[t][i], z);
+            H1[t][o] = z > 0.0f ? bf16r(z) : 0.0f;
+        }
+        for (int o = 0; o < 64; ++o) {
+            float z = b2[o];
+#pragma unroll 8
+            for (int i = 0; i < 64; ++i) z = fmaf(W2[o * 64 + i], H1[t][i], z);
+            H2[t][o] = z > 0.0f ? bf16r(z) : 0.0f;
+        }
+        const uint8_t* tg = N.targets + ((size_t)iy * N.tex_res + ix) * 8;
+        const float inv = 1.0f / (8.0f * (float)batch);
+        for (int o = 0; o < 8; ++o) {
+            float z = b3[o];
+#pragma unroll 8
+            for (int i = 0; i < 64; ++i) z = fmaf(W3[o * 64 + i], H2[t][i], z);
+            const float e = live ? z - (float)tg[o] * (1.0f / 255.0f) : 0.0f;
+            loss = fmaf(e * e, inv, loss);
+            DY[t][o] = 2.0f * e * inv;
+        }
+    }
+    // block loss
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
+    if ((t & 31) == 0) red[t >> 5] = loss;
+    __syncthreads();
+    if (t == 0) atomicAdd(loss_sum, red[0] + red[1] + red[2] + red[3]);
+
+    float* G = N.grad32;
+    // dW3, db3 (512 + 8 outputs)
+    for (int j = t; j < 8 * 64 + 8; j += TB) {
+        float a = 0.0f;
+        if (j < 512) { const int o = j >> 6, i = j & 63; for (int s = 0; s < TB; ++s) a = fmaf(DY[s][o], H2[s][i], a); }
+        else { const int o = j - 512; for (int s = 0; s < TB; ++s) a += DY[s][o]; }
+        atomicAdd(&G[j < 512 ? 2048 + 64 + 4096 + 64 + j : 2048 + 64 + 4096 + 64 + 512 + (j - 512)], a);
+    }
+    __syncthreads();
+    // dh2 = W3^T dy (.) [h2 > 0]   (overwrites H2)
+    for (int i = 0; i < 64; ++i) {
+        float a = 0.0f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) a = fmaf(W3[o * 64 + i], DY[t][o], a);
+        H2[t][i] = H2[t][i] > 0.0f ? a : 0.0f;
+    }
+    __syncthreads();
+    // dW2, db2
+    for (int j = t; j < 64 * 64 + 64; j += TB) {
+        float a = 0.0f;
+        if (j < 4096) { const int o = j >> 6, i = j & 63; for (int s = 0; s < TB; ++s) a = fmaf(H2[s][o], H1[s][i], a); }
+        else { const int o = j - 4096; for (int s = 0; s < TB; ++s) a += H2[s][o]; }
+        atomicAdd(&G[j < 4096 ? 2048 + 64 + j : 2048 + 64 + 4096 + (j - 4096)], a);
+    }
+    __syncthreads();
+    // dh1 = W2^T dh2 (.) [h1 > 0]   (overwrites H1)
+    float dh1[64];
+    for (int i = 0; i < 64; ++i) {
+        float a = 0.0f;
+#pragma unroll 8
+        for (int o = 0; o < 64; ++o) a = fmaf(W2[o * 64 + i], H2[t][o], a);
+        dh1[i] = H1[t][i] > 0.0f ? a : 0.0f;
+    }
+    __syncthreads();
+    for (int i = 0; i < 64; ++i) H1[t][i] = dh1[i];
+    __syncthreads();
+    // dW1, db1
+    for (int j = t; j < 64 * 32 + 64; j += TB) {
+        float a = 0.0f;
+        if (j < 2048) { const int o = j >> 5, i = j & 31; for (int s = 0; s < TB; ++s) a = fmaf(H1[s][o], X[s][i], a); }
+        else { const int o = j - 2048; for (int s = 0; s < TB; ++s) a += H1[s][o]; }
+        atomicAdd(&G[j < 2048 ? j : 2048 + (j - 2048)], a);
+    }
+    // dx = W1^T dh1 -> latent gradient scatter with the bilinear weights
+    if (live) {
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+            const LTap tp = latent_taps(N, g, ix, iy);
+            float dx[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float a = 0.0f;
+                for (int o = 0; o < 64; ++o) a = fmaf(W1[o * 32 + 8 * g + c], dh1[o], a);
+                dx[c] = a;
+            }
+            float* dl = N.dlat + N.lat_off[g];
+            const int R = N.res[g];
+            const int xs[4] = {tp.x0, tp.x1, tp.x0, tp.x1}, ys[4] = {tp.y0, tp.y0, tp.y1, tp.y1};
+            const float ws[4] = {tp.w00, tp.w10, tp.w01, tp.w11};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float* p = dl + ((size_t)ys[q] * R + xs[q]) * 8;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) atomicAdd(p + c, ws[q] * dx[c]);
+            }
+        }
+    }
+}
+
+// Adam with bias correction; consumes and zeroes the gradient
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+        m[i] = mi; v[i] = vi; g[i] = 0.0f;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ------------------------------------------------------------------ quantisation
+__global__ void k_to_fp16(const float* __restrict__ src, __half* __restrict__ dst, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+// per-grid max |latent| (non-negative floats order like their bit patterns)
+__global__ void k_absmax(const float* __restrict__ src, uint64_t n, unsigned int* out) {
+    float m = 0.0f;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(src[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+// FP8 E4M3 (round to nearest even, saturating to +-448) of latent / scale
+__global__ void k_to_e4m3(const float* __restrict__ src, uint8_t* __restrict__ dst, uint64_t n, const unsigned int* amax) {
+    const float scale = fmaxf(__uint_as_float(*amax), 1e-30f) / 448.0f;
+    const float inv = 1.0f / scale;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = (uint8_t)__nv_cvt_float_to_fp8(src[i] * inv, __NV_SATFINITE, __NV_E4M3);
+}
+__global__ void k_scale_from_amax(const unsigned int* amax, float* scale, int n) {
+    if (threadIdx.x < n) scale[threadIdx.x] = fmaxf(__uint_as_float(amax[threadIdx.x]), 1e-30f) / 448.0f;
+}
+// MLP master -> BF16 weights [W1 64x32 | W2 64x64 | W3 padded 16x64] and FP32 biases [b1|b2|b3 pad 16]
+__global__ void k_pack_mlp(const float* __restrict__ P, __nv_bfloat16* __restrict__ wb, float* __restrict__ bias) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2048 + 4096 + 1024; i += gridDim.x * blockDim.x) {
+        float w;
+        if (i < 2048) w = P[i];
+        else if (i < 6144) w = P[2048 + 64 + (i - 2048)];
+        else { const int j = i - 6144; w = j < 512 ? P[2048 + 64 + 4096 + 64 + j] : 0.0f; }
+        wb[i] = __float2bfloat16_rn(w);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 64 + 64 + 16; i += gridDim.x * blockDim.x) {
+        float b;
+        if (i < 64) b = P[2048 + i];
+        else if (i < 128) b = P[2048 + 64 + 4096 + (i - 64)];
+        else { const int j = i - 128; b = j < 8 ? P[2048 + 64 + 4096 + 64 + 512 + j] : 0.0f; }
+        bias[i] = b;
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core decode
+constexpr int NT_ROWS = 128;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+struct __align__(128) DecodeSmem {
+    uint8_t A1[NT_ROWS * 32 * 2];     // 8 KB: features, K = 32
+    uint8_t A2[NT_ROWS * 64 * 2];     // 16 KB: hidden activations, K = 64
+    uint8_t W1[64 * 32 * 2];          // 4 KB
+    uint8_t W2[64 * 64 * 2];          // 8 KB
+    uint8_t W3[16 * 64 * 2];          // 2 KB (rows 8..15 zero)
+    float bias[64 + 64 + 16];
+    float ch[NT_ROWS][9];             // decoded channels per row
+    float wt[NT_ROWS];                // row weight
+    long long pair[NT_ROWS];          // (query, sample) pair of the row, -1 = idle
+    uint64_t bar;
+    uint32_t tmem;
+    int abort_flag;
+};
+
+// copy a row-major [N][K] BF16 matrix into the K-major no-swizzle core-matrix layout
+__device__ __forceinline__ void stage_weights(uint8_t* dst, const __nv_bfloat16* src, int Nr, int K) {
+    const int chunks = Nr * K / 8;          // 16-byte chunks
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        const int row = c / (K / 8), kc = c % (K / 8);
+        const uint4 v = *reinterpret_cast<const uint4*>(src + (size_t)row * K + kc * 8);
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, kc * 8, K)) = v;
+    }
+}
+
+// Row generation for the filter modes: row -> (pair, texel, weight).
+struct RowOut { long long pair; int ix, iy; float w; };
+
+template <int FILTER, int MODE>
+__device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const RoundKeys& K, uint64_t row) {
+    constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
+    constexpr int NR = (MODE == M_STOCHASTIC) ? 1 : (MODE == M_POSITIVIZED ? 2 : NT * NT);
+    RowOut o{-1, 0, 0, 0.0f};
+    const uint64_t pair = row / NR;
+    const int j = (int)(row % NR);
+    if (pair >= a.n * (uint64_t)a.spp) return o;
+    const uint64_t q = pair / a.spp;
+    const uint32_t s = (uint32_t)(pair % a.spp);
+    const uint64_t id = a.id_base + q;
+    const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+    const U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+    float x = a.u[q], y = a.v[q];
+    if (a.has_derivs) {
+        const float jx = __fsub_rn(A.u[0], 0.5f), jy = __fsub_rn(A.u[1], 0.5f);
+        x = __fadd_rn(__fadd_rn(x, __fmul_rn(jx, a.dudx[q])), __fmul_rn(jy, a.dudy[q]));
+        y = __fadd_rn(__fadd_rn(y, __fmul_rn(jx, a.dvdx[q])), __fmul_rn(jy, a.dvdy[q]));
+    }
+    const int R = a.tex_res;
+    const AxisPos ax = axis_pos(x, (float)R), ay = axis_pos(y, (float)R);
+    float wx[4], wy[4];
+    axis_weights<FILTER>(ax.t, wx);
+    axis_weights<FILTER>(ay.t, wy);
+    o.pair = (long long)pair;
+    if (MODE == M_STOCHASTIC) {
+        float Sx, Sy;
+        const int kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
+        const int ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
+        float W = 1.0f;
+        if (is_signed(FILTER)) {
+            bool nx = false, ny = false;
+#pragma unroll
+            for (int k = 0; k < NT; ++k) { nx = (k == kx) ? (wx[k] < 0.0f) : nx; ny = (k == ky) ? (wy[k] < 0.0f) : ny; }
+            W = (nx != ny) ? -Sx * Sy : Sx * Sy;
+        }
+        o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R); o.w = W;
+    } else if (MODE == M_POSITIVIZED) {
+        float Px, Nx, Py, Ny;
+        cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
+        cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
+        const float Wp = __fadd_rn(__fmul_rn(Px, Py), __fmul_rn(Nx, Ny));
+        const float Wn = __fadd_rn(__fmul_rn(Px, Ny), __fmul_rn(Nx, Py));
+        const U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+        if (j == 0) {
+            const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
+            const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr), ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
+            o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R); o.w = Wp;
+        } else if (Wn > 0.0f) {
+            const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
+            const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr), qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
+            o.ix = wrap_index(ax.i0 + T0 + qx, R); o.iy = wrap_index(ay.i0 + T0 + qy, R); o.w = -Wn;
+        } else {
+            o.ix = 0; o.iy = 0; o.w = 0.0f;
+        }
+    } else {
+        const int kx = j % NT, ky = j / NT;
+        float wsx = wx[0], wsy = wy[0];
+#pragma unroll
+        for (int k = 1; k < NT; ++k) { wsx = (k == kx) ? wx[k] : wsx; wsy = (k == ky) ? wy[k] : wsy; }
+        o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R); o.w = wsx * wsy;
+    }
+    return o;
+}
+
+template <int FILTER, int MODE>
+__global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralDecodeArgs a, RoundKeys K, ShadeConst SC) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    DecodeSmem& S = *reinterpret_cast<DecodeSmem*>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+
+    stage_weights(S.W1, N.wbf, 64, 32);
+    stage_weights(S.W2, N.wbf + 2048, 64, 64);
+    stage_weights(S.W3, N.wbf + 6144, 16, 64);
+    for (int i = t; i < 144; i += NT_ROWS) S.bias[i] = N.bias[i];
+    if (t == 0) { mbar_init(&S.bar, 1); S.abort_flag = 0; }
+    if (warp == 0) tmem_alloc(&S.tmem, TMEM_COLS);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t a1 = smem_u32(S.A1), a2 = smem_u32(S.A2);
+    const uint32_t w1 = smem_u32(S.W1), w2 = smem_u32(S.W2), w3 = smem_u32(S.W3);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    const uint64_t nrows = a.nrows;
+    const uint64_t ntiles = (nrows + NT_ROWS - 1) / NT_ROWS;
+    for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        // ---- rows -> features -> A1
+        const uint64_t row = tile * NT_ROWS + t;
+        int ix = 0, iy = 0;
+        long long pr = -1;
+        float w = 0.0f;
+        if (row < nrows) {
+            if constexpr (MODE < 0) {
+                ix = a.ex_ix[row]; iy = a.ex_iy[row]; pr = (long long)row; w = 1.0f;
+            } else {
+                const RowOut r = make_row<FILTER, MODE>(a, K, row);
+                ix = r.ix; iy = r.iy; pr = r.pair; w = r.w;
+            }
+        }
+        S.pair[t] = pr;
+        S.wt[t] = w;
+        float f[32];
+        features(N, N.latent_fmt, ix, iy, f);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            __nv_bfloat162 p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(f[8 * c + 2 * i], f[8 * c + 2 * i + 1]);
+            *reinterpret_cast<uint4*>(S.A1 + kmaj_off(t, 8 * c, 32)) = *reinterpret_cast<uint4*>(p);
+        }
+        // ---- three GEMM layers
+#pragma unroll 1
+        for (int layer = 0; layer < 3; ++layer) {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (t == 0) {
+                tc_fence_after();
+                if (layer == 0) {
+                    for (int s = 0; s < 2; ++s)
+                        mma_bf16(tmem, smem_desc(a1 + 256 * s, 128, 512), smem_desc(w1 + 256 * s, 128, 512),
+                                 idesc_bf16(128, 64), s > 0);
+                } else if (layer == 1) {
+                    for (int s = 0; s < 4; ++s)
+                        mma_bf16(tmem + 64, smem_desc(a2 + 256 * s, 128, 1024), smem_desc(w2 + 256 * s, 128, 1024),
+                                 idesc_bf16(128, 64), s > 0);
+                } else {
+                    for (int s = 0; s < 4; ++s)
+                        mma_bf16(tmem, smem_desc(a2 + 256 * s, 128, 1024), smem_desc(w3 + 256 * s, 128, 1024),
+                                 idesc_bf16(128, 16), s > 0);
+                }
+                mma_commit(&S.bar);
+            }
+            if (!mbar_wait_bounded(&S.bar, phase, WAIT_CYCLES)) atomicOr(&S.abort_flag, 1);
+            phase ^= 1u;
+            tc_fence_after();
+            __syncthreads();
+            if (S.abort_flag) { ok = false; break; }
+            if (layer < 2) {
+                uint32_t r[4][16];
+                const uint32_t col = layer == 0 ? 0u : 64u;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) tmem_ld16(tmem + lane_base + col + 16 * c, r[c]);
+                tmem_wait_ld();
+                const float* bias = S.bias + (layer == 0 ? 0 : 64);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    __nv_bfloat162 p[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k0 = 8 * c + 2 * i;
+                        const float z0 = __uint_as_float(r[k0 >> 4][k0 & 15]) + bias[k0];
+                        const float z1 = __uint_as_float(r[(k0 + 1) >> 4][(k0 + 1) & 15]) + bias[k0 + 1];
+                        p[i] = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+                    }
+                    *reinterpret_cast<uint4*>(S.A2 + kmaj_off(t, 8 * c, 64)) = *reinterpret_cast<uint4*>(p);
+                }
+            } else {
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) S.ch[t][i] = __uint_as_float(r[i]) + S.bias[128 + i];
+            }
+        }
+        if (!ok) break;
+        __syncthreads();
+        // ---- epilogue
+        if constexpr (MODE < 0) {
+            if (row < nrows) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a.y_out[row * 8 + i] = S.ch[t][i];
+            }
+        } else {
+            // one thread per (query, sample) pair (its rows are contiguous within the tile,
+            // because the rows per pair, 1, 2, 4 or 16, divide 128)
+            const long long p = S.pair[t];
+            const bool head = p >= 0 && (t == 0 || S.pair[t - 1] != p);
+            if (head) {
+                float est[3] = {0.f, 0.f, 0.f};
+                if constexpr (MODE == M_NTAP_BEFORE) {
+                    float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    for (int r = t; r < NT_ROWS && S.pair[r] == p; ++r)
+                        for (int i = 0; i < 8; ++i) c[i] = fmaf(S.wt[r], S.ch[r][i], c[i]);
+                    const float3 f3 = shade(a.shade, material_from_channels(c), SC);
+                    est[0] = f3.x; est[1] = f3.y; est[2] = f3.z;
+                } else {
+                    for (int r = t; r < NT_ROWS && S.pair[r] == p; ++r) {
+                        if (S.wt[r] == 0.0f) continue;
+                        const float3 f3 = shade(a.shade, material_from_channels(S.ch[r]), SC);
+                        est[0] = fmaf(S.wt[r], f3.x, est[0]);
+                        est[1] = fmaf(S.wt[r], f3.y, est[1]);
+                        est[2] = fmaf(S.wt[r], f3.z, est[2]);
+                    }
+                }
+                const uint64_t q = (uint64_t)p / a.spp;
+                const float inv = 1.0f / (float)a.spp;
+                atomicAdd(a.r + q, est[0] * inv);
+                atomicAdd(a.g + q, est[1] * inv);
+                atomicAdd(a.b + q, est[2] * inv);
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok && t == 0) atomicOr(a.status, DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint64_t seed, float* loss_sum,
+                             const int32_t* ex_ix, const int32_t* ex_iy, cudaStream_t st) {
+    const int grid = (int)((batch + TB - 1) / TB);
+    cudaFuncSetAttribute(k_ntc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
+    k_ntc_train<<<grid, TB, sizeof(TrainSmem), st>>>(N, step, batch, expand_key(seed), loss_sum, ex_ix != nullptr,
+                                                     ex_ix, ex_iy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
+                        int t, cudaStream_t st) {
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    const uint64_t blocks = (n + 255) / 256;
+    k_adam<<<(int)(blocks < 4096 ? (blocks ? blocks : 1) : 4096), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ntc_quantize(const NeuralView& N, uint64_t lat_total, int fmt, unsigned int* amax_scratch,
+                                cudaStream_t st) {
+    k_pack_mlp<<<8, 256, 0, st>>>(N.mlp32, N.wbf, N.bias);
+    if (fmt == 0) {
+        k_to_fp16<<<1024, 256, 0, st>>>(N.lat32, const_cast<__half*>(N.lat16), lat_total);
+    } else {
+        cudaMemsetAsync(amax_scratch, 0, 4 * sizeof(unsigned int), st);
+        for (int g = 0; g < 4; ++g) {
+            const uint64_t n = (uint64_t)N.res[g] * N.res[g] * 8;
+            k_absmax<<<256, 256, 0, st>>>(N.lat32 + N.lat_off[g], n, amax_scratch + g);
+            k_to_e4m3<<<512, 256, 0, st>>>(N.lat32 + N.lat_off[g], const_cast<uint8_t*>(N.lat8) + N.lat_off[g], n,
+                                           amax_scratch + g);
+        }
+        k_scale_from_amax<<<1, 32, 0, st>>>(amax_scratch, N.scale_dev, 4);
+    }
+    return cudaGetLastError();
+}
+
+size_t ntc_decode_smem_bytes() { return sizeof(DecodeSmem) + 1024; }
+
+template <int FILTER, int MODE>
+static cudaError_t launch_dec(const NeuralView& N, const NeuralDecodeArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = sizeof(DecodeSmem);
+    cudaFuncSetAttribute(k_ntc_decode_tc<FILTER, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ntc_decode_tc<FILTER, MODE><<<grid, NT_ROWS, smem, st>>>(N, a, expand_key(a.seed), make_shade_const());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ntc_decode(const NeuralView& N, const NeuralDecodeArgs& a, int num_sms, cudaStream_t st) {
+    const uint64_t tiles = (a.nrows + NT_ROWS - 1) / NT_ROWS;
+    const uint64_t cap = (uint64_t)num_sms * 4;
+    const int grid = (int)(tiles < cap ? (tiles ? tiles : 1) : cap);
+    if (a.mode < 0) return launch_dec<F_LINEAR, -1>(N, a, grid, st);
+#define STF_DEC_MODES(F)                                                             \
+    if (a.filter == F) {                                                             \
+        switch (a.mode) {                                                            \
+            case M_NTAP_BEFORE: return launch_dec<F, M_NTAP_BEFORE>(N, a, grid, st); \
+            case M_NTAP_AFTER: return launch_dec<F, M_NTAP_AFTER>(N, a, grid, st);   \
+            case M_STOCHASTIC: return launch_dec<F, M_STOCHASTIC>(N, a, grid, st);   \
+            default: break;                                                          \
+        }                                                                            \
+    }
+    STF_DEC_MODES(F_LINEAR)
+    STF_DEC_MODES(F_BSPLINE)
+    STF_DEC_MODES(F_CATMULL_ROM)
+    STF_DEC_MODES(F_MITCHELL)
+#undef STF_DEC_MODES
+    if (a.mode == M_POSITIVIZED) {
+        if (a.filter == F_MITCHELL) return launch_dec<F_MITCHELL, M_POSITIVIZED>(N, a, grid, st);
+        if (a.filter == F_CATMULL_ROM) return launch_dec<F_CATMULL_ROM, M_POSITIVIZED>(N, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stf

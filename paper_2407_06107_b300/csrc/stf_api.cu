@@ -9,37 +9,11 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/stf.h"
-#include "stf_kernels.h"
+#include "stf_ctx.h"
 
-struct TexRec {
-    void* mem = nullptr;
-    stf::TexView view{};
-};
-struct VolRec {
-    void* mem = nullptr;
-    uint32_t nx = 0, ny = 0, nz = 0;
-    float sigma_scale = 1.0f;
-};
+using stfi::CurrentDevice;
 
-struct stf_ctx_s {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int num_sms = 148;
-    uint32_t* d_status = nullptr;
-    std::string last_error;
-    uint64_t next_handle = 1;
-    std::unordered_map<uint64_t, TexRec> tex;
-    std::unordered_map<uint64_t, VolRec> vol;
-    void* stage = nullptr;          // device staging for the host-buffer entry points
-    size_t stage_bytes = 0;
-    int fault = 0;                  // host-side fault injection (STF_FAULT), 0 = off
-};
-
-namespace {
-
-enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2 };
-
+namespace stfi {
 stf_status fail(stf_ctx c, stf_status s, const char* msg) {
     if (c) c->last_error = msg;
     return s;
@@ -54,6 +28,13 @@ stf_status dev_alloc(stf_ctx c, void** p, size_t bytes) {
     if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(c, e, "cudaMalloc"); }
     return STF_OK;
 }
+}  // namespace stfi
+
+namespace {
+using stfi::fail;
+using stfi::cuda_fail;
+using stfi::dev_alloc;
+
 bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 bool bad_enum_filter(int f) { return f < 0 || f > 3; }
 bool bad_enum_mode(int m) { return m < 0 || m > 3; }
@@ -64,11 +45,6 @@ int square_side(uint32_t spp) {
 }
 uint32_t level_dim(uint32_t d, uint32_t l) { uint32_t x = d >> l; return x ? x : 1u; }
 
-struct CurrentDevice {
-    int prev = -1;
-    explicit CurrentDevice(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
-    ~CurrentDevice() { int now = -1; cudaGetDevice(&now); if (prev >= 0 && now != prev) cudaSetDevice(prev); }
-};
 
 stf_status ensure_stage(stf_ctx c, size_t bytes) {
     if (c->stage_bytes >= bytes) return STF_OK;
@@ -110,6 +86,12 @@ stf_status validate_filter_call(stf_ctx c, stf_tex t, const stf_queries* q, cons
 }
 
 }  // namespace
+
+using stfi::fail;
+using stfi::cuda_fail;
+using stfi::dev_alloc;
+using stfi::FAULT_ALLOC;
+using stfi::FAULT_LAUNCH;
 
 extern "C" {
 
@@ -158,6 +140,7 @@ stf_status stf_destroy(stf_ctx c) {
     cudaStreamSynchronize(c->stream);
     for (auto& kv : c->tex) cudaFree(kv.second.mem);
     for (auto& kv : c->vol) cudaFree(kv.second.mem);
+    for (auto& kv : c->neural) { cudaFree(kv.second.mem); if (kv.second.loss) cudaFree(kv.second.loss); }
     if (c->stage) cudaFree(c->stage);
     if (c->d_status) cudaFree(c->d_status);
     delete c;

@@ -1,0 +1,57 @@
+// Internal: the context object and helpers shared by the C-ABI translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+
+#include "../../include/stf.h"
+#include "stf_kernels.h"
+
+struct TexRec {
+    void* mem = nullptr;
+    stf::TexView view{};
+};
+struct VolRec {
+    void* mem = nullptr;
+    uint32_t nx = 0, ny = 0, nz = 0;
+    float sigma_scale = 1.0f;
+};
+struct NeuralRec {
+    void* mem = nullptr;           // one allocation for every array below
+    stf::NeuralView view{};
+    uint64_t lat_total = 0;        // latent elements over all grids
+    float *m_lat = nullptr, *v_lat = nullptr, *m_mlp = nullptr, *v_mlp = nullptr;
+    unsigned int* amax = nullptr;  // FP8 scale reduction
+    float* loss = nullptr;         // per-step losses (grown on demand)
+    uint32_t loss_cap = 0;
+    uint32_t step = 0;             // optimiser steps taken
+    int latent_fmt = 0;
+    bool trainable = false;
+};
+
+struct stf_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 148;
+    uint32_t* d_status = nullptr;
+    std::string last_error;
+    uint64_t next_handle = 1;
+    std::unordered_map<uint64_t, TexRec> tex;
+    std::unordered_map<uint64_t, VolRec> vol;
+    std::unordered_map<uint64_t, NeuralRec> neural;
+    void* stage = nullptr;          // device staging for the host-buffer entry points
+    size_t stage_bytes = 0;
+    int fault = 0;                  // host-side fault injection (STF_FAULT), 0 = off
+};
+
+namespace stfi {
+enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2 };
+stf_status fail(stf_ctx c, stf_status s, const char* msg);
+stf_status cuda_fail(stf_ctx c, cudaError_t e, const char* where);
+stf_status dev_alloc(stf_ctx c, void** p, size_t bytes);
+struct CurrentDevice {
+    int prev = -1;
+    explicit CurrentDevice(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~CurrentDevice() { int now = -1; cudaGetDevice(&now); if (prev >= 0 && now != prev) cudaSetDevice(prev); }
+};
+}  // namespace stfi

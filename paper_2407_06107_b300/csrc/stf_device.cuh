@@ -15,7 +15,7 @@ enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 
 enum { SH_GGX = 0, SH_LINEAR = 1 };
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
 enum { FLAG_STRATIFIED = 1u };
-enum { DEV_NAN_INPUT = 1u, DEV_BAD_INDEX = 2u };
+enum { DEV_NAN_INPUT = 1u, DEV_BAD_INDEX = 2u, DEV_TIMEOUT = 4u };
 constexpr uint32_t NO_PICK = 0xFFFFFFFFu;
 
 __host__ __device__ constexpr int ntaps(int f) { return f == F_LINEAR ? 2 : 4; }
@@ -24,20 +24,55 @@ __host__ __device__ constexpr bool is_signed(int f) { return f == F_CATMULL_ROM 
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC 2011).  ctr = (id_lo, id_hi, sample, stream), key = seed.
+// The ten round keys depend on the seed only: the host expands them once per launch
+// (RoundKeys, passed as a kernel parameter), so a round is two wide multiplies and two
+// three-input XORs.
+struct RoundKeys { uint32_t k[20]; };
+
+inline RoundKeys expand_key(uint64_t seed) {
+    RoundKeys r;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) { r.k[2 * i] = k0; r.k[2 * i + 1] = k1; k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    return r;
+}
+
 __device__ __forceinline__ uint4 philox(uint32_t id_lo, uint32_t id_hi, uint32_t sample,
-                                        uint32_t stream, uint32_t k0, uint32_t k1) {
+                                        uint32_t stream, const RoundKeys& K) {
     uint32_t x0 = id_lo, x1 = id_hi, x2 = sample, x3 = stream;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
-        x0 = hi1 ^ x1 ^ k0; x1 = lo1; x2 = hi0 ^ x3 ^ k1; x3 = lo0;
-        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0, p1 = (uint64_t)0xCD9E8D57u * x2;
+        x0 = (uint32_t)(p1 >> 32) ^ x1 ^ K.k[2 * r];
+        x1 = (uint32_t)p1;
+        x2 = (uint32_t)(p0 >> 32) ^ x3 ^ K.k[2 * r + 1];
+        x3 = (uint32_t)p0;
     }
     return make_uint4(x0, x1, x2, x3);
 }
 // top 24 bits scaled by 2^-24: exact in FP32
 __device__ __forceinline__ float unif(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-8f; }
+
+// five 24-bit uniforms per Philox output: four high parts, plus the low bytes of words 0-2
+struct U5 { float u[5]; };
+__device__ __forceinline__ U5 uniforms5(uint4 w) {
+    U5 r;
+    r.u[0] = unif(w.x); r.u[1] = unif(w.y); r.u[2] = unif(w.z); r.u[3] = unif(w.w);
+    const uint32_t f = ((w.x & 0xFFu) << 16) | ((w.y & 0xFFu) << 8) | (w.z & 0xFFu);
+    r.u[4] = __uint2float_rn(f) * 5.9604644775390625e-8f;
+    return r;
+}
+// six 21-bit uniforms per Philox output: three for each of two volume march steps
+__device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
+    const float k = 4.76837158203125e-7f;
+    if (!odd) {
+        u[0] = __uint2float_rn(w.x >> 11) * k; u[1] = __uint2float_rn(w.y >> 11) * k;
+        u[2] = __uint2float_rn(w.z >> 11) * k;
+    } else {
+        u[0] = __uint2float_rn(w.w >> 11) * k;
+        u[1] = __uint2float_rn((w.x & 0x7FFu) | ((w.y & 0x3FFu) << 11)) * k;
+        u[2] = __uint2float_rn((w.z & 0x7FFu) | ((w.w & 0x3FFu) << 11)) * k;
+    }
+}
 
 // ---------------------------------------------------------------- FP32 decision weights
 // Per-axis weights for the taps at distances 1+t, t, 1-t, 2-t (cubic) or 1-t, t
@@ -130,6 +165,7 @@ __device__ __forceinline__ AxisPos axis_pos(float x, float res) {
 }
 
 __device__ __forceinline__ int wrap_index(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;          // common case: no wrap
     int r = i % n;
     return r < 0 ? r + n : r;
 }
@@ -158,12 +194,14 @@ __device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst&
     const float3 nxh = cross3(m.n, C.h), nxl = cross3(m.n, C.l), nxv = cross3(m.n, C.v);
     const float nh = dot3(m.n, C.h);
     const float q = fmaf(a2 * nh, nh, dot3(nxh, nxh));
-    const float D = a2 / (3.14159265358979f * q * q);
+    const float D = __fdividef(a2 * 0.318309886183790672f, q * q);
     // Lambda = (sqrt(1 + a2 tan^2) - 1)/2 written without cancellation: x / (2 (sqrt(1+x)+1))
-    const float xl = a2 * dot3(nxl, nxl) / (nl * nl), xv = a2 * dot3(nxv, nxv) / (nv * nv);
-    const float Ll = 0.5f * xl / (sqrtf(1.0f + xl) + 1.0f), Lv = 0.5f * xv / (sqrtf(1.0f + xv) + 1.0f);
-    const float G = 1.0f / (1.0f + Ll + Lv);
-    const float spec = D * G * C.F / (4.0f * nv);
+    const float xl = __fdividef(a2 * dot3(nxl, nxl), nl * nl), xv = __fdividef(a2 * dot3(nxv, nxv), nv * nv);
+    const float sl = 1.0f + xl, sv = 1.0f + xv;
+    const float Ll = __fdividef(0.5f * xl, fmaf(sl, rsqrtf(sl), 1.0f));
+    const float Lv = __fdividef(0.5f * xv, fmaf(sv, rsqrtf(sv), 1.0f));
+    const float G = __frcp_rn(1.0f + Ll + Lv);
+    const float spec = __fdividef(D * G * C.F, 4.0f * nv);
     const float kd = nl * 0.318309886183790672f;
     return make_float3(fmaf(m.rho.x, kd, spec), fmaf(m.rho.y, kd, spec), fmaf(m.rho.z, kd, spec));
 }
@@ -179,15 +217,16 @@ __device__ __forceinline__ float3 shade(int sh, const Material& m, const ShadeCo
 __device__ __forceinline__ float3 decode_normal_rg8(uint32_t xy) {
     const float X = (float)(int)(2u * (xy & 0xFFu)) - 255.0f;
     const float Y = (float)(int)(2u * ((xy >> 8) & 0xFFu)) - 255.0f;
-    const float Z = sqrtf(fmaxf(0.0f, 65025.0f - X * X - Y * Y));   // exact integer radicand
-    const float inv = 1.0f / sqrtf(X * X + Y * Y + Z * Z);
+    const float R = fmaxf(0.0f, 65025.0f - X * X - Y * Y);          // exact integer radicand
+    const float Z = R > 0.0f ? R * rsqrtf(R) : 0.0f;
+    const float inv = rsqrtf(X * X + Y * Y + Z * Z);
     return make_float3(X * inv, Y * inv, Z * inv);
 }
 __device__ __forceinline__ Material decode_rgba8(uint2 t, bool has_normal) {
     Material m;
     const float k = 1.0f / 255.0f;
-    m.rho = make_float3((float)(t.x & 0xFFu) / 255.0f, (float)((t.x >> 8) & 0xFFu) / 255.0f,
-                        (float)((t.x >> 16) & 0xFFu) / 255.0f);
+    m.rho = make_float3((float)(t.x & 0xFFu) * k, (float)((t.x >> 8) & 0xFFu) * k,
+                        (float)((t.x >> 16) & 0xFFu) * k);
     m.rough = fmaf(0.95f, (float)(t.x >> 24) * k, 0.05f);
     m.n = has_normal ? decode_normal_rg8(t.y) : make_float3(0.f, 0.f, 1.f);
     return m;

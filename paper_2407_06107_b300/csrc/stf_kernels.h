@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 namespace stf {
 
@@ -42,6 +43,51 @@ struct MarchArgs {
     uint32_t* picks;
     uint32_t* status;
 };
+
+// learned texture: device view
+struct NeuralView {
+    int tex_res;
+    int res[4];
+    uint64_t lat_off[4];        // element offset of each grid (same in every latent format)
+    int latent_fmt;             // inference latents: 0 FP16, 1 FP8 E4M3 x scale
+    const __half* lat16;
+    const uint8_t* lat8;
+    float* lat32;               // FP32 master latents (training)
+    float* dlat;                // latent gradients
+    float scale[4];             // FP8 per-grid scales (host copy)
+    float* scale_dev;
+    float* mlp32;               // FP32 master MLP: W1[64x32] b1[64] W2[64x64] b2[64] W3[8x64] b3[8]
+    float* grad32;              // gradients, same layout
+    __nv_bfloat16* wbf;         // inference weights: W1 | W2 | W3 padded to 16 rows
+    float* bias;                // inference biases: b1 | b2 | b3 padded to 16
+    const uint8_t* targets;     // explicit 8-channel texture [tex_res][tex_res][8]
+};
+
+struct NeuralDecodeArgs {
+    uint64_t n, id_base;
+    const float *u, *v, *dudx, *dvdx, *dudy, *dvdy;
+    int has_derivs;
+    int filter, mode, shade;    // mode < 0: decode the explicit texel list ex_ix/ex_iy
+    uint32_t spp;
+    uint64_t seed;
+    int tex_res;
+    uint64_t nrows;             // rows (texel decodes) of the launch
+    const int32_t *ex_ix, *ex_iy;
+    float* y_out;               // decode-only: [n][8]
+    float *r, *g, *b;           // filter modes: accumulated, must be zero on entry
+    uint32_t* status;
+};
+
+cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint64_t seed, float* loss_sum,
+                             const int32_t* ex_ix, const int32_t* ex_iy, cudaStream_t st);
+cudaError_t launch_adam(float* p, float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
+                        int t, cudaStream_t st);
+cudaError_t launch_ntc_quantize(const NeuralView& N, uint64_t lat_total, int fmt, unsigned int* amax_scratch,
+                                cudaStream_t st);
+cudaError_t launch_ntc_decode(const NeuralView& N, const NeuralDecodeArgs& a, int num_sms, cudaStream_t st);
+
+struct ShadeConst;
+ShadeConst make_shade_const();
 
 cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int num_sms, cudaStream_t st);
 cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);

@@ -265,3 +265,37 @@ def camera_pinhole(width: int, height: int, eye=(0.5, 0.5, -1.2), look=(0.5, 0.5
     asp = width / height
     f32 = lambda a: tuple(float(np.float32(x)) for x in a)
     return Camera(f32(e), f32(f), f32(r * th * asp), f32(uu * th))
+
+
+# ---------------------------------------------------------------------------------
+# learned form: 8-channel targets and initial parameters
+# ---------------------------------------------------------------------------------
+NTC_MLP_SIZE = 64 * 32 + 64 + 64 * 64 + 64 + 8 * 64 + 8     # 6792
+
+
+def ntc_targets(material: Material, seed: int = 104) -> np.ndarray:
+    """(H, W, 8) uint8 channels of level 0: albedo RGB, roughness, normal XY, metalness
+    (a binary fBm threshold -- a 'discrete quantity'), height."""
+    ar, nm, h = material.albedo_rough[0], material.normal[0], material.height
+    size = ar.shape[0]
+    metal = fbm2d(size, 6, 4, seed) > 0.62
+    out = np.empty((size, size, 8), dtype=np.uint8)
+    out[..., 0:4] = ar
+    out[..., 4:6] = nm
+    out[..., 6] = np.where(metal, 255, 0).astype(np.uint8)
+    hmin, hmax = float(h.min()), float(h.max())
+    out[..., 7] = _rne_u8(255 * (h - hmin) / max(hmax - hmin, 1e-12))
+    return out
+
+
+def ntc_init(grid_res=(1024, 512, 256, 128), seed: int = 104):
+    """Latents U(-0.1, 0.1) per grid (res, res, 8) float32; MLP He-uniform weights
+    (bound sqrt(6 / fan_in)) and zero biases, packed W1 b1 W2 b2 W3 b3 (row-major [out][in])."""
+    rng = np.random.default_rng(seed)
+    lat = [rng.uniform(-0.1, 0.1, (r, r, 8)).astype(np.float32) for r in grid_res]
+    parts = []
+    for fan_in, fan_out in ((32, 64), (64, 64), (64, 8)):
+        b = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-b, b, (fan_out, fan_in)).astype(np.float32).ravel())
+        parts.append(np.zeros(fan_out, dtype=np.float32))
+    return lat, np.concatenate(parts)

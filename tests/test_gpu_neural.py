@@ -1,0 +1,166 @@
+"""Parity of the learned form (tensor-core decode, training kernels) with the FP64 oracle.
+
+Inputs are seeded initial parameters from stf_synth; the oracle builds its own inference
+form (BF16 weights, FP16 or FP8 latents) from them.  Tolerances derived from the
+arithmetic:
+  * decoded channels: both sides round the same FP32 features to BF16; the GPU then
+    accumulates K <= 64 BF16 products in FP32 (relative error <= 64 * 2^-24 ~ 4e-6 of
+    sum|w h|), so |dy| <= 1e-4 (1 + |y|) bounds it with margin.  Decodes whose hidden
+    activations lie within 2e-5 (relative) of a BF16 rounding boundary may round to the
+    neighbouring BF16 value on the GPU (a counted boundary case, like a CDF boundary).
+  * shaded values: the GGX condition number with respect to the normal is <= 2/alpha
+    = 40 at alpha >= 0.05, giving |df| <= 5e-4 sum|terms| + 1e-6.
+  * gradients: FP32 atomics vs FP64 sums; relative L2 <= 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import stf_synth as synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+R0 = 64
+GRIDS = (32, 16, 8, 4)
+LAT_TOTAL = sum(r * r * 8 for r in GRIDS)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_06107_b300 as stf
+    c = stf.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def data():
+    lat, mlp = synth.ntc_init(GRIDS, 21)
+    mlp[2048:2112] = 0.02          # small positive first-layer biases: fewer dead units at init
+    m = synth.material_rgba8(R0, 31, octaves=4, base=2, mips=False)
+    return lat, mlp, synth.ntc_targets(m, 33)
+
+
+@pytest.fixture
+def net(ctx, data):
+    lat, mlp, tg = data
+    h = ctx.neural_create(R0, lat, mlp, tg)
+    yield h
+    ctx.neural_destroy(h)
+
+
+def _all_texels():
+    ix, iy = np.meshgrid(np.arange(R0, dtype=np.int32), np.arange(R0, dtype=np.int32))
+    return ix.ravel(), iy.ravel()
+
+
+def _check_decode(ctx, h, nt):
+    ix, iy = _all_texels()
+    y = ctx.neural_decode(h, torch.from_numpy(ix).cuda(), torch.from_numpy(iy).cuda()).cpu().numpy()
+    ref, rd = oracle.ntc_decode(nt, ix, iy)
+    near = rd < 2e-5
+    err = np.abs(y - ref)
+    assert near.mean() < 0.05, near.mean()
+    tol = 1e-4 * (1 + np.abs(ref))
+    bad = (err > tol).any(1) & ~near
+    assert not bad.any(), f"{bad.sum()} decodes off by up to {err[bad].max():.3g}"
+    assert np.all(err[near] <= 3e-2 * (1 + np.abs(ref[near])))
+    return y
+
+
+def test_decode_fp16_matches_oracle(ctx, net, data):
+    lat, mlp, _ = data
+    _check_decode(ctx, net, oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp16"))
+
+
+def test_decode_fp8_matches_oracle(ctx, net, data):
+    lat, mlp, _ = data
+    ctx.neural_quantize(net, "fp8")
+    nt = oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp8")
+    np.testing.assert_array_equal(ctx.neural_get(net, "scales", LAT_TOTAL), np.array(nt.scales, np.float32))
+    y8 = _check_decode(ctx, net, nt)
+    # FP8 vs FP16 latents: the error the 8-bit form adds, stated against the FP64 decode
+    y16, _ = oracle.ntc_decode(oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp16"), *_all_texels())
+    assert np.sqrt(np.mean((y8 - y16) ** 2)) < 0.05
+
+
+def test_gradients_match_oracle(ctx, net, data):
+    lat, mlp, tg = data
+    step, batch, seed = 3, 512, 7
+    ix, iy = oracle.ntc_sample_texels(step, batch, seed, R0)
+    loss = ctx.neural_grad(net, step, batch, seed)
+    gm = ctx.neural_get(net, "grad_mlp", LAT_TOTAL).astype(np.float64)
+    gl = ctx.neural_get(net, "grad_latents", LAT_TOTAL).astype(np.float64)
+    rl, rgm, rgl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True)
+    assert abs(loss - rl) <= 1e-5 * rl
+    for got, ref in ((gm, rgm), (gl, rgl)):
+        assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+    # explicit texel list gives the same gradients as the Philox-drawn one
+    loss2 = ctx.neural_grad(net, 0, batch, seed, torch.from_numpy(ix).cuda(), torch.from_numpy(iy).cuda())
+    assert abs(loss2 - loss) <= 1e-6 * loss
+    gm2 = ctx.neural_get(net, "grad_mlp", LAT_TOTAL).astype(np.float64)
+    assert np.linalg.norm(gm2 - gm) <= 1e-5 * np.linalg.norm(gm)
+
+
+def test_adam_step_matches_oracle(ctx, net, data):
+    lat, mlp, tg = data
+    lr_l, lr_m, seed, batch = 1e-2, 5e-3, 5, 1024
+    ctx.neural_train(net, 1, batch, lr_l, lr_m, seed)
+    ix, iy = oracle.ntc_sample_texels(0, batch, seed, R0)
+    _, gm, gl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True)
+    for p0, g, lr, what in ((mlp, gm, lr_m, "mlp"), (np.concatenate([x.ravel() for x in lat]), gl, lr_l, "latents")):
+        p = p0.astype(np.float64).copy()
+        oracle.adam(p, g, np.zeros_like(p), np.zeros_like(p), 1, lr)
+        got = ctx.neural_get(net, what, LAT_TOTAL).astype(np.float64)
+        sig = np.abs(g) > 1e-3 * np.abs(g).max()          # where the gradient sign is well defined
+        np.testing.assert_allclose(got[sig], p[sig], rtol=0, atol=1e-6 + 1e-3 * lr)
+        assert int(ctx.neural_get(net, "step", LAT_TOTAL)[0]) == 1
+
+
+def test_training_reduces_loss(ctx, net):
+    losses = ctx.neural_train(net, 150, 4096, 1e-2, 5e-3, seed=11)
+    assert np.all(np.isfinite(losses))
+    assert losses[-10:].mean() < 0.5 * losses[:3].mean(), (losses[:3], losses[-10:])
+
+
+CASES = [("bspline", "stochastic"), ("bspline", "ntap_before"), ("linear", "ntap_after"),
+         ("mitchell", "positivized"), ("mitchell", "stochastic")]
+
+
+@pytest.mark.parametrize("filter,mode", CASES)
+def test_filter_shade_matches_oracle(ctx, net, data, filter, mode):
+    lat, mlp, _ = data
+    q = synth.queries_uniform(1500, 17, const_derivs=(0.3 / R0, 0.0, 0.0, 0.3 / R0))
+    t = lambda a: torch.from_numpy(a).cuda()
+    r, g, b = ctx.neural_filter_shade(net, t(q.u), t(q.v), [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)],
+                                      filter, mode, "ggx", spp=3, seed=9)
+    got = torch.stack([r, g, b], 1).cpu().numpy().astype(np.float64)
+    nt = oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp16")
+    ref = oracle.filter_shade(oracle.Texture(None, neural=nt), q, filter, mode, "ggx", 3, 9, want_picks=False)
+    near = ref.rdist < 2e-5
+    assert near.mean() < 0.2
+    err = np.abs(got - ref.rgb)[~near]
+    tol = (5e-4 * ref.mag + 1e-6)[~near]
+    assert np.all(err <= tol), float((err / tol).max())
+
+
+def test_checkpoint_roundtrip(ctx, net, data, tmp_path):
+    lat, mlp, tg = data
+    ctx.neural_train(net, 3, 1024, seed=2)
+    path = str(tmp_path / "net.stfn")
+    ctx.neural_save(net, path)
+    lat2, mlp2 = synth.ntc_init(GRIDS, 99)
+    other = ctx.neural_create(R0, lat2, mlp2, tg)
+    ctx.neural_load(other, path)
+    for what in ("latents", "mlp", "adam", "step"):
+        np.testing.assert_array_equal(ctx.neural_get(other, what, LAT_TOTAL), ctx.neural_get(net, what, LAT_TOTAL))
+    a = ctx.neural_train(net, 4, 1024, seed=2)
+    b = ctx.neural_train(other, 4, 1024, seed=2)
+    np.testing.assert_allclose(a, b, rtol=1e-4)          # same samples; FP32 atomics order only
+    ctx.neural_destroy(other)
