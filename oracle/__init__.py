@@ -221,7 +221,7 @@ class FilterResult:
     picks64: np.ndarray | None  # same, FP64 decisions (NO_PICK-1 where the level differs)
     bdist: np.ndarray | None   # (n,) distance of the nearest uniform to an FP64 boundary
     mag: np.ndarray | None = None  # (n, 3) mean over samples of sum |w f_hat| over the summed terms
-    rdist: np.ndarray | None = None  # (n,) learned texels: min relative distance to a BF16 rounding boundary
+    rdist: np.ndarray | None = None  # (n,) learned texels: smallest BF16 rounding margin (see ntc_decode)
 
 
 def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", spp: int = 1,
@@ -374,7 +374,9 @@ def ntc_features(nt: NeuralTexture, ix, iy) -> np.ndarray:
 
 
 def ntc_decode(nt: NeuralTexture, ix, iy):
-    """(y [n, 8] float64, rdist [n]): decode and min relative distance to a BF16 boundary."""
+    """(y [n, 8] float64, rdist [n]): decode, and the smallest rounding margin of its hidden
+    BF16 activations (distance to the rounding midpoint / (sqrt(K) sum|w x|)); a margin
+    below ~4 * 2^-24 can round differently under another FP32 summation order."""
     ix = np.ascontiguousarray(ix, dtype=np.int32)
     iy = np.ascontiguousarray(iy, dtype=np.int32)
     y = np.zeros((len(ix), 8))

@@ -97,29 +97,32 @@ void features32(const NeuralTex& N, int ix, int iy, float f[32]) {
     }
 }
 
-// distance of v to the nearest BF16 rounding midpoint, relative to |v|
-static double bf16_boundary_rel(double v) {
-    if (v == 0.0) return 1.0;
+// Margin of the BF16 rounding of a pre-activation v = b + sum_i w_i x_i: the distance of
+// v to the nearest BF16 rounding midpoint divided by S = |b| + sum_i |w_i x_i|.  An FP32
+// accumulation of the same (exact) products in another order differs from v by about
+// sqrt(K) 2^-24 S, so a margin below a few times that may round the other way.
+static double bf16_margin(double v, double S) {
+    if (v == 0.0 || S == 0.0) return 1.0;
     int e;
     std::frexp(std::fabs(v), &e);
     double quantum = std::ldexp(1.0, (e - 1) - 7);
     double q = std::fabs(v) / quantum;
     double frac = q - std::floor(q);
-    return std::fabs(frac - 0.5) * quantum / std::fabs(v);
+    return std::fabs(frac - 0.5) * quantum / S;
 }
 
 void mlp_forward(const Mlp& M, const double x[32], double h1[64], double h2[64], double y[8],
                  double* rdist, bool round_hidden) {
     for (int o = 0; o < 64; ++o) {
-        double z = M.b1[o];
-        for (int i = 0; i < 32; ++i) z += M.W1[o * 32 + i] * x[i];
-        if (rdist && z > 0) *rdist = std::min(*rdist, bf16_boundary_rel(z));
+        double z = M.b1[o], S = std::fabs(M.b1[o]);
+        for (int i = 0; i < 32; ++i) { z += M.W1[o * 32 + i] * x[i]; S += std::fabs(M.W1[o * 32 + i] * x[i]); }
+        if (rdist && z > 0) *rdist = std::min(*rdist, bf16_margin(z, S) / std::sqrt(33.0));
         h1[o] = z > 0 ? (round_hidden ? to_bf16(z) : z) : 0.0;
     }
     for (int o = 0; o < 64; ++o) {
-        double z = M.b2[o];
-        for (int i = 0; i < 64; ++i) z += M.W2[o * 64 + i] * h1[i];
-        if (rdist && z > 0) *rdist = std::min(*rdist, bf16_boundary_rel(z));
+        double z = M.b2[o], S = std::fabs(M.b2[o]);
+        for (int i = 0; i < 64; ++i) { z += M.W2[o * 64 + i] * h1[i]; S += std::fabs(M.W2[o * 64 + i] * h1[i]); }
+        if (rdist && z > 0) *rdist = std::min(*rdist, bf16_margin(z, S) / std::sqrt(65.0));
         h2[o] = z > 0 ? (round_hidden ? to_bf16(z) : z) : 0.0;
     }
     for (int o = 0; o < 8; ++o) {
@@ -133,10 +136,7 @@ void neural_decode(const NeuralTex& N, int ix, int iy, double y[8], double* rdis
     float f[32];
     features32(N, ix, iy, f);
     double x[32], h1[64], h2[64];
-    for (int i = 0; i < 32; ++i) {
-        if (rdist) *rdist = std::min(*rdist, bf16_boundary_rel(f[i]));
-        x[i] = to_bf16(f[i]);
-    }
+    for (int i = 0; i < 32; ++i) x[i] = to_bf16(f[i]);   // same FP32 features on both sides
     mlp_forward(*N.mlp, x, h1, h2, y, rdist, true);
 }
 
@@ -154,7 +154,8 @@ void orc_ntc_features(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, co
     for (uint64_t i = 0; i < n; ++i) orc::features32(*N, ix[i], iy[i], out + 32 * i);
 }
 
-// decode n texels: y[n*8] (FP64), rdist[n] (nullable)
+// decode n texels: y[n*8] (FP64), rdist[n] (nullable): the smallest BF16 rounding margin of
+// the hidden activations in units of sqrt(K) 2^-24 sum|w x| ... scaled as a plain number
 void orc_ntc_decode(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, const int32_t* iy,
                     double* y, double* rdist) {
     for (uint64_t i = 0; i < n; ++i) {
