@@ -154,6 +154,25 @@ stf_status stf_filter_shade_host(stf_ctx ctx, stf_tex tex, const stf_queries* q,
                                  stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                                  uint64_t seed, uint32_t flags, const stf_output* out);
 
+/* Same computation as stf_filter_shade_host, for callers that must not allocate device
+ * memory while they look up textures (a frame loop with a fixed memory budget, or a
+ * plug-in inside an application that owns all device allocations).  The paper has no
+ * counterpart: this is a deployment variant.  Queries, results and the device status word
+ * are staged in one fixed device array of the library (a little over 9 MiB, held by every
+ * GPU that loads the library until the process exits) instead of context-owned buffers
+ * grown with cudaMalloc, so the call allocates nothing.
+ *   - At most 262144 queries per call (STF_ERR_INVALID_ARG beyond); picks must be NULL
+ *     (STF_ERR_UNSUPPORTED otherwise).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other streams, other
+ *     host threads, other contexts on the same device) race and corrupt each other.
+ *   - Synchronises the context stream; returns STF_ERR_DEVICE_STATUS if the kernel
+ *     flagged its inputs (the results are still written). */
+stf_status stf_filter_shade_host_noalloc(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
+                                         stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
+                                         uint64_t seed, uint32_t flags, const stf_output* out);
+
 /* ---- 3-D volume march (Sec. 5 "Offline rendering", transmittance exp(-sigma dt)) ------- */
 /* data: nz*ny*nx FP16 densities (x fastest); sigma = sigma_scale * density. */
 stf_status stf_create_volume(stf_ctx ctx, uint32_t nx, uint32_t ny, uint32_t nz, stf_format format,

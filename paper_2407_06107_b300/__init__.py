@@ -81,6 +81,8 @@ SIGNATURES = {
                           _U32, C.POINTER(_Output)], _I),
     "stf_filter_shade_host": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                _U64, _U32, C.POINTER(_Output)], _I),
+    "stf_filter_shade_host_noalloc": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
+                                       _U64, _U32, C.POINTER(_Output)], _I),
     "stf_create_volume": ([_P, _U32, _U32, _U32, _I, _F, _P, _I, C.POINTER(_U64)], _I),
     "stf_destroy_volume": ([_P, _U64], _I),
     "stf_march_volume": ([_P, _U64, _P, _U32, _U32, _U32, _I, _I, _U32, _U64, _U32, _U64, _U64, _P, _P], _I),
@@ -241,6 +243,21 @@ class Context:
                                          FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
         self._check(st, self.h)
         return out[0], out[1], out[2], picks
+
+    def filter_shade_host_noalloc(self, tex: int, u, v, derivs=None, filter: str = "bspline",
+                                  mode: str = "stochastic", shade: str = "ggx", spp: int = 1, seed: int = 1,
+                                  flags: int = 0, id_base: int = 0, out=None):
+        """stf_filter_shade_host without any device allocation (at most 2^18 queries per
+        call; the library's fixed staging array is shared by all calls on a device)."""
+        n = int(u.shape[0])
+        if out is None:
+            out = [np.empty(n, dtype=np.float32) for _ in range(3)]
+        q, d, o = self._args(u, v, derivs, out, None, n, id_base)
+        st = lib().stf_filter_shade_host_noalloc(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
+                                                 FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags,
+                                                 C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2]
 
     def march_volume(self, vol: int, cam, width: int, height: int, steps: int = 128,
                      filter: str = "bspline", mode: str = "stochastic", spp: int = 1, seed: int = 1,
