@@ -154,8 +154,8 @@ void orc_ntc_features(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, co
     for (uint64_t i = 0; i < n; ++i) orc::features32(*N, ix[i], iy[i], out + 32 * i);
 }
 
-// decode n texels: y[n*8] (FP64), rdist[n] (nullable): the smallest BF16 rounding margin of
-// the hidden activations in units of sqrt(K) 2^-24 sum|w x| ... scaled as a plain number
+// decode n texels: y[n*8] (FP64); rdist[n] (nullable): the smallest BF16 rounding margin of
+// the hidden activations, |v - midpoint| / (sqrt(K) sum|w x|)
 void orc_ntc_decode(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, const int32_t* iy,
                     double* y, double* rdist) {
     for (uint64_t i = 0; i < n; ++i) {
