@@ -37,6 +37,8 @@ LOD_RANGE = 8.0
 SPP = 8
 FILTERS = ("linear", "bspline", "mitchell")
 METRIC = "shaded texture lookups/s, stochastic 1-tap vs N-tap, at equal RMSE vs FP64"
+LATTICE = 2                       # STF_FLAG_LATTICE
+SPP_GRID = (1, 2, 4, 6, 8, 9, 10, 11, 12, 14, 16, 20, 24, 32, 48, 64)
 
 
 def env_rank():
@@ -229,6 +231,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras:
         line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
         line["volume"] = volume_block(ctx, dev, args)
+        line["table"] = table_block(ctx, dev)
+        line["neural"] = neural_block(ctx, dev, material)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(material)
     if rank == 0:
@@ -276,20 +280,24 @@ def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
         ctx.filter_shade(tex, sub(u), sub(v), ds, filt, "ntap_after", "ggx", 256, 1, 1, out=ref)
         R = torch.stack(ref, 1).double()
 
-        def rmse(mode, spp, seed=7):
+        def rmse(mode, spp, seed=7, flags=0):
             o = mk()
-            ctx.filter_shade(tex, sub(u), sub(v), ds, filt, mode, "ggx", spp, seed, 0, out=o)
+            ctx.filter_shade(tex, sub(u), sub(v), ds, filt, mode, "ggx", spp, seed, flags, out=o)
             return float(((torch.stack(o, 1).double() - R) ** 2).mean().sqrt())
         r_before = rmse("ntap_before", 8)
         r_after = rmse("ntap_after", 8)
-        curve = {s: rmse("stochastic", s) for s in (1, 2, 4, 8, 16, 32, 64)}
-        s_star = next((s for s in sorted(curve) if curve[s] <= r_before), None)
+        curve = {s: rmse("stochastic", s) for s in SPP_GRID}
+        lat = {s: rmse("stochastic", s, flags=LATTICE) for s in SPP_GRID}
+        s_star = next((s for s in SPP_GRID if curve[s] <= r_before), None)
+        s_lat = next((s for s in SPP_GRID if lat[s] <= r_before), None)
         nfull = u.shape[0]
         outf = [torch.empty(nfull, dtype=torch.float32, device=dev) for _ in range(3)]
         t_before = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "ntap_before", "ggx", 8, 1, 0, out=outf))
         t_s8 = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", 8, 1, 0, out=outf))
         t_star = (_time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", s_star, 1, 0, out=outf))
                   if s_star else None)
+        t_lat = (_time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", s_lat, 1, LATTICE, out=outf))
+                 if s_lat else None)
         res[filt] = {
             "rmse_ntap_before_8spp": r_before, "rmse_ntap_after_8spp": r_after,
             "rmse_stochastic": {str(k): v for k, v in curve.items()},
@@ -299,6 +307,8 @@ def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
             "stochastic_lookups_per_s": nfull * 8 / (t_s8 / 1e3),
             "equal_spp_speedup": t_before / t_s8, "s_star": s_star,
             "equal_rmse_speedup": (t_before / t_star) if t_star else None,
+            "rmse_stochastic_lattice": {str(k): v for k, v in lat.items()}, "s_star_lattice": s_lat,
+            "equal_rmse_speedup_lattice": (t_before / t_lat) if t_lat else None,
         }
     return res
 
@@ -323,25 +333,123 @@ def volume_block(ctx, dev, args):
                          pix_begin=band_begin, pix_count=band, out=ref)
         R = ref.double()
 
-        def rmse(mode, spp):
-            ctx.march_volume(vh, cam, W, H, steps, filt, mode, spp=spp, seed=5, pix_begin=band_begin,
+        def rmse(mode, spp, flags=0):
+            ctx.march_volume(vh, cam, W, H, steps, filt, mode, spp=spp, seed=5, flags=flags, pix_begin=band_begin,
                              pix_count=band, out=sub)
             return float(((sub.double() - R) ** 2).mean().sqrt())
         r_before = rmse("ntap_before", 8)
         curve = {s: rmse("stochastic", s) for s in (1, 2, 4, 8, 16)}
-        s_star = next((s for s in sorted(curve) if curve[s] <= r_before), None)
+        lat = {s: rmse("stochastic", s, LATTICE) for s in SPP_GRID}
+        s_ind = next((s for s in SPP_GRID if rmse("stochastic", s) <= r_before), None)
+        s_lat = next((s for s in SPP_GRID if lat[s] <= r_before), None)
         t_before = _time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "ntap_before", spp=8, seed=5, out=out), 2)
         t_s8 = _time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "stochastic", spp=8, seed=5, out=out), 2)
-        t_star = (_time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "stochastic", spp=s_star, seed=5, out=out), 2)
-                  if s_star else None)
+        tt = lambda s, fl: (_time_launch(lambda: ctx.march_volume(vh, cam, W, H, steps, filt, "stochastic", spp=s,
+                                                                  seed=5, flags=fl, out=out), 2) if s else None)
+        t_ind, t_lat = tt(s_ind, 0), tt(s_lat, LATTICE)
         res[filt] = {"taps": taps, "rmse_ntap_before_8spp": r_before,
-                     "rmse_stochastic": {str(k): v for k, v in curve.items()}, "s_star": s_star,
+                     "rmse_stochastic": {str(k): v for k, v in curve.items()},
+                     "rmse_stochastic_lattice": {str(k): v for k, v in lat.items()},
+                     "s_star": s_ind, "s_star_lattice": s_lat,
                      "ms_ntap_before_8spp": t_before, "ms_stochastic_8spp": t_s8,
                      "ntap_step_lookups_per_s": n * 8 * steps / (t_before / 1e3),
                      "stochastic_step_lookups_per_s": n * 8 * steps / (t_s8 / 1e3),
                      "equal_spp_speedup": t_before / t_s8,
-                     "equal_rmse_speedup": (t_before / t_star) if t_star else None}
+                     "equal_rmse_speedup": (t_before / t_ind) if t_ind else None,
+                     "equal_rmse_speedup_lattice": (t_before / t_lat) if t_lat else None}
     ctx.destroy_volume(vh)
+    return res
+
+
+def neural_block(ctx, dev, material, steps=256, batch=1 << 18, nq=1 << 24, spp=8):
+    """Learned form at the task's scale: 8 channels at 4096^2 in 4 latent grids
+    (1024^2/512^2/256^2/128^2 x 8) + MLP 32-64-64-8, trained on 2^26 texels (256 x 2^18);
+    then filter + shade of 2^24 queries at 8 spp decoding the MLP once per sample
+    (stochastic) vs decode-then-filter with 4 (bilinear) and 16 (bicubic) decodes per sample."""
+    import torch
+    R0, grids = 4096, (1024, 512, 256, 128)
+    targets = synth.ntc_targets(material, 104)
+    lat, mlp = synth.ntc_init(grids, 104)
+    lat_bytes_fp16 = sum(r * r * 8 * 2 for r in grids)
+    net = ctx.neural_create(R0, lat, mlp, targets)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ctx.neural_train(net, steps, batch, 1e-2, 5e-3, seed=1)
+    train_s = time.perf_counter() - t0
+    res = {"train": {"steps": steps, "batch": batch, "seconds": train_s, "samples_per_s": steps * batch / train_s,
+                     "loss_first": float(losses[:4].mean()), "loss_last": float(losses[-8:].mean())}}
+    # explicit-texture judge on 2^20 random texels: channel MSE of the decode vs the targets,
+    # and the same-memory explicit alternative (targets box-downsampled to the byte budget of
+    # the FP16 latents, then bilinearly magnified)
+    rng = np.random.default_rng(3)
+    ix = rng.integers(0, R0, 1 << 20).astype(np.int32)
+    iy = rng.integers(0, R0, 1 << 20).astype(np.int32)
+    tix, tiy = torch.from_numpy(ix).to(dev), torch.from_numpy(iy).to(dev)
+    tg = targets[iy, ix].astype(np.float64) / 255.0
+    y16 = ctx.neural_decode(net, tix, tiy).cpu().numpy().astype(np.float64)
+    r_eq = int(math.sqrt(lat_bytes_fp16 / 8))
+    small = torch.nn.functional.interpolate(torch.from_numpy(targets).permute(2, 0, 1)[None].double(),
+                                            size=(r_eq, r_eq), mode="area")
+    up = torch.nn.functional.interpolate(small, size=(R0, R0), mode="bilinear", align_corners=False)[0]
+    base = up.permute(1, 2, 0).numpy()[iy, ix] / 255.0
+    res["judge"] = {"mse_neural_fp16": float(((y16 - tg) ** 2).mean()),
+                    "mse_same_memory_explicit": float(((base - tg) ** 2).mean()),
+                    "same_memory_explicit_res": r_eq, "latent_bytes_fp16": lat_bytes_fp16,
+                    "explicit_bytes": R0 * R0 * 8}
+    # shading judge: same seed, no MIPs -> the neural and explicit stochastic paths pick the
+    # same texels; the difference is the decode error as it reaches the shaded value
+    q = synth.queries_uniform(nq, 9)
+    u, v = torch.from_numpy(q.u).to(dev), torch.from_numpy(q.v).to(dev)
+    ex = ctx.create_texture([material.albedo_rough[0]], [material.normal[0]])
+    ea = ctx.filter_shade(ex, u[:1 << 20], v[:1 << 20], None, "bspline", "stochastic", "ggx", spp, 1)
+    na = ctx.neural_filter_shade(net, u[:1 << 20], v[:1 << 20], None, "bspline", "stochastic", "ggx", spp, 1)
+    E, N = torch.stack(ea[:3], 1).double(), torch.stack(na, 1).double()
+    res["judge"]["shaded_rmse_neural_vs_explicit"] = float(((N - E) ** 2).mean().sqrt())
+    res["judge"]["shaded_rms_explicit"] = float((E ** 2).mean().sqrt())
+    ctx.destroy_texture(ex)
+    out = [torch.empty(nq, dtype=torch.float32, device=dev) for _ in range(3)]
+    flop_per_decode = 2 * (32 * 64 + 64 * 64 + 64 * 8)
+    for name, (f, mode, per) in {"stochastic_1tap": ("bspline", "stochastic", 1),
+                                 "bilinear_4tap_decode_then_filter": ("linear", "ntap_before", 4),
+                                 "bicubic_16tap_decode_then_filter": ("bspline", "ntap_before", 16)}.items():
+        ms = _time_launch(lambda: ctx.neural_filter_shade(net, u, v, None, f, mode, "ggx", spp, 1, out=out), 2)
+        dec = nq * spp * per
+        res[name] = {"ms": ms, "lookups_per_s": nq * spp / (ms / 1e3), "decodes_per_s": dec / (ms / 1e3),
+                     "mlp_tflops": dec * flop_per_decode / (ms / 1e3) / 1e12}
+    res["speedup_1tap_vs_16tap"] = res["bicubic_16tap_decode_then_filter"]["ms"] / res["stochastic_1tap"]["ms"]
+    ctx.neural_quantize(net, "fp8")
+    y8 = ctx.neural_decode(net, tix, tiy).cpu().numpy().astype(np.float64)
+    ms8 = _time_launch(lambda: ctx.neural_filter_shade(net, u, v, None, "bspline", "stochastic", "ggx", spp, 1,
+                                                       out=out), 2)
+    res["fp8"] = {"mse_vs_targets": float(((y8 - tg) ** 2).mean()), "rmse_vs_fp16_form": float(np.sqrt(((y8 - y16) ** 2).mean())),
+                  "ms_stochastic_1tap": ms8, "latent_bytes": lat_bytes_fp16 // 2}
+    ctx.neural_destroy(net)
+    return res
+
+
+def table_block(ctx, dev, ntex=256, nq=1 << 26):
+    """Bindless table: 256 RGBA8 textures with sides log-uniform in [64, 4096] (~2 GiB), 2^26
+    mixed queries (texture id uniform), one persistent launch, Mitchell at 4 spp."""
+    import torch
+    texs = synth.texture_table_rgba8(ntex, 64, 4096, seed=105)
+    handles = [ctx.create_texture([t]) for t in texs]
+    tbytes = sum(t.nbytes for t in texs)
+    del texs
+    table = ctx.create_texture_table(handles)
+    rng = np.random.default_rng(5)
+    u = torch.from_numpy((rng.integers(0, 1 << 24, nq) * 2.0 ** -24).astype(np.float32)).to(dev)
+    v = torch.from_numpy((rng.integers(0, 1 << 24, nq) * 2.0 ** -24).astype(np.float32)).to(dev)
+    tid = torch.from_numpy(rng.integers(0, ntex, nq).astype(np.int32)).to(dev)
+    out = [torch.empty(nq, dtype=torch.float32, device=dev) for _ in range(3)]
+    res = {"textures": ntex, "texel_bytes": tbytes, "queries": nq, "spp": 4}
+    for mode in ("stochastic", "positivized"):
+        ms = _time_launch(lambda: ctx.filter_shade_table(table, u, v, tid, None, "mitchell", mode, "ggx", 4, 1,
+                                                         out=out), 2)
+        res[mode] = {"ms": ms, "lookups_per_s": nq * 4 / (ms / 1e3),
+                     "texel_fetches_per_lookup": 1 if mode == "stochastic" else 2}
+    ctx.destroy_texture_table(table)
+    for h in handles:
+        ctx.destroy_texture(h)
     return res
 
 

@@ -82,6 +82,9 @@ typedef enum { STF_ADDRESS_WRAP = 0, STF_ADDRESS_CLAMP = 1 } stf_address;
 
 /* flags */
 #define STF_FLAG_STRATIFIED 1u  /* jitter on a sqrt(spp) x sqrt(spp) grid (spp must be a square) */
+#define STF_FLAG_LATTICE 2u     /* stochastic modes: the pick uniforms of the spp samples of a query
+                                   (pixel) form a randomly shifted lattice, frac(s/spp + phi), so they
+                                   are stratified across samples; each stays uniform (unbiased) */
 
 /* device status bits */
 #define STF_DEV_NAN_INPUT 1u
@@ -153,6 +156,20 @@ stf_status stf_filter_shade(stf_ctx ctx, stf_tex tex, const stf_queries* q, cons
 stf_status stf_filter_shade_host(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
                                  stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                                  uint64_t seed, uint32_t flags, const stf_output* out);
+
+/* ---- bindless texture table: many textures in one persistent launch ------------------ */
+typedef uint64_t stf_table;
+/* A table of n existing textures (any sizes, formats and MIP counts); the textures must
+ * outlive the table (stf_destroy_texture refuses a texture a table still references). */
+stf_status stf_create_texture_table(stf_ctx ctx, uint32_t n, const stf_tex* textures, stf_table* out);
+stf_status stf_destroy_texture_table(stf_ctx ctx, stf_table table);
+/* stf_filter_shade over mixed textures: query i uses table entry tex_id[i] (device uint32
+ * [n]); one persistent launch whose blocks claim query chunks from an atomic work counter
+ * (table-owned, reset by each call; one call per table at a time).  An out-of-range id
+ * sets STF_DEV_BAD_INDEX and yields 0 for that query. */
+stf_status stf_filter_shade_table(stf_ctx ctx, stf_table table, const stf_queries* q, const uint32_t* tex_id,
+                                  const stf_derivs* d, stf_filter filter, stf_mode mode, stf_shade shade,
+                                  uint32_t spp, uint64_t seed, uint32_t flags, const stf_output* out);
 
 /* Same computation as stf_filter_shade_host, for callers that must not allocate device
  * memory while they look up textures (a frame loop with a fixed memory budget, or a

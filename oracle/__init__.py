@@ -32,6 +32,7 @@ FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FLAG_STRATIFIED = 1
+FLAG_LATTICE = 2
 NO_PICK = 0xFFFFFFFF
 
 

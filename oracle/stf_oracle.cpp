@@ -43,7 +43,7 @@ namespace {
 enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
-enum { FLAG_STRATIFIED = 1u };
+enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u };
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_NEURAL = 2 };
 enum { ADDR_WRAP = 0, ADDR_CLAMP = 1 };
 const uint32_t NO_PICK = 0xFFFFFFFFu;
@@ -80,6 +80,25 @@ void uniforms5(const uint32_t w[4], float u[5]) {
     for (int i = 0; i < 4; ++i) u[i] = unif(w[i]);
     uint32_t f = ((w[0] & 0xFFu) << 16) | ((w[1] & 0xFFu) << 8) | (w[2] & 0xFFu);
     u[4] = (float)f * 5.9604644775390625e-8f;
+}
+
+// Integer forms of uniforms5 (24-bit numerators) and uniforms6 (21-bit numerators).
+void ints5(const uint32_t w[4], uint32_t f[5]) {
+    for (int i = 0; i < 4; ++i) f[i] = w[i] >> 8;
+    f[4] = ((w[0] & 0xFFu) << 16) | ((w[1] & 0xFFu) << 8) | (w[2] & 0xFFu);
+}
+void ints6(const uint32_t w[4], uint32_t f[6]) {
+    for (int i = 0; i < 4; ++i) f[i] = w[i] >> 11;
+    f[4] = (w[0] & 0x7FFu) | ((w[1] & 0x3FFu) << 11);
+    f[5] = (w[2] & 0x7FFu) | ((w[3] & 0x3FFu) << 11);
+}
+// Randomly shifted lattice over the spp samples of one query (FLAG_LATTICE): sample s of
+// spp takes frac(s/spp + phi), phi a per-query Philox offset; in exact integer arithmetic
+// on the 2^bits grid.  Each value is uniform; the spp values are stratified.
+float lattice(uint32_t phi, uint32_t s, uint32_t spp, int bits) {
+    uint32_t mask = (1u << bits) - 1u;
+    uint32_t shift = (uint32_t)(((uint64_t)s << bits) / spp);
+    return (float)((phi + shift) & mask) * std::ldexp(1.0f, -bits);
 }
 
 // Six 21-bit uniforms from one Philox output (two volume march steps, three each).
@@ -375,6 +394,17 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
         float a[5], b[5];
         uniforms5(r0, a);
         uniforms5(r1, b);
+        if (flags & FLAG_LATTICE) {
+            // pick uniforms (level, pick x/y, class and negative picks) from a shifted
+            // lattice across the samples; the jitter stays independent per sample
+            uint32_t z0[4], z1[4], f0[5], f1[5];
+            draw(seed, id, 0xFFFFFFFFu, 0, z0);
+            draw(seed, id, 0xFFFFFFFFu, 1, z1);
+            ints5(z0, f0);
+            ints5(z1, f1);
+            for (int k = 2; k < 5; ++k) a[k] = lattice(f0[k], s, spp, 24);
+            for (int k = 0; k < 4; ++k) b[k] = lattice(f1[k], s, spp, 24);
+        }
         // screen-space jitter inside the pixel footprint (FP32, fixed order)
         float x = Q.u[q], y = Q.v[q];
         if (Q.dudx) {
@@ -615,8 +645,15 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
             // steps 2p and 2p+1 share stream p+1: six 21-bit uniforms, three per step
             uint32_t rr[4];
             float u6[6];
-            draw(seed, pix, s, (k >> 1) + 1, rr);
-            uniforms6(rr, u6);
+            if (flags & FLAG_LATTICE) {
+                uint32_t f6[6];
+                draw(seed, pix, 0xFFFFFFFFu, (k >> 1) + 1, rr);
+                ints6(rr, f6);
+                for (int j = 0; j < 6; ++j) u6[j] = lattice(f6[j], s, spp, 21);
+            } else {
+                draw(seed, pix, s, (k >> 1) + 1, rr);
+                uniforms6(rr, u6);
+            }
             const float* uk = u6 + 3 * (k & 1);
             int kk[3];
             for (int a = 0; a < 3; ++a) {

@@ -20,6 +20,7 @@ MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F = 0, 1, 2, 3
 FLAG_STRATIFIED = 1
+FLAG_LATTICE = 2
 DEV_NAN_INPUT, DEV_BAD_INDEX = 1, 2
 NO_PICK = 0xFFFFFFFF
 
@@ -81,6 +82,10 @@ SIGNATURES = {
                           _U32, C.POINTER(_Output)], _I),
     "stf_filter_shade_host": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                _U64, _U32, C.POINTER(_Output)], _I),
+    "stf_create_texture_table": ([_P, _U32, _P, C.POINTER(_U64)], _I),
+    "stf_destroy_texture_table": ([_P, _U64], _I),
+    "stf_filter_shade_table": ([_P, _U64, C.POINTER(_Queries), _P, C.POINTER(_Derivs), _I, _I, _I, _U32, _U64, _U32,
+                                C.POINTER(_Output)], _I),
     "stf_filter_shade_host_noalloc": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                        _U64, _U32, C.POINTER(_Output)], _I),
     "stf_create_volume": ([_P, _U32, _U32, _U32, _I, _F, _P, _I, C.POINTER(_U64)], _I),
@@ -241,6 +246,31 @@ class Context:
         q, d, o = self._args(u, v, derivs, out, picks, n, id_base)
         st = lib().stf_filter_shade_host(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
                                          FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2], picks
+
+    def create_texture_table(self, textures) -> int:
+        arr = (C.c_uint64 * len(textures))(*textures)
+        out = C.c_uint64(0)
+        self._check(lib().stf_create_texture_table(self.h, len(textures), arr, C.byref(out)), self.h)
+        return int(out.value)
+
+    def destroy_texture_table(self, table: int):
+        self._check(lib().stf_destroy_texture_table(self.h, table), self.h)
+
+    def filter_shade_table(self, table: int, u, v, tex_id, derivs=None, filter: str = "mitchell",
+                           mode: str = "stochastic", shade: str = "ggx", spp: int = 1, seed: int = 1,
+                           flags: int = 0, id_base: int = 0, out=None, want_picks: bool = False):
+        """tex_id: int32/uint32 cuda tensor [n] of table entries."""
+        torch = self.torch
+        n = int(u.shape[0])
+        if out is None:
+            out = [torch.empty(n, dtype=torch.float32, device=u.device) for _ in range(3)]
+        picks = torch.empty((n, spp, 2), dtype=torch.int32, device=u.device) if want_picks else None
+        q, d, o = self._args(u, v, derivs, out, picks, n, id_base)
+        st = lib().stf_filter_shade_table(self.h, table, C.byref(q), C.c_void_p(_ptr(tex_id)),
+                                          C.byref(d) if d is not None else None, FILTERS[filter], MODES[mode],
+                                          SHADES[shade], spp, seed, flags, C.byref(o))
         self._check(st, self.h)
         return out[0], out[1], out[2], picks
 

@@ -13,13 +13,6 @@
 
 namespace stf {
 
-struct FetchCtx {
-    const unsigned char* base;
-    int fmt, levels, has_normal;
-    uint64_t off[16];
-    int w[16], h[16];
-};
-
 __device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, int iy) {
     const size_t idx = (size_t)iy * (size_t)T.w[lvl] + (size_t)ix;
     if (T.fmt == FMT_RGBA32F) {
@@ -51,14 +44,15 @@ __device__ __forceinline__ float lod_aniso(float dudx, float dvdx, float dudy, f
     return fminf(fmaxf(l, 0.0f), (float)(levels - 1));
 }
 
+// One query: all its samples, written to a.r/g/b[q].  T is the texture (a kernel
+// parameter, or a descriptor in global memory for the bindless table).
 template <int FILTER, int MODE>
-__global__ void __launch_bounds__(256)
-k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC, RoundKeys K) {
+__device__ __forceinline__ void query_body(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
+                                           const RoundKeys& K, uint64_t q) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
     const float inv_spp = 1.0f / (float)a.spp;
     const int kside = a.kside;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n;
-         q += (uint64_t)gridDim.x * blockDim.x) {
+    {
         const float u = a.u[q], v = a.v[q];
         float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f;
         float lam = 0.0f;
@@ -73,10 +67,20 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC, RoundKeys K) {
         const uint64_t id = a.id_base + q;
         const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
         float3 acc = make_float3(0.f, 0.f, 0.f);
+        const bool lat = (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) && (a.flags & FLAG_LATTICE);
+        I5 LA{}, LB{};
+        if (lat) {   // per-query lattice offsets of the pick uniforms
+            LA = ints5(philox(id_lo, id_hi, 0xFFFFFFFFu, 0u, K));
+            if (MODE == M_POSITIVIZED) LB = ints5(philox(id_lo, id_hi, 0xFFFFFFFFu, 1u, K));
+        }
 
         for (uint32_t s = 0; s < a.spp; ++s) {
             // stream 0: (jitter x, jitter y, level, pick x, pick y)
-            const U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            if (lat) {
+#pragma unroll
+                for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], s, a.spp, 24);
+            }
             float x = u, y = v;
             if (a.has_derivs) {
                 float jx, jy;
@@ -131,7 +135,11 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC, RoundKeys K) {
                     const float Wp = __fadd_rn(__fmul_rn(Px, Py), __fmul_rn(Nx, Ny));
                     const float Wn = __fadd_rn(__fmul_rn(Px, Ny), __fmul_rn(Nx, Py));
                     // stream 1: (positive class, negative pick x, negative pick y, negative class)
-                    const U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                    U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                    if (lat) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], s, a.spp, 24);
+                    }
                     const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
                     const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
                     const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
@@ -227,6 +235,42 @@ k_filter_shade(FilterShadeArgs a, FetchCtx T, ShadeConst SC, RoundKeys K) {
 }
 
 template <int FILTER, int MODE>
+__global__ void __launch_bounds__(256)
+k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n;
+         q += (uint64_t)gridDim.x * blockDim.x)
+        query_body<FILTER, MODE>(a, T, SC, K, q);
+}
+
+// Bindless persistent launch: one grid sized to the SMs; each block claims the next
+// chunk of blockDim.x queries from an atomic work counter (zero on entry) and looks up
+// each query's texture descriptor in the table.  An out-of-range texture id sets
+// DEV_BAD_INDEX and yields 0.
+template <int FILTER, int MODE>
+__global__ void __launch_bounds__(256)
+k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint32_t ntex,
+                     const uint32_t* __restrict__ tex_id, unsigned long long* counter, ShadeConst SC, RoundKeys K) {
+    __shared__ unsigned long long chunk;
+    for (;;) {
+        if (threadIdx.x == 0) chunk = atomicAdd(counter, (unsigned long long)blockDim.x);
+        __syncthreads();
+        const unsigned long long base = chunk;
+        __syncthreads();
+        if (base >= a.n) break;
+        const uint64_t q = base + threadIdx.x;
+        if (q < a.n) {
+            const uint32_t t = __ldg(tex_id + q);
+            if (t < ntex) {
+                query_body<FILTER, MODE>(a, table[t], SC, K, q);
+            } else {
+                atomicOr(a.status, DEV_BAD_INDEX);
+                a.r[q] = 0.0f; a.g[q] = 0.0f; a.b[q] = 0.0f;
+            }
+        }
+    }
+}
+
+template <int FILTER, int MODE>
 static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                              int grid, cudaStream_t st) {
     k_filter_shade<FILTER, MODE><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
@@ -260,13 +304,53 @@ ShadeConst make_shade_const() {
     return C;
 }
 
-cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int num_sms, cudaStream_t st) {
+FetchCtx make_fetch_ctx(const TexView& tv) {
     FetchCtx T;
     T.base = static_cast<const unsigned char*>(tv.base);
     T.fmt = tv.fmt;
     T.levels = tv.levels;
     T.has_normal = tv.has_normal;
     for (int i = 0; i < 16; ++i) { T.off[i] = tv.off[i]; T.w[i] = tv.w[i]; T.h[i] = tv.h[i]; }
+    return T;
+}
+
+template <int FILTER, int MODE>
+static cudaError_t launch_table_fm(const FilterShadeArgs& a, const FetchCtx* table, uint32_t ntex,
+                                   const uint32_t* tex_id, unsigned long long* counter, int num_sms, cudaStream_t st) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_shade_table<FILTER, MODE>, 256, 0);
+    const int grid = num_sms * (per_sm > 0 ? per_sm : 1);
+    k_filter_shade_table<FILTER, MODE><<<grid, 256, 0, st>>>(a, table, ntex, tex_id, counter, make_shade_const(),
+                                                             expand_key(a.seed));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_shade_table(const FilterShadeArgs& a, const FetchCtx* table, uint32_t ntex,
+                                      const uint32_t* tex_id, unsigned long long* counter, int num_sms,
+                                      cudaStream_t st) {
+#define STF_TABLE_MODES(F)                                                                               \
+    if (a.filter == F) {                                                                                \
+        switch (a.mode) {                                                                               \
+            case M_NTAP_BEFORE: return launch_table_fm<F, M_NTAP_BEFORE>(a, table, ntex, tex_id, counter, num_sms, st); \
+            case M_NTAP_AFTER: return launch_table_fm<F, M_NTAP_AFTER>(a, table, ntex, tex_id, counter, num_sms, st);   \
+            case M_STOCHASTIC: return launch_table_fm<F, M_STOCHASTIC>(a, table, ntex, tex_id, counter, num_sms, st);   \
+            default: break;                                                                             \
+        }                                                                                               \
+    }
+    STF_TABLE_MODES(F_LINEAR)
+    STF_TABLE_MODES(F_BSPLINE)
+    STF_TABLE_MODES(F_CATMULL_ROM)
+    STF_TABLE_MODES(F_MITCHELL)
+#undef STF_TABLE_MODES
+    if (a.mode == M_POSITIVIZED) {
+        if (a.filter == F_MITCHELL) return launch_table_fm<F_MITCHELL, M_POSITIVIZED>(a, table, ntex, tex_id, counter, num_sms, st);
+        if (a.filter == F_CATMULL_ROM) return launch_table_fm<F_CATMULL_ROM, M_POSITIVIZED>(a, table, ntex, tex_id, counter, num_sms, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int num_sms, cudaStream_t st) {
+    const FetchCtx T = make_fetch_ctx(tv);
     const ShadeConst SC = make_shade_const();
     const uint64_t blocks_needed = (a.n + 255) / 256;
     const uint64_t cap = (uint64_t)num_sms * 8;

@@ -85,9 +85,17 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                 for (int c = 0; c < 3; ++c) axis_weights<FILTER>(ap[c].t, w[c]);
                 if (MODE == M_STOCHASTIC) {
                     // steps 2p and 2p+1 share stream p+1 (six 21-bit uniforms)
-                    if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
                     float uk[3];
-                    uniforms3_of6(rw, (int)(k & 1u), uk);
+                    if (a.flags & FLAG_LATTICE) {   // per-pixel offsets, shifted lattice over samples
+                        if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, 0xFFFFFFFFu, (k >> 1) + 1u, K);
+                        uint32_t f[3];
+                        ints3_of6(rw, (int)(k & 1u), f);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) uk[c] = lattice(f[c], s, a.spp, 21);
+                    } else {
+                        if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
+                        uniforms3_of6(rw, (int)(k & 1u), uk);
+                    }
                     const int kx = cdf_pick<NT>(w[0], uk[0], 0, nullptr);
                     const int ky = cdf_pick<NT>(w[1], uk[1], 0, nullptr);
                     const int kz = cdf_pick<NT>(w[2], uk[2], 0, nullptr);

@@ -67,7 +67,7 @@ stf_status validate_filter_call(stf_ctx c, stf_tex t, const stf_queries* q, cons
     if (m == STF_MODE_STOCHASTIC_POSITIVIZED && !signed_filter(f))
         return fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
     if (spp == 0) return fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
-    if (flags & ~(uint32_t)STF_FLAG_STRATIFIED) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
     if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0)
         return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
     if (q->n == 0) return STF_OK;
@@ -140,6 +140,7 @@ stf_status stf_destroy(stf_ctx c) {
     cudaStreamSynchronize(c->stream);
     for (auto& kv : c->tex) cudaFree(kv.second.mem);
     for (auto& kv : c->vol) cudaFree(kv.second.mem);
+    for (auto& kv : c->tables) cudaFree(kv.second.mem);
     for (auto& kv : c->neural) { cudaFree(kv.second.mem); if (kv.second.loss) cudaFree(kv.second.loss); }
     if (c->stage) cudaFree(c->stage);
     if (c->d_status) cudaFree(c->d_status);
@@ -249,6 +250,9 @@ stf_status stf_destroy_texture(stf_ctx c, stf_tex t) {
     if (!c) return STF_ERR_INVALID_ARG;
     auto it = c->tex.find(t);
     if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle");
+    for (auto& kv : c->tables)
+        for (uint64_t m : kv.second.members)
+            if (m == t) return fail(c, STF_ERR_INVALID_ARG, "texture is referenced by a texture table");
     CurrentDevice cd(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(it->second.mem);
@@ -320,6 +324,75 @@ stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, con
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "device->host copy");
 }
 
+// ---------------------------------------------------------------------------- texture table
+stf_status stf_create_texture_table(stf_ctx c, uint32_t n, const stf_tex* textures, stf_table* out) {
+    if (!c || !textures || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
+    *out = 0;
+    if (n < 1 || n > (1u << 20)) return fail(c, STF_ERR_INVALID_ARG, "table size must be 1..2^20");
+    std::vector<stf::FetchCtx> host(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        auto it = c->tex.find(textures[i]);
+        if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle in table");
+        host[i] = stf::make_fetch_ctx(it->second.view);
+    }
+    CurrentDevice cd(c->device);
+    TableRec rec;
+    rec.n = n;
+    rec.members.assign(textures, textures + n);
+    const size_t bytes = (size_t)n * sizeof(stf::FetchCtx);
+    const size_t cnt_off = (bytes + 255) & ~(size_t)255;
+    stf_status s = dev_alloc(c, &rec.mem, cnt_off + 256);
+    if (s != STF_OK) return s;
+    rec.counter = (unsigned long long*)((char*)rec.mem + cnt_off);
+    cudaError_t e = cudaMemcpyAsync(rec.mem, host.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { cudaFree(rec.mem); return cuda_fail(c, e, "table upload"); }
+    const uint64_t h = c->next_handle++;
+    c->tables[h] = std::move(rec);
+    *out = h;
+    return STF_OK;
+}
+
+stf_status stf_destroy_texture_table(stf_ctx c, stf_table t) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    auto it = c->tables.find(t);
+    if (it == c->tables.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown table handle");
+    CurrentDevice cd(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(it->second.mem);
+    c->tables.erase(it);
+    return STF_OK;
+}
+
+stf_status stf_filter_shade_table(stf_ctx c, stf_table t, const stf_queries* q, const uint32_t* tex_id,
+                                  const stf_derivs* d, stf_filter f, stf_mode m, stf_shade sh, uint32_t spp,
+                                  uint64_t seed, uint32_t flags, const stf_output* out) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    auto it = c->tables.find(t);
+    if (it == c->tables.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown table handle");
+    if (c->tex.empty()) return fail(c, STF_ERR_BAD_HANDLE, "no textures");
+    // validate everything but the texture handle with the regular checks
+    TexRec* any = nullptr;
+    stf_status s = validate_filter_call(c, c->tex.begin()->first, q, d, f, m, sh, spp, flags, out, &any);
+    if (s != STF_OK || q->n == 0) return s;
+    if (!tex_id || !aligned4(tex_id)) return fail(c, STF_ERR_INVALID_ARG, "tex_id must be non-null and 4-byte aligned");
+    if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
+    CurrentDevice cd(c->device);
+    stf::FilterShadeArgs a{};
+    a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v;
+    a.has_derivs = d ? 1 : 0;
+    if (d) { a.dudx = d->dudx; a.dvdx = d->dvdx; a.dudy = d->dudy; a.dvdy = d->dvdy; }
+    a.filter = f; a.mode = m; a.shade = sh; a.spp = spp; a.flags = flags;
+    a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
+    a.seed = seed; a.r = out->r; a.g = out->g; a.b = out->b; a.picks = out->picks;
+    a.status = c->d_status;
+    cudaError_t e = cudaMemsetAsync(it->second.counter, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess)
+        e = stf::launch_filter_shade_table(a, (const stf::FetchCtx*)it->second.mem, it->second.n, tex_id,
+                                           it->second.counter, c->num_sms, c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "filter_shade_table launch");
+}
+
 // --------------------------------------------------------------------------------- volume
 stf_status stf_create_volume(stf_ctx c, uint32_t nx, uint32_t ny, uint32_t nz, stf_format fmt,
                              float sigma_scale, const void* data, int on_device, stf_vol* out) {
@@ -367,7 +440,7 @@ stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t wid
     if (m != STF_MODE_NTAP_BEFORE && m != STF_MODE_NTAP_AFTER && m != STF_MODE_STOCHASTIC)
         return fail(c, STF_ERR_UNSUPPORTED, "volume mode must be NTAP_BEFORE, NTAP_AFTER or STOCHASTIC");
     if (width < 1 || height < 1 || steps < 1 || steps > 65535 || spp < 1) return fail(c, STF_ERR_INVALID_ARG, "bad image size, steps or spp");
-    if (flags & ~(uint32_t)STF_FLAG_STRATIFIED) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
     if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0) return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
     if (pix_begin + pix_count > (uint64_t)width * height) return fail(c, STF_ERR_INVALID_ARG, "pixel range outside the image");
     if (pix_count == 0) return STF_OK;

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "../../include/stf.h"
 #include "stf_kernels.h"
@@ -29,6 +30,13 @@ struct NeuralRec {
     bool trainable = false;
 };
 
+struct TableRec {
+    void* mem = nullptr;              // FetchCtx[n] followed by the 8-byte work counter
+    uint32_t n = 0;
+    std::vector<uint64_t> members;    // texture handles (they must outlive the table)
+    unsigned long long* counter = nullptr;
+};
+
 struct stf_ctx_s {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -39,6 +47,7 @@ struct stf_ctx_s {
     std::unordered_map<uint64_t, TexRec> tex;
     std::unordered_map<uint64_t, VolRec> vol;
     std::unordered_map<uint64_t, NeuralRec> neural;
+    std::unordered_map<uint64_t, TableRec> tables;
     void* stage = nullptr;          // device staging for the host-buffer entry points
     size_t stage_bytes = 0;
     int fault = 0;                  // host-side fault injection (STF_FAULT), 0 = off

@@ -14,7 +14,7 @@ enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { SH_GGX = 0, SH_LINEAR = 1 };
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
-enum { FLAG_STRATIFIED = 1u };
+enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u };
 enum { DEV_NAN_INPUT = 1u, DEV_BAD_INDEX = 2u, DEV_TIMEOUT = 4u };
 constexpr uint32_t NO_PICK = 0xFFFFFFFFu;
 
@@ -61,6 +61,31 @@ __device__ __forceinline__ U5 uniforms5(uint4 w) {
     r.u[4] = __uint2float_rn(f) * 5.9604644775390625e-8f;
     return r;
 }
+// Randomly shifted lattice across the spp samples of one query (FLAG_LATTICE): sample s
+// takes frac(s/spp + phi) with a per-query offset phi, in exact integer arithmetic on the
+// 2^bits grid.
+__device__ __forceinline__ float lattice(uint32_t phi, uint32_t s, uint32_t spp, int bits) {
+    const uint32_t shift = (uint32_t)(((uint64_t)s << bits) / spp);
+    return __uint2float_rn((phi + shift) & ((1u << bits) - 1u)) * __int_as_float((127 - bits) << 23);
+}
+// integer numerators of uniforms5
+struct I5 { uint32_t f[5]; };
+__device__ __forceinline__ I5 ints5(uint4 w) {
+    I5 r;
+    r.f[0] = w.x >> 8; r.f[1] = w.y >> 8; r.f[2] = w.z >> 8; r.f[3] = w.w >> 8;
+    r.f[4] = ((w.x & 0xFFu) << 16) | ((w.y & 0xFFu) << 8) | (w.z & 0xFFu);
+    return r;
+}
+// integer numerators of the three 21-bit uniforms of step parity `odd`
+__device__ __forceinline__ void ints3_of6(uint4 w, int odd, uint32_t f[3]) {
+    if (!odd) { f[0] = w.x >> 11; f[1] = w.y >> 11; f[2] = w.z >> 11; }
+    else {
+        f[0] = w.w >> 11;
+        f[1] = (w.x & 0x7FFu) | ((w.y & 0x3FFu) << 11);
+        f[2] = (w.z & 0x7FFu) | ((w.w & 0x3FFu) << 11);
+    }
+}
+
 // six 21-bit uniforms per Philox output: three for each of two volume march steps
 __device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
     const float k = 4.76837158203125e-7f;

@@ -17,6 +17,14 @@ struct TexView {
     int w[16], h[16];
 };
 
+// texture as the kernels read it (kernel parameter, or one entry of a bindless table)
+struct FetchCtx {
+    const unsigned char* base;
+    int fmt, levels, has_normal;
+    uint64_t off[16];
+    int w[16], h[16];
+};
+
 struct FilterShadeArgs {
     uint64_t n, id_base;
     const float *u, *v, *dudx, *dvdx, *dudy, *dvdy;
@@ -90,6 +98,10 @@ struct ShadeConst;
 ShadeConst make_shade_const();
 
 cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int num_sms, cudaStream_t st);
+FetchCtx make_fetch_ctx(const TexView& tv);
+cudaError_t launch_filter_shade_table(const FilterShadeArgs& a, const FetchCtx* table, uint32_t ntex,
+                                      const uint32_t* tex_id, unsigned long long* counter, int num_sms,
+                                      cudaStream_t st);
 cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_pack_rgba8(const void* rgba, const void* rg, void* out, uint64_t n, cudaStream_t st);
 

@@ -299,3 +299,24 @@ def ntc_init(grid_res=(1024, 512, 256, 128), seed: int = 104):
         parts.append(rng.uniform(-b, b, (fan_out, fan_in)).astype(np.float32).ravel())
         parts.append(np.zeros(fan_out, dtype=np.float32))
     return lat, np.concatenate(parts)
+
+
+# ---------------------------------------------------------------------------------
+# bindless table: many textures of uneven sizes
+# ---------------------------------------------------------------------------------
+def texture_table_rgba8(n: int = 256, lo: int = 64, hi: int = 4096, seed: int = 105, fbm_below: int = 0):
+    """n RGBA8 textures (single level) with side lengths log-uniform in [lo, hi] (any
+    integer, non-powers of two included).  Texels are white-noise bytes: the gather
+    pattern, not the content, is what a table of uneven textures stresses, and generating
+    ~2 GiB of fBm on the host would dominate a run.  Textures with a side below
+    ``fbm_below`` get fBm content instead."""
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), n))).astype(int)
+    out = []
+    for i, s_ in enumerate(sides):
+        if s_ < fbm_below:
+            m = material_rgba8(int(s_), seed * 1000 + i, octaves=3, base=2, mips=False) if s_ >= 4 else None
+            out.append(m.albedo_rough[0] if m is not None else rng.integers(0, 256, (s_, s_, 4), dtype=np.uint8))
+        else:
+            out.append(rng.integers(0, 256, (int(s_), int(s_), 4), dtype=np.uint8))
+    return out

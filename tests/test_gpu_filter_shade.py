@@ -204,3 +204,11 @@ def _full_handle(ctx, m):
     if "h" not in _FULL:
         _FULL["h"] = ctx.create_texture(m.albedo_rough, m.normal)
     return _FULL["h"]
+
+
+@pytest.mark.parametrize("filter,mode", [("bspline", "stochastic"), ("mitchell", "positivized"),
+                                         ("linear", "stochastic")])
+def test_lattice_sampler(ctx, material, filter, mode):
+    import oracle as _o
+    h, otex, q = material
+    _check(ctx, h, otex, q, filter, mode, spp=6, seed=13, flags=_o.FLAG_LATTICE)

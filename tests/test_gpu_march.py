@@ -103,3 +103,15 @@ def _full_handle(ctx, vol):
     if "h" not in _FULL:
         _FULL["h"] = ctx.create_volume(vol, 20.0)
     return _FULL["h"]
+
+
+@pytest.mark.parametrize("filter", ["linear", "bspline"])
+def test_lattice_sampler(ctx, small, filter):
+    h, vol = small
+    cam = synth.camera_pinhole(W, H).as_array()
+    T, pk = ctx.march_volume(h, cam, W, H, 128, filter, "stochastic", spp=5, seed=8, flags=oracle.FLAG_LATTICE,
+                             want_picks=True)
+    ref = oracle.march(vol, 20.0, cam, W, H, 128, filter, "stochastic", spp=5, seed=8, flags=oracle.FLAG_LATTICE,
+                       want_picks=True)
+    mism = compare_picks(pk.cpu().numpy().view(np.uint32), ref, W * H)
+    assert_values(T.cpu().numpy(), ref.T, mism)

@@ -462,3 +462,54 @@ def test_jitter_footprint_matches_scipy():
             acc[:, c] += ndimage.map_coordinates(img[..., c], [y * 16 - 0.5, x * 16 - 0.5], order=1,
                                                  mode="grid-wrap", prefilter=False)
     np.testing.assert_allclose(r.rgb, acc / (k * k), atol=1e-6)
+
+
+# ------------------------------------------------------------------------ lattice sampler
+def test_lattice_picks_are_stratified():
+    # FLAG_LATTICE: the pick uniform of sample s is frac(s/spp + phi), so over the spp
+    # samples of one query (no jitter, one level) each tap is chosen floor or ceil of
+    # spp * p_k times -- the lattice's stratification, with the exact per-tap probability
+    tex = _tiny_tex(16, seed=3)
+    q = synth.queries_uniform(200, 81)
+    spp = 16
+    r = oracle.filter_shade(tex, q, "bspline", "stochastic", spp=spp, seed=5, flags=oracle.FLAG_LATTICE,
+                            want_picks=True)
+    for i in range(q.n):
+        px = float(np.float32(q.u[i]) * np.float32(16)) - 0.5
+        tx = px - math.floor(px)
+        p = np.array([oracle.kernel("bspline", tx - k) for k in _taps("bspline")])
+        ix0 = math.floor(px)
+        xs = (r.picks[i, :, 0] & 0x3FFF).astype(int)
+        counts = np.array([np.sum(xs == (ix0 + k) % 16) for k in _taps("bspline")])
+        assert np.all(np.abs(counts - spp * p) <= 1.0 + 1e-9), (counts, spp * p)
+
+
+@pytest.mark.parametrize("f,mode", [("bspline", "stochastic"), ("mitchell", "positivized")])
+def test_lattice_estimator_unbiased(f, mode):
+    m = synth.material_rgba8(8, 3, octaves=3, base=2)
+    tex = oracle.Texture(m.albedo_rough, m.normal)
+    q = synth.queries_uniform(4, 19, res=8, lod_range=2.5)
+    d = []
+    for seed in range(1, 2001):
+        s = oracle.filter_shade(tex, q, f, mode, spp=4, seed=seed, flags=oracle.FLAG_LATTICE).rgb
+        a = oracle.filter_shade(tex, q, f, "ntap_after", spp=4, seed=seed).rgb
+        d.append(s - a)
+    d = np.array(d)
+    z = np.abs(d.mean(0)) / (d.std(0) / math.sqrt(len(d)) + 1e-12)
+    assert z.max() < 4.5, z.max()
+
+
+def test_volume_lattice_unbiased_and_lower_variance():
+    vol = synth.volume_cloud(16, 5, zero_frac=0.5, octaves=3, base=2)
+    W, H = 4, 3
+    cam = synth.camera_pinhole(W, H).as_array()
+    ind, lat = [], []
+    for seed in range(1, 801):
+        a = oracle.march(vol, 20.0, cam, W, H, 48, "bspline", "ntap_after", spp=8, seed=seed, pix_begin=5, pix_count=1).T[0]
+        ind.append(oracle.march(vol, 20.0, cam, W, H, 48, "bspline", "stochastic", spp=8, seed=seed,
+                                pix_begin=5, pix_count=1).T[0] - a)
+        lat.append(oracle.march(vol, 20.0, cam, W, H, 48, "bspline", "stochastic", spp=8, seed=seed,
+                                flags=oracle.FLAG_LATTICE, pix_begin=5, pix_count=1).T[0] - a)
+    ind, lat = np.array(ind), np.array(lat)
+    assert abs(lat.mean()) < 4 * lat.std() / math.sqrt(len(lat)) + 1e-12
+    assert lat.std() < ind.std()
