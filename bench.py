@@ -388,7 +388,7 @@ def neural_block(ctx, dev, material, steps=256, batch=1 << 18, nq=1 << 24, spp=8
     tg = targets[iy, ix].astype(np.float64) / 255.0
     y16 = ctx.neural_decode(net, tix, tiy).cpu().numpy().astype(np.float64)
     r_eq = int(math.sqrt(lat_bytes_fp16 / 8))
-    small = torch.nn.functional.interpolate(torch.from_numpy(targets).permute(2, 0, 1)[None].double(),
+    small = torch.nn.functional.interpolate(torch.from_numpy(targets).permute(2, 0, 1)[None].float(),
                                             size=(r_eq, r_eq), mode="area")
     up = torch.nn.functional.interpolate(small, size=(R0, R0), mode="bilinear", align_corners=False)[0]
     base = up.permute(1, 2, 0).numpy()[iy, ix] / 255.0
