@@ -522,6 +522,44 @@ def run_volume(args):
     ctx.close()
 
 
+def run_neural(args):
+    """Learned-form workload: 4096^2 neural texture (briefly trained), filter + shade of
+    --queries queries at 8 spp with one tensor-core MLP decode per sample (single GPU)."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    material = synth.material_rgba8(TEX_RES, 102, octaves=6)
+    lat, mlp = synth.ntc_init((1024, 512, 256, 128), 104)
+    net = ctx.neural_create(TEX_RES, lat, mlp, synth.ntc_targets(material, 104))
+    ctx.neural_train(net, 16, 1 << 18, seed=1)
+    q = synth.queries_uniform(args.queries, 9)
+    u, v = torch.from_numpy(q.u).to(dev), torch.from_numpy(q.v).to(dev)
+    out = [torch.empty(args.queries, dtype=torch.float32, device=dev) for _ in range(3)]
+    go = lambda: ctx.neural_filter_shade(net, u, v, None, args.nfilter, args.nmode, "ggx", SPP, 1, out=out)
+    for _ in range(args.warmup):
+        go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        go()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    per = {"stochastic": 1, "positivized": 2}.get(args.nmode, 4 if args.nfilter == "linear" else 16)
+    dec = args.queries * SPP * per
+    print(json.dumps({"metric": "neural filter+shade lookups/s", "value": args.queries * SPP / (ms / 1e3),
+                      "unit": "lookups/s", "ms_per_step": ms, "decodes_per_s": dec / (ms / 1e3),
+                      "mlp_tflops": dec * 2 * (32 * 64 + 64 * 64 + 64 * 8) / (ms / 1e3) / 1e12,
+                      "config": {"workload": f"neural 4096^2, {args.queries} queries, {args.nfilter} {args.nmode}, {SPP} spp"}}),
+          flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,7 +570,9 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1 << 13)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="material", choices=["material", "volume"])
+    ap.add_argument("--workload", default="material", choices=["material", "volume", "neural"])
+    ap.add_argument("--nfilter", default="bspline", choices=["bspline", "linear", "mitchell"])
+    ap.add_argument("--nmode", default="stochastic", choices=["stochastic", "ntap_before", "positivized"])
     ap.add_argument("--vfilter", default="bspline", choices=["bspline", "linear"])
     ap.add_argument("--vmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after"])
     ap.add_argument("--width", type=int, default=1920)
@@ -544,6 +584,8 @@ def main():
         run_reference(args)
     elif args.workload == "volume":
         run_volume(args)
+    elif args.workload == "neural":
+        run_neural(args)
     else:
         run_ours(args)
 

@@ -74,8 +74,8 @@ struct Tap { int x, y; float w; };
 // bilinear taps of grid g at the centre of texel (ix, iy) of the tex_res^2 texture (FP32)
 static void taps(const NeuralTex& N, int ix, int iy, int g, Tap t[4]) {
     float s = (float)N.res[g] / (float)N.tex_res;
-    float px = ((float)ix + 0.5f) * s; px = px - 0.5f;
-    float py = ((float)iy + 0.5f) * s; py = py - 0.5f;
+    float px = std::fmaf((float)ix + 0.5f, s, -0.5f);
+    float py = std::fmaf((float)iy + 0.5f, s, -0.5f);
     float fx = std::floor(px), fy = std::floor(py);
     float tx = px - fx, ty = py - fy, ux = 1.0f - tx, uy = 1.0f - ty;
     int x0 = wrapi((int)fx, N.res[g]), y0 = wrapi((int)fy, N.res[g]);
@@ -84,14 +84,15 @@ static void taps(const NeuralTex& N, int ix, int iy, int g, Tap t[4]) {
     t[2] = {x0, y1, ux * ty}; t[3] = {x1, y1, tx * ty};
 }
 
-// interpolated latent features, FP32 fixed order: ((w00 a + w10 b) + w01 c) + w11 d
+// interpolated latent features, FP32 fixed order with fused multiply-adds:
+// fma(w11, d, fma(w01, c, fma(w10, b, w00 a)))
 void features32(const NeuralTex& N, int ix, int iy, float f[32]) {
     for (int g = 0; g < 4; ++g) {
         Tap t[4];
         taps(N, ix, iy, g, t);
         for (int c = 0; c < 8; ++c) {
             float v = t[0].w * (float)N.latent(g, t[0].x, t[0].y, c);
-            for (int k = 1; k < 4; ++k) v = v + t[k].w * (float)N.latent(g, t[k].x, t[k].y, c);
+            for (int k = 1; k < 4; ++k) v = std::fmaf(t[k].w, (float)N.latent(g, t[k].x, t[k].y, c), v);
             f[8 * g + c] = v;
         }
     }

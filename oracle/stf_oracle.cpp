@@ -17,8 +17,9 @@
 //     positivization (Sec. 2.2 "Positivization").
 //
 // Precision.  Everything that *decides an integer* (which MIP level, which texel) is
-// evaluated in FP32 exactly as the paper's listings do (they are float code), with a
-// fixed operation order and no fused multiply-add.  Every *value* (filter weights used
+// evaluated in FP32 as the paper's listings do (they are float code), with a fixed
+// operation order; multiply-add chains use explicit single-rounded fmaf and nothing else
+// is contracted.  Every *value* (filter weights used
 // for sums, shading, transmittance, averages) is FP64.  For every decision the oracle
 // also takes the same decision from FP64 quantities and reports the distance of the
 // uniform to the nearest FP64 CDF boundary, so that tests can check that FP32 and FP64
@@ -149,9 +150,10 @@ int first_tap(int f) { return f == F_LINEAR ? 0 : -1; }   // offset of tap 0 fro
 bool signed_filter(int f) { return f == F_CATMULL_ROM || f == F_MITCHELL; }
 
 // ------------------------------------------------------------------ FP32 decision weights
-// Per-axis weights in float, written as the paper's listings compute them (the B-spline
-// polynomials of the bicubic/tricubic listings; the cubic kernels evaluated at the four
-// tap distances 1+t, t, 1-t, 2-t).  Used only to take decisions.
+// Per-axis weights in float (the B-spline polynomials of the paper's bicubic/tricubic
+// listings; the cubic kernels evaluated at the four tap distances 1+t, t, 1-t, 2-t), in
+// Horner form with fused multiply-adds -- the listings do not fix contraction, and a
+// single-rounded fmaf is reproducible on any IEEE machine.  Used only to take decisions.
 float k32_cubic(int f, float d) {
     float c3, c2, c0, q3, q2, q1, q0;
     if (f == F_CATMULL_ROM) {
@@ -160,8 +162,8 @@ float k32_cubic(int f, float d) {
         c3 = 7.0f / 6.0f; c2 = -2.0f; c0 = 8.0f / 9.0f;
         q3 = -7.0f / 18.0f; q2 = 2.0f; q1 = -10.0f / 3.0f; q0 = 16.0f / 9.0f;
     }
-    if (d < 1.0f) { float a = c3 * d; a = a + c2; a = a * d; a = a * d; return a + c0; }
-    if (d < 2.0f) { float a = q3 * d; a = a + q2; a = a * d; a = a + q1; a = a * d; return a + q0; }
+    if (d < 1.0f) { float a = std::fmaf(c3, d, c2); a = a * d; return std::fmaf(a, d, c0); }
+    if (d < 2.0f) { float a = std::fmaf(q3, d, q2); a = std::fmaf(a, d, q1); return std::fmaf(a, d, q0); }
     return 0.0f;
 }
 int weights32(int f, float t, float w[4]) {
@@ -170,10 +172,14 @@ int weights32(int f, float t, float w[4]) {
         const float s = 1.0f / 6.0f;
         float t2 = t * t, t3 = t * t2;
         float a;
-        a = -t3; a = a + 3.0f * t2; a = a - 3.0f * t; a = a + 1.0f; w[0] = s * a;
-        a = (3.0f * t) * t2; a = a - 6.0f * t2; a = a + 4.0f; w[1] = s * a;
-        a = (-3.0f * t) * t2; a = a + 3.0f * t2; a = a + 3.0f * t; a = a + 1.0f; w[2] = s * a;
-        w[3] = s * t3;
+        // the listing's polynomials in Horner form with fused multiply-adds:
+        //   (1-t)^3, t^2 (3t - 6) + 4, t (t (3 - 3t) + 3) + 1, t^3, each times 1/6
+        (void)t3;
+        float omt = 1.0f - t;
+        w[0] = s * ((omt * omt) * omt);
+        a = std::fmaf(3.0f, t, -6.0f); w[1] = s * std::fmaf(t2, a, 4.0f);
+        a = std::fmaf(-3.0f, t, 3.0f); a = std::fmaf(t, a, 3.0f); w[2] = s * std::fmaf(t, a, 1.0f);
+        w[3] = s * (t2 * t);
         return 4;
     }
     w[0] = k32_cubic(f, 1.0f + t); w[1] = k32_cubic(f, t);
@@ -332,8 +338,8 @@ void lod(const Tex& T, const Queries& Q, uint64_t q, float* lam32, double* lam64
     if (!Q.dudx || T.levels <= 1) { *lam32 = 0.0f; *lam64 = 0.0; return; }
     float W = (float)T.width[0], H = (float)T.height[0];
     float ax = Q.dudx[q] * W, ay = Q.dvdx[q] * H, bx = Q.dudy[q] * W, by = Q.dvdy[q] * H;
-    float la = ax * ax; la = la + ay * ay;
-    float lb = bx * bx; lb = lb + by * by;
+    float la = std::fmaf(ay, ay, ax * ax);
+    float lb = std::fmaf(by, by, bx * bx);
     float mn = la, mx = lb;
     if (mn > mx) { mn = lb; mx = la; }
     float minl = std::sqrt(mn), maxl = std::sqrt(mx);
@@ -362,8 +368,7 @@ struct Out {
 // per level: FP32 texel position and tap geometry on one axis
 struct Axis { int i0; float t; double pos; };
 Axis axis_at(float x, int res) {
-    float p = x * (float)res;
-    p = p - 0.5f;
+    float p = std::fmaf(x, (float)res, -0.5f);
     float fl = std::floor(p);
     return {(int)fl, p - fl, (double)p};
 }
@@ -416,10 +421,8 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 jx = a[0] - 0.5f;
                 jy = a[1] - 0.5f;
             }
-            float a = jx * Q.dudx[q], b = jy * Q.dudy[q];
-            x = x + a; x = x + b;
-            float c = jx * Q.dvdx[q], d = jy * Q.dvdy[q];
-            y = y + c; y = y + d;
+            x = std::fmaf(jy, Q.dudy[q], std::fmaf(jx, Q.dudx[q], x));
+            y = std::fmaf(jy, Q.dvdy[q], std::fmaf(jx, Q.dvdx[q], y));
         }
         uint32_t* pk = O.picks ? O.picks + (q * spp + s) * 2 : nullptr;
         uint32_t* pk64 = O.picks64 ? O.picks64 + (q * spp + s) * 2 : nullptr;
@@ -515,8 +518,8 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 float Px, Nx, Py, Ny;
                 pick32(wx, nt, 0.0f, +1, &Px); pick32(wx, nt, 0.0f, -1, &Nx);
                 pick32(wy, nt, 0.0f, +1, &Py); pick32(wy, nt, 0.0f, -1, &Ny);
-                float Wp = Px * Py; Wp = Wp + Nx * Ny;
-                float Wn = Px * Ny; Wn = Wn + Nx * Py;
+                float Wp = std::fmaf(Nx, Ny, Px * Py);
+                float Wn = std::fmaf(Nx, Py, Px * Ny);
                 double Px64 = 0, Nx64 = 0, Py64 = 0, Ny64 = 0;
                 for (int k = 0; k < nt; ++k) {
                     (wx64[k] > 0 ? Px64 : Nx64) += std::fabs(wx64[k]);
@@ -602,12 +605,12 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
         draw(seed, pix, s, 0, r);
         jx = unif(r[0]); jy = unif(r[1]);
     }
-    float sx = (float)px + jx; sx = sx * (2.0f / (float)W); sx = sx - 1.0f;
-    float sy = (float)py + jy; sy = sy * (2.0f / (float)H); sy = 1.0f - sy;
+    float sx = std::fmaf((float)px + jx, 2.0f / (float)W, -1.0f);
+    float sy = std::fmaf(-((float)py + jy), 2.0f / (float)H, 1.0f);
     const float *e = cam, *f = cam + 3, *r = cam + 6, *u = cam + 9;
     float d[3];
-    for (int a = 0; a < 3; ++a) { float t = sx * r[a]; t = f[a] + t; float t2 = sy * u[a]; d[a] = t + t2; }
-    float l2 = d[0] * d[0]; l2 = l2 + d[1] * d[1]; l2 = l2 + d[2] * d[2];
+    for (int a = 0; a < 3; ++a) d[a] = std::fmaf(sy, u[a], std::fmaf(sx, r[a], f[a]));
+    float l2 = std::fmaf(d[2], d[2], std::fmaf(d[1], d[1], d[0] * d[0]));
     float inv = 1.0f / std::sqrt(l2);
     for (int a = 0; a < 3; ++a) d[a] = d[a] * inv;
     float tmin = 0.0f, tmax = INFINITY;
@@ -631,10 +634,10 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
     double sig = (double)V.sigma_scale, dt64 = (double)dt;
     double sum_sigma = 0.0, prod = 1.0;
     for (uint32_t k = 0; k < steps; ++k) {
-        float tk = (float)k + 0.5f; tk = tk * dt; tk = tmin + tk;
+        float tk = std::fmaf((float)k + 0.5f, dt, tmin);
         Axis ax[3];
         for (int a = 0; a < 3; ++a) {
-            float p = tk * d[a]; p = e[a] + p;
+            float p = std::fmaf(tk, d[a], e[a]);
             ax[a] = axis_at(p, res[a]);
         }
         auto vox = [&](int ix, int iy, int iz) {

@@ -33,8 +33,8 @@ __device__ __forceinline__ float lod_aniso(float dudx, float dvdx, float dudy, f
                                            float W, float H, int levels) {
     const float ax = __fmul_rn(dudx, W), ay = __fmul_rn(dvdx, H);
     const float bx = __fmul_rn(dudy, W), by = __fmul_rn(dvdy, H);
-    const float la = __fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay));
-    const float lb = __fadd_rn(__fmul_rn(bx, bx), __fmul_rn(by, by));
+    const float la = __fmaf_rn(ay, ay, __fmul_rn(ax, ax));
+    const float lb = __fmaf_rn(by, by, __fmul_rn(bx, bx));
     float mn = la, mx = lb;
     if (mn > mx) { mn = lb; mx = la; }
     float minl = sqrtf(mn);
@@ -77,9 +77,10 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
         for (uint32_t s = 0; s < a.spp; ++s) {
             // stream 0: (jitter x, jitter y, level, pick x, pick y)
             U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            const uint32_t lshift = lat ? lattice_shift(s, a.spp, 24) : 0u;
             if (lat) {
 #pragma unroll
-                for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], s, a.spp, 24);
+                for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
             }
             float x = u, y = v;
             if (a.has_derivs) {
@@ -91,8 +92,8 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                     jx = __fsub_rn(A.u[0], 0.5f);
                     jy = __fsub_rn(A.u[1], 0.5f);
                 }
-                x = __fadd_rn(__fadd_rn(x, __fmul_rn(jx, dudx)), __fmul_rn(jy, dudy));
-                y = __fadd_rn(__fadd_rn(y, __fmul_rn(jx, dvdx)), __fmul_rn(jy, dvdy));
+                x = __fmaf_rn(jy, dudy, __fmaf_rn(jx, dudx, x));
+                y = __fmaf_rn(jy, dvdy, __fmaf_rn(jx, dvdx, y));
             }
             float3 est;
             if (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) {
@@ -132,13 +133,13 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                     float Px, Nx, Py, Ny;
                     cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
                     cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
-                    const float Wp = __fadd_rn(__fmul_rn(Px, Py), __fmul_rn(Nx, Ny));
-                    const float Wn = __fadd_rn(__fmul_rn(Px, Ny), __fmul_rn(Nx, Py));
+                    const float Wp = __fmaf_rn(Nx, Ny, __fmul_rn(Px, Py));
+                    const float Wn = __fmaf_rn(Nx, Py, __fmul_rn(Px, Ny));
                     // stream 1: (positive class, negative pick x, negative pick y, negative class)
                     U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
                     if (lat) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], s, a.spp, 24);
+                        for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], lshift, 24);
                     }
                     const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
                     const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);

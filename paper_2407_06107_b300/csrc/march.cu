@@ -40,15 +40,15 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                 const uint4 r = philox(id_lo, id_hi, s, 0u, K);
                 jx = unif(r.x); jy = unif(r.y);
             }
-            float sx = __fsub_rn(__fmul_rn(__fadd_rn((float)px, jx), __fdiv_rn(2.0f, (float)a.width)), 1.0f);
-            float sy = __fsub_rn(1.0f, __fmul_rn(__fadd_rn((float)py, jy), __fdiv_rn(2.0f, (float)a.height)));
+            const float sx = __fmaf_rn(__fadd_rn((float)px, jx), __fdiv_rn(2.0f, (float)a.width), -1.0f);
+            const float sy = __fmaf_rn(-__fadd_rn((float)py, jy), __fdiv_rn(2.0f, (float)a.height), 1.0f);
             float d[3], e[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 e[c] = a.cam[c];
-                d[c] = __fadd_rn(__fadd_rn(a.cam[3 + c], __fmul_rn(sx, a.cam[6 + c])), __fmul_rn(sy, a.cam[9 + c]));
+                d[c] = __fmaf_rn(sy, a.cam[9 + c], __fmaf_rn(sx, a.cam[6 + c], a.cam[3 + c]));
             }
-            const float l2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+            const float l2 = __fmaf_rn(d[2], d[2], __fmaf_rn(d[1], d[1], __fmul_rn(d[0], d[0])));
             const float inv = __fdiv_rn(1.0f, __fsqrt_rn(l2));
 #pragma unroll
             for (int c = 0; c < 3; ++c) d[c] = __fmul_rn(d[c], inv);
@@ -75,11 +75,12 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
             float P = 1.0f, Pe = 0.0f;              // after: compensated product
             const float sdt = a.sigma_scale * dt;
             uint4 rw = make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t lshift = (a.flags & FLAG_LATTICE) ? lattice_shift(s, a.spp, 21) : 0u;
             for (uint32_t k = 0; k < a.steps; ++k) {
-                const float tk = __fadd_rn(tmin, __fmul_rn(__fadd_rn((float)k, 0.5f), dt));
+                const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
                 AxisPos ap[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ap[c] = axis_pos(__fadd_rn(e[c], __fmul_rn(tk, d[c])), res[c]);
+                for (int c = 0; c < 3; ++c) ap[c] = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
                 float w[3][4];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) axis_weights<FILTER>(ap[c].t, w[c]);
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                         uint32_t f[3];
                         ints3_of6(rw, (int)(k & 1u), f);
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) uk[c] = lattice(f[c], s, a.spp, 21);
+                        for (int c = 0; c < 3; ++c) uk[c] = lattice(f[c], lshift, 21);
                     } else {
                         if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
                         uniforms3_of6(rw, (int)(k & 1u), uk);

@@ -102,8 +102,8 @@ __host__ __device__ constexpr uint32_t kmaj_off(uint32_t row, uint32_t k, uint32
 struct LTap { int x0, y0, x1, y1; float w00, w10, w01, w11; };
 __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, int iy) {
     const float s = __fdiv_rn((float)N.res[g], (float)N.tex_res);
-    const float px = __fsub_rn(__fmul_rn(__fadd_rn((float)ix, 0.5f), s), 0.5f);
-    const float py = __fsub_rn(__fmul_rn(__fadd_rn((float)iy, 0.5f), s), 0.5f);
+    const float px = __fmaf_rn(__fadd_rn((float)ix, 0.5f), s, -0.5f);
+    const float py = __fmaf_rn(__fadd_rn((float)iy, 0.5f), s, -0.5f);
     const float fx = floorf(px), fy = floorf(py);
     const float tx = __fsub_rn(px, fx), ty = __fsub_rn(py, fy);
     const float ux = __fsub_rn(1.0f, tx), uy = __fsub_rn(1.0f, ty);
@@ -151,9 +151,9 @@ __device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, i
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             float v = __fmul_rn(t.w00, a[k]);
-            v = __fadd_rn(v, __fmul_rn(t.w10, b[k]));
-            v = __fadd_rn(v, __fmul_rn(t.w01, c[k]));
-            v = __fadd_rn(v, __fmul_rn(t.w11, d[k]));
+            v = __fmaf_rn(t.w10, b[k], v);
+            v = __fmaf_rn(t.w01, c[k], v);
+            v = __fmaf_rn(t.w11, d[k], v);
             f[8 * g + k] = v;
         }
     }
@@ -425,8 +425,8 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     float x = a.u[q], y = a.v[q];
     if (a.has_derivs) {
         const float jx = __fsub_rn(A.u[0], 0.5f), jy = __fsub_rn(A.u[1], 0.5f);
-        x = __fadd_rn(__fadd_rn(x, __fmul_rn(jx, a.dudx[q])), __fmul_rn(jy, a.dudy[q]));
-        y = __fadd_rn(__fadd_rn(y, __fmul_rn(jx, a.dvdx[q])), __fmul_rn(jy, a.dvdy[q]));
+        x = __fmaf_rn(jy, a.dudy[q], __fmaf_rn(jx, a.dudx[q], x));
+        y = __fmaf_rn(jy, a.dvdy[q], __fmaf_rn(jx, a.dvdx[q], y));
     }
     const int R = a.tex_res;
     const AxisPos ax = axis_pos(x, (float)R), ay = axis_pos(y, (float)R);
@@ -450,8 +450,8 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
         float Px, Nx, Py, Ny;
         cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
         cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
-        const float Wp = __fadd_rn(__fmul_rn(Px, Py), __fmul_rn(Nx, Ny));
-        const float Wn = __fadd_rn(__fmul_rn(Px, Ny), __fmul_rn(Nx, Py));
+        const float Wp = __fmaf_rn(Nx, Ny, __fmul_rn(Px, Py));
+        const float Wn = __fmaf_rn(Nx, Py, __fmul_rn(Px, Ny));
         const U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
         if (j == 0) {
             const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;

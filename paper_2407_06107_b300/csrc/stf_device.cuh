@@ -1,8 +1,9 @@
 // Device-side building blocks of stochastic texture filtering (sm_103a).
 //
-// Decision arithmetic (positions, weights, CDFs) uses __fmul_rn / __fadd_rn so that the
-// compiler cannot contract it into FMAs: the selected texel is then a deterministic
-// function of the FP32 inputs, the precision of the paper's float listings.  Value
+// Decision arithmetic (positions, weights, CDFs) spells every rounding out with
+// __fmul_rn / __fadd_rn / __fmaf_rn, so the compiler can neither contract nor reorder it:
+// the selected texel is then a deterministic function of the FP32 inputs (the precision
+// of the paper's float listings), reproduced by the CPU oracle with fmaf.  Value
 // arithmetic (shading, sums) is free to use FMA.
 #pragma once
 #include <cstdint>
@@ -64,8 +65,10 @@ __device__ __forceinline__ U5 uniforms5(uint4 w) {
 // Randomly shifted lattice across the spp samples of one query (FLAG_LATTICE): sample s
 // takes frac(s/spp + phi) with a per-query offset phi, in exact integer arithmetic on the
 // 2^bits grid.
-__device__ __forceinline__ float lattice(uint32_t phi, uint32_t s, uint32_t spp, int bits) {
-    const uint32_t shift = (uint32_t)(((uint64_t)s << bits) / spp);
+__device__ __forceinline__ uint32_t lattice_shift(uint32_t s, uint32_t spp, int bits) {
+    return (uint32_t)(((uint64_t)s << bits) / spp);          // floor(s 2^bits / spp), once per sample
+}
+__device__ __forceinline__ float lattice(uint32_t phi, uint32_t shift, int bits) {
     return __uint2float_rn((phi + shift) & ((1u << bits) - 1u)) * __int_as_float((127 - bits) << 23);
 }
 // integer numerators of uniforms5
@@ -102,7 +105,8 @@ __device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
 // ---------------------------------------------------------------- FP32 decision weights
 // Per-axis weights for the taps at distances 1+t, t, 1-t, 2-t (cubic) or 1-t, t
 // (linear).  The B-spline uses the polynomials of the paper's bicubic listing; the cubic
-// kernels (Keys a=-1/2, Mitchell-Netravali BC(1/3,1/3)) are evaluated in Horner form.
+// kernels (Keys a=-1/2, Mitchell-Netravali BC(1/3,1/3)) are evaluated in Horner form;
+// multiply-add chains are explicit single-rounded FMAs (__fmaf_rn), nothing else fuses.
 template <int F>
 __device__ __forceinline__ float k_cubic(float d) {
     float c3, c2, c0, q3, q2, q1, q0;
@@ -113,19 +117,13 @@ __device__ __forceinline__ float k_cubic(float d) {
         q3 = -7.0f / 18.0f; q2 = 2.0f; q1 = -10.0f / 3.0f; q0 = 16.0f / 9.0f;
     }
     if (d < 1.0f) {
-        float a = __fmul_rn(c3, d);
-        a = __fadd_rn(a, c2);
-        a = __fmul_rn(a, d);
-        a = __fmul_rn(a, d);
-        return __fadd_rn(a, c0);
+        const float a = __fmul_rn(__fmaf_rn(c3, d, c2), d);
+        return __fmaf_rn(a, d, c0);
     }
     if (d < 2.0f) {
-        float a = __fmul_rn(q3, d);
-        a = __fadd_rn(a, q2);
-        a = __fmul_rn(a, d);
-        a = __fadd_rn(a, q1);
-        a = __fmul_rn(a, d);
-        return __fadd_rn(a, q0);
+        float a = __fmaf_rn(q3, d, q2);
+        a = __fmaf_rn(a, d, q1);
+        return __fmaf_rn(a, d, q0);
     }
     return 0.0f;
 }
@@ -136,23 +134,15 @@ __device__ __forceinline__ void axis_weights(float t, float w[4]) {
         w[0] = __fsub_rn(1.0f, t);
         w[1] = t;
     } else if (F == F_BSPLINE) {
+        // the listing's polynomials in Horner form with fused multiply-adds:
+        //   (1-t)^3, t^2 (3t - 6) + 4, t (t (3 - 3t) + 3) + 1, t^3, each times 1/6
         const float s = 1.0f / 6.0f;
-        const float t2 = __fmul_rn(t, t), t3 = __fmul_rn(t, t2);
-        float a = -t3;
-        a = __fadd_rn(a, __fmul_rn(3.0f, t2));
-        a = __fsub_rn(a, __fmul_rn(3.0f, t));
-        a = __fadd_rn(a, 1.0f);
-        w[0] = __fmul_rn(s, a);
-        a = __fmul_rn(__fmul_rn(3.0f, t), t2);
-        a = __fsub_rn(a, __fmul_rn(6.0f, t2));
-        a = __fadd_rn(a, 4.0f);
-        w[1] = __fmul_rn(s, a);
-        a = __fmul_rn(__fmul_rn(-3.0f, t), t2);
-        a = __fadd_rn(a, __fmul_rn(3.0f, t2));
-        a = __fadd_rn(a, __fmul_rn(3.0f, t));
-        a = __fadd_rn(a, 1.0f);
-        w[2] = __fmul_rn(s, a);
-        w[3] = __fmul_rn(s, t3);
+        const float t2 = __fmul_rn(t, t);
+        const float omt = __fsub_rn(1.0f, t);
+        w[0] = __fmul_rn(s, __fmul_rn(__fmul_rn(omt, omt), omt));
+        w[1] = __fmul_rn(s, __fmaf_rn(t2, __fmaf_rn(3.0f, t, -6.0f), 4.0f));
+        w[2] = __fmul_rn(s, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-3.0f, t, 3.0f), 3.0f), 1.0f));
+        w[3] = __fmul_rn(s, __fmul_rn(t2, t));
     } else {
         w[0] = k_cubic<F>(__fadd_rn(1.0f, t));
         w[1] = k_cubic<F>(t);
@@ -184,7 +174,7 @@ __device__ __forceinline__ int cdf_pick(const float w[4], float xi, int cls, flo
 // raster position on one axis: p = x*res - 1/2, i0 = floor(p), t = p - i0 (FP32)
 struct AxisPos { int i0; float t; };
 __device__ __forceinline__ AxisPos axis_pos(float x, float res) {
-    float p = __fsub_rn(__fmul_rn(x, res), 0.5f);
+    float p = __fmaf_rn(x, res, -0.5f);
     float fl = floorf(p);
     return {(int)fl, __fsub_rn(p, fl)};
 }
