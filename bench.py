@@ -38,6 +38,10 @@ SPP = 8
 FILTERS = ("linear", "bspline", "mitchell")
 METRIC = "shaded texture lookups/s, stochastic 1-tap vs N-tap, at equal RMSE vs FP64"
 LATTICE = 2                       # STF_FLAG_LATTICE
+# algorithmic ALU operations per stochastic lookup (8 spp; per-query work amortised), counted
+# step by step in the design notes: Philox-10 (40), 5 uniforms (19), jitter (6), level (3),
+# two axes of position + weights + CDF, sign/weight, addressing, decode (30), GGX (80), accumulate
+ALG_OPS = {"linear": 220, "bspline": 262, "mitchell": 274}
 SPP_GRID = (1, 2, 4, 6, 8, 9, 10, 11, 12, 14, 16, 20, 24, 32, 48, 64)
 
 
@@ -207,17 +211,20 @@ def run_ours(args):
     e2e = {"value": world * units_step / e2e_s, "unit": "lookups/s",
            "h2d_bytes_per_step": len(FILTERS) * nq * 24, "d2h_bytes_per_step": len(FILTERS) * nq * 12}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (issue/ALU-bound: see the design notes)
     mean = per.mean(0)
     dom = int(np.argmax(mean))
-    pk = peaks()
     units_launch = nq * SPP
-    alg_bytes = units_launch * 8 + nq * (24 + 12)    # one 8-B texel per lookup + query in / rgb out
-    achieved = alg_bytes / (mean[dom] / 1e3) / 1e9
-    traffic = load_traffic(FILTERS[dom], "stochastic")
-    roof = {"kernel": f"k_filter_shade<{FILTERS[dom]}, stochastic>", "bound": "hbm", "achieved": achieved,
-            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"],
-            "traffic": traffic, "ms_per_launch": float(mean[dom])}
+    ops = ALG_OPS[FILTERS[dom]]
+    achieved = ops * units_launch / (mean[dom] / 1e3) / 1e12
+    peak = alu_peak_tops()
+    traffic = load_traffic(f"k_filter_shade<{FILTERS[dom]},stochastic>", nq)
+    roof = {"kernel": f"k_filter_shade<{FILTERS[dom]}, stochastic>", "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "Tops/s", "frac": achieved / peak, "peak_src":
+            "148 SMs x 128 INT32/FP32 lanes x 2032 MHz (recipe unit counts and max SM clock)",
+            "alg_ops_per_lookup": ops, "traffic": traffic, "ms_per_launch": float(mean[dom]),
+            "alg_bytes_per_launch": units_launch * 8 + nq * (24 + 12),
+            "hbm_frac_of_measured": (units_launch * 8 + nq * 36) / (mean[dom] / 1e3) / 1e9 / peaks()["hbm_gbs"]}
 
     line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -242,14 +249,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def load_traffic(filter_name: str, mode: str):
-    """dram bytes per launch from the committed ncu summary, if it covers this kernel."""
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_06107_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str, nq: int):
+    """DRAM bytes per launch (dram__bytes_read + write) of `kernel` from the committed ncu
+    summary, scaled from its capture size to nq queries; None when the kernel sources
+    changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    return d.get(f"{filter_name}/{mode}")
+    if d.get("csrc_hash") != kernel_source_hash() or kernel not in d.get("kernels", {}):
+        return None
+    k = d["kernels"][kernel]
+    return k["dram_bytes"] * nq / k["queries"]
+
+
+def alu_peak_tops() -> float:
+    return 148 * 128 * 2.032e9 / 1e12
 
 
 def _time_launch(fn, reps=3):
@@ -294,6 +320,9 @@ def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
         outf = [torch.empty(nfull, dtype=torch.float32, device=dev) for _ in range(3)]
         t_before = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "ntap_before", "ggx", 8, 1, 0, out=outf))
         t_s8 = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", 8, 1, 0, out=outf))
+        order = ctx.bin_queries(u, v, tile_log2=6)
+        t_s8b = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", 8, 1, 0, out=outf,
+                                                      order=order))
         t_star = (_time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", s_star, 1, 0, out=outf))
                   if s_star else None)
         t_lat = (_time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", s_lat, 1, LATTICE, out=outf))
@@ -303,6 +332,7 @@ def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
             "rmse_stochastic": {str(k): v for k, v in curve.items()},
             "mse_increase_stochastic_vs_after_8spp": curve[8] ** 2 / r_after ** 2 - 1.0,
             "ntap_taps": 32, "ms_ntap_before_8spp": t_before, "ms_stochastic_8spp": t_s8,
+            "ms_stochastic_8spp_binned": t_s8b,
             "ntap_before_lookups_per_s": nfull * 8 / (t_before / 1e3),
             "stochastic_lookups_per_s": nfull * 8 / (t_s8 / 1e3),
             "equal_spp_speedup": t_before / t_s8, "s_star": s_star,
@@ -442,11 +472,17 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
     tid = torch.from_numpy(rng.integers(0, ntex, nq).astype(np.int32)).to(dev)
     out = [torch.empty(nq, dtype=torch.float32, device=dev) for _ in range(3)]
     res = {"textures": ntex, "texel_bytes": tbytes, "queries": nq, "spp": 4}
+    order = torch.empty(nq, dtype=torch.int32, device=dev)
+    ms_bin = _time_launch(lambda: ctx.bin_queries(u, v, tid, ntex=ntex, tile_log2=6, order=order), 2)
     for mode in ("stochastic", "positivized"):
         ms = _time_launch(lambda: ctx.filter_shade_table(table, u, v, tid, None, "mitchell", mode, "ggx", 4, 1,
                                                          out=out), 2)
+        msb = _time_launch(lambda: ctx.filter_shade_table(table, u, v, tid, None, "mitchell", mode, "ggx", 4, 1,
+                                                          out=out, order=order), 2)
         res[mode] = {"ms": ms, "lookups_per_s": nq * 4 / (ms / 1e3),
-                     "texel_fetches_per_lookup": 1 if mode == "stochastic" else 2}
+                     "texel_fetches_per_lookup": 1 if mode == "stochastic" else 2,
+                     "binned_ms": msb, "binned_lookups_per_s": nq * 4 / (msb / 1e3)}
+    res["bin_ms"] = ms_bin
     ctx.destroy_texture_table(table)
     for h in handles:
         ctx.destroy_texture(h)

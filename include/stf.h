@@ -108,6 +108,9 @@ typedef struct {
     uint64_t id_base;    /* Philox id of query 0                                            */
     const float* u;      /* [n] texture coordinates, any real value (wrapped / clamped)     */
     const float* v;      /* [n]                                                             */
+    const uint32_t* order;  /* nullable: [n] permutation; thread i evaluates query order[i]
+                            (e.g. from stf_bin_queries, for gather locality).  Results land in
+                            each query's own slot and are identical with or without it.    */
 } stf_queries;
 
 typedef struct {         /* screen-space derivatives of (u, v), [n] each                    */
@@ -170,6 +173,14 @@ stf_status stf_destroy_texture_table(stf_ctx ctx, stf_table table);
 stf_status stf_filter_shade_table(stf_ctx ctx, stf_table table, const stf_queries* q, const uint32_t* tex_id,
                                   const stf_derivs* d, stf_filter filter, stf_mode mode, stf_shade shade,
                                   uint32_t spp, uint64_t seed, uint32_t flags, const stf_output* out);
+
+/* ---- pick binning: spatial ordering of queries for gather locality -------------------- */
+/* Counting sort of the n queries by bin = (tex_id[i], tile of (frac(u), frac(v)) on a
+ * 2^tile_log2 x 2^tile_log2 grid): order_out[n] (device uint32) lists the queries bin by
+ * bin.  tex_id nullable (one texture); ntex = number of texture ids (1 if tex_id is NULL);
+ * ntex * 4^tile_log2 <= 2^26, n < 2^32.  Uses context-owned scratch for the histogram. */
+stf_status stf_bin_queries(stf_ctx ctx, uint64_t n, const float* u, const float* v, const uint32_t* tex_id,
+                           uint32_t ntex, uint32_t tile_log2, uint32_t* order_out);
 
 /* Same computation as stf_filter_shade_host, for callers that must not allocate device
  * memory while they look up textures (a frame loop with a fixed memory budget, or a

@@ -41,7 +41,8 @@ class _TextureDesc(C.Structure):
 
 
 class _Queries(C.Structure):
-    _fields_ = [("n", C.c_uint64), ("id_base", C.c_uint64), ("u", C.c_void_p), ("v", C.c_void_p)]
+    _fields_ = [("n", C.c_uint64), ("id_base", C.c_uint64), ("u", C.c_void_p), ("v", C.c_void_p),
+                ("order", C.c_void_p)]
 
 
 class _Derivs(C.Structure):
@@ -82,6 +83,7 @@ SIGNATURES = {
                           _U32, C.POINTER(_Output)], _I),
     "stf_filter_shade_host": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                _U64, _U32, C.POINTER(_Output)], _I),
+    "stf_bin_queries": ([_P, _U64, _P, _P, _P, _U32, _U32, _P], _I),
     "stf_create_texture_table": ([_P, _U32, _P, C.POINTER(_U64)], _I),
     "stf_destroy_texture_table": ([_P, _U64], _I),
     "stf_filter_shade_table": ([_P, _U64, C.POINTER(_Queries), _P, C.POINTER(_Derivs), _I, _I, _I, _U32, _U64, _U32,
@@ -212,8 +214,8 @@ class Context:
         self._check(lib().stf_destroy_volume(self.h, vol), self.h)
 
     # -------------------------------------------------------------- hot path
-    def _args(self, u, v, derivs, out, picks, n, id_base):
-        q = _Queries(n, id_base, _ptr(u), _ptr(v))
+    def _args(self, u, v, derivs, out, picks, n, id_base, order=None):
+        q = _Queries(n, id_base, _ptr(u), _ptr(v), _ptr(order))
         d = None
         if derivs is not None:
             d = _Derivs(*[_ptr(x) for x in derivs])
@@ -222,14 +224,15 @@ class Context:
 
     def filter_shade(self, tex: int, u, v, derivs=None, filter: str = "bspline", mode: str = "stochastic",
                      shade: str = "ggx", spp: int = 1, seed: int = 1, flags: int = 0, id_base: int = 0,
-                     out=None, want_picks: bool = False):
-        """u, v, derivs (dudx, dvdx, dudy, dvdy): float32 cuda tensors.  Returns (r, g, b, picks)."""
+                     out=None, want_picks: bool = False, order=None):
+        """u, v, derivs (dudx, dvdx, dudy, dvdy): float32 cuda tensors; order: optional int32
+        cuda permutation (execution order).  Returns (r, g, b, picks)."""
         torch = self.torch
         n = int(u.shape[0])
         if out is None:
             out = [torch.empty(n, dtype=torch.float32, device=u.device) for _ in range(3)]
         picks = torch.empty((n, spp, 2), dtype=torch.int32, device=u.device) if want_picks else None
-        q, d, o = self._args(u, v, derivs, out, picks, n, id_base)
+        q, d, o = self._args(u, v, derivs, out, picks, n, id_base, order)
         st = lib().stf_filter_shade(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
                                     FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
         self._check(st, self.h)
@@ -249,6 +252,15 @@ class Context:
         self._check(st, self.h)
         return out[0], out[1], out[2], picks
 
+    def bin_queries(self, u, v, tex_id=None, ntex: int = 1, tile_log2: int = 6, order=None):
+        """Spatial execution order (int32 cuda tensor [n]) for filter_shade(order=...)."""
+        n = int(u.shape[0])
+        if order is None:
+            order = self.torch.empty(n, dtype=self.torch.int32, device=u.device)
+        self._check(lib().stf_bin_queries(self.h, n, _ptr(u), _ptr(v), _ptr(tex_id), ntex, tile_log2, _ptr(order)),
+                    self.h)
+        return order
+
     def create_texture_table(self, textures) -> int:
         arr = (C.c_uint64 * len(textures))(*textures)
         out = C.c_uint64(0)
@@ -260,14 +272,14 @@ class Context:
 
     def filter_shade_table(self, table: int, u, v, tex_id, derivs=None, filter: str = "mitchell",
                            mode: str = "stochastic", shade: str = "ggx", spp: int = 1, seed: int = 1,
-                           flags: int = 0, id_base: int = 0, out=None, want_picks: bool = False):
-        """tex_id: int32/uint32 cuda tensor [n] of table entries."""
+                           flags: int = 0, id_base: int = 0, out=None, want_picks: bool = False, order=None):
+        """tex_id: int32/uint32 cuda tensor [n] of table entries; order: optional permutation."""
         torch = self.torch
         n = int(u.shape[0])
         if out is None:
             out = [torch.empty(n, dtype=torch.float32, device=u.device) for _ in range(3)]
         picks = torch.empty((n, spp, 2), dtype=torch.int32, device=u.device) if want_picks else None
-        q, d, o = self._args(u, v, derivs, out, picks, n, id_base)
+        q, d, o = self._args(u, v, derivs, out, picks, n, id_base, order)
         st = lib().stf_filter_shade_table(self.h, table, C.byref(q), C.c_void_p(_ptr(tex_id)),
                                           C.byref(d) if d is not None else None, FILTERS[filter], MODES[mode],
                                           SHADES[shade], spp, seed, flags, C.byref(o))

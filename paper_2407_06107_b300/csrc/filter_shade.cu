@@ -238,9 +238,9 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
 template <int FILTER, int MODE>
 __global__ void __launch_bounds__(256)
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n;
-         q += (uint64_t)gridDim.x * blockDim.x)
-        query_body<FILTER, MODE>(a, T, SC, K, q);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        query_body<FILTER, MODE>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
 }
 
 // Bindless persistent launch: one grid sized to the SMs; each block claims the next
@@ -258,8 +258,9 @@ k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint
         const unsigned long long base = chunk;
         __syncthreads();
         if (base >= a.n) break;
-        const uint64_t q = base + threadIdx.x;
-        if (q < a.n) {
+        const uint64_t i = base + threadIdx.x;
+        if (i < a.n) {
+            const uint64_t q = a.order ? (uint64_t)__ldg(a.order + i) : i;
             const uint32_t t = __ldg(tex_id + q);
             if (t < ntex) {
                 query_body<FILTER, MODE>(a, table[t], SC, K, q);

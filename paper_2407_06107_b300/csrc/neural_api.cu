@@ -322,6 +322,7 @@ stf_status stf_neural_filter_shade(stf_ctx c, stf_neural h, const stf_queries* q
     if (flags != 0) return fail(c, STF_ERR_INVALID_ARG, "flags must be 0");
     if (q->n == 0) return STF_OK;
     if (!q->u || !q->v || !out->r || !out->g || !out->b) return fail(c, STF_ERR_INVALID_ARG, "null query/output pointer");
+    if (q->order) return fail(c, STF_ERR_UNSUPPORTED, "the neural path takes no execution order");
     if (d && (!d->dudx || !d->dvdx || !d->dudy || !d->dvdy)) return fail(c, STF_ERR_INVALID_ARG, "null derivative pointer");
     const int nt = f == STF_FILTER_LINEAR ? 2 : 4;
     const uint64_t nr = m == STF_MODE_STOCHASTIC ? 1 : (m == STF_MODE_STOCHASTIC_POSITIVIZED ? 2 : (uint64_t)nt * nt);

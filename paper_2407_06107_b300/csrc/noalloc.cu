@@ -74,6 +74,7 @@ extern "C" stf_status stf_filter_shade_host_noalloc(stf_ctx c, stf_tex t, const 
         return stfi::fail(c, STF_ERR_INVALID_ARG,
                           "stf_filter_shade_host_noalloc: at most 262144 queries per call (split larger batches)");
     if (q->n == 0) return STF_OK;
+    if (q->order) return stfi::fail(c, STF_ERR_UNSUPPORTED, "the host-buffer entry points take no execution order");
     const void* ptrs[5] = {q->u, q->v, out->r, out->g, out->b};
     for (const void* p : ptrs)
         if (!p || !aligned4(p)) return stfi::fail(c, STF_ERR_INVALID_ARG, "query/output pointers must be non-null and 4-byte aligned");

@@ -266,7 +266,7 @@ static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries
                                  uint32_t flags, const stf_output* out) {
     if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
     stf::FilterShadeArgs a{};
-    a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v;
+    a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v; a.order = q->order;
     a.has_derivs = d ? 1 : 0;
     if (d) { a.dudx = d->dudx; a.dvdx = d->dvdx; a.dudy = d->dudy; a.dvdy = d->dvdy; }
     a.filter = f; a.mode = m; a.shade = sh; a.spp = spp; a.flags = flags;
@@ -309,7 +309,8 @@ stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, con
         e = cudaMemcpyAsync(dv[i], hv[i], n * 4, cudaMemcpyHostToDevice, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "host->device copy");
-    stf_queries dq{n, q->id_base, dv[0], dv[1]};
+    if (q->order) return fail(c, STF_ERR_UNSUPPORTED, "the host-buffer entry point takes no execution order");
+    stf_queries dq{n, q->id_base, dv[0], dv[1], nullptr};
     stf_derivs dd{};
     if (d) dd = stf_derivs{dv[2], dv[3], dv[4], dv[5]};
     stf_output dout{(float*)(base + fb * nin), (float*)(base + fb * (nin + 1)), (float*)(base + fb * (nin + 2)),
@@ -379,7 +380,7 @@ stf_status stf_filter_shade_table(stf_ctx c, stf_table t, const stf_queries* q, 
     if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
     CurrentDevice cd(c->device);
     stf::FilterShadeArgs a{};
-    a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v;
+    a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v; a.order = q->order;
     a.has_derivs = d ? 1 : 0;
     if (d) { a.dudx = d->dudx; a.dvdx = d->dvdx; a.dudy = d->dudy; a.dvdy = d->dvdy; }
     a.filter = f; a.mode = m; a.shade = sh; a.spp = spp; a.flags = flags;
@@ -391,6 +392,28 @@ stf_status stf_filter_shade_table(stf_ctx c, stf_table t, const stf_queries* q, 
         e = stf::launch_filter_shade_table(a, (const stf::FetchCtx*)it->second.mem, it->second.n, tex_id,
                                            it->second.counter, c->num_sms, c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "filter_shade_table launch");
+}
+
+// ----------------------------------------------------------------------------- binning
+stf_status stf_bin_queries(stf_ctx c, uint64_t n, const float* u, const float* v, const uint32_t* tex_id,
+                           uint32_t ntex, uint32_t tile_log2, uint32_t* order_out) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    if (n == 0) return STF_OK;
+    if (!u || !v || !order_out || !aligned4(u) || !aligned4(v) || !aligned4(order_out))
+        return fail(c, STF_ERR_INVALID_ARG, "u, v and order must be non-null and 4-byte aligned");
+    if (n >= (1ull << 32)) return fail(c, STF_ERR_INVALID_ARG, "at most 2^32 - 1 queries");
+    if (!tex_id) ntex = 1;
+    if (ntex < 1 || tile_log2 > 12 || (uint64_t)ntex << (2 * tile_log2) > (1ull << 26))
+        return fail(c, STF_ERR_INVALID_ARG, "ntex * 4^tile_log2 must be in 1..2^26");
+    if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
+    CurrentDevice cd(c->device);
+    const uint64_t nbins = (uint64_t)ntex << (2 * tile_log2);
+    const uint64_t nblk = (nbins + 1023) / 1024;
+    stf_status s = ensure_stage(c, (nblk * 1024 + nblk) * 4);
+    if (s != STF_OK) return s;
+    cudaError_t e = stf::launch_bin_queries(n, u, v, tex_id, ntex, tile_log2, order_out, (uint32_t*)c->stage, nbins,
+                                            c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "bin launch");
 }
 
 // --------------------------------------------------------------------------------- volume

@@ -27,6 +27,7 @@ struct FetchCtx {
 
 struct FilterShadeArgs {
     uint64_t n, id_base;
+    const uint32_t* order;    // nullable execution order
     const float *u, *v, *dudx, *dvdx, *dudy, *dvdy;
     int has_derivs;
     int filter, mode, shade;
@@ -103,6 +104,9 @@ cudaError_t launch_filter_shade_table(const FilterShadeArgs& a, const FetchCtx* 
                                       const uint32_t* tex_id, unsigned long long* counter, int num_sms,
                                       cudaStream_t st);
 cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_bin_queries(uint64_t n, const float* u, const float* v, const uint32_t* tex_id, uint32_t ntex,
+                               uint32_t tile_log2, uint32_t* order, uint32_t* scratch, uint64_t nbins,
+                               cudaStream_t st);
 cudaError_t launch_pack_rgba8(const void* rgba, const void* rg, void* out, uint64_t n, cudaStream_t st);
 
 }  // namespace stf

@@ -212,3 +212,21 @@ def test_lattice_sampler(ctx, material, filter, mode):
     import oracle as _o
     h, otex, q = material
     _check(ctx, h, otex, q, filter, mode, spp=6, seed=13, flags=_o.FLAG_LATTICE)
+
+
+def test_binned_order_is_permutation_and_results_identical(ctx, material):
+    h, _, q = material
+    u, v, d = _dev(q)
+    order = ctx.bin_queries(u, v, tile_log2=4)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(q.n))
+    # queries appear grouped by tile: tile index is non-decreasing along the order
+    fu = np.mod(q.u.astype(np.float64), 1.0)
+    fv = np.mod(q.v.astype(np.float64), 1.0)
+    tile = (np.minimum((fv * 16).astype(int), 15) << 4) | np.minimum((fu * 16).astype(int), 15)
+    assert np.all(np.diff(tile[o]) >= 0)
+    for f, mode in (("bspline", "stochastic"), ("mitchell", "positivized"), ("linear", "ntap_before")):
+        a = ctx.filter_shade(h, u, v, d, f, mode, "ggx", 3, 4, want_picks=True)
+        b = ctx.filter_shade(h, u, v, d, f, mode, "ggx", 3, 4, want_picks=True, order=order)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)

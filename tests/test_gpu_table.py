@@ -83,3 +83,25 @@ def test_bad_texture_id_and_lifetime(ctx):
     ctx.destroy_texture_table(table)
     for h in hs:
         ctx.destroy_texture(h)
+
+
+def test_binned_table_identical(ctx):
+    texs = synth.texture_table_rgba8(12, 20, 200, seed=109, fbm_below=300)
+    hs = [ctx.create_texture([t]) for t in texs]
+    table = ctx.create_texture_table(hs)
+    n = 30000
+    rng = np.random.default_rng(3)
+    u = torch.rand(n, device="cuda")
+    v = torch.rand(n, device="cuda")
+    tid = torch.from_numpy(rng.integers(0, 12, n).astype(np.int32)).cuda()
+    order = ctx.bin_queries(u, v, tid, ntex=12, tile_log2=3)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(n))
+    assert np.all(np.diff(tid.cpu().numpy()[o]) >= 0)          # texture id is the major key
+    a = ctx.filter_shade_table(table, u, v, tid, None, "mitchell", "stochastic", "ggx", 4, 1)
+    b = ctx.filter_shade_table(table, u, v, tid, None, "mitchell", "stochastic", "ggx", 4, 1, order=order)
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+    ctx.destroy_texture_table(table)
+    for hh in hs:
+        ctx.destroy_texture(hh)
