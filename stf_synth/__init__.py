@@ -192,7 +192,7 @@ class Queries:
         return self.dudx is not None
 
     def subset(self, idx) -> "Queries":
-        f = (lambda a: None if a is None else np.ascontiguousarray(a[idx]))
+        f = (lambda a: None if a is None else np.array(a[idx], copy=True))   # never a view
         return Queries(f(self.u), f(self.v), f(self.dudx), f(self.dvdx), f(self.dudy), f(self.dvdy))
 
 
