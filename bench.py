@@ -148,7 +148,8 @@ def run_ours(args):
     tex = ctx.create_texture(material.albedo_rough, material.normal)
     nq = args.queries
     q = make_queries(nq, rank)
-    id_base = rank * nq
+    from paper_2407_06107_b300.sharding import weak_id_base
+    id_base = weak_id_base(rank, nq)
     t = lambda a: torch.from_numpy(a).to(dev)
     u, v = t(q.u), t(q.v)
     d = [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]

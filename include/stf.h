@@ -20,6 +20,11 @@
  *     library owns textures and volumes: it COPIES the data in at creation and frees it at
  *     destruction.
  *   - A context is not thread-safe; use one per host thread.
+ *   - Fault injection for tests (environment variable STF_FAULT, read by stf_create):
+ *     "alloc" makes every device allocation of the context fail (STF_ERR_OOM), "launch"
+ *     makes every kernel launch fail (STF_ERR_CUDA) without launching, "mma_timeout"
+ *     makes the tensor-core decode issue no MMA so its bounded wait runs out (the kernel
+ *     frees its tensor memory and sets STF_DEV_TIMEOUT).
  *   - Query ids are 64-bit (they key the Philox counter): the id of query i of a call is
  *     queries->id_base + i, so that shards of one batch draw the same numbers as the whole.
  */

@@ -236,7 +236,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
 }
 
 template <int FILTER, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -248,7 +248,7 @@ k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst
 // each query's texture descriptor in the table.  An out-of-range texture id sets
 // DEV_BAD_INDEX and yields 0.
 template <int FILTER, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint32_t ntex,
                      const uint32_t* __restrict__ tex_id, unsigned long long* counter, ShadeConst SC, RoundKeys K) {
     __shared__ unsigned long long chunk;

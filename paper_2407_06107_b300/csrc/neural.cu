@@ -378,12 +378,15 @@ __global__ void k_pack_mlp(const float* __restrict__ P, __nv_bfloat16* __restric
 
 // ------------------------------------------------------------------ tensor-core decode
 constexpr int NT_ROWS = 128;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 64;     // the three layers reuse columns 0..63 in turn
+constexpr int DEC_CTAS_PER_SM = 6;     // 6 x 64 TMEM columns <= 512, 6 x ~37 KB smem <= 228 KB
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 struct __align__(128) DecodeSmem {
-    uint8_t A1[NT_ROWS * 32 * 2];     // 8 KB: features, K = 32
-    uint8_t A2[NT_ROWS * 64 * 2];     // 16 KB: hidden activations, K = 64
+    // 16 KB operand tile: the features (K = 32, first 8 KB) for layer 1, then the hidden
+    // activations (K = 64) for layers 2 and 3; each write happens after the MMA that read
+    // the previous contents has completed
+    uint8_t A[NT_ROWS * 64 * 2];
     uint8_t W1[64 * 32 * 2];          // 4 KB
     uint8_t W2[64 * 64 * 2];          // 8 KB
     uint8_t W3[16 * 64 * 2];          // 2 KB (rows 8..15 zero)
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
     tc_fence_after();
     const uint32_t tmem = S.tmem;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const uint32_t a1 = smem_u32(S.A1), a2 = smem_u32(S.A2);
+    const uint32_t a1 = smem_u32(S.A), a2 = a1;
     const uint32_t w1 = smem_u32(S.W1), w2 = smem_u32(S.W2), w3 = smem_u32(S.W3);
     uint32_t phase = 0;
     bool ok = true;
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
             __nv_bfloat162 p[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(f[8 * c + 2 * i], f[8 * c + 2 * i + 1]);
-            *reinterpret_cast<uint4*>(S.A1 + kmaj_off(t, 8 * c, 32)) = *reinterpret_cast<uint4*>(p);
+            *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 32)) = *reinterpret_cast<uint4*>(p);
         }
         // ---- three GEMM layers
 #pragma unroll 1
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
-            if (t == 0) {
+            if (t == 0 && !a.inject_timeout) {
                 tc_fence_after();
                 if (layer == 0) {
                     for (int s = 0; s < 2; ++s)
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                                  idesc_bf16(128, 64), s > 0);
                 } else if (layer == 1) {
                     for (int s = 0; s < 4; ++s)
-                        mma_bf16(tmem + 64, smem_desc(a2 + 256 * s, 128, 1024), smem_desc(w2 + 256 * s, 128, 1024),
+                        mma_bf16(tmem, smem_desc(a2 + 256 * s, 128, 1024), smem_desc(w2 + 256 * s, 128, 1024),
                                  idesc_bf16(128, 64), s > 0);
                 } else {
                     for (int s = 0; s < 4; ++s)
@@ -548,14 +551,14 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                 }
                 mma_commit(&S.bar);
             }
-            if (!mbar_wait_bounded(&S.bar, phase, WAIT_CYCLES)) atomicOr(&S.abort_flag, 1);
+            if (!mbar_wait_bounded(&S.bar, phase, a.inject_timeout ? 2000000LL : WAIT_CYCLES)) atomicOr(&S.abort_flag, 1);
             phase ^= 1u;
             tc_fence_after();
             __syncthreads();
             if (S.abort_flag) { ok = false; break; }
             if (layer < 2) {
                 uint32_t r[4][16];
-                const uint32_t col = layer == 0 ? 0u : 64u;
+                const uint32_t col = 0u;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) tmem_ld16(tmem + lane_base + col + 16 * c, r[c]);
                 tmem_wait_ld();
@@ -570,7 +573,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                         const float z1 = __uint_as_float(r[(k0 + 1) >> 4][(k0 + 1) & 15]) + bias[k0 + 1];
                         p[i] = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
                     }
-                    *reinterpret_cast<uint4*>(S.A2 + kmaj_off(t, 8 * c, 64)) = *reinterpret_cast<uint4*>(p);
+                    *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 64)) = *reinterpret_cast<uint4*>(p);
                 }
             } else {
                 uint32_t r[16];
@@ -673,7 +676,7 @@ static cudaError_t launch_dec(const NeuralView& N, const NeuralDecodeArgs& a, in
 
 cudaError_t launch_ntc_decode(const NeuralView& N, const NeuralDecodeArgs& a, int num_sms, cudaStream_t st) {
     const uint64_t tiles = (a.nrows + NT_ROWS - 1) / NT_ROWS;
-    const uint64_t cap = (uint64_t)num_sms * 4;
+    const uint64_t cap = (uint64_t)num_sms * DEC_CTAS_PER_SM;
     const int grid = (int)(tiles < cap ? (tiles ? tiles : 1) : cap);
     if (a.mode < 0) return launch_dec<F_LINEAR, -1>(N, a, grid, st);
 #define STF_DEC_MODES(F)                                                             \

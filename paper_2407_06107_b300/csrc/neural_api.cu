@@ -303,6 +303,7 @@ stf_status stf_neural_decode(stf_ctx c, stf_neural h, uint64_t n, const int32_t*
     stf::NeuralDecodeArgs a{};
     a.n = n; a.mode = -1; a.filter = 0; a.spp = 1; a.nrows = n; a.tex_res = r->view.tex_res;
     a.ex_ix = ix; a.ex_iy = iy; a.y_out = y; a.status = c->d_status;
+    a.inject_timeout = c->fault == stfi::FAULT_MMA_TIMEOUT;
     cudaError_t e = stf::launch_ntc_decode(r->view, a, c->num_sms, c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "neural decode launch");
 }
@@ -340,6 +341,7 @@ stf_status stf_neural_filter_shade(stf_ctx c, stf_neural h, const stf_queries* q
     if (d) { a.dudx = d->dudx; a.dvdx = d->dvdx; a.dudy = d->dudy; a.dvdy = d->dvdy; }
     a.filter = f; a.mode = m; a.shade = sh; a.spp = spp; a.seed = seed; a.tex_res = r->view.tex_res;
     a.nrows = rows; a.r = out->r; a.g = out->g; a.b = out->b; a.status = c->d_status;
+    a.inject_timeout = c->fault == stfi::FAULT_MMA_TIMEOUT;
     e = stf::launch_ntc_decode(r->view, a, c->num_sms, c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "neural filter_shade launch");
 }

@@ -124,6 +124,7 @@ stf_status stf_create(int device, void* cuda_stream, stf_ctx* out) {
     if (const char* f = std::getenv("STF_FAULT")) {
         if (!std::strcmp(f, "alloc")) c->fault = FAULT_ALLOC;
         else if (!std::strcmp(f, "launch")) c->fault = FAULT_LAUNCH;
+        else if (!std::strcmp(f, "mma_timeout")) c->fault = stfi::FAULT_MMA_TIMEOUT;
     }
     CurrentDevice cd(device);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);

@@ -54,7 +54,7 @@ struct stf_ctx_s {
 };
 
 namespace stfi {
-enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2 };
+enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2, FAULT_MMA_TIMEOUT = 3 };
 stf_status fail(stf_ctx c, stf_status s, const char* msg);
 stf_status cuda_fail(stf_ctx c, cudaError_t e, const char* where);
 stf_status dev_alloc(stf_ctx c, void** p, size_t bytes);

@@ -85,6 +85,7 @@ struct NeuralDecodeArgs {
     float* y_out;               // decode-only: [n][8]
     float *r, *g, *b;           // filter modes: accumulated, must be zero on entry
     uint32_t* status;
+    int inject_timeout;         // fault injection: issue no MMA and wait with a short limit
 };
 
 cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint64_t seed, float* loss_sum,
