@@ -90,6 +90,9 @@ typedef enum { STF_ADDRESS_WRAP = 0, STF_ADDRESS_CLAMP = 1 } stf_address;
 #define STF_FLAG_LATTICE 2u     /* stochastic modes: the pick uniforms of the spp samples of a query
                                    (pixel) form a randomly shifted lattice, frac(s/spp + phi), so they
                                    are stratified across samples; each stays uniform (unbiased) */
+#define STF_FLAG_REUSE 4u       /* 1-tap stochastic mode: one uniform per sample (per step in a volume)
+                                   drives the level and every axis, remapped after each decision
+                                   (Eq. uniform-sample-reuse; the listings' sample reuse) */
 
 /* device status bits */
 #define STF_DEV_NAN_INPUT 1u

@@ -33,6 +33,7 @@ MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
+FLAG_REUSE = 4
 NO_PICK = 0xFFFFFFFF
 
 
@@ -77,6 +78,7 @@ def lib():
         L.orc_kernel_keys.restype = C.c_double
         L.orc_weights32.argtypes = [C.c_int, C.c_float, P]
         L.orc_pick32.argtypes = [P, C.c_int, C.c_float, C.c_int]
+        L.orc_pick32_reuse.argtypes = [P, C.c_int, C.c_float, P]
         L.orc_pick_array.argtypes = [P, C.c_int, C.c_double]
         L.orc_ggx_eval.argtypes = [P, P, P, C.c_double, P, C.c_double, P]
         L.orc_ggx_D.argtypes = [C.c_double, C.c_double]
@@ -143,6 +145,14 @@ def weights32(filter_name: str, t: float) -> np.ndarray:
 def pick32(w, xi: float, cls: int = 0) -> int:
     w = np.ascontiguousarray(w, dtype=np.float32)
     return lib().orc_pick32(_p(w), len(w), float(np.float32(xi)), cls)
+
+
+def pick32_reuse(w, xi: float):
+    """(pick, remapped uniform) of the FP32 sample-reuse decision."""
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    r = np.zeros(1, dtype=np.float32)
+    k = lib().orc_pick32_reuse(_p(w), len(w), float(np.float32(xi)), _p(r))
+    return k, float(r[0])
 
 
 def pick_array(w, xi: float) -> int:

@@ -44,7 +44,7 @@ namespace {
 enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
-enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u };
+enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u };
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_NEURAL = 2 };
 enum { ADDR_WRAP = 0, ADDR_CLAMP = 1 };
 const uint32_t NO_PICK = 0xFFFFFFFFu;
@@ -201,6 +201,26 @@ int pick32(const float* w, int n, float xi, int cls, float* total) {
     for (int k = 0; k < n; ++k) if (target < C[k]) return k;
     return n - 1;
 }
+// Sample reuse (FLAG_REUSE): the same CDF pick, and the uniform remapped into the chosen
+// interval, u' = (xi S - C_{k-1}) / (C_k - C_{k-1}) -- Eq. uniform-sample-reuse applied to a
+// sampling array, as the bicubic listing's SampleDiscrete returns it.  FP32.
+int pick32_reuse(const float* w, int n, float xi, float* remapped) {
+    float C[4], acc = 0.0f;
+    for (int k = 0; k < n; ++k) { acc = acc + std::fabs(w[k]); C[k] = acc; }
+    float target = xi * acc;
+    int k = n - 1;
+    for (int j = n - 2; j >= 0; --j) if (target < C[j]) k = j;
+    float lo = k > 0 ? C[k - 1] : 0.0f;
+    *remapped = (target - lo) / (C[k] - lo);
+    return k;
+}
+// Level decision with reuse: level+1 if xi < f, xi' = xi / f, else xi' = (xi - f) / (1 - f).
+int level_reuse(float xi, float f, float* remapped) {
+    if (xi < f) { *remapped = xi / f; return 1; }
+    *remapped = (xi - f) / (1.0f - f);
+    return 0;
+}
+
 // Same decision from FP64 weights; also the distance of xi to the nearest interior
 // boundary of the FP64 CDF.
 int pick64(const double* w, int n, double xi, int cls, double* bdist) {
@@ -471,7 +491,9 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
         } else {
             // stochastic MIP level: floor(lambda) + [xi < frac(lambda)] (stochastic lerp)
             float xl = a[2];
+            float ru = a[2];                       // FLAG_REUSE: one uniform, remapped per decision
             int lvl = l0 + ((xl < fr) ? 1 : 0);
+            if (flags & FLAG_REUSE) { float r2; lvl = l0 + level_reuse(xl, fr, &r2); ru = r2; }
             int lvl64 = l0_64 + (((double)xl < fr64) ? 1 : 0);
             if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs((double)xl - fr64));
             lvl = std::min(lvl, T.levels - 1);
@@ -494,10 +516,21 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
             };
             if (mode == M_STOCHASTIC) {
                 float Sx, Sy;
-                int kx = pick32(wx, nt, a[3], 0, &Sx);
-                int ky = pick32(wy, nt, a[4], 0, &Sy);
-                int kx64 = pick64(wx64, nt, a[3], 0, &bd);
-                int ky64 = pick64(wy64, nt, a[4], 0, &bd);
+                float ux = a[3], uy = a[4];
+                int kx, ky;
+                if (flags & FLAG_REUSE) {
+                    ux = ru;
+                    kx = pick32_reuse(wx, nt, ux, &uy);
+                    float dummy;
+                    ky = pick32_reuse(wy, nt, uy, &dummy);
+                    pick32(wx, nt, 0.0f, 0, &Sx);
+                    pick32(wy, nt, 0.0f, 0, &Sy);
+                } else {
+                    kx = pick32(wx, nt, a[3], 0, &Sx);
+                    ky = pick32(wy, nt, a[4], 0, &Sy);
+                }
+                int kx64 = pick64(wx64, nt, ux, 0, &bd);
+                int ky64 = pick64(wy64, nt, uy, 0, &bd);
                 auto t = texel(lvl, kx, ky);
                 Mat m = fetch(T, lvl, t.first, t.second, &rd);
                 double o[3];
@@ -659,13 +692,20 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
             }
             const float* uk = u6 + 3 * (k & 1);
             int kk[3];
+            float ru = uk[0];                      // FLAG_REUSE: x, y, z from one remapped uniform
             for (int a = 0; a < 3; ++a) {
                 float w[4];
                 double w64[4];
                 weights32(filter, ax[a].t, w);
                 for (int j = 0; j < nt; ++j) w64[j] = kernel64(filter, ax[a].pos - (double)(ax[a].i0 + ft + j));
-                kk[a] = pick32(w, nt, uk[a], 0, nullptr);
-                pick64(w64, nt, uk[a], 0, bd);
+                float xi = uk[a];
+                if (flags & FLAG_REUSE) {
+                    xi = ru;
+                    kk[a] = pick32_reuse(w, nt, xi, &ru);
+                } else {
+                    kk[a] = pick32(w, nt, xi, 0, nullptr);
+                }
+                pick64(w64, nt, xi, 0, bd);
             }
             int ix = ax[0].i0 + ft + kk[0], iy = ax[1].i0 + ft + kk[1], iz = ax[2].i0 + ft + kk[2];
             sum_sigma += sig * vox(ix, iy, iz);
@@ -733,6 +773,7 @@ int orc_weights32(int filter, float t, float* w) { return weights32(filter, t, w
 
 // FP32 CDF pick (cls 0 = all taps, +1 positive taps, -1 negative taps)
 int orc_pick32(const float* w, int n, float xi, int cls) { return pick32(w, n, xi, cls, nullptr); }
+int orc_pick32_reuse(const float* w, int n, float xi, float* remapped) { return pick32_reuse(w, n, xi, remapped); }
 
 // FP64 CDF pick over an arbitrary array of up to 64 non-negative weights
 int orc_pick_array(const double* w, int n, double xi) {
@@ -778,6 +819,7 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
     if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 3 || mode < 0 || mode > 3) return 1;
     if (tex->levels < 1 || tex->levels > 16) return 1;
     if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
+    if ((flags & FLAG_REUSE) && mode == M_POSITIVIZED) return 1;
     if (flags & FLAG_STRATIFIED) {
         long k = std::lround(std::sqrt((double)spp));
         if ((uint32_t)(k * k) != spp) return 1;

@@ -21,6 +21,7 @@ SHADES = {"ggx": 0, "linear": 1}
 FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F = 0, 1, 2, 3
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
+FLAG_REUSE = 4
 DEV_NAN_INPUT, DEV_BAD_INDEX, DEV_TIMEOUT = 1, 2, 4
 NO_PICK = 0xFFFFFFFF
 

@@ -98,6 +98,12 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             float3 est;
             if (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) {
                 int lvl = l0 + ((A.u[2] < fr) ? 1 : 0);
+                float ru = A.u[2];                 // FLAG_REUSE: one uniform, remapped per decision
+                if (MODE == M_STOCHASTIC && (a.flags & FLAG_REUSE)) {
+                    float r2;
+                    lvl = l0 + level_reuse(A.u[2], fr, &r2);
+                    ru = r2;
+                }
                 lvl = min(lvl, T.levels - 1);
                 const int W = T.w[lvl], H = T.h[lvl];
                 const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
@@ -106,8 +112,16 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 axis_weights<FILTER>(ay.t, wy);
                 if (MODE == M_STOCHASTIC) {
                     float Sx, Sy;
-                    const int kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
-                    const int ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
+                    int kx, ky;
+                    if (a.flags & FLAG_REUSE) {
+                        float uy, dummy;
+                        kx = cdf_pick_reuse<NT>(wx, ru, &uy);
+                        ky = cdf_pick_reuse<NT>(wy, uy, &dummy);
+                        if (is_signed(FILTER)) { cdf_pick<NT>(wx, 0.0f, 0, &Sx); cdf_pick<NT>(wy, 0.0f, 0, &Sy); }
+                    } else {
+                        kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
+                        ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
+                    }
                     const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
                     const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
                     float Wt = 1.0f;

@@ -97,9 +97,17 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                         if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
                         uniforms3_of6(rw, (int)(k & 1u), uk);
                     }
-                    const int kx = cdf_pick<NT>(w[0], uk[0], 0, nullptr);
-                    const int ky = cdf_pick<NT>(w[1], uk[1], 0, nullptr);
-                    const int kz = cdf_pick<NT>(w[2], uk[2], 0, nullptr);
+                    int kx, ky, kz;
+                    if (a.flags & FLAG_REUSE) {      // x, y, z from one uniform, remapped
+                        float r1, r2, r3;
+                        kx = cdf_pick_reuse<NT>(w[0], uk[0], &r1);
+                        ky = cdf_pick_reuse<NT>(w[1], r1, &r2);
+                        kz = cdf_pick_reuse<NT>(w[2], r2, &r3);
+                    } else {
+                        kx = cdf_pick<NT>(w[0], uk[0], 0, nullptr);
+                        ky = cdf_pick<NT>(w[1], uk[1], 0, nullptr);
+                        kz = cdf_pick<NT>(w[2], uk[2], 0, nullptr);
+                    }
                     const int ix = clamp_index(ap[0].i0 + T0 + kx, a.nx);
                     const int iy = clamp_index(ap[1].i0 + T0 + ky, a.ny);
                     const int iz = clamp_index(ap[2].i0 + T0 + kz, a.nz);

@@ -551,10 +551,13 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                 }
                 mma_commit(&S.bar);
             }
-            if (!mbar_wait_bounded(&S.bar, phase, a.inject_timeout ? 2000000LL : WAIT_CYCLES)) atomicOr(&S.abort_flag, 1);
+            // one thread polls the MMA-completion barrier; the others wait at the block
+            // barrier, which costs no issue slots
+            if (t == 0 && !mbar_wait_bounded(&S.bar, phase, a.inject_timeout ? 2000000LL : WAIT_CYCLES))
+                S.abort_flag = 1;
             phase ^= 1u;
-            tc_fence_after();
             __syncthreads();
+            tc_fence_after();
             if (S.abort_flag) { ok = false; break; }
             if (layer < 2) {
                 uint32_t r[4][16];

@@ -63,7 +63,9 @@ extern "C" stf_status stf_filter_shade_host_noalloc(stf_ctx c, stf_tex t, const 
     if (m == STF_MODE_STOCHASTIC_POSITIVIZED && f != STF_FILTER_CATMULL_ROM && f != STF_FILTER_MITCHELL)
         return stfi::fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
     if (spp == 0) return stfi::fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
-    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE)) return stfi::fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & STF_FLAG_REUSE) && m == STF_MODE_STOCHASTIC_POSITIVIZED)
+        return stfi::fail(c, STF_ERR_UNSUPPORTED, "sample reuse is defined for the 1-tap estimator");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE)) return stfi::fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
     int kside = 1;
     if (flags & STF_FLAG_STRATIFIED) {
         while ((uint32_t)(kside * kside) < spp) ++kside;

@@ -67,7 +67,9 @@ stf_status validate_filter_call(stf_ctx c, stf_tex t, const stf_queries* q, cons
     if (m == STF_MODE_STOCHASTIC_POSITIVIZED && !signed_filter(f))
         return fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
     if (spp == 0) return fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
-    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & STF_FLAG_REUSE) && m == STF_MODE_STOCHASTIC_POSITIVIZED)
+        return fail(c, STF_ERR_UNSUPPORTED, "sample reuse is defined for the 1-tap estimator");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
     if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0)
         return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
     if (q->n == 0) return STF_OK;
@@ -464,7 +466,7 @@ stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t wid
     if (m != STF_MODE_NTAP_BEFORE && m != STF_MODE_NTAP_AFTER && m != STF_MODE_STOCHASTIC)
         return fail(c, STF_ERR_UNSUPPORTED, "volume mode must be NTAP_BEFORE, NTAP_AFTER or STOCHASTIC");
     if (width < 1 || height < 1 || steps < 1 || steps > 65535 || spp < 1) return fail(c, STF_ERR_INVALID_ARG, "bad image size, steps or spp");
-    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
     if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0) return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
     if (pix_begin + pix_count > (uint64_t)width * height) return fail(c, STF_ERR_INVALID_ARG, "pixel range outside the image");
     if (pix_count == 0) return STF_OK;

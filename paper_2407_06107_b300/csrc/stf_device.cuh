@@ -15,7 +15,7 @@ enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { SH_GGX = 0, SH_LINEAR = 1 };
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
-enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u };
+enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u };
 enum { DEV_NAN_INPUT = 1u, DEV_BAD_INDEX = 2u, DEV_TIMEOUT = 4u };
 constexpr uint32_t NO_PICK = 0xFFFFFFFFu;
 
@@ -169,6 +169,30 @@ __device__ __forceinline__ int cdf_pick(const float w[4], float xi, int cls, flo
 #pragma unroll
     for (int j = N - 2; j >= 0; --j) k = (target < c[j]) ? j : k;
     return k;
+}
+
+// Sample reuse: the same pick, and the uniform remapped into the chosen interval,
+// u' = (xi S - C_{k-1}) / (C_k - C_{k-1}) (Eq. uniform-sample-reuse on a sampling array).
+template <int N>
+__device__ __forceinline__ int cdf_pick_reuse(const float w[4], float xi, float* remapped) {
+    float c[N];
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) { acc = __fadd_rn(acc, fabsf(w[k])); c[k] = acc; }
+    const float target = __fmul_rn(xi, acc);
+    int k = N - 1;
+    float lo = c[N - 2], hi = c[N - 1];
+#pragma unroll
+    for (int j = N - 2; j >= 0; --j) {
+        if (target < c[j]) { k = j; hi = c[j]; lo = j > 0 ? c[j - 1] : 0.0f; }
+    }
+    *remapped = __fdiv_rn(__fsub_rn(target, lo), __fsub_rn(hi, lo));
+    return k;
+}
+__device__ __forceinline__ int level_reuse(float xi, float f, float* remapped) {
+    if (xi < f) { *remapped = __fdiv_rn(xi, f); return 1; }
+    *remapped = __fdiv_rn(__fsub_rn(xi, f), __fsub_rn(1.0f, f));
+    return 0;
 }
 
 // raster position on one axis: p = x*res - 1/2, i0 = floor(p), t = p - i0 (FP32)

@@ -230,3 +230,10 @@ def test_binned_order_is_permutation_and_results_identical(ctx, material):
         b = ctx.filter_shade(h, u, v, d, f, mode, "ggx", 3, 4, want_picks=True, order=order)
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("filter,flags", [("bspline", 4), ("mitchell", 4), ("linear", 4), ("catmull_rom", 6)])
+def test_reuse_sampler(ctx, material, filter, flags):
+    # flags 4 = sample reuse; 6 = reuse on a shifted lattice
+    h, otex, q = material
+    _check(ctx, h, otex, q, filter, "stochastic", spp=3, seed=17, flags=flags)

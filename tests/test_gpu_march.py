@@ -115,3 +115,15 @@ def test_lattice_sampler(ctx, small, filter):
                        want_picks=True)
     mism = compare_picks(pk.cpu().numpy().view(np.uint32), ref, W * H)
     assert_values(T.cpu().numpy(), ref.T, mism)
+
+
+@pytest.mark.parametrize("filter", ["linear", "bspline"])
+def test_reuse_sampler(ctx, small, filter):
+    h, vol = small
+    cam = synth.camera_pinhole(W, H).as_array()
+    T, pk = ctx.march_volume(h, cam, W, H, 96, filter, "stochastic", spp=3, seed=12, flags=oracle.FLAG_REUSE,
+                             want_picks=True)
+    ref = oracle.march(vol, 20.0, cam, W, H, 96, filter, "stochastic", spp=3, seed=12, flags=oracle.FLAG_REUSE,
+                       want_picks=True)
+    mism = compare_picks(pk.cpu().numpy().view(np.uint32), ref, W * H)
+    assert_values(T.cpu().numpy(), ref.T, mism)

@@ -513,3 +513,51 @@ def test_volume_lattice_unbiased_and_lower_variance():
     ind, lat = np.array(ind), np.array(lat)
     assert abs(lat.mean()) < 4 * lat.std() / math.sqrt(len(lat)) + 1e-12
     assert lat.std() < ind.std()
+
+
+# ------------------------------------------------------------------------ sample reuse
+@pytest.mark.parametrize("f", FILTERS)
+def test_reuse_joint_distribution_by_enumeration(f):
+    # one uniform drives both axes, remapped after the first decision: the u-measure of
+    # every (kx, ky) cell equals p_x(kx) p_y(ky) (Eq. uniform-sample-reuse)
+    rng = np.random.default_rng(17)
+    m = 1 << 14
+    for tx, ty in rng.random((3, 2)).astype(np.float32):
+        wx, wy = oracle.weights32(f, tx), oracle.weights32(f, ty)
+        px = np.abs(wx.astype(np.float64)); px /= px.sum()
+        py = np.abs(wy.astype(np.float64)); py /= py.sum()
+        hist = np.zeros((len(wx), len(wy)))
+        for u in (np.arange(m) + 0.5) / m:
+            kx, r = oracle.pick32_reuse(wx, u)
+            ky, _ = oracle.pick32_reuse(wy, r)
+            hist[kx, ky] += 1.0 / m
+        np.testing.assert_allclose(hist, np.outer(px, py), atol=3.0 / m)
+
+
+@pytest.mark.parametrize("f", ["bspline", "mitchell"])
+def test_reuse_estimator_unbiased(f):
+    m = synth.material_rgba8(8, 3, octaves=3, base=2)
+    tex = oracle.Texture(m.albedo_rough, m.normal)
+    q = synth.queries_uniform(4, 23, res=8, lod_range=2.5)
+    d = []
+    for seed in range(1, 2001):
+        s = oracle.filter_shade(tex, q, f, "stochastic", spp=4, seed=seed, flags=oracle.FLAG_REUSE).rgb
+        a = oracle.filter_shade(tex, q, f, "ntap_after", spp=4, seed=seed).rgb
+        d.append(s - a)
+    d = np.array(d)
+    z = np.abs(d.mean(0)) / (d.std(0) / math.sqrt(len(d)) + 1e-12)
+    assert z.max() < 4.5, z.max()
+
+
+def test_volume_reuse_unbiased():
+    vol = synth.volume_cloud(16, 6, zero_frac=0.5, octaves=3, base=2)
+    W, H = 4, 3
+    cam = synth.camera_pinhole(W, H).as_array()
+    d = []
+    for seed in range(1, 1201):
+        a = oracle.march(vol, 20.0, cam, W, H, 48, "bspline", "ntap_after", spp=1, seed=seed, pix_begin=5, pix_count=1).T[0]
+        s = oracle.march(vol, 20.0, cam, W, H, 48, "bspline", "stochastic", spp=1, seed=seed, flags=oracle.FLAG_REUSE,
+                         pix_begin=5, pix_count=1).T[0]
+        d.append(s - a)
+    d = np.array(d)
+    assert abs(d.mean()) < 4 * d.std() / math.sqrt(len(d)) + 1e-12
