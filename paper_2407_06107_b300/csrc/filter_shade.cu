@@ -13,14 +13,22 @@
 
 namespace stf {
 
-__device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, int iy) {
+// A texel as loaded: RGBA32F uses all four words, RGBA8 + RG8 the first two.  Loading and
+// decoding are separate so that a sample's load can be issued before the previous
+// sample is shaded.
+__device__ __forceinline__ uint4 load_texel(const FetchCtx& T, int lvl, int ix, int iy) {
     const size_t idx = (size_t)iy * (size_t)T.w[lvl] + (size_t)ix;
-    if (T.fmt == FMT_RGBA32F) {
-        const float4* p = reinterpret_cast<const float4*>(T.base + T.off[lvl]);
-        return decode_rgba32f(__ldg(p + idx));
-    }
-    const uint2* p = reinterpret_cast<const uint2*>(T.base + T.off[lvl]);
-    return decode_rgba8(__ldg(p + idx), T.has_normal != 0);
+    if (T.fmt == FMT_RGBA32F) return __ldg(reinterpret_cast<const uint4*>(T.base + T.off[lvl]) + idx);
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(T.base + T.off[lvl]) + idx);
+    return make_uint4(t.x, t.y, 0u, 0u);
+}
+__device__ __forceinline__ Material decode_texel(const FetchCtx& T, uint4 r) {
+    if (T.fmt == FMT_RGBA32F)
+        return decode_rgba32f(make_float4(__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z), __uint_as_float(r.w)));
+    return decode_rgba8(make_uint2(r.x, r.y), T.has_normal != 0);
+}
+__device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, int iy) {
+    return decode_texel(T, load_texel(T, lvl, ix, iy));
 }
 
 __device__ __forceinline__ uint32_t pack_pick(int lvl, int ix, int iy) {
@@ -42,6 +50,22 @@ __device__ __forceinline__ float lod_aniso(float dudx, float dvdx, float dudy, f
     if (minl > 0.0f && __fmul_rn(minl, 64.0f) < maxl) minl = __fmul_rn(maxl, 1.0f / 64.0f);
     const float l = log2f(minl);
     return fminf(fmaxf(l, 0.0f), (float)(levels - 1));
+}
+
+// Screen-space jitter of sample s inside the derivative footprint (Sec. 4.2.1): a uniform
+// offset in [-1/2, 1/2)^2, or the centre of cell s of a kside x kside grid (stratified).
+__device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, const U5& A, float dudx, float dvdx,
+                                       float dudy, float dvdy, float* x, float* y) {
+    float jx, jy;
+    if (flags & FLAG_STRATIFIED) {
+        jx = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s % kside), 0.5f), (float)kside), 0.5f);
+        jy = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s / kside), 0.5f), (float)kside), 0.5f);
+    } else {
+        jx = __fsub_rn(A.u[0], 0.5f);
+        jy = __fsub_rn(A.u[1], 0.5f);
+    }
+    *x = __fmaf_rn(jy, dudy, __fmaf_rn(jx, dudx, *x));
+    *y = __fmaf_rn(jy, dvdy, __fmaf_rn(jx, dvdx, *y));
 }
 
 // One query: all its samples, written to a.r/g/b[q].  T is the texture (a kernel
@@ -74,32 +98,21 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             if (MODE == M_POSITIVIZED) LB = ints5(philox(id_lo, id_hi, 0xFFFFFFFFu, 1u, K));
         }
 
-        for (uint32_t s = 0; s < a.spp; ++s) {
-            // stream 0: (jitter x, jitter y, level, pick x, pick y)
-            U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
-            const uint32_t lshift = lat ? lattice_shift(s, a.spp, 24) : 0u;
-            if (lat) {
+        if constexpr (MODE == M_STOCHASTIC) {
+            // Software-pipelined: sample s+1 is picked and its texel load issued before
+            // sample s is decoded and shaded, so the gather latency hides behind shading.
+            auto pick = [&](uint32_t s, float* wt) -> uint4 {
+                U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+                if (lat) {
+                    const uint32_t lshift = lattice_shift(s, a.spp, 24);
 #pragma unroll
-                for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
-            }
-            float x = u, y = v;
-            if (a.has_derivs) {
-                float jx, jy;
-                if (a.flags & FLAG_STRATIFIED) {
-                    jx = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s % kside), 0.5f), (float)kside), 0.5f);
-                    jy = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s / kside), 0.5f), (float)kside), 0.5f);
-                } else {
-                    jx = __fsub_rn(A.u[0], 0.5f);
-                    jy = __fsub_rn(A.u[1], 0.5f);
+                    for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
                 }
-                x = __fmaf_rn(jy, dudy, __fmaf_rn(jx, dudx, x));
-                y = __fmaf_rn(jy, dvdy, __fmaf_rn(jx, dvdx, y));
-            }
-            float3 est;
-            if (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) {
+                float x = u, y = v;
+                if (a.has_derivs) jitter(s, kside, a.flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
                 int lvl = l0 + ((A.u[2] < fr) ? 1 : 0);
                 float ru = A.u[2];                 // FLAG_REUSE: one uniform, remapped per decision
-                if (MODE == M_STOCHASTIC && (a.flags & FLAG_REUSE)) {
+                if (a.flags & FLAG_REUSE) {
                     float r2;
                     lvl = l0 + level_reuse(A.u[2], fr, &r2);
                     ru = r2;
@@ -110,74 +123,111 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 float wx[4], wy[4];
                 axis_weights<FILTER>(ax.t, wx);
                 axis_weights<FILTER>(ay.t, wy);
-                if (MODE == M_STOCHASTIC) {
-                    float Sx, Sy;
-                    int kx, ky;
-                    if (a.flags & FLAG_REUSE) {
-                        float uy, dummy;
-                        kx = cdf_pick_reuse<NT>(wx, ru, &uy);
-                        ky = cdf_pick_reuse<NT>(wy, uy, &dummy);
-                        if (is_signed(FILTER)) { cdf_pick<NT>(wx, 0.0f, 0, &Sx); cdf_pick<NT>(wy, 0.0f, 0, &Sy); }
-                    } else {
-                        kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
-                        ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
-                    }
-                    const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
-                    const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
-                    float Wt = 1.0f;
+                float Sx, Sy;
+                int kx, ky;
+                bool nx = false, ny = false;     // sign of the picked weight per axis
+                if (a.flags & FLAG_REUSE) {
+                    float uy, dummy;
+                    kx = cdf_pick_reuse<NT>(wx, ru, &uy);
+                    ky = cdf_pick_reuse<NT>(wy, uy, &dummy);
                     if (is_signed(FILTER)) {
-                        // sign of the picked weight, selected without dynamic register indexing
-                        bool nx = false, ny = false;
+                        cdf_pick<NT>(wx, 0.0f, 0, &Sx); cdf_pick<NT>(wy, 0.0f, 0, &Sy);
+                        // the sign of the picked weight, selected without dynamic register indexing
 #pragma unroll
                         for (int k = 0; k < NT; ++k) {
                             nx = (k == kx) ? (wx[k] < 0.0f) : nx;
                             ny = (k == ky) ? (wy[k] < 0.0f) : ny;
                         }
-                        Wt = Sx * Sy;
-                        if (nx != ny) Wt = -Wt;
                     }
-                    est = make_float3(Wt * f.x, Wt * f.y, Wt * f.z);
-                    if (a.picks) {
-                        uint32_t* pk = a.picks + (q * a.spp + s) * 2;
-                        pk[0] = pack_pick(lvl, ix, iy);
-                        pk[1] = NO_PICK;
-                    }
+                } else if (is_signed(FILTER)) {
+                    kx = cdf_pick_sign<NT>(wx, A.u[3], &Sx, &nx);
+                    ky = cdf_pick_sign<NT>(wy, A.u[4], &Sy, &ny);
                 } else {
-                    // positivization: one sample from each sign set, separable (Sec. 2.2)
-                    float Px, Nx, Py, Ny;
-                    cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
-                    cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
-                    const float Wp = __fmaf_rn(Nx, Ny, __fmul_rn(Px, Py));
-                    const float Wn = __fmaf_rn(Nx, Py, __fmul_rn(Px, Ny));
-                    // stream 1: (positive class, negative pick x, negative pick y, negative class)
-                    U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
-                    if (lat) {
+                    kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
+                    ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
+                }
+                const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
+                float Wt = 1.0f;
+                if (is_signed(FILTER)) {
+                    Wt = Sx * Sy;
+                    if (nx != ny) Wt = -Wt;
+                }
+                *wt = Wt;
+                if (a.picks) {
+                    uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                    pk[0] = pack_pick(lvl, ix, iy);
+                    pk[1] = NO_PICK;
+                }
+                return load_texel(T, lvl, ix, iy);
+            };
+            float wt_next;
+            uint4 raw_next = pick(0, &wt_next);
+            for (uint32_t s = 0; s < a.spp; ++s) {
+                const uint4 raw = raw_next;
+                const float Wt = wt_next;
+                if (s + 1 < a.spp) raw_next = pick(s + 1, &wt_next);
+                const float3 f = shade(a.shade, decode_texel(T, raw), SC);
+                acc.x += Wt * f.x; acc.y += Wt * f.y; acc.z += Wt * f.z;
+            }
+        } else
+        for (uint32_t s = 0; s < a.spp; ++s) {
+            // stream 0: (jitter x, jitter y, level, pick x, pick y)
+            U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            const uint32_t lshift = lat ? lattice_shift(s, a.spp, 24) : 0u;
+            if (lat) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], lshift, 24);
-                    }
-                    const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
-                    const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
-                    const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
-                    const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
-                    const float3 f = shade(a.shade, fetch(T, lvl, ix, iy), SC);
-                    est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
-                    uint32_t negpick = NO_PICK;
-                    if (Wn > 0.0f) {
-                        const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
-                        const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
-                        const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
-                        const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
-                        const float3 g = shade(a.shade, fetch(T, lvl, jx, jy), SC);
-                        est.x = fmaf(-Wn, g.x, est.x);
-                        est.y = fmaf(-Wn, g.y, est.y);
-                        est.z = fmaf(-Wn, g.z, est.z);
-                        negpick = pack_pick(lvl, jx, jy);
-                    }
-                    if (a.picks) {
-                        uint32_t* pk = a.picks + (q * a.spp + s) * 2;
-                        pk[0] = pack_pick(lvl, ix, iy);
-                        pk[1] = negpick;
-                    }
+                for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
+            }
+            float x = u, y = v;
+            if (a.has_derivs) jitter(s, kside, a.flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
+            float3 est;
+            if (MODE == M_POSITIVIZED) {
+                const int lvl = min(l0 + ((A.u[2] < fr) ? 1 : 0), T.levels - 1);
+                const int W = T.w[lvl], H = T.h[lvl];
+                const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+                float wx[4], wy[4];
+                axis_weights<FILTER>(ax.t, wx);
+                axis_weights<FILTER>(ay.t, wy);
+                // positivization: one sample from each sign set, separable (Sec. 2.2)
+                float Px, Nx, Py, Ny;
+                cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
+                cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
+                const float Wp = __fmaf_rn(Nx, Ny, __fmul_rn(Px, Py));
+                const float Wn = __fmaf_rn(Nx, Py, __fmul_rn(Px, Ny));
+                // stream 1: (positive class, negative pick x, negative pick y, negative class)
+                U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                if (lat) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], lshift, 24);
+                }
+                const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
+                const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
+                const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
+                const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
+                const uint4 raw_p = load_texel(T, lvl, ix, iy);
+                // both loads are issued before either texel is shaded
+                uint32_t negpick = NO_PICK;
+                uint4 raw_n = make_uint4(0u, 0u, 0u, 0u);
+                if (Wn > 0.0f) {
+                    const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
+                    const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
+                    const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
+                    const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
+                    raw_n = load_texel(T, lvl, jx, jy);
+                    negpick = pack_pick(lvl, jx, jy);
+                }
+                const float3 f = shade(a.shade, decode_texel(T, raw_p), SC);
+                est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
+                if (Wn > 0.0f) {
+                    const float3 g = shade(a.shade, decode_texel(T, raw_n), SC);
+                    est.x = fmaf(-Wn, g.x, est.x);
+                    est.y = fmaf(-Wn, g.y, est.y);
+                    est.z = fmaf(-Wn, g.z, est.z);
+                }
+                if (a.picks) {
+                    uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                    pk[0] = pack_pick(lvl, ix, iy);
+                    pk[1] = negpick;
                 }
             } else {
                 // N-tap: every tap of levels floor(lam) and floor(lam)+1

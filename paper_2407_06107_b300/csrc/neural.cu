@@ -101,7 +101,7 @@ __host__ __device__ constexpr uint32_t kmaj_off(uint32_t row, uint32_t k, uint32
 // bilinear taps of grid g at the centre of texel (ix, iy): FP32 in the oracle's order
 struct LTap { int x0, y0, x1, y1; float w00, w10, w01, w11; };
 __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, int iy) {
-    const float s = __fdiv_rn((float)N.res[g], (float)N.tex_res);
+    const float s = N.gscale[g];
     const float px = __fmaf_rn(__fadd_rn((float)ix, 0.5f), s, -0.5f);
     const float py = __fmaf_rn(__fadd_rn((float)iy, 0.5f), s, -0.5f);
     const float fx = floorf(px), fy = floorf(py);
@@ -439,15 +439,11 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     o.pair = (long long)pair;
     if (MODE == M_STOCHASTIC) {
         float Sx, Sy;
-        const int kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
-        const int ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
+        bool nx = false, ny = false;
+        const int kx = cdf_pick_sign<NT>(wx, A.u[3], &Sx, &nx);
+        const int ky = cdf_pick_sign<NT>(wy, A.u[4], &Sy, &ny);
         float W = 1.0f;
-        if (is_signed(FILTER)) {
-            bool nx = false, ny = false;
-#pragma unroll
-            for (int k = 0; k < NT; ++k) { nx = (k == kx) ? (wx[k] < 0.0f) : nx; ny = (k == ky) ? (wy[k] < 0.0f) : ny; }
-            W = (nx != ny) ? -Sx * Sy : Sx * Sy;
-        }
+        if (is_signed(FILTER)) W = (nx != ny) ? -Sx * Sy : Sx * Sy;
         o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R); o.w = W;
     } else if (MODE == M_POSITIVIZED) {
         float Px, Nx, Py, Ny;
@@ -565,15 +561,17 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
 #pragma unroll
                 for (int c = 0; c < 4; ++c) tmem_ld16(tmem + lane_base + col + 16 * c, r[c]);
                 tmem_wait_ld();
-                const float* bias = S.bias + (layer == 0 ? 0 : 64);
+                const float4* bias4 = reinterpret_cast<const float4*>(S.bias + (layer == 0 ? 0 : 64));
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
+                    const float4 ba = bias4[2 * c], bb = bias4[2 * c + 1];
+                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
                     __nv_bfloat162 p[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int k0 = 8 * c + 2 * i;
-                        const float z0 = __uint_as_float(r[k0 >> 4][k0 & 15]) + bias[k0];
-                        const float z1 = __uint_as_float(r[(k0 + 1) >> 4][(k0 + 1) & 15]) + bias[k0 + 1];
+                        const float z0 = __uint_as_float(r[k0 >> 4][k0 & 15]) + bv[2 * i];
+                        const float z1 = __uint_as_float(r[(k0 + 1) >> 4][(k0 + 1) & 15]) + bv[2 * i + 1];
                         p[i] = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
                     }
                     *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 64)) = *reinterpret_cast<uint4*>(p);

@@ -66,6 +66,7 @@ stf_status stf_neural_create(stf_ctx c, const stf_neural_desc* d, stf_neural* ou
     uint64_t T = 0;
     for (int g = 0; g < 4; ++g) {
         r.view.res[g] = (int)d->grid_res[g];
+        r.view.gscale[g] = (float)d->grid_res[g] / (float)d->tex_res;   // correctly rounded, as on the device
         r.view.lat_off[g] = T;
         T += (uint64_t)d->grid_res[g] * d->grid_res[g] * 8;
         r.view.scale[g] = 1.0f;

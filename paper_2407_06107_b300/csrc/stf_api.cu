@@ -1,5 +1,6 @@
 // C-ABI layer of libstf: contexts, handles, argument validation, uploads and launches.
 // See include/stf.h for the contract of every entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -145,6 +146,10 @@ stf_status stf_destroy(stf_ctx c) {
     for (auto& kv : c->vol) cudaFree(kv.second.mem);
     for (auto& kv : c->tables) cudaFree(kv.second.mem);
     for (auto& kv : c->neural) { cudaFree(kv.second.mem); if (kv.second.loss) cudaFree(kv.second.loss); }
+    for (int i = 0; i < STF_LANES; ++i) {
+        if (c->lane[i]) { cudaStreamSynchronize(c->lane[i]); cudaStreamDestroy(c->lane[i]); }
+    }
+    if (c->entry_ev) cudaEventDestroy(c->entry_ev);
     if (c->stage) cudaFree(c->stage);
     if (c->d_status) cudaFree(c->d_status);
     delete c;
@@ -266,7 +271,7 @@ stf_status stf_destroy_texture(stf_ctx c, stf_tex t) {
 // ------------------------------------------------------------------------- filter + shade
 static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries* q, const stf_derivs* d,
                                  stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
-                                 uint32_t flags, const stf_output* out) {
+                                 uint32_t flags, const stf_output* out, cudaStream_t stream) {
     if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
     stf::FilterShadeArgs a{};
     a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v; a.order = q->order;
@@ -276,7 +281,7 @@ static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries
     a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
     a.seed = seed; a.r = out->r; a.g = out->g; a.b = out->b; a.picks = out->picks;
     a.status = c->d_status;
-    cudaError_t e = stf::launch_filter_shade(a, rec.view, c->num_sms, c->stream);
+    cudaError_t e = stf::launch_filter_shade(a, rec.view, c->num_sms, stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "filter_shade launch");
 }
 
@@ -287,7 +292,25 @@ stf_status stf_filter_shade(stf_ctx c, stf_tex t, const stf_queries* q, const st
     stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, &rec);
     if (s != STF_OK || q->n == 0) return s;
     CurrentDevice cd(c->device);
-    return enqueue_filter(c, *rec, q, d, f, m, sh, spp, seed, flags, out);
+    return enqueue_filter(c, *rec, q, d, f, m, sh, spp, seed, flags, out, c->stream);
+}
+
+// The host-buffer path is a copy pipeline: the queries are cut into chunks, and chunk k
+// goes to lane k mod STF_LANES (its own stream and staging buffers), so that one chunk's
+// host->device copy, another's kernel and a third's device->host copy run at once on the
+// two copy engines and the SMs.  Each chunk keeps its global query ids (id_base + offset),
+// so the random numbers, and therefore the results, do not depend on the chunking.
+static stf_status ensure_lanes(stf_ctx c) {
+    for (int i = 0; i < STF_LANES; ++i) {
+        if (c->lane[i]) continue;
+        cudaError_t e = cudaStreamCreateWithFlags(&c->lane[i], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lane stream creation");
+    }
+    if (!c->entry_ev) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->entry_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(c, e, "event creation");
+    }
+    return STF_OK;
 }
 
 stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
@@ -296,36 +319,59 @@ stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, con
     TexRec* rec = nullptr;
     stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, &rec);
     if (s != STF_OK || q->n == 0) return s;
+    if (q->order) return fail(c, STF_ERR_UNSUPPORTED, "the host-buffer entry point takes no execution order");
     CurrentDevice cd(c->device);
     const uint64_t n = q->n;
-    const size_t fb = ((n * 4 + 255) / 256) * 256;
     const int nin = d ? 6 : 2;
-    const size_t pick_b = out->picks ? n * (size_t)spp * 2 * 4 : 0;
-    s = ensure_stage(c, fb * (nin + 3) + pick_b);
+    // chunk: about 64 MB of staging per lane, 2^16 .. 2^21 queries, a multiple of 256
+    const uint64_t per_q = (uint64_t)(nin + 3) * 4 + (out->picks ? (uint64_t)spp * 8 : 0);
+    uint64_t chunk = std::min<uint64_t>(1ull << 21, std::max<uint64_t>(1ull << 16, (64ull << 20) / per_q)) & ~255ull;
+    chunk = std::min(chunk, n);
+    const uint64_t nchunks = (n + chunk - 1) / chunk;
+    const int lanes = (int)std::min<uint64_t>(STF_LANES, nchunks);
+    const size_t fb = ((chunk * 4 + 255) / 256) * 256;
+    const size_t pick_b = out->picks ? ((chunk * spp * 8 + 255) / 256) * 256 : 0;
+    const size_t lane_b = fb * (nin + 3) + pick_b;
+    s = ensure_lanes(c);
+    if (s == STF_OK) s = ensure_stage(c, lane_b * lanes);
     if (s != STF_OK) return s;
-    char* base = (char*)c->stage;
-    float* dv[6];
+    cudaError_t e = cudaEventRecord(c->entry_ev, c->stream);   // earlier work on the caller's stream
+    for (int i = 0; i < lanes && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->lane[i], c->entry_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream ordering");
     const float* hv[6] = {q->u, q->v, d ? d->dudx : nullptr, d ? d->dvdx : nullptr, d ? d->dudy : nullptr, d ? d->dvdy : nullptr};
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < nin && e == cudaSuccess; ++i) {
-        dv[i] = (float*)(base + fb * i);
-        e = cudaMemcpyAsync(dv[i], hv[i], n * 4, cudaMemcpyHostToDevice, c->stream);
+    float* ho[3] = {out->r, out->g, out->b};
+    stf_status first = STF_OK;
+    for (uint64_t k = 0; k < nchunks && first == STF_OK; ++k) {
+        const int li = (int)(k % lanes);
+        cudaStream_t st = c->lane[li];
+        char* base = (char*)c->stage + lane_b * li;
+        const uint64_t off = k * chunk, cn = std::min(chunk, n - off);
+        float* dv[6] = {};
+        for (int i = 0; i < nin && e == cudaSuccess; ++i) {
+            dv[i] = (float*)(base + fb * i);
+            e = cudaMemcpyAsync(dv[i], hv[i] + off, cn * 4, cudaMemcpyHostToDevice, st);
+        }
+        if (e != cudaSuccess) { first = cuda_fail(c, e, "host->device copy"); break; }
+        stf_queries dq{cn, q->id_base + off, dv[0], dv[1], nullptr};
+        stf_derivs dd{};
+        if (d) dd = stf_derivs{dv[2], dv[3], dv[4], dv[5]};
+        float* dout3[3] = {(float*)(base + fb * nin), (float*)(base + fb * (nin + 1)), (float*)(base + fb * (nin + 2))};
+        uint32_t* dpk = out->picks ? (uint32_t*)(base + fb * (nin + 3)) : nullptr;
+        stf_output dout{dout3[0], dout3[1], dout3[2], dpk};
+        first = enqueue_filter(c, *rec, &dq, d ? &dd : nullptr, f, m, sh, spp, seed, flags, &dout, st);
+        if (first != STF_OK) break;
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(ho[i] + off, dout3[i], cn * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && dpk)
+            e = cudaMemcpyAsync(out->picks + off * spp * 2, dpk, cn * spp * 8, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) first = cuda_fail(c, e, "device->host copy");
     }
-    if (e != cudaSuccess) return cuda_fail(c, e, "host->device copy");
-    if (q->order) return fail(c, STF_ERR_UNSUPPORTED, "the host-buffer entry point takes no execution order");
-    stf_queries dq{n, q->id_base, dv[0], dv[1], nullptr};
-    stf_derivs dd{};
-    if (d) dd = stf_derivs{dv[2], dv[3], dv[4], dv[5]};
-    stf_output dout{(float*)(base + fb * nin), (float*)(base + fb * (nin + 1)), (float*)(base + fb * (nin + 2)),
-                    out->picks ? (uint32_t*)(base + fb * (nin + 3)) : nullptr};
-    s = enqueue_filter(c, *rec, &dq, d ? &dd : nullptr, f, m, sh, spp, seed, flags, &dout);
-    if (s != STF_OK) return s;
-    e = cudaMemcpyAsync(out->r, dout.r, n * 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out->g, dout.g, n * 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out->b, dout.b, n * 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && out->picks) e = cudaMemcpyAsync(out->picks, dout.picks, pick_b, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "device->host copy");
+    // every lane drains before returning (also after an error: staging stays in use until then)
+    for (int i = 0; i < lanes; ++i) {
+        cudaError_t ei = cudaStreamSynchronize(c->lane[i]);
+        if (ei != cudaSuccess && first == STF_OK) first = cuda_fail(c, ei, "lane synchronise");
+    }
+    return first;
 }
 
 // ---------------------------------------------------------------------------- texture table

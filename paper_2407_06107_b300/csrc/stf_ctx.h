@@ -8,6 +8,8 @@
 #include "../../include/stf.h"
 #include "stf_kernels.h"
 
+enum { STF_LANES = 3 };
+
 struct TexRec {
     void* mem = nullptr;
     stf::TexView view{};
@@ -50,6 +52,8 @@ struct stf_ctx_s {
     std::unordered_map<uint64_t, TableRec> tables;
     void* stage = nullptr;          // device staging for the host-buffer entry points
     size_t stage_bytes = 0;
+    cudaStream_t lane[STF_LANES] = {};   // copy-pipeline streams of the host-buffer path
+    cudaEvent_t entry_ev = nullptr;      // orders the lanes after the caller's stream
     int fault = 0;                  // host-side fault injection (STF_FAULT), 0 = off
 };
 

@@ -107,33 +107,41 @@ __device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
 // (linear).  The B-spline uses the polynomials of the paper's bicubic listing; the cubic
 // kernels (Keys a=-1/2, Mitchell-Netravali BC(1/3,1/3)) are evaluated in Horner form;
 // multiply-add chains are explicit single-rounded FMAs (__fmaf_rn), nothing else fuses.
+template <int F> struct CubicCoef;
+template <> struct CubicCoef<F_CATMULL_ROM> {
+    static constexpr float c3 = 1.5f, c2 = -2.5f, c0 = 1.0f, q3 = -0.5f, q2 = 2.5f, q1 = -4.0f, q0 = 2.0f;
+};
+template <> struct CubicCoef<F_MITCHELL> {
+    static constexpr float c3 = 7.0f / 6.0f, c2 = -2.0f, c0 = 8.0f / 9.0f;
+    static constexpr float q3 = -7.0f / 18.0f, q2 = 2.0f, q1 = -10.0f / 3.0f, q0 = 16.0f / 9.0f;
+};
+// inner piece (|d| < 1) and outer piece (1 <= |d| < 2)
+template <int F>
+__device__ __forceinline__ float k_cubic_inner(float d) {
+    using C = CubicCoef<F>;
+    const float a = __fmul_rn(__fmaf_rn(C::c3, d, C::c2), d);
+    return __fmaf_rn(a, d, C::c0);
+}
+template <int F>
+__device__ __forceinline__ float k_cubic_outer(float d) {
+    using C = CubicCoef<F>;
+    float a = __fmaf_rn(C::q3, d, C::q2);
+    a = __fmaf_rn(a, d, C::q1);
+    return __fmaf_rn(a, d, C::q0);
+}
 template <int F>
 __device__ __forceinline__ float k_cubic(float d) {
-    float c3, c2, c0, q3, q2, q1, q0;
-    if (F == F_CATMULL_ROM) {
-        c3 = 1.5f; c2 = -2.5f; c0 = 1.0f; q3 = -0.5f; q2 = 2.5f; q1 = -4.0f; q0 = 2.0f;
-    } else {
-        c3 = 7.0f / 6.0f; c2 = -2.0f; c0 = 8.0f / 9.0f;
-        q3 = -7.0f / 18.0f; q2 = 2.0f; q1 = -10.0f / 3.0f; q0 = 16.0f / 9.0f;
-    }
-    if (d < 1.0f) {
-        const float a = __fmul_rn(__fmaf_rn(c3, d, c2), d);
-        return __fmaf_rn(a, d, c0);
-    }
-    if (d < 2.0f) {
-        float a = __fmaf_rn(q3, d, q2);
-        a = __fmaf_rn(a, d, q1);
-        return __fmaf_rn(a, d, q0);
-    }
+    if (d < 1.0f) return k_cubic_inner<F>(d);
+    if (d < 2.0f) return k_cubic_outer<F>(d);
     return 0.0f;
 }
 
 template <int F>
 __device__ __forceinline__ void axis_weights(float t, float w[4]) {
-    if (F == F_LINEAR) {
+    if constexpr (F == F_LINEAR) {
         w[0] = __fsub_rn(1.0f, t);
         w[1] = t;
-    } else if (F == F_BSPLINE) {
+    } else if constexpr (F == F_BSPLINE) {
         // the listing's polynomials in Horner form with fused multiply-adds:
         //   (1-t)^3, t^2 (3t - 6) + 4, t (t (3 - 3t) + 3) + 1, t^3, each times 1/6
         const float s = 1.0f / 6.0f;
@@ -144,10 +152,17 @@ __device__ __forceinline__ void axis_weights(float t, float w[4]) {
         w[2] = __fmul_rn(s, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-3.0f, t, 3.0f), 3.0f), 1.0f));
         w[3] = __fmul_rn(s, __fmul_rn(t2, t));
     } else {
-        w[0] = k_cubic<F>(__fadd_rn(1.0f, t));
-        w[1] = k_cubic<F>(t);
-        w[2] = k_cubic<F>(__fsub_rn(1.0f, t));
-        w[3] = k_cubic<F>(__fsub_rn(2.0f, t));
+        // k_cubic at the four distances without its branches: for t in [0, 1] the
+        // distances 1+t and 2-t lie in [1, 2] (outer piece, or 0 where they round to 2)
+        // and t, 1-t in [0, 1] (inner piece, or the outer piece's value at 1 where they
+        // reach 1), so each tap needs one polynomial, a compare and a select; the values
+        // equal k_cubic's bit for bit
+        const float k1 = k_cubic<F>(1.0f);
+        const float d0 = __fadd_rn(1.0f, t), d2 = __fsub_rn(1.0f, t), d3 = __fsub_rn(2.0f, t);
+        w[0] = d0 < 2.0f ? k_cubic_outer<F>(d0) : 0.0f;
+        w[1] = t < 1.0f ? k_cubic_inner<F>(t) : k1;
+        w[2] = d2 < 1.0f ? k_cubic_inner<F>(d2) : k1;
+        w[3] = d3 < 2.0f ? k_cubic_outer<F>(d3) : 0.0f;
     }
 }
 
@@ -168,6 +183,28 @@ __device__ __forceinline__ int cdf_pick(const float w[4], float xi, int cls, flo
     int k = N - 1;
 #pragma unroll
     for (int j = N - 2; j >= 0; --j) k = (target < c[j]) ? j : k;
+    return k;
+}
+
+// cdf_pick over all taps (class 0) that also reports whether the picked weight is negative,
+// selected in the same compare chain as the index
+template <int N>
+__device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* total, bool* neg) {
+    float c[N];
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) { acc = __fadd_rn(acc, fabsf(w[k])); c[k] = acc; }
+    *total = acc;
+    const float target = __fmul_rn(xi, acc);
+    int k = N - 1;
+    bool ng = w[N - 1] < 0.0f;
+#pragma unroll
+    for (int j = N - 2; j >= 0; --j) {
+        const bool hit = target < c[j];
+        k = hit ? j : k;
+        ng = hit ? (w[j] < 0.0f) : ng;
+    }
+    *neg = ng;
     return k;
 }
 
@@ -239,7 +276,7 @@ __device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst&
     const float sl = 1.0f + xl, sv = 1.0f + xv;
     const float Ll = __fdividef(0.5f * xl, fmaf(sl, rsqrtf(sl), 1.0f));
     const float Lv = __fdividef(0.5f * xv, fmaf(sv, rsqrtf(sv), 1.0f));
-    const float G = __frcp_rn(1.0f + Ll + Lv);
+    const float G = __fdividef(1.0f, 1.0f + Ll + Lv);
     const float spec = __fdividef(D * G * C.F, 4.0f * nv);
     const float kd = nl * 0.318309886183790672f;
     return make_float3(fmaf(m.rho.x, kd, spec), fmaf(m.rho.y, kd, spec), fmaf(m.rho.z, kd, spec));
@@ -253,9 +290,19 @@ __device__ __forceinline__ float3 shade(int sh, const Material& m, const ShadeCo
 // ---------------------------------------------------------------- texel decode
 // RGBA8 material texel packed with its RG8 normal into 8 bytes (uint2):
 //   x = albedo R | G<<8 | B<<16 | roughness byte<<24, y = normal X | Y<<8, has_normal flag
+// Byte j of w as the float 2^23 + byte (one byte permute into the bits of 2^23).
+__device__ __forceinline__ float byte_plus_2p23(uint32_t w, uint32_t j) {
+    return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7540u | j));
+}
+// byte j of w times k, rounded once: the fused (2^23 + b) k - 2^23 k is exactly b k
+// (2^23 k is exact), so this equals the FP32 product (float)b * k
+__device__ __forceinline__ float byte_times(uint32_t w, uint32_t j, float k) {
+    return __fmaf_rn(byte_plus_2p23(w, j), k, -8388608.0f * k);
+}
 __device__ __forceinline__ float3 decode_normal_rg8(uint32_t xy) {
-    const float X = (float)(int)(2u * (xy & 0xFFu)) - 255.0f;
-    const float Y = (float)(int)(2u * ((xy >> 8) & 0xFFu)) - 255.0f;
+    // 2b - 255 exactly: (2^23 + b) - (2^23 + 127) = b - 127, then 2 (b - 127) - 1
+    const float X = __fmaf_rn(2.0f, __fsub_rn(byte_plus_2p23(xy, 0), 8388735.0f), -1.0f);
+    const float Y = __fmaf_rn(2.0f, __fsub_rn(byte_plus_2p23(xy, 1), 8388735.0f), -1.0f);
     const float R = fmaxf(0.0f, 65025.0f - X * X - Y * Y);          // exact integer radicand
     const float Z = R > 0.0f ? R * rsqrtf(R) : 0.0f;
     const float inv = rsqrtf(X * X + Y * Y + Z * Z);
@@ -264,9 +311,8 @@ __device__ __forceinline__ float3 decode_normal_rg8(uint32_t xy) {
 __device__ __forceinline__ Material decode_rgba8(uint2 t, bool has_normal) {
     Material m;
     const float k = 1.0f / 255.0f;
-    m.rho = make_float3((float)(t.x & 0xFFu) * k, (float)((t.x >> 8) & 0xFFu) * k,
-                        (float)((t.x >> 16) & 0xFFu) * k);
-    m.rough = fmaf(0.95f, (float)(t.x >> 24) * k, 0.05f);
+    m.rho = make_float3(byte_times(t.x, 0, k), byte_times(t.x, 1, k), byte_times(t.x, 2, k));
+    m.rough = fmaf(0.95f, byte_times(t.x, 3, k), 0.05f);
     m.n = has_normal ? decode_normal_rg8(t.y) : make_float3(0.f, 0.f, 1.f);
     return m;
 }

@@ -57,6 +57,7 @@ struct MarchArgs {
 struct NeuralView {
     int tex_res;
     int res[4];
+    float gscale[4];            // res[g] / tex_res, FP32-rounded on the host (IEEE division)
     uint64_t lat_off[4];        // element offset of each grid (same in every latent format)
     int latent_fmt;             // inference latents: 0 FP16, 1 FP8 E4M3 x scale
     const __half* lat16;

@@ -170,6 +170,22 @@ def test_host_entry_point_matches_device(ctx, material):
     assert np.array_equal(pk2, pk)
 
 
+@pytest.mark.parametrize("filter,flags", [("bspline", 0), ("mitchell", 2)])
+def test_host_entry_point_chunked(ctx, material, filter, flags):
+    # enough queries (with picks at 8 spp) that the host path pipelines several chunks over
+    # its lanes, the last one ragged; query ids stay global, so every result and pick equals
+    # the one-launch device path bit for bit
+    h, _, _ = material
+    q = synth.queries_uniform(1_500_001, 23, res=256, lod_range=5.0)
+    dev, pk = _run(ctx, h, q, filter, "stochastic", 8, seed=4, flags=flags, id_base=77)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    r, g, b, pk2 = ctx.filter_shade_host(h, f(q.u), f(q.v), [f(q.dudx), f(q.dvdx), f(q.dudy), f(q.dvdy)],
+                                         filter, "stochastic", "ggx", 8, 4, flags=flags, id_base=77,
+                                         want_picks=True)
+    assert np.array_equal(np.stack([r, g, b], 1).astype(np.float64), dev)
+    assert np.array_equal(pk2, pk)
+
+
 # ---------------------------------------------------------------- full size, sampled
 @pytest.mark.parametrize("filter", ["linear", "bspline", "mitchell"])
 def test_full_size_sampled(ctx, filter):
