@@ -17,7 +17,8 @@ namespace stf {
 // decoding are separate so that a sample's load can be issued before the previous
 // sample is shaded.
 __device__ __forceinline__ uint4 load_texel(const FetchCtx& T, int lvl, int ix, int iy) {
-    const size_t idx = (size_t)iy * (size_t)T.w[lvl] + (size_t)ix;
+    // a level has at most 16384^2 = 2^28 texels: the index fits 32 bits
+    const uint32_t idx = (uint32_t)iy * (uint32_t)T.w[lvl] + (uint32_t)ix;
     if (T.fmt == FMT_RGBA32F) return __ldg(reinterpret_cast<const uint4*>(T.base + T.off[lvl]) + idx);
     const uint2 t = __ldg(reinterpret_cast<const uint2*>(T.base + T.off[lvl]) + idx);
     return make_uint4(t.x, t.y, 0u, 0u);
@@ -69,13 +70,16 @@ __device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, co
 }
 
 // One query: all its samples, written to a.r/g/b[q].  T is the texture (a kernel
-// parameter, or a descriptor in global memory for the bindless table).
-template <int FILTER, int MODE>
+// parameter, or a descriptor in global memory for the bindless table).  PLAIN: the call has
+// no flags and reports no picks, so those per-sample tests are compiled out.
+template <int FILTER, int MODE, bool PLAIN = false>
 __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                                            const RoundKeys& K, uint64_t q) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
     const float inv_spp = 1.0f / (float)a.spp;
     const int kside = a.kside;
+    const uint32_t flags = PLAIN ? 0u : a.flags;
+    uint32_t* const picks = PLAIN ? nullptr : a.picks;
     {
         const float u = a.u[q], v = a.v[q];
         float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f;
@@ -91,7 +95,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
         const uint64_t id = a.id_base + q;
         const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
         float3 acc = make_float3(0.f, 0.f, 0.f);
-        const bool lat = (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) && (a.flags & FLAG_LATTICE);
+        const bool lat = (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) && (flags & FLAG_LATTICE);
         I5 LA{}, LB{};
         if (lat) {   // per-query lattice offsets of the pick uniforms
             LA = ints5(philox(id_lo, id_hi, 0xFFFFFFFFu, 0u, K));
@@ -109,10 +113,10 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                     for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
                 }
                 float x = u, y = v;
-                if (a.has_derivs) jitter(s, kside, a.flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
+                if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
                 int lvl = l0 + ((A.u[2] < fr) ? 1 : 0);
                 float ru = A.u[2];                 // FLAG_REUSE: one uniform, remapped per decision
-                if (a.flags & FLAG_REUSE) {
+                if (flags & FLAG_REUSE) {
                     float r2;
                     lvl = l0 + level_reuse(A.u[2], fr, &r2);
                     ru = r2;
@@ -126,7 +130,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 float Sx, Sy;
                 int kx, ky;
                 bool nx = false, ny = false;     // sign of the picked weight per axis
-                if (a.flags & FLAG_REUSE) {
+                if (flags & FLAG_REUSE) {
                     float uy, dummy;
                     kx = cdf_pick_reuse<NT>(wx, ru, &uy);
                     ky = cdf_pick_reuse<NT>(wy, uy, &dummy);
@@ -153,8 +157,8 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                     if (nx != ny) Wt = -Wt;
                 }
                 *wt = Wt;
-                if (a.picks) {
-                    uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                if (picks) {
+                    uint32_t* pk = picks + (q * a.spp + s) * 2;
                     pk[0] = pack_pick(lvl, ix, iy);
                     pk[1] = NO_PICK;
                 }
@@ -179,7 +183,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
             }
             float x = u, y = v;
-            if (a.has_derivs) jitter(s, kside, a.flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
+            if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
             float3 est;
             if (MODE == M_POSITIVIZED) {
                 const int lvl = min(l0 + ((A.u[2] < fr) ? 1 : 0), T.levels - 1);
@@ -224,8 +228,8 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                     est.y = fmaf(-Wn, g.y, est.y);
                     est.z = fmaf(-Wn, g.z, est.z);
                 }
-                if (a.picks) {
-                    uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                if (picks) {
+                    uint32_t* pk = picks + (q * a.spp + s) * 2;
                     pk[0] = pack_pick(lvl, ix, iy);
                     pk[1] = negpick;
                 }
@@ -285,8 +289,8 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 } else {
                     est = fsum;
                 }
-                if (a.picks) {
-                    uint32_t* pk = a.picks + (q * a.spp + s) * 2;
+                if (picks) {
+                    uint32_t* pk = picks + (q * a.spp + s) * 2;
                     pk[0] = NO_PICK;
                     pk[1] = NO_PICK;
                 }
@@ -299,12 +303,12 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
     }
 }
 
-template <int FILTER, int MODE>
-__global__ void __launch_bounds__(256, 4)
+template <int FILTER, int MODE, bool PLAIN>
+__global__ void __launch_bounds__(256, PLAIN ? 5 : 4)
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
          i += (uint64_t)gridDim.x * blockDim.x)
-        query_body<FILTER, MODE>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
+        query_body<FILTER, MODE, PLAIN>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
 }
 
 // Bindless persistent launch: one grid sized to the SMs; each block claims the next
@@ -336,22 +340,48 @@ k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint
     }
 }
 
-template <int FILTER, int MODE>
-static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
-                             int grid, cudaStream_t st) {
-    k_filter_shade<FILTER, MODE><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
+// Blocks of 256 threads one SM keeps resident for an instantiation (queried once).
+template <int FILTER, int MODE, bool PLAIN>
+static int resident_blocks() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_filter_shade<FILTER, MODE, PLAIN>, 256, 0);
+        per_sm = b > 0 ? b : 1;
+    }
+    return per_sm;
+}
+
+// One wave: the grid is the resident block count of every SM (or fewer blocks for a small
+// call), and the threads stride over the queries.
+template <int FILTER, int MODE, bool PLAIN>
+static cudaError_t launch_one(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, int num_sms,
+                              cudaStream_t st) {
+    const uint64_t blocks_needed = (a.n + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms * resident_blocks<FILTER, MODE, PLAIN>();
+    const int grid = (int)(blocks_needed < cap ? (blocks_needed ? blocks_needed : 1) : cap);
+    k_filter_shade<FILTER, MODE, PLAIN><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
     return cudaGetLastError();
+}
+
+template <int FILTER, int MODE>
+static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, int num_sms,
+                             cudaStream_t st) {
+    if constexpr (MODE == M_STOCHASTIC) {
+        if (a.flags == 0 && a.picks == nullptr) return launch_one<FILTER, MODE, true>(a, T, SC, num_sms, st);
+    }
+    return launch_one<FILTER, MODE, false>(a, T, SC, num_sms, st);
 }
 
 template <int FILTER>
 static cudaError_t launch_f(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
-                            int grid, cudaStream_t st) {
+                            int num_sms, cudaStream_t st) {
     switch (a.mode) {
-        case M_NTAP_BEFORE: return launch_fm<FILTER, M_NTAP_BEFORE>(a, T, SC, grid, st);
-        case M_NTAP_AFTER: return launch_fm<FILTER, M_NTAP_AFTER>(a, T, SC, grid, st);
-        case M_STOCHASTIC: return launch_fm<FILTER, M_STOCHASTIC>(a, T, SC, grid, st);
+        case M_NTAP_BEFORE: return launch_fm<FILTER, M_NTAP_BEFORE>(a, T, SC, num_sms, st);
+        case M_NTAP_AFTER: return launch_fm<FILTER, M_NTAP_AFTER>(a, T, SC, num_sms, st);
+        case M_STOCHASTIC: return launch_fm<FILTER, M_STOCHASTIC>(a, T, SC, num_sms, st);
         case M_POSITIVIZED:
-            if constexpr (is_signed(FILTER)) return launch_fm<FILTER, M_POSITIVIZED>(a, T, SC, grid, st);
+            if constexpr (is_signed(FILTER)) return launch_fm<FILTER, M_POSITIVIZED>(a, T, SC, num_sms, st);
             return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
@@ -418,14 +448,11 @@ cudaError_t launch_filter_shade_table(const FilterShadeArgs& a, const FetchCtx* 
 cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int num_sms, cudaStream_t st) {
     const FetchCtx T = make_fetch_ctx(tv);
     const ShadeConst SC = make_shade_const();
-    const uint64_t blocks_needed = (a.n + 255) / 256;
-    const uint64_t cap = (uint64_t)num_sms * 8;
-    const int grid = (int)(blocks_needed < cap ? (blocks_needed ? blocks_needed : 1) : cap);
     switch (a.filter) {
-        case F_LINEAR: return launch_f<F_LINEAR>(a, T, SC, grid, st);
-        case F_BSPLINE: return launch_f<F_BSPLINE>(a, T, SC, grid, st);
-        case F_CATMULL_ROM: return launch_f<F_CATMULL_ROM>(a, T, SC, grid, st);
-        case F_MITCHELL: return launch_f<F_MITCHELL>(a, T, SC, grid, st);
+        case F_LINEAR: return launch_f<F_LINEAR>(a, T, SC, num_sms, st);
+        case F_BSPLINE: return launch_f<F_BSPLINE>(a, T, SC, num_sms, st);
+        case F_CATMULL_ROM: return launch_f<F_CATMULL_ROM>(a, T, SC, num_sms, st);
+        case F_MITCHELL: return launch_f<F_MITCHELL>(a, T, SC, num_sms, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -23,6 +23,45 @@ namespace stf {
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Packed FP32 pairs (lo, hi) in one 64-bit register pair: the .f32x2 forms of mul, add and
+// fma round each lane to nearest like the scalar instructions, so a pair operation equals
+// two scalar ones bit for bit at half the issue cost.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t r) {
+    float2 f;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+    return f;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// BF16 pair (lo in the low half) of a packed FP32 pair, round to nearest; with RELU,
+// negative values become 0 (ReLU then rounding equals rounding then ReLU)
+template <bool RELU>
+__device__ __forceinline__ uint32_t bf16x2_of(uint64_t v) {
+    const float2 f = upk2(v);
+    uint32_t r;
+    if (RELU) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f.y), "f"(f.x));
+    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f.y), "f"(f.x));
+    return r;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -114,49 +153,60 @@ __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, 
     return t;
 }
 
-// 8 latent channels of one grid texel as floats (FP16, FP8 x scale, or FP32 master)
-__device__ __forceinline__ void load_latent8(const NeuralView& N, int fmt, int g, int x, int y, float v[8]) {
+// 8 latent channels of one grid texel as 4 packed FP32 pairs (FP16, FP8 x scale, or FP32
+// master latents); every value is exact in FP32
+__device__ __forceinline__ void load_latent8(const NeuralView& N, int fmt, int g, int x, int y, uint64_t v[4]) {
     const size_t o = ((size_t)y * N.res[g] + x) * 8;
     if (fmt == 0) {
         const uint4 q = __ldg(reinterpret_cast<const uint4*>(N.lat16 + N.lat_off[g] + o));
         const __half2* h = reinterpret_cast<const __half2*>(&q);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { const float2 f = __half22float2(h[i]); v[2 * i] = f.x; v[2 * i + 1] = f.y; }
+        for (int i = 0; i < 4; ++i) { const float2 f = __half22float2(h[i]); v[i] = pk2(f.x, f.y); }
     } else if (fmt == 1) {
         const uint2 q = __ldg(reinterpret_cast<const uint2*>(N.lat8 + N.lat_off[g] + o));
         const uint8_t* b = reinterpret_cast<const uint8_t*>(&q);
-        const float sc = N.scale[g];
+        const uint64_t sc = pk2(N.scale[g], N.scale[g]);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            __nv_fp8_e4m3 e;
-            e.__x = b[i];
-            v[i] = __fmul_rn((float)e, sc);
+        for (int i = 0; i < 4; ++i) {
+            __nv_fp8_e4m3 e0, e1;
+            e0.__x = b[2 * i];
+            e1.__x = b[2 * i + 1];
+            v[i] = mul2(pk2((float)e0, (float)e1), sc);
         }
     } else {
         const float4* p = reinterpret_cast<const float4*>(N.lat32 + N.lat_off[g] + o);
         const float4 a = p[0], b = p[1];
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        v[0] = pk2(a.x, a.y); v[1] = pk2(a.z, a.w); v[2] = pk2(b.x, b.y); v[3] = pk2(b.z, b.w);
     }
 }
 
-__device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, int iy, float f[32]) {
+// 32 features as 16 packed pairs: per grid and channel, w00 a + w10 b + w01 c + w11 d in
+// this order, each step one rounding (the oracle's order)
+__device__ __forceinline__ void features2(const NeuralView& N, int fmt, int ix, int iy, uint64_t f[16]) {
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const LTap t = latent_taps(N, g, ix, iy);
-        float a[8], b[8], c[8], d[8];
+        uint64_t a[4], b[4], c[4], d[4];
         load_latent8(N, fmt, g, t.x0, t.y0, a);
         load_latent8(N, fmt, g, t.x1, t.y0, b);
         load_latent8(N, fmt, g, t.x0, t.y1, c);
         load_latent8(N, fmt, g, t.x1, t.y1, d);
+        const uint64_t w00 = pk2(t.w00, t.w00), w10 = pk2(t.w10, t.w10);
+        const uint64_t w01 = pk2(t.w01, t.w01), w11 = pk2(t.w11, t.w11);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            float v = __fmul_rn(t.w00, a[k]);
-            v = __fmaf_rn(t.w10, b[k], v);
-            v = __fmaf_rn(t.w01, c[k], v);
-            v = __fmaf_rn(t.w11, d[k], v);
-            f[8 * g + k] = v;
+        for (int k = 0; k < 4; ++k) {
+            uint64_t v = mul2(w00, a[k]);
+            v = fma2(w10, b[k], v);
+            v = fma2(w01, c[k], v);
+            f[4 * g + k] = fma2(w11, d[k], v);
         }
     }
+}
+__device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, int iy, float f[32]) {
+    uint64_t p[16];
+    features2(N, fmt, ix, iy, p);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) { const float2 v = upk2(p[i]); f[2 * i] = v.x; f[2 * i + 1] = v.y; }
 }
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -167,14 +217,14 @@ __device__ __forceinline__ Material material_from_channels(const float y[8]) {
     m.rho = make_float3(__saturatef(y[0]), __saturatef(y[1]), __saturatef(y[2]));
     m.rough = fmaf(0.95f, __saturatef(y[3]), 0.05f);
     const float x = fmaf(2.0f, __saturatef(y[4]), -1.0f), yy = fmaf(2.0f, __saturatef(y[5]), -1.0f);
-    const float z2 = fmaxf(0.0f, 1.0f - x * x - yy * yy);
-    const float z = z2 > 0.0f ? z2 * rsqrtf(z2) : 0.0f;
-    const float l2 = x * x + yy * yy + z * z;
-    if (l2 > 0.0f) {
-        const float inv = rsqrtf(l2);
-        m.n = make_float3(x * inv, yy * inv, z * inv);
+    const float z2 = 1.0f - x * x - yy * yy;
+    // z2 > 0: (x, y, sqrt z2) is a unit vector already; otherwise z = 0 and (x, y), which is
+    // then at least unit length, is normalised
+    if (z2 > 0.0f) {
+        m.n = make_float3(x, yy, z2 * rsqrt_approx(z2));
     } else {
-        m.n = make_float3(0.f, 0.f, 1.f);
+        const float inv = rsqrt_approx(x * x + yy * yy);
+        m.n = make_float3(x * inv, yy * inv, 0.0f);
     }
     return m;
 }
@@ -393,7 +443,7 @@ struct __align__(128) DecodeSmem {
     float bias[64 + 64 + 16];
     float ch[NT_ROWS][9];             // decoded channels per row
     float wt[NT_ROWS];                // row weight
-    long long pair[NT_ROWS];          // (query, sample) pair of the row, -1 = idle
+    long long pair[NT_ROWS];          // query of the row's (query, sample) pair, -1 = idle
     uint64_t bar;
     uint32_t tmem;
     int abort_flag;
@@ -409,19 +459,35 @@ __device__ __forceinline__ void stage_weights(uint8_t* dst, const __nv_bfloat16*
     }
 }
 
-// Row generation for the filter modes: row -> (pair, texel, weight).
-struct RowOut { long long pair; int ix, iy; float w; };
+// Rows per (query, sample) pair: 1 (stochastic), 2 (positivized), NT x NT (N-tap).  They
+// divide the 128-row tile, so a pair's rows form an aligned group inside one tile.
+template <int FILTER, int MODE>
+__host__ __device__ constexpr int rows_per_pair() {
+    return (MODE == M_STOCHASTIC) ? 1 : (MODE == M_POSITIVIZED ? 2 : ntaps(FILTER) * ntaps(FILTER));
+}
+
+// Row generation for the filter modes: row -> (query, texel, weight); query -1 = idle.
+struct RowOut { long long query; int ix, iy; float w; };
 
 template <int FILTER, int MODE>
 __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const RoundKeys& K, uint64_t row) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
-    constexpr int NR = (MODE == M_STOCHASTIC) ? 1 : (MODE == M_POSITIVIZED ? 2 : NT * NT);
+    constexpr int NR = rows_per_pair<FILTER, MODE>();
     RowOut o{-1, 0, 0, 0.0f};
     const uint64_t pair = row / NR;
     const int j = (int)(row % NR);
-    if (pair >= a.n * (uint64_t)a.spp) return o;
-    const uint64_t q = pair / a.spp;
-    const uint32_t s = (uint32_t)(pair % a.spp);
+    const uint64_t npairs = a.n * (uint64_t)a.spp;
+    if (pair >= npairs) return o;
+    uint64_t q;
+    uint32_t s;
+    if (npairs <= 0xFFFFFFFFull) {        // 32-bit division (the 64-bit one is a long sequence)
+        const uint32_t p32 = (uint32_t)pair;
+        q = p32 / a.spp;
+        s = p32 - (uint32_t)q * a.spp;
+    } else {
+        q = pair / a.spp;
+        s = (uint32_t)(pair - q * a.spp);
+    }
     const uint64_t id = a.id_base + q;
     const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
     const U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
@@ -436,7 +502,7 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     float wx[4], wy[4];
     axis_weights<FILTER>(ax.t, wx);
     axis_weights<FILTER>(ay.t, wy);
-    o.pair = (long long)pair;
+    o.query = (long long)q;
     if (MODE == M_STOCHASTIC) {
         float Sx, Sy;
         bool nx = false, ny = false;
@@ -510,20 +576,18 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                 ix = a.ex_ix[row]; iy = a.ex_iy[row]; pr = (long long)row; w = 1.0f;
             } else {
                 const RowOut r = make_row<FILTER, MODE>(a, K, row);
-                ix = r.ix; iy = r.iy; pr = r.pair; w = r.w;
+                ix = r.ix; iy = r.iy; pr = r.query; w = r.w;
             }
         }
         S.pair[t] = pr;
         S.wt[t] = w;
-        float f[32];
-        features(N, N.latent_fmt, ix, iy, f);
+        uint64_t f[16];
+        features2(N, N.latent_fmt, ix, iy, f);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            __nv_bfloat162 p[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(f[8 * c + 2 * i], f[8 * c + 2 * i + 1]);
-            *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 32)) = *reinterpret_cast<uint4*>(p);
-        }
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 32)) =
+                make_uint4(bf16x2_of<false>(f[4 * c]), bf16x2_of<false>(f[4 * c + 1]),
+                           bf16x2_of<false>(f[4 * c + 2]), bf16x2_of<false>(f[4 * c + 3]));
         // ---- three GEMM layers
 #pragma unroll 1
         for (int layer = 0; layer < 3; ++layer) {
@@ -561,20 +625,21 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
 #pragma unroll
                 for (int c = 0; c < 4; ++c) tmem_ld16(tmem + lane_base + col + 16 * c, r[c]);
                 tmem_wait_ld();
-                const float4* bias4 = reinterpret_cast<const float4*>(S.bias + (layer == 0 ? 0 : 64));
+                // bias (FP32 pairs), ReLU and BF16 rounding of 8 columns at a time
+                const ulonglong2* bias2 = reinterpret_cast<const ulonglong2*>(S.bias + (layer == 0 ? 0 : 64));
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float4 ba = bias4[2 * c], bb = bias4[2 * c + 1];
-                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                    __nv_bfloat162 p[4];
+                    const ulonglong2 ba = bias2[2 * c], bb = bias2[2 * c + 1];
+                    const uint64_t bv[4] = {ba.x, ba.y, bb.x, bb.y};
+                    uint32_t p[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int k0 = 8 * c + 2 * i;
-                        const float z0 = __uint_as_float(r[k0 >> 4][k0 & 15]) + bv[2 * i];
-                        const float z1 = __uint_as_float(r[(k0 + 1) >> 4][(k0 + 1) & 15]) + bv[2 * i + 1];
-                        p[i] = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+                        const uint64_t z = add2(pk2(__uint_as_float(r[k0 >> 4][k0 & 15]),
+                                                    __uint_as_float(r[(k0 + 1) >> 4][(k0 + 1) & 15])), bv[i]);
+                        p[i] = bf16x2_of<true>(z);
                     }
-                    *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 64)) = *reinterpret_cast<uint4*>(p);
+                    *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 64)) = make_uint4(p[0], p[1], p[2], p[3]);
                 }
             } else {
                 uint32_t r[16];
@@ -593,20 +658,19 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                 for (int i = 0; i < 8; ++i) a.y_out[row * 8 + i] = S.ch[t][i];
             }
         } else {
-            // one thread per (query, sample) pair (its rows are contiguous within the tile,
-            // because the rows per pair, 1, 2, 4 or 16, divide 128)
-            const long long p = S.pair[t];
-            const bool head = p >= 0 && (t == 0 || S.pair[t - 1] != p);
-            if (head) {
+            // one thread per (query, sample) pair: the first row of its aligned group
+            constexpr int NR = rows_per_pair<FILTER, MODE>();
+            const long long qq = S.pair[t];
+            if (qq >= 0 && t % NR == 0) {
                 float est[3] = {0.f, 0.f, 0.f};
                 if constexpr (MODE == M_NTAP_BEFORE) {
                     float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    for (int r = t; r < NT_ROWS && S.pair[r] == p; ++r)
+                    for (int r = t; r < t + NR; ++r)
                         for (int i = 0; i < 8; ++i) c[i] = fmaf(S.wt[r], S.ch[r][i], c[i]);
                     const float3 f3 = shade(a.shade, material_from_channels(c), SC);
                     est[0] = f3.x; est[1] = f3.y; est[2] = f3.z;
                 } else {
-                    for (int r = t; r < NT_ROWS && S.pair[r] == p; ++r) {
+                    for (int r = t; r < t + NR; ++r) {
                         if (S.wt[r] == 0.0f) continue;
                         const float3 f3 = shade(a.shade, material_from_channels(S.ch[r]), SC);
                         est[0] = fmaf(S.wt[r], f3.x, est[0]);
@@ -614,7 +678,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
                         est[2] = fmaf(S.wt[r], f3.z, est[2]);
                     }
                 }
-                const uint64_t q = (uint64_t)p / a.spp;
+                const uint64_t q = (uint64_t)qq;
                 const float inv = 1.0f / (float)a.spp;
                 atomicAdd(a.r + q, est[0] * inv);
                 atomicAdd(a.g + q, est[1] * inv);

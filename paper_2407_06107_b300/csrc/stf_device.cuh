@@ -262,22 +262,41 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+// Approximate reciprocal and reciprocal square root: one MUFU instruction each, flushing
+// subnormals.  Used only in shading and decoding, whose results carry a tolerance, never in
+// a decision.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // f_hat = [rho/pi + D G2 F / (4 nl nv)] nl  (GGX, height-correlated Smith, Schlick)
 __device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst& C) {
     const float nl = dot3(m.n, C.l), nv = dot3(m.n, C.v);
     if (!(nl > 0.0f) || !(nv > 0.0f)) return make_float3(0.f, 0.f, 0.f);
     const float a = fminf(fmaxf(m.rough, 0.05f), 1.0f), a2 = a * a;
-    const float3 nxh = cross3(m.n, C.h), nxl = cross3(m.n, C.l), nxv = cross3(m.n, C.v);
+    const float3 nxh = cross3(m.n, C.h);
     const float nh = dot3(m.n, C.h);
+    // |n x h|^2 instead of 1 - (n.h)^2: D = a2 / (pi q^2) is relative to q >= a2 (n.h)^2,
+    // so the cancellation of 1 - (n.h)^2 near n = h would show in D
     const float q = fmaf(a2 * nh, nh, dot3(nxh, nxh));
-    const float D = __fdividef(a2 * 0.318309886183790672f, q * q);
-    // Lambda = (sqrt(1 + a2 tan^2) - 1)/2 written without cancellation: x / (2 (sqrt(1+x)+1))
-    const float xl = __fdividef(a2 * dot3(nxl, nxl), nl * nl), xv = __fdividef(a2 * dot3(nxv, nxv), nv * nv);
+    const float rq = rcp_approx(q), rnl = rcp_approx(nl), rnv = rcp_approx(nv);
+    const float D = a2 * 0.318309886183790672f * rq * rq;
+    // Lambda = (sqrt(1 + a2 tan^2) - 1) / 2 with sin^2 = 1 - (n.w)^2 (|n| = 1): G2 =
+    // 1 / (1 + Ll + Lv) only sees absolute errors of Lambda, which the two subtractions
+    // keep at a few ulp of 1
+    const float xl = a2 * fmaf(-nl, nl, 1.0f) * rnl * rnl, xv = a2 * fmaf(-nv, nv, 1.0f) * rnv * rnv;
     const float sl = 1.0f + xl, sv = 1.0f + xv;
-    const float Ll = __fdividef(0.5f * xl, fmaf(sl, rsqrtf(sl), 1.0f));
-    const float Lv = __fdividef(0.5f * xv, fmaf(sv, rsqrtf(sv), 1.0f));
-    const float G = __fdividef(1.0f, 1.0f + Ll + Lv);
-    const float spec = __fdividef(D * G * C.F, 4.0f * nv);
+    const float Ll = 0.5f * fmaf(sl, rsqrt_approx(sl), -1.0f);
+    const float Lv = 0.5f * fmaf(sv, rsqrt_approx(sv), -1.0f);
+    const float G = rcp_approx(1.0f + Ll + Lv);
+    const float spec = D * G * C.F * 0.25f * rnv;
     const float kd = nl * 0.318309886183790672f;
     return make_float3(fmaf(m.rho.x, kd, spec), fmaf(m.rho.y, kd, spec), fmaf(m.rho.z, kd, spec));
 }
@@ -303,10 +322,14 @@ __device__ __forceinline__ float3 decode_normal_rg8(uint32_t xy) {
     // 2b - 255 exactly: (2^23 + b) - (2^23 + 127) = b - 127, then 2 (b - 127) - 1
     const float X = __fmaf_rn(2.0f, __fsub_rn(byte_plus_2p23(xy, 0), 8388735.0f), -1.0f);
     const float Y = __fmaf_rn(2.0f, __fsub_rn(byte_plus_2p23(xy, 1), 8388735.0f), -1.0f);
-    const float R = fmaxf(0.0f, 65025.0f - X * X - Y * Y);          // exact integer radicand
-    const float Z = R > 0.0f ? R * rsqrtf(R) : 0.0f;
-    const float inv = rsqrtf(X * X + Y * Y + Z * Z);
-    return make_float3(X * inv, Y * inv, Z * inv);
+    const float R = 65025.0f - X * X - Y * Y;                        // exact integer radicand
+    // R > 0: |(X, Y, sqrt R)| = 255 exactly; otherwise z = 0 and (X, Y) is normalised
+    if (R > 0.0f) {
+        const float k = 1.0f / 255.0f;
+        return make_float3(X * k, Y * k, R * rsqrt_approx(R) * k);
+    }
+    const float inv = rsqrt_approx(X * X + Y * Y);
+    return make_float3(X * inv, Y * inv, 0.0f);
 }
 __device__ __forceinline__ Material decode_rgba8(uint2 t, bool has_normal) {
     Material m;
