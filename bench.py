@@ -250,11 +250,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# the sources the 2-D filter kernels are compiled from
+FILTER_KERNEL_SOURCES = ("filter_shade.cu", "stf_device.cuh", "stf_kernels.h")
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2407_06107_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in FILTER_KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]

@@ -20,10 +20,13 @@ __device__ __forceinline__ float vox(const MarchArgs& a, int x, int y, int z) {
     return __half2float(a.vox[((size_t)z * a.ny + y) * a.nx + x]);
 }
 
-template <int FILTER, int MODE>
+// PLAIN: no flags and no pick output (the stochastic steps then run in pairs, see below).
+template <int FILTER, int MODE, bool PLAIN>
 __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
     const float res[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
+    const uint32_t flags = PLAIN ? 0u : a.flags;
+    uint32_t* const picks = PLAIN ? nullptr : a.picks;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.pix_count;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t pix = a.pix_begin + i;
@@ -31,9 +34,9 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
         const uint32_t id_lo = (uint32_t)pix, id_hi = (uint32_t)(pix >> 32);
         float acc = 0.0f;
         for (uint32_t s = 0; s < a.spp; ++s) {
-            uint32_t* pk = a.picks ? a.picks + (i * a.spp + s) * a.steps : nullptr;
+            uint32_t* pk = picks ? picks + (i * a.spp + s) * a.steps : nullptr;
             float jx, jy;
-            if (a.flags & FLAG_STRATIFIED) {
+            if (flags & FLAG_STRATIFIED) {
                 jx = __fdiv_rn(__fadd_rn((float)(s % a.kside), 0.5f), (float)a.kside);
                 jy = __fdiv_rn(__fadd_rn((float)(s / a.kside), 0.5f), (float)a.kside);
             } else {
@@ -75,7 +78,41 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
             float P = 1.0f, Pe = 0.0f;              // after: compensated product
             const float sdt = a.sigma_scale * dt;
             uint4 rw = make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t lshift = (a.flags & FLAG_LATTICE) ? lattice_shift(s, a.spp, 21) : 0u;
+            const uint32_t lshift = (flags & FLAG_LATTICE) ? lattice_shift(s, a.spp, 21) : 0u;
+            if constexpr (PLAIN && MODE == M_STOCHASTIC) {
+                // Steps 2p and 2p+1 take their uniforms from the same Philox call: both picks
+                // are made and both voxel loads issued before either density is added, so
+                // two gathers are in flight per thread.
+                auto voxel = [&](uint32_t k, const float uk[3]) -> uint32_t {
+                    const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
+                    int idx[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const AxisPos ap = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
+                        float w[4];
+                        axis_weights<FILTER>(ap.t, w);
+                        const int n = c == 0 ? a.nx : (c == 1 ? a.ny : a.nz);
+                        idx[c] = clamp_index(ap.i0 + T0 + cdf_pick<NT>(w, uk[c], 0, nullptr), n);
+                    }
+                    // at most 1024^3 voxels: the index fits 32 bits
+                    return ((uint32_t)idx[2] * (uint32_t)a.ny + (uint32_t)idx[1]) * (uint32_t)a.nx + (uint32_t)idx[0];
+                };
+                uint32_t k = 0;
+                for (; k + 1 < a.steps; k += 2) {
+                    const uint4 rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
+                    float u0[3], u1[3];
+                    uniforms3_of6(rw, 0, u0);
+                    uniforms3_of6(rw, 1, u1);
+                    const uint32_t v0 = voxel(k, u0), v1 = voxel(k + 1, u1);
+                    const float d0 = __half2float(a.vox[v0]), d1 = __half2float(a.vox[v1]);
+                    fixed_sum += (uint64_t)(d0 * 16777216.0f) + (uint64_t)(d1 * 16777216.0f);
+                }
+                if (k < a.steps) {
+                    float u0[3];
+                    uniforms3_of6(philox(id_lo, id_hi, s, (k >> 1) + 1u, K), 0, u0);
+                    fixed_sum += (uint64_t)(__half2float(a.vox[voxel(k, u0)]) * 16777216.0f);
+                }
+            } else
             for (uint32_t k = 0; k < a.steps; ++k) {
                 const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
                 AxisPos ap[3];
@@ -87,7 +124,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                 if (MODE == M_STOCHASTIC) {
                     // steps 2p and 2p+1 share stream p+1 (six 21-bit uniforms)
                     float uk[3];
-                    if (a.flags & FLAG_LATTICE) {   // per-pixel offsets, shifted lattice over samples
+                    if (flags & FLAG_LATTICE) {   // per-pixel offsets, shifted lattice over samples
                         if ((k & 1u) == 0u) rw = philox(id_lo, id_hi, 0xFFFFFFFFu, (k >> 1) + 1u, K);
                         uint32_t f[3];
                         ints3_of6(rw, (int)(k & 1u), f);
@@ -98,7 +135,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                         uniforms3_of6(rw, (int)(k & 1u), uk);
                     }
                     int kx, ky, kz;
-                    if (a.flags & FLAG_REUSE) {      // x, y, z from one uniform, remapped
+                    if (flags & FLAG_REUSE) {      // x, y, z from one uniform, remapped
                         float r1, r2, r3;
                         kx = cdf_pick_reuse<NT>(w[0], uk[0], &r1);
                         ky = cdf_pick_reuse<NT>(w[1], r1, &r2);
@@ -156,23 +193,39 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
     }
 }
 
-template <int FILTER>
-static cudaError_t launch_f(const MarchArgs& a, int grid, cudaStream_t st) {
-    switch (a.mode) {
-        case M_NTAP_BEFORE: k_march<FILTER, M_NTAP_BEFORE><<<grid, 128, 0, st>>>(a, expand_key(a.seed)); break;
-        case M_NTAP_AFTER: k_march<FILTER, M_NTAP_AFTER><<<grid, 128, 0, st>>>(a, expand_key(a.seed)); break;
-        case M_STOCHASTIC: k_march<FILTER, M_STOCHASTIC><<<grid, 128, 0, st>>>(a, expand_key(a.seed)); break;
-        default: return cudaErrorInvalidValue;
+// One wave: the resident block count of every SM (queried once per instantiation), or
+// fewer blocks for a small call; threads stride over the pixels, which spreads the cheap
+// rays that miss the volume over all threads.
+template <int FILTER, int MODE, bool PLAIN>
+static cudaError_t launch_one(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_march<FILTER, MODE, PLAIN>, 128, 0);
+        per_sm = b > 0 ? b : 1;
     }
+    const uint64_t need = (a.pix_count + 127) / 128;
+    const uint64_t cap = (uint64_t)num_sms * per_sm;
+    const int grid = (int)(need < cap ? (need ? need : 1) : cap);
+    k_march<FILTER, MODE, PLAIN><<<grid, 128, 0, st>>>(a, expand_key(a.seed));
     return cudaGetLastError();
 }
 
+template <int FILTER>
+static cudaError_t launch_f(const MarchArgs& a, int num_sms, cudaStream_t st) {
+    switch (a.mode) {
+        case M_NTAP_BEFORE: return launch_one<FILTER, M_NTAP_BEFORE, false>(a, num_sms, st);
+        case M_NTAP_AFTER: return launch_one<FILTER, M_NTAP_AFTER, false>(a, num_sms, st);
+        case M_STOCHASTIC:
+            if (a.flags == 0 && a.picks == nullptr) return launch_one<FILTER, M_STOCHASTIC, true>(a, num_sms, st);
+            return launch_one<FILTER, M_STOCHASTIC, false>(a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st) {
-    const uint64_t need = (a.pix_count + 127) / 128;
-    const uint64_t cap = (uint64_t)num_sms * 16;
-    const int grid = (int)(need < cap ? (need ? need : 1) : cap);
-    if (a.filter == F_LINEAR) return launch_f<F_LINEAR>(a, grid, st);
-    if (a.filter == F_BSPLINE) return launch_f<F_BSPLINE>(a, grid, st);
+    if (a.filter == F_LINEAR) return launch_f<F_LINEAR>(a, num_sms, st);
+    if (a.filter == F_BSPLINE) return launch_f<F_BSPLINE>(a, num_sms, st);
     return cudaErrorInvalidValue;
 }
 
