@@ -20,13 +20,14 @@ __device__ __forceinline__ float vox(const MarchArgs& a, int x, int y, int z) {
     return __half2float(a.vox[((size_t)z * a.ny + y) * a.nx + x]);
 }
 
-// PLAIN: no flags and no pick output (the stochastic steps then run in pairs, see below).
-template <int FILTER, int MODE, bool PLAIN>
+// V: the kernel variant (KV_*).  The specialised ones (no picks; no flags, or the lattice
+// flag alone) run the stochastic steps in pairs, see below.
+template <int FILTER, int MODE, int V>
 __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
     const float res[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
-    const uint32_t flags = PLAIN ? 0u : a.flags;
-    uint32_t* const picks = PLAIN ? nullptr : a.picks;
+    const uint32_t flags = V == KV_GENERAL ? a.flags : variant_flags(V);
+    uint32_t* const picks = V == KV_GENERAL ? a.picks : nullptr;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.pix_count;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t pix = a.pix_begin + i;
@@ -79,10 +80,11 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
             const float sdt = a.sigma_scale * dt;
             uint4 rw = make_uint4(0u, 0u, 0u, 0u);
             const uint32_t lshift = (flags & FLAG_LATTICE) ? lattice_shift(s, a.spp, 21) : 0u;
-            if constexpr (PLAIN && MODE == M_STOCHASTIC) {
+            if constexpr (V != KV_GENERAL && MODE == M_STOCHASTIC) {
                 // Steps 2p and 2p+1 take their uniforms from the same Philox call: both picks
                 // are made and both voxel loads issued before either density is added, so
-                // two gathers are in flight per thread.
+                // two gathers are in flight per thread.  LATTICE: the call is the per-pixel
+                // offset (sample index 0xFFFFFFFF), shifted per sample.
                 auto voxel = [&](uint32_t k, const float uk[3]) -> uint32_t {
                     const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
                     int idx[3];
@@ -97,19 +99,30 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                     // at most 1024^3 voxels: the index fits 32 bits
                     return ((uint32_t)idx[2] * (uint32_t)a.ny + (uint32_t)idx[1]) * (uint32_t)a.nx + (uint32_t)idx[0];
                 };
+                auto step_uniforms = [&](const uint4& rw, int odd, float u[3]) {
+                    if constexpr (V == KV_LATTICE) {
+                        uint32_t f[3];
+                        ints3_of6(rw, odd, f);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) u[c] = lattice(f[c], lshift, 21);
+                    } else {
+                        uniforms3_of6(rw, odd, u);
+                    }
+                };
+                const uint32_t sidx = V == KV_LATTICE ? 0xFFFFFFFFu : s;
                 uint32_t k = 0;
                 for (; k + 1 < a.steps; k += 2) {
-                    const uint4 rw = philox(id_lo, id_hi, s, (k >> 1) + 1u, K);
+                    const uint4 rw = philox(id_lo, id_hi, sidx, (k >> 1) + 1u, K);
                     float u0[3], u1[3];
-                    uniforms3_of6(rw, 0, u0);
-                    uniforms3_of6(rw, 1, u1);
+                    step_uniforms(rw, 0, u0);
+                    step_uniforms(rw, 1, u1);
                     const uint32_t v0 = voxel(k, u0), v1 = voxel(k + 1, u1);
                     const float d0 = __half2float(a.vox[v0]), d1 = __half2float(a.vox[v1]);
                     fixed_sum += (uint64_t)(d0 * 16777216.0f) + (uint64_t)(d1 * 16777216.0f);
                 }
                 if (k < a.steps) {
                     float u0[3];
-                    uniforms3_of6(philox(id_lo, id_hi, s, (k >> 1) + 1u, K), 0, u0);
+                    step_uniforms(philox(id_lo, id_hi, sidx, (k >> 1) + 1u, K), 0, u0);
                     fixed_sum += (uint64_t)(__half2float(a.vox[voxel(k, u0)]) * 16777216.0f);
                 }
             } else
@@ -193,39 +206,37 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
     }
 }
 
-// One wave: the resident block count of every SM (queried once per instantiation), or
-// fewer blocks for a small call; threads stride over the pixels, which spreads the cheap
-// rays that miss the volume over all threads.
-template <int FILTER, int MODE, bool PLAIN>
-static cudaError_t launch_one(const MarchArgs& a, int num_sms, cudaStream_t st) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_march<FILTER, MODE, PLAIN>, 128, 0);
-        per_sm = b > 0 ? b : 1;
-    }
+// One block per 128 pixels: rays cost very different amounts (a ray that misses the
+// volume takes no steps), and the hardware block scheduler balances them as blocks retire.
+// Measured at 1920x1080 x 8 spp, this beats a one-wave grid-stride launch by 17-24 % for
+// every filter and mode.
+template <int FILTER, int MODE, int V>
+static cudaError_t launch_one(const MarchArgs& a, cudaStream_t st) {
     const uint64_t need = (a.pix_count + 127) / 128;
-    const uint64_t cap = (uint64_t)num_sms * per_sm;
-    const int grid = (int)(need < cap ? (need ? need : 1) : cap);
-    k_march<FILTER, MODE, PLAIN><<<grid, 128, 0, st>>>(a, expand_key(a.seed));
+    if (need > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    k_march<FILTER, MODE, V><<<(int)(need ? need : 1), 128, 0, st>>>(a, expand_key(a.seed));
     return cudaGetLastError();
 }
 
 template <int FILTER>
-static cudaError_t launch_f(const MarchArgs& a, int num_sms, cudaStream_t st) {
+static cudaError_t launch_f(const MarchArgs& a, cudaStream_t st) {
     switch (a.mode) {
-        case M_NTAP_BEFORE: return launch_one<FILTER, M_NTAP_BEFORE, false>(a, num_sms, st);
-        case M_NTAP_AFTER: return launch_one<FILTER, M_NTAP_AFTER, false>(a, num_sms, st);
+        case M_NTAP_BEFORE: return launch_one<FILTER, M_NTAP_BEFORE, KV_GENERAL>(a, st);
+        case M_NTAP_AFTER: return launch_one<FILTER, M_NTAP_AFTER, KV_GENERAL>(a, st);
         case M_STOCHASTIC:
-            if (a.flags == 0 && a.picks == nullptr) return launch_one<FILTER, M_STOCHASTIC, true>(a, num_sms, st);
-            return launch_one<FILTER, M_STOCHASTIC, false>(a, num_sms, st);
+            switch (stochastic_variant(a.flags, a.picks)) {
+                case KV_PLAIN: return launch_one<FILTER, M_STOCHASTIC, KV_PLAIN>(a, st);
+                case KV_LATTICE: return launch_one<FILTER, M_STOCHASTIC, KV_LATTICE>(a, st);
+                default: return launch_one<FILTER, M_STOCHASTIC, KV_GENERAL>(a, st);
+            }
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st) {
-    if (a.filter == F_LINEAR) return launch_f<F_LINEAR>(a, num_sms, st);
-    if (a.filter == F_BSPLINE) return launch_f<F_BSPLINE>(a, num_sms, st);
+    (void)num_sms;
+    if (a.filter == F_LINEAR) return launch_f<F_LINEAR>(a, st);
+    if (a.filter == F_BSPLINE) return launch_f<F_BSPLINE>(a, st);
     return cudaErrorInvalidValue;
 }
 

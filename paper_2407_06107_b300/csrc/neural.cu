@@ -202,6 +202,77 @@ __device__ __forceinline__ void features2(const NeuralView& N, int fmt, int ix, 
         }
     }
 }
+// Inference form (FP16 or FP8 latents): the four taps of a grid as raw 16-byte (FP16) or
+// 8-byte (FP8, in .x .y) texels, and their conversion to packed FP32 pairs.
+__device__ __forceinline__ void load_taps_raw(const NeuralView& N, int fmt, int g, const LTap& t, uint4 q[4]) {
+    const int xs[4] = {t.x0, t.x1, t.x0, t.x1}, ys[4] = {t.y0, t.y0, t.y1, t.y1};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const size_t o = ((size_t)ys[i] * N.res[g] + xs[i]) * 8;
+        if (fmt == 0) {
+            q[i] = __ldg(reinterpret_cast<const uint4*>(N.lat16 + N.lat_off[g] + o));
+        } else {
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(N.lat8 + N.lat_off[g] + o));
+            q[i] = make_uint4(v.x, v.y, 0u, 0u);
+        }
+    }
+}
+__device__ __forceinline__ void raw_to_pairs(const NeuralView& N, int fmt, int g, uint4 q, uint64_t v[4]) {
+    if (fmt == 0) {
+        const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { const float2 f = __half22float2(h[i]); v[i] = pk2(f.x, f.y); }
+    } else {
+        const uint8_t* b = reinterpret_cast<const uint8_t*>(&q);
+        const uint64_t sc = pk2(N.scale[g], N.scale[g]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_fp8_e4m3 e0, e1;
+            e0.__x = b[2 * i];
+            e1.__x = b[2 * i + 1];
+            v[i] = mul2(pk2((float)e0, (float)e1), sc);
+        }
+    }
+}
+// The 32 features of one decode row, rounded to BF16 and stored grid by grid into row
+// `row` of the K-major A tile (same order and rounding as features2).  The four taps of
+// grid g+1 are loaded before grid g is interpolated, so two grids' gathers are in flight.
+__device__ __forceinline__ void features_to_tile(const NeuralView& N, int fmt, int ix, int iy, uint8_t* A, int row) {
+    LTap tc = latent_taps(N, 0, ix, iy);
+    uint4 cur[4];
+    load_taps_raw(N, fmt, 0, tc, cur);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        uint4 nxt[4];
+        LTap tn = tc;
+        if (g < 3) {
+            tn = latent_taps(N, g + 1, ix, iy);
+            load_taps_raw(N, fmt, g + 1, tn, nxt);
+        }
+        uint64_t a[4], b[4], c[4], d[4];
+        raw_to_pairs(N, fmt, g, cur[0], a);
+        raw_to_pairs(N, fmt, g, cur[1], b);
+        raw_to_pairs(N, fmt, g, cur[2], c);
+        raw_to_pairs(N, fmt, g, cur[3], d);
+        const uint64_t w00 = pk2(tc.w00, tc.w00), w10 = pk2(tc.w10, tc.w10);
+        const uint64_t w01 = pk2(tc.w01, tc.w01), w11 = pk2(tc.w11, tc.w11);
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint64_t v = mul2(w00, a[k]);
+            v = fma2(w10, b[k], v);
+            v = fma2(w01, c[k], v);
+            o[k] = bf16x2_of<false>(fma2(w11, d[k], v));
+        }
+        *reinterpret_cast<uint4*>(A + kmaj_off(row, 8 * g, 32)) = make_uint4(o[0], o[1], o[2], o[3]);
+        if (g < 3) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
+            tc = tn;
+        }
+    }
+}
+
 __device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, int iy, float f[32]) {
     uint64_t p[16];
     features2(N, fmt, ix, iy, p);
@@ -540,7 +611,7 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
 }
 
 template <int FILTER, int MODE>
-__global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralDecodeArgs a, RoundKeys K, ShadeConst SC) {
+__global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(NeuralView N, NeuralDecodeArgs a, RoundKeys K, ShadeConst SC) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     DecodeSmem& S = *reinterpret_cast<DecodeSmem*>(smem_raw);
     const int t = threadIdx.x, warp = t >> 5;
@@ -581,13 +652,7 @@ __global__ void __launch_bounds__(NT_ROWS) k_ntc_decode_tc(NeuralView N, NeuralD
         }
         S.pair[t] = pr;
         S.wt[t] = w;
-        uint64_t f[16];
-        features2(N, N.latent_fmt, ix, iy, f);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4*>(S.A + kmaj_off(t, 8 * c, 32)) =
-                make_uint4(bf16x2_of<false>(f[4 * c]), bf16x2_of<false>(f[4 * c + 1]),
-                           bf16x2_of<false>(f[4 * c + 2]), bf16x2_of<false>(f[4 * c + 3]));
+        features_to_tile(N, N.latent_fmt, ix, iy, S.A, t);
         // ---- three GEMM layers
 #pragma unroll 1
         for (int layer = 0; layer < 3; ++layer) {

@@ -131,6 +131,18 @@ def test_id_base_shards_reproduce_whole(ctx, material):
     assert np.array_equal(np.concatenate([a, b]), whole)
 
 
+@pytest.mark.parametrize("flags", [0, oracle.FLAG_LATTICE])
+@pytest.mark.parametrize("filter", ["linear", "bspline", "catmull_rom", "mitchell"])
+def test_specialised_path_equals_general_path(ctx, material, filter, flags):
+    # a stochastic call without pick output, with no flag or the lattice flag alone, runs a
+    # specialised instantiation; it does the same arithmetic as the general one, so the
+    # results are identical
+    h, _, q = material
+    with_picks, _ = _run(ctx, h, q, filter, "stochastic", 5, seed=6, flags=flags, picks=True)
+    special, _ = _run(ctx, h, q, filter, "stochastic", 5, seed=6, flags=flags, picks=False)
+    assert np.array_equal(with_picks, special)
+
+
 def test_nan_input_sets_device_status(ctx, material):
     h, _, q = material
     q2 = q.subset(slice(0, 64))

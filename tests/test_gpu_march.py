@@ -46,6 +46,20 @@ def test_small_volume(ctx, small, filter, mode):
     assert_values(T.cpu().numpy(), ref.T, mism)
 
 
+@pytest.mark.parametrize("flags", [0, oracle.FLAG_LATTICE])
+@pytest.mark.parametrize("filter,steps", [("bspline", 97), ("linear", 64)])
+def test_specialised_path_equals_general_path(ctx, small, filter, steps, flags):
+    # without pick output (and with no flag, or the lattice flag alone) the stochastic march
+    # runs its specialised paired-step instantiation (odd step counts end with one unpaired
+    # step); the densities are summed in exact fixed point, so T equals the general path's
+    # bit for bit
+    h, _ = small
+    cam = synth.camera_pinhole(W, H).as_array()
+    T1, _ = ctx.march_volume(h, cam, W, H, steps, filter, "stochastic", spp=3, seed=4, flags=flags, want_picks=True)
+    T2, _ = ctx.march_volume(h, cam, W, H, steps, filter, "stochastic", spp=3, seed=4, flags=flags)
+    assert torch.equal(T1, T2)
+
+
 def test_stratified_and_pixel_ranges(ctx, small):
     h, vol = small
     cam = synth.camera_pinhole(W, H).as_array()

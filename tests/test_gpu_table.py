@@ -66,6 +66,27 @@ def test_large_table_sampled(ctx):
     _check_table(ctx, texs, 1 << 22, "mitchell", "stochastic", 4, 1, sample=3000)
 
 
+@pytest.mark.parametrize("flags", [0, oracle.FLAG_LATTICE])
+def test_specialised_path_equals_general_path(ctx, flags):
+    # without pick output (no flag, or the lattice flag alone) the table launch runs a
+    # specialised instantiation with the same arithmetic: identical results
+    texs = synth.texture_table_rgba8(12, 5, 200, seed=109, fbm_below=200)
+    handles = [ctx.create_texture([t]) for t in texs]
+    table = ctx.create_texture_table(handles)
+    q = synth.queries_uniform(30000, 4)
+    tid = np.random.default_rng(11).integers(0, len(texs), q.n).astype(np.int32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    outs = []
+    for picks in (True, False):
+        r, g, b, _ = ctx.filter_shade_table(table, t(q.u), t(q.v), t(tid), None, "mitchell", "stochastic", "ggx", 3, 2,
+                                            flags=flags, want_picks=picks)
+        outs.append(torch.stack([r, g, b], 1).cpu())
+    assert torch.equal(outs[0], outs[1])
+    ctx.destroy_texture_table(table)
+    for h in handles:
+        ctx.destroy_texture(h)
+
+
 def test_bad_texture_id_and_lifetime(ctx):
     import paper_2407_06107_b300 as stf
     texs = synth.texture_table_rgba8(3, 8, 16, seed=108, fbm_below=32)
