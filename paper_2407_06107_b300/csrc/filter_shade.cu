@@ -304,8 +304,13 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
     }
 }
 
+// Resident 256-thread blocks per SM the register budget is set for: 5 for the specialised
+// 1-tap variants (<= 51 registers), 4 otherwise (<= 64; positivization needs them).
+template <int MODE, int V>
+constexpr int min_blocks() { return (V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
+
 template <int FILTER, int MODE, int V>
-__global__ void __launch_bounds__(256, V == KV_GENERAL ? 4 : 5)
+__global__ void __launch_bounds__(256, min_blocks<MODE, V>())
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -317,7 +322,7 @@ k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst
 // each query's texture descriptor in the table.  An out-of-range texture id sets
 // DEV_BAD_INDEX and yields 0.
 template <int FILTER, int MODE, int V>
-__global__ void __launch_bounds__(256, V == KV_GENERAL ? 4 : 5)
+__global__ void __launch_bounds__(256, min_blocks<MODE, V>())
 k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint32_t ntex,
                      const uint32_t* __restrict__ tex_id, unsigned long long* counter, ShadeConst SC, RoundKeys K) {
     __shared__ unsigned long long chunk;
@@ -356,12 +361,13 @@ template <int FILTER, int MODE>
 static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, int num_sms,
                              cudaStream_t st) {
     (void)num_sms;
-    if constexpr (MODE == M_STOCHASTIC) {
-        switch (stochastic_variant(a.flags, a.picks)) {
-            case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
-            case KV_LATTICE: return launch_one<FILTER, MODE, KV_LATTICE>(a, T, SC, st);
-            default: break;
-        }
+    switch (kernel_variant(a.flags, a.picks)) {
+        case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
+        case KV_LATTICE:   // the lattice flag changes only the stochastic picks
+            if constexpr (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED)
+                return launch_one<FILTER, MODE, KV_LATTICE>(a, T, SC, st);
+            break;
+        default: break;
     }
     return launch_one<FILTER, MODE, KV_GENERAL>(a, T, SC, st);
 }
@@ -421,13 +427,13 @@ static cudaError_t launch_table_one(const FilterShadeArgs& a, const FetchCtx* ta
 template <int FILTER, int MODE>
 static cudaError_t launch_table_fm(const FilterShadeArgs& a, const FetchCtx* table, uint32_t ntex,
                                    const uint32_t* tex_id, unsigned long long* counter, int num_sms, cudaStream_t st) {
-    if constexpr (MODE == M_STOCHASTIC) {
-        switch (stochastic_variant(a.flags, a.picks)) {
-            case KV_PLAIN: return launch_table_one<FILTER, MODE, KV_PLAIN>(a, table, ntex, tex_id, counter, num_sms, st);
-            case KV_LATTICE:
+    switch (kernel_variant(a.flags, a.picks)) {
+        case KV_PLAIN: return launch_table_one<FILTER, MODE, KV_PLAIN>(a, table, ntex, tex_id, counter, num_sms, st);
+        case KV_LATTICE:
+            if constexpr (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED)
                 return launch_table_one<FILTER, MODE, KV_LATTICE>(a, table, ntex, tex_id, counter, num_sms, st);
-            default: break;
-        }
+            break;
+        default: break;
     }
     return launch_table_one<FILTER, MODE, KV_GENERAL>(a, table, ntex, tex_id, counter, num_sms, st);
 }

@@ -220,11 +220,14 @@ static cudaError_t launch_one(const MarchArgs& a, cudaStream_t st) {
 
 template <int FILTER>
 static cudaError_t launch_f(const MarchArgs& a, cudaStream_t st) {
+    const bool plain = a.flags == 0 && a.picks == nullptr;
     switch (a.mode) {
-        case M_NTAP_BEFORE: return launch_one<FILTER, M_NTAP_BEFORE, KV_GENERAL>(a, st);
-        case M_NTAP_AFTER: return launch_one<FILTER, M_NTAP_AFTER, KV_GENERAL>(a, st);
+        case M_NTAP_BEFORE:
+            return plain ? launch_one<FILTER, M_NTAP_BEFORE, KV_PLAIN>(a, st) : launch_one<FILTER, M_NTAP_BEFORE, KV_GENERAL>(a, st);
+        case M_NTAP_AFTER:
+            return plain ? launch_one<FILTER, M_NTAP_AFTER, KV_PLAIN>(a, st) : launch_one<FILTER, M_NTAP_AFTER, KV_GENERAL>(a, st);
         case M_STOCHASTIC:
-            switch (stochastic_variant(a.flags, a.picks)) {
+            switch (kernel_variant(a.flags, a.picks)) {
                 case KV_PLAIN: return launch_one<FILTER, M_STOCHASTIC, KV_PLAIN>(a, st);
                 case KV_LATTICE: return launch_one<FILTER, M_STOCHASTIC, KV_LATTICE>(a, st);
                 default: return launch_one<FILTER, M_STOCHASTIC, KV_GENERAL>(a, st);

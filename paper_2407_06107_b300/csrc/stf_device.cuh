@@ -23,13 +23,13 @@ __host__ __device__ constexpr int ntaps(int f) { return f == F_LINEAR ? 2 : 4; }
 __host__ __device__ constexpr int tap0(int f) { return f == F_LINEAR ? 0 : -1; }
 __host__ __device__ constexpr bool is_signed(int f) { return f == F_CATMULL_ROM || f == F_MITCHELL; }
 
-// Kernel variants of the stochastic paths.  GENERAL handles every flag and the pick output;
-// PLAIN is a call with no flags and no picks; LATTICE a call whose only flag is
-// FLAG_LATTICE, without picks.  The specialised variants compile the unused branches out
-// and need fewer registers.
+// Kernel variants.  GENERAL handles every flag and the pick output; PLAIN is a call with no
+// flags and no picks; LATTICE a call whose only flag is FLAG_LATTICE, without picks (it
+// matters to the stochastic modes only).  The specialised variants compile the unused
+// branches out and need fewer registers.
 enum { KV_GENERAL = 0, KV_PLAIN = 1, KV_LATTICE = 2 };
 __host__ __device__ constexpr uint32_t variant_flags(int v) { return v == KV_LATTICE ? (uint32_t)FLAG_LATTICE : 0u; }
-inline int stochastic_variant(uint32_t flags, const void* picks) {
+inline int kernel_variant(uint32_t flags, const void* picks) {
     if (picks) return KV_GENERAL;
     if (flags == 0) return KV_PLAIN;
     return flags == (uint32_t)FLAG_LATTICE ? KV_LATTICE : KV_GENERAL;
