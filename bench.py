@@ -226,6 +226,16 @@ def run_ours(args):
             "alg_ops_per_lookup": ops, "traffic": traffic, "ms_per_launch": float(mean[dom]),
             "alg_bytes_per_launch": units_launch * 8 + nq * (24 + 12),
             "hbm_frac_of_measured": (units_launch * 8 + nq * 36) / (mean[dom] / 1e3) / 1e9 / peaks()["hbm_gbs"]}
+    # gather roofline: algorithmic 32-byte sectors per lookup (the 8-byte texel lies in one
+    # sector; the 36 bytes of query I/O are shared by the spp samples) against the measured
+    # random-sector read rate at L2 (32 MiB buffer) and from DRAM (1 GiB buffer)
+    sectors_per_lookup = 1.0 + 36.0 / 32.0 / SPP
+    l2_rate, dram_rate = ctx.measure_sector_rate(32 << 20), ctx.measure_sector_rate(1 << 30)
+    g_ach = sectors_per_lookup * units_launch / (mean[dom] / 1e3)
+    gather = {"kernel": roof["kernel"], "bound": "l2_sectors", "unit": "sectors/s", "achieved": g_ach,
+              "alg_sectors_per_lookup": sectors_per_lookup, "peak": l2_rate, "frac": g_ach / l2_rate,
+              "peak_src": "measured: random 32-B sector reads at L2, 32 MiB buffer (stf_measure_sector_rate)",
+              "dram_sector_peak": dram_rate, "frac_of_dram_sector_peak": g_ach / dram_rate}
 
     line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -235,7 +245,7 @@ def run_ours(args):
                        "queries_per_gpu": nq, "spp": SPP, "filters": list(FILTERS), "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"query-sharded x{world}"},
             "ms_per_launch": {f: float(mean[i]) for i, f in enumerate(FILTERS)},
-            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * len(FILTERS), "clocks": clocks}
+            "roofline": roof, "gather_roofline": gather, "e2e": e2e, "gpu_launches": args.steps * len(FILTERS), "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_extras:
         line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
         line["volume"] = volume_block(ctx, dev, args)
@@ -490,6 +500,7 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
     tid = torch.from_numpy(rng.integers(0, ntex, nq).astype(np.int32)).to(dev)
     out = [torch.empty(nq, dtype=torch.float32, device=dev) for _ in range(3)]
     res = {"textures": ntex, "texel_bytes": tbytes, "queries": nq, "spp": 4}
+    dram_rate = ctx.measure_sector_rate(1 << 30)   # random 32-B sectors from DRAM (1 GiB buffer)
     order = torch.empty(nq, dtype=torch.int32, device=dev)
     ms_bin = _time_launch(lambda: ctx.bin_queries(u, v, tid, ntex=ntex, tile_log2=6, order=order), 2)
     for mode in ("stochastic", "positivized"):
@@ -497,10 +508,15 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
                                                          out=out), 2)
         msb = _time_launch(lambda: ctx.filter_shade_table(table, u, v, tid, None, "mitchell", mode, "ggx", 4, 1,
                                                           out=out, order=order), 2)
+        fetches = 1 if mode == "stochastic" else 2
+        # one 32-B sector per 4-B texel fetch, plus 24 B of query I/O shared by the 4 samples
+        sectors = (fetches + 24.0 / 32.0 / 4) * nq * 4 / (ms / 1e3)
         res[mode] = {"ms": ms, "lookups_per_s": nq * 4 / (ms / 1e3),
-                     "texel_fetches_per_lookup": 1 if mode == "stochastic" else 2,
+                     "texel_fetches_per_lookup": fetches,
+                     "alg_sectors_per_s": sectors, "frac_of_dram_sector_peak": sectors / dram_rate,
                      "binned_ms": msb, "binned_lookups_per_s": nq * 4 / (msb / 1e3)}
     res["bin_ms"] = ms_bin
+    res["dram_sector_peak"] = dram_rate
     ctx.destroy_texture_table(table)
     for h in handles:
         ctx.destroy_texture(h)

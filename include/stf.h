@@ -293,6 +293,16 @@ stf_status stf_neural_filter_shade(stf_ctx ctx, stf_neural net, const stf_querie
                                    stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                                    uint64_t seed, uint32_t flags, const stf_output* out);
 
+/* ---- measurement: the gather roofline's denominator ----------------------------------
+ * The paper has no counterpart: this is the measured peak against which the 1-tap kernels'
+ * gather rate is reported.  Reads random, independent 32-byte sectors of a device buffer of
+ * buffer_bytes (a power of two, 1 MiB .. 1 GiB; a buffer well inside the 126 MB L2 measures
+ * the L2 hit rate, one larger than L2 the DRAM sector rate) at L2 (bypassing L1), and writes
+ * the best of 3 timed runs as sectors per second to *sectors_per_s (host).  Allocates and
+ * frees the buffer; synchronises the context stream.  STF_ERR_INVALID_ARG for a bad size or
+ * a null output. */
+stf_status stf_measure_sector_rate(stf_ctx ctx, uint64_t buffer_bytes, double* sectors_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,7 @@ SIGNATURES = {
                                 C.POINTER(_Output)], _I),
     "stf_filter_shade_host_noalloc": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                        _U64, _U32, C.POINTER(_Output)], _I),
+    "stf_measure_sector_rate": ([_P, _U64, C.POINTER(C.c_double)], _I),
     "stf_create_volume": ([_P, _U32, _U32, _U32, _I, _F, _P, _I, C.POINTER(_U64)], _I),
     "stf_destroy_volume": ([_P, _U64], _I),
     "stf_march_volume": ([_P, _U64, _P, _U32, _U32, _U32, _I, _I, _U32, _U64, _U32, _U64, _U64, _P, _P], _I),
@@ -301,6 +302,13 @@ class Context:
                                                  C.byref(o))
         self._check(st, self.h)
         return out[0], out[1], out[2]
+
+    def measure_sector_rate(self, buffer_bytes: int = 32 << 20) -> float:
+        """Random 32-byte sector reads per second at L2 over a buffer of buffer_bytes (the
+        gather roofline's measured denominator)."""
+        out = C.c_double(0.0)
+        self._check(lib().stf_measure_sector_rate(self.h, buffer_bytes, C.byref(out)), self.h)
+        return float(out.value)
 
     def march_volume(self, vol: int, cam, width: int, height: int, steps: int = 128,
                      filter: str = "bspline", mode: str = "stochastic", spp: int = 1, seed: int = 1,
