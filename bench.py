@@ -228,14 +228,15 @@ def run_ours(args):
             "hbm_frac_of_measured": (units_launch * 8 + nq * 36) / (mean[dom] / 1e3) / 1e9 / peaks()["hbm_gbs"]}
     # gather roofline: algorithmic 32-byte sectors per lookup (the 8-byte texel lies in one
     # sector; the 36 bytes of query I/O are shared by the spp samples) against the measured
-    # random-sector read rate at L2 (32 MiB buffer) and from DRAM (1 GiB buffer)
+    # random-sector read rate at L2 (32 MiB buffer).  Most lookups hit L2, so the DRAM random-
+    # sector rate (1 GiB buffer) is context, not the bound.
     sectors_per_lookup = 1.0 + 36.0 / 32.0 / SPP
     l2_rate, dram_rate = ctx.measure_sector_rate(32 << 20), ctx.measure_sector_rate(1 << 30)
     g_ach = sectors_per_lookup * units_launch / (mean[dom] / 1e3)
     gather = {"kernel": roof["kernel"], "bound": "l2_sectors", "unit": "sectors/s", "achieved": g_ach,
               "alg_sectors_per_lookup": sectors_per_lookup, "peak": l2_rate, "frac": g_ach / l2_rate,
               "peak_src": "measured: random 32-B sector reads at L2, 32 MiB buffer (stf_measure_sector_rate)",
-              "dram_sector_peak": dram_rate, "frac_of_dram_sector_peak": g_ach / dram_rate}
+              "dram_sector_rate": dram_rate}
 
     line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -500,7 +501,9 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
     tid = torch.from_numpy(rng.integers(0, ntex, nq).astype(np.int32)).to(dev)
     out = [torch.empty(nq, dtype=torch.float32, device=dev) for _ in range(3)]
     res = {"textures": ntex, "texel_bytes": tbytes, "queries": nq, "spp": 4}
-    dram_rate = ctx.measure_sector_rate(1 << 30)   # random 32-B sectors from DRAM (1 GiB buffer)
+    # measured random 32-B sector read rates: at L2 (32 MiB buffer) and from DRAM (1 GiB); the
+    # table's small textures mostly hit L2, its large ones go to DRAM
+    l2_rate, dram_rate = ctx.measure_sector_rate(32 << 20), ctx.measure_sector_rate(1 << 30)
     order = torch.empty(nq, dtype=torch.int32, device=dev)
     ms_bin = _time_launch(lambda: ctx.bin_queries(u, v, tid, ntex=ntex, tile_log2=6, order=order), 2)
     for mode in ("stochastic", "positivized"):
@@ -513,10 +516,10 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
         sectors = (fetches + 24.0 / 32.0 / 4) * nq * 4 / (ms / 1e3)
         res[mode] = {"ms": ms, "lookups_per_s": nq * 4 / (ms / 1e3),
                      "texel_fetches_per_lookup": fetches,
-                     "alg_sectors_per_s": sectors, "frac_of_dram_sector_peak": sectors / dram_rate,
+                     "alg_sectors_per_s": sectors, "frac_of_l2_sector_rate": sectors / l2_rate,
                      "binned_ms": msb, "binned_lookups_per_s": nq * 4 / (msb / 1e3)}
     res["bin_ms"] = ms_bin
-    res["dram_sector_peak"] = dram_rate
+    res["l2_sector_rate"], res["dram_sector_rate"] = l2_rate, dram_rate
     ctx.destroy_texture_table(table)
     for h in handles:
         ctx.destroy_texture(h)
