@@ -68,7 +68,16 @@ typedef enum {
     STF_FILTER_LINEAR = 0,       /* tent K1: bilinear / trilinear, 2 taps per axis        */
     STF_FILTER_BSPLINE = 1,      /* cubic B-spline K_bs, 4 taps per axis                  */
     STF_FILTER_CATMULL_ROM = 2,  /* Keys cubic K3 with a = -1/2, 4 taps, negative lobes   */
-    STF_FILTER_MITCHELL = 3      /* Mitchell-Netravali BC(1/3,1/3), 4 taps, neg. lobes    */
+    STF_FILTER_MITCHELL = 3,     /* Mitchell-Netravali BC(1/3,1/3), 4 taps, neg. lobes    */
+    STF_FILTER_EWA = 4           /* elliptically weighted average over a Gaussian (supplement
+                                    "Stochastic EWA", as pbrt evaluates it): the ellipse of the
+                                    derivative footprint plus a one-texel reconstruction term,
+                                    eccentricity capped at 64, weights exp(-2r^2)-exp(-2) from a
+                                    128-entry table.  stf_filter_shade only; modes NTAP_BEFORE,
+                                    NTAP_AFTER (each level normalised by its weight sum) and
+                                    STOCHASTIC (one texel by weighted reservoir sampling over the
+                                    ellipse's box, raster order, uniform remapped per decision);
+                                    no screen-space jitter; flags: LOD0 only */
 } stf_filter;
 
 typedef enum {
@@ -93,6 +102,8 @@ typedef enum { STF_ADDRESS_WRAP = 0, STF_ADDRESS_CLAMP = 1 } stf_address;
 #define STF_FLAG_REUSE 4u       /* 1-tap stochastic mode: one uniform per sample (per step in a volume)
                                    drives the level and every axis, remapped after each decision
                                    (Eq. uniform-sample-reuse; the listings' sample reuse) */
+#define STF_FLAG_LOD0 8u        /* 2-D: sample the finest MIP level only (no MIP prefiltering, Sec.
+                                   4.2.1's "no MIP mapping" variant and its point-sampled reference) */
 
 /* device status bits */
 #define STF_DEV_NAN_INPUT 1u

@@ -28,12 +28,13 @@ SRCS = [os.path.join(HERE, f) for f in ("stf_oracle.cpp", "ntc_oracle.cpp")]
 DEPS = SRCS + [os.path.join(HERE, "oracle_internal.h")]
 LIB = os.path.join(HERE, "liboracle.so")
 
-FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3}
+FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
 FLAG_REUSE = 4
+FLAG_LOD0 = 8
 NO_PICK = 0xFFFFFFFF
 
 
@@ -78,6 +79,8 @@ def lib():
         L.orc_kernel_keys.restype = C.c_double
         L.orc_weights32.argtypes = [C.c_int, C.c_float, P]
         L.orc_pick32.argtypes = [P, C.c_int, C.c_float, C.c_int]
+        L.orc_ewa_table.argtypes = [P]
+        L.orc_ewa_box.argtypes = [C.c_float] * 6 + [C.c_int, C.c_int, P, P, C.c_int]
         L.orc_pick32_reuse.argtypes = [P, C.c_int, C.c_float, P]
         L.orc_pick_array.argtypes = [P, C.c_int, C.c_double]
         L.orc_ggx_eval.argtypes = [P, P, P, C.c_double, P, C.c_double, P]
@@ -145,6 +148,26 @@ def weights32(filter_name: str, t: float) -> np.ndarray:
 def pick32(w, xi: float, cls: int = 0) -> int:
     w = np.ascontiguousarray(w, dtype=np.float32)
     return lib().orc_pick32(_p(w), len(w), float(np.float32(xi)), cls)
+
+
+def ewa_table() -> np.ndarray:
+    """The 128 Gaussian weights exp(-2 r^2) - exp(-2) at r^2 = i/127 (FP32)."""
+    out = np.zeros(128, np.float32)
+    lib().orc_ewa_table(_p(out))
+    return out
+
+
+def ewa_box(x, y, dudx, dvdx, dudy, dvdy, W, H, cap=1 << 20):
+    """The EWA ellipse's bounding box (s0, s1, t0, t1) at a W x H level and the FP32 weights of
+    its texels as a (t, s) array (zero outside the ellipse)."""
+    box = np.zeros(4, np.int32)
+    w = np.zeros(cap, np.float32)
+    f = lambda a: float(np.float32(a))
+    n = lib().orc_ewa_box(f(x), f(y), f(dudx), f(dvdx), f(dudy), f(dvdy), int(W), int(H), _p(box), _p(w), cap)
+    if n < 0:
+        raise ValueError("box too large" if n == -1 else "non-finite ellipse")
+    s0, s1, t0, t1 = (int(b) for b in box)
+    return (s0, s1, t0, t1), w[:n].reshape(t1 - t0 + 1, s1 - s0 + 1).copy()
 
 
 def pick32_reuse(w, xi: float):

@@ -41,10 +41,10 @@
 namespace {
 
 // ------------------------------------------------------------------ enums (API values)
-enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3 };
+enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3, F_EWA = 4 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
-enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u };
+enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u, FLAG_LOD0 = 8u };
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_NEURAL = 2 };
 enum { ADDR_WRAP = 0, ADDR_CLAMP = 1 };
 const uint32_t NO_PICK = 0xFFFFFFFFu;
@@ -393,10 +393,199 @@ Axis axis_at(float x, int res) {
     return {(int)fl, p - fl, (double)p};
 }
 
+// ------------------------------------------------------------------ EWA
+// Elliptically weighted average over a Gaussian (Greene and Heckbert 1986; Heckbert 1989),
+// as the supplement's "Stochastic EWA" evaluates it, following pbrt.
+//   * The ellipse is the implicit A s^2 + B s t + C t^2 < 1 in the texel space of the
+//     chosen level (texel centres at integers, s = x W - 1/2).
+//   * It is built from the two screen-space derivative vectors, each plus a one-texel
+//     reconstruction term, with the minor axis stretched to major/64 when the eccentricity
+//     exceeds 64 (the same cap as the LOD).
+//   * Weights are exp(-2 r^2) - exp(-2), read from a 128-entry table at floor(128 r^2).
+// The geometry and the table lookups decide which texels take part and with which
+// weight, so they are FP32 with a fixed operation order (fmaf written out); every sum is
+// FP64.  The bounding box's half-extents are capped at EWA_MAX_HALF texels (only a
+// footprint many times larger than the coarsest level reaches the cap).
+const int EWA_LUT_N = 128;
+const float EWA_MAX_HALF = 256.0f;
+
+const float* ewa_table() {
+    static const std::vector<float> lut = [] {
+        std::vector<float> t(EWA_LUT_N);
+        for (int i = 0; i < EWA_LUT_N; ++i) {
+            const double r2 = (double)i / (double)(EWA_LUT_N - 1);
+            t[i] = (float)(std::exp(-2.0 * r2) - std::exp(-2.0));
+        }
+        return t;
+    }();
+    return lut.data();
+}
+
+struct Ewa {
+    float cx, cy, A, B, C;
+    int s0, s1, t0, t1;
+    bool ok;
+};
+
+Ewa ewa_setup(float x, float y, float dudx, float dvdx, float dudy, float dvdy, int W, int H) {
+    Ewa e{};
+    e.cx = std::fmaf(x, (float)W, -0.5f);
+    e.cy = std::fmaf(y, (float)H, -0.5f);
+    float ax = dudx * (float)W, ay = dvdx * (float)H;   // screen x axis, in texels
+    float bx = dudy * (float)W, by = dvdy * (float)H;   // screen y axis
+    float la = std::fmaf(ay, ay, ax * ax), lb = std::fmaf(by, by, bx * bx);
+    if (la < lb) { std::swap(ax, bx); std::swap(ay, by); std::swap(la, lb); }   // a: major axis
+    const float lmaj = std::sqrt(la), lmin = std::sqrt(lb);
+    if (lmin > 0.0f && lmin * 64.0f < lmaj) {
+        const float sc = lmaj / (lmin * 64.0f);
+        bx = bx * sc;
+        by = by * sc;
+    }
+    float A = std::fmaf(ay, ay, std::fmaf(by, by, 1.0f));
+    float B = -2.0f * std::fmaf(ax, ay, bx * by);
+    float C = std::fmaf(ax, ax, std::fmaf(bx, bx, 1.0f));
+    const float iF = 1.0f / std::fmaf(A, C, -0.25f * (B * B));
+    A = A * iF; B = B * iF; C = C * iF;
+    const float det = std::fmaf(4.0f * A, C, -(B * B));
+    const float iD = 2.0f * (1.0f / det);
+    const float hs = iD * std::sqrt(det * C), ht = iD * std::sqrt(A * det);
+    e.A = A; e.B = B; e.C = C;
+    e.ok = std::isfinite(e.cx) && std::isfinite(e.cy) && std::isfinite(hs) && std::isfinite(ht) &&
+           std::fabs(e.cx) < 16777216.0f && std::fabs(e.cy) < 16777216.0f;
+    if (!e.ok) return e;
+    const float fx = std::floor(e.cx), fy = std::floor(e.cy);
+    e.s0 = (int)std::ceil(std::fmax(e.cx - hs, fx - EWA_MAX_HALF));
+    e.s1 = (int)std::floor(std::fmin(e.cx + hs, fx + EWA_MAX_HALF));
+    e.t0 = (int)std::ceil(std::fmax(e.cy - ht, fy - EWA_MAX_HALF));
+    e.t1 = (int)std::floor(std::fmin(e.cy + ht, fy + EWA_MAX_HALF));
+    return e;
+}
+
+float ewa_weight(const Ewa& e, int s, int t) {
+    const float ss = (float)s - e.cx, tt = (float)t - e.cy;
+    const float r2 = std::fmaf(e.A * ss, ss, std::fmaf(e.B * ss, tt, (e.C * tt) * tt));
+    if (!(r2 < 1.0f)) return 0.0f;
+    const int idx = std::min((int)(r2 * (float)EWA_LUT_N), EWA_LUT_N - 1);
+    return ewa_table()[idx];
+}
+
+// EWA lookups of one query (no screen-space jitter: the ellipse is the footprint).
+//   * N-tap modes: both MIP levels, each normalised by its own weight sum, blended linearly.
+//   * Stochastic: the stochastic level, then one texel by weighted reservoir sampling over the
+//     box in raster order (t outer, s inner).  The uniform is remapped after every decision, as
+//     in the listing.  bdist records the smallest |u - p| over the decisions.
+void run_query_ewa(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int mode, int smode, uint32_t spp,
+                   uint64_t seed, float lam32, double lam64, double bd, Out& O) {
+    const int l0 = (int)std::floor(lam32);
+    const float fr = lam32 - (float)l0;
+    const float du0 = Q.dudx ? Q.dudx[q] : 0.0f, dv0 = Q.dudx ? Q.dvdx[q] : 0.0f;
+    const float du1 = Q.dudx ? Q.dudy[q] : 0.0f, dv1 = Q.dudx ? Q.dvdy[q] : 0.0f;
+    const float x = Q.u[q], y = Q.v[q];
+    double acc[3] = {0, 0, 0}, mag[3] = {0, 0, 0};
+    double rd = 1.0;
+    for (uint32_t s = 0; s < spp; ++s) {
+        uint32_t r0[4];
+        draw(seed, id, s, 0, r0);
+        float a[5];
+        uniforms5(r0, a);
+        uint32_t* pk = O.picks ? O.picks + (q * spp + s) * 2 : nullptr;
+        uint32_t* pk64 = O.picks64 ? O.picks64 + (q * spp + s) * 2 : nullptr;
+        if (pk) pk[0] = pk[1] = NO_PICK;
+        if (pk64) pk64[0] = pk64[1] = NO_PICK;
+        double est[3] = {0, 0, 0};
+        if (mode == M_STOCHASTIC) {
+            int lvl = std::min(l0 + ((a[2] < fr) ? 1 : 0), T.levels - 1);
+            if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs((double)a[2] - (lam64 - std::floor(lam64))));
+            const int W = T.width[lvl], H = T.height[lvl];
+            const Ewa e = ewa_setup(x, y, du0, dv0, du1, dv1, W, H);
+            float u = a[3], sum = 0.0f;
+            int ps = 0, pt = 0;
+            bool any = false;
+            if (e.ok) {
+                for (int t = e.t0; t <= e.t1; ++t)
+                    for (int si = e.s0; si <= e.s1; ++si) {
+                        const float w = ewa_weight(e, si, t);
+                        if (!(w > 0.0f)) continue;
+                        sum = sum + w;
+                        const float p = w / sum;
+                        if (any) bd = std::min(bd, std::fabs((double)u - (double)p));
+                        if (u < p) { ps = si; pt = t; any = true; u = u / p; }
+                        else u = (u - p) / (1.0f - p);
+                    }
+            }
+            if (any) {
+                const int ix = wrapi(ps, W, T.address), iy = wrapi(pt, H, T.address);
+                double o[3];
+                shade(smode, fetch(T, lvl, ix, iy, &rd), o);
+                for (int c = 0; c < 3; ++c) { est[c] = o[c]; mag[c] += std::fabs(o[c]); }
+                if (pk) pk[0] = pack2d(lvl, ix, iy);
+                if (pk64) pk64[0] = pack2d(lvl, ix, iy);
+            }
+        } else {
+            const double wl[2] = {1.0 - (double)fr, (double)fr};
+            Mat fm{}; fm.n = {0, 0, 0};
+            double fsum[3] = {0, 0, 0};
+            for (int li = 0; li < 2; ++li) {
+                const int lvl = l0 + li;
+                if (wl[li] == 0.0 || lvl >= T.levels) continue;
+                const int W = T.width[lvl], H = T.height[lvl];
+                const Ewa e = ewa_setup(x, y, du0, dv0, du1, dv1, W, H);
+                if (!e.ok) continue;
+                double S = 0.0, mb[7] = {0, 0, 0, 0, 0, 0, 0}, ma[3] = {0, 0, 0}, mm[3] = {0, 0, 0};
+                for (int t = e.t0; t <= e.t1; ++t)
+                    for (int si = e.s0; si <= e.s1; ++si) {
+                        const double w = ewa_weight(e, si, t);
+                        if (!(w > 0.0)) continue;
+                        S += w;
+                        const Mat m = fetch(T, lvl, wrapi(si, W, T.address), wrapi(t, H, T.address), &rd);
+                        if (mode == M_NTAP_BEFORE) {
+                            for (int c = 0; c < 3; ++c) mb[c] += w * m.rho[c];
+                            mb[3] += w * m.rough;
+                            mb[4] += w * m.n.x; mb[5] += w * m.n.y; mb[6] += w * m.n.z;
+                        } else {
+                            double o[3];
+                            shade(smode, m, o);
+                            for (int c = 0; c < 3; ++c) { ma[c] += w * o[c]; mm[c] += std::fabs(w * o[c]); }
+                        }
+                    }
+                if (!(S > 0.0)) continue;
+                const double k = wl[li] / S;
+                if (mode == M_NTAP_BEFORE) {
+                    for (int c = 0; c < 3; ++c) fm.rho[c] += k * mb[c];
+                    fm.rough += k * mb[3];
+                    fm.n.x += k * mb[4]; fm.n.y += k * mb[5]; fm.n.z += k * mb[6];
+                } else {
+                    for (int c = 0; c < 3; ++c) { fsum[c] += k * ma[c]; mag[c] += k * mm[c]; }
+                }
+            }
+            if (mode == M_NTAP_BEFORE) {
+                const double ln = std::sqrt(dot(fm.n, fm.n));
+                fm.n = ln > 0 ? V3{fm.n.x / ln, fm.n.y / ln, fm.n.z / ln} : V3{0, 0, 1};
+                shade(smode, fm, est);
+                for (int c = 0; c < 3; ++c) mag[c] += std::fabs(est[c]);
+            } else {
+                for (int c = 0; c < 3; ++c) est[c] = fsum[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) acc[c] += est[c];
+    }
+    for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c] / (double)spp;
+    if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c] / (double)spp;
+    if (O.rdist) O.rdist[q] = rd;
+    if (O.bdist) O.bdist[q] = bd;
+}
+
 void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filter, int mode, int smode,
                uint32_t spp, uint64_t seed, uint32_t flags, Out& O) {
     float lam32; double lam64;
     lod(T, Q, q, &lam32, &lam64);
+    if (flags & FLAG_LOD0) { lam32 = 0.0f; lam64 = 0.0; }   // finest level only (no MIP prefiltering)
+    if (filter == F_EWA) {
+        double bd0 = 1e30;
+        if (lam64 > 0.0 && lam64 < T.levels - 1) bd0 = std::fabs(lam64 - std::nearbyint(lam64));
+        run_query_ewa(T, Q, q, id, mode, smode, spp, seed, lam32, lam64, bd0, O);
+        return;
+    }
     int l0 = (int)std::floor(lam32);
     float fr = lam32 - (float)l0;
     int l0_64 = (int)std::floor(lam64);
@@ -771,6 +960,23 @@ double orc_kernel_keys(double a, double d) { return k_keys(a, d); }
 
 int orc_weights32(int filter, float t, float* w) { return weights32(filter, t, w); }
 
+// EWA pieces for the pins: the weight table, and the weights of an ellipse's bounding box
+// (box[4] = s0, s1, t0, t1; w gets (s1-s0+1)*(t1-t0+1) weights, t outer), or -1 if the box
+// holds more than cap weights
+void orc_ewa_table(float* out) { std::memcpy(out, ewa_table(), sizeof(float) * EWA_LUT_N); }
+int orc_ewa_box(float x, float y, float dudx, float dvdx, float dudy, float dvdy, int W, int H, int* box,
+                float* w, int cap) {
+    const Ewa e = ewa_setup(x, y, dudx, dvdx, dudy, dvdy, W, H);
+    if (!e.ok) return -2;
+    box[0] = e.s0; box[1] = e.s1; box[2] = e.t0; box[3] = e.t1;
+    const long n = (long)(e.s1 - e.s0 + 1) * (long)(e.t1 - e.t0 + 1);
+    if (n > cap) return -1;
+    int k = 0;
+    for (int t = e.t0; t <= e.t1; ++t)
+        for (int s = e.s0; s <= e.s1; ++s) w[k++] = ewa_weight(e, s, t);
+    return k;
+}
+
 // FP32 CDF pick (cls 0 = all taps, +1 positive taps, -1 negative taps)
 int orc_pick32(const float* w, int n, float xi, int cls) { return pick32(w, n, xi, cls, nullptr); }
 int orc_pick32_reuse(const float* w, int n, float xi, float* remapped) { return pick32_reuse(w, n, xi, remapped); }
@@ -816,9 +1022,10 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
                      const uint64_t* ids, int filter, int mode, int smode, uint32_t spp, uint64_t seed,
                      uint32_t flags, double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist,
                      double* mag, double* rdist, int nthreads) {
-    if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 3 || mode < 0 || mode > 3) return 1;
+    if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 4 || mode < 0 || mode > 3) return 1;
     if (tex->levels < 1 || tex->levels > 16) return 1;
     if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
+    if (filter == F_EWA && (flags & ~(uint32_t)FLAG_LOD0)) return 1;   // EWA: no jitter, lattice or reuse
     if ((flags & FLAG_REUSE) && mode == M_POSITIVIZED) return 1;
     if (flags & FLAG_STRATIFIED) {
         long k = std::lround(std::sqrt((double)spp));

@@ -15,13 +15,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstf.so")
 
-FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3}
+FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F = 0, 1, 2, 3
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
 FLAG_REUSE = 4
+FLAG_LOD0 = 8
 DEV_NAN_INPUT, DEV_BAD_INDEX, DEV_TIMEOUT = 1, 2, 4
 NO_PICK = 0xFFFFFFFF
 

@@ -89,6 +89,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             dudx = a.dudx[q]; dvdx = a.dvdx[q]; dudy = a.dudy[q]; dvdy = a.dvdy[q];
             if (T.levels > 1) lam = lod_aniso(dudx, dvdx, dudy, dvdy, (float)T.w[0], (float)T.h[0], T.levels);
         }
+        if (flags & FLAG_LOD0) lam = 0.0f;      // finest level only
         if (isnan(u) || isnan(v) || isnan(dudx) || isnan(dvdx) || isnan(dudy) || isnan(dvdy))
             atomicOr(a.status, DEV_NAN_INPUT);
         const int l0 = (int)floorf(lam);
@@ -304,17 +305,226 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
     }
 }
 
+// ---------------------------------------------------------------- EWA
+// Elliptically weighted average over a Gaussian (supplement "Stochastic EWA", as pbrt
+// evaluates it).  The ellipse A s^2 + B s t + C t^2 < 1 lives in the texel space of one
+// level (texel centres at integers).  It is built from the two derivative vectors in texels,
+// each plus a one-texel reconstruction term, with the minor axis stretched to major/64 past
+// an eccentricity of 64.  Weights come from the 128-entry table at floor(128 r^2).  The
+// geometry decides which texels take part, so it is FP32 in a fixed operation order (IEEE
+// division and square root, FMAs written out).  The box half-extents are capped at 256
+// texels, which only a footprint many times the size of the coarsest level reaches.
+struct EwaBox {
+    float cx, cy, A, B, C;
+    int s0, s1, t0, t1;
+};
+
+__device__ __forceinline__ EwaBox ewa_setup(float x, float y, float dudx, float dvdx, float dudy, float dvdy,
+                                            int W, int H) {
+    EwaBox e;
+    const float fW = (float)W, fH = (float)H;
+    e.cx = __fmaf_rn(x, fW, -0.5f);
+    e.cy = __fmaf_rn(y, fH, -0.5f);
+    float ax = __fmul_rn(dudx, fW), ay = __fmul_rn(dvdx, fH);     // screen x axis, in texels
+    float bx = __fmul_rn(dudy, fW), by = __fmul_rn(dvdy, fH);     // screen y axis
+    float la = __fmaf_rn(ay, ay, __fmul_rn(ax, ax)), lb = __fmaf_rn(by, by, __fmul_rn(bx, bx));
+    if (la < lb) {                                                // a: the major axis
+        float t0 = ax; ax = bx; bx = t0;
+        t0 = ay; ay = by; by = t0;
+        t0 = la; la = lb; lb = t0;
+    }
+    const float lmaj = __fsqrt_rn(la), lmin = __fsqrt_rn(lb);
+    if (lmin > 0.0f && __fmul_rn(lmin, 64.0f) < lmaj) {
+        const float sc = __fdiv_rn(lmaj, __fmul_rn(lmin, 64.0f));
+        bx = __fmul_rn(bx, sc);
+        by = __fmul_rn(by, sc);
+    }
+    float A = __fmaf_rn(ay, ay, __fmaf_rn(by, by, 1.0f));
+    float B = __fmul_rn(-2.0f, __fmaf_rn(ax, ay, __fmul_rn(bx, by)));
+    float C = __fmaf_rn(ax, ax, __fmaf_rn(bx, bx, 1.0f));
+    const float iF = __fdiv_rn(1.0f, __fmaf_rn(A, C, __fmul_rn(-0.25f, __fmul_rn(B, B))));
+    A = __fmul_rn(A, iF);
+    B = __fmul_rn(B, iF);
+    C = __fmul_rn(C, iF);
+    const float det = __fmaf_rn(__fmul_rn(4.0f, A), C, -__fmul_rn(B, B));
+    const float iD = __fmul_rn(2.0f, __fdiv_rn(1.0f, det));
+    const float hs = __fmul_rn(iD, __fsqrt_rn(__fmul_rn(det, C)));
+    const float ht = __fmul_rn(iD, __fsqrt_rn(__fmul_rn(A, det)));
+    e.A = A; e.B = B; e.C = C;
+    const bool ok = isfinite(e.cx) && isfinite(e.cy) && isfinite(hs) && isfinite(ht) &&
+                    fabsf(e.cx) < 16777216.0f && fabsf(e.cy) < 16777216.0f;
+    if (!ok) { e.s0 = 0; e.s1 = -1; e.t0 = 0; e.t1 = -1; return e; }   // empty box
+    const float fx = floorf(e.cx), fy = floorf(e.cy);
+    e.s0 = (int)ceilf(fmaxf(__fsub_rn(e.cx, hs), __fsub_rn(fx, 256.0f)));
+    e.s1 = (int)floorf(fminf(__fadd_rn(e.cx, hs), __fadd_rn(fx, 256.0f)));
+    e.t0 = (int)ceilf(fmaxf(__fsub_rn(e.cy, ht), __fsub_rn(fy, 256.0f)));
+    e.t1 = (int)floorf(fminf(__fadd_rn(e.cy, ht), __fadd_rn(fy, 256.0f)));
+    return e;
+}
+
+__device__ __forceinline__ float ewa_weight(const EwaBox& e, int s, int t, const float* lut) {
+    const float ss = __fsub_rn((float)s, e.cx), tt = __fsub_rn((float)t, e.cy);
+    const float r2 = __fmaf_rn(__fmul_rn(e.A, ss), ss,
+                               __fmaf_rn(__fmul_rn(e.B, ss), tt, __fmul_rn(__fmul_rn(e.C, tt), tt)));
+    if (!(r2 < 1.0f)) return 0.0f;
+    return lut[min((int)__fmul_rn(r2, (float)EWA_LUT_N), EWA_LUT_N - 1)];
+}
+
+// One query through EWA (no screen-space jitter: the ellipse is the footprint).
+// STOCHASTIC: the stochastic level, then one texel by weighted reservoir sampling over the
+// box in raster order, the uniform remapped after every decision; the estimate is the
+// picked texel's shade.  N-tap modes: both levels, each normalised by its own weight sum,
+// blended linearly.
+template <int MODE, int V>
+__device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
+                                          const RoundKeys& K, uint64_t q, const float* lut) {
+    const uint32_t flags = V == KV_GENERAL ? a.flags : 0u;
+    uint32_t* const picks = V == KV_GENERAL ? a.picks : nullptr;
+    const float u = a.u[q], v = a.v[q];
+    float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f, lam = 0.0f;
+    if (a.has_derivs) {
+        dudx = a.dudx[q]; dvdx = a.dvdx[q]; dudy = a.dudy[q]; dvdy = a.dvdy[q];
+        if (T.levels > 1) lam = lod_aniso(dudx, dvdx, dudy, dvdy, (float)T.w[0], (float)T.h[0], T.levels);
+    }
+    if (isnan(u) || isnan(v) || isnan(dudx) || isnan(dvdx) || isnan(dudy) || isnan(dvdy))
+        atomicOr(a.status, DEV_NAN_INPUT);
+    if (flags & FLAG_LOD0) lam = 0.0f;
+    const int l0 = (int)floorf(lam);
+    const float fr = __fsub_rn(lam, (float)l0);
+    const uint64_t id = a.id_base + q;
+    const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (uint32_t s = 0; s < a.spp; ++s) {
+        float3 est = make_float3(0.f, 0.f, 0.f);
+        if constexpr (MODE == M_STOCHASTIC) {
+            const U5 A5 = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            const int lvl = min(l0 + ((A5.u[2] < fr) ? 1 : 0), T.levels - 1);
+            const int W = T.w[lvl], H = T.h[lvl];
+            const EwaBox e = ewa_setup(u, v, dudx, dvdx, dudy, dvdy, W, H);
+            float uu = A5.u[3], sum = 0.0f;
+            int ps = 0, pt = 0;
+            bool any = false;
+            for (int t = e.t0; t <= e.t1; ++t)
+                for (int si = e.s0; si <= e.s1; ++si) {
+                    const float w = ewa_weight(e, si, t, lut);
+                    if (!(w > 0.0f)) continue;
+                    sum = __fadd_rn(sum, w);
+                    const float p = __fdiv_rn(w, sum);
+                    if (uu < p) { ps = si; pt = t; any = true; uu = __fdiv_rn(uu, p); }
+                    else uu = __fdiv_rn(__fsub_rn(uu, p), __fsub_rn(1.0f, p));
+                }
+            uint32_t pk = NO_PICK;
+            if (any) {
+                const int ix = wrap_index(ps, W), iy = wrap_index(pt, H);
+                est = shade(a.shade, fetch(T, lvl, ix, iy), SC);
+                pk = pack_pick(lvl, ix, iy);
+            }
+            if (picks) {
+                uint32_t* p2 = picks + (q * a.spp + s) * 2;
+                p2[0] = pk;
+                p2[1] = NO_PICK;
+            }
+        } else {
+            Material fm;
+            fm.rho = make_float3(0.f, 0.f, 0.f);
+            fm.rough = 0.f;
+            fm.n = make_float3(0.f, 0.f, 0.f);
+#pragma unroll 1
+            for (int li = 0; li < 2; ++li) {
+                const int lvl = l0 + li;
+                const float wl = li == 0 ? __fsub_rn(1.0f, fr) : fr;
+                if (wl == 0.0f || lvl >= T.levels) continue;
+                const int W = T.w[lvl], H = T.h[lvl];
+                const EwaBox e = ewa_setup(u, v, dudx, dvdx, dudy, dvdy, W, H);
+                float S = 0.0f;
+                Material mb;
+                mb.rho = make_float3(0.f, 0.f, 0.f);
+                mb.rough = 0.f;
+                mb.n = make_float3(0.f, 0.f, 0.f);
+                float3 ma = make_float3(0.f, 0.f, 0.f);
+                for (int t = e.t0; t <= e.t1; ++t) {
+                    const int iy = wrap_index(t, H);
+                    for (int si = e.s0; si <= e.s1; ++si) {
+                        const float w = ewa_weight(e, si, t, lut);
+                        if (!(w > 0.0f)) continue;
+                        S += w;
+                        const Material m = fetch(T, lvl, wrap_index(si, W), iy);
+                        if (MODE == M_NTAP_BEFORE) {
+                            mb.rho.x = fmaf(w, m.rho.x, mb.rho.x);
+                            mb.rho.y = fmaf(w, m.rho.y, mb.rho.y);
+                            mb.rho.z = fmaf(w, m.rho.z, mb.rho.z);
+                            mb.rough = fmaf(w, m.rough, mb.rough);
+                            mb.n.x = fmaf(w, m.n.x, mb.n.x);
+                            mb.n.y = fmaf(w, m.n.y, mb.n.y);
+                            mb.n.z = fmaf(w, m.n.z, mb.n.z);
+                        } else {
+                            const float3 f = shade(a.shade, m, SC);
+                            ma.x = fmaf(w, f.x, ma.x);
+                            ma.y = fmaf(w, f.y, ma.y);
+                            ma.z = fmaf(w, f.z, ma.z);
+                        }
+                    }
+                }
+                if (!(S > 0.0f)) continue;
+                const float k = wl / S;
+                if (MODE == M_NTAP_BEFORE) {
+                    fm.rho.x = fmaf(k, mb.rho.x, fm.rho.x);
+                    fm.rho.y = fmaf(k, mb.rho.y, fm.rho.y);
+                    fm.rho.z = fmaf(k, mb.rho.z, fm.rho.z);
+                    fm.rough = fmaf(k, mb.rough, fm.rough);
+                    fm.n.x = fmaf(k, mb.n.x, fm.n.x);
+                    fm.n.y = fmaf(k, mb.n.y, fm.n.y);
+                    fm.n.z = fmaf(k, mb.n.z, fm.n.z);
+                } else {
+                    est.x = fmaf(k, ma.x, est.x);
+                    est.y = fmaf(k, ma.y, est.y);
+                    est.z = fmaf(k, ma.z, est.z);
+                }
+            }
+            if (MODE == M_NTAP_BEFORE) {
+                const float ln2 = dot3(fm.n, fm.n);
+                if (ln2 > 0.0f) {
+                    const float inv = 1.0f / sqrtf(ln2);
+                    fm.n = make_float3(fm.n.x * inv, fm.n.y * inv, fm.n.z * inv);
+                } else {
+                    fm.n = make_float3(0.f, 0.f, 1.f);
+                }
+                est = shade(a.shade, fm, SC);
+            }
+            if (picks) {
+                uint32_t* p2 = picks + (q * a.spp + s) * 2;
+                p2[0] = NO_PICK;
+                p2[1] = NO_PICK;
+            }
+        }
+        acc.x += est.x; acc.y += est.y; acc.z += est.z;
+    }
+    const float inv_spp = 1.0f / (float)a.spp;
+    a.r[q] = acc.x * inv_spp;
+    a.g[q] = acc.y * inv_spp;
+    a.b[q] = acc.z * inv_spp;
+}
+
 // Resident 256-thread blocks per SM the register budget is set for: 5 for the specialised
 // 1-tap variants (<= 51 registers), 4 otherwise (<= 64; positivization needs them).
-template <int MODE, int V>
-constexpr int min_blocks() { return (V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
+template <int FILTER, int MODE, int V>
+constexpr int min_blocks() { return (FILTER != F_EWA && V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
 
 template <int FILTER, int MODE, int V>
-__global__ void __launch_bounds__(256, min_blocks<MODE, V>())
+__global__ void __launch_bounds__(256, min_blocks<FILTER, MODE, V>())
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        query_body<FILTER, MODE, V>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
+    if constexpr (FILTER == F_EWA) {
+        __shared__ float lut[EWA_LUT_N];
+        for (int i = threadIdx.x; i < EWA_LUT_N; i += blockDim.x) lut[i] = a.ewa_lut[i];
+        __syncthreads();
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            ewa_query<MODE, V>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i, lut);
+    } else {
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            query_body<FILTER, MODE, V>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
+    }
 }
 
 // Bindless persistent launch: one grid sized to the SMs; each block claims the next
@@ -322,7 +532,7 @@ k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst
 // each query's texture descriptor in the table.  An out-of-range texture id sets
 // DEV_BAD_INDEX and yields 0.
 template <int FILTER, int MODE, int V>
-__global__ void __launch_bounds__(256, min_blocks<MODE, V>())
+__global__ void __launch_bounds__(256, min_blocks<FILTER, MODE, V>())
 k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint32_t ntex,
                      const uint32_t* __restrict__ tex_id, unsigned long long* counter, ShadeConst SC, RoundKeys K) {
     __shared__ unsigned long long chunk;
@@ -363,8 +573,8 @@ static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const 
     (void)num_sms;
     switch (kernel_variant(a.flags, a.picks)) {
         case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
-        case KV_LATTICE:   // the lattice flag changes only the stochastic picks
-            if constexpr (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED)
+        case KV_LATTICE:   // the lattice flag changes only the separable stochastic picks
+            if constexpr (FILTER != F_EWA && (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED))
                 return launch_one<FILTER, MODE, KV_LATTICE>(a, T, SC, st);
             break;
         default: break;
@@ -470,6 +680,7 @@ cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int
         case F_BSPLINE: return launch_f<F_BSPLINE>(a, T, SC, num_sms, st);
         case F_CATMULL_ROM: return launch_f<F_CATMULL_ROM>(a, T, SC, num_sms, st);
         case F_MITCHELL: return launch_f<F_MITCHELL>(a, T, SC, num_sms, st);
+        case F_EWA: return launch_f<F_EWA>(a, T, SC, num_sms, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -63,14 +63,18 @@ stf_status validate_filter_call(stf_ctx c, stf_tex t, const stf_queries* q, cons
     if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle");
     *rec = &it->second;
     if (!q || !out) return fail(c, STF_ERR_INVALID_ARG, "queries and output must be non-null");
-    if (bad_enum_filter(f) || bad_enum_mode(m) || (sh != STF_SHADE_GGX_LAMBERT && sh != STF_SHADE_LINEAR))
+    if ((bad_enum_filter(f) && f != STF_FILTER_EWA) || bad_enum_mode(m) ||
+        (sh != STF_SHADE_GGX_LAMBERT && sh != STF_SHADE_LINEAR))
         return fail(c, STF_ERR_INVALID_ARG, "filter, mode or shade out of range");
     if (m == STF_MODE_STOCHASTIC_POSITIVIZED && !signed_filter(f))
         return fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
     if (spp == 0) return fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
     if ((flags & STF_FLAG_REUSE) && m == STF_MODE_STOCHASTIC_POSITIVIZED)
         return fail(c, STF_ERR_UNSUPPORTED, "sample reuse is defined for the 1-tap estimator");
-    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE)) return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE | STF_FLAG_LOD0))
+        return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if (f == STF_FILTER_EWA && (flags & ~(uint32_t)STF_FLAG_LOD0))
+        return fail(c, STF_ERR_UNSUPPORTED, "EWA takes no jitter, lattice or reuse flags");
     if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0)
         return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
     if (q->n == 0) return STF_OK;
@@ -134,6 +138,16 @@ stf_status stf_create(int device, void* cuda_stream, stf_ctx* out) {
     stf_status s = dev_alloc(c, (void**)&c->d_status, sizeof(uint32_t));
     if (s != STF_OK) { delete c; return s; }
     cudaMemset(c->d_status, 0, sizeof(uint32_t));
+    // EWA weights exp(-2 r^2) - exp(-2) at r^2 = i/127, rounded once to FP32
+    float lut[stf::EWA_LUT_N];
+    for (int i = 0; i < stf::EWA_LUT_N; ++i) {
+        const double r2 = (double)i / (double)(stf::EWA_LUT_N - 1);
+        lut[i] = (float)(std::exp(-2.0 * r2) - std::exp(-2.0));
+    }
+    s = dev_alloc(c, (void**)&c->d_ewa_lut, sizeof(lut));
+    if (s == STF_OK && cudaMemcpy(c->d_ewa_lut, lut, sizeof(lut), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = STF_ERR_CUDA;
+    if (s != STF_OK) { cudaFree(c->d_status); if (c->d_ewa_lut) cudaFree(c->d_ewa_lut); delete c; return s; }
     *out = c;
     return STF_OK;
 }
@@ -152,6 +166,7 @@ stf_status stf_destroy(stf_ctx c) {
     if (c->entry_ev) cudaEventDestroy(c->entry_ev);
     if (c->stage) cudaFree(c->stage);
     if (c->d_status) cudaFree(c->d_status);
+    if (c->d_ewa_lut) cudaFree(c->d_ewa_lut);
     delete c;
     return STF_OK;
 }
@@ -281,6 +296,7 @@ static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries
     a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
     a.seed = seed; a.r = out->r; a.g = out->g; a.b = out->b; a.picks = out->picks;
     a.status = c->d_status;
+    a.ewa_lut = c->d_ewa_lut;
     cudaError_t e = stf::launch_filter_shade(a, rec.view, c->num_sms, stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "filter_shade launch");
 }
@@ -423,6 +439,8 @@ stf_status stf_filter_shade_table(stf_ctx c, stf_table t, const stf_queries* q, 
     auto it = c->tables.find(t);
     if (it == c->tables.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown table handle");
     if (c->tex.empty()) return fail(c, STF_ERR_BAD_HANDLE, "no textures");
+    if (f == STF_FILTER_EWA || (flags & STF_FLAG_LOD0))
+        return fail(c, STF_ERR_UNSUPPORTED, "the texture table takes the separable filters and no LOD0 flag");
     // validate everything but the texture handle with the regular checks
     TexRec* any = nullptr;
     stf_status s = validate_filter_call(c, c->tex.begin()->first, q, d, f, m, sh, spp, flags, out, &any);

@@ -44,6 +44,7 @@ struct stf_ctx_s {
     cudaStream_t stream = nullptr;
     int num_sms = 148;
     uint32_t* d_status = nullptr;
+    float* d_ewa_lut = nullptr;     // EWA Gaussian weight table (128 floats)
     std::string last_error;
     uint64_t next_handle = 1;
     std::unordered_map<uint64_t, TexRec> tex;

@@ -37,7 +37,10 @@ struct FilterShadeArgs {
     float *r, *g, *b;
     uint32_t* picks;
     uint32_t* status;
+    const float* ewa_lut;     // EWA: the 128 Gaussian weights (context-owned device array)
 };
+
+constexpr int EWA_LUT_N = 128;
 
 struct MarchArgs {
     const __half* vox;    // nz*ny*nx FP16

@@ -222,6 +222,28 @@ def queries_uniform(n: int, seed: int, res: int | None = None, lod_range: float 
     return Queries(u, v)
 
 
+def queries_aniso(n: int, seed: int, res: int, lod_range: float = 4.0, max_aniso: float = 64.0) -> Queries:
+    """uv uniform on the 2^-24 grid with anisotropic footprints: the minor axis is
+    2^lam / res long (lam ~ U[0, lod_range)), the major axis a times longer (a log-uniform in
+    [1, max_aniso]), at a random rotation; which of ddx / ddy is the major axis is random."""
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, 1 << 24, size=(2, n), dtype=np.int64)
+    u = (k[0].astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    v = (k[1].astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    lam = lod_range * rng.random(n)
+    a = np.exp(np.log(max_aniso) * rng.random(n))
+    th = 2 * math.pi * rng.random(n)
+    mn = np.exp2(lam) / res
+    c, s = np.cos(th), np.sin(th)
+    maj = np.stack([c * mn * a, s * mn * a])          # (2, n): (du, dv) of the major axis
+    mnr = np.stack([-s * mn, c * mn])
+    swap = rng.random(n) < 0.5
+    dx = np.where(swap, mnr, maj)
+    dy = np.where(swap, maj, mnr)
+    f = lambda x: x.astype(np.float32)
+    return Queries(u, v, f(dx[0]), f(dx[1]), f(dy[0]), f(dy[1]))
+
+
 # ---------------------------------------------------------------------------------
 # volume and camera
 # ---------------------------------------------------------------------------------

@@ -561,3 +561,137 @@ def test_volume_reuse_unbiased():
         d.append(s - a)
     d = np.array(d)
     assert abs(d.mean()) < 4 * d.std() / math.sqrt(len(d)) + 1e-12
+
+
+# ------------------------------------------------------------------------ EWA (supplement "Stochastic EWA")
+def test_ewa_table_closed_form():
+    # 128 Gaussian weights exp(-2 r^2) - exp(-2) at r^2 = i/127: 1 - e^-2 at the centre, 0 at
+    # the rim, strictly decreasing
+    t = oracle.ewa_table().astype(np.float64)
+    r2 = np.arange(128) / 127.0
+    np.testing.assert_allclose(t, np.exp(-2 * r2) - math.exp(-2), rtol=1e-7, atol=1e-8)
+    assert t[0] == np.float32(1 - math.exp(-2)) and t[127] == 0.0
+    assert np.all(np.diff(t) < 0)
+
+
+@pytest.mark.parametrize("case", [
+    (0.31, 0.47, 0.0, 0.0, 0.0, 0.0, 64),                      # magnification: unit circle
+    (0.5, 0.5, 8 / 64, 0.0, 0.0, 1 / 64, 64),                  # axis-aligned, 8 x 1 texels
+    (0.2, 0.7, 0.09, 0.05, -0.012, 0.02, 64),                  # rotated, anisotropic
+    (0.6, 0.3, 0.5 / 64, 1.2 / 64, 0.011 / 64, -0.005 / 64, 64),  # eccentricity above 64: capped
+])
+def test_ewa_weights_match_fp64_quadratic_form(case):
+    # r^2 = x^T (J J^T + I)^-1 x: the covariance of the pixel footprint (columns of J = the
+    # derivative vectors in texels, the minor one stretched to major/64 if the ratio is
+    # larger) plus a one-texel reconstruction term.  Brute force in FP64 with numpy's
+    # inverse; the FP32 weights must equal table[floor(128 r^2)] except at bin edges.
+    x, y, a, b, c, d, R = case
+    box, w = oracle.ewa_box(x, y, a, b, c, d, R, R)
+    f32 = lambda z: float(np.float32(z))
+    J = np.array([[f32(a) * R, f32(c) * R], [f32(b) * R, f32(d) * R]], dtype=np.float64)
+    l0, l1 = np.linalg.norm(J[:, 0]), np.linalg.norm(J[:, 1])
+    if min(l0, l1) > 0 and min(l0, l1) * 64 < max(l0, l1):
+        k = 0 if l0 < l1 else 1
+        J[:, k] *= max(l0, l1) / (min(l0, l1) * 64)
+    Minv = np.linalg.inv(J @ J.T + np.eye(2))
+    cx, cy = f32(x) * R - 0.5, f32(y) * R - 0.5
+    table = oracle.ewa_table()
+    s0, s1, t0, t1 = box
+    checked = 0
+    for t in range(t0, t1 + 1):
+        for s in range(s0, s1 + 1):
+            p = np.array([s - cx, t - cy])
+            r2 = float(p @ Minv @ p)
+            got = w[t - t0, s - s0]
+            if abs(r2 - 1.0) < 1e-4 or abs(r2 * 128 - round(r2 * 128)) < 1e-3:
+                continue      # FP32 and FP64 may fall on either side of an edge
+            want = table[int(r2 * 128)] if r2 < 1.0 else 0.0
+            assert got == want, (s, t, r2, got, want)
+            checked += 1
+    assert checked > 0
+    # the box covers the ellipse: no texel just outside it is inside the ellipse
+    for t in range(t0 - 1, t1 + 2):
+        for s in (s0 - 1, s1 + 1):
+            p = np.array([s - cx, t - cy])
+            assert float(p @ Minv @ p) > 1.0 - 1e-4
+
+
+def _ewa_query(du0, dv0, du1, dv1, n=1, u=0.37, v=0.61):
+    f = lambda z: np.full(n, z, dtype=np.float32)
+    return synth.Queries(f(u), f(v), f(du0), f(dv0), f(du1), f(dv1))
+
+
+def test_ewa_magnification_at_texel_centre_is_point_sample():
+    # zero footprint at a texel centre: the unit circle holds only that texel (its
+    # neighbours are at r^2 = 1, outside), so every EWA mode returns that texel exactly
+    tex = _tiny_tex(8, seed=23)
+    img = tex.levels[0].astype(np.float64)
+    q = synth.Queries(np.array([2.5 / 8], np.float32), np.array([5.5 / 8], np.float32))
+    want = oracle.shade_batch(img[5, 2, :3][None], [img[5, 2, 3]], [[0, 0, 1]])[0]
+    for mode in ("ntap_before", "ntap_after", "stochastic"):
+        r = oracle.filter_shade(tex, q, "ewa", mode, spp=2, want_picks=True)
+        np.testing.assert_allclose(r.rgb[0], want, rtol=1e-12)
+        if mode == "stochastic":
+            assert np.all(r.picks[0, :, 0] == ((5 << 14) | 2))
+
+
+def test_ewa_constant_texture_reproduced():
+    c = np.zeros((16, 16, 4), dtype=np.float32)
+    c[...] = [0.3, 0.5, 0.1, 0.6]
+    tex = oracle.Texture([c])
+    q = synth.queries_aniso(200, 3, res=16, lod_range=1.0, max_aniso=16)
+    want = oracle.shade_batch(c[0, 0, :3].astype(np.float64)[None], [c[0, 0, 3]], [[0, 0, 1]])[0]
+    for mode in ("ntap_before", "ntap_after", "stochastic"):
+        r = oracle.filter_shade(tex, q, "ewa", mode, spp=3)
+        np.testing.assert_allclose(r.rgb, np.broadcast_to(want, r.rgb.shape), rtol=1e-12)
+
+
+def test_ewa_stochastic_pick_frequencies_follow_weights():
+    # the reservoir pick over the ellipse chooses texel i with probability w_i / sum w:
+    # chi-square of 2^16 picks of one query (one level) against the table weights
+    tex = _tiny_tex(64, seed=5)
+    q = _ewa_query(5 / 64, 1.5 / 64, -0.8 / 64, 2.2 / 64)
+    spp = 1 << 16
+    r = oracle.filter_shade(tex, q, "ewa", "stochastic", spp=spp, seed=9, flags=oracle.FLAG_LOD0, want_picks=True)
+    box, w = oracle.ewa_box(q.u[0], q.v[0], q.dudx[0], q.dvdx[0], q.dudy[0], q.dvdy[0], 64, 64)
+    s0, s1, t0, t1 = box
+    pk = r.picks[0, :, 0]
+    ix, iy = pk & 0x3FFF, (pk >> 14) & 0x3FFF
+    counts = np.zeros_like(w, dtype=np.float64)
+    ss = (np.arange(s0, s1 + 1) % 64)
+    tt = (np.arange(t0, t1 + 1) % 64)
+    for j, t in enumerate(tt):
+        for i, s in enumerate(ss):
+            counts[j, i] = np.count_nonzero((ix == s) & (iy == t))
+    assert counts[w == 0].sum() == 0
+    p = w[w > 0].astype(np.float64) / w.sum(dtype=np.float64)
+    e = spp * p
+    chi2 = float(((counts[w > 0] - e) ** 2 / e).sum())
+    dof = p.size - 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof), (chi2, dof)
+
+
+def test_ewa_stochastic_mean_converges_to_filter_after():
+    # unbiasedness: with the same seeds the stochastic level choice is shared, and the
+    # single-tap mean converges to the N-tap filter-after value (3 sigma on the difference)
+    m = synth.material_rgba8(32, 6, octaves=4, base=2)
+    tex = oracle.Texture(m.albedo_rough, m.normal)
+    q = synth.queries_aniso(6, 8, res=32, lod_range=2.0, max_aniso=8)
+    spp = 1 << 14
+    s = oracle.filter_shade(tex, q, "ewa", "stochastic", spp=spp, seed=4)
+    a = oracle.filter_shade(tex, q, "ewa", "ntap_after", spp=1, seed=4)
+    small = np.array([oracle.filter_shade(tex, q, "ewa", "stochastic", spp=1, seed=500 + k).rgb for k in range(256)])
+    sd = small.std(axis=0) + 1e-6
+    z = np.abs(s.rgb - a.rgb) / (sd / math.sqrt(spp))
+    assert z.max() < 4.5, z.max()
+
+
+def test_lod0_flag_uses_the_finest_level_only():
+    m = synth.material_rgba8(32, 6, octaves=4, base=2)
+    tex = oracle.Texture(m.albedo_rough, m.normal)
+    q = synth.queries_aniso(200, 11, res=32, lod_range=4.0)
+    for f in ("bspline", "ewa"):
+        r = oracle.filter_shade(tex, q, f, "stochastic", spp=2, flags=oracle.FLAG_LOD0, want_picks=True)
+        assert np.all((r.picks[..., 0] >> 28) == 0)
+        base = oracle.filter_shade(tex, q, f, "stochastic", spp=2, want_picks=True)
+        assert np.any((base.picks[..., 0] >> 28) > 0)
