@@ -37,7 +37,9 @@ LOD_RANGE = 8.0
 SPP = 8
 FILTERS = ("linear", "bspline", "mitchell")
 METRIC = "shaded texture lookups/s, stochastic 1-tap vs N-tap, at equal RMSE vs FP64"
+STRATIFIED = 1                    # STF_FLAG_STRATIFIED
 LATTICE = 2                       # STF_FLAG_LATTICE
+LOD0 = 8                          # STF_FLAG_LOD0
 # algorithmic ALU operations per stochastic lookup (8 spp; per-query work amortised), counted
 # step by step in the design notes: Philox-10 (40), 5 uniforms (19), jitter (6), level (3),
 # two axes of position + weights + CDF, sign/weight, addressing, decode (30), GGX (80), accumulate
@@ -249,6 +251,7 @@ def run_ours(args):
             "roofline": roof, "gather_roofline": gather, "e2e": e2e, "gpu_launches": args.steps * len(FILTERS), "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_extras:
         line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
+        line["aniso"] = aniso_block(ctx, tex, dev)
         line["volume"] = volume_block(ctx, dev, args)
         line["table"] = table_block(ctx, dev)
         line["neural"] = neural_block(ctx, dev, material)
@@ -368,6 +371,61 @@ def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
             "s_star_below_8_allowed": s_any,
             "equal_rmse_speedup_below_8_allowed": (t_before / t_any) if t_any else None,
         }
+    return res
+
+
+def aniso_block(ctx, tex, dev, nq=1 << 22, nsub=1 << 16, lod_range=3.0, max_aniso=32.0):
+    """Anisotropic minification (Sec. 4.2.1, supplement "Stochastic EWA"): 2^22 queries on the
+    4096^2 material whose footprints have a minor axis of 1-8 texels and an anisotropy of 1-32
+    (log-uniform), random rotation.  Reference: the footprint integral of the level-0
+    filter-after-shading value, 64 x 64 stratified screen-space samples of bilinear lookups
+    at the finest level, on a 2^16-query subset.  Methods: screen-space jitter with the
+    minor-axis stochastic level (trilinear and B-spline, 1 tap), the same at the finest
+    level only, stochastic EWA (1 tap), and EWA filter-before / filter-after (N taps)."""
+    import torch
+    q = synth.queries_aniso(nq, 44, res=TEX_RES, lod_range=lod_range, max_aniso=max_aniso)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    u, v, d = t(q.u), t(q.v), [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]
+    sub = lambda x: x[:nsub]
+    us, vs, ds = sub(u), sub(v), [sub(x) for x in d]
+    mk = lambda n: [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    ref = mk(nsub)
+    ctx.filter_shade(tex, us, vs, ds, "linear", "ntap_after", "ggx", 64 * 64, 1, LOD0 | STRATIFIED, out=ref)
+    R = torch.stack(ref, 1).double()
+    out_s, out_f = mk(nsub), mk(nq)
+    methods = {"stochastic_trilinear_jitter": ("linear", "stochastic", 0),
+               "stochastic_bspline_jitter": ("bspline", "stochastic", 0),
+               "stochastic_bspline_jitter_lod0": ("bspline", "stochastic", LOD0),
+               "stochastic_ewa": ("ewa", "stochastic", 0),
+               "ewa_ntap_before": ("ewa", "ntap_before", 0),
+               "ewa_ntap_after": ("ewa", "ntap_after", 0)}
+    res = {"queries": nq, "rmse_subset": nsub, "minor_axis_texels": [1, 2 ** lod_range], "max_aniso": max_aniso,
+           "reference": "level-0 filter-after footprint integral, 64x64 stratified bilinear samples"}
+    for name, (filt, mode, flags) in methods.items():
+        ntap = mode != "stochastic"
+        grid = (1,) if ntap else (1, 2, 4, 8, 16, 32)
+        curve = {}
+        for spp in grid:
+            ctx.filter_shade(tex, us, vs, ds, filt, mode, "ggx", spp, 7, flags, out=out_s)
+            curve[spp] = float(((torch.stack(out_s, 1).double() - R) ** 2).mean().sqrt())
+        spp_t = 1 if ntap else 8
+        ms = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, mode, "ggx", spp_t, 7, flags, out=out_f))
+        res[name] = {"rmse": {str(k): v for k, v in curve.items()}, "ms": ms, "spp_timed": spp_t,
+                     "lookups_per_s": nq * spp_t / (ms / 1e3)}
+    # equal RMSE against EWA filter-before (the conventional anisotropic filter): the least
+    # spp on the grid whose RMSE reaches it, timed at that spp on all queries
+    target = res["ewa_ntap_before"]["rmse"]["1"]
+    t_before = res["ewa_ntap_before"]["ms"]
+    for name in ("stochastic_trilinear_jitter", "stochastic_bspline_jitter", "stochastic_ewa"):
+        r = res[name]
+        filt, mode, flags = methods[name]
+        s_star = next((int(k) for k, v in r["rmse"].items() if v <= target), None)
+        r["s_star_vs_ewa_before"] = s_star
+        if s_star:
+            ms = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, mode, "ggx", s_star, 7, flags, out=out_f))
+            r["equal_rmse_speedup_vs_ewa_before"] = t_before / ms
+        else:
+            r["equal_rmse_speedup_vs_ewa_before"] = None
     return res
 
 

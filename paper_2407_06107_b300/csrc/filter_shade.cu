@@ -362,6 +362,23 @@ __device__ __forceinline__ EwaBox ewa_setup(float x, float y, float dudx, float 
     return e;
 }
 
+// The columns of row t that can lie inside the ellipse: the roots of A s^2 + (B t) s +
+// (C t^2 - 1) = 0 around the centre, widened by one texel against FP32 error and clipped
+// to the box.  Texels outside the ellipse have weight 0 and change no sum and no reservoir
+// state, so scanning only this range gives the same results as scanning the whole box.
+// Every texel with a non-zero weight has r^2 < 127/128 (table entry 127 is exactly 0), so
+// its row's discriminant is far from zero and cannot round to a negative value.
+__device__ __forceinline__ void ewa_row(const EwaBox& e, int t, int* lo, int* hi) {
+    const float tt = (float)t - e.cy;
+    const float b = e.B * tt, c = fmaf(e.C * tt, tt, -1.0f);
+    const float disc = fmaf(b, b, -4.0f * e.A * c);
+    if (!(disc >= 0.0f)) { *lo = 0; *hi = -1; return; }
+    const float r = sqrtf(disc), inv2a = 0.5f / e.A;
+    const float s_lo = e.cx + (-b - r) * inv2a - 1.0f, s_hi = e.cx + (-b + r) * inv2a + 1.0f;
+    *lo = max(e.s0, (int)ceilf(fmaxf(s_lo, (float)e.s0)));
+    *hi = min(e.s1, (int)floorf(fminf(s_hi, (float)e.s1)));
+}
+
 __device__ __forceinline__ float ewa_weight(const EwaBox& e, int s, int t, const float* lut) {
     const float ss = __fsub_rn((float)s, e.cx), tt = __fsub_rn((float)t, e.cy);
     const float r2 = __fmaf_rn(__fmul_rn(e.A, ss), ss,
@@ -404,8 +421,10 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
             float uu = A5.u[3], sum = 0.0f;
             int ps = 0, pt = 0;
             bool any = false;
-            for (int t = e.t0; t <= e.t1; ++t)
-                for (int si = e.s0; si <= e.s1; ++si) {
+            for (int t = e.t0; t <= e.t1; ++t) {
+                int rlo, rhi;
+                ewa_row(e, t, &rlo, &rhi);
+                for (int si = rlo; si <= rhi; ++si) {
                     const float w = ewa_weight(e, si, t, lut);
                     if (!(w > 0.0f)) continue;
                     sum = __fadd_rn(sum, w);
@@ -413,6 +432,7 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
                     if (uu < p) { ps = si; pt = t; any = true; uu = __fdiv_rn(uu, p); }
                     else uu = __fdiv_rn(__fsub_rn(uu, p), __fsub_rn(1.0f, p));
                 }
+            }
             uint32_t pk = NO_PICK;
             if (any) {
                 const int ix = wrap_index(ps, W), iy = wrap_index(pt, H);
@@ -444,7 +464,9 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
                 float3 ma = make_float3(0.f, 0.f, 0.f);
                 for (int t = e.t0; t <= e.t1; ++t) {
                     const int iy = wrap_index(t, H);
-                    for (int si = e.s0; si <= e.s1; ++si) {
+                    int rlo, rhi;
+                    ewa_row(e, t, &rlo, &rhi);
+                    for (int si = rlo; si <= rhi; ++si) {
                         const float w = ewa_weight(e, si, t, lut);
                         if (!(w > 0.0f)) continue;
                         S += w;
