@@ -252,6 +252,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras:
         line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
         line["aniso"] = aniso_block(ctx, tex, dev)
+        line["dct"] = dct_block(ctx, material, u, v, d, dev)
         line["volume"] = volume_block(ctx, dev, args)
         line["table"] = table_block(ctx, dev)
         line["neural"] = neural_block(ctx, dev, material)
@@ -426,6 +427,53 @@ def aniso_block(ctx, tex, dev, nq=1 << 22, nsub=1 << 16, lod_range=3.0, max_anis
             r["equal_rmse_speedup_vs_ewa_before"] = t_before / ms
         else:
             r["equal_rmse_speedup_vs_ewa_before"] = None
+    return res
+
+
+def dct_block(ctx, material, u, v, d, dev, nsub=1 << 16):
+    """DCT-compressed material (supplement "Texture compression"): the 4096^2 material's MIP
+    chain in 8 x 8 blocks of six DCT coefficients per channel (4 bytes each, 16x smaller than
+    the 8-bit channels; the 32-byte blocks carry 8 bytes of padding).  A stochastic lookup
+    decodes one texel per sample where trilinear filter-before decodes 8 and bicubic 32.  Times
+    over the bench's 2^24 queries at 8 and at 1 spp; RMSE against the exact filter-after value
+    on the compressed texture (16 x 16 stratified footprint samples) on a 2^16-query subset."""
+    import torch
+    blocks = synth.dct_compress(material)
+    th = ctx.create_texture_dct(blocks, TEX_RES, TEX_RES)
+    raw = sum(a.nbytes + b.nbytes for a, b in zip(material.albedo_rough, material.normal))
+    res = {"compressed_bytes": int(sum(b.nbytes for b in blocks)), "uncompressed_bytes": int(raw)}
+    sub = lambda x: x[:nsub]
+    us, vs, ds = sub(u), sub(v), [sub(x) for x in d]
+    mk = lambda n: [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    nfull = u.shape[0]
+    outf = mk(nfull)
+    for filt in ("linear", "bspline"):
+        ref = mk(nsub)
+        ctx.filter_shade(th, us, vs, ds, filt, "ntap_after", "ggx", 256, 1, STRATIFIED, out=ref)
+        R = torch.stack(ref, 1).double()
+
+        def rmse(mode, spp):
+            o = mk(nsub)
+            ctx.filter_shade(th, us, vs, ds, filt, mode, "ggx", spp, 7, 0, out=o)
+            return float(((torch.stack(o, 1).double() - R) ** 2).mean().sqrt())
+        r_before = rmse("ntap_before", 8)
+        curve = {sp: rmse("stochastic", sp) for sp in SPP_GRID}
+        s_star, _ = _s_star(curve, r_before)
+        t = {}
+        for mode in ("ntap_before", "stochastic"):
+            for sp in (1, 8):
+                t[(mode, sp)] = _time_launch(lambda: ctx.filter_shade(th, u, v, d, filt, mode, "ggx", sp, 1, 0, out=outf))
+        t_star = (_time_launch(lambda: ctx.filter_shade(th, u, v, d, filt, "stochastic", "ggx", s_star, 1, 0, out=outf))
+                  if s_star else None)
+        res[filt] = {"taps": 8 if filt == "linear" else 32, "rmse_ntap_before_8spp": r_before,
+                     "rmse_stochastic": {str(k): val for k, val in curve.items()},
+                     "ms_ntap_before_1spp": t[("ntap_before", 1)], "ms_stochastic_1spp": t[("stochastic", 1)],
+                     "ms_ntap_before_8spp": t[("ntap_before", 8)], "ms_stochastic_8spp": t[("stochastic", 8)],
+                     "speedup_1spp": t[("ntap_before", 1)] / t[("stochastic", 1)],
+                     "equal_spp_speedup_8spp": t[("ntap_before", 8)] / t[("stochastic", 8)],
+                     "stochastic_lookups_per_s": nfull * 8 / (t[("stochastic", 8)] / 1e3),
+                     "s_star": s_star, "equal_rmse_speedup": (t[("ntap_before", 8)] / t_star) if t_star else None}
+    ctx.destroy_texture(th)
     return res
 
 

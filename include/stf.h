@@ -58,7 +58,18 @@ typedef enum {
     STF_FMT_RGBA32F = 0,  /* RGB albedo, A = roughness (GGX alpha), 16 B/texel            */
     STF_FMT_RGBA8 = 1,    /* UNORM albedo RGB, A byte -> roughness 0.05 + 0.95 a/255       */
     STF_FMT_RG8 = 2,      /* tangent-space normal XY (UNORM, z reconstructed)              */
-    STF_FMT_R16F = 3      /* FP16 density (volumes)                                       */
+    STF_FMT_R16F = 3,     /* FP16 density (volumes)                                       */
+    STF_FMT_DCT6 = 4      /* DCT-compressed material (supplement "Texture compression"): per
+                             level, ceil(H/8) x ceil(W/8) blocks of 32 bytes, row-major, each 6
+                             little-endian uint32 channel words (albedo R, G, B, roughness,
+                             normal X, Y, each in [0,1]) and 8 padding bytes.  A word holds the
+                             orthonormal 2-D DCT-II coefficients u + v <= 2 of one 8 x 8 block:
+                             bits 0-6 the DC term (q * 8/127), then 5-bit fields for (u,v) =
+                             (1,0), (0,1), (2,0), (1,1), (0,2) ((q - 15) * 2/15).  Levels narrower
+                             than 8 repeat periodically inside their block.  A texel decodes to
+                             the inverse DCT of those six terms at its position; roughness maps
+                             to 0.05 + 0.95 r, the normal to (2x-1, 2y-1, z) normalised.
+                             stf_filter_shade only (not texture tables); no normal_data. */
 } stf_format;
 
 /* 1-D reconstruction kernels, applied separably (supplement "Filter Kernels").

@@ -80,6 +80,8 @@ def lib():
         L.orc_weights32.argtypes = [C.c_int, C.c_float, P]
         L.orc_pick32.argtypes = [P, C.c_int, C.c_float, C.c_int]
         L.orc_ewa_table.argtypes = [P]
+        L.orc_dct_texel.argtypes = [C.c_uint32, C.c_int, C.c_int]
+        L.orc_dct_texel.restype = C.c_double
         L.orc_ewa_box.argtypes = [C.c_float] * 6 + [C.c_int, C.c_int, P, P, C.c_int]
         L.orc_pick32_reuse.argtypes = [P, C.c_int, C.c_float, P]
         L.orc_pick_array.argtypes = [P, C.c_int, C.c_double]
@@ -150,6 +152,11 @@ def pick32(w, xi: float, cls: int = 0) -> int:
     return lib().orc_pick32(_p(w), len(w), float(np.float32(xi)), cls)
 
 
+def dct_texel(word: int, x: int, y: int) -> float:
+    """Raw decoded value of one DCT channel word at (x, y) in its block."""
+    return float(lib().orc_dct_texel(int(word), int(x), int(y)))
+
+
 def ewa_table() -> np.ndarray:
     """The 128 Gaussian weights exp(-2 r^2) - exp(-2) at r^2 = i/127 (FP32)."""
     out = np.zeros(128, np.float32)
@@ -216,6 +223,7 @@ class Texture:
     address: str = "wrap"
 
     neural: "NeuralTexture | None" = None
+    dct: list | None = None      # DCT blocks per level ((H8, W8, 32) uint8); levels = level sizes
 
     def _struct(self):
         t = _Tex()
@@ -224,6 +232,15 @@ class Texture:
             t.width[0] = t.height[0] = self.neural.tex_res
             self._nt = self.neural._struct()
             t.data[0] = C.cast(C.pointer(self._nt), C.c_void_p).value
+            return t
+        if self.dct is not None:          # DCT-compressed set: self.levels holds (H, W) per level
+            t.format, t.levels, t.address = 3, len(self.dct), 0
+            self._keep = []
+            for i, (b, hw) in enumerate(zip(self.dct, self.levels)):
+                b = np.ascontiguousarray(b)
+                self._keep.append(b)
+                t.height[i], t.width[i] = int(hw[0]), int(hw[1])
+                t.data[i] = b.ctypes.data
             return t
         fmt = 0 if self.levels[0].dtype == np.float32 else 1
         t.format, t.levels = fmt, len(self.levels)

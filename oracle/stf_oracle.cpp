@@ -45,7 +45,7 @@ enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3, F_EWA = 4
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
 enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u, FLAG_LOD0 = 8u };
-enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_NEURAL = 2 };
+enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_NEURAL = 2, FMT_DCT = 3 };
 enum { ADDR_WRAP = 0, ADDR_CLAMP = 1 };
 const uint32_t NO_PICK = 0xFFFFFFFFu;
 
@@ -316,8 +316,34 @@ Mat material_from_channels(const double y[8]) {
     return m;
 }
 
+// DCT-compressed texel (supplement "Texture compression"): the inverse orthonormal 2-D DCT-II
+// of one 8 x 8 block, restricted to the six stored frequencies u + v <= 2, evaluated at the
+// texel's position (x, y) in the block.  Word layout: DC in bits 0-6 (q * 8/127), then the
+// AC terms (1,0), (0,1), (2,0), (1,1), (0,2) in 5-bit fields ((q - 15) * 2/15).
+double dct_texel(uint32_t w, int x, int y) {
+    const double pi = 3.14159265358979323846;
+    auto alpha = [](int k) { return k == 0 ? 1.0 / (2.0 * std::sqrt(2.0)) : 0.5; };
+    auto basis = [&](int u, int v) {
+        return alpha(u) * alpha(v) * std::cos((2 * x + 1) * u * pi / 16.0) * std::cos((2 * y + 1) * v * pi / 16.0);
+    };
+    double f = (double)(w & 127u) * (8.0 / 127.0) * basis(0, 0);
+    const int uv[5][2] = {{1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
+    for (int j = 0; j < 5; ++j) {
+        const int q = (int)((w >> (7 + 5 * j)) & 31u) - 15;
+        f += (double)q * (2.0 / 15.0) * basis(uv[j][0], uv[j][1]);
+    }
+    return f;
+}
+
 Mat fetch(const Tex& T, int lvl, int ix, int iy, double* rdist = nullptr) {
     Mat m;
+    if (T.format == FMT_DCT) {        // six channels: albedo RGB, roughness, normal X, Y
+        const int W8 = (T.width[lvl] + 7) / 8;
+        const uint32_t* blk = (const uint32_t*)T.data[lvl] + ((size_t)(iy / 8) * W8 + (size_t)(ix / 8)) * 8;
+        double y[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < 6; ++c) y[c] = dct_texel(blk[c], ix % 8, iy % 8);
+        return material_from_channels(y);
+    }
     if (T.format == FMT_NEURAL) {     // learned texel: one MLP decode
         double y[8];
         orc::neural_decode(*(const orc::NeuralTex*)T.data[0], ix, iy, y, rdist);
@@ -963,6 +989,9 @@ int orc_weights32(int filter, float t, float* w) { return weights32(filter, t, w
 // EWA pieces for the pins: the weight table, and the weights of an ellipse's bounding box
 // (box[4] = s0, s1, t0, t1; w gets (s1-s0+1)*(t1-t0+1) weights, t outer), or -1 if the box
 // holds more than cap weights
+// raw DCT decode of one channel word at (x, y) in its 8 x 8 block (for the pins)
+double orc_dct_texel(uint32_t word, int x, int y) { return dct_texel(word, x, y); }
+
 void orc_ewa_table(float* out) { std::memcpy(out, ewa_table(), sizeof(float) * EWA_LUT_N); }
 int orc_ewa_box(float x, float y, float dudx, float dvdx, float dudy, float dvdy, int W, int H, int* box,
                 float* w, int cap) {

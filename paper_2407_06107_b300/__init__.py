@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libstf.so")
 FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
-FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F = 0, 1, 2, 3
+FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F, FMT_DCT6 = 0, 1, 2, 3, 4
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
 FLAG_REUSE = 4
@@ -195,6 +195,17 @@ class Context:
             narr = (C.c_void_p * len(nk))(*[_ptr(x) for x in nk])
         d = _TextureDesc(int(keep[0].shape[1]), int(keep[0].shape[0]), len(levels), fmt,
                          0 if address == "wrap" else 1, arr, narr, 1 if on_dev else 0)
+        out = C.c_uint64(0)
+        self._check(lib().stf_create_texture(self.h, C.byref(d), C.byref(out)), self.h)
+        return int(out.value)
+
+    def create_texture_dct(self, blocks, width: int, height: int) -> int:
+        """DCT-compressed material: per level a (ceil(H/8), ceil(W/8), 32) uint8 block array
+        (numpy host or torch cuda); width, height of level 0."""
+        on_dev = not isinstance(blocks[0], np.ndarray)
+        keep = [b if on_dev else np.ascontiguousarray(b, dtype=np.uint8) for b in blocks]
+        arr = (C.c_void_p * len(keep))(*[_ptr(x) for x in keep])
+        d = _TextureDesc(int(width), int(height), len(keep), FMT_DCT6, 0, arr, None, 1 if on_dev else 0)
         out = C.c_uint64(0)
         self._check(lib().stf_create_texture(self.h, C.byref(d), C.byref(out)), self.h)
         return int(out.value)

@@ -32,6 +32,28 @@ __device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, in
     return decode_texel(T, load_texel(T, lvl, ix, iy));
 }
 
+// Texture-format family of a kernel instantiation: BASIC (RGBA32F or RGBA8 + RG8, told apart
+// at run time) or DCT (compressed blocks, decoded per texel).  A loaded texel's type and its
+// decode depend on the family, so the DCT path adds no registers to the other one.
+enum { TF_BASIC = 0, TF_DCT = 1 };
+template <int TF> struct RawOf { using type = uint4; };
+template <> struct RawOf<TF_DCT> { using type = DctRaw; };
+
+template <int TF>
+__device__ __forceinline__ typename RawOf<TF>::type load_raw(const FetchCtx& T, int lvl, int ix, int iy) {
+    if constexpr (TF == TF_DCT) return load_dct(T.base + T.off[lvl], T.w[lvl], ix, iy);
+    else return load_texel(T, lvl, ix, iy);
+}
+template <int TF>
+__device__ __forceinline__ Material decode_raw(const FetchCtx& T, const typename RawOf<TF>::type& r) {
+    if constexpr (TF == TF_DCT) return decode_dct(r);
+    else return decode_texel(T, r);
+}
+template <int TF>
+__device__ __forceinline__ Material fetch_t(const FetchCtx& T, int lvl, int ix, int iy) {
+    return decode_raw<TF>(T, load_raw<TF>(T, lvl, ix, iy));
+}
+
 __device__ __forceinline__ uint32_t pack_pick(int lvl, int ix, int iy) {
     return ((uint32_t)lvl << 28) | ((uint32_t)iy << 14) | (uint32_t)ix;
 }
@@ -73,7 +95,7 @@ __device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, co
 // parameter, or a descriptor in global memory for the bindless table).  V: the kernel
 // variant (KV_*); the specialised ones have their flags fixed and report no picks, so those
 // per-sample tests are compiled out.
-template <int FILTER, int MODE, int V = KV_GENERAL>
+template <int FILTER, int MODE, int V = KV_GENERAL, int TF = TF_BASIC>
 __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                                            const RoundKeys& K, uint64_t q) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
@@ -107,7 +129,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
         if constexpr (MODE == M_STOCHASTIC) {
             // Software-pipelined: sample s+1 is picked and its texel load issued before
             // sample s is decoded and shaded, so the gather latency hides behind shading.
-            auto pick = [&](uint32_t s, float* wt) -> uint4 {
+            auto pick = [&](uint32_t s, float* wt) -> typename RawOf<TF>::type {
                 U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
                 if (lat) {
                     const uint32_t lshift = lattice_shift(s, a.spp, 24);
@@ -164,15 +186,15 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                     pk[0] = pack_pick(lvl, ix, iy);
                     pk[1] = NO_PICK;
                 }
-                return load_texel(T, lvl, ix, iy);
+                return load_raw<TF>(T, lvl, ix, iy);
             };
             float wt_next;
-            uint4 raw_next = pick(0, &wt_next);
+            typename RawOf<TF>::type raw_next = pick(0, &wt_next);
             for (uint32_t s = 0; s < a.spp; ++s) {
-                const uint4 raw = raw_next;
+                const typename RawOf<TF>::type raw = raw_next;
                 const float Wt = wt_next;
                 if (s + 1 < a.spp) raw_next = pick(s + 1, &wt_next);
-                const float3 f = shade(a.shade, decode_texel(T, raw), SC);
+                const float3 f = shade(a.shade, decode_raw<TF>(T, raw), SC);
                 acc.x += Wt * f.x; acc.y += Wt * f.y; acc.z += Wt * f.z;
             }
         } else
@@ -210,22 +232,22 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
                 const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
                 const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
-                const uint4 raw_p = load_texel(T, lvl, ix, iy);
+                const typename RawOf<TF>::type raw_p = load_raw<TF>(T, lvl, ix, iy);
                 // both loads are issued before either texel is shaded
                 uint32_t negpick = NO_PICK;
-                uint4 raw_n = make_uint4(0u, 0u, 0u, 0u);
+                typename RawOf<TF>::type raw_n{};
                 if (Wn > 0.0f) {
                     const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
                     const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
                     const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
                     const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
-                    raw_n = load_texel(T, lvl, jx, jy);
+                    raw_n = load_raw<TF>(T, lvl, jx, jy);
                     negpick = pack_pick(lvl, jx, jy);
                 }
-                const float3 f = shade(a.shade, decode_texel(T, raw_p), SC);
+                const float3 f = shade(a.shade, decode_raw<TF>(T, raw_p), SC);
                 est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
                 if (Wn > 0.0f) {
-                    const float3 g = shade(a.shade, decode_texel(T, raw_n), SC);
+                    const float3 g = shade(a.shade, decode_raw<TF>(T, raw_n), SC);
                     est.x = fmaf(-Wn, g.x, est.x);
                     est.y = fmaf(-Wn, g.y, est.y);
                     est.z = fmaf(-Wn, g.z, est.z);
@@ -261,7 +283,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                             const float w = wyl * wx[i];
                             if (w == 0.0f) continue;
                             const int ix = wrap_index(ax.i0 + T0 + i, W);
-                            const Material m = fetch(T, lvl, ix, iy);
+                            const Material m = fetch_t<TF>(T, lvl, ix, iy);
                             if (MODE == M_NTAP_BEFORE) {
                                 fm.rho.x = fmaf(w, m.rho.x, fm.rho.x);
                                 fm.rho.y = fmaf(w, m.rho.y, fm.rho.y);
@@ -392,7 +414,7 @@ __device__ __forceinline__ float ewa_weight(const EwaBox& e, int s, int t, const
 // box in raster order, the uniform remapped after every decision; the estimate is the
 // picked texel's shade.  N-tap modes: both levels, each normalised by its own weight sum,
 // blended linearly.
-template <int MODE, int V>
+template <int MODE, int V, int TF>
 __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                                           const RoundKeys& K, uint64_t q, const float* lut) {
     const uint32_t flags = V == KV_GENERAL ? a.flags : 0u;
@@ -436,7 +458,7 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
             uint32_t pk = NO_PICK;
             if (any) {
                 const int ix = wrap_index(ps, W), iy = wrap_index(pt, H);
-                est = shade(a.shade, fetch(T, lvl, ix, iy), SC);
+                est = shade(a.shade, fetch_t<TF>(T, lvl, ix, iy), SC);
                 pk = pack_pick(lvl, ix, iy);
             }
             if (picks) {
@@ -470,7 +492,7 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
                         const float w = ewa_weight(e, si, t, lut);
                         if (!(w > 0.0f)) continue;
                         S += w;
-                        const Material m = fetch(T, lvl, wrap_index(si, W), iy);
+                        const Material m = fetch_t<TF>(T, lvl, wrap_index(si, W), iy);
                         if (MODE == M_NTAP_BEFORE) {
                             mb.rho.x = fmaf(w, m.rho.x, mb.rho.x);
                             mb.rho.y = fmaf(w, m.rho.y, mb.rho.y);
@@ -532,7 +554,7 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
 template <int FILTER, int MODE, int V>
 constexpr int min_blocks() { return (FILTER != F_EWA && V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
 
-template <int FILTER, int MODE, int V>
+template <int FILTER, int MODE, int V, int TF>
 __global__ void __launch_bounds__(256, min_blocks<FILTER, MODE, V>())
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
     if constexpr (FILTER == F_EWA) {
@@ -541,11 +563,11 @@ k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst
         __syncthreads();
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
              i += (uint64_t)gridDim.x * blockDim.x)
-            ewa_query<MODE, V>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i, lut);
+            ewa_query<MODE, V, TF>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i, lut);
     } else {
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
              i += (uint64_t)gridDim.x * blockDim.x)
-            query_body<FILTER, MODE, V>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
+            query_body<FILTER, MODE, V, TF>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
     }
 }
 
@@ -581,11 +603,11 @@ k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint
 // One block per 256 queries (one query per thread): the block scheduler keeps every SM
 // full until the last blocks.  Measured on the 2^24-query material, this is 12-13 % faster
 // than a one-wave grid-stride launch.
-template <int FILTER, int MODE, int V>
+template <int FILTER, int MODE, int V, int TF = TF_BASIC>
 static cudaError_t launch_one(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, cudaStream_t st) {
     const uint64_t blocks_needed = (a.n + 255) / 256;
     const int grid = (int)(blocks_needed < 0x7FFFFFFFull ? (blocks_needed ? blocks_needed : 1) : 0x7FFFFFFFull);
-    k_filter_shade<FILTER, MODE, V><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
+    k_filter_shade<FILTER, MODE, V, TF><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
     return cudaGetLastError();
 }
 
@@ -593,6 +615,7 @@ template <int FILTER, int MODE>
 static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, int num_sms,
                              cudaStream_t st) {
     (void)num_sms;
+    if (T.fmt == FMT_DCT) return launch_one<FILTER, MODE, KV_GENERAL, TF_DCT>(a, T, SC, st);
     switch (kernel_variant(a.flags, a.picks)) {
         case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
         case KV_LATTICE:   // the lattice flag changes only the separable stochastic picks

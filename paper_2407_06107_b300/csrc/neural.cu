@@ -282,24 +282,6 @@ __device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, i
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// decoded channels -> material (albedo, roughness, tangent-space normal)
-__device__ __forceinline__ Material material_from_channels(const float y[8]) {
-    Material m;
-    m.rho = make_float3(__saturatef(y[0]), __saturatef(y[1]), __saturatef(y[2]));
-    m.rough = fmaf(0.95f, __saturatef(y[3]), 0.05f);
-    const float x = fmaf(2.0f, __saturatef(y[4]), -1.0f), yy = fmaf(2.0f, __saturatef(y[5]), -1.0f);
-    const float z2 = 1.0f - x * x - yy * yy;
-    // z2 > 0: (x, y, sqrt z2) is a unit vector already; otherwise z = 0 and (x, y), which is
-    // then at least unit length, is normalised
-    if (z2 > 0.0f) {
-        m.n = make_float3(x, yy, z2 * rsqrt_approx(z2));
-    } else {
-        const float inv = rsqrt_approx(x * x + yy * yy);
-        m.n = make_float3(x * inv, yy * inv, 0.0f);
-    }
-    return m;
-}
-
 // ------------------------------------------------------------------ training (SIMT FP32)
 // One block = 128 samples.  Forward with BF16-rounded operands (as the tensor-core decode
 // computes), MSE loss, analytic backward; block partial gradients are atomically added.

@@ -197,14 +197,49 @@ stf_status stf_get_device_status(stf_ctx c, uint32_t* flags) {
 }
 
 // ------------------------------------------------------------------------------ textures
+// DCT-compressed levels are stored as given: ceil(H/8) x ceil(W/8) blocks of 32 bytes each.
+static stf_status create_dct_texture(stf_ctx c, const stf_texture_desc* d, stf_tex* out) {
+    if (d->normal_data) return fail(c, STF_ERR_INVALID_ARG, "DCT6 textures carry their normals in the blocks");
+    TexRec rec;
+    rec.view.fmt = stf::FMT_DCT;
+    rec.view.levels = (int)d->num_levels;
+    rec.view.has_normal = 1;
+    rec.view.address = 0;
+    size_t total = 0;
+    size_t bytes[STF_MAX_LEVELS] = {};
+    for (uint32_t l = 0; l < d->num_levels; ++l) {
+        const uint32_t w = level_dim(d->width, l), h = level_dim(d->height, l);
+        if (d->data_on_device && ((uintptr_t)d->level_data[l] & 15u))
+            return fail(c, STF_ERR_INVALID_ARG, "device DCT6 levels must be 16-byte aligned");
+        rec.view.w[l] = (int)w; rec.view.h[l] = (int)h;
+        rec.view.off[l] = total;
+        bytes[l] = (size_t)((w + 7) / 8) * ((h + 7) / 8) * 32;
+        total += (bytes[l] + 255) & ~(size_t)255;
+    }
+    for (uint32_t l = d->num_levels; l < STF_MAX_LEVELS; ++l) { rec.view.w[l] = rec.view.h[l] = 1; rec.view.off[l] = 0; }
+    stf_status s = dev_alloc(c, &rec.mem, total);
+    if (s != STF_OK) return s;
+    rec.view.base = rec.mem;
+    const cudaMemcpyKind kind = d->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaSuccess;
+    for (uint32_t l = 0; l < d->num_levels && e == cudaSuccess; ++l)
+        e = cudaMemcpyAsync((char*)rec.mem + rec.view.off[l], d->level_data[l], bytes[l], kind, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { cudaFree(rec.mem); return cuda_fail(c, e, "DCT texture upload"); }
+    const uint64_t h = c->next_handle++;
+    c->tex[h] = rec;
+    *out = h;
+    return STF_OK;
+}
+
 stf_status stf_create_texture(stf_ctx c, const stf_texture_desc* d, stf_tex* out) {
     if (!c || !d || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
     *out = 0;
     if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
         return fail(c, STF_ERR_INVALID_ARG, "texture size must be 1..16384");
     if (d->num_levels < 1 || d->num_levels > STF_MAX_LEVELS) return fail(c, STF_ERR_INVALID_ARG, "num_levels must be 1..16");
-    if (d->format != STF_FMT_RGBA32F && d->format != STF_FMT_RGBA8)
-        return fail(c, STF_ERR_INVALID_ARG, "2-D textures are RGBA32F or RGBA8");
+    if (d->format != STF_FMT_RGBA32F && d->format != STF_FMT_RGBA8 && d->format != STF_FMT_DCT6)
+        return fail(c, STF_ERR_INVALID_ARG, "2-D textures are RGBA32F, RGBA8 or DCT6");
     if (d->address != STF_ADDRESS_WRAP) return fail(c, STF_ERR_UNSUPPORTED, "2-D textures use wrap addressing");
     if (!d->level_data) return fail(c, STF_ERR_INVALID_ARG, "level_data is null");
     if (d->normal_data && d->format != STF_FMT_RGBA8) return fail(c, STF_ERR_INVALID_ARG, "normal maps accompany RGBA8 textures");
@@ -216,6 +251,7 @@ stf_status stf_create_texture(stf_ctx c, const stf_texture_desc* d, stf_tex* out
             return fail(c, STF_ERR_INVALID_ARG, "device RGBA8 levels must be 4-byte and RG8 levels 2-byte aligned");
     }
     CurrentDevice cd(c->device);
+    if (d->format == STF_FMT_DCT6) return create_dct_texture(c, d, out);
     const size_t texel = d->format == STF_FMT_RGBA32F ? 16 : 8;
     TexRec rec;
     rec.view.fmt = d->format == STF_FMT_RGBA32F ? 0 : 1;
@@ -401,6 +437,8 @@ stf_status stf_create_texture_table(stf_ctx c, uint32_t n, const stf_tex* textur
     for (uint32_t i = 0; i < n; ++i) {
         auto it = c->tex.find(textures[i]);
         if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle in table");
+        if (it->second.view.fmt == stf::FMT_DCT)
+            return fail(c, STF_ERR_UNSUPPORTED, "texture tables take RGBA32F and RGBA8 textures");
         host[i] = stf::make_fetch_ctx(it->second.view);
     }
     CurrentDevice cd(c->device);

@@ -9,12 +9,13 @@
 #include <cstdint>
 #include <cuda_fp16.h>
 
+#include "stf_kernels.h"
+
 namespace stf {
 
 enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3, F_EWA = 4 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { SH_GGX = 0, SH_LINEAR = 1 };
-enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1 };
 enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u, FLAG_LOD0 = 8u };
 enum { DEV_NAN_INPUT = 1u, DEV_BAD_INDEX = 2u, DEV_TIMEOUT = 4u };
 constexpr uint32_t NO_PICK = 0xFFFFFFFFu;
@@ -351,12 +352,80 @@ __device__ __forceinline__ Material decode_rgba8(uint2 t, bool has_normal) {
     m.n = has_normal ? decode_normal_rg8(t.y) : make_float3(0.f, 0.f, 1.f);
     return m;
 }
+// Decoded channels (albedo RGB, roughness, normal X and Y, each in [0,1] up to decoding
+// error) -> material: clamped albedo, roughness 0.05 + 0.95 r, normal (2x-1, 2y-1, z)
+// normalised.  Used by the learned and the DCT-compressed textures.
+__device__ __forceinline__ Material material_from_channels(const float y[8]) {
+    Material m;
+    m.rho = make_float3(__saturatef(y[0]), __saturatef(y[1]), __saturatef(y[2]));
+    m.rough = fmaf(0.95f, __saturatef(y[3]), 0.05f);
+    const float x = fmaf(2.0f, __saturatef(y[4]), -1.0f), yy = fmaf(2.0f, __saturatef(y[5]), -1.0f);
+    const float z2 = 1.0f - x * x - yy * yy;
+    // z2 > 0: (x, y, sqrt z2) is a unit vector already; otherwise z = 0 and (x, y), which is
+    // then at least unit length, is normalised
+    if (z2 > 0.0f) {
+        m.n = make_float3(x, yy, z2 * rsqrt_approx(z2));
+    } else {
+        const float inv = rsqrt_approx(x * x + yy * yy);
+        m.n = make_float3(x * inv, yy * inv, 0.0f);
+    }
+    return m;
+}
+
 __device__ __forceinline__ Material decode_rgba32f(float4 t) {
     Material m;
     m.rho = make_float3(t.x, t.y, t.z);
     m.rough = t.w;
     m.n = make_float3(0.f, 0.f, 1.f);
     return m;
+}
+
+// ---------------------------------------------------------------- DCT-compressed texels
+// 8 x 8 blocks of six channel words (supplement "Texture compression"): per channel the
+// six lowest frequencies (u + v <= 2) of the orthonormal 2-D DCT-II, DC in bits 0-6
+// (q * 8/127), AC terms (1,0), (0,1), (2,0), (1,1), (0,2) in 5-bit fields ((q - 15) * 2/15);
+// blocks are 32 bytes (24 used), row-major per level.
+struct DctRaw {
+    uint4 a;     // channel words 0-3 (albedo RGB, roughness)
+    uint2 b;     // channel words 4-5 (normal X, Y)
+    int lx, ly;  // texel position inside the block
+};
+__device__ __forceinline__ DctRaw load_dct(const unsigned char* level, int w, int ix, int iy) {
+    const uint32_t w8 = ((uint32_t)w + 7u) >> 3;
+    const uint32_t blk = ((uint32_t)iy >> 3) * w8 + ((uint32_t)ix >> 3);
+    const uint4* p = reinterpret_cast<const uint4*>(level) + (size_t)blk * 2;
+    DctRaw r;
+    r.a = __ldg(p);
+    r.b = __ldg(reinterpret_cast<const uint2*>(p + 1));
+    r.lx = ix & 7;
+    r.ly = iy & 7;
+    return r;
+}
+// one channel: q0/127 + (2/15) [a1 a0 (q1 cx1 + q2 cy1 + q3 cx2 + q5 cy2) + a1 a1 q4 cx1 cy1],
+// a0 = 1/(2 sqrt 2), a1 = 1/2 (the orthonormal scale factors)
+__device__ __forceinline__ float dct_channel(uint32_t w, float cx1, float cx2, float cy1, float cy2) {
+    const float q1 = (float)((int)((w >> 7) & 31u) - 15), q2 = (float)((int)((w >> 12) & 31u) - 15);
+    const float q3 = (float)((int)((w >> 17) & 31u) - 15), q4 = (float)((int)((w >> 22) & 31u) - 15);
+    const float q5 = (float)((int)((w >> 27) & 31u) - 15);
+    const float s10 = 0.17677669529663688f * (2.0f / 15.0f), s11 = 0.25f * (2.0f / 15.0f);
+    float f = fmaf(q1, cx1, q2 * cy1);
+    f = fmaf(q3, cx2, f);
+    f = fmaf(q5, cy2, f);
+    return fmaf(f, s10, fmaf(q4 * s11, cx1 * cy1, (float)(w & 127u) * (1.0f / 127.0f)));
+}
+__device__ __forceinline__ Material decode_dct(const DctRaw& r) {
+    // cos((2x+1) pi / 16) per axis, and cos(2 theta) = 2 cos^2 theta - 1
+    const float cx1 = cospif((float)(2 * r.lx + 1) * 0.0625f), cy1 = cospif((float)(2 * r.ly + 1) * 0.0625f);
+    const float cx2 = fmaf(2.0f * cx1, cx1, -1.0f), cy2 = fmaf(2.0f * cy1, cy1, -1.0f);
+    float y[8];
+    y[0] = dct_channel(r.a.x, cx1, cx2, cy1, cy2);
+    y[1] = dct_channel(r.a.y, cx1, cx2, cy1, cy2);
+    y[2] = dct_channel(r.a.z, cx1, cx2, cy1, cy2);
+    y[3] = dct_channel(r.a.w, cx1, cx2, cy1, cy2);
+    y[4] = dct_channel(r.b.x, cx1, cx2, cy1, cy2);
+    y[5] = dct_channel(r.b.y, cx1, cx2, cy1, cy2);
+    y[6] = y[7] = 0.0f;
+    return material_from_channels(y);
 }
 
 }  // namespace stf

@@ -7,9 +7,13 @@
 
 namespace stf {
 
+// 2-D texture storage formats
+enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_DCT = 2 };
+
 struct TexView {
     const void* base;     // one device allocation holding every level
-    int fmt;              // 0 RGBA32F (float4 texels), 1 RGBA8 material (uint2 texels)
+    int fmt;              // FMT_RGBA32F (float4 texels), FMT_RGBA8 (uint2 material texels) or
+                          // FMT_DCT (32-byte blocks of 8 x 8 texels)
     int levels;
     int has_normal;
     int address;          // 0 wrap (2-D textures are always wrap here)

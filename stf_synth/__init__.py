@@ -175,6 +175,41 @@ def material_rgba8(size: int = 4096, seed: int = 102, octaves: int = 8,
 # ---------------------------------------------------------------------------------
 # queries
 # ---------------------------------------------------------------------------------
+# DCT-compressed texture set (supplement "Texture compression"): per 8 x 8 block and channel
+# the six lowest frequencies (u + v <= 2) of the orthonormal 2-D DCT-II, packed into one 32-bit
+# word: bits 0-6 the DC term, quantised over [0, 8] to 7 bits; then five 5-bit fields, one
+# per AC term in the order (u, v) = (1,0), (0,1), (2,0), (1,1), (0,2), each stored as q + 15
+# with q = round(X / (2/15)) clamped to [-15, 15].  Six channels (albedo RGB, roughness,
+# normal X and Y, each byte/255) make 24 bytes, padded to a 32-byte block; levels narrower
+# than 8 texels repeat periodically inside their block.
+DCT_AC = ((1, 0), (0, 1), (2, 0), (1, 1), (0, 2))
+DCT_DC_MAX, DCT_AC_STEP = 8.0, 2.0 / 15.0
+
+
+def dct_compress(material: Material) -> list:
+    """Per MIP level a (ceil(H/8), ceil(W/8), 32) uint8 array of DCT blocks (see above)."""
+    from scipy.fft import dctn
+    out = []
+    for ar, nm in zip(material.albedo_rough, material.normal):
+        H, W = ar.shape[:2]
+        ch = np.concatenate([ar.astype(np.float64), nm.astype(np.float64)], axis=2) / 255.0   # (H, W, 6)
+        H8, W8 = -(-H // 8), -(-W // 8)
+        yy = np.arange(H8 * 8) % H
+        xx = np.arange(W8 * 8) % W
+        full = ch[yy][:, xx]                                          # periodic extension
+        blocks = full.reshape(H8, 8, W8, 8, 6).transpose(0, 2, 4, 1, 3)   # (H8, W8, 6, y, x)
+        X = dctn(blocks, type=2, norm="ortho", axes=(3, 4))             # X[..., v, u]
+        dc = np.clip(np.rint(X[..., 0, 0] / DCT_DC_MAX * 127.0), 0, 127).astype(np.uint32)
+        word = dc.copy()
+        for j, (u, v) in enumerate(DCT_AC):
+            q = np.clip(np.rint(X[..., v, u] / DCT_AC_STEP), -15, 15).astype(np.int64) + 15
+            word |= q.astype(np.uint32) << np.uint32(7 + 5 * j)
+        blk = np.zeros((H8, W8, 8), dtype=np.uint32)
+        blk[..., :6] = word
+        out.append(blk.view(np.uint8).reshape(H8, W8, 32))
+    return out
+
+
 @dataclass
 class Queries:
     u: np.ndarray

@@ -695,3 +695,61 @@ def test_lod0_flag_uses_the_finest_level_only():
         assert np.all((r.picks[..., 0] >> 28) == 0)
         base = oracle.filter_shade(tex, q, f, "stochastic", spp=2, want_picks=True)
         assert np.any((base.picks[..., 0] >> 28) > 0)
+
+
+# ------------------------------------------------------------------------ DCT texture compression
+def _dct_coeffs(word):
+    # dequantised 8 x 8 coefficient array X[v, u] of one channel word (zeros elsewhere)
+    X = np.zeros((8, 8))
+    X[0, 0] = (word & 127) * 8.0 / 127.0
+    for j, (u, v) in enumerate(synth.DCT_AC):
+        X[v, u] = (((word >> (7 + 5 * j)) & 31) - 15) * 2.0 / 15.0
+    return X
+
+
+def test_dct_decode_matches_scipy_inverse_dct():
+    # the oracle's restricted basis sum equals scipy's orthonormal 2-D inverse DCT of the
+    # dequantised coefficients, at every texel of the block
+    from scipy.fft import idctn
+    rng = np.random.default_rng(3)
+    for word in rng.integers(0, 1 << 32, 12, dtype=np.uint64):
+        word = int(word) & 0xFFFFFFFF
+        ref = idctn(_dct_coeffs(word), type=2, norm="ortho")    # ref[y, x]
+        got = np.array([[oracle.dct_texel(word, x, y) for x in range(8)] for y in range(8)])
+        np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+def test_dct_roundtrip_and_constant_blocks():
+    # smooth content survives within the quantisation error; a constant on the DC grid is exact
+    n = 64
+    yy, xx = np.mgrid[0:n, 0:n] / n
+    smooth = 0.5 + 0.25 * np.sin(2 * np.pi * xx) * np.cos(2 * np.pi * yy)
+    b = synth._rne_u8(255 * smooth)
+    m = synth.Material([np.repeat(b[..., None], 4, axis=2)], [np.repeat(b[..., None], 2, axis=2)], smooth)
+    blk = synth.dct_compress(m)[0].view(np.uint32).reshape(n // 8, n // 8, 8)
+    dec = np.array([[oracle.dct_texel(int(blk[y // 8, x // 8, 0]), x % 8, y % 8) for x in range(n)] for y in range(n)])
+    # quantisation bound: half a DC step times 1/8 plus five half AC steps times the largest
+    # basis value 1/4 (~0.087), and the truncated higher frequencies of the sine are small
+    err = dec - b / 255.0
+    assert np.abs(err).max() < 0.087 and np.sqrt(np.mean(err ** 2)) < 0.02, (np.abs(err).max(), np.sqrt(np.mean(err ** 2)))
+    c = 64 / 127                        # DC = 8 c lands on the 7-bit grid
+    m2 = synth.Material([np.full((16, 16, 4), 0, np.uint8)], [np.full((16, 16, 2), 0, np.uint8)], None)
+    word = (64 | (15 << 7) | (15 << 12) | (15 << 17) | (15 << 22) | (15 << 27))
+    assert all(abs(oracle.dct_texel(word, x, y) - c) < 1e-15 for x in range(8) for y in range(8))
+    blk2 = synth.dct_compress(m2)[0].view(np.uint32)
+    assert np.all(blk2[..., :6] == (15 << 7) | (15 << 12) | (15 << 17) | (15 << 22) | (15 << 27))
+
+
+def test_dct_texture_filters_reproduce_a_constant():
+    # every stored word decodes to the same constant: all estimators return its shade
+    word = (64 | (15 << 7) | (15 << 12) | (15 << 17) | (15 << 22) | (15 << 27))
+    blocks = [np.tile(np.array([word] * 6 + [0, 0], np.uint32), (2, 2, 1)).view(np.uint8)]
+    tex = oracle.Texture([(16, 16)], dct=blocks)
+    c = 64 / 127
+    nx = 2 * c - 1
+    nz = math.sqrt(max(0.0, 1 - 2 * nx * nx))
+    want = oracle.shade_batch(np.array([[c, c, c]]), [0.05 + 0.95 * c], [[nx, nx, nz]])[0]
+    q = synth.queries_uniform(200, 4, const_derivs=(1 / 64, 0.0, 0.0, 1 / 64))
+    for f, mode in (("linear", "stochastic"), ("bspline", "ntap_before"), ("linear", "ntap_after")):
+        r = oracle.filter_shade(tex, q, f, mode, spp=2)
+        np.testing.assert_allclose(r.rgb, np.broadcast_to(want, r.rgb.shape), rtol=1e-12)
