@@ -253,6 +253,7 @@ def run_ours(args):
         line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
         line["aniso"] = aniso_block(ctx, tex, dev)
         line["dct"] = dct_block(ctx, material, u, v, d, dev)
+        line["fis"] = fis_block(ctx, tex, dev)
         line["volume"] = volume_block(ctx, dev, args)
         line["table"] = table_block(ctx, dev)
         line["neural"] = neural_block(ctx, dev, material)
@@ -474,6 +475,57 @@ def dct_block(ctx, material, u, v, d, dev, nsub=1 << 16):
                      "stochastic_lookups_per_s": nfull * 8 / (t[("stochastic", 8)] / 1e3),
                      "s_star": s_star, "equal_rmse_speedup": (t[("ntap_before", 8)] / t_star) if t_star else None}
     ctx.destroy_texture(th)
+    return res
+
+
+def fis_block(ctx, tex, dev, nq=1 << 22, nsub=1 << 16):
+    """Filter importance sampling against filter reservoir sampling (Sec. 4.2 FIS; the
+    supplement's Gaussian listings) under 4x magnification on the 4096^2 material (level 0, a
+    quarter-texel pixel footprint), 2^22 queries.  Gaussians with sigma 0.3 / 0.5 / 0.8 texels:
+    FRS over the 4 x 4 window against FIS (Box-Muller, then the nearest texel); and the cubic
+    B-spline by FRS against FIS (the sum of three uniforms, then the nearest texel).
+    References (16 x 16 stratified screen-space samples of the exact N-tap filter-after value,
+    2^16-query subset): the discrete Gaussian at texel centres, which FRS samples apart from its
+    4 x 4 truncation, and the Gaussian convolved with the texel box, which FIS samples."""
+    import torch
+    q = synth.queries_uniform(nq, 45, const_derivs=(0.25 / TEX_RES, 0.0, 0.0, 0.25 / TEX_RES))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    u, v, d = t(q.u), t(q.v), [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]
+    sub = lambda x: x[:nsub]
+    us, vs, ds = sub(u), sub(v), [sub(x) for x in d]
+    mk = lambda n: [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    out_s, out_f = mk(nsub), mk(nq)
+    grid = (1, 2, 4, 8, 16, 32)
+
+    def ref(filt, sampler, sigma):
+        o = mk(nsub)
+        ctx.filter_shade(tex, us, vs, ds, filt, "ntap_after", "ggx", 256, 1, STRATIFIED, out=o, sampler=sampler,
+                         sigma=sigma)
+        return torch.stack(o, 1).double()
+
+    def curve(filt, sampler, sigma, R):
+        c = {}
+        for sp in grid:
+            ctx.filter_shade(tex, us, vs, ds, filt, "stochastic", "ggx", sp, 7, 0, out=out_s, sampler=sampler,
+                             sigma=sigma)
+            c[str(sp)] = float(((torch.stack(out_s, 1).double() - R) ** 2).mean().sqrt())
+        return c
+
+    def timed(filt, sampler, sigma):
+        return _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "stochastic", "ggx", 8, 1, 0, out=out_f,
+                                                     sampler=sampler, sigma=sigma))
+    res = {"queries": nq, "rmse_subset": nsub, "magnification": 4}
+    for sigma in (0.3, 0.5, 0.8):
+        r_disc, r_box = ref("gauss", "frs", sigma), ref("gauss", "fis", sigma)
+        res[f"gauss_sigma_{sigma}"] = {
+            "frs": {"rmse_vs_discrete": curve("gauss", "frs", sigma, r_disc),
+                    "rmse_vs_box": curve("gauss", "frs", sigma, r_box), "ms_8spp": timed("gauss", "frs", sigma)},
+            "fis": {"rmse_vs_discrete": curve("gauss", "fis", sigma, r_disc),
+                    "rmse_vs_box": curve("gauss", "fis", sigma, r_box), "ms_8spp": timed("gauss", "fis", sigma)},
+            "rmse_discrete_vs_box_reference": float(((r_disc - r_box) ** 2).mean().sqrt())}
+    r_bs = ref("bspline", "frs", 0.0)
+    res["bspline"] = {"frs": {"rmse": curve("bspline", "frs", 0.0, r_bs), "ms_8spp": timed("bspline", "frs", 0.0)},
+                      "fis": {"rmse": curve("bspline", "fis", 0.0, r_bs), "ms_8spp": timed("bspline", "fis", 0.0)}}
     return res
 
 

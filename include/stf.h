@@ -80,16 +80,40 @@ typedef enum {
     STF_FILTER_BSPLINE = 1,      /* cubic B-spline K_bs, 4 taps per axis                  */
     STF_FILTER_CATMULL_ROM = 2,  /* Keys cubic K3 with a = -1/2, 4 taps, negative lobes   */
     STF_FILTER_MITCHELL = 3,     /* Mitchell-Netravali BC(1/3,1/3), 4 taps, neg. lobes    */
-    STF_FILTER_EWA = 4           /* elliptically weighted average over a Gaussian (supplement
+    STF_FILTER_EWA = 4,          /* elliptically weighted average over a Gaussian (supplement
                                     "Stochastic EWA", as pbrt evaluates it): the ellipse of the
                                     derivative footprint plus a one-texel reconstruction term,
                                     eccentricity capped at 64, weights exp(-2r^2)-exp(-2) from a
-                                    128-entry table.  stf_filter_shade only; modes NTAP_BEFORE,
+                                    128-entry table.  Modes NTAP_BEFORE,
                                     NTAP_AFTER (each level normalised by its weight sum) and
                                     STOCHASTIC (one texel by weighted reservoir sampling over the
                                     ellipse's box, raster order, uniform remapped per decision);
                                     no screen-space jitter; flags: LOD0 only */
+    STF_FILTER_GAUSSIAN = 5      /* Gaussian exp(-d^2/(2 sigma^2)) at texel centres, normalised
+                                    (Sec. 4.2 FIS, supplement Gaussian listings); needs
+                                    stf_filter_shade_ex for sigma and the sampler */
 } stf_filter;
+
+/* How a stochastic lookup draws its texel (stf_filter_shade_ex):
+ *   FRS: filter reservoir sampling, i.e. CDF picks over the discrete weights.  For the Gaussian
+ *        the window is the 4 x 4 texels at offsets -1..2 from floor(p), as in the listing.
+ *   FIS: filter importance sampling.  A continuous offset o (texels) is drawn from a density
+ *        whose convolution with the unit box is the filter, then the nearest texel
+ *        floor(x W + o) is taken:
+ *          LINEAR   o = u - 1/2, which gives the tent;
+ *          BSPLINE  o = u1 + u2 + u3 - 3/2, the quadratic B-spline, which gives the cubic one;
+ *          GAUSSIAN o = sigma * Box-Muller(1 - u_a, u_b), which gives the Gaussian convolved
+ *                   with the box.
+ *        The N-tap modes with FIS evaluate the filter that FIS converges to: the tent, the
+ *        cubic B-spline, or the box-convolved Gaussian.
+ * Gaussian N-tap windows cover |i - p| <= ceil(5 sigma) + 1 per axis. */
+typedef enum { STF_SAMPLER_FRS = 0, STF_SAMPLER_FIS = 1 } stf_sampler;
+
+typedef struct {
+    stf_filter filter;
+    stf_sampler sampler;
+    float sigma;         /* Gaussian standard deviation in texels, (0, 8]; ignored otherwise */
+} stf_filter_desc;
 
 typedef enum {
     STF_MODE_NTAP_BEFORE = 0,           /* shade(sum_i w_i t_i)             Eq. filter-before-shading */
@@ -182,6 +206,14 @@ stf_status stf_destroy_texture(stf_ctx ctx, stf_tex tex);
 stf_status stf_filter_shade(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
                             stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                             uint64_t seed, uint32_t flags, const stf_output* out);
+
+/* stf_filter_shade with a filter descriptor (filter, sampler, sigma).  FRS with filters 0-4
+ * is stf_filter_shade.  GAUSSIAN and FIS: no positivization (STF_ERR_UNSUPPORTED); flags
+ * STRATIFIED and LOD0 only; FIS for LINEAR, BSPLINE and GAUSSIAN (else STF_ERR_UNSUPPORTED);
+ * sigma outside (0, 8] for GAUSSIAN is STF_ERR_INVALID_ARG. */
+stf_status stf_filter_shade_ex(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
+                               const stf_filter_desc* filter, stf_mode mode, stf_shade shade, uint32_t spp,
+                               uint64_t seed, uint32_t flags, const stf_output* out);
 
 /* Same computation from HOST buffers (u, v, derivs, r, g, b, picks all host memory):
  * copies the inputs to library-owned device staging memory, runs, copies the results back

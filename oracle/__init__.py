@@ -28,7 +28,7 @@ SRCS = [os.path.join(HERE, f) for f in ("stf_oracle.cpp", "ntc_oracle.cpp")]
 DEPS = SRCS + [os.path.join(HERE, "oracle_internal.h")]
 LIB = os.path.join(HERE, "liboracle.so")
 
-FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4}
+FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4, "gauss": 5}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FLAG_STRATIFIED = 1
@@ -93,7 +93,7 @@ def lib():
         L.orc_shade_batch.argtypes = [C.c_uint64, C.c_int, P, P, P, P]
         L.orc_fetch.argtypes = [C.POINTER(_Tex), C.c_int, C.c_int, C.c_int, P]
         L.orc_filter_shade.argtypes = [C.POINTER(_Tex), C.c_uint64] + [P] * 7 + [
-            C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, P, C.c_int]
+            C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, P, C.c_int, C.c_float]
         L.orc_march.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_float, P, C.c_uint32, C.c_uint32,
                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                 C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
@@ -275,10 +275,25 @@ class FilterResult:
     rdist: np.ndarray | None = None  # (n,) learned texels: smallest BF16 rounding margin (see ntc_decode)
 
 
+def _internal_filter(filter: str, sampler: str, mode: str) -> int:
+    """The oracle's filter id: FIS picks are their own filters (STOCHASTIC only); the N-tap form
+    of a FIS filter is the filter it converges to (the same tent / B-spline, and for the
+    Gaussian its convolution with the unit box)."""
+    if sampler == "frs":
+        return FILTERS[filter]
+    if sampler != "fis" or filter not in ("linear", "bspline", "gauss"):
+        raise ValueError("FIS samples the tent, the cubic B-spline and the Gaussian")
+    if mode == "stochastic":
+        return {"linear": 7, "bspline": 8, "gauss": 9}[filter]
+    return {"linear": 0, "bspline": 1, "gauss": 6}[filter]
+
+
 def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", spp: int = 1,
                  seed: int = 1, flags: int = 0, want_picks: bool = False,
-                 nthreads: int | None = None, ids=None) -> FilterResult:
-    """Evaluate queries q; the Philox id of query i is ids[i] (default: i)."""
+                 nthreads: int | None = None, ids=None, sampler: str = "frs", sigma: float = 0.5) -> FilterResult:
+    """Evaluate queries q; the Philox id of query i is ids[i] (default: i).  sampler: "frs"
+    (filter reservoir sampling) or "fis" (filter importance sampling); sigma: the Gaussian's
+    standard deviation in texels."""
     n = q.n
     rgb = np.zeros((n, 3))
     picks = np.zeros((n, spp, 2), dtype=np.uint32) if want_picks else None
@@ -290,9 +305,9 @@ def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", sp
     arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None
             for a in (q.u, q.v, q.dudx, q.dvdx, q.dudy, q.dvdy)]
     ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint64)
-    rc = lib().orc_filter_shade(C.byref(t), n, *[_p(a) for a in arrs], _p(ids), FILTERS[filter], MODES[mode],
-                                SHADES[shade], spp, seed, flags, _p(rgb), _p(picks), _p(picks64),
-                                _p(bd), _p(mag), _p(rdist), nthreads or nthreads_default())
+    rc = lib().orc_filter_shade(C.byref(t), n, *[_p(a) for a in arrs], _p(ids), _internal_filter(filter, sampler, mode),
+                                MODES[mode], SHADES[shade], spp, seed, flags, _p(rgb), _p(picks), _p(picks64),
+                                _p(bd), _p(mag), _p(rdist), nthreads or nthreads_default(), float(sigma))
     if rc != 0:
         raise ValueError("oracle: invalid filter_shade arguments")
     return FilterResult(rgb, picks, picks64, bd, mag, rdist)

@@ -41,7 +41,8 @@
 namespace {
 
 // ------------------------------------------------------------------ enums (API values)
-enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3, F_EWA = 4 };
+enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3, F_EWA = 4,
+       F_GAUSS = 5, F_GAUSS_BOX = 6, F_FIS_LINEAR = 7, F_FIS_BSPLINE = 8, F_FIS_GAUSS = 9 };
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { S_GGX_LAMBERT = 0, S_LINEAR = 1 };
 enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u, FLAG_LOD0 = 8u };
@@ -601,11 +602,192 @@ void run_query_ewa(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int 
     if (O.bdist) O.bdist[q] = bd;
 }
 
+// ------------------------------------------------------------------ Gaussian filters and FIS
+// Sec. 4.2 "Filter Importance Sampling" and the supplement's Gaussian listings.
+//   F_GAUSS      the Gaussian exp(-d^2 / (2 sigma^2)) at texel centres, normalised.
+//                STOCHASTIC: filter reservoir sampling over the listing's 4 x 4 window (offsets
+//                -1..2 from floor(p)), taken as separable CDF picks (the weights factor per
+//                axis; the same distribution as the listing's 16-tap reservoir); the estimate is
+//                the picked texel's shade.  N-tap: the window |i - p| <= ceil(5 sigma) + 1.
+//   F_GAUSS_BOX  the Gaussian convolved with the unit box, per axis
+//                Phi((i + 1/2 - p) / sigma) - Phi((i - 1/2 - p) / sigma): the filter that FIS with
+//                a nearest lookup realises.  N-tap only.
+//   F_FIS_*      FIS (STOCHASTIC only): a continuous offset o in texels, then the nearest texel
+//                floor(x W + o).  LINEAR: o = u - 1/2 (box, hence the tent); BSPLINE: o = u1 + u2
+//                + u3 - 3/2 (the quadratic B-spline, hence the cubic one, by the Cox-de Boor
+//                recursion); GAUSS: o = sigma * Box-Muller(1 - u_a, u_b) (1 - u keeps the log
+//                finite when u = 0).
+// Decisions are FP32 in a fixed order (the Box-Muller transcendentals as double, rounded to
+// float); bdist reports the distance of each decision to its FP64 boundary (for FIS, of the
+// sample position to a texel edge, in texels).
+double phi64(double z) { return 0.5 * std::erfc(-z / std::sqrt(2.0)); }
+
+void gauss_weights32(float t, float inv_s2, float w[4]) {
+    for (int k = 0; k < 4; ++k) {
+        const float d = t - (float)(k - 1);
+        w[k] = std::exp((-0.5f * (d * d)) * inv_s2);
+    }
+}
+
+void run_query_gauss(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filter, int mode, int smode,
+                     uint32_t spp, uint64_t seed, uint32_t flags, float sigma, float lam32, double lam64, Out& O) {
+    const int l0 = (int)std::floor(lam32);
+    const float fr = lam32 - (float)l0;
+    const double fr64 = lam64 - std::floor(lam64);
+    const float inv_s2 = 1.0f / (sigma * sigma);
+    const double sg = (double)sigma;
+    double bd = 1e30;
+    if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::fabs(lam64 - std::nearbyint(lam64));
+    int kside = 1;
+    if (flags & FLAG_STRATIFIED) kside = (int)std::lround(std::sqrt((double)spp));
+    double acc[3] = {0, 0, 0}, mag[3] = {0, 0, 0};
+    double rd = 1.0;
+    for (uint32_t s = 0; s < spp; ++s) {
+        uint32_t r0[4], r1[4];
+        draw(seed, id, s, 0, r0);
+        draw(seed, id, s, 1, r1);
+        float a[5], b[5];
+        uniforms5(r0, a);
+        uniforms5(r1, b);
+        float x = Q.u[q], y = Q.v[q];
+        if (Q.dudx) {
+            float jx, jy;
+            if (flags & FLAG_STRATIFIED) {
+                jx = ((float)(s % kside) + 0.5f) / (float)kside - 0.5f;
+                jy = ((float)(s / kside) + 0.5f) / (float)kside - 0.5f;
+            } else {
+                jx = a[0] - 0.5f;
+                jy = a[1] - 0.5f;
+            }
+            x = std::fmaf(jy, Q.dudy[q], std::fmaf(jx, Q.dudx[q], x));
+            y = std::fmaf(jy, Q.dvdy[q], std::fmaf(jx, Q.dvdx[q], y));
+        }
+        uint32_t* pk = O.picks ? O.picks + (q * spp + s) * 2 : nullptr;
+        uint32_t* pk64 = O.picks64 ? O.picks64 + (q * spp + s) * 2 : nullptr;
+        if (pk) pk[0] = pk[1] = NO_PICK;
+        if (pk64) pk64[0] = pk64[1] = NO_PICK;
+        double est[3] = {0, 0, 0};
+        if (mode == M_STOCHASTIC) {
+            const int lvl = std::min(l0 + ((a[2] < fr) ? 1 : 0), T.levels - 1);
+            if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs((double)a[2] - fr64));
+            const int W = T.width[lvl], H = T.height[lvl];
+            int ix, iy;
+            if (filter == F_GAUSS) {
+                const Axis ax = axis_at(x, W), ay = axis_at(y, H);
+                float wx[4], wy[4];
+                gauss_weights32(ax.t, inv_s2, wx);
+                gauss_weights32(ay.t, inv_s2, wy);
+                double wx64[4], wy64[4];
+                for (int k = 0; k < 4; ++k) {
+                    const double dx = ax.pos - (double)(ax.i0 - 1 + k), dy = ay.pos - (double)(ay.i0 - 1 + k);
+                    wx64[k] = std::exp(-0.5 * dx * dx / (sg * sg));
+                    wy64[k] = std::exp(-0.5 * dy * dy / (sg * sg));
+                }
+                const int kx = pick32(wx, 4, a[3], 0, nullptr), ky = pick32(wy, 4, a[4], 0, nullptr);
+                pick64(wx64, 4, a[3], 0, &bd);
+                pick64(wy64, 4, a[4], 0, &bd);
+                ix = ax.i0 - 1 + kx;
+                iy = ay.i0 - 1 + ky;
+            } else {
+                float ox, oy;
+                double ox64, oy64;
+                if (filter == F_FIS_LINEAR) {
+                    ox = a[3] - 0.5f; oy = a[4] - 0.5f;
+                    ox64 = (double)a[3] - 0.5; oy64 = (double)a[4] - 0.5;
+                } else if (filter == F_FIS_BSPLINE) {
+                    ox = ((a[3] + b[0]) + b[1]) - 1.5f;
+                    oy = ((a[4] + b[2]) + b[3]) - 1.5f;
+                    ox64 = ((double)a[3] + b[0] + b[1]) - 1.5;
+                    oy64 = ((double)a[4] + b[2] + b[3]) - 1.5;
+                } else {
+                    const double pi = 3.14159265358979323846;
+                    const float lg = (float)std::log((double)(1.0f - a[3]));
+                    const float r = std::sqrt(-2.0f * lg);
+                    const float c = (float)std::cos(2.0 * pi * (double)a[4]), sn = (float)std::sin(2.0 * pi * (double)a[4]);
+                    ox = sigma * (r * c);
+                    oy = sigma * (r * sn);
+                    const double r64 = std::sqrt(-2.0 * std::log(1.0 - (double)a[3]));
+                    ox64 = sg * r64 * std::cos(2.0 * pi * (double)a[4]);
+                    oy64 = sg * r64 * std::sin(2.0 * pi * (double)a[4]);
+                }
+                const float sx = std::fmaf(x, (float)W, ox), sy = std::fmaf(y, (float)H, oy);
+                ix = (int)std::floor(sx);
+                iy = (int)std::floor(sy);
+                const double sx64 = (double)x * W + ox64, sy64 = (double)y * H + oy64;
+                bd = std::min(bd, std::min(std::fabs(sx64 - std::nearbyint(sx64)), std::fabs(sy64 - std::nearbyint(sy64))));
+            }
+            const int wx_ = wrapi(ix, W, T.address), wy_ = wrapi(iy, H, T.address);
+            double o[3];
+            shade(smode, fetch(T, lvl, wx_, wy_, &rd), o);
+            for (int c = 0; c < 3; ++c) { est[c] = o[c]; mag[c] += std::fabs(o[c]); }
+            if (pk) pk[0] = pack2d(lvl, wx_, wy_);
+            if (pk64) pk64[0] = pack2d(lvl, wx_, wy_);
+        } else {
+            // N-tap: the window around p on both levels, each axis normalised
+            const double wl[2] = {1.0 - (double)fr, (double)fr};
+            const int R = (int)std::ceil(5.0 * sg) + 1;
+            Mat fm{}; fm.n = {0, 0, 0};
+            double fsum[3] = {0, 0, 0};
+            for (int li = 0; li < 2; ++li) {
+                const int lvl = l0 + li;
+                if (wl[li] == 0.0 || lvl >= T.levels) continue;
+                const int W = T.width[lvl], H = T.height[lvl];
+                const Axis ax = axis_at(x, W), ay = axis_at(y, H);
+                std::vector<double> wx(2 * R + 2), wy(2 * R + 2);
+                double sx = 0, sy = 0;
+                for (int k = 0; k < 2 * R + 2; ++k) {
+                    const double dx = (double)(ax.i0 - R + k) - ax.pos, dy = (double)(ay.i0 - R + k) - ay.pos;
+                    if (filter == F_GAUSS) {
+                        wx[k] = std::exp(-0.5 * dx * dx / (sg * sg));
+                        wy[k] = std::exp(-0.5 * dy * dy / (sg * sg));
+                    } else {
+                        wx[k] = phi64((dx + 0.5) / sg) - phi64((dx - 0.5) / sg);
+                        wy[k] = phi64((dy + 0.5) / sg) - phi64((dy - 0.5) / sg);
+                    }
+                    sx += wx[k]; sy += wy[k];
+                }
+                for (int j = 0; j < 2 * R + 2; ++j)
+                    for (int i = 0; i < 2 * R + 2; ++i) {
+                        const double w = wl[li] * (wx[i] / sx) * (wy[j] / sy);
+                        if (w == 0.0) continue;
+                        const Mat m = fetch(T, lvl, wrapi(ax.i0 - R + i, W, T.address), wrapi(ay.i0 - R + j, H, T.address), &rd);
+                        if (mode == M_NTAP_BEFORE) {
+                            for (int c = 0; c < 3; ++c) fm.rho[c] += w * m.rho[c];
+                            fm.rough += w * m.rough;
+                            fm.n.x += w * m.n.x; fm.n.y += w * m.n.y; fm.n.z += w * m.n.z;
+                        } else {
+                            double o[3];
+                            shade(smode, m, o);
+                            for (int c = 0; c < 3; ++c) { fsum[c] += w * o[c]; mag[c] += std::fabs(w * o[c]); }
+                        }
+                    }
+            }
+            if (mode == M_NTAP_BEFORE) {
+                const double ln = std::sqrt(dot(fm.n, fm.n));
+                fm.n = ln > 0 ? V3{fm.n.x / ln, fm.n.y / ln, fm.n.z / ln} : V3{0, 0, 1};
+                shade(smode, fm, est);
+                for (int c = 0; c < 3; ++c) mag[c] += std::fabs(est[c]);
+            } else {
+                for (int c = 0; c < 3; ++c) est[c] = fsum[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) acc[c] += est[c];
+    }
+    for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c] / (double)spp;
+    if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c] / (double)spp;
+    if (O.rdist) O.rdist[q] = rd;
+    if (O.bdist) O.bdist[q] = bd;
+}
+
 void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filter, int mode, int smode,
-               uint32_t spp, uint64_t seed, uint32_t flags, Out& O) {
+               uint32_t spp, uint64_t seed, uint32_t flags, float sigma, Out& O) {
     float lam32; double lam64;
     lod(T, Q, q, &lam32, &lam64);
     if (flags & FLAG_LOD0) { lam32 = 0.0f; lam64 = 0.0; }   // finest level only (no MIP prefiltering)
+    if (filter >= F_GAUSS) {
+        run_query_gauss(T, Q, q, id, filter, mode, smode, spp, seed, flags, sigma, lam32, lam64, O);
+        return;
+    }
     if (filter == F_EWA) {
         double bd0 = 1e30;
         if (lam64 > 0.0 && lam64 < T.levels - 1) bd0 = std::fabs(lam64 - std::nearbyint(lam64));
@@ -1050,8 +1232,14 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
                      const float* dudx, const float* dvdx, const float* dudy, const float* dvdy,
                      const uint64_t* ids, int filter, int mode, int smode, uint32_t spp, uint64_t seed,
                      uint32_t flags, double* rgb, uint32_t* picks, uint32_t* picks64, double* bdist,
-                     double* mag, double* rdist, int nthreads) {
-    if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 4 || mode < 0 || mode > 3) return 1;
+                     double* mag, double* rdist, int nthreads, float sigma) {
+    if (!tex || !u || !v || !rgb || spp == 0 || filter < 0 || filter > 9 || mode < 0 || mode > 3) return 1;
+    if (filter >= F_GAUSS) {
+        if (!(sigma > 0.0f) || sigma > 8.0f || mode == M_POSITIVIZED) return 1;
+        if (flags & ~(uint32_t)(FLAG_STRATIFIED | FLAG_LOD0)) return 1;
+        if (filter == F_GAUSS_BOX && mode == M_STOCHASTIC) return 1;
+        if (filter >= F_FIS_LINEAR && mode != M_STOCHASTIC) return 1;
+    }
     if (tex->levels < 1 || tex->levels > 16) return 1;
     if ((mode == M_POSITIVIZED) && !signed_filter(filter)) return 1;
     if (filter == F_EWA && (flags & ~(uint32_t)FLAG_LOD0)) return 1;   // EWA: no jitter, lattice or reuse
@@ -1064,7 +1252,7 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
     Queries Q{n, u, v, dudx, dvdx, dudy, dvdy};
     Out O{rgb, picks, picks64, bdist, mag, rdist};
     parallel_for(n, nthreads, [&](uint64_t q) {
-        run_query(T, Q, q, ids ? ids[q] : q, filter, mode, smode, spp, seed, flags, O);
+        run_query(T, Q, q, ids ? ids[q] : q, filter, mode, smode, spp, seed, flags, sigma, O);
     });
     return 0;
 }

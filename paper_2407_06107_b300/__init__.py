@@ -15,7 +15,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstf.so")
 
-FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4}
+FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4, "gauss": 5}
+SAMPLERS = {"frs": 0, "fis": 1}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
 FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F, FMT_DCT6 = 0, 1, 2, 3, 4
@@ -55,6 +56,10 @@ class _Output(C.Structure):
     _fields_ = [("r", C.c_void_p), ("g", C.c_void_p), ("b", C.c_void_p), ("picks", C.c_void_p)]
 
 
+class _FilterDesc(C.Structure):
+    _fields_ = [("filter", C.c_int), ("sampler", C.c_int), ("sigma", C.c_float)]
+
+
 class _NeuralDesc(C.Structure):
     _fields_ = [("tex_res", C.c_uint32), ("grid_res", C.c_uint32 * 4), ("latent_init", C.POINTER(C.c_void_p)),
                 ("mlp_init", C.c_void_p), ("targets", C.c_void_p)]
@@ -83,6 +88,8 @@ SIGNATURES = {
     "stf_destroy_texture": ([_P, _U64], _I),
     "stf_filter_shade": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32, _U64,
                           _U32, C.POINTER(_Output)], _I),
+    "stf_filter_shade_ex": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), C.POINTER(_FilterDesc), _I, _I,
+                             _U32, _U64, _U32, C.POINTER(_Output)], _I),
     "stf_filter_shade_host": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                _U64, _U32, C.POINTER(_Output)], _I),
     "stf_bin_queries": ([_P, _U64, _P, _P, _P, _U32, _U32, _P], _I),
@@ -238,17 +245,24 @@ class Context:
 
     def filter_shade(self, tex: int, u, v, derivs=None, filter: str = "bspline", mode: str = "stochastic",
                      shade: str = "ggx", spp: int = 1, seed: int = 1, flags: int = 0, id_base: int = 0,
-                     out=None, want_picks: bool = False, order=None):
+                     out=None, want_picks: bool = False, order=None, sampler: str = "frs", sigma: float = 0.0):
         """u, v, derivs (dudx, dvdx, dudy, dvdy): float32 cuda tensors; order: optional int32
-        cuda permutation (execution order).  Returns (r, g, b, picks)."""
+        cuda permutation (execution order); sampler "frs" / "fis" and sigma (texels) for the
+        Gaussian go through stf_filter_shade_ex.  Returns (r, g, b, picks)."""
         torch = self.torch
         n = int(u.shape[0])
         if out is None:
             out = [torch.empty(n, dtype=torch.float32, device=u.device) for _ in range(3)]
         picks = torch.empty((n, spp, 2), dtype=torch.int32, device=u.device) if want_picks else None
         q, d, o = self._args(u, v, derivs, out, picks, n, id_base, order)
-        st = lib().stf_filter_shade(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
-                                    FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
+        dp = C.byref(d) if d is not None else None
+        if sampler != "frs" or filter == "gauss":
+            fd = _FilterDesc(FILTERS[filter], SAMPLERS[sampler], float(sigma))
+            st = lib().stf_filter_shade_ex(self.h, tex, C.byref(q), dp, C.byref(fd), MODES[mode], SHADES[shade],
+                                           spp, seed, flags, C.byref(o))
+        else:
+            st = lib().stf_filter_shade(self.h, tex, C.byref(q), dp, FILTERS[filter], MODES[mode], SHADES[shade],
+                                        spp, seed, flags, C.byref(o))
         self._check(st, self.h)
         return out[0], out[1], out[2], picks
 

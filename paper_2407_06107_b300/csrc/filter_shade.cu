@@ -549,10 +549,161 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
     a.b[q] = acc.z * inv_spp;
 }
 
+// ---------------------------------------------------------------- Gaussian filters and FIS
+// Sec. 4.2 "Filter Importance Sampling" and the supplement's Gaussian listings.
+//   F_GAUSS      exp(-d^2 / (2 sigma^2)) at texel centres, normalised.  STOCHASTIC: separable
+//                CDF picks over the 4 x 4 window at offsets -1..2 from floor(p) (filter
+//                reservoir sampling); the estimate is the picked texel's shade.
+//   F_GAUSS_BOX  the Gaussian convolved with the unit box (what FIS with a nearest lookup
+//                converges to), N-tap only.  N-tap windows are |i - p| <= ceil(5 sigma) + 1,
+//                each axis normalised.
+//   F_FIS_*      STOCHASTIC only: a continuous offset o in texels, then the nearest texel
+//                floor(x W + o): the tent from o = u - 1/2, the cubic B-spline from o = u1 + u2 +
+//                u3 - 3/2 (Cox-de Boor), the Gaussian from o = sigma * Box-Muller(1 - u_a, u_b).
+// Picks are FP32 in a fixed order; the Box-Muller transcendentals (logf, sqrtf, sincospif)
+// agree with correctly rounded ones to an ulp or two, which can move a sample that lies
+// within an ulp of x W of a texel edge.
+template <int FILTER, int MODE, int V, int TF>
+__device__ __forceinline__ void gauss_query(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
+                                            const RoundKeys& K, uint64_t q) {
+    const uint32_t flags = V == KV_GENERAL ? a.flags : 0u;
+    uint32_t* const picks = V == KV_GENERAL ? a.picks : nullptr;
+    const float u = a.u[q], v = a.v[q];
+    float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f, lam = 0.0f;
+    if (a.has_derivs) {
+        dudx = a.dudx[q]; dvdx = a.dvdx[q]; dudy = a.dudy[q]; dvdy = a.dvdy[q];
+        if (T.levels > 1) lam = lod_aniso(dudx, dvdx, dudy, dvdy, (float)T.w[0], (float)T.h[0], T.levels);
+    }
+    if (isnan(u) || isnan(v) || isnan(dudx) || isnan(dvdx) || isnan(dudy) || isnan(dvdy))
+        atomicOr(a.status, DEV_NAN_INPUT);
+    if (flags & FLAG_LOD0) lam = 0.0f;
+    const int l0 = (int)floorf(lam);
+    const float fr = __fsub_rn(lam, (float)l0);
+    const uint64_t id = a.id_base + q;
+    const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (uint32_t s = 0; s < a.spp; ++s) {
+        const U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+        float x = u, y = v;
+        if (a.has_derivs) jitter(s, a.kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
+        float3 est = make_float3(0.f, 0.f, 0.f);
+        if constexpr (MODE == M_STOCHASTIC) {
+            const int lvl = min(l0 + ((A.u[2] < fr) ? 1 : 0), T.levels - 1);
+            const int W = T.w[lvl], H = T.h[lvl];
+            int ix, iy;
+            if constexpr (FILTER == F_GAUSS) {
+                const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+                float wx[4], wy[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float dx = __fsub_rn(ax.t, (float)(k - 1)), dy = __fsub_rn(ay.t, (float)(k - 1));
+                    wx[k] = expf(__fmul_rn(__fmul_rn(-0.5f, __fmul_rn(dx, dx)), a.inv_s2));
+                    wy[k] = expf(__fmul_rn(__fmul_rn(-0.5f, __fmul_rn(dy, dy)), a.inv_s2));
+                }
+                ix = ax.i0 - 1 + cdf_pick<4>(wx, A.u[3], 0, nullptr);
+                iy = ay.i0 - 1 + cdf_pick<4>(wy, A.u[4], 0, nullptr);
+            } else {
+                float ox, oy;
+                if constexpr (FILTER == F_FIS_LINEAR) {
+                    ox = __fsub_rn(A.u[3], 0.5f);
+                    oy = __fsub_rn(A.u[4], 0.5f);
+                } else if constexpr (FILTER == F_FIS_BSPLINE) {
+                    const U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                    ox = __fsub_rn(__fadd_rn(__fadd_rn(A.u[3], B.u[0]), B.u[1]), 1.5f);
+                    oy = __fsub_rn(__fadd_rn(__fadd_rn(A.u[4], B.u[2]), B.u[3]), 1.5f);
+                } else {
+                    const float r = __fsqrt_rn(__fmul_rn(-2.0f, logf(__fsub_rn(1.0f, A.u[3]))));
+                    float sn, c;
+                    sincospif(__fmul_rn(2.0f, A.u[4]), &sn, &c);
+                    ox = __fmul_rn(a.sigma, __fmul_rn(r, c));
+                    oy = __fmul_rn(a.sigma, __fmul_rn(r, sn));
+                }
+                ix = (int)floorf(__fmaf_rn(x, (float)W, ox));
+                iy = (int)floorf(__fmaf_rn(y, (float)H, oy));
+            }
+            const int wx_ = wrap_index(ix, W), wy_ = wrap_index(iy, H);
+            est = shade(a.shade, fetch_t<TF>(T, lvl, wx_, wy_), SC);
+            if (picks) {
+                uint32_t* p2 = picks + (q * a.spp + s) * 2;
+                p2[0] = pack_pick(lvl, wx_, wy_);
+                p2[1] = NO_PICK;
+            }
+        } else {
+            Material fm;
+            fm.rho = make_float3(0.f, 0.f, 0.f);
+            fm.rough = 0.f;
+            fm.n = make_float3(0.f, 0.f, 0.f);
+            const int R = (int)ceilf(5.0f * a.sigma) + 1;
+#pragma unroll 1
+            for (int li = 0; li < 2; ++li) {
+                const int lvl = l0 + li;
+                const float wl = li == 0 ? __fsub_rn(1.0f, fr) : fr;
+                if (wl == 0.0f || lvl >= T.levels) continue;
+                const int W = T.w[lvl], H = T.h[lvl];
+                const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+                auto wgt = [&](float d) {
+                    if (FILTER == F_GAUSS) return expf(-0.5f * d * d * a.inv_s2);
+                    const float k = 1.0f / a.sigma;
+                    return normcdff((d + 0.5f) * k) - normcdff((d - 0.5f) * k);
+                };
+                float sx = 0.0f, sy = 0.0f;
+                for (int k = 0; k < 2 * R + 2; ++k) {
+                    sx += wgt((float)(k - R) - ax.t);
+                    sy += wgt((float)(k - R) - ay.t);
+                }
+                const float nrm = wl / (sx * sy);
+                for (int j = 0; j < 2 * R + 2; ++j) {
+                    const float wyj = wgt((float)(j - R) - ay.t) * nrm;
+                    const int iy = wrap_index(ay.i0 - R + j, H);
+                    for (int i = 0; i < 2 * R + 2; ++i) {
+                        const float w = wyj * wgt((float)(i - R) - ax.t);
+                        if (w == 0.0f) continue;
+                        const Material m = fetch_t<TF>(T, lvl, wrap_index(ax.i0 - R + i, W), iy);
+                        if (MODE == M_NTAP_BEFORE) {
+                            fm.rho.x = fmaf(w, m.rho.x, fm.rho.x);
+                            fm.rho.y = fmaf(w, m.rho.y, fm.rho.y);
+                            fm.rho.z = fmaf(w, m.rho.z, fm.rho.z);
+                            fm.rough = fmaf(w, m.rough, fm.rough);
+                            fm.n.x = fmaf(w, m.n.x, fm.n.x);
+                            fm.n.y = fmaf(w, m.n.y, fm.n.y);
+                            fm.n.z = fmaf(w, m.n.z, fm.n.z);
+                        } else {
+                            const float3 f = shade(a.shade, m, SC);
+                            est.x = fmaf(w, f.x, est.x);
+                            est.y = fmaf(w, f.y, est.y);
+                            est.z = fmaf(w, f.z, est.z);
+                        }
+                    }
+                }
+            }
+            if (MODE == M_NTAP_BEFORE) {
+                const float ln2 = dot3(fm.n, fm.n);
+                if (ln2 > 0.0f) {
+                    const float inv = 1.0f / sqrtf(ln2);
+                    fm.n = make_float3(fm.n.x * inv, fm.n.y * inv, fm.n.z * inv);
+                } else {
+                    fm.n = make_float3(0.f, 0.f, 1.f);
+                }
+                est = shade(a.shade, fm, SC);
+            }
+            if (picks) {
+                uint32_t* p2 = picks + (q * a.spp + s) * 2;
+                p2[0] = NO_PICK;
+                p2[1] = NO_PICK;
+            }
+        }
+        acc.x += est.x; acc.y += est.y; acc.z += est.z;
+    }
+    const float inv_spp = 1.0f / (float)a.spp;
+    a.r[q] = acc.x * inv_spp;
+    a.g[q] = acc.y * inv_spp;
+    a.b[q] = acc.z * inv_spp;
+}
+
 // Resident 256-thread blocks per SM the register budget is set for: 5 for the specialised
 // 1-tap variants (<= 51 registers), 4 otherwise (<= 64; positivization needs them).
 template <int FILTER, int MODE, int V>
-constexpr int min_blocks() { return (FILTER != F_EWA && V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
+constexpr int min_blocks() { return (FILTER < F_EWA && V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
 
 template <int FILTER, int MODE, int V, int TF>
 __global__ void __launch_bounds__(256, min_blocks<FILTER, MODE, V>())
@@ -564,6 +715,10 @@ k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
              i += (uint64_t)gridDim.x * blockDim.x)
             ewa_query<MODE, V, TF>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i, lut);
+    } else if constexpr (FILTER >= F_GAUSS) {
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            gauss_query<FILTER, MODE, V, TF>(a, T, SC, K, a.order ? (uint64_t)__ldg(a.order + i) : i);
     } else {
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
              i += (uint64_t)gridDim.x * blockDim.x)
@@ -619,7 +774,7 @@ static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const 
     switch (kernel_variant(a.flags, a.picks)) {
         case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
         case KV_LATTICE:   // the lattice flag changes only the separable stochastic picks
-            if constexpr (FILTER != F_EWA && (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED))
+            if constexpr (FILTER < F_EWA && (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED))
                 return launch_one<FILTER, MODE, KV_LATTICE>(a, T, SC, st);
             break;
         default: break;
@@ -630,15 +785,24 @@ static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const 
 template <int FILTER>
 static cudaError_t launch_f(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                             int num_sms, cudaStream_t st) {
-    switch (a.mode) {
-        case M_NTAP_BEFORE: return launch_fm<FILTER, M_NTAP_BEFORE>(a, T, SC, num_sms, st);
-        case M_NTAP_AFTER: return launch_fm<FILTER, M_NTAP_AFTER>(a, T, SC, num_sms, st);
-        case M_STOCHASTIC: return launch_fm<FILTER, M_STOCHASTIC>(a, T, SC, num_sms, st);
-        case M_POSITIVIZED:
-            if constexpr (is_signed(FILTER)) return launch_fm<FILTER, M_POSITIVIZED>(a, T, SC, num_sms, st);
-            return cudaErrorInvalidValue;
+    if constexpr (FILTER >= F_FIS_LINEAR) {          // FIS: a stochastic pick only
+        if (a.mode != M_STOCHASTIC) return cudaErrorInvalidValue;
+        return launch_fm<FILTER, M_STOCHASTIC>(a, T, SC, num_sms, st);
+    } else if constexpr (FILTER == F_GAUSS_BOX) {    // the FIS Gaussian's N-tap form
+        if (a.mode == M_NTAP_BEFORE) return launch_fm<FILTER, M_NTAP_BEFORE>(a, T, SC, num_sms, st);
+        if (a.mode == M_NTAP_AFTER) return launch_fm<FILTER, M_NTAP_AFTER>(a, T, SC, num_sms, st);
+        return cudaErrorInvalidValue;
+    } else {
+        switch (a.mode) {
+            case M_NTAP_BEFORE: return launch_fm<FILTER, M_NTAP_BEFORE>(a, T, SC, num_sms, st);
+            case M_NTAP_AFTER: return launch_fm<FILTER, M_NTAP_AFTER>(a, T, SC, num_sms, st);
+            case M_STOCHASTIC: return launch_fm<FILTER, M_STOCHASTIC>(a, T, SC, num_sms, st);
+            case M_POSITIVIZED:
+                if constexpr (is_signed(FILTER)) return launch_fm<FILTER, M_POSITIVIZED>(a, T, SC, num_sms, st);
+                return cudaErrorInvalidValue;
+        }
+        return cudaErrorInvalidValue;
     }
-    return cudaErrorInvalidValue;
 }
 
 ShadeConst make_shade_const() {
@@ -726,6 +890,11 @@ cudaError_t launch_filter_shade(const FilterShadeArgs& a, const TexView& tv, int
         case F_CATMULL_ROM: return launch_f<F_CATMULL_ROM>(a, T, SC, num_sms, st);
         case F_MITCHELL: return launch_f<F_MITCHELL>(a, T, SC, num_sms, st);
         case F_EWA: return launch_f<F_EWA>(a, T, SC, num_sms, st);
+        case F_GAUSS: return launch_f<F_GAUSS>(a, T, SC, num_sms, st);
+        case F_GAUSS_BOX: return launch_f<F_GAUSS_BOX>(a, T, SC, num_sms, st);
+        case F_FIS_LINEAR: return launch_f<F_FIS_LINEAR>(a, T, SC, num_sms, st);
+        case F_FIS_BSPLINE: return launch_f<F_FIS_BSPLINE>(a, T, SC, num_sms, st);
+        case F_FIS_GAUSS: return launch_f<F_FIS_GAUSS>(a, T, SC, num_sms, st);
     }
     return cudaErrorInvalidValue;
 }

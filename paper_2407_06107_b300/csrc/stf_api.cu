@@ -321,8 +321,8 @@ stf_status stf_destroy_texture(stf_ctx c, stf_tex t) {
 
 // ------------------------------------------------------------------------- filter + shade
 static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries* q, const stf_derivs* d,
-                                 stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
-                                 uint32_t flags, const stf_output* out, cudaStream_t stream) {
+                                 int f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                                 uint32_t flags, const stf_output* out, cudaStream_t stream, float sigma = 0.0f) {
     if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
     stf::FilterShadeArgs a{};
     a.n = q->n; a.id_base = q->id_base; a.u = q->u; a.v = q->v; a.order = q->order;
@@ -333,6 +333,8 @@ static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries
     a.seed = seed; a.r = out->r; a.g = out->g; a.b = out->b; a.picks = out->picks;
     a.status = c->d_status;
     a.ewa_lut = c->d_ewa_lut;
+    a.sigma = sigma;
+    a.inv_s2 = sigma > 0.0f ? 1.0f / (sigma * sigma) : 0.0f;
     cudaError_t e = stf::launch_filter_shade(a, rec.view, c->num_sms, stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "filter_shade launch");
 }
@@ -345,6 +347,37 @@ stf_status stf_filter_shade(stf_ctx c, stf_tex t, const stf_queries* q, const st
     if (s != STF_OK || q->n == 0) return s;
     CurrentDevice cd(c->device);
     return enqueue_filter(c, *rec, q, d, f, m, sh, spp, seed, flags, out, c->stream);
+}
+
+stf_status stf_filter_shade_ex(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
+                               const stf_filter_desc* fd, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                               uint32_t flags, const stf_output* out) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    if (!fd) return fail(c, STF_ERR_INVALID_ARG, "null filter descriptor");
+    if (fd->sampler != STF_SAMPLER_FRS && fd->sampler != STF_SAMPLER_FIS)
+        return fail(c, STF_ERR_INVALID_ARG, "sampler out of range");
+    const bool gauss = fd->filter == STF_FILTER_GAUSSIAN, fis = fd->sampler == STF_SAMPLER_FIS;
+    if (!gauss && !fis) return stf_filter_shade(c, t, q, d, fd->filter, m, sh, spp, seed, flags, out);
+    if (fis && fd->filter != STF_FILTER_LINEAR && fd->filter != STF_FILTER_BSPLINE && !gauss)
+        return fail(c, STF_ERR_UNSUPPORTED, "FIS samples the tent, the cubic B-spline and the Gaussian");
+    if (gauss && !(fd->sigma > 0.0f && fd->sigma <= 8.0f))
+        return fail(c, STF_ERR_INVALID_ARG, "sigma must lie in (0, 8]");
+    if (m == STF_MODE_STOCHASTIC_POSITIVIZED) return fail(c, STF_ERR_UNSUPPORTED, "no positivization for these filters");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LOD0))
+        return fail(c, STF_ERR_UNSUPPORTED, "Gaussian and FIS lookups take the STRATIFIED and LOD0 flags only");
+    // internal filter id: FIS picks are their own kernels; an N-tap FIS call evaluates the
+    // filter that FIS converges to
+    int fi;
+    if (!fis) fi = stf::F_GAUSS;
+    else if (m == STF_MODE_STOCHASTIC) fi = fd->filter == STF_FILTER_LINEAR ? stf::F_FIS_LINEAR
+                                          : fd->filter == STF_FILTER_BSPLINE ? stf::F_FIS_BSPLINE : stf::F_FIS_GAUSS;
+    else fi = fd->filter == STF_FILTER_LINEAR ? stf::F_LINEAR : fd->filter == STF_FILTER_BSPLINE ? stf::F_BSPLINE
+                                                                                                : stf::F_GAUSS_BOX;
+    TexRec* rec = nullptr;
+    stf_status s = validate_filter_call(c, t, q, d, STF_FILTER_LINEAR, m, sh, spp, flags, out, &rec);
+    if (s != STF_OK || q->n == 0) return s;
+    CurrentDevice cd(c->device);
+    return enqueue_filter(c, *rec, q, d, fi, m, sh, spp, seed, flags, out, c->stream, gauss ? fd->sigma : 0.0f);
 }
 
 // The host-buffer path is a copy pipeline: the queries are cut into chunks, and chunk k

@@ -10,6 +10,12 @@ namespace stf {
 // 2-D texture storage formats
 enum { FMT_RGBA32F = 0, FMT_RGBA8 = 1, FMT_DCT = 2 };
 
+// Filters.  0-5 are the API's; F_GAUSS_BOX and F_FIS_* are internal ids: the Gaussian convolved
+// with the unit box (the N-tap form of FIS), and the FIS picks of the tent, the cubic B-spline
+// and the Gaussian.
+enum { F_LINEAR = 0, F_BSPLINE = 1, F_CATMULL_ROM = 2, F_MITCHELL = 3, F_EWA = 4,
+       F_GAUSS = 5, F_GAUSS_BOX = 6, F_FIS_LINEAR = 7, F_FIS_BSPLINE = 8, F_FIS_GAUSS = 9 };
+
 struct TexView {
     const void* base;     // one device allocation holding every level
     int fmt;              // FMT_RGBA32F (float4 texels), FMT_RGBA8 (uint2 material texels) or
@@ -42,6 +48,7 @@ struct FilterShadeArgs {
     uint32_t* picks;
     uint32_t* status;
     const float* ewa_lut;     // EWA: the 128 Gaussian weights (context-owned device array)
+    float sigma, inv_s2;      // Gaussian filters: standard deviation in texels, 1 / sigma^2
 };
 
 constexpr int EWA_LUT_N = 128;

@@ -753,3 +753,74 @@ def test_dct_texture_filters_reproduce_a_constant():
     for f, mode in (("linear", "stochastic"), ("bspline", "ntap_before"), ("linear", "ntap_after")):
         r = oracle.filter_shade(tex, q, f, mode, spp=2)
         np.testing.assert_allclose(r.rgb, np.broadcast_to(want, r.rgb.shape), rtol=1e-12)
+
+
+# ------------------------------------------------------------------------ Gaussian filters and FIS
+@pytest.mark.parametrize("sigma", [0.3, 0.5, 0.8])
+def test_gauss_ntap_matches_scipy_gaussian_filter(sigma):
+    # the discrete Gaussian filter at texel centres (t = 0) is scipy's sampled, normalised
+    # Gaussian kernel with periodic addressing; our window reaches ceil(5 sigma) + 1 texels
+    tex = _tiny_tex(16, seed=19)
+    img = tex.levels[0].astype(np.float64)
+    iy, ix = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+    q = synth.Queries(((ix.ravel() + 0.5) / 16).astype(np.float32), ((iy.ravel() + 0.5) / 16).astype(np.float32))
+    r = oracle.filter_shade(tex, q, "gauss", "ntap_before", "linear", sigma=sigma)
+    s32 = float(np.float32(sigma))             # the API's sigma is FP32
+    R = math.ceil(5 * s32) + 1
+    for c in range(3):
+        ref = ndimage.gaussian_filter(img[..., c], s32, mode="wrap", truncate=(R + 0.25) / s32)
+        np.testing.assert_allclose(r.rgb[:, c].reshape(16, 16), ref, atol=1e-10)
+
+
+def test_box_gaussian_weights_integrate_the_density():
+    # the FIS Gaussian's N-tap form weighs texel i by the Gaussian mass over its cell
+    # [i - 1/2, i + 1/2] (in texel-centre coordinates): checked against scipy's quadrature
+    tex = _tiny_tex(16, seed=20)
+    img = tex.levels[0].astype(np.float64)
+    q = synth.queries_uniform(6, 22)
+    sigma = float(np.float32(0.6))
+    r = oracle.filter_shade(tex, q, "gauss", "ntap_before", "linear", sampler="fis", sigma=sigma)
+    pdf = lambda z: math.exp(-0.5 * (z / sigma) ** 2) / (sigma * math.sqrt(2 * math.pi))
+    for i in range(q.n):
+        px, py = float(np.float32(q.u[i]) * np.float32(16)) - 0.5, float(np.float32(q.v[i]) * np.float32(16)) - 0.5
+        ks = np.arange(math.floor(px) - 8, math.floor(px) + 10)
+        wx = np.array([integrate.quad(pdf, k - 0.5 - px, k + 0.5 - px)[0] for k in ks])
+        ls = np.arange(math.floor(py) - 8, math.floor(py) + 10)
+        wy = np.array([integrate.quad(pdf, l - 0.5 - py, l + 0.5 - py)[0] for l in ls])
+        w = np.outer(wy / wy.sum(), wx / wx.sum())
+        ref = np.einsum("yx,yxc->c", w, img[np.ix_(ls % 16, ks % 16)][..., :3])
+        np.testing.assert_allclose(r.rgb[i], ref, atol=1e-9)
+
+
+@pytest.mark.parametrize("filter,sampler,target,sigma", [
+    ("linear", "fis", ("linear", "frs"), 0.5), ("bspline", "fis", ("bspline", "frs"), 0.5),
+    ("gauss", "fis", ("gauss", "fis"), 0.4), ("gauss", "fis", ("gauss", "fis"), 0.8),
+    ("gauss", "frs", ("gauss", "frs"), 0.5)])
+def test_fis_and_frs_gaussian_means_converge(filter, sampler, target, sigma):
+    # unbiasedness: the 1-tap mean converges to the N-tap filter it samples.  FIS with a
+    # nearest lookup realises the sampled density convolved with the box: the tent from a
+    # box, the cubic B-spline from the quadratic one (Cox-de Boor), the box-convolved Gaussian
+    # from the Gaussian.  FRS's 4 x 4 Gaussian window is exact to ~3e-4 at sigma 0.5.
+    tex = _tiny_tex(16, seed=21)
+    q = synth.queries_uniform(8, 23)
+    spp = 1 << 15
+    s = oracle.filter_shade(tex, q, filter, "stochastic", "linear", spp=spp, seed=3, sampler=sampler, sigma=sigma)
+    a = oracle.filter_shade(tex, q, target[0], "ntap_after", "linear", sampler=target[1], sigma=sigma)
+    small = np.array([oracle.filter_shade(tex, q, filter, "stochastic", "linear", spp=1, seed=900 + k,
+                                          sampler=sampler, sigma=sigma).rgb for k in range(256)])
+    sd = small.std(axis=0) + 1e-6
+    z = np.abs(s.rgb - a.rgb) / (sd / math.sqrt(spp))
+    tol = 4.5 + (0 if filter != "gauss" or sampler != "frs" else 3e-4 / (sd.min() / math.sqrt(spp)))
+    assert z.max() < tol, z.max()
+
+
+def test_gaussian_and_fis_reproduce_a_constant():
+    c = np.zeros((16, 16, 4), dtype=np.float32)
+    c[...] = [0.2, 0.7, 0.4, 0.5]
+    tex = oracle.Texture([c])
+    q = synth.queries_uniform(100, 5, const_derivs=(1 / 64, 0.0, 0.0, 1 / 64))
+    want = oracle.shade_batch(c[0, 0, :3].astype(np.float64)[None], [c[0, 0, 3]], [[0, 0, 1]])[0]
+    for f, sm, mode in (("gauss", "frs", "stochastic"), ("gauss", "frs", "ntap_after"), ("gauss", "fis", "stochastic"),
+                        ("gauss", "fis", "ntap_before"), ("bspline", "fis", "stochastic"), ("linear", "fis", "stochastic")):
+        r = oracle.filter_shade(tex, q, f, mode, spp=3, sampler=sm, sigma=0.7)
+        np.testing.assert_allclose(r.rgb, np.broadcast_to(want, r.rgb.shape), rtol=1e-12)
