@@ -254,6 +254,7 @@ def run_ours(args):
         line["aniso"] = aniso_block(ctx, tex, dev)
         line["dct"] = dct_block(ctx, material, u, v, d, dev)
         line["fis"] = fis_block(ctx, tex, dev)
+        line["triplanar"] = triplanar_block(ctx, tex, material, dev)
         line["volume"] = volume_block(ctx, dev, args)
         line["table"] = table_block(ctx, dev)
         line["neural"] = neural_block(ctx, dev, material)
@@ -439,7 +440,7 @@ def dct_block(ctx, material, u, v, d, dev, nsub=1 << 16):
     over the bench's 2^24 queries at 8 and at 1 spp; RMSE against the exact filter-after value
     on the compressed texture (16 x 16 stratified footprint samples) on a 2^16-query subset."""
     import torch
-    blocks = synth.dct_compress(material)
+    blocks = dct_blocks(material)
     th = ctx.create_texture_dct(blocks, TEX_RES, TEX_RES)
     raw = sum(a.nbytes + b.nbytes for a, b in zip(material.albedo_rough, material.normal))
     res = {"compressed_bytes": int(sum(b.nbytes for b in blocks)), "uncompressed_bytes": int(raw)}
@@ -475,6 +476,74 @@ def dct_block(ctx, material, u, v, d, dev, nsub=1 << 16):
                      "stochastic_lookups_per_s": nfull * 8 / (t[("stochastic", 8)] / 1e3),
                      "s_star": s_star, "equal_rmse_speedup": (t[("ntap_before", 8)] / t_star) if t_star else None}
     ctx.destroy_texture(th)
+    return res
+
+
+_DCT_CACHE = {}
+
+
+def dct_blocks(material):
+    """The material's DCT6 blocks (computed once per material)."""
+    if id(material) not in _DCT_CACHE:
+        _DCT_CACHE[id(material)] = synth.dct_compress(material)
+    return _DCT_CACHE[id(material)]
+
+
+def triplanar_block(ctx, tex, material, dev, nq=1 << 22, nsub=1 << 16):
+    """Triplanar mapping (Sec. 5 "Triplanar mapping"; Sec. 4.4): 2^22 surface points with
+    normals uniform on the sphere and tangent-plane footprints (minor axis over 6 MIP levels,
+    anisotropy up to 8), the 4096^2 material on all three planes, trilinear, GGX.  Fully
+    deterministic: filter-before on every plane, blended (24 texels per sample); stochastic
+    filter with the full blend (3 texels); stochastic filter and stochastic blend (1 texel).
+    Then the same on the DCT-compressed material: the paper's DCT + stochastic-triplanar
+    combination against fully deterministic filtering.  RMSE against the exact filter-after
+    full blend (16 x 16 stratified footprint samples) on a 2^16-point subset."""
+    import torch
+    q = synth.queries_triplanar(nq, 51, res=TEX_RES, lod_range=6.0, max_aniso=8.0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    P, N = [t(q.px), t(q.py), t(q.pz)], [t(q.nx), t(q.ny), t(q.nz)]
+    D = [t(x) for x in (*q.dpdx, *q.dpdy)]
+    sub = lambda xs: [x[:nsub] for x in xs]
+    Ps, Ns, Ds = sub(P), sub(N), sub(D)
+    mk = lambda n: [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    outf, outs = mk(nq), mk(nsub)
+    tdct = ctx.create_texture_dct(dct_blocks(material), TEX_RES, TEX_RES)
+    configs = {"fully_deterministic": ("ntap_before", "full", 24), "ntap_after_full_blend": ("ntap_after", "full", 24),
+               "stochastic_filter_full_blend": ("stochastic", "full", 3),
+               "fully_stochastic": ("stochastic", "stochastic", 1)}
+    res = {"surface_points": nq, "rmse_subset": nsub, "filter": "linear (trilinear)", "paper_dct_triplanar_speedup": 7.9}
+    for name, h in (("rgba8", tex), ("dct6", tdct)):
+        hs = [h, h, h]
+        ref = mk(nsub)
+        ctx.triplanar_shade(hs, 1.0, Ps, Ns, Ds, "linear", "ntap_after", "full", "ggx", 256, 1, STRATIFIED, out=ref)
+        R = torch.stack(ref, 1).double()
+
+        def rmse(mode, blend, spp):
+            ctx.triplanar_shade(hs, 1.0, Ps, Ns, Ds, "linear", mode, blend, "ggx", spp, 7, 0, out=outs)
+            return float(((torch.stack(outs, 1).double() - R) ** 2).mean().sqrt())
+
+        def timed(mode, blend, spp):
+            return _time_launch(lambda: ctx.triplanar_shade(hs, 1.0, P, N, D, "linear", mode, blend, "ggx", spp, 1, 0,
+                                                            out=outf))
+        entry = {}
+        for key, (mode, blend, texels) in configs.items():
+            ms1, ms8 = timed(mode, blend, 1), timed(mode, blend, 8)
+            entry[key] = {"texels_per_sample": texels, "ms_1spp": ms1, "ms_8spp": ms8,
+                          "points_per_s_1spp": nq / (ms1 / 1e3),
+                          "rmse_1spp": rmse(mode, blend, 1), "rmse_8spp": rmse(mode, blend, 8)}
+        det = entry["fully_deterministic"]
+        for key in ("stochastic_filter_full_blend", "fully_stochastic"):
+            entry[key]["speedup_vs_fully_deterministic_1spp"] = det["ms_1spp"] / entry[key]["ms_1spp"]
+            entry[key]["speedup_vs_fully_deterministic_8spp"] = det["ms_8spp"] / entry[key]["ms_8spp"]
+        curve = {sp: rmse("stochastic", "stochastic", sp) for sp in SPP_GRID}
+        s_star, s_free = _s_star(curve, det["rmse_8spp"])
+        t_star = timed("stochastic", "stochastic", s_star) if s_star else None
+        entry["fully_stochastic"].update({"rmse_curve": {str(k): v for k, v in curve.items()}, "s_star": s_star,
+                                          "s_star_unconstrained": s_free,
+                                          "equal_rmse_speedup_vs_deterministic_8spp":
+                                              (det["ms_8spp"] / t_star) if t_star else None})
+        res[name] = entry
+    ctx.destroy_texture(tdct)
     return res
 
 

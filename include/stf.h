@@ -236,6 +236,55 @@ stf_status stf_filter_shade_table(stf_ctx ctx, stf_table table, const stf_querie
                                   const stf_derivs* d, stf_filter filter, stf_mode mode, stf_shade shade,
                                   uint32_t spp, uint64_t seed, uint32_t flags, const stf_output* out);
 
+/* ---- triplanar mapping (Sec. 5 "Triplanar mapping"; Sec. 4.4 material graphs) --------- */
+/* A surface point P with normal N is looked up on three planes: plane 0 at
+ * (u, v) = scale * (P.y, P.z), plane 1 at scale * (P.x, P.z), plane 2 at scale * (P.x, P.y),
+ * each in its own texture, with the derivatives of P projected the same way.  The blend
+ * weights are b_i = |N_i|^4 / sum_j |N_j|^4 (FP32, fixed order); a normal whose weights all
+ * vanish uses plane 2 alone.  Each plane's lookup is the 2-D lookup of stf_filter_shade
+ * (jitter in the plane's footprint, level from its derivatives and its texture's level-0
+ * size, the filter in `mode`), all planes of a sample from the same uniforms. */
+typedef enum {
+    STF_BLEND_FULL = 0,        /* every plane with b_i > 0, weighted: sum_i b_i L_i.  With
+                                  NTAP_BEFORE the planes' filtered materials are blended and the
+                                  result is shaded once.                                      */
+    STF_BLEND_STOCHASTIC = 1   /* one plane per sample, drawn with probability b_i (Eq.
+                                  stochastic-sum over the blend), from the fifth uniform of the
+                                  sample's second Philox stream; weight b_i / p_i = 1          */
+} stf_blend;
+
+typedef struct {
+    uint64_t n;          /* number of queries (0 is a valid no-op)                          */
+    uint64_t id_base;    /* Philox id of query 0                                            */
+    const float* px;     /* [n] surface position, world units                               */
+    const float* py;
+    const float* pz;
+    const float* nx;     /* [n] surface normal, any length                                  */
+    const float* ny;
+    const float* nz;
+    const uint32_t* order;  /* nullable: [n] execution order, as in stf_queries              */
+} stf_tri_queries;
+
+typedef struct {         /* screen-space derivatives of P, [n] each                         */
+    const float* dpdx_x;
+    const float* dpdx_y;
+    const float* dpdx_z;
+    const float* dpdy_x;
+    const float* dpdy_y;
+    const float* dpdy_z;
+} stf_tri_derivs;
+
+/* Triplanar filter + shade.  tex: three texture handles (planes 0, 1, 2; they may repeat),
+ * either all DCT6 or none; filters LINEAR, BSPLINE, CATMULL_ROM, MITCHELL; flags STRATIFIED,
+ * LATTICE and LOD0 (REUSE: STF_ERR_UNSUPPORTED); scale finite and non-zero.  derivs NULL: no
+ * jitter, level 0.  out->picks (nullable) is [n][spp][3][2]: per plane the stf_output pick
+ * pair, 0xFFFFFFFF for a plane the sample did not look up (and for N-tap modes).
+ * Device memory throughout; asynchronous on the context's stream. */
+stf_status stf_triplanar_shade(stf_ctx ctx, const stf_tex tex[3], float scale, const stf_tri_queries* q,
+                               const stf_tri_derivs* d, stf_filter filter, stf_mode mode, stf_blend blend,
+                               stf_shade shade, uint32_t spp, uint64_t seed, uint32_t flags,
+                               const stf_output* out);
+
 /* ---- pick binning: spatial ordering of queries for gather locality -------------------- */
 /* Counting sort of the n queries by bin = (tex_id[i], tile of (frac(u), frac(v)) on a
  * 2^tile_log2 x 2^tile_log2 grid): order_out[n] (device uint32) lists the queries bin by

@@ -31,6 +31,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4, "gauss": 5}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
+BLENDS = {"full": 0, "stochastic": 1}
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
 FLAG_REUSE = 4
@@ -97,6 +98,8 @@ def lib():
         L.orc_march.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_float, P, C.c_uint32, C.c_uint32,
                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                 C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
+        L.orc_triplanar_shade.argtypes = [P, C.c_uint64] + [P] * 13 + [
+            C.c_float, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, C.c_int]
         D = C.c_double
         for nm in ("orc_round_bf16", "orc_round_fp16", "orc_round_e4m3"):
             getattr(L, nm).argtypes = [D]
@@ -311,6 +314,35 @@ def filter_shade(tex: Texture, q, filter: str, mode: str, shade: str = "ggx", sp
     if rc != 0:
         raise ValueError("oracle: invalid filter_shade arguments")
     return FilterResult(rgb, picks, picks64, bd, mag, rdist)
+
+
+def triplanar_shade(texs, q, scale: float, filter: str, mode: str, blend: str, shade: str = "ggx", spp: int = 1,
+                    seed: int = 1, flags: int = 0, want_picks: bool = False, nthreads: int | None = None,
+                    ids=None) -> FilterResult:
+    """Triplanar lookups (Sec. 5 "Triplanar mapping"): texs = three Textures (planes along x, y,
+    z; they may repeat); q a stf_synth.TriQueries.  picks / picks64: (n, spp, 3, 2)."""
+    n = q.n
+    rgb = np.zeros((n, 3))
+    picks = np.zeros((n, spp, 3, 2), dtype=np.uint32) if want_picks else None
+    picks64 = np.zeros((n, spp, 3, 2), dtype=np.uint32) if want_picks else None
+    bd = np.zeros(n)
+    mag = np.zeros((n, 3))
+    structs, seen = [], {}
+    for t in texs:                      # one struct per distinct texture (it owns the level refs)
+        if id(t) not in seen:
+            seen[id(t)] = t._struct()
+        structs.append(seen[id(t)])
+    arr = (_Tex * 3)(*structs)
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    arrs = [f32(a) for a in (q.px, q.py, q.pz, q.nx, q.ny, q.nz)]
+    d = [f32(a) for a in ((q.dpdx + q.dpdy) if q.dpdx is not None else (None,) * 6)]
+    ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint64)
+    rc = lib().orc_triplanar_shade(C.cast(arr, C.c_void_p), n, *[_p(a) for a in arrs + d], _p(ids), float(scale),
+                                   FILTERS[filter], MODES[mode], BLENDS[blend], SHADES[shade], spp, seed, flags,
+                                   _p(rgb), _p(picks), _p(picks64), _p(bd), _p(mag), nthreads or nthreads_default())
+    if rc != 0:
+        raise ValueError("oracle: invalid triplanar_shade arguments")
+    return FilterResult(rgb, picks, picks64, bd, mag, None)
 
 
 @dataclass

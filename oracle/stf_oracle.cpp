@@ -779,8 +779,10 @@ void run_query_gauss(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, in
     if (O.bdist) O.bdist[q] = bd;
 }
 
+// keep (nullable, [spp]): samples with keep[s] == 0 add nothing (and report no picks) but
+// still count in the mean; the triplanar blend uses it to give each plane its own samples.
 void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filter, int mode, int smode,
-               uint32_t spp, uint64_t seed, uint32_t flags, float sigma, Out& O) {
+               uint32_t spp, uint64_t seed, uint32_t flags, float sigma, Out& O, const uint8_t* keep = nullptr) {
     float lam32; double lam64;
     lod(T, Q, q, &lam32, &lam64);
     if (flags & FLAG_LOD0) { lam32 = 0.0f; lam64 = 0.0; }   // finest level only (no MIP prefiltering)
@@ -845,6 +847,7 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
         uint32_t* pk64 = O.picks64 ? O.picks64 + (q * spp + s) * 2 : nullptr;
         if (pk) pk[0] = pk[1] = NO_PICK;
         if (pk64) pk64[0] = pk64[1] = NO_PICK;
+        if (keep && !keep[s]) continue;
         double est[3] = {0, 0, 0};
 
         if (mode == M_NTAP_BEFORE || mode == M_NTAP_AFTER) {
@@ -1002,6 +1005,191 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
     if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c] / (double)spp;
     if (O.rdist) O.rdist[q] = rd;
     if (O.bdist) O.bdist[q] = bd;
+}
+
+// ------------------------------------------------------------------ triplanar mapping
+// Sec. 5 "Triplanar mapping" and Sec. 4.4 (material graphs): the lookups at the surface point
+// projected along x, y and z are blended with weights b_i = |n_i|^4 / sum_j |n_j|^4.  The
+// blend is a weighted sum of three values, so Eq. stochastic-sum applies to it.
+//   plane i reads texture i at (u, v) = scale * (P_y, P_z), (P_x, P_z), (P_x, P_y) for
+//   i = 0, 1, 2; the derivatives of P project the same way; each plane's lookup is run_query
+//   on that 2-D query with the query's own id (so every plane sees the same uniforms);
+//   blend FULL: sum_i b_i L_i over the planes with b_i > 0; filter-before blends the planes'
+//   filtered materials (both levels, all taps) and shades once;
+//   blend STOCHASTIC: sample s looks up one plane, drawn ~ b from the fifth uniform of
+//   stream 1 (on the lattice with FLAG_LATTICE in the stochastic modes), weight 1.
+// FP32: the plane coordinates and derivatives (one product each), the weights n_i^2 squared,
+// their sum and the plane pick; FP64: the blend values b_i.  A normal whose FP32 weights
+// all vanish takes plane 2 alone.
+struct TriQueries {
+    uint64_t n;
+    const float *px, *py, *pz, *nx, *ny, *nz;
+    const float *dxx, *dxy, *dxz, *dyx, *dyy, *dyz;   // dP/dx, dP/dy (all or none)
+};
+
+struct PlaneQuery { float u, v, d[4]; };
+
+PlaneQuery plane_query(const TriQueries& Q, uint64_t q, int i, float scale) {
+    const float P[3] = {Q.px[q], Q.py[q], Q.pz[q]};
+    const int a = i == 0 ? 1 : 0, b = i == 2 ? 1 : 2;
+    PlaneQuery p{P[a] * scale, P[b] * scale, {0.0f, 0.0f, 0.0f, 0.0f}};
+    if (Q.dxx) {
+        const float dx[3] = {Q.dxx[q], Q.dxy[q], Q.dxz[q]}, dy[3] = {Q.dyx[q], Q.dyy[q], Q.dyz[q]};
+        p.d[0] = dx[a] * scale; p.d[1] = dx[b] * scale;
+        p.d[2] = dy[a] * scale; p.d[3] = dy[b] * scale;
+    }
+    return p;
+}
+
+// the filter-before sum of one plane at (x, y): every tap of levels floor(lambda) and
+// floor(lambda) + 1 with FP64 weights, scaled by wb, added into fm
+void ntap_material(const Tex& T, float x, float y, float lam32, int filter, double wb, Mat& fm, double* rd) {
+    const int l0 = (int)std::floor(lam32);
+    const float fr = lam32 - (float)l0;
+    const double wl[2] = {1.0 - (double)fr, (double)fr};
+    const int nt = ntaps(filter), ft = first_tap(filter);
+    for (int li = 0; li < 2; ++li) {
+        const int lvl = l0 + li;
+        if (wl[li] == 0.0 || lvl >= T.levels) continue;
+        const int W = T.width[lvl], H = T.height[lvl];
+        const Axis ax = axis_at(x, W), ay = axis_at(y, H);
+        for (int j = 0; j < nt; ++j) {
+            const int iy = ay.i0 + ft + j;
+            const double wy = kernel64(filter, ay.pos - (double)iy);
+            for (int i = 0; i < nt; ++i) {
+                const int ix = ax.i0 + ft + i;
+                const double w = wb * wl[li] * kernel64(filter, ax.pos - (double)ix) * wy;
+                if (w == 0.0) continue;
+                const Mat m = fetch(T, lvl, wrapi(ix, W, T.address), wrapi(iy, H, T.address), rd);
+                for (int c = 0; c < 3; ++c) fm.rho[c] += w * m.rho[c];
+                fm.rough += w * m.rough;
+                fm.n.x += w * m.n.x; fm.n.y += w * m.n.y; fm.n.z += w * m.n.z;
+            }
+        }
+    }
+}
+
+void run_query_triplanar(const Tex* const T[3], const TriQueries& TQ, uint64_t q, uint64_t id, float scale,
+                         int filter, int mode, int blend, int smode, uint32_t spp, uint64_t seed, uint32_t flags,
+                         Out& O) {
+    const float nrm[3] = {TQ.nx[q], TQ.ny[q], TQ.nz[q]};
+    float w32[3];
+    double b64[3], W64 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        const float a2 = nrm[i] * nrm[i];
+        w32[i] = a2 * a2;
+        const double d = (double)nrm[i];
+        W64 += d * d * d * d;
+    }
+    const float W32 = (w32[0] + w32[1]) + w32[2];
+    for (int i = 0; i < 3; ++i) {
+        const double d = (double)nrm[i];
+        b64[i] = W32 > 0.0f ? (w32[i] > 0.0f ? d * d * d * d / W64 : 0.0) : (i == 2 ? 1.0 : 0.0);
+    }
+    PlaneQuery pq[3];
+    for (int i = 0; i < 3; ++i) pq[i] = plane_query(TQ, q, i, scale);
+    const bool has_d = TQ.dxx != nullptr;
+    auto plane_queries = [&](int i) {
+        return Queries{1, &pq[i].u, &pq[i].v, has_d ? &pq[i].d[0] : nullptr, has_d ? &pq[i].d[1] : nullptr,
+                       has_d ? &pq[i].d[2] : nullptr, has_d ? &pq[i].d[3] : nullptr};
+    };
+    double acc[3] = {0, 0, 0}, mag[3] = {0, 0, 0}, bd = 1e30, rd = 1.0;
+    uint32_t* pk = O.picks ? O.picks + q * spp * 6 : nullptr;
+    uint32_t* pk64 = O.picks64 ? O.picks64 + q * spp * 6 : nullptr;
+    if (pk) for (uint32_t k = 0; k < spp * 6; ++k) pk[k] = NO_PICK;
+    if (pk64) for (uint32_t k = 0; k < spp * 6; ++k) pk64[k] = NO_PICK;
+
+    if (blend == 0 && mode == M_NTAP_BEFORE) {
+        // one filtered material over all planes and taps, shaded once per sample
+        int kside = 1;
+        if (flags & FLAG_STRATIFIED) kside = (int)std::lround(std::sqrt((double)spp));
+        for (uint32_t s = 0; s < spp; ++s) {
+            uint32_t r0[4];
+            draw(seed, id, s, 0, r0);
+            float a[5];
+            uniforms5(r0, a);
+            Mat fm{}; fm.n = {0, 0, 0};
+            for (int i = 0; i < 3; ++i) {
+                if (b64[i] == 0.0) continue;
+                const Queries Qi = plane_queries(i);
+                float lam32; double lam64;
+                lod(*T[i], Qi, 0, &lam32, &lam64);
+                if (flags & FLAG_LOD0) { lam32 = 0.0f; lam64 = 0.0; }
+                if (lam64 > 0.0 && lam64 < T[i]->levels - 1) bd = std::min(bd, std::fabs(lam64 - std::nearbyint(lam64)));
+                float x = pq[i].u, y = pq[i].v;
+                if (has_d) {   // the screen-space jitter of run_query, in this plane's footprint
+                    float jx, jy;
+                    if (flags & FLAG_STRATIFIED) {
+                        jx = ((float)(s % kside) + 0.5f) / (float)kside - 0.5f;
+                        jy = ((float)(s / kside) + 0.5f) / (float)kside - 0.5f;
+                    } else {
+                        jx = a[0] - 0.5f;
+                        jy = a[1] - 0.5f;
+                    }
+                    x = std::fmaf(jy, pq[i].d[2], std::fmaf(jx, pq[i].d[0], x));
+                    y = std::fmaf(jy, pq[i].d[3], std::fmaf(jx, pq[i].d[1], y));
+                }
+                ntap_material(*T[i], x, y, lam32, filter, b64[i], fm, &rd);
+            }
+            const double ln = std::sqrt(dot(fm.n, fm.n));
+            fm.n = ln > 0 ? V3{fm.n.x / ln, fm.n.y / ln, fm.n.z / ln} : V3{0, 0, 1};
+            double est[3];
+            shade(smode, fm, est);
+            for (int c = 0; c < 3; ++c) { acc[c] += est[c]; mag[c] += std::fabs(est[c]); }
+        }
+        for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c] / (double)spp;
+        if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c] / (double)spp;
+        if (O.bdist) O.bdist[q] = bd;
+        if (O.rdist) O.rdist[q] = rd;
+        return;
+    }
+
+    // which samples each plane evaluates, and with what blend factor
+    std::vector<uint8_t> keep(3 * (size_t)spp, 1);
+    double factor[3] = {b64[0], b64[1], b64[2]};
+    if (blend == 1) {
+        const bool lat = (mode == M_STOCHASTIC || mode == M_POSITIVIZED) && (flags & FLAG_LATTICE);
+        uint32_t f1[5] = {0, 0, 0, 0, 0};
+        if (lat) { uint32_t z1[4]; draw(seed, id, 0xFFFFFFFFu, 1, z1); ints5(z1, f1); }
+        for (uint32_t s = 0; s < spp; ++s) {
+            uint32_t r1[4];
+            draw(seed, id, s, 1, r1);
+            float b[5];
+            uniforms5(r1, b);
+            if (lat) b[4] = lattice(f1[4], s, spp, 24);
+            int plane = 2;
+            if (W32 > 0.0f) {
+                plane = pick32(w32, 3, b[4], 0, nullptr);
+                pick64(b64, 3, (double)b[4], 0, &bd);
+            }
+            for (int i = 0; i < 3; ++i) keep[i * (size_t)spp + s] = plane == i;
+        }
+        factor[0] = factor[1] = factor[2] = 1.0;
+    }
+    std::vector<uint32_t> lp(2 * (size_t)spp), lp64(2 * (size_t)spp);
+    for (int i = 0; i < 3; ++i) {
+        if (blend == 0 && b64[i] == 0.0) continue;
+        bool any = false;
+        for (uint32_t s = 0; s < spp; ++s) any |= keep[i * (size_t)spp + s] != 0;
+        if (!any) continue;
+        const Queries Qi = plane_queries(i);
+        double rgb1[3], mag1[3], bd1 = 1e30, rd1 = 1.0;
+        Out O1{rgb1, pk ? lp.data() : nullptr, pk64 ? lp64.data() : nullptr, &bd1, mag1, &rd1};
+        run_query(*T[i], Qi, 0, id, filter, mode, smode, spp, seed, flags, 0.0f, O1,
+                  blend == 1 ? &keep[i * (size_t)spp] : nullptr);
+        for (int c = 0; c < 3; ++c) { acc[c] += factor[i] * rgb1[c]; mag[c] += factor[i] * mag1[c]; }
+        bd = std::min(bd, bd1);
+        rd = std::min(rd, rd1);
+        for (uint32_t s = 0; s < spp; ++s)
+            for (int k = 0; k < 2; ++k) {
+                if (pk) pk[(s * 3 + i) * 2 + k] = lp[s * 2 + k];
+                if (pk64) pk64[(s * 3 + i) * 2 + k] = lp64[s * 2 + k];
+            }
+    }
+    for (int c = 0; c < 3; ++c) O.rgb[q * 3 + c] = acc[c];
+    if (O.mag) for (int c = 0; c < 3; ++c) O.mag[q * 3 + c] = mag[c];
+    if (O.bdist) O.bdist[q] = bd;
+    if (O.rdist) O.rdist[q] = rd;
 }
 
 // ------------------------------------------------------------------ volume march
@@ -1253,6 +1441,38 @@ int orc_filter_shade(const orc_texture* tex, uint64_t n, const float* u, const f
     Out O{rgb, picks, picks64, bdist, mag, rdist};
     parallel_for(n, nthreads, [&](uint64_t q) {
         run_query(T, Q, q, ids ? ids[q] : q, filter, mode, smode, spp, seed, flags, sigma, O);
+    });
+    return 0;
+}
+
+// triplanar filter + shade: tex points at three textures (planes 0, 1, 2); rgb[n*3];
+// picks / picks64 (nullable) [n][spp][3][2]
+int orc_triplanar_shade(const orc_texture* tex, uint64_t n, const float* px, const float* py, const float* pz,
+                        const float* nx, const float* ny, const float* nz, const float* dxx, const float* dxy,
+                        const float* dxz, const float* dyx, const float* dyy, const float* dyz,
+                        const uint64_t* ids, float scale, int filter, int mode, int blend, int smode, uint32_t spp,
+                        uint64_t seed, uint32_t flags, double* rgb, uint32_t* picks, uint32_t* picks64,
+                        double* bdist, double* mag, int nthreads) {
+    if (!tex || !px || !py || !pz || !nx || !ny || !nz || !rgb || spp == 0) return 1;
+    if (filter < 0 || filter > 3 || mode < 0 || mode > 3 || (blend != 0 && blend != 1)) return 1;
+    if (mode == M_POSITIVIZED && !signed_filter(filter)) return 1;
+    if (flags & ~(uint32_t)(FLAG_STRATIFIED | FLAG_LATTICE | FLAG_LOD0)) return 1;
+    if (!std::isfinite(scale) || scale == 0.0f) return 1;
+    if (flags & FLAG_STRATIFIED) {
+        long k = std::lround(std::sqrt((double)spp));
+        if ((uint32_t)(k * k) != spp) return 1;
+    }
+    Tex T[3];
+    const Tex* Tp[3];
+    for (int i = 0; i < 3; ++i) {
+        if (tex[i].levels < 1 || tex[i].levels > 16) return 1;
+        std::memcpy(&T[i], &tex[i], sizeof(Tex));
+        Tp[i] = &T[i];
+    }
+    TriQueries Q{n, px, py, pz, nx, ny, nz, dxx, dxy, dxz, dyx, dyy, dyz};
+    Out O{rgb, picks, picks64, bdist, mag, nullptr};
+    parallel_for(n, nthreads, [&](uint64_t q) {
+        run_query_triplanar(Tp, Q, q, ids ? ids[q] : q, scale, filter, mode, blend, smode, spp, seed, flags, O);
     });
     return 0;
 }

@@ -19,6 +19,7 @@ FILTERS = {"linear": 0, "bspline": 1, "catmull_rom": 2, "mitchell": 3, "ewa": 4,
 SAMPLERS = {"frs": 0, "fis": 1}
 MODES = {"ntap_before": 0, "ntap_after": 1, "stochastic": 2, "positivized": 3}
 SHADES = {"ggx": 0, "linear": 1}
+BLENDS = {"full": 0, "stochastic": 1}
 FMT_RGBA32F, FMT_RGBA8, FMT_RG8, FMT_R16F, FMT_DCT6 = 0, 1, 2, 3, 4
 FLAG_STRATIFIED = 1
 FLAG_LATTICE = 2
@@ -54,6 +55,15 @@ class _Derivs(C.Structure):
 
 class _Output(C.Structure):
     _fields_ = [("r", C.c_void_p), ("g", C.c_void_p), ("b", C.c_void_p), ("picks", C.c_void_p)]
+
+
+class _TriQueries(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("id_base", C.c_uint64)] + [
+        (k, C.c_void_p) for k in ("px", "py", "pz", "nx", "ny", "nz", "order")]
+
+
+class _TriDerivs(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("dpdx_x", "dpdx_y", "dpdx_z", "dpdy_x", "dpdy_y", "dpdy_z")]
 
 
 class _FilterDesc(C.Structure):
@@ -100,6 +110,8 @@ SIGNATURES = {
     "stf_filter_shade_host_noalloc": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                        _U64, _U32, C.POINTER(_Output)], _I),
     "stf_measure_sector_rate": ([_P, _U64, C.POINTER(C.c_double)], _I),
+    "stf_triplanar_shade": ([_P, _P, _F, C.POINTER(_TriQueries), C.POINTER(_TriDerivs), _I, _I, _I, _I, _U32, _U64,
+                             _U32, C.POINTER(_Output)], _I),
     "stf_create_volume": ([_P, _U32, _U32, _U32, _I, _F, _P, _I, C.POINTER(_U64)], _I),
     "stf_destroy_volume": ([_P, _U64], _I),
     "stf_march_volume": ([_P, _U64, _P, _U32, _U32, _U32, _I, _I, _U32, _U64, _U32, _U64, _U64, _P, _P], _I),
@@ -263,6 +275,28 @@ class Context:
         else:
             st = lib().stf_filter_shade(self.h, tex, C.byref(q), dp, FILTERS[filter], MODES[mode], SHADES[shade],
                                         spp, seed, flags, C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2], picks
+
+    def triplanar_shade(self, textures, scale: float, p, nrm, derivs=None, filter: str = "linear",
+                        mode: str = "stochastic", blend: str = "stochastic", shade: str = "ggx", spp: int = 1,
+                        seed: int = 1, flags: int = 0, id_base: int = 0, out=None, want_picks: bool = False,
+                        order=None):
+        """Triplanar lookups of surface points: textures = three handles (planes along x, y, z);
+        p = (px, py, pz) and nrm = (nx, ny, nz) float32 cuda tensors; derivs = (dP/dx xyz,
+        dP/dy xyz), six tensors, or None.  Returns (r, g, b, picks [n, spp, 3, 2])."""
+        torch = self.torch
+        n = int(p[0].shape[0])
+        if out is None:
+            out = [torch.empty(n, dtype=torch.float32, device=p[0].device) for _ in range(3)]
+        picks = torch.empty((n, spp, 3, 2), dtype=torch.int32, device=p[0].device) if want_picks else None
+        texs = (C.c_uint64 * 3)(*[int(t) for t in textures])
+        q = _TriQueries(n, id_base, *[_ptr(x) for x in p], *[_ptr(x) for x in nrm], _ptr(order))
+        d = _TriDerivs(*[_ptr(x) for x in derivs]) if derivs is not None else None
+        o = _Output(_ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(picks))
+        st = lib().stf_triplanar_shade(self.h, texs, float(scale), C.byref(q), C.byref(d) if d is not None else None,
+                                       FILTERS[filter], MODES[mode], BLENDS[blend], SHADES[shade], spp, seed, flags,
+                                       C.byref(o))
         self._check(st, self.h)
         return out[0], out[1], out[2], picks
 

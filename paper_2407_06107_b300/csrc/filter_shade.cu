@@ -10,86 +10,9 @@
 // tap (Eq. filtering-after-shading).
 #include "stf_kernels.h"
 #include "stf_device.cuh"
+#include "stf_lookup.cuh"
 
 namespace stf {
-
-// A texel as loaded: RGBA32F uses all four words, RGBA8 + RG8 the first two.  Loading and
-// decoding are separate so that a sample's load can be issued before the previous
-// sample is shaded.
-__device__ __forceinline__ uint4 load_texel(const FetchCtx& T, int lvl, int ix, int iy) {
-    // a level has at most 16384^2 = 2^28 texels: the index fits 32 bits
-    const uint32_t idx = (uint32_t)iy * (uint32_t)T.w[lvl] + (uint32_t)ix;
-    if (T.fmt == FMT_RGBA32F) return __ldg(reinterpret_cast<const uint4*>(T.base + T.off[lvl]) + idx);
-    const uint2 t = __ldg(reinterpret_cast<const uint2*>(T.base + T.off[lvl]) + idx);
-    return make_uint4(t.x, t.y, 0u, 0u);
-}
-__device__ __forceinline__ Material decode_texel(const FetchCtx& T, uint4 r) {
-    if (T.fmt == FMT_RGBA32F)
-        return decode_rgba32f(make_float4(__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z), __uint_as_float(r.w)));
-    return decode_rgba8(make_uint2(r.x, r.y), T.has_normal != 0);
-}
-__device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, int iy) {
-    return decode_texel(T, load_texel(T, lvl, ix, iy));
-}
-
-// Texture-format family of a kernel instantiation: BASIC (RGBA32F or RGBA8 + RG8, told apart
-// at run time) or DCT (compressed blocks, decoded per texel).  A loaded texel's type and its
-// decode depend on the family, so the DCT path adds no registers to the other one.
-enum { TF_BASIC = 0, TF_DCT = 1 };
-template <int TF> struct RawOf { using type = uint4; };
-template <> struct RawOf<TF_DCT> { using type = DctRaw; };
-
-template <int TF>
-__device__ __forceinline__ typename RawOf<TF>::type load_raw(const FetchCtx& T, int lvl, int ix, int iy) {
-    if constexpr (TF == TF_DCT) return load_dct(T.base + T.off[lvl], T.w[lvl], ix, iy);
-    else return load_texel(T, lvl, ix, iy);
-}
-template <int TF>
-__device__ __forceinline__ Material decode_raw(const FetchCtx& T, const typename RawOf<TF>::type& r) {
-    if constexpr (TF == TF_DCT) return decode_dct(r);
-    else return decode_texel(T, r);
-}
-template <int TF>
-__device__ __forceinline__ Material fetch_t(const FetchCtx& T, int lvl, int ix, int iy) {
-    return decode_raw<TF>(T, load_raw<TF>(T, lvl, ix, iy));
-}
-
-__device__ __forceinline__ uint32_t pack_pick(int lvl, int ix, int iy) {
-    return ((uint32_t)lvl << 28) | ((uint32_t)iy << 14) | (uint32_t)ix;
-}
-
-// LOD from the derivative footprint: log2 of the minor axis in level-0 texels with the
-// anisotropy capped at 64 (supplement listing computeLodAniso), clamped to [0, L-1].
-__device__ __forceinline__ float lod_aniso(float dudx, float dvdx, float dudy, float dvdy,
-                                           float W, float H, int levels) {
-    const float ax = __fmul_rn(dudx, W), ay = __fmul_rn(dvdx, H);
-    const float bx = __fmul_rn(dudy, W), by = __fmul_rn(dvdy, H);
-    const float la = __fmaf_rn(ay, ay, __fmul_rn(ax, ax));
-    const float lb = __fmaf_rn(by, by, __fmul_rn(bx, bx));
-    float mn = la, mx = lb;
-    if (mn > mx) { mn = lb; mx = la; }
-    float minl = sqrtf(mn);
-    const float maxl = sqrtf(mx);
-    if (minl > 0.0f && __fmul_rn(minl, 64.0f) < maxl) minl = __fmul_rn(maxl, 1.0f / 64.0f);
-    const float l = log2f(minl);
-    return fminf(fmaxf(l, 0.0f), (float)(levels - 1));
-}
-
-// Screen-space jitter of sample s inside the derivative footprint (Sec. 4.2.1): a uniform
-// offset in [-1/2, 1/2)^2, or the centre of cell s of a kside x kside grid (stratified).
-__device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, const U5& A, float dudx, float dvdx,
-                                       float dudy, float dvdy, float* x, float* y) {
-    float jx, jy;
-    if (flags & FLAG_STRATIFIED) {
-        jx = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s % kside), 0.5f), (float)kside), 0.5f);
-        jy = __fsub_rn(__fdiv_rn(__fadd_rn((float)(s / kside), 0.5f), (float)kside), 0.5f);
-    } else {
-        jx = __fsub_rn(A.u[0], 0.5f);
-        jy = __fsub_rn(A.u[1], 0.5f);
-    }
-    *x = __fmaf_rn(jy, dudy, __fmaf_rn(jx, dudx, *x));
-    *y = __fmaf_rn(jy, dvdy, __fmaf_rn(jx, dvdx, *y));
-}
 
 // One query: all its samples, written to a.r/g/b[q].  T is the texture (a kernel
 // parameter, or a descriptor in global memory for the bindless table).  V: the kernel
@@ -98,7 +21,6 @@ __device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, co
 template <int FILTER, int MODE, int V = KV_GENERAL, int TF = TF_BASIC>
 __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC,
                                            const RoundKeys& K, uint64_t q) {
-    constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
     const float inv_spp = 1.0f / (float)a.spp;
     const int kside = a.kside;
     const uint32_t flags = V == KV_GENERAL ? a.flags : variant_flags(V);
@@ -138,55 +60,14 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 }
                 float x = u, y = v;
                 if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
-                int lvl = l0 + ((A.u[2] < fr) ? 1 : 0);
-                float ru = A.u[2];                 // FLAG_REUSE: one uniform, remapped per decision
-                if (flags & FLAG_REUSE) {
-                    float r2;
-                    lvl = l0 + level_reuse(A.u[2], fr, &r2);
-                    ru = r2;
-                }
-                lvl = min(lvl, T.levels - 1);
-                const int W = T.w[lvl], H = T.h[lvl];
-                const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
-                float wx[4], wy[4];
-                axis_weights<FILTER>(ax.t, wx);
-                axis_weights<FILTER>(ay.t, wy);
-                float Sx, Sy;
-                int kx, ky;
-                bool nx = false, ny = false;     // sign of the picked weight per axis
-                if (flags & FLAG_REUSE) {
-                    float uy, dummy;
-                    kx = cdf_pick_reuse<NT>(wx, ru, &uy);
-                    ky = cdf_pick_reuse<NT>(wy, uy, &dummy);
-                    if (is_signed(FILTER)) {
-                        cdf_pick<NT>(wx, 0.0f, 0, &Sx); cdf_pick<NT>(wy, 0.0f, 0, &Sy);
-                        // the sign of the picked weight, selected without dynamic register indexing
-#pragma unroll
-                        for (int k = 0; k < NT; ++k) {
-                            nx = (k == kx) ? (wx[k] < 0.0f) : nx;
-                            ny = (k == ky) ? (wy[k] < 0.0f) : ny;
-                        }
-                    }
-                } else if (is_signed(FILTER)) {
-                    kx = cdf_pick_sign<NT>(wx, A.u[3], &Sx, &nx);
-                    ky = cdf_pick_sign<NT>(wy, A.u[4], &Sy, &ny);
-                } else {
-                    kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
-                    ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
-                }
-                const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
-                float Wt = 1.0f;
-                if (is_signed(FILTER)) {
-                    Wt = Sx * Sy;
-                    if (nx != ny) Wt = -Wt;
-                }
-                *wt = Wt;
+                const Pick1 p = pick_1tap<FILTER>(T, x, y, l0, fr, A, (flags & FLAG_REUSE) != 0);
+                *wt = p.wt;
                 if (picks) {
                     uint32_t* pk = picks + (q * a.spp + s) * 2;
-                    pk[0] = pack_pick(lvl, ix, iy);
+                    pk[0] = pack_pick(p.lvl, p.ix, p.iy);
                     pk[1] = NO_PICK;
                 }
-                return load_raw<TF>(T, lvl, ix, iy);
+                return load_raw<TF>(T, p.lvl, p.ix, p.iy);
             };
             float wt_next;
             typename RawOf<TF>::type raw_next = pick(0, &wt_next);
@@ -210,109 +91,24 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
             float3 est;
             if (MODE == M_POSITIVIZED) {
-                const int lvl = min(l0 + ((A.u[2] < fr) ? 1 : 0), T.levels - 1);
-                const int W = T.w[lvl], H = T.h[lvl];
-                const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
-                float wx[4], wy[4];
-                axis_weights<FILTER>(ax.t, wx);
-                axis_weights<FILTER>(ay.t, wy);
-                // positivization: one sample from each sign set, separable (Sec. 2.2)
-                float Px, Nx, Py, Ny;
-                cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
-                cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
-                const float Wp = __fmaf_rn(Nx, Ny, __fmul_rn(Px, Py));
-                const float Wn = __fmaf_rn(Nx, Py, __fmul_rn(Px, Ny));
                 // stream 1: (positive class, negative pick x, negative pick y, negative class)
                 U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
                 if (lat) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], lshift, 24);
                 }
-                const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
-                const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
-                const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
-                const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
-                const typename RawOf<TF>::type raw_p = load_raw<TF>(T, lvl, ix, iy);
-                // both loads are issued before either texel is shaded
-                uint32_t negpick = NO_PICK;
-                typename RawOf<TF>::type raw_n{};
-                if (Wn > 0.0f) {
-                    const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
-                    const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
-                    const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
-                    const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
-                    raw_n = load_raw<TF>(T, lvl, jx, jy);
-                    negpick = pack_pick(lvl, jx, jy);
-                }
-                const float3 f = shade(a.shade, decode_raw<TF>(T, raw_p), SC);
-                est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
-                if (Wn > 0.0f) {
-                    const float3 g = shade(a.shade, decode_raw<TF>(T, raw_n), SC);
-                    est.x = fmaf(-Wn, g.x, est.x);
-                    est.y = fmaf(-Wn, g.y, est.y);
-                    est.z = fmaf(-Wn, g.z, est.z);
-                }
+                uint32_t pk0, pk1;
+                est = positivized_sample<FILTER, TF>(T, x, y, l0, fr, A, B, a.shade, SC, &pk0, &pk1);
                 if (picks) {
                     uint32_t* pk = picks + (q * a.spp + s) * 2;
-                    pk[0] = pack_pick(lvl, ix, iy);
-                    pk[1] = negpick;
+                    pk[0] = pk0;
+                    pk[1] = pk1;
                 }
             } else {
-                // N-tap: every tap of levels floor(lam) and floor(lam)+1
-                Material fm;
-                fm.rho = make_float3(0.f, 0.f, 0.f);
-                fm.rough = 0.f;
-                fm.n = make_float3(0.f, 0.f, 0.f);
+                Material fm = zero_material();
                 float3 fsum = make_float3(0.f, 0.f, 0.f);
-#pragma unroll 1
-                for (int li = 0; li < 2; ++li) {
-                    const int lvl = l0 + li;
-                    const float wl = li == 0 ? __fsub_rn(1.0f, fr) : fr;
-                    if (wl == 0.0f || lvl >= T.levels) continue;
-                    const int W = T.w[lvl], H = T.h[lvl];
-                    const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
-                    float wx[4], wy[4];
-                    axis_weights<FILTER>(ax.t, wx);
-                    axis_weights<FILTER>(ay.t, wy);
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) {
-                        const int iy = wrap_index(ay.i0 + T0 + j, H);
-                        const float wyl = wl * wy[j];
-#pragma unroll
-                        for (int i = 0; i < NT; ++i) {
-                            const float w = wyl * wx[i];
-                            if (w == 0.0f) continue;
-                            const int ix = wrap_index(ax.i0 + T0 + i, W);
-                            const Material m = fetch_t<TF>(T, lvl, ix, iy);
-                            if (MODE == M_NTAP_BEFORE) {
-                                fm.rho.x = fmaf(w, m.rho.x, fm.rho.x);
-                                fm.rho.y = fmaf(w, m.rho.y, fm.rho.y);
-                                fm.rho.z = fmaf(w, m.rho.z, fm.rho.z);
-                                fm.rough = fmaf(w, m.rough, fm.rough);
-                                fm.n.x = fmaf(w, m.n.x, fm.n.x);
-                                fm.n.y = fmaf(w, m.n.y, fm.n.y);
-                                fm.n.z = fmaf(w, m.n.z, fm.n.z);
-                            } else {
-                                const float3 f = shade(a.shade, m, SC);
-                                fsum.x = fmaf(w, f.x, fsum.x);
-                                fsum.y = fmaf(w, f.y, fsum.y);
-                                fsum.z = fmaf(w, f.z, fsum.z);
-                            }
-                        }
-                    }
-                }
-                if (MODE == M_NTAP_BEFORE) {
-                    const float ln2 = dot3(fm.n, fm.n);
-                    if (ln2 > 0.0f) {
-                        const float inv = 1.0f / sqrtf(ln2);
-                        fm.n = make_float3(fm.n.x * inv, fm.n.y * inv, fm.n.z * inv);
-                    } else {
-                        fm.n = make_float3(0.f, 0.f, 1.f);
-                    }
-                    est = shade(a.shade, fm, SC);
-                } else {
-                    est = fsum;
-                }
+                ntap_accumulate<FILTER, MODE, TF>(T, x, y, l0, fr, 1.0f, a.shade, SC, fm, fsum);
+                est = MODE == M_NTAP_BEFORE ? shade_filtered(a.shade, fm, SC) : fsum;
                 if (picks) {
                     uint32_t* pk = picks + (q * a.spp + s) * 2;
                     pk[0] = NO_PICK;

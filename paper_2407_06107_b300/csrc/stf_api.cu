@@ -380,6 +380,65 @@ stf_status stf_filter_shade_ex(stf_ctx c, stf_tex t, const stf_queries* q, const
     return enqueue_filter(c, *rec, q, d, fi, m, sh, spp, seed, flags, out, c->stream, gauss ? fd->sigma : 0.0f);
 }
 
+// ------------------------------------------------------------------------- triplanar
+stf_status stf_triplanar_shade(stf_ctx c, const stf_tex tex[3], float scale, const stf_tri_queries* q,
+                               const stf_tri_derivs* d, stf_filter f, stf_mode m, stf_blend blend, stf_shade sh,
+                               uint32_t spp, uint64_t seed, uint32_t flags, const stf_output* out) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    if (!tex || !q || !out) return fail(c, STF_ERR_INVALID_ARG, "textures, queries and output must be non-null");
+    TexRec* rec[3];
+    for (int i = 0; i < 3; ++i) {
+        auto it = c->tex.find(tex[i]);
+        if (it == c->tex.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle");
+        rec[i] = &it->second;
+    }
+    const bool dct0 = rec[0]->view.fmt == stf::FMT_DCT;
+    if ((rec[1]->view.fmt == stf::FMT_DCT) != dct0 || (rec[2]->view.fmt == stf::FMT_DCT) != dct0)
+        return fail(c, STF_ERR_INVALID_ARG, "the three textures must all be DCT6 or all be uncompressed");
+    if (bad_enum_filter(f) || bad_enum_mode(m) || (sh != STF_SHADE_GGX_LAMBERT && sh != STF_SHADE_LINEAR) ||
+        (blend != STF_BLEND_FULL && blend != STF_BLEND_STOCHASTIC))
+        return fail(c, STF_ERR_INVALID_ARG, "filter, mode, blend or shade out of range");
+    if (m == STF_MODE_STOCHASTIC_POSITIVIZED && !signed_filter(f))
+        return fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
+    if (spp == 0) return fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
+    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE | STF_FLAG_LOD0))
+        return fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    if (flags & STF_FLAG_REUSE) return fail(c, STF_ERR_UNSUPPORTED, "triplanar lookups take no sample reuse");
+    if ((flags & STF_FLAG_STRATIFIED) && square_side(spp) < 0)
+        return fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
+    if (!std::isfinite(scale) || scale == 0.0f) return fail(c, STF_ERR_INVALID_ARG, "scale must be finite and non-zero");
+    if (q->n == 0) return STF_OK;
+    if (q->n > (1ull << 40)) return fail(c, STF_ERR_INVALID_ARG, "too many queries");
+    if (out->picks && q->n * (uint64_t)spp > (1ull << 38)) return fail(c, STF_ERR_INVALID_ARG, "pick buffer too large");
+    const void* ptrs[9] = {q->px, q->py, q->pz, q->nx, q->ny, q->nz, out->r, out->g, out->b};
+    for (const void* p : ptrs)
+        if (!p || !aligned4(p)) return fail(c, STF_ERR_INVALID_ARG, "query/output pointers must be non-null and 4-byte aligned");
+    if (d) {
+        const void* dp[6] = {d->dpdx_x, d->dpdx_y, d->dpdx_z, d->dpdy_x, d->dpdy_y, d->dpdy_z};
+        for (const void* p : dp)
+            if (!p || !aligned4(p)) return fail(c, STF_ERR_INVALID_ARG, "derivative pointers must be all non-null and 4-byte aligned");
+    }
+    if (out->picks && !aligned4(out->picks)) return fail(c, STF_ERR_INVALID_ARG, "picks must be 4-byte aligned");
+    if (c->fault == FAULT_LAUNCH) return fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
+    CurrentDevice cd(c->device);
+    stf::TriplanarArgs a{};
+    a.n = q->n; a.id_base = q->id_base; a.order = q->order;
+    a.px = q->px; a.py = q->py; a.pz = q->pz; a.nx = q->nx; a.ny = q->ny; a.nz = q->nz;
+    a.has_derivs = d ? 1 : 0;
+    if (d) {
+        a.dxx = d->dpdx_x; a.dxy = d->dpdx_y; a.dxz = d->dpdx_z;
+        a.dyx = d->dpdy_x; a.dyy = d->dpdy_y; a.dyz = d->dpdy_z;
+    }
+    a.scale = scale;
+    a.filter = f; a.mode = m; a.blend = blend; a.shade = sh; a.spp = spp; a.flags = flags;
+    a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
+    a.seed = seed; a.r = out->r; a.g = out->g; a.b = out->b; a.picks = out->picks;
+    a.status = c->d_status;
+    const stf::TexView tv[3] = {rec[0]->view, rec[1]->view, rec[2]->view};
+    cudaError_t e = stf::launch_triplanar(a, tv, c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "triplanar launch");
+}
+
 // The host-buffer path is a copy pipeline: the queries are cut into chunks, and chunk k
 // goes to lane k mod STF_LANES (its own stream and staging buffers), so that one chunk's
 // host->device copy, another's kernel and a third's device->host copy run at once on the

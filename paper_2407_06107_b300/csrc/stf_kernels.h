@@ -53,6 +53,26 @@ struct FilterShadeArgs {
 
 constexpr int EWA_LUT_N = 128;
 
+// Triplanar lookups: plane i projects the surface point along axis i (plane 0 reads (y, z),
+// plane 1 (x, z), plane 2 (x, y)), each plane with its own texture.
+enum { BLEND_FULL = 0, BLEND_STOCHASTIC = 1 };
+
+struct TriplanarArgs {
+    uint64_t n, id_base;
+    const uint32_t* order;      // nullable execution order
+    const float *px, *py, *pz, *nx, *ny, *nz;
+    const float *dxx, *dxy, *dxz, *dyx, *dyy, *dyz;   // dP/dx and dP/dy components
+    int has_derivs;
+    float scale;                // texture coordinates per world unit
+    int filter, mode, blend, shade;
+    uint32_t spp, flags;
+    int kside;
+    uint64_t seed;
+    float *r, *g, *b;
+    uint32_t* picks;            // nullable: [n][spp][3][2]
+    uint32_t* status;
+};
+
 struct MarchArgs {
     const __half* vox;    // nz*ny*nx FP16
     int nx, ny, nz;
@@ -119,6 +139,7 @@ FetchCtx make_fetch_ctx(const TexView& tv);
 cudaError_t launch_filter_shade_table(const FilterShadeArgs& a, const FetchCtx* table, uint32_t ntex,
                                       const uint32_t* tex_id, unsigned long long* counter, int num_sms,
                                       cudaStream_t st);
+cudaError_t launch_triplanar(const TriplanarArgs& a, const TexView tv[3], cudaStream_t st);
 cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_bin_queries(uint64_t n, const float* u, const float* v, const uint32_t* tex_id, uint32_t ntex,
                                uint32_t tile_log2, uint32_t* order, uint32_t* scratch, uint64_t nbins,

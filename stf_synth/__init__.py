@@ -279,6 +279,63 @@ def queries_aniso(n: int, seed: int, res: int, lod_range: float = 4.0, max_aniso
     return Queries(u, v, f(dx[0]), f(dx[1]), f(dy[0]), f(dy[1]))
 
 
+@dataclass
+class TriQueries:
+    """Surface points for triplanar lookups: position, normal, screen-space dP/dx and dP/dy
+    (tuples of three float32 arrays, or None)."""
+    px: np.ndarray
+    py: np.ndarray
+    pz: np.ndarray
+    nx: np.ndarray
+    ny: np.ndarray
+    nz: np.ndarray
+    dpdx: tuple | None = None
+    dpdy: tuple | None = None
+
+    @property
+    def n(self) -> int:
+        return int(self.px.shape[0])
+
+    def subset(self, idx) -> "TriQueries":
+        f = (lambda a: np.array(a[idx], copy=True))
+        t = (lambda d: None if d is None else tuple(f(a) for a in d))
+        return TriQueries(f(self.px), f(self.py), f(self.pz), f(self.nx), f(self.ny), f(self.nz),
+                          t(self.dpdx), t(self.dpdy))
+
+
+def queries_triplanar(n: int, seed: int, res: int, scale: float = 1.0, extent: float = 4.0,
+                      lod_range: float = 4.0, max_aniso: float = 8.0, derivs: bool = True) -> TriQueries:
+    """Points on surfaces of random orientation: P uniform in [0, extent)^3 on the 2^-20 grid,
+    N uniform on the unit sphere, and a screen-space footprint in the tangent plane whose minor
+    axis is 2^lam / (res * scale) world units (lam ~ U[0, lod_range)), the major axis a times
+    longer (a log-uniform in [1, max_aniso]), at a random rotation."""
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, int(extent * (1 << 20)), size=(3, n), dtype=np.int64)
+    P = (k.astype(np.float64) * 2.0 ** -20).astype(np.float32)
+    g = rng.standard_normal((3, n))
+    N = g / np.linalg.norm(g, axis=0, keepdims=True)
+    f = lambda x: x.astype(np.float32)
+    if not derivs:
+        return TriQueries(P[0], P[1], P[2], f(N[0]), f(N[1]), f(N[2]))
+    # tangent frame: T = normalize(N x e) with e the axis least aligned with N, B = N x T
+    e = np.zeros((3, n))
+    e[np.argmin(np.abs(N), axis=0), np.arange(n)] = 1.0
+    T = np.cross(N, e, axis=0)
+    T /= np.linalg.norm(T, axis=0, keepdims=True)
+    B = np.cross(N, T, axis=0)
+    lam = lod_range * rng.random(n)
+    a = np.exp(np.log(max_aniso) * rng.random(n))
+    th = 2 * math.pi * rng.random(n)
+    mn = np.exp2(lam) / (res * scale)
+    c, s_ = np.cos(th), np.sin(th)
+    maj = (c * mn * a) * T + (s_ * mn * a) * B
+    mnr = (-s_ * mn) * T + (c * mn) * B
+    swap = rng.random(n) < 0.5
+    dx = np.where(swap, mnr, maj)
+    dy = np.where(swap, maj, mnr)
+    return TriQueries(P[0], P[1], P[2], f(N[0]), f(N[1]), f(N[2]), tuple(f(x) for x in dx), tuple(f(x) for x in dy))
+
+
 # ---------------------------------------------------------------------------------
 # volume and camera
 # ---------------------------------------------------------------------------------
