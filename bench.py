@@ -268,7 +268,7 @@ def run_ours(args):
 
 
 # the sources the 2-D filter kernels are compiled from
-FILTER_KERNEL_SOURCES = ("filter_shade.cu", "stf_device.cuh", "stf_kernels.h")
+FILTER_KERNEL_SOURCES = ("filter_shade.cu", "stf_lookup.cuh", "stf_device.cuh", "stf_kernels.h")
 
 
 def kernel_source_hash() -> str:
@@ -860,6 +860,44 @@ def run_neural(args):
     ctx.close()
 
 
+def run_triplanar(args):
+    """Triplanar workload: --queries surface points on the 4096^2 material (or its DCT6 form)
+    on all three planes, trilinear, 1 spp, --tmode / --tblend (single GPU)."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    material = synth.material_rgba8(TEX_RES, 102)
+    if args.tformat == "dct6":
+        h = ctx.create_texture_dct(synth.dct_compress(material), TEX_RES, TEX_RES)
+    else:
+        h = ctx.create_texture(material.albedo_rough, material.normal)
+    q = synth.queries_triplanar(args.queries, 51, res=TEX_RES, lod_range=6.0, max_aniso=8.0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    P, N = [t(q.px), t(q.py), t(q.pz)], [t(q.nx), t(q.ny), t(q.nz)]
+    D = [t(x) for x in (*q.dpdx, *q.dpdy)]
+    out = [torch.empty(args.queries, dtype=torch.float32, device=dev) for _ in range(3)]
+    go = lambda: ctx.triplanar_shade([h, h, h], 1.0, P, N, D, "linear", args.tmode, args.tblend, "ggx", 1, 1, out=out)
+    for _ in range(args.warmup):
+        go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        go()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "triplanar surface points/s", "value": args.queries / (ms / 1e3), "unit": "points/s",
+                      "ms_per_step": ms,
+                      "config": {"workload": f"triplanar, {args.queries} points, {args.tformat} 4096^2 on 3 planes, "
+                                             f"trilinear {args.tmode}, blend {args.tblend}, 1 spp"}}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -870,7 +908,10 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1 << 13)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="material", choices=["material", "volume", "neural"])
+    ap.add_argument("--workload", default="material", choices=["material", "volume", "neural", "triplanar"])
+    ap.add_argument("--tmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after"])
+    ap.add_argument("--tblend", default="stochastic", choices=["stochastic", "full"])
+    ap.add_argument("--tformat", default="rgba8", choices=["rgba8", "dct6"])
     ap.add_argument("--nfilter", default="bspline", choices=["bspline", "linear", "mitchell"])
     ap.add_argument("--nmode", default="stochastic", choices=["stochastic", "ntap_before", "positivized"])
     ap.add_argument("--vfilter", default="bspline", choices=["bspline", "linear"])
@@ -886,6 +927,8 @@ def main():
         run_volume(args)
     elif args.workload == "neural":
         run_neural(args)
+    elif args.workload == "triplanar":
+        run_triplanar(args)
     else:
         run_ours(args)
 
