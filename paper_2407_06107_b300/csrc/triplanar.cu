@@ -84,11 +84,11 @@ __device__ __forceinline__ float3 plane_sample(const FetchCtx& T, const PlaneQ& 
 
 // Resident 256-thread blocks per SM: 4 (<= 64 registers); 3 for positivization and the DCT
 // N-tap sums, which spill at 64.
-template <int MODE, int TF>
-constexpr int tri_min_blocks() { return (MODE == M_POSITIVIZED || (TF == TF_DCT && MODE != M_STOCHASTIC)) ? 3 : 4; }
+template <int MODE, int V, int TF>
+constexpr int tri_min_blocks() { return (MODE == M_POSITIVIZED || (TF == TF_DCT && MODE != M_STOCHASTIC)) ? 3 : (MODE == M_STOCHASTIC && V != KV_GENERAL && TF == TF_BASIC) ? 5 : 4; }
 
 template <int FILTER, int MODE, int BLEND, int V, int TF>
-__global__ void __launch_bounds__(256, tri_min_blocks<MODE, TF>())
+__global__ void __launch_bounds__(256, tri_min_blocks<MODE, V, TF>())
 k_triplanar(TriplanarArgs a, const __grid_constant__ TriTex TT, ShadeConst SC, RoundKeys K) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
