@@ -497,12 +497,16 @@ __device__ __forceinline__ void gauss_query(const FilterShadeArgs& a, const Fetc
 }
 
 // Resident 256-thread blocks per SM the register budget is set for: 5 for the specialised
-// 1-tap variants (<= 51 registers), 4 otherwise (<= 64; positivization needs them).
-template <int FILTER, int MODE, int V>
-constexpr int min_blocks() { return (FILTER < F_EWA && V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5 : 4; }
+// 1-tap variants (<= 51 registers), 3 for positivization on DCT textures (two compressed
+// texels in flight spill at 64), 4 otherwise (<= 64).
+template <int FILTER, int MODE, int V, int TF = TF_BASIC>
+constexpr int min_blocks() {
+    return (FILTER < F_EWA && V != KV_GENERAL && MODE == M_STOCHASTIC) ? 5
+           : (TF == TF_DCT && MODE == M_POSITIVIZED) ? 3 : 4;
+}
 
 template <int FILTER, int MODE, int V, int TF>
-__global__ void __launch_bounds__(256, min_blocks<FILTER, MODE, V>())
+__global__ void __launch_bounds__(256, min_blocks<FILTER, MODE, V, TF>())
 k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
     if constexpr (FILTER == F_EWA) {
         __shared__ float lut[EWA_LUT_N];
@@ -566,7 +570,11 @@ template <int FILTER, int MODE>
 static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, int num_sms,
                              cudaStream_t st) {
     (void)num_sms;
-    if (T.fmt == FMT_DCT) return launch_one<FILTER, MODE, KV_GENERAL, TF_DCT>(a, T, SC, st);
+    if (T.fmt == FMT_DCT) {
+        if constexpr (FILTER < F_EWA)
+            if (kernel_variant(a.flags, a.picks) == KV_PLAIN) return launch_one<FILTER, MODE, KV_PLAIN, TF_DCT>(a, T, SC, st);
+        return launch_one<FILTER, MODE, KV_GENERAL, TF_DCT>(a, T, SC, st);
+    }
     switch (kernel_variant(a.flags, a.picks)) {
         case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
         case KV_LATTICE:   // the lattice flag changes only the separable stochastic picks

@@ -85,7 +85,10 @@ __device__ __forceinline__ float3 plane_sample(const FetchCtx& T, const PlaneQ& 
 // Resident 256-thread blocks per SM: 4 (<= 64 registers); 3 for positivization and the DCT
 // N-tap sums, which spill at 64.
 template <int MODE, int V, int TF>
-constexpr int tri_min_blocks() { return (MODE == M_POSITIVIZED || (TF == TF_DCT && MODE != M_STOCHASTIC)) ? 3 : (MODE == M_STOCHASTIC && V != KV_GENERAL && TF == TF_BASIC) ? 5 : 4; }
+constexpr int tri_min_blocks() {
+    return (MODE == M_POSITIVIZED || (TF == TF_DCT && MODE != M_STOCHASTIC)) ? 3
+           : (MODE == M_STOCHASTIC && V != KV_GENERAL) ? 5 : 4;
+}
 
 template <int FILTER, int MODE, int BLEND, int V, int TF>
 __global__ void __launch_bounds__(256, tri_min_blocks<MODE, V, TF>())
@@ -185,7 +188,10 @@ static cudaError_t launch_tri_one(const TriplanarArgs& a, const TriTex& TT, cuda
 
 template <int FILTER, int MODE, int BLEND>
 static cudaError_t launch_tri_fmb(const TriplanarArgs& a, const TriTex& TT, cudaStream_t st) {
-    if (TT.t[0].fmt == FMT_DCT) return launch_tri_one<FILTER, MODE, BLEND, KV_GENERAL, TF_DCT>(a, TT, st);
+    if (TT.t[0].fmt == FMT_DCT) {
+        if (kernel_variant(a.flags, a.picks) == KV_PLAIN) return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_DCT>(a, TT, st);
+        return launch_tri_one<FILTER, MODE, BLEND, KV_GENERAL, TF_DCT>(a, TT, st);
+    }
     switch (kernel_variant(a.flags, a.picks)) {
         case KV_PLAIN: return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_BASIC>(a, TT, st);
         case KV_LATTICE:

@@ -57,6 +57,9 @@ def test_dct_matches_oracle(ctx, dct_tex, filter, mode, spp):
     ref = oracle.filter_shade(otex, q, filter, mode, "ggx", spp, 5, want_picks=True)
     mism = compare_picks(pk, ref, q.n)
     assert_values(rgb, ref.rgb, mism, rel=REL_DCT, scale=ref.mag)
+    # the specialised (no flags, no picks) DCT kernels return the same values
+    rgb2, _ = _run(ctx, h, q, filter, mode, spp, seed=5, picks=False)
+    assert_values(rgb2, ref.rgb, mism, rel=REL_DCT, scale=ref.mag)
 
 
 def test_dct_without_derivatives_and_lattice(ctx, dct_tex):

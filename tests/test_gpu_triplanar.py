@@ -98,7 +98,10 @@ def test_triplanar_dct_matches_oracle(ctx, dct_planes, filter, mode, blend, spp)
     q = synth.queries_triplanar(2500, 42, res=128, lod_range=5.0)
     rgb, pk = _run(ctx, hs, q, 1.0, filter, mode, blend, spp, seed=8)
     ref = oracle.triplanar_shade(ts, q, 1.0, filter, mode, blend, "ggx", spp, 8, want_picks=True)
-    assert_values(rgb, ref.rgb, compare_picks(pk, ref, q.n * 3), rel=REL_DCT, scale=ref.mag)
+    mism = compare_picks(pk, ref, q.n * 3)
+    assert_values(rgb, ref.rgb, mism, rel=REL_DCT, scale=ref.mag)
+    rgb2, _ = _run(ctx, hs, q, 1.0, filter, mode, blend, spp, seed=8, picks=False)
+    assert_values(rgb2, ref.rgb, mism, rel=REL_DCT, scale=ref.mag)
 
 
 def test_triplanar_edge_cases(ctx, planes):
