@@ -647,9 +647,10 @@ def volume_block(ctx, dev, args):
     return res
 
 
-def neural_block(ctx, dev, material, steps=256, batch=1 << 18, nq=1 << 24, spp=8):
+def neural_block(ctx, dev, material, steps=1 << 14, batch=1 << 12, nq=1 << 24, spp=8):
     """Learned form at the task's scale: 8 channels at 4096^2 in 4 latent grids
-    (1024^2/512^2/256^2/128^2 x 8) + MLP 32-64-64-8, trained on 2^26 texels (256 x 2^18);
+    (1024^2/512^2/256^2/128^2 x 8) + MLP 32-64-64-8, trained on 2^26 texels (2^14 Adam steps of
+    2^12, learning rates decayed on a half cosine to a tenth);
     then filter + shade of 2^24 queries at 8 spp decoding the MLP once per sample
     (stochastic) vs decode-then-filter with 4 (bilinear) and 16 (bicubic) decodes per sample."""
     import torch
@@ -660,7 +661,7 @@ def neural_block(ctx, dev, material, steps=256, batch=1 << 18, nq=1 << 24, spp=8
     net = ctx.neural_create(R0, lat, mlp, targets)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = ctx.neural_train(net, steps, batch, 1e-2, 5e-3, seed=1)
+    losses = ctx.neural_train(net, steps, batch, 1e-2, 2e-3, seed=1, lr_min_frac=0.1)
     train_s = time.perf_counter() - t0
     res = {"train": {"steps": steps, "batch": batch, "seconds": train_s, "samples_per_s": steps * batch / train_s,
                      "loss_first": float(losses[:4].mean()), "loss_last": float(losses[-8:].mean())}}

@@ -348,7 +348,11 @@ typedef struct {
     const uint8_t* targets;         /* host [tex_res^2][8] bytes, nullable (no training)     */
 } stf_neural_desc;
 
-typedef struct { float lr_latent, lr_mlp, beta1, beta2, eps; } stf_adam_params;
+/* Adam (Kingma & Ba 2015) with bias correction.  lr_min_frac < 1 decays both learning rates
+ * over the `steps` of one stf_neural_train call on a half cosine, from lr at the first step
+ * to lr * lr_min_frac at the last: lr_k = lr (f + (1 - f)(1 + cos(pi k / steps)) / 2),
+ * k = 0 .. steps-1.  lr_min_frac = 1 keeps them constant. */
+typedef struct { float lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac; } stf_adam_params;
 
 typedef enum {
     STF_LATENT_FP16 = 0,            /* inference latents FP16 (round to nearest even)        */

@@ -77,7 +77,7 @@ class _NeuralDesc(C.Structure):
 
 class _Adam(C.Structure):
     _fields_ = [("lr_latent", C.c_float), ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float)]
+                ("eps", C.c_float), ("lr_min_frac", C.c_float)]
 
 
 NEURAL_BLOCKS = {"latents": 0, "mlp": 1, "grad_latents": 2, "grad_mlp": 3, "adam": 4, "scales": 5, "step": 6}
@@ -406,9 +406,12 @@ class Context:
         self._check(lib().stf_neural_destroy(self.h, net), self.h)
 
     def neural_train(self, net: int, steps: int, batch: int, lr_latent: float = 1e-2, lr_mlp: float = 5e-3,
-                     seed: int = 1, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> np.ndarray:
+                     seed: int = 1, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                     lr_min_frac: float = 1.0) -> np.ndarray:
+        """steps Adam steps of batch samples; lr_min_frac < 1 decays the learning rates on a half
+        cosine to lr * lr_min_frac over the call.  Returns the per-step losses."""
         losses = np.zeros(steps, dtype=np.float32)
-        ap = _Adam(lr_latent, lr_mlp, beta1, beta2, eps)
+        ap = _Adam(lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac)
         self._check(lib().stf_neural_train(self.h, net, steps, batch, C.byref(ap), seed,
                                            losses.ctypes.data if steps else None), self.h)
         return losses

@@ -1,5 +1,6 @@
 // C-ABI layer of the learned form (neural texture): creation, training, quantisation,
 // checkpoints, tensor-core decode and filter + shade.  Contract: include/stf.h.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -134,6 +135,8 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
     if (!ap) return fail(c, STF_ERR_INVALID_ARG, "adam parameters are required");
     if (!r->trainable) return fail(c, STF_ERR_UNSUPPORTED, "created without targets");
     if (batch < 1 || batch > (1u << 24)) return fail(c, STF_ERR_INVALID_ARG, "batch must be 1..2^24");
+    if (!(ap->lr_min_frac >= 0.0f && ap->lr_min_frac <= 1.0f))
+        return fail(c, STF_ERR_INVALID_ARG, "lr_min_frac must lie in [0, 1]");
     if (steps == 0) return STF_OK;
     CurrentDevice cd(c->device);
     if (r->loss_cap < steps) {
@@ -148,12 +151,14 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
     for (uint32_t k = 0; k < steps && e == cudaSuccess; ++k) {
         e = stf::launch_ntc_train(r->view, r->step, batch, seed, r->loss + k, nullptr, nullptr, c->stream);
         const int t = (int)r->step + 1;
+        // half-cosine decay over this call's steps (factor 1 when lr_min_frac = 1)
+        const double f = ap->lr_min_frac, fk = f + (1.0 - f) * 0.5 * (1.0 + std::cos(M_PI * (double)k / (double)steps));
         if (e == cudaSuccess)
-            e = stf::launch_adam(r->view.lat32, r->view.dlat, r->m_lat, r->v_lat, r->lat_total, ap->lr_latent,
+            e = stf::launch_adam(r->view.lat32, r->view.dlat, r->m_lat, r->v_lat, r->lat_total,
+                                 (float)(ap->lr_latent * fk), ap->beta1, ap->beta2, ap->eps, t, c->stream);
+        if (e == cudaSuccess)
+            e = stf::launch_adam(r->view.mlp32, r->view.grad32, r->m_mlp, r->v_mlp, MLP_N, (float)(ap->lr_mlp * fk),
                                  ap->beta1, ap->beta2, ap->eps, t, c->stream);
-        if (e == cudaSuccess)
-            e = stf::launch_adam(r->view.mlp32, r->view.grad32, r->m_mlp, r->v_mlp, MLP_N, ap->lr_mlp, ap->beta1,
-                                 ap->beta2, ap->eps, t, c->stream);
         r->step++;
     }
     if (e == cudaSuccess && losses) e = cudaMemcpyAsync(losses, r->loss, steps * 4, cudaMemcpyDeviceToHost, c->stream);
