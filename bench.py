@@ -861,6 +861,39 @@ def run_neural(args):
     ctx.close()
 
 
+def run_ntap(args):
+    """N-tap comparator workload: filter-before over the material workload's queries (--queries),
+    8 spp, trilinear / bicubic B-spline / Mitchell with all taps of both MIP levels (8 / 32 / 32
+    taps), timed per filter over --steps launches."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    material = synth.material_rgba8(TEX_RES, 102)
+    tex = ctx.create_texture(material.albedo_rough, material.normal)
+    q = make_queries(args.queries, 0)
+    t = lambda a: torch.from_numpy(a).to(dev)
+    u, v = t(q.u), t(q.v)
+    d = [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]
+    out = [torch.empty(args.queries, dtype=torch.float32, device=dev) for _ in range(3)]
+    go = lambda f: ctx.filter_shade(tex, u, v, d, f, "ntap_before", "ggx", SPP, 1, out=out)
+    for _ in range(args.warmup):
+        for f in FILTERS:
+            go(f)
+    torch.cuda.synchronize()
+    ms = {}
+    for f in FILTERS:
+        ms[f] = _time_launch(lambda: go(f), reps=args.steps)
+    print(json.dumps({"metric": "N-tap filter-before shaded lookups/s", "unit": "lookups/s",
+                      "value": args.queries * SPP * len(FILTERS) / (sum(ms.values()) / 1e3), "ms_per_launch": ms,
+                      "config": {"workload": f"2-D material, {args.queries} queries, {SPP} spp, filter-before over "
+                                             "both MIP levels (8 / 32 / 32 taps)"}}), flush=True)
+    ctx.close()
+
+
 def run_triplanar(args):
     """Triplanar workload: --queries surface points on the 4096^2 material (or its DCT6 form)
     on all three planes, trilinear, 1 spp, --tmode / --tblend (single GPU)."""
@@ -909,7 +942,7 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1 << 13)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="material", choices=["material", "volume", "neural", "triplanar"])
+    ap.add_argument("--workload", default="material", choices=["material", "volume", "neural", "triplanar", "ntap"])
     ap.add_argument("--tmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after"])
     ap.add_argument("--tblend", default="stochastic", choices=["stochastic", "full"])
     ap.add_argument("--tformat", default="rgba8", choices=["rgba8", "dct6"])
@@ -930,6 +963,8 @@ def main():
         run_neural(args)
     elif args.workload == "triplanar":
         run_triplanar(args)
+    elif args.workload == "ntap":
+        run_ntap(args)
     else:
         run_ours(args)
 

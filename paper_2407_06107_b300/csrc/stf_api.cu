@@ -677,6 +677,11 @@ stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t wid
     a.width = width; a.height = height; a.steps = steps; a.spp = spp; a.flags = flags;
     a.kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
     a.filter = f; a.mode = m; a.seed = seed; a.pix_begin = pix_begin; a.pix_count = pix_count;
+    // 8 x 4 pixel tiles per warp where they measured faster at 1920x1080 x 8 spp (1-tap: 2-5 %,
+    // tricubic filter-after: 17 %); filter-before keeps row order (tiles: tricubic +-0 %,
+    // trilinear 15 % slower)
+    const uint64_t band = 4ull * width;
+    a.tiled = (m != STF_MODE_NTAP_BEFORE && width % 8 == 0 && pix_begin % band == 0 && pix_count % band == 0) ? 1 : 0;
     a.T = out_T; a.picks = out_picks; a.status = c->d_status;
     cudaError_t e = stf::launch_march(a, c->num_sms, c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "march launch");

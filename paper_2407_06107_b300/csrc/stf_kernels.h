@@ -82,6 +82,7 @@ struct MarchArgs {
     int kside;
     int filter, mode;
     uint64_t seed, pix_begin, pix_count;
+    int tiled;            // threads walk 8 x 4 pixel tiles (width % 8 == 0, range in whole 4-row bands)
     float* T;
     uint32_t* picks;
     uint32_t* status;
