@@ -575,11 +575,19 @@ static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const 
             if (kernel_variant(a.flags, a.picks) == KV_PLAIN) return launch_one<FILTER, MODE, KV_PLAIN, TF_DCT>(a, T, SC, st);
         return launch_one<FILTER, MODE, KV_GENERAL, TF_DCT>(a, T, SC, st);
     }
+    // the specialised variants of the separable filters also fix the texture family when it is
+    // RGBA8 with a normal map
+    const bool rgba8n = texture_family(T) == TF_RGBA8N;
     switch (kernel_variant(a.flags, a.picks)) {
-        case KV_PLAIN: return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
+        case KV_PLAIN:
+            if constexpr (FILTER < F_EWA)
+                if (rgba8n) return launch_one<FILTER, MODE, KV_PLAIN, TF_RGBA8N>(a, T, SC, st);
+            return launch_one<FILTER, MODE, KV_PLAIN>(a, T, SC, st);
         case KV_LATTICE:   // the lattice flag changes only the separable stochastic picks
-            if constexpr (FILTER < F_EWA && (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED))
+            if constexpr (FILTER < F_EWA && (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED)) {
+                if (rgba8n) return launch_one<FILTER, MODE, KV_LATTICE, TF_RGBA8N>(a, T, SC, st);
                 return launch_one<FILTER, MODE, KV_LATTICE>(a, T, SC, st);
+            }
             break;
         default: break;
     }

@@ -28,20 +28,34 @@ __device__ __forceinline__ Material fetch(const FetchCtx& T, int lvl, int ix, in
 }
 
 // Texture-format family of a kernel instantiation: BASIC (RGBA32F or RGBA8 + RG8, told apart
-// at run time) or DCT (compressed blocks, decoded per texel).  A loaded texel's type and its
-// decode depend on the family, so the DCT path adds no registers to the other one.
-enum { TF_BASIC = 0, TF_DCT = 1 };
+// at run time), RGBA8N (RGBA8 with its RG8 normal map, fixed at compile time: no format tests
+// per texel) or DCT (compressed blocks, decoded per texel).  A loaded texel's type and its
+// decode depend on the family, so the DCT path adds no registers to the others.
+enum { TF_BASIC = 0, TF_DCT = 1, TF_RGBA8N = 2 };
 template <int TF> struct RawOf { using type = uint4; };
 template <> struct RawOf<TF_DCT> { using type = DctRaw; };
+template <> struct RawOf<TF_RGBA8N> { using type = uint2; };
+
+// the family a texture's kernels may use: RGBA8N for RGBA8 textures with a normal map
+inline int texture_family(const FetchCtx& T) {
+    return T.fmt == FMT_DCT ? TF_DCT : (T.fmt == FMT_RGBA8 && T.has_normal) ? TF_RGBA8N : TF_BASIC;
+}
 
 template <int TF>
 __device__ __forceinline__ typename RawOf<TF>::type load_raw(const FetchCtx& T, int lvl, int ix, int iy) {
-    if constexpr (TF == TF_DCT) return load_dct(T.base + T.off[lvl], T.w[lvl], ix, iy);
-    else return load_texel(T, lvl, ix, iy);
+    if constexpr (TF == TF_DCT) {
+        return load_dct(T.base + T.off[lvl], T.w[lvl], ix, iy);
+    } else if constexpr (TF == TF_RGBA8N) {
+        const uint32_t idx = (uint32_t)iy * (uint32_t)T.w[lvl] + (uint32_t)ix;
+        return __ldg(reinterpret_cast<const uint2*>(T.base + T.off[lvl]) + idx);
+    } else {
+        return load_texel(T, lvl, ix, iy);
+    }
 }
 template <int TF>
 __device__ __forceinline__ Material decode_raw(const FetchCtx& T, const typename RawOf<TF>::type& r) {
     if constexpr (TF == TF_DCT) return decode_dct(r);
+    else if constexpr (TF == TF_RGBA8N) return decode_rgba8(r, true);
     else return decode_texel(T, r);
 }
 template <int TF>
@@ -215,15 +229,26 @@ __device__ __forceinline__ void ntap_accumulate(const FetchCtx& T, float x, floa
         float wx[4], wy[4];
         axis_weights<FILTER>(ax.t, wx);
         axis_weights<FILTER>(ay.t, wy);
+        // the window's wrapped columns and rows: one full wrap per axis, then +1 steps
+        int cx[4], ry[4];
+        cx[0] = wrap_index(ax.i0 + T0, W);
+        ry[0] = wrap_index(ay.i0 + T0, H);
+#pragma unroll
+        for (int k = 1; k < NT; ++k) {
+            cx[k] = cx[k - 1] + 1 == W ? 0 : cx[k - 1] + 1;
+            ry[k] = ry[k - 1] + 1 == H ? 0 : ry[k - 1] + 1;
+        }
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
-            const int iy = wrap_index(ay.i0 + T0 + j, H);
+            const int iy = ry[j];
             const float wyl = wl * wy[j];
 #pragma unroll
             for (int i = 0; i < NT; ++i) {
                 const float w = wyl * wx[i];
-                if (w == 0.0f) continue;
-                const int ix = wrap_index(ax.i0 + T0 + i, W);
+                // a zero weight adds nothing to finite texels; RGBA8 and DCT decodes are always
+                // finite, RGBA32F ones need not be, and 0 * inf must not enter the sum
+                if (TF == TF_BASIC && w == 0.0f) continue;
+                const int ix = cx[i];
                 const Material m = fetch_t<TF>(T, lvl, ix, iy);
                 if (MODE == M_NTAP_BEFORE) {
                     fm.rho.x = fmaf(w, m.rho.x, fm.rho.x);

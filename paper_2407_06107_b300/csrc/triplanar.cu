@@ -192,11 +192,17 @@ static cudaError_t launch_tri_fmb(const TriplanarArgs& a, const TriTex& TT, cuda
         if (kernel_variant(a.flags, a.picks) == KV_PLAIN) return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_DCT>(a, TT, st);
         return launch_tri_one<FILTER, MODE, BLEND, KV_GENERAL, TF_DCT>(a, TT, st);
     }
+    const bool rgba8n = texture_family(TT.t[0]) == TF_RGBA8N && texture_family(TT.t[1]) == TF_RGBA8N &&
+                        texture_family(TT.t[2]) == TF_RGBA8N;
     switch (kernel_variant(a.flags, a.picks)) {
-        case KV_PLAIN: return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_BASIC>(a, TT, st);
+        case KV_PLAIN:
+            if (rgba8n) return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_RGBA8N>(a, TT, st);
+            return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_BASIC>(a, TT, st);
         case KV_LATTICE:
-            if constexpr (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED)
+            if constexpr (MODE == M_STOCHASTIC || MODE == M_POSITIVIZED) {
+                if (rgba8n) return launch_tri_one<FILTER, MODE, BLEND, KV_LATTICE, TF_RGBA8N>(a, TT, st);
                 return launch_tri_one<FILTER, MODE, BLEND, KV_LATTICE, TF_BASIC>(a, TT, st);
+            }
             break;
         default: break;
     }
