@@ -526,6 +526,56 @@ k_filter_shade(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst
     }
 }
 
+// The 1-tap lookup at one sample per query with no flags, split at the texel load: the first
+// half (query loads, LOD, Philox, jitter, picks) issues the load, the second decodes, shades and
+// stores.  A thread runs the first half of two queries before the second half of either, so two
+// gathers are in flight per thread where query_body would have one.  Same arithmetic as
+// query_body at spp = 1.
+template <int TF> struct Pending1 { typename RawOf<TF>::type raw; float wt; };
+
+template <int FILTER, int TF>
+__device__ __forceinline__ Pending1<TF> pick_1spp(const FilterShadeArgs& a, const FetchCtx& T, const RoundKeys& K,
+                                                  uint64_t q) {
+    const float u = a.u[q], v = a.v[q];
+    float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f;
+    float lam = 0.0f;
+    if (a.has_derivs) {
+        dudx = a.dudx[q]; dvdx = a.dvdx[q]; dudy = a.dudy[q]; dvdy = a.dvdy[q];
+        if (T.levels > 1) lam = lod_aniso(dudx, dvdx, dudy, dvdy, (float)T.w[0], (float)T.h[0], T.levels);
+    }
+    if (isnan(u) || isnan(v) || isnan(dudx) || isnan(dvdx) || isnan(dudy) || isnan(dvdy))
+        atomicOr(a.status, DEV_NAN_INPUT);
+    const int l0 = (int)floorf(lam);
+    const float fr = __fsub_rn(lam, (float)l0);
+    const uint64_t id = a.id_base + q;
+    const U5 A = uniforms5(philox((uint32_t)id, (uint32_t)(id >> 32), 0u, 0u, K));
+    float x = u, y = v;
+    if (a.has_derivs) jitter(0u, 1, 0u, A, dudx, dvdx, dudy, dvdy, &x, &y);
+    const Pick1 p = pick_1tap<FILTER>(T, x, y, l0, fr, A, false);
+    return {load_raw<TF>(T, p.lvl, p.ix, p.iy), p.wt};
+}
+
+template <int FILTER, int TF>
+__global__ void __launch_bounds__(256, 5)
+k_filter_shade_1spp_pair(FilterShadeArgs a, const __grid_constant__ FetchCtx T, ShadeConst SC, RoundKeys K) {
+    const uint64_t half = (a.n + 1) / 2;
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= half) return;
+    const uint64_t j = i + half;
+    const bool two = j < a.n;
+    const uint64_t q0 = a.order ? (uint64_t)__ldg(a.order + i) : i;
+    const uint64_t q1 = two ? (a.order ? (uint64_t)__ldg(a.order + j) : j) : q0;
+    const Pending1<TF> r0 = pick_1spp<FILTER, TF>(a, T, K, q0);
+    Pending1<TF> r1{};
+    if (two) r1 = pick_1spp<FILTER, TF>(a, T, K, q1);
+    const float3 f0 = shade(a.shade, decode_raw<TF>(T, r0.raw), SC);
+    a.r[q0] = r0.wt * f0.x; a.g[q0] = r0.wt * f0.y; a.b[q0] = r0.wt * f0.z;
+    if (two) {
+        const float3 f1 = shade(a.shade, decode_raw<TF>(T, r1.raw), SC);
+        a.r[q1] = r1.wt * f1.x; a.g[q1] = r1.wt * f1.y; a.b[q1] = r1.wt * f1.z;
+    }
+}
+
 // Bindless persistent launch: one grid sized to the SMs; each block claims the next
 // chunk of blockDim.x queries from an atomic work counter (zero on entry) and looks up
 // each query's texture descriptor in the table.  An out-of-range texture id sets
@@ -566,10 +616,27 @@ static cudaError_t launch_one(const FilterShadeArgs& a, const FetchCtx& T, const
     return cudaGetLastError();
 }
 
+template <int FILTER, int TF>
+static cudaError_t launch_pair(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, cudaStream_t st) {
+    const uint64_t blocks = ((a.n + 1) / 2 + 255) / 256;
+    const int grid = (int)(blocks < 0x7FFFFFFFull ? (blocks ? blocks : 1) : 0x7FFFFFFFull);
+    k_filter_shade_1spp_pair<FILTER, TF><<<grid, 256, 0, st>>>(a, T, SC, expand_key(a.seed));
+    return cudaGetLastError();
+}
+
 template <int FILTER, int MODE>
 static cudaError_t launch_fm(const FilterShadeArgs& a, const FetchCtx& T, const ShadeConst& SC, int num_sms,
                              cudaStream_t st) {
     (void)num_sms;
+    if constexpr (FILTER < F_EWA && MODE == M_STOCHASTIC) {
+        // one sample, no flags, no picks: two queries per thread
+        if (a.spp == 1 && kernel_variant(a.flags, a.picks) == KV_PLAIN) {
+            const int fam = texture_family(T);
+            if (fam == TF_DCT) return launch_pair<FILTER, TF_DCT>(a, T, SC, st);
+            if (fam == TF_RGBA8N) return launch_pair<FILTER, TF_RGBA8N>(a, T, SC, st);
+            return launch_pair<FILTER, TF_BASIC>(a, T, SC, st);
+        }
+    }
     if (T.fmt == FMT_DCT) {
         if constexpr (FILTER < F_EWA)
             if (kernel_variant(a.flags, a.picks) == KV_PLAIN) return launch_one<FILTER, MODE, KV_PLAIN, TF_DCT>(a, T, SC, st);

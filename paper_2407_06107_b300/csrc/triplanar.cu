@@ -178,6 +178,70 @@ k_triplanar(TriplanarArgs a, const __grid_constant__ TriTex TT, ShadeConst SC, R
     a.b[q] = acc.z * inv_spp;
 }
 
+// The fully stochastic lookup at one sample per point with no flags, split at the texel
+// load: the first half picks the plane and the texel and issues the load, the second decodes,
+// shades and stores.  A thread runs the first half of two points before the second half of
+// either, so two gathers are in flight per thread.  Same arithmetic as k_triplanar.
+template <int TF> struct TriPick { typename RawOf<TF>::type raw; float wt; int plane; };
+
+template <int FILTER, int TF>
+__device__ __forceinline__ TriPick<TF> tri_pick_1spp(const TriplanarArgs& a, const TriTex& TT, const RoundKeys& K,
+                                                     uint64_t q) {
+    const bool has_d = a.has_derivs != 0;
+    const float3 P = make_float3(a.px[q], a.py[q], a.pz[q]);
+    const float3 N = make_float3(a.nx[q], a.ny[q], a.nz[q]);
+    float3 DX = make_float3(0.f, 0.f, 0.f), DY = DX;
+    if (has_d) {
+        DX = make_float3(a.dxx[q], a.dxy[q], a.dxz[q]);
+        DY = make_float3(a.dyx[q], a.dyy[q], a.dyz[q]);
+    }
+    if (isnan(P.x) || isnan(P.y) || isnan(P.z) || isnan(N.x) || isnan(N.y) || isnan(N.z) || isnan(DX.x) ||
+        isnan(DX.y) || isnan(DX.z) || isnan(DY.x) || isnan(DY.y) || isnan(DY.z))
+        atomicOr(a.status, DEV_NAN_INPUT);
+    float w[4];
+    const float W = tri_weights(N.x, N.y, N.z, w);
+    const uint64_t id = a.id_base + q;
+    const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
+    const U5 A = uniforms5(philox(id_lo, id_hi, 0u, 0u, K));
+    const U5 B = uniforms5(philox(id_lo, id_hi, 0u, 1u, K));
+    TriPick<TF> r;
+    r.plane = W > 0.0f ? cdf_pick<3>(w, B.u[4], 0, nullptr) : 2;
+    const FetchCtx& T = TT.t[r.plane];
+    const PlaneQ p = plane_query(r.plane, P, DX, DY, has_d, a.scale, T, 0u);
+    float x = p.u, y = p.v;
+    if (has_d) jitter(0u, 1, 0u, A, p.dudx, p.dvdx, p.dudy, p.dvdy, &x, &y);
+    const Pick1 k = pick_1tap<FILTER>(T, x, y, p.l0, p.fr, A, false);
+    r.raw = load_raw<TF>(T, k.lvl, k.ix, k.iy);
+    r.wt = k.wt;
+    return r;
+}
+
+template <int TF>
+__device__ __forceinline__ void tri_finish_1spp(const TriplanarArgs& a, const TriTex& TT, const ShadeConst& SC,
+                                                const TriPick<TF>& r, uint64_t q) {
+    const float3 f = shade(a.shade, decode_raw<TF>(TT.t[r.plane], r.raw), SC);
+    a.r[q] = r.wt * f.x;
+    a.g[q] = r.wt * f.y;
+    a.b[q] = r.wt * f.z;
+}
+
+template <int FILTER, int TF>
+__global__ void __launch_bounds__(256, 5)
+k_triplanar_1spp_pair(TriplanarArgs a, const __grid_constant__ TriTex TT, ShadeConst SC, RoundKeys K) {
+    const uint64_t half = (a.n + 1) / 2;
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= half) return;
+    const uint64_t j = i + half;
+    const bool two = j < a.n;
+    const uint64_t q0 = a.order ? (uint64_t)__ldg(a.order + i) : i;
+    const uint64_t q1 = two ? (a.order ? (uint64_t)__ldg(a.order + j) : j) : q0;
+    const TriPick<TF> r0 = tri_pick_1spp<FILTER, TF>(a, TT, K, q0);
+    TriPick<TF> r1{};
+    if (two) r1 = tri_pick_1spp<FILTER, TF>(a, TT, K, q1);
+    tri_finish_1spp<TF>(a, TT, SC, r0, q0);
+    if (two) tri_finish_1spp<TF>(a, TT, SC, r1, q1);
+}
+
 template <int FILTER, int MODE, int BLEND, int V, int TF>
 static cudaError_t launch_tri_one(const TriplanarArgs& a, const TriTex& TT, cudaStream_t st) {
     const uint64_t blocks = (a.n + 255) / 256;
@@ -186,14 +250,30 @@ static cudaError_t launch_tri_one(const TriplanarArgs& a, const TriTex& TT, cuda
     return cudaGetLastError();
 }
 
+template <int FILTER, int TF>
+static cudaError_t launch_tri_pair(const TriplanarArgs& a, const TriTex& TT, cudaStream_t st) {
+    const uint64_t blocks = ((a.n + 1) / 2 + 255) / 256;
+    const int grid = (int)(blocks < 0x7FFFFFFFull ? (blocks ? blocks : 1) : 0x7FFFFFFFull);
+    k_triplanar_1spp_pair<FILTER, TF><<<grid, 256, 0, st>>>(a, TT, make_shade_const(), expand_key(a.seed));
+    return cudaGetLastError();
+}
+
 template <int FILTER, int MODE, int BLEND>
 static cudaError_t launch_tri_fmb(const TriplanarArgs& a, const TriTex& TT, cudaStream_t st) {
-    if (TT.t[0].fmt == FMT_DCT) {
+    const bool dct = TT.t[0].fmt == FMT_DCT;
+    const bool rgba8n = texture_family(TT.t[0]) == TF_RGBA8N && texture_family(TT.t[1]) == TF_RGBA8N &&
+                        texture_family(TT.t[2]) == TF_RGBA8N;
+    if constexpr (MODE == M_STOCHASTIC && BLEND == BLEND_STOCHASTIC) {
+        // one sample, no flags, no picks: two points per thread
+        if (a.spp == 1 && kernel_variant(a.flags, a.picks) == KV_PLAIN) {
+            if (dct) return launch_tri_pair<FILTER, TF_DCT>(a, TT, st);
+            return rgba8n ? launch_tri_pair<FILTER, TF_RGBA8N>(a, TT, st) : launch_tri_pair<FILTER, TF_BASIC>(a, TT, st);
+        }
+    }
+    if (dct) {
         if (kernel_variant(a.flags, a.picks) == KV_PLAIN) return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_DCT>(a, TT, st);
         return launch_tri_one<FILTER, MODE, BLEND, KV_GENERAL, TF_DCT>(a, TT, st);
     }
-    const bool rgba8n = texture_family(TT.t[0]) == TF_RGBA8N && texture_family(TT.t[1]) == TF_RGBA8N &&
-                        texture_family(TT.t[2]) == TF_RGBA8N;
     switch (kernel_variant(a.flags, a.picks)) {
         case KV_PLAIN:
             if (rgba8n) return launch_tri_one<FILTER, MODE, BLEND, KV_PLAIN, TF_RGBA8N>(a, TT, st);

@@ -131,15 +131,15 @@ def test_id_base_shards_reproduce_whole(ctx, material):
     assert np.array_equal(np.concatenate([a, b]), whole)
 
 
-@pytest.mark.parametrize("flags", [0, oracle.FLAG_LATTICE])
+@pytest.mark.parametrize("flags,spp", [(0, 5), (oracle.FLAG_LATTICE, 5), (0, 1)])
 @pytest.mark.parametrize("filter", ["linear", "bspline", "catmull_rom", "mitchell"])
-def test_specialised_path_equals_general_path(ctx, material, filter, flags):
+def test_specialised_path_equals_general_path(ctx, material, filter, flags, spp):
     # a stochastic call without pick output, with no flag or the lattice flag alone, runs a
-    # specialised instantiation; it does the same arithmetic as the general one, so the
-    # results are identical
+    # specialised instantiation (at one sample and no flags: two queries per thread); it does
+    # the same arithmetic as the general one, so the results are identical
     h, _, q = material
-    with_picks, _ = _run(ctx, h, q, filter, "stochastic", 5, seed=6, flags=flags, picks=True)
-    special, _ = _run(ctx, h, q, filter, "stochastic", 5, seed=6, flags=flags, picks=False)
+    with_picks, _ = _run(ctx, h, q, filter, "stochastic", spp, seed=6, flags=flags, picks=True)
+    special, _ = _run(ctx, h, q, filter, "stochastic", spp, seed=6, flags=flags, picks=False)
     assert np.array_equal(with_picks, special)
 
 
@@ -265,3 +265,14 @@ def test_reuse_sampler(ctx, material, filter, flags):
     # flags 4 = sample reuse; 6 = reuse on a shifted lattice
     h, otex, q = material
     _check(ctx, h, otex, q, filter, "stochastic", spp=3, seed=17, flags=flags)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 255, 257, 5999])
+def test_one_sample_pairs_ragged(ctx, material, n):
+    # at one sample with no flags and no picks a thread takes queries i and i + ceil(n/2);
+    # odd counts leave the last thread one query.  Same values as the general path.
+    h, _, q = material
+    qs = q.subset(np.arange(n))
+    with_picks, _ = _run(ctx, h, qs, "bspline", "stochastic", 1, seed=9, picks=True)
+    special, _ = _run(ctx, h, qs, "bspline", "stochastic", 1, seed=9, picks=False)
+    assert np.array_equal(with_picks, special)
