@@ -258,6 +258,11 @@ def test_binned_order_is_permutation_and_results_identical(ctx, material):
         b = ctx.filter_shade(h, u, v, d, f, mode, "ggx", 3, 4, want_picks=True, order=order)
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+    # one sample, no picks: the two-queries-per-thread kernel follows the order too
+    a = ctx.filter_shade(h, u, v, d, "bspline", "stochastic", "ggx", 1, 4)
+    b = ctx.filter_shade(h, u, v, d, "bspline", "stochastic", "ggx", 1, 4, order=order)
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
 
 
 @pytest.mark.parametrize("filter,flags", [("bspline", 4), ("mitchell", 4), ("linear", 4), ("catmull_rom", 6)])

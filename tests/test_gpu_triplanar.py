@@ -128,10 +128,13 @@ def test_triplanar_edge_cases(ctx, planes):
 def test_triplanar_order_and_empty(ctx, planes):
     hs, _ = planes
     q = synth.queries_triplanar(5000, 45, res=128)
-    a, _ = _run(ctx, hs, q, 1.0, "linear", "stochastic", "stochastic", 2, seed=11, picks=False)
     perm = torch.from_numpy(np.random.default_rng(3).permutation(q.n).astype(np.int32)).cuda()
-    b, _ = _run(ctx, hs, q, 1.0, "linear", "stochastic", "stochastic", 2, seed=11, picks=False, order=perm)
-    assert np.array_equal(a, b)
+    for spp in (2, 1):    # one sample, no picks: two points per thread
+        a, _ = _run(ctx, hs, q, 1.0, "linear", "stochastic", "stochastic", spp, seed=11, picks=False)
+        b, _ = _run(ctx, hs, q, 1.0, "linear", "stochastic", "stochastic", spp, seed=11, picks=False, order=perm)
+        assert np.array_equal(a, b)
+        c, _ = _run(ctx, hs, q, 1.0, "linear", "stochastic", "stochastic", spp, seed=11, picks=True)
+        assert np.array_equal(a, c)
     e = synth.queries_triplanar(0, 46, res=128)
     rgb, _ = _run(ctx, hs, e, 1.0, "linear", "stochastic", "stochastic", 1, picks=False)
     assert rgb.shape == (0, 3)
