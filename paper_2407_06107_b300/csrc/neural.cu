@@ -147,8 +147,10 @@ __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, 
     const float tx = __fsub_rn(px, fx), ty = __fsub_rn(py, fy);
     const float ux = __fsub_rn(1.0f, tx), uy = __fsub_rn(1.0f, ty);
     LTap t;
-    t.x0 = wrap_index((int)fx, N.res[g]); t.y0 = wrap_index((int)fy, N.res[g]);
-    t.x1 = wrap_index((int)fx + 1, N.res[g]); t.y1 = wrap_index((int)fy + 1, N.res[g]);
+    const int R = N.res[g];
+    t.x0 = wrap_index((int)fx, R); t.y0 = wrap_index((int)fy, R);
+    t.x1 = t.x0 + 1 == R ? 0 : t.x0 + 1;     // the next texel, wrapped
+    t.y1 = t.y0 + 1 == R ? 0 : t.y0 + 1;
     t.w00 = __fmul_rn(ux, uy); t.w10 = __fmul_rn(tx, uy); t.w01 = __fmul_rn(ux, ty); t.w11 = __fmul_rn(tx, ty);
     return t;
 }
@@ -204,12 +206,13 @@ __device__ __forceinline__ void features2(const NeuralView& N, int fmt, int ix, 
 }
 // Inference form (FP16 or FP8 latents): the four taps of a grid as raw 16-byte (FP16) or
 // 8-byte (FP8, in .x .y) texels, and their conversion to packed FP32 pairs.
-__device__ __forceinline__ void load_taps_raw(const NeuralView& N, int fmt, int g, const LTap& t, uint4 q[4]) {
+template <int LF>
+__device__ __forceinline__ void load_taps_raw(const NeuralView& N, int g, const LTap& t, uint4 q[4]) {
     const int xs[4] = {t.x0, t.x1, t.x0, t.x1}, ys[4] = {t.y0, t.y0, t.y1, t.y1};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const size_t o = ((size_t)ys[i] * N.res[g] + xs[i]) * 8;
-        if (fmt == 0) {
+        if constexpr (LF == 0) {
             q[i] = __ldg(reinterpret_cast<const uint4*>(N.lat16 + N.lat_off[g] + o));
         } else {
             const uint2 v = __ldg(reinterpret_cast<const uint2*>(N.lat8 + N.lat_off[g] + o));
@@ -217,8 +220,9 @@ __device__ __forceinline__ void load_taps_raw(const NeuralView& N, int fmt, int 
         }
     }
 }
-__device__ __forceinline__ void raw_to_pairs(const NeuralView& N, int fmt, int g, uint4 q, uint64_t v[4]) {
-    if (fmt == 0) {
+template <int LF>
+__device__ __forceinline__ void raw_to_pairs(const NeuralView& N, int g, uint4 q, uint64_t v[4]) {
+    if constexpr (LF == 0) {
         const __half2* h = reinterpret_cast<const __half2*>(&q);
 #pragma unroll
         for (int i = 0; i < 4; ++i) { const float2 f = __half22float2(h[i]); v[i] = pk2(f.x, f.y); }
@@ -237,23 +241,25 @@ __device__ __forceinline__ void raw_to_pairs(const NeuralView& N, int fmt, int g
 // The 32 features of one decode row, rounded to BF16 and stored grid by grid into row
 // `row` of the K-major A tile (same order and rounding as features2).  The four taps of
 // grid g+1 are loaded before grid g is interpolated, so two grids' gathers are in flight.
-__device__ __forceinline__ void features_to_tile(const NeuralView& N, int fmt, int ix, int iy, uint8_t* A, int row) {
+// LF: the latent format (0 FP16, 1 FP8 x scale), fixed per kernel instantiation.
+template <int LF>
+__device__ __forceinline__ void features_to_tile(const NeuralView& N, int ix, int iy, uint8_t* A, int row) {
     LTap tc = latent_taps(N, 0, ix, iy);
     uint4 cur[4];
-    load_taps_raw(N, fmt, 0, tc, cur);
+    load_taps_raw<LF>(N, 0, tc, cur);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         uint4 nxt[4];
         LTap tn = tc;
         if (g < 3) {
             tn = latent_taps(N, g + 1, ix, iy);
-            load_taps_raw(N, fmt, g + 1, tn, nxt);
+            load_taps_raw<LF>(N, g + 1, tn, nxt);
         }
         uint64_t a[4], b[4], c[4], d[4];
-        raw_to_pairs(N, fmt, g, cur[0], a);
-        raw_to_pairs(N, fmt, g, cur[1], b);
-        raw_to_pairs(N, fmt, g, cur[2], c);
-        raw_to_pairs(N, fmt, g, cur[3], d);
+        raw_to_pairs<LF>(N, g, cur[0], a);
+        raw_to_pairs<LF>(N, g, cur[1], b);
+        raw_to_pairs<LF>(N, g, cur[2], c);
+        raw_to_pairs<LF>(N, g, cur[3], d);
         const uint64_t w00 = pk2(tc.w00, tc.w00), w10 = pk2(tc.w10, tc.w10);
         const uint64_t w01 = pk2(tc.w01, tc.w01), w11 = pk2(tc.w11, tc.w11);
         uint32_t o[4];
@@ -592,7 +598,7 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     return o;
 }
 
-template <int FILTER, int MODE>
+template <int FILTER, int MODE, int LF>
 __global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(NeuralView N, NeuralDecodeArgs a, RoundKeys K, ShadeConst SC) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     DecodeSmem& S = *reinterpret_cast<DecodeSmem*>(smem_raw);
@@ -634,7 +640,7 @@ __global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(Neur
         }
         S.pair[t] = pr;
         S.wt[t] = w;
-        features_to_tile(N, N.latent_fmt, ix, iy, S.A, t);
+        features_to_tile<LF>(N, ix, iy, S.A, t);
         // ---- three GEMM layers
 #pragma unroll 1
         for (int layer = 0; layer < 3; ++layer) {
@@ -778,12 +784,16 @@ cudaError_t launch_ntc_quantize(const NeuralView& N, uint64_t lat_total, int fmt
 
 size_t ntc_decode_smem_bytes() { return sizeof(DecodeSmem) + 1024; }
 
+template <int FILTER, int MODE, int LF>
+static cudaError_t launch_dec_lf(const NeuralView& N, const NeuralDecodeArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = sizeof(DecodeSmem);
+    cudaFuncSetAttribute(k_ntc_decode_tc<FILTER, MODE, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ntc_decode_tc<FILTER, MODE, LF><<<grid, NT_ROWS, smem, st>>>(N, a, expand_key(a.seed), make_shade_const());
+    return cudaGetLastError();
+}
 template <int FILTER, int MODE>
 static cudaError_t launch_dec(const NeuralView& N, const NeuralDecodeArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = sizeof(DecodeSmem);
-    cudaFuncSetAttribute(k_ntc_decode_tc<FILTER, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ntc_decode_tc<FILTER, MODE><<<grid, NT_ROWS, smem, st>>>(N, a, expand_key(a.seed), make_shade_const());
-    return cudaGetLastError();
+    return N.latent_fmt == 0 ? launch_dec_lf<FILTER, MODE, 0>(N, a, grid, st) : launch_dec_lf<FILTER, MODE, 1>(N, a, grid, st);
 }
 
 cudaError_t launch_ntc_decode(const NeuralView& N, const NeuralDecodeArgs& a, int num_sms, cudaStream_t st) {
