@@ -374,6 +374,16 @@ def equal_rmse_2d(ctx, tex, u, v, d, dev, nsub=1 << 16):
             "s_star_below_8_allowed": s_any,
             "equal_rmse_speedup_below_8_allowed": (t_before / t_any) if t_any else None,
         }
+        if filt == "mitchell":
+            # positivization (Sec. 2.2): one texel from each sign set, two per sample
+            pos = {sp: rmse("positivized", sp) for sp in SPP_GRID}
+            s_pos, _ = _s_star(pos, r_before)
+            t_p8 = _time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "positivized", "ggx", 8, 1, 0, out=outf))
+            t_pos = (_time_launch(lambda: ctx.filter_shade(tex, u, v, d, filt, "positivized", "ggx", s_pos, 1, 0,
+                                                           out=outf)) if s_pos else None)
+            res[filt].update({"rmse_positivized": {str(k): v for k, v in pos.items()}, "ms_positivized_8spp": t_p8,
+                              "s_star_positivized": s_pos,
+                              "equal_rmse_speedup_positivized": (t_before / t_pos) if t_pos else None})
     return res
 
 
