@@ -904,6 +904,45 @@ def run_ntap(args):
     ctx.close()
 
 
+def run_lookup(args):
+    """One 2-D lookup configuration alone, for profiling the follow-on paths: --queries queries
+    on the 4096^2 material (--lformat rgba8 or dct6), --lfilter / --lmode / --lsampler / --lsigma,
+    --lspp samples; --lqueries picks the query set: the material workload's, the anisotropic
+    one (minor axis 1-8 texels, anisotropy up to 32) or 4x magnification at level 0."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    material = synth.material_rgba8(TEX_RES, 102)
+    if args.lformat == "dct6":
+        h = ctx.create_texture_dct(synth.dct_compress(material), TEX_RES, TEX_RES)
+    else:
+        h = ctx.create_texture(material.albedo_rough, material.normal)
+    if args.lqueries == "aniso":
+        q = synth.queries_aniso(args.queries, 44, res=TEX_RES, lod_range=3.0, max_aniso=32.0)
+    elif args.lqueries == "magnified":
+        q = synth.queries_uniform(args.queries, 45, const_derivs=(0.25 / TEX_RES, 0.0, 0.0, 0.25 / TEX_RES))
+    else:
+        q = make_queries(args.queries, 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    u, v, d = t(q.u), t(q.v), [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]
+    out = [torch.empty(args.queries, dtype=torch.float32, device=dev) for _ in range(3)]
+    go = lambda: ctx.filter_shade(h, u, v, d, args.lfilter, args.lmode, "ggx", args.lspp, 1, 0, out=out,
+                                  sampler=args.lsampler, sigma=args.lsigma)
+    for _ in range(args.warmup):
+        go()
+    torch.cuda.synchronize()
+    ms = _time_launch(go, reps=args.steps)
+    print(json.dumps({"metric": "shaded lookups/s", "value": args.queries * args.lspp / (ms / 1e3), "unit": "lookups/s",
+                      "ms_per_launch": ms,
+                      "config": {"workload": f"2-D lookup, {args.queries} {args.lqueries} queries, {args.lformat} 4096^2, "
+                                             f"{args.lfilter} {args.lsampler} {args.lmode}, {args.lspp} spp"}}), flush=True)
+    ctx.close()
+
+
 def run_triplanar(args):
     """Triplanar workload: --queries surface points on the 4096^2 material (or its DCT6 form)
     on all three planes, trilinear, 1 spp, --tmode / --tblend (single GPU)."""
@@ -952,7 +991,15 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1 << 13)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="material", choices=["material", "volume", "neural", "triplanar", "ntap"])
+    ap.add_argument("--workload", default="material",
+                    choices=["material", "volume", "neural", "triplanar", "ntap", "lookup"])
+    ap.add_argument("--lfilter", default="linear", choices=["linear", "bspline", "catmull_rom", "mitchell", "ewa", "gauss"])
+    ap.add_argument("--lmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after", "positivized"])
+    ap.add_argument("--lsampler", default="frs", choices=["frs", "fis"])
+    ap.add_argument("--lsigma", type=float, default=0.5)
+    ap.add_argument("--lspp", type=int, default=8)
+    ap.add_argument("--lformat", default="rgba8", choices=["rgba8", "dct6"])
+    ap.add_argument("--lqueries", default="material", choices=["material", "aniso", "magnified"])
     ap.add_argument("--tmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after"])
     ap.add_argument("--tblend", default="stochastic", choices=["stochastic", "full"])
     ap.add_argument("--tformat", default="rgba8", choices=["rgba8", "dct6"])
@@ -975,6 +1022,8 @@ def main():
         run_triplanar(args)
     elif args.workload == "ntap":
         run_ntap(args)
+    elif args.workload == "lookup":
+        run_lookup(args)
     else:
         run_ours(args)
 
