@@ -124,9 +124,9 @@ def cpu_baseline(material, seconds: float = 12.0) -> dict:
         for f in FILTERS:
             oracle.filter_shade(otex, q, f, "stochastic", "ggx", SPP, 1, nthreads=cores)
         dt = time.perf_counter() - t0
-        if dt > seconds / 4 or n >= (1 << 22):
+        if dt > seconds / 2 or n >= (1 << 24):
             break
-        n = min(1 << 22, int(n * max(2.0, seconds / 4 / max(dt, 1e-3))))
+        n = min(1 << 24, int(n * max(2.0, seconds / 2 / max(dt, 1e-3))))
         n = 1 << int(math.log2(n))
     units = n * SPP * len(FILTERS)
     return {"value": units / dt, "unit": "lookups/s", "cores": cores, "kind": "oracle",
