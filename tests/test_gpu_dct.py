@@ -46,7 +46,8 @@ def _run(ctx, h, q, filter, mode, spp, seed=1, flags=0, picks=True):
     return rgb, (pk.cpu().numpy().view(np.uint32) if pk is not None else None)
 
 
-@pytest.mark.parametrize("filter,mode,spp", [("linear", "stochastic", 4), ("linear", "ntap_before", 1),
+@pytest.mark.parametrize("filter,mode,spp", [("linear", "stochastic", 4), ("linear", "stochastic", 1),
+                                             ("mitchell", "stochastic", 1), ("linear", "ntap_before", 1),
                                              ("linear", "ntap_after", 1), ("bspline", "stochastic", 3),
                                              ("mitchell", "positivized", 2), ("ewa", "stochastic", 2),
                                              ("ewa", "ntap_before", 1)])
