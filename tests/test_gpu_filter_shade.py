@@ -188,7 +188,7 @@ def test_host_entry_point_chunked(ctx, material, filter, flags):
     # its lanes, the last one ragged; query ids stay global, so every result and pick equals
     # the one-launch device path bit for bit
     h, _, _ = material
-    q = synth.queries_uniform(1_500_001, 23, res=256, lod_range=5.0)
+    q = synth.queries_uniform(4_500_001, 23, res=256, lod_range=5.0)   # three chunks of <= 2^21
     dev, pk = _run(ctx, h, q, filter, "stochastic", 8, seed=4, flags=flags, id_base=77)
     f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     r, g, b, pk2 = ctx.filter_shade_host(h, f(q.u), f(q.v), [f(q.dudx), f(q.dvdx), f(q.dudy), f(q.dvdy)],
