@@ -10,7 +10,7 @@ lobes): 3 x 2^24 x 8 shaded lookups.  Inputs (384 MiB of queries, 171 MiB of tex
 larger than L2, so no flush is needed between steps.
 
 value   = shaded lookups/s over all ranks (kernel time, inputs resident in HBM)
-e2e     = the same step through stf_filter_shade_host from pinned host buffers
+e2e     = the same step through stf_filter_shade_host_async from pinned host buffers
 equal_rmse / volume = N-tap comparators and the equal-RMSE speedups (rank 0, N = 1)
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 """
@@ -192,14 +192,16 @@ def run_ours(args):
     value = world * units_step * args.steps / (ms_total / 1e3)
     clocks = clk.summary()
 
-    # ---- end to end: pinned host buffers through stf_filter_shade_host
+    # ---- end to end: pinned host buffers through stf_filter_shade_host_async, one call per
+    # filter queued back to back on the copy pipeline, and one synchronize per step
     hq = [torch.from_numpy(a).pin_memory() for a in (q.u, q.v, q.dudx, q.dvdx, q.dudy, q.dvdy)]
-    hout = [torch.empty(nq, dtype=torch.float32).pin_memory() for _ in range(3)]
+    hout = {f: [torch.empty(nq, dtype=torch.float32).pin_memory() for _ in range(3)] for f in FILTERS}
 
     def e2e_step():
         for f in FILTERS:
-            ctx.filter_shade_host(tex, hq[0], hq[1], hq[2:], f, "stochastic", "ggx", SPP, 1, 0,
-                                  id_base=id_base, out=hout)
+            ctx.filter_shade_host_async(tex, hq[0], hq[1], hq[2:], f, "stochastic", "ggx", SPP, 1, 0,
+                                        id_base=id_base, out=hout[f])
+        ctx.synchronize()
     e2e_step()
     torch.cuda.synchronize()
     ke = max(2, min(args.steps, 5))

@@ -188,8 +188,8 @@ stf_status stf_create(int device, void* cuda_stream, stf_ctx* out);
 stf_status stf_destroy(stf_ctx ctx);
 stf_status stf_set_stream(stf_ctx ctx, void* cuda_stream);
 stf_status stf_synchronize(stf_ctx ctx);
-/* Reads and clears the device status word (synchronises the stream).  Returns
- * STF_ERR_DEVICE_STATUS if any bit was set. */
+/* Reads and clears the device status word (synchronises the stream and the host-buffer
+ * pipeline).  Returns STF_ERR_DEVICE_STATUS if any bit was set. */
 stf_status stf_get_device_status(stf_ctx ctx, uint32_t* flags);
 const char* stf_status_string(stf_status s);
 const char* stf_last_error(stf_ctx ctx);
@@ -221,6 +221,16 @@ stf_status stf_filter_shade_ex(stf_ctx ctx, stf_tex tex, const stf_queries* q, c
 stf_status stf_filter_shade_host(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
                                  stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                                  uint64_t seed, uint32_t flags, const stf_output* out);
+/* stf_filter_shade_host without the final wait: the copies and launches are queued on the
+ * library's copy-pipeline streams and the call returns.  Consecutive calls keep the pipeline
+ * full (the next call's first copies overlap the previous call's last ones).  The host query
+ * buffers must stay unchanged, and the results are valid, only after stf_synchronize (which
+ * waits for these streams as well as the context's stream).  stf_get_device_status,
+ * stf_destroy_texture and stf_destroy also wait for them.  The call still validates its
+ * arguments synchronously; a failure while queueing waits for the pipeline and is returned. */
+stf_status stf_filter_shade_host_async(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
+                                       stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
+                                       uint64_t seed, uint32_t flags, const stf_output* out);
 
 /* ---- bindless texture table: many textures in one persistent launch ------------------ */
 typedef uint64_t stf_table;

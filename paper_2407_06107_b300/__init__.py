@@ -102,6 +102,8 @@ SIGNATURES = {
                              _U32, _U64, _U32, C.POINTER(_Output)], _I),
     "stf_filter_shade_host": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
                                _U64, _U32, C.POINTER(_Output)], _I),
+    "stf_filter_shade_host_async": ([_P, _U64, C.POINTER(_Queries), C.POINTER(_Derivs), _I, _I, _I, _U32,
+                                     _U64, _U32, C.POINTER(_Output)], _I),
     "stf_bin_queries": ([_P, _U64, _P, _P, _P, _U32, _U32, _P], _I),
     "stf_create_texture_table": ([_P, _U32, _P, C.POINTER(_U64)], _I),
     "stf_destroy_texture_table": ([_P, _U64], _I),
@@ -313,6 +315,21 @@ class Context:
                                          FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags, C.byref(o))
         self._check(st, self.h)
         return out[0], out[1], out[2], picks
+
+    def filter_shade_host_async(self, tex: int, u, v, derivs=None, filter: str = "bspline",
+                                mode: str = "stochastic", shade: str = "ggx", spp: int = 1, seed: int = 1,
+                                flags: int = 0, id_base: int = 0, out=None):
+        """filter_shade_host without the final wait: the results (and the inputs' release) are
+        valid after synchronize().  The arrays passed or returned must stay alive until then."""
+        n = int(u.shape[0])
+        if out is None:
+            out = [np.empty(n, dtype=np.float32) for _ in range(3)]
+        q, d, o = self._args(u, v, derivs, out, None, n, id_base)
+        st = lib().stf_filter_shade_host_async(self.h, tex, C.byref(q), C.byref(d) if d is not None else None,
+                                               FILTERS[filter], MODES[mode], SHADES[shade], spp, seed, flags,
+                                               C.byref(o))
+        self._check(st, self.h)
+        return out[0], out[1], out[2]
 
     def bin_queries(self, u, v, tex_id=None, ntex: int = 1, tile_log2: int = 6, order=None):
         """Spatial execution order (int32 cuda tensor [n]) for filter_shade(order=...)."""

@@ -47,9 +47,19 @@ int square_side(uint32_t spp) {
 uint32_t level_dim(uint32_t d, uint32_t l) { uint32_t x = d >> l; return x ? x : 1u; }
 
 
+// Waits for the copy-pipeline lanes (asynchronous host-buffer calls may still use them).
+void drain_lanes(stf_ctx c) {
+    for (int i = 0; i < STF_LANES; ++i)
+        if (c->lane[i]) cudaStreamSynchronize(c->lane[i]);
+}
+
 stf_status ensure_stage(stf_ctx c, size_t bytes) {
     if (c->stage_bytes >= bytes) return STF_OK;
-    if (c->stage) { cudaStreamSynchronize(c->stream); cudaFree(c->stage); c->stage = nullptr; c->stage_bytes = 0; }
+    if (c->stage) {
+        cudaStreamSynchronize(c->stream);
+        drain_lanes(c);
+        cudaFree(c->stage); c->stage = nullptr; c->stage_bytes = 0;
+    }
     stf_status s = dev_alloc(c, &c->stage, bytes);
     if (s == STF_OK) c->stage_bytes = bytes;
     return s;
@@ -156,6 +166,7 @@ stf_status stf_destroy(stf_ctx c) {
     if (!c) return STF_ERR_INVALID_ARG;
     CurrentDevice cd(c->device);
     cudaStreamSynchronize(c->stream);
+    drain_lanes(c);
     for (auto& kv : c->tex) cudaFree(kv.second.mem);
     for (auto& kv : c->vol) cudaFree(kv.second.mem);
     for (auto& kv : c->tables) cudaFree(kv.second.mem);
@@ -181,12 +192,15 @@ stf_status stf_synchronize(stf_ctx c) {
     if (!c) return STF_ERR_INVALID_ARG;
     CurrentDevice cd(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < STF_LANES && e == cudaSuccess; ++i)
+        if (c->lane[i]) e = cudaStreamSynchronize(c->lane[i]);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "cudaStreamSynchronize");
 }
 
 stf_status stf_get_device_status(stf_ctx c, uint32_t* flags) {
     if (!c || !flags) return STF_ERR_INVALID_ARG;
     CurrentDevice cd(c->device);
+    drain_lanes(c);      // kernels of asynchronous host-buffer calls report here too
     uint32_t h = 0;
     cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream);
@@ -314,6 +328,7 @@ stf_status stf_destroy_texture(stf_ctx c, stf_tex t) {
             if (m == t) return fail(c, STF_ERR_INVALID_ARG, "texture is referenced by a texture table");
     CurrentDevice cd(c->device);
     cudaStreamSynchronize(c->stream);
+    drain_lanes(c);
     cudaFree(it->second.mem);
     c->tex.erase(it);
     return STF_OK;
@@ -457,9 +472,9 @@ static stf_status ensure_lanes(stf_ctx c) {
     return STF_OK;
 }
 
-stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
-                                 stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
-                                 uint32_t flags, const stf_output* out) {
+static stf_status host_pipeline(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d, stf_filter f,
+                                stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed, uint32_t flags,
+                                const stf_output* out, bool async) {
     TexRec* rec = nullptr;
     stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, &rec);
     if (s != STF_OK || q->n == 0) return s;
@@ -514,12 +529,26 @@ stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, con
             e = cudaMemcpyAsync(out->picks + off * spp * 2, dpk, cn * spp * 8, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) first = cuda_fail(c, e, "device->host copy");
     }
-    // every lane drains before returning (also after an error: staging stays in use until then)
+    // every lane drains before returning (also after an error: staging stays in use until
+    // then); an asynchronous call leaves them running, and the next call's chunks queue behind
+    if (async && first == STF_OK) return STF_OK;
     for (int i = 0; i < lanes; ++i) {
         cudaError_t ei = cudaStreamSynchronize(c->lane[i]);
         if (ei != cudaSuccess && first == STF_OK) first = cuda_fail(c, ei, "lane synchronise");
     }
     return first;
+}
+
+stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
+                                 stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                                 uint32_t flags, const stf_output* out) {
+    return host_pipeline(c, t, q, d, f, m, sh, spp, seed, flags, out, false);
+}
+
+stf_status stf_filter_shade_host_async(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
+                                       stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
+                                       uint32_t flags, const stf_output* out) {
+    return host_pipeline(c, t, q, d, f, m, sh, spp, seed, flags, out, true);
 }
 
 // ---------------------------------------------------------------------------- texture table

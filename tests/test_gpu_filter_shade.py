@@ -281,3 +281,20 @@ def test_one_sample_pairs_ragged(ctx, material, n):
     with_picks, _ = _run(ctx, h, qs, "bspline", "stochastic", 1, seed=9, picks=True)
     special, _ = _run(ctx, h, qs, "bspline", "stochastic", 1, seed=9, picks=False)
     assert np.array_equal(with_picks, special)
+
+
+def test_host_entry_point_async(ctx, material):
+    # asynchronous host-buffer calls queue behind one another on the copy pipeline; after
+    # synchronize() every result equals the one-launch device path bit for bit
+    h, _, _ = material
+    q = synth.queries_uniform(2_500_001, 24, res=256, lod_range=5.0)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hu, hv, hd = f(q.u), f(q.v), [f(q.dudx), f(q.dvdx), f(q.dudy), f(q.dvdy)]
+    outs = {}
+    for filt in ("linear", "bspline", "mitchell"):
+        outs[filt] = [torch.empty(q.n, dtype=torch.float32).pin_memory() for _ in range(3)]
+        ctx.filter_shade_host_async(h, hu, hv, hd, filt, "stochastic", "ggx", 8, 5, out=outs[filt])
+    ctx.synchronize()
+    for filt in ("linear", "bspline", "mitchell"):
+        dev, _ = _run(ctx, h, q, filt, "stochastic", 8, seed=5, picks=False)
+        assert np.array_equal(torch.stack(outs[filt], 1).numpy().astype(np.float64), dev)
