@@ -188,6 +188,19 @@ int weights32(int f, float t, float w[4]) {
     return 4;
 }
 
+// FP32 weights for a pick, where only their ratios matter: the B-spline's polynomials without
+// the common factor 1/6, in the same operation order (the CDF inversion divides the factor out,
+// and a positive filter's estimate carries weight 1); the other filters' weights32.
+int pick_weights32(int f, float t, float w[4]) {
+    if (f != F_BSPLINE) return weights32(f, t, w);
+    const float t2 = t * t, omt = 1.0f - t;
+    w[0] = (omt * omt) * omt;
+    w[1] = std::fmaf(t2, std::fmaf(3.0f, t, -6.0f), 4.0f);
+    w[2] = std::fmaf(t, std::fmaf(t, std::fmaf(-3.0f, t, 3.0f), 3.0f), 1.0f);
+    w[3] = t2 * t;
+    return 4;
+}
+
 // CDF inversion ("Sampling arrays"): first k with xi * S < prefix_k, S = sum |w|,
 // restricted to taps of a sign class (cls = 0 all, +1 w > 0, -1 w < 0).
 int pick32(const float* w, int n, float xi, int cls, float* total) {
@@ -901,8 +914,8 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
             int W = T.width[lvl], H = T.height[lvl];
             Axis ax = axis_at(x, W), ay = axis_at(y, H);
             float wx[4], wy[4];
-            weights32(filter, ax.t, wx);
-            weights32(filter, ay.t, wy);
+            pick_weights32(filter, ax.t, wx);
+            pick_weights32(filter, ay.t, wy);
             double wx64[4], wy64[4];
             for (int k = 0; k < nt; ++k) {
                 wx64[k] = kernel64(filter, ax.pos - (double)(ax.i0 + ft + k));
@@ -1281,7 +1294,7 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
             for (int a = 0; a < 3; ++a) {
                 float w[4];
                 double w64[4];
-                weights32(filter, ax[a].t, w);
+                pick_weights32(filter, ax[a].t, w);
                 for (int j = 0; j < nt; ++j) w64[j] = kernel64(filter, ax[a].pos - (double)(ax[a].i0 + ft + j));
                 float xi = uk[a];
                 if (flags & FLAG_REUSE) {

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                     for (int c = 0; c < 3; ++c) {
                         const AxisPos ap = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
                         float w[4];
-                        axis_weights<FILTER>(ap.t, w);
+                        axis_pick_weights<FILTER>(ap.t, w);
                         const int n = c == 0 ? a.nx : (c == 1 ? a.ny : a.nz);
                         idx[c] = clamp_index(ap.i0 + T0 + cdf_pick<NT>(w, uk[c], 0, nullptr), n);
                     }
@@ -141,7 +141,10 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                 for (int c = 0; c < 3; ++c) ap[c] = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
                 float w[3][4];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) axis_weights<FILTER>(ap[c].t, w[c]);
+                for (int c = 0; c < 3; ++c) {
+                    if constexpr (MODE == M_STOCHASTIC) axis_pick_weights<FILTER>(ap[c].t, w[c]);
+                    else axis_weights<FILTER>(ap[c].t, w[c]);
+                }
                 if (MODE == M_STOCHASTIC) {
                     // steps 2p and 2p+1 share stream p+1 (six 21-bit uniforms)
                     float uk[3];

@@ -559,8 +559,13 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     const int R = a.tex_res;
     const AxisPos ax = axis_pos(x, (float)R), ay = axis_pos(y, (float)R);
     float wx[4], wy[4];
-    axis_weights<FILTER>(ax.t, wx);
-    axis_weights<FILTER>(ay.t, wy);
+    if constexpr (MODE == M_STOCHASTIC) {
+        axis_pick_weights<FILTER>(ax.t, wx);
+        axis_pick_weights<FILTER>(ay.t, wy);
+    } else {
+        axis_weights<FILTER>(ax.t, wx);
+        axis_weights<FILTER>(ay.t, wy);
+    }
     o.query = (long long)q;
     if (MODE == M_STOCHASTIC) {
         float Sx, Sy;

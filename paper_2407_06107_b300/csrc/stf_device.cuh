@@ -178,6 +178,23 @@ __device__ __forceinline__ void axis_weights(float t, float w[4]) {
     }
 }
 
+// Weights for a pick, where only their ratios matter: the B-spline's polynomials without the
+// common factor 1/6 (the CDF pick divides it out; the estimate's weight is 1 for a positive
+// filter), the other filters' weights as axis_weights gives them.
+template <int F>
+__device__ __forceinline__ void axis_pick_weights(float t, float w[4]) {
+    if constexpr (F == F_BSPLINE) {
+        const float t2 = __fmul_rn(t, t);
+        const float omt = __fsub_rn(1.0f, t);
+        w[0] = __fmul_rn(__fmul_rn(omt, omt), omt);
+        w[1] = __fmaf_rn(t2, __fmaf_rn(3.0f, t, -6.0f), 4.0f);
+        w[2] = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-3.0f, t, 3.0f), 3.0f), 1.0f);
+        w[3] = __fmul_rn(t2, t);
+    } else {
+        axis_weights<F>(t, w);
+    }
+}
+
 // CDF inversion over one axis: first k with xi*S < prefix_k, S = sum of |w| over the
 // taps of sign class CLS (0: all, +1: w > 0, -1: w < 0).  Returns the tap index.
 template <int N>

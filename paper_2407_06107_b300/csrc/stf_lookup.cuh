@@ -126,8 +126,8 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
     const int W = T.w[lvl], H = T.h[lvl];
     const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
     float wx[4], wy[4];
-    axis_weights<FILTER>(ax.t, wx);
-    axis_weights<FILTER>(ay.t, wy);
+    axis_pick_weights<FILTER>(ax.t, wx);
+    axis_pick_weights<FILTER>(ay.t, wy);
     float Sx, Sy;
     int kx, ky;
     bool nx = false, ny = false;     // sign of the picked weight per axis
