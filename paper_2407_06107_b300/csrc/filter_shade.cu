@@ -693,7 +693,8 @@ ShadeConst make_shade_const() {
     const double hl = std::sqrt(hx * hx + hy * hy + hz * hz);
     C.h = make_float3((float)(hx / hl), (float)(hy / hl), (float)(hz / hl));
     const double vh = (-0.28 * hx + 0.96 * hz) / hl, m = 1.0 - vh;
-    C.F = (float)(0.04 + 0.96 * m * m * m * m * m);
+    const double F = 0.04 + 0.96 * m * m * m * m * m;
+    C.Fk = (float)(F / (2.0 * 3.14159265358979323846));   // D G F / 4 = a2/(pi q^2) * 2/(...) * F / 4
     return C;
 }
 

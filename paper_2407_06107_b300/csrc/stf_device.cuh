@@ -283,7 +283,7 @@ struct Material { float3 rho; float rough; float3 n; };
 // F(v.h) and 1/pi.  The half vector is FP32-rounded normalize(l+v).
 struct ShadeConst {
     float3 l, v, h;
-    float F;   // Schlick Fresnel at v.h with F0 = 0.04
+    float Fk;   // F / (2 pi): Schlick Fresnel at v.h (F0 = 0.04) with the constant factors of D G F / 4
 };
 
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
@@ -316,16 +316,13 @@ __device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst&
     // so the cancellation of 1 - (n.h)^2 near n = h would show in D
     const float q = fmaf(a2 * nh, nh, dot3(nxh, nxh));
     const float rq = rcp_approx(q), rnl = rcp_approx(nl), rnv = rcp_approx(nv);
-    const float D = a2 * 0.318309886183790672f * rq * rq;
-    // Lambda = (sqrt(1 + a2 tan^2) - 1) / 2 with sin^2 = 1 - (n.w)^2 (|n| = 1): G2 =
-    // 1 / (1 + Ll + Lv) only sees absolute errors of Lambda, which the two subtractions
-    // keep at a few ulp of 1
+    // D = a2 / (pi q^2).  Lambda = (sqrt(1 + a2 tan^2) - 1) / 2 with sin^2 = 1 - (n.w)^2
+    // (|n| = 1), so G2 = 1 / (1 + Ll + Lv) = 2 / (sqrt(sl) + sqrt(sv)): a sum of two positive
+    // roots, one reciprocal, no cancellation.  The constants 1/pi, 2 and 1/4 sit in C.Fk.
     const float xl = a2 * fmaf(-nl, nl, 1.0f) * rnl * rnl, xv = a2 * fmaf(-nv, nv, 1.0f) * rnv * rnv;
     const float sl = 1.0f + xl, sv = 1.0f + xv;
-    const float Ll = 0.5f * fmaf(sl, rsqrt_approx(sl), -1.0f);
-    const float Lv = 0.5f * fmaf(sv, rsqrt_approx(sv), -1.0f);
-    const float G = rcp_approx(1.0f + Ll + Lv);
-    const float spec = D * G * C.F * 0.25f * rnv;
+    const float rg = rcp_approx(fmaf(sl, rsqrt_approx(sl), sv * rsqrt_approx(sv)));
+    const float spec = a2 * rq * rq * rg * C.Fk * rnv;
     const float kd = nl * 0.318309886183790672f;
     return make_float3(fmaf(m.rho.x, kd, spec), fmaf(m.rho.y, kd, spec), fmaf(m.rho.z, kd, spec));
 }
