@@ -186,6 +186,8 @@ typedef struct {
 /* device: CUDA ordinal; cuda_stream: cudaStream_t or NULL for the legacy default stream. */
 stf_status stf_create(int device, void* cuda_stream, stf_ctx* out);
 stf_status stf_destroy(stf_ctx ctx);
+/* Later calls queue on cuda_stream.  Synchronises the previous stream first: the context's
+ * scratch (binning histogram, device status word) is then never in use on two streams. */
 stf_status stf_set_stream(stf_ctx ctx, void* cuda_stream);
 stf_status stf_synchronize(stf_ctx ctx);
 /* Reads and clears the device status word (synchronises the stream and the host-buffer
@@ -226,8 +228,11 @@ stf_status stf_filter_shade_host(stf_ctx ctx, stf_tex tex, const stf_queries* q,
  * full (the next call's first copies overlap the previous call's last ones).  The host query
  * buffers must stay unchanged, and the results are valid, only after stf_synchronize (which
  * waits for these streams as well as the context's stream).  stf_get_device_status,
- * stf_destroy_texture and stf_destroy also wait for them.  The call still validates its
- * arguments synchronously; a failure while queueing waits for the pipeline and is returned. */
+ * stf_destroy_texture and stf_destroy also wait for them.  Calls of any sizes may follow
+ * one another: a call whose staging layout differs from the previous call's waits, on the
+ * GPU and not on the host, for all earlier pipeline work before it reuses the staging.  The
+ * call still validates its arguments synchronously; a failure while queueing waits for the
+ * pipeline and is returned. */
 stf_status stf_filter_shade_host_async(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
                                        stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                                        uint64_t seed, uint32_t flags, const stf_output* out);
@@ -299,7 +304,10 @@ stf_status stf_triplanar_shade(stf_ctx ctx, const stf_tex tex[3], float scale, c
 /* Counting sort of the n queries by bin = (tex_id[i], tile of (frac(u), frac(v)) on a
  * 2^tile_log2 x 2^tile_log2 grid): order_out[n] (device uint32) lists the queries bin by
  * bin.  tex_id nullable (one texture); ntex = number of texture ids (1 if tex_id is NULL);
- * ntex * 4^tile_log2 <= 2^26, n < 2^32.  Uses context-owned scratch for the histogram. */
+ * ntex * 4^tile_log2 <= 2^26, n < 2^32.  Uses context-owned scratch for the histogram
+ * (grown on demand, which synchronises the context stream; separate from the host-buffer
+ * pipeline's staging, so it may overlap asynchronous host-buffer calls).  The order within
+ * a bin is not deterministic. */
 stf_status stf_bin_queries(stf_ctx ctx, uint64_t n, const float* u, const float* v, const uint32_t* tex_id,
                            uint32_t ntex, uint32_t tile_log2, uint32_t* order_out);
 

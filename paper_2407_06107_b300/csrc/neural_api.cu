@@ -222,20 +222,23 @@ static stf_status neural_copy(stf_ctx c, stf_neural h, int what, void* host, siz
         return fail(c, STF_ERR_UNSUPPORTED, "scales are derived by stf_neural_quantize");
     }
     struct Part { void* dev; size_t bytes; };
-    std::vector<Part> parts;
+    Part parts[4] = {};
+    int np = 1;
     switch (what) {
-        case STF_NEURAL_LATENTS: parts = {{r->view.lat32, r->lat_total * 4}}; break;
-        case STF_NEURAL_GRAD_LATENTS: parts = {{r->view.dlat, r->lat_total * 4}}; break;
-        case STF_NEURAL_MLP: parts = {{r->view.mlp32, MLP_N * 4}}; break;
-        case STF_NEURAL_GRAD_MLP: parts = {{r->view.grad32, MLP_N * 4}}; break;
+        case STF_NEURAL_LATENTS: parts[0] = {r->view.lat32, r->lat_total * 4}; break;
+        case STF_NEURAL_GRAD_LATENTS: parts[0] = {r->view.dlat, r->lat_total * 4}; break;
+        case STF_NEURAL_MLP: parts[0] = {r->view.mlp32, MLP_N * 4}; break;
+        case STF_NEURAL_GRAD_MLP: parts[0] = {r->view.grad32, MLP_N * 4}; break;
         case STF_NEURAL_ADAM:
-            parts = {{r->m_lat, r->lat_total * 4}, {r->v_lat, r->lat_total * 4}, {r->m_mlp, MLP_N * 4}, {r->v_mlp, MLP_N * 4}};
+            parts[0] = {r->m_lat, r->lat_total * 4}; parts[1] = {r->v_lat, r->lat_total * 4};
+            parts[2] = {r->m_mlp, MLP_N * 4}; parts[3] = {r->v_mlp, MLP_N * 4};
+            np = 4;
             break;
     }
     char* hp = (char*)host;
     cudaError_t e = cudaSuccess;
-    for (const Part& p : parts) {
-        if (e != cudaSuccess) break;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+        const Part& p = parts[i];
         e = to_host ? cudaMemcpyAsync(hp, p.dev, p.bytes, cudaMemcpyDeviceToHost, c->stream)
                     : cudaMemcpyAsync(p.dev, hp, p.bytes, cudaMemcpyHostToDevice, c->stream);
         hp += p.bytes;

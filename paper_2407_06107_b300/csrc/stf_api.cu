@@ -53,15 +53,27 @@ void drain_lanes(stf_ctx c) {
         if (c->lane[i]) cudaStreamSynchronize(c->lane[i]);
 }
 
+// Staging of the host-buffer pipeline; only the lanes touch it.
 stf_status ensure_stage(stf_ctx c, size_t bytes) {
     if (c->stage_bytes >= bytes) return STF_OK;
     if (c->stage) {
-        cudaStreamSynchronize(c->stream);
         drain_lanes(c);
-        cudaFree(c->stage); c->stage = nullptr; c->stage_bytes = 0;
+        cudaFree(c->stage); c->stage = nullptr; c->stage_bytes = 0; c->lane_bytes = 0;
     }
     stf_status s = dev_alloc(c, &c->stage, bytes);
     if (s == STF_OK) c->stage_bytes = bytes;
+    return s;
+}
+
+// Histogram scratch of the binning call; only the context stream touches it.
+stf_status ensure_bin_scratch(stf_ctx c, size_t bytes) {
+    if (c->bin_scratch_bytes >= bytes) return STF_OK;
+    if (c->bin_scratch) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->bin_scratch); c->bin_scratch = nullptr; c->bin_scratch_bytes = 0;
+    }
+    stf_status s = dev_alloc(c, &c->bin_scratch, bytes);
+    if (s == STF_OK) c->bin_scratch_bytes = bytes;
     return s;
 }
 
@@ -174,8 +186,11 @@ stf_status stf_destroy(stf_ctx c) {
     for (int i = 0; i < STF_LANES; ++i) {
         if (c->lane[i]) { cudaStreamSynchronize(c->lane[i]); cudaStreamDestroy(c->lane[i]); }
     }
+    for (int i = 0; i < STF_LANES; ++i)
+        if (c->lane_ev[i]) cudaEventDestroy(c->lane_ev[i]);
     if (c->entry_ev) cudaEventDestroy(c->entry_ev);
     if (c->stage) cudaFree(c->stage);
+    if (c->bin_scratch) cudaFree(c->bin_scratch);
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_ewa_lut) cudaFree(c->d_ewa_lut);
     delete c;
@@ -184,8 +199,12 @@ stf_status stf_destroy(stf_ctx c) {
 
 stf_status stf_set_stream(stf_ctx c, void* stream) {
     if (!c) return STF_ERR_INVALID_ARG;
+    // the binning scratch and the status word are context-owned: work queued on the old
+    // stream finishes before work on the new one can reuse them
+    CurrentDevice cd(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
     c->stream = (cudaStream_t)stream;
-    return STF_OK;
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "cudaStreamSynchronize");
 }
 
 stf_status stf_synchronize(stf_ctx c) {
@@ -465,8 +484,11 @@ static stf_status ensure_lanes(stf_ctx c) {
         cudaError_t e = cudaStreamCreateWithFlags(&c->lane[i], cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(c, e, "lane stream creation");
     }
-    if (!c->entry_ev) {
-        cudaError_t e = cudaEventCreateWithFlags(&c->entry_ev, cudaEventDisableTiming);
+    cudaEvent_t* evs[STF_LANES + 1] = {&c->entry_ev};
+    for (int i = 0; i < STF_LANES; ++i) evs[i + 1] = &c->lane_ev[i];
+    for (cudaEvent_t* ev : evs) {
+        if (*ev) continue;
+        cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(c, e, "event creation");
     }
     return STF_OK;
@@ -500,7 +522,16 @@ static stf_status host_pipeline(stf_ctx c, stf_tex t, const stf_queries* q, cons
     if (s != STF_OK) return s;
     cudaError_t e = cudaEventRecord(c->entry_ev, c->stream);   // earlier work on the caller's stream
     for (int i = 0; i < lanes && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->lane[i], c->entry_ev, 0);
+    // Lane i stages in [i * lane_b, (i + 1) * lane_b).  Calls with the same layout reuse each
+    // region on the same lane, so stream order protects it.  A new layout moves the regions
+    // across the old ones: every lane (used by this call or not, so that later calls with
+    // this layout inherit the order) then also waits for the other lanes' earlier work.
+    if (c->lane_bytes != 0 && c->lane_bytes != lane_b)
+        for (int i = 0; i < STF_LANES && e == cudaSuccess; ++i)
+            for (int j = 0; j < STF_LANES && e == cudaSuccess; ++j)
+                if (j != i) e = cudaStreamWaitEvent(c->lane[i], c->lane_ev[j], 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream ordering");
+    c->lane_bytes = lane_b;
     const float* hv[6] = {q->u, q->v, d ? d->dudx : nullptr, d ? d->dvdx : nullptr, d ? d->dudy : nullptr, d ? d->dvdy : nullptr};
     float* ho[3] = {out->r, out->g, out->b};
     stf_status first = STF_OK;
@@ -531,6 +562,10 @@ static stf_status host_pipeline(stf_ctx c, stf_tex t, const stf_queries* q, cons
     }
     // every lane drains before returning (also after an error: staging stays in use until
     // then); an asynchronous call leaves them running, and the next call's chunks queue behind
+    for (int i = 0; i < lanes && e == cudaSuccess && first == STF_OK; ++i) {
+        e = cudaEventRecord(c->lane_ev[i], c->lane[i]);
+        if (e != cudaSuccess) first = cuda_fail(c, e, "lane event");
+    }
     if (async && first == STF_OK) return STF_OK;
     for (int i = 0; i < lanes; ++i) {
         cudaError_t ei = cudaStreamSynchronize(c->lane[i]);
@@ -639,9 +674,9 @@ stf_status stf_bin_queries(stf_ctx c, uint64_t n, const float* u, const float* v
     CurrentDevice cd(c->device);
     const uint64_t nbins = (uint64_t)ntex << (2 * tile_log2);
     const uint64_t nblk = (nbins + 1023) / 1024;
-    stf_status s = ensure_stage(c, (nblk * 1024 + nblk) * 4);
+    stf_status s = ensure_bin_scratch(c, (nblk * 1024 + nblk) * 4);
     if (s != STF_OK) return s;
-    cudaError_t e = stf::launch_bin_queries(n, u, v, tex_id, ntex, tile_log2, order_out, (uint32_t*)c->stage, nbins,
+    cudaError_t e = stf::launch_bin_queries(n, u, v, tex_id, ntex, tile_log2, order_out, (uint32_t*)c->bin_scratch, nbins,
                                             c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "bin launch");
 }

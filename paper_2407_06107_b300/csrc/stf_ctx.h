@@ -51,10 +51,14 @@ struct stf_ctx_s {
     std::unordered_map<uint64_t, VolRec> vol;
     std::unordered_map<uint64_t, NeuralRec> neural;
     std::unordered_map<uint64_t, TableRec> tables;
-    void* stage = nullptr;          // device staging for the host-buffer entry points
+    void* stage = nullptr;          // device staging for the host-buffer entry points (lanes only)
     size_t stage_bytes = 0;
+    void* bin_scratch = nullptr;    // histogram scratch of stf_bin_queries (context stream only)
+    size_t bin_scratch_bytes = 0;
     cudaStream_t lane[STF_LANES] = {};   // copy-pipeline streams of the host-buffer path
     cudaEvent_t entry_ev = nullptr;      // orders the lanes after the caller's stream
+    cudaEvent_t lane_ev[STF_LANES] = {}; // end of each lane's work in the latest host-buffer call
+    size_t lane_bytes = 0;               // staging bytes per lane in the latest host-buffer call
     int fault = 0;                  // host-side fault injection (STF_FAULT), 0 = off
 };
 
