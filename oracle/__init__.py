@@ -484,8 +484,11 @@ def ntc_decode(nt: NeuralTexture, ix, iy):
     return y, rd
 
 
-def ntc_loss_grad(tex_res: int, lat32, mlp32, targets, ix, iy, round_bf16: bool = True):
-    """Loss and gradients of one batch from FP32 master parameters."""
+def ntc_loss_grad(tex_res: int, lat32, mlp32, targets, ix, iy, round_bf16: bool = True,
+                  bf16_backward: bool = False):
+    """Loss and gradients of one batch from FP32 master parameters.  round_bf16: BF16
+    operands in the forward GEMMs; bf16_backward (with round_bf16): also the backward GEMMs'
+    operands dy, dh2 and dh1 rounded to BF16 where they are formed."""
     nt = NeuralTexture(tex_res, [np.asarray(g, np.float32) for g in lat32], np.zeros(6792), "fp32")
     s = nt._struct()
     m = np.ascontiguousarray(mlp32, dtype=np.float32)
@@ -498,7 +501,7 @@ def ntc_loss_grad(tex_res: int, lat32, mlp32, targets, ix, iy, round_bf16: bool 
     iy = np.ascontiguousarray(iy, dtype=np.int32)
     tg = np.ascontiguousarray(targets, dtype=np.uint8)
     loss = lib().orc_ntc_loss_grad(C.byref(s), *[_p(p) for p in parts], _p(tg), len(ix), _p(ix), _p(iy),
-                                   1 if round_bf16 else 0, *[_p(g) for g in grads], dlp)
+                                   (2 if bf16_backward else 1) if round_bf16 else 0, *[_p(g) for g in grads], dlp)
     return loss, np.concatenate(grads), np.concatenate(dl)
 
 

@@ -167,9 +167,14 @@ void orc_ntc_decode(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, cons
 }
 
 // Loss and gradients of one training batch.  Latents are FP32 master values (latent_fmt
-// 2); the MLP's FP32 master weights are rounded to BF16 for the forward pass when
-// round_bf16 != 0 (the backward treats every rounding as identity).  targets:
-// tex_res^2 x 8 bytes.  Gradients are ACCUMULATED into the double arrays.
+// 2).  round_bf16 selects where BF16 operands stand in for exact values:
+//   0: nowhere (exact FP64 forward and backward);
+//   1: the forward GEMMs' operands (features, FP32 master weights, hidden activations);
+//   2: as 1, and also the backward GEMMs' operands dy, dh2 (.) [h2 > 0] and
+//      dh1 (.) [h1 > 0], each rounded once where it is formed, then used for the weight,
+//      bias and input gradients alike (a BF16 tensor-core backward).
+// Every rounding is treated as identity when differentiating.  targets: tex_res^2 x 8
+// bytes.  Gradients are ACCUMULATED into the double arrays.
 double orc_ntc_loss_grad(const orc::NeuralTex* N, const float* W1, const float* b1, const float* W2,
                          const float* b2, const float* W3, const float* b3, const uint8_t* targets,
                          uint64_t n, const int32_t* ix, const int32_t* iy, int round_bf16,
@@ -177,6 +182,7 @@ double orc_ntc_loss_grad(const orc::NeuralTex* N, const float* W1, const float* 
                          double* const* dlat) {
     std::vector<double> w1(64 * 32), w2(64 * 64), w3(8 * 64);
     auto rnd = [&](double v) { return round_bf16 ? orc::to_bf16(v) : v; };
+    auto rndb = [&](double v) { return round_bf16 >= 2 ? orc::to_bf16(v) : v; };
     for (int i = 0; i < 64 * 32; ++i) w1[i] = rnd(W1[i]);
     for (int i = 0; i < 64 * 64; ++i) w2[i] = rnd(W2[i]);
     for (int i = 0; i < 8 * 64; ++i) w3[i] = rnd(W3[i]);
@@ -195,14 +201,14 @@ double orc_ntc_loss_grad(const orc::NeuralTex* N, const float* W1, const float* 
         for (int o = 0; o < 8; ++o) {
             double e = y[o] - t[o] / 255.0;
             loss += e * e * inv;
-            dy[o] = 2.0 * e * inv;
+            dy[o] = rndb(2.0 * e * inv);
             db3[o] += dy[o];
             for (int i = 0; i < 64; ++i) dW3[o * 64 + i] += dy[o] * h2[i];
         }
         for (int i = 0; i < 64; ++i) {
             double a = 0.0;
             for (int o = 0; o < 8; ++o) a += w3[o * 64 + i] * dy[o];
-            dh2[i] = h2[i] > 0 ? a : 0.0;
+            dh2[i] = h2[i] > 0 ? rndb(a) : 0.0;
             db2[i] += dh2[i];
         }
         for (int o = 0; o < 64; ++o)
@@ -210,7 +216,7 @@ double orc_ntc_loss_grad(const orc::NeuralTex* N, const float* W1, const float* 
         for (int i = 0; i < 64; ++i) {
             double a = 0.0;
             for (int o = 0; o < 64; ++o) a += w2[o * 64 + i] * dh2[o];
-            dh1[i] = h1[i] > 0 ? a : 0.0;
+            dh1[i] = h1[i] > 0 ? rndb(a) : 0.0;
             db1[i] += dh1[i];
         }
         for (int o = 0; o < 64; ++o)

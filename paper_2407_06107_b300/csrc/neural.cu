@@ -155,44 +155,25 @@ __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, 
     return t;
 }
 
-// 8 latent channels of one grid texel as 4 packed FP32 pairs (FP16, FP8 x scale, or FP32
-// master latents); every value is exact in FP32
-__device__ __forceinline__ void load_latent8(const NeuralView& N, int fmt, int g, int x, int y, uint64_t v[4]) {
-    const size_t o = ((size_t)y * N.res[g] + x) * 8;
-    if (fmt == 0) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(N.lat16 + N.lat_off[g] + o));
-        const __half2* h = reinterpret_cast<const __half2*>(&q);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { const float2 f = __half22float2(h[i]); v[i] = pk2(f.x, f.y); }
-    } else if (fmt == 1) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2*>(N.lat8 + N.lat_off[g] + o));
-        const uint8_t* b = reinterpret_cast<const uint8_t*>(&q);
-        const uint64_t sc = pk2(N.scale[g], N.scale[g]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __nv_fp8_e4m3 e0, e1;
-            e0.__x = b[2 * i];
-            e1.__x = b[2 * i + 1];
-            v[i] = mul2(pk2((float)e0, (float)e1), sc);
-        }
-    } else {
-        const float4* p = reinterpret_cast<const float4*>(N.lat32 + N.lat_off[g] + o);
-        const float4 a = p[0], b = p[1];
-        v[0] = pk2(a.x, a.y); v[1] = pk2(a.z, a.w); v[2] = pk2(b.x, b.y); v[3] = pk2(b.z, b.w);
-    }
+// 8 FP32 master latent channels of one grid texel as 4 packed pairs
+__device__ __forceinline__ void load_master8(const NeuralView& N, int g, int x, int y, uint64_t v[4]) {
+    const float4* p = reinterpret_cast<const float4*>(N.lat32 + N.lat_off[g] + ((size_t)y * N.res[g] + x) * 8);
+    const float4 a = p[0], b = p[1];
+    v[0] = pk2(a.x, a.y); v[1] = pk2(a.z, a.w); v[2] = pk2(b.x, b.y); v[3] = pk2(b.z, b.w);
 }
 
-// 32 features as 16 packed pairs: per grid and channel, w00 a + w10 b + w01 c + w11 d in
-// this order, each step one rounding (the oracle's order)
-__device__ __forceinline__ void features2(const NeuralView& N, int fmt, int ix, int iy, uint64_t f[16]) {
+// The 32 features of a training sample from the FP32 master latents, as 16 packed pairs:
+// per grid and channel, w00 a + w10 b + w01 c + w11 d in this order, each step one
+// rounding (the oracle's order).  No stores in between, so all 16 gathers can be in flight.
+__device__ __forceinline__ void master_features(const NeuralView& N, int ix, int iy, uint64_t f[16]) {
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const LTap t = latent_taps(N, g, ix, iy);
         uint64_t a[4], b[4], c[4], d[4];
-        load_latent8(N, fmt, g, t.x0, t.y0, a);
-        load_latent8(N, fmt, g, t.x1, t.y0, b);
-        load_latent8(N, fmt, g, t.x0, t.y1, c);
-        load_latent8(N, fmt, g, t.x1, t.y1, d);
+        load_master8(N, g, t.x0, t.y0, a);
+        load_master8(N, g, t.x1, t.y0, b);
+        load_master8(N, g, t.x0, t.y1, c);
+        load_master8(N, g, t.x1, t.y1, d);
         const uint64_t w00 = pk2(t.w00, t.w00), w10 = pk2(t.w10, t.w10);
         const uint64_t w01 = pk2(t.w01, t.w01), w11 = pk2(t.w11, t.w11);
 #pragma unroll
@@ -239,7 +220,7 @@ __device__ __forceinline__ void raw_to_pairs(const NeuralView& N, int g, uint4 q
     }
 }
 // The 32 features of one decode row, rounded to BF16 and stored grid by grid into row
-// `row` of the K-major A tile (same order and rounding as features2).  The four taps of
+// `row` of the K-major A tile (same order and rounding as master_features).  The four taps of
 // grid g+1 are loaded before grid g is interpolated, so two grids' gathers are in flight.
 // LF: the latent format (0 FP16, 1 FP8 x scale), fixed per kernel instantiation.
 template <int LF>
@@ -279,159 +260,7 @@ __device__ __forceinline__ void features_to_tile(const NeuralView& N, int ix, in
     }
 }
 
-__device__ __forceinline__ void features(const NeuralView& N, int fmt, int ix, int iy, float f[32]) {
-    uint64_t p[16];
-    features2(N, fmt, ix, iy, p);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) { const float2 v = upk2(p[i]); f[2 * i] = v.x; f[2 * i + 1] = v.y; }
-}
-
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// ------------------------------------------------------------------ training (SIMT FP32)
-// One block = 128 samples.  Forward with BF16-rounded operands (as the tensor-core decode
-// computes), MSE loss, analytic backward; block partial gradients are atomically added.
-constexpr int TB = 128;
-
-struct TrainSmem {
-    float W1[64 * 32], W2[64 * 64], W3[8 * 64], b1[64], b2[64], b3[8];
-    float X[TB][33], H1[TB][65], H2[TB][65], DY[TB][9];
-    float red[TB / 32];
-};
-
-__global__ void __launch_bounds__(TB) k_ntc_train(NeuralView N, uint32_t step, uint32_t batch, RoundKeys K,
-                                                  float* loss_sum, uint32_t use_explicit, const int32_t* ex_ix,
-                                                  const int32_t* ex_iy) {
-    extern __shared__ __align__(16) uint8_t train_raw[];
-    TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_raw);
-    float (&W1)[64 * 32] = S.W1; float (&W2)[64 * 64] = S.W2; float (&W3)[8 * 64] = S.W3;
-    float (&b1)[64] = S.b1; float (&b2)[64] = S.b2; float (&b3)[8] = S.b3;
-    float (&X)[TB][33] = S.X; float (&H1)[TB][65] = S.H1; float (&H2)[TB][65] = S.H2; float (&DY)[TB][9] = S.DY;
-    float (&red)[TB / 32] = S.red;
-    const int t = threadIdx.x;
-    const float* P = N.mlp32;
-    for (int i = t; i < 64 * 32; i += TB) W1[i] = bf16r(P[i]);
-    for (int i = t; i < 64; i += TB) { b1[i] = P[2048 + i]; b2[i] = P[2048 + 64 + 4096 + i]; }
-    for (int i = t; i < 64 * 64; i += TB) W2[i] = bf16r(P[2048 + 64 + i]);
-    for (int i = t; i < 8 * 64; i += TB) W3[i] = bf16r(P[2048 + 64 + 4096 + 64 + i]);
-    if (t < 8) b3[t] = P[2048 + 64 + 4096 + 64 + 512 + t];
-    __syncthreads();
-
-    const uint32_t k = blockIdx.x * TB + t;
-    const bool live = k < batch;
-    int ix = 0, iy = 0;
-    if (live) {
-        if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
-        else {
-            const uint4 w = philox(k, step, 0u, 0x4E54u, K);
-            ix = (int)__umulhi(w.x, (uint32_t)N.tex_res);
-            iy = (int)__umulhi(w.y, (uint32_t)N.tex_res);
-        }
-    }
-    float loss = 0.0f;
-    {   // forward
-        float f[32];
-        features(N, 2, ix, iy, f);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) X[t][i] = bf16r(f[i]);
-        for (int o = 0; o < 64; ++o) {
-            float z = b1[o];
-#pragma unroll 8
-            for (int i = 0; i < 32; ++i) z = fmaf(W1[o * 32 + i], X[t][i], z);
-            H1[t][o] = z > 0.0f ? bf16r(z) : 0.0f;
-        }
-        for (int o = 0; o < 64; ++o) {
-            float z = b2[o];
-#pragma unroll 8
-            for (int i = 0; i < 64; ++i) z = fmaf(W2[o * 64 + i], H1[t][i], z);
-            H2[t][o] = z > 0.0f ? bf16r(z) : 0.0f;
-        }
-        const uint8_t* tg = N.targets + ((size_t)iy * N.tex_res + ix) * 8;
-        const float inv = 1.0f / (8.0f * (float)batch);
-        for (int o = 0; o < 8; ++o) {
-            float z = b3[o];
-#pragma unroll 8
-            for (int i = 0; i < 64; ++i) z = fmaf(W3[o * 64 + i], H2[t][i], z);
-            const float e = live ? z - (float)tg[o] * (1.0f / 255.0f) : 0.0f;
-            loss = fmaf(e * e, inv, loss);
-            DY[t][o] = 2.0f * e * inv;
-        }
-    }
-    // block loss
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
-    if ((t & 31) == 0) red[t >> 5] = loss;
-    __syncthreads();
-    if (t == 0) atomicAdd(loss_sum, red[0] + red[1] + red[2] + red[3]);
-
-    float* G = N.grad32;
-    // dW3, db3 (512 + 8 outputs)
-    for (int j = t; j < 8 * 64 + 8; j += TB) {
-        float a = 0.0f;
-        if (j < 512) { const int o = j >> 6, i = j & 63; for (int s = 0; s < TB; ++s) a = fmaf(DY[s][o], H2[s][i], a); }
-        else { const int o = j - 512; for (int s = 0; s < TB; ++s) a += DY[s][o]; }
-        atomicAdd(&G[j < 512 ? 2048 + 64 + 4096 + 64 + j : 2048 + 64 + 4096 + 64 + 512 + (j - 512)], a);
-    }
-    __syncthreads();
-    // dh2 = W3^T dy (.) [h2 > 0]   (overwrites H2)
-    for (int i = 0; i < 64; ++i) {
-        float a = 0.0f;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) a = fmaf(W3[o * 64 + i], DY[t][o], a);
-        H2[t][i] = H2[t][i] > 0.0f ? a : 0.0f;
-    }
-    __syncthreads();
-    // dW2, db2
-    for (int j = t; j < 64 * 64 + 64; j += TB) {
-        float a = 0.0f;
-        if (j < 4096) { const int o = j >> 6, i = j & 63; for (int s = 0; s < TB; ++s) a = fmaf(H2[s][o], H1[s][i], a); }
-        else { const int o = j - 4096; for (int s = 0; s < TB; ++s) a += H2[s][o]; }
-        atomicAdd(&G[j < 4096 ? 2048 + 64 + j : 2048 + 64 + 4096 + (j - 4096)], a);
-    }
-    __syncthreads();
-    // dh1 = W2^T dh2 (.) [h1 > 0]   (overwrites H1)
-    float dh1[64];
-    for (int i = 0; i < 64; ++i) {
-        float a = 0.0f;
-#pragma unroll 8
-        for (int o = 0; o < 64; ++o) a = fmaf(W2[o * 64 + i], H2[t][o], a);
-        dh1[i] = H1[t][i] > 0.0f ? a : 0.0f;
-    }
-    __syncthreads();
-    for (int i = 0; i < 64; ++i) H1[t][i] = dh1[i];
-    __syncthreads();
-    // dW1, db1
-    for (int j = t; j < 64 * 32 + 64; j += TB) {
-        float a = 0.0f;
-        if (j < 2048) { const int o = j >> 5, i = j & 31; for (int s = 0; s < TB; ++s) a = fmaf(H1[s][o], X[s][i], a); }
-        else { const int o = j - 2048; for (int s = 0; s < TB; ++s) a += H1[s][o]; }
-        atomicAdd(&G[j < 2048 ? j : 2048 + (j - 2048)], a);
-    }
-    // dx = W1^T dh1 -> latent gradient scatter with the bilinear weights
-    if (live) {
-#pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-            const LTap tp = latent_taps(N, g, ix, iy);
-            float dx[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float a = 0.0f;
-                for (int o = 0; o < 64; ++o) a = fmaf(W1[o * 32 + 8 * g + c], dh1[o], a);
-                dx[c] = a;
-            }
-            float* dl = N.dlat + N.lat_off[g];
-            const int R = N.res[g];
-            const int xs[4] = {tp.x0, tp.x1, tp.x0, tp.x1}, ys[4] = {tp.y0, tp.y0, tp.y1, tp.y1};
-            const float ws[4] = {tp.w00, tp.w10, tp.w01, tp.w11};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float* p = dl + ((size_t)ys[q] * R + xs[q]) * 8;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) atomicAdd(p + c, ws[q] * dx[c]);
-            }
-        }
-    }
-}
-
+// ------------------------------------------------------------------ optimiser
 // Adam with bias correction; consumes and zeroes the gradient
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -751,13 +580,357 @@ __global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(Neur
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ------------------------------------------------------------------ training (tcgen05)
+// One CTA of 128 threads; one training sample (one row) per thread in each 128-sample tile.
+// Forward: the decode's three GEMMs on BF16 operands.  Backward, per tile:
+//   dH2 = dY W3            (A dY, K-major;  B W3 read MN-major)          -> TMEM scratch
+//   dW3^T += [H2 | 1]^T dY (A the H2 tile read MN-major; B dY MN-major)  -> TMEM accumulator
+//   dH1 = dZ2 W2,  dW2 += dZ2^T [H1 | 1]
+//   dX  = dZ1 W1,  dW1 += dZ1^T [X | 1]
+// with dZ = dH (.) [Z > 0] and dY = 2 (y - target) / (8 batch), each rounded to BF16 as a
+// GEMM operand.  The activation tiles are written once, row = sample, in the K-major layout
+// of the forward GEMMs.  A K-major core matrix (8 samples x 8 features) is also an MN-major
+// core matrix of the transposed tile (8 features contiguous, 8 samples), so the
+// weight-gradient GEMMs read the same bytes with features along M or N and samples along K;
+// the weights, stored K-major for the forward, are read MN-major as the backward's B.
+// A block of ones after the features of X, H1 and H2 makes each bias gradient one more
+// column (or lane) of a weight-gradient accumulator.  The weight-gradient GEMMs run at
+// M = 128 with 64 (H2: 80) meaningful rows; the rows beyond read the next tiles of the
+// shared-memory struct, and their lanes are never read.  The accumulators sum over
+// all tiles of a CTA and are added to the global gradient once, at the end.
+constexpr int TR_ROWS = 128;
+constexpr int TR_CTAS_PER_SM = 2;              // 2 x 256 TMEM columns = 512
+constexpr uint32_t TR_TMEM_COLS = 256;
+constexpr uint32_t TC_DW2 = 64, TC_DW1 = 144, TC_DW3 = 192;   // accumulator columns (80, 48, 16)
+constexpr int FX = 48, FH = 80, FZ2 = 64, FY = 16;            // row lengths of the tiles (elements)
+constexpr uint32_t IDESC_A_MN = 1u << 15, IDESC_B_MN = 1u << 16;
+
+struct TrainSmem {
+    uint8_t X[TR_ROWS * FX * 2];      // 32 latent features | 16 ones
+    uint8_t H1[TR_ROWS * FH * 2];     // 64 activations | 16 ones
+    uint8_t H2[TR_ROWS * FH * 2];     // 64 activations | 16 ones; later dZ1 | 16 ones
+    uint8_t dZ2[TR_ROWS * FZ2 * 2];
+    uint8_t dY[TR_ROWS * FY * 2];     // 8 output gradients | 8 zeros
+    uint8_t W1[64 * 32 * 2], W2[64 * 64 * 2], W3[16 * 64 * 2];
+    float bias[144];
+    uint64_t bar;
+    uint32_t tmem;
+    int abort_flag;
+    float red[4];
+};
+// The M = 128 reads past the 64 (80) features of dZ2, H2 and dZ1 land in the next tiles of
+// the struct (at most 70,656 B from its start); W3 ends last, at 88,064 B.
+static_assert(sizeof(TrainSmem) * 3 > 228 * 1024, "at most 2 CTAs (2 x 256 TMEM columns) per SM");
+
+// FP32 master weights [rows][K] (rows >= present are zero) -> BF16, K-major tile
+__device__ __forceinline__ void stage_weights_f32(uint8_t* dst, const float* src, int rows, int K, int present) {
+    const int chunks = rows * K / 8;
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        const int row = c / (K / 8), kc = c % (K / 8);
+        uint32_t p[4] = {0u, 0u, 0u, 0u};
+        if (row < present) {
+            const float* s = src + (size_t)row * K + kc * 8;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) p[i] = bf16x2_of<false>(pk2(s[2 * i], s[2 * i + 1]));
+        }
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, kc * 8, K)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+}
+
+// Descriptor of an MN-major no-swizzle operand: core matrices (8 K rows x 16 B along MN)
+// mn_stride apart along MN and k_stride apart along K.  As for K-major operands, the
+// leading byte offset is the stride along K and the stride byte offset the one along M or
+// N (the gradient tests fail with the two exchanged).
+__device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t mn_stride, uint32_t k_stride) {
+    return smem_desc(saddr, k_stride, mn_stride);
+}
+
+// All threads: publish this thread's shared-memory writes to the tensor core and meet;
+// thread 0 issues the MMAs and waits (bounded) for their completion; all meet again.
+template <class Issue>
+__device__ __forceinline__ bool tc_round(TrainSmem& S, uint32_t& phase, Issue issue) {
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        issue();
+        mma_commit(&S.bar);
+        if (!mbar_wait_bounded(&S.bar, phase, WAIT_CYCLES)) S.abort_flag = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    tc_fence_after();
+    return S.abort_flag == 0;
+}
+
+// Hidden layer epilogue: 64 pre-activations from TMEM + bias -> ReLU -> BF16 row of a tile
+// with F columns; returns the mask [z > 0] (bit j = feature j)
+template <int F>
+__device__ __forceinline__ uint2 hidden_epilogue(uint32_t taddr, const float* bias, uint8_t* dst, int row) {
+    uint32_t r[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, r[c]);
+    tmem_wait_ld();
+    const ulonglong2* bias2 = reinterpret_cast<const ulonglong2*>(bias);
+    uint32_t m[2] = {0u, 0u};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const ulonglong2 ba = bias2[2 * c], bb = bias2[2 * c + 1];
+        const uint64_t bv[4] = {ba.x, ba.y, bb.x, bb.y};
+        uint32_t p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = 8 * c + 2 * i;
+            const uint64_t z = add2(pk2(__uint_as_float(r[j >> 4][j & 15]), __uint_as_float(r[(j + 1) >> 4][(j + 1) & 15])),
+                                    bv[i]);
+            const float2 zf = upk2(z);
+            m[j >> 5] |= (zf.x > 0.0f ? 1u : 0u) << (j & 31);
+            m[j >> 5] |= (zf.y > 0.0f ? 1u : 0u) << ((j + 1) & 31);
+            p[i] = bf16x2_of<true>(z);
+        }
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, 8 * c, F)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+    return make_uint2(m[0], m[1]);
+}
+
+// Gradient epilogue: 64 values from TMEM, masked by [z > 0], as a BF16 row of a tile
+template <int F>
+__device__ __forceinline__ void grad_epilogue(uint32_t taddr, uint2 mask, uint8_t* dst, int row) {
+    uint32_t r[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, r[c]);
+    tmem_wait_ld();
+    const uint32_t m[2] = {mask.x, mask.y};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = 8 * c + 2 * i;
+            const float a = (m[j >> 5] >> (j & 31)) & 1u ? __uint_as_float(r[j >> 4][j & 15]) : 0.0f;
+            const float b = (m[j >> 5] >> ((j + 1) & 31)) & 1u ? __uint_as_float(r[(j + 1) >> 4][(j + 1) & 15]) : 0.0f;
+            p[i] = bf16x2_of<false>(pk2(a, b));
+        }
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, 8 * c, F)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+}
+
+__global__ void __launch_bounds__(TR_ROWS, TR_CTAS_PER_SM)
+k_ntc_train_tc(NeuralView N, uint32_t step, uint32_t batch, RoundKeys K, float* loss_sum, uint32_t use_explicit,
+               const int32_t* ex_ix, const int32_t* ex_iy, uint32_t* status) {
+    extern __shared__ __align__(1024) uint8_t train_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+    const float* P = N.mlp32;       // W1 [64][32], b1, W2 [64][64], b2, W3 [8][64], b3
+    stage_weights_f32(S.W1, P, 64, 32, 64);
+    stage_weights_f32(S.W2, P + 2112, 64, 64, 64);
+    stage_weights_f32(S.W3, P + 6272, 16, 64, 8);
+    for (int i = t; i < 64; i += TR_ROWS) { S.bias[i] = P[2048 + i]; S.bias[64 + i] = P[6208 + i]; }
+    if (t < 16) S.bias[128 + t] = t < 8 ? P[6784 + t] : 0.0f;
+    {   // constant blocks of this thread's rows: ones after the features, zeros after dY
+        const uint4 one = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            *reinterpret_cast<uint4*>(S.X + kmaj_off(t, 32 + 8 * h, FX)) = one;
+            *reinterpret_cast<uint4*>(S.H1 + kmaj_off(t, 64 + 8 * h, FH)) = one;
+            *reinterpret_cast<uint4*>(S.H2 + kmaj_off(t, 64 + 8 * h, FH)) = one;
+        }
+        *reinterpret_cast<uint4*>(S.dY + kmaj_off(t, 8, FY)) = zero;
+    }
+    if (t == 0) { mbar_init(&S.bar, 1); S.abort_flag = 0; }
+    if (warp == 0) tmem_alloc(&S.tmem, TR_TMEM_COLS);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t sX = smem_u32(S.X), sH1 = smem_u32(S.H1), sH2 = smem_u32(S.H2), sZ2 = smem_u32(S.dZ2);
+    const uint32_t sY = smem_u32(S.dY), sW1 = smem_u32(S.W1), sW2 = smem_u32(S.W2), sW3 = smem_u32(S.W3);
+    const float inv = 1.0f / (8.0f * (float)batch);
+    uint32_t phase = 0;
+    bool ok = true, any = false;
+    float loss = 0.0f;
+    const uint32_t ntiles = (batch + TR_ROWS - 1) / TR_ROWS;
+    for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const uint32_t acc0 = any ? 1u : 0u;    // accumulators: first tile of this CTA overwrites
+        const uint32_t k = tile * TR_ROWS + t;
+        const bool live = k < batch;
+        int ix = 0, iy = 0;
+        if (live) {
+            if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
+            else {
+                const uint4 w = philox(k, step, 0u, 0x4E54u, K);
+                ix = (int)__umulhi(w.x, (uint32_t)N.tex_res);
+                iy = (int)__umulhi(w.y, (uint32_t)N.tex_res);
+            }
+        }
+        {   // latent features (FP32 master latents) -> BF16 row of X
+            uint64_t f[16];
+            master_features(N, ix, iy, f);
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                *reinterpret_cast<uint4*>(S.X + kmaj_off(t, 8 * g, FX)) =
+                    make_uint4(bf16x2_of<false>(f[4 * g]), bf16x2_of<false>(f[4 * g + 1]),
+                               bf16x2_of<false>(f[4 * g + 2]), bf16x2_of<false>(f[4 * g + 3]));
+        }
+        // ---- forward
+        ok = tc_round(S, phase, [&] {
+            for (int s = 0; s < 2; ++s)
+                mma_bf16(tmem, smem_desc(sX + 256 * s, 128, FX * 16), smem_desc(sW1 + 256 * s, 128, 512),
+                         idesc_bf16(128, 64), s > 0);
+        });
+        if (!ok) break;
+        const uint2 mask1 = hidden_epilogue<FH>(tmem + lane_base, S.bias, S.H1, t);
+        ok = tc_round(S, phase, [&] {
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem, smem_desc(sH1 + 256 * s, 128, FH * 16), smem_desc(sW2 + 256 * s, 128, 1024),
+                         idesc_bf16(128, 64), s > 0);
+        });
+        if (!ok) break;
+        const uint2 mask2 = hidden_epilogue<FH>(tmem + lane_base, S.bias + 64, S.H2, t);
+        ok = tc_round(S, phase, [&] {
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem, smem_desc(sH2 + 256 * s, 128, FH * 16), smem_desc(sW3 + 256 * s, 128, 1024),
+                         idesc_bf16(128, 16), s > 0);
+        });
+        if (!ok) break;
+        {   // outputs -> MSE loss and dY (BF16 row of the dY tile)
+            uint32_t r[16];
+            tmem_ld16(tmem + lane_base, r);
+            tmem_wait_ld();
+            float dy[8];
+            const uint8_t* tg = N.targets + ((size_t)iy * N.tex_res + ix) * 8;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const float y = __uint_as_float(r[o]) + S.bias[128 + o];
+                const float e = live ? y - (float)tg[o] * (1.0f / 255.0f) : 0.0f;
+                loss = fmaf(e * e, inv, loss);
+                dy[o] = 2.0f * e * inv;
+            }
+            *reinterpret_cast<uint4*>(S.dY + kmaj_off(t, 0, FY)) =
+                make_uint4(bf16x2_of<false>(pk2(dy[0], dy[1])), bf16x2_of<false>(pk2(dy[2], dy[3])),
+                           bf16x2_of<false>(pk2(dy[4], dy[5])), bf16x2_of<false>(pk2(dy[6], dy[7])));
+        }
+        // ---- backward, layer 3: dH2 = dY W3;  dW3^T | db3 += [H2 | 1]^T dY
+        ok = tc_round(S, phase, [&] {
+            mma_bf16(tmem, smem_desc(sY, 128, FY * 16), mn_desc(sW3, 128, 1024), idesc_bf16(128, 64) | IDESC_B_MN, 0);
+            for (int s = 0; s < 8; ++s)
+                mma_bf16(tmem + TC_DW3, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
+                         mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16), idesc_bf16(128, 16) | IDESC_A_MN | IDESC_B_MN,
+                         acc0 | (s > 0));
+        });
+        if (!ok) break;
+        grad_epilogue<FZ2>(tmem + lane_base, mask2, S.dZ2, t);
+        // ---- layer 2: dH1 = dZ2 W2;  dW2 | db2 += dZ2^T [H1 | 1]
+        ok = tc_round(S, phase, [&] {
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem, smem_desc(sZ2 + 256 * s, 128, FZ2 * 16), mn_desc(sW2 + 2048 * s, 128, 1024),
+                         idesc_bf16(128, 64) | IDESC_B_MN, s > 0);
+            for (int s = 0; s < 8; ++s)
+                mma_bf16(tmem + TC_DW2, mn_desc(sZ2 + 2 * FZ2 * 16 * s, 128, FZ2 * 16),
+                         mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(128, 80) | IDESC_A_MN | IDESC_B_MN,
+                         acc0 | (s > 0));
+        });
+        if (!ok) break;
+        grad_epilogue<FH>(tmem + lane_base, mask1, S.H2, t);      // dZ1 replaces H2 (same layout)
+        // ---- layer 1: dX = dZ1 W1;  dW1 | db1 += dZ1^T [X | 1]
+        ok = tc_round(S, phase, [&] {
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem, smem_desc(sH2 + 256 * s, 128, FH * 16), mn_desc(sW1 + 1024 * s, 128, 512),
+                         idesc_bf16(128, 32) | IDESC_B_MN, s > 0);
+            for (int s = 0; s < 8; ++s)
+                mma_bf16(tmem + TC_DW1, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
+                         mn_desc(sX + 2 * FX * 16 * s, 128, FX * 16), idesc_bf16(128, 48) | IDESC_A_MN | IDESC_B_MN,
+                         acc0 | (s > 0));
+        });
+        if (!ok) break;
+        any = true;
+        {   // dX -> latent gradients, spread over each grid's 4 taps with the bilinear weights
+            uint32_t r0[16], r1[16];
+            tmem_ld16(tmem + lane_base, r0);
+            tmem_ld16(tmem + lane_base + 16, r1);
+            tmem_wait_ld();
+            if (live) {
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const LTap tp = latent_taps(N, g, ix, iy);
+                    float dx[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) dx[c] = __uint_as_float(g < 2 ? r0[8 * g + c] : r1[8 * (g - 2) + c]);
+                    float* dl = N.dlat + N.lat_off[g];
+                    const int R = N.res[g];
+                    const int xs[4] = {tp.x0, tp.x1, tp.x0, tp.x1}, ys[4] = {tp.y0, tp.y0, tp.y1, tp.y1};
+                    const float ws[4] = {tp.w00, tp.w10, tp.w01, tp.w11};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float4* p = reinterpret_cast<float4*>(dl + ((size_t)ys[q] * R + xs[q]) * 8);
+                        atomicAdd(p, make_float4(ws[q] * dx[0], ws[q] * dx[1], ws[q] * dx[2], ws[q] * dx[3]));
+                        atomicAdd(p + 1, make_float4(ws[q] * dx[4], ws[q] * dx[5], ws[q] * dx[6], ws[q] * dx[7]));
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();    // the next tile's features overwrite X only after every dX read
+    }
+    // loss of this CTA's samples
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
+    if ((t & 31) == 0) S.red[warp] = loss;
+    __syncthreads();
+    if (t == 0) atomicAdd(loss_sum, (S.red[0] + S.red[1]) + (S.red[2] + S.red[3]));
+    // accumulators -> global gradients (lane = output feature; lane 64 of dW3^T = db3)
+    if (ok && any) {
+        tc_fence_after();
+        float* G = N.grad32;
+        uint32_t r[16];
+#pragma unroll 1
+        for (int c = 0; c < 5; ++c) {            // dW2 [64][64] | db2
+            tmem_ld16(tmem + lane_base + TC_DW2 + 16 * c, r);
+            tmem_wait_ld();
+            if (t < 64)
+                for (int j = 0; j < 16; ++j) {
+                    const int col = 16 * c + j;
+                    if (col < 64) atomicAdd(G + 2112 + t * 64 + col, __uint_as_float(r[j]));
+                    else if (col == 64) atomicAdd(G + 6208 + t, __uint_as_float(r[j]));
+                }
+        }
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {            // dW1 [64][32] | db1
+            tmem_ld16(tmem + lane_base + TC_DW1 + 16 * c, r);
+            tmem_wait_ld();
+            if (t < 64)
+                for (int j = 0; j < 16; ++j) {
+                    const int col = 16 * c + j;
+                    if (col < 32) atomicAdd(G + t * 32 + col, __uint_as_float(r[j]));
+                    else if (col == 32) atomicAdd(G + 2048 + t, __uint_as_float(r[j]));
+                }
+        }
+        tmem_ld16(tmem + lane_base + TC_DW3, r);   // dW3^T [64][8] | db3
+        tmem_wait_ld();
+        if (t < 64)
+            for (int o = 0; o < 8; ++o) atomicAdd(G + 6272 + o * 64 + t, __uint_as_float(r[o]));
+        else if (t == 64)
+            for (int o = 0; o < 8; ++o) atomicAdd(G + 6784 + o, __uint_as_float(r[o]));
+    }
+    if (!ok && t == 0) atomicOr(status, DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TR_TMEM_COLS);
+}
+
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint64_t seed, float* loss_sum,
-                             const int32_t* ex_ix, const int32_t* ex_iy, cudaStream_t st) {
-    const int grid = (int)((batch + TB - 1) / TB);
-    cudaFuncSetAttribute(k_ntc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
-    k_ntc_train<<<grid, TB, sizeof(TrainSmem), st>>>(N, step, batch, expand_key(seed), loss_sum, ex_ix != nullptr,
-                                                     ex_ix, ex_iy);
+                             const int32_t* ex_ix, const int32_t* ex_iy, int num_sms, uint32_t* status,
+                             cudaStream_t st) {
+    const uint32_t tiles = (batch + TR_ROWS - 1) / TR_ROWS;
+    const uint32_t cap = (uint32_t)num_sms * TR_CTAS_PER_SM;
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    cudaFuncSetAttribute(k_ntc_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
+    k_ntc_train_tc<<<grid, TR_ROWS, sizeof(TrainSmem), st>>>(N, step, batch, expand_key(seed), loss_sum,
+                                                             ex_ix != nullptr, ex_ix, ex_iy, status);
     return cudaGetLastError();
 }
 

@@ -149,7 +149,8 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.grad32, 0, MLP_N * 4, c->stream) : e;
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.dlat, 0, r->lat_total * 4, c->stream) : e;
     for (uint32_t k = 0; k < steps && e == cudaSuccess; ++k) {
-        e = stf::launch_ntc_train(r->view, r->step, batch, seed, r->loss + k, nullptr, nullptr, c->stream);
+        e = stf::launch_ntc_train(r->view, r->step, batch, seed, r->loss + k, nullptr, nullptr, c->num_sms,
+                                     c->d_status, c->stream);
         const int t = (int)r->step + 1;
         // half-cosine decay over this call's steps (factor 1 when lr_min_frac = 1)
         const double f = ap->lr_min_frac, fk = f + (1.0 - f) * 0.5 * (1.0 + std::cos(M_PI * (double)k / (double)steps));
@@ -185,7 +186,8 @@ stf_status stf_neural_grad(stf_ctx c, stf_neural h, uint32_t step, uint32_t batc
     cudaError_t e = cudaMemsetAsync(r->loss, 0, 4, c->stream);
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.grad32, 0, MLP_N * 4, c->stream) : e;
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.dlat, 0, r->lat_total * 4, c->stream) : e;
-    if (e == cudaSuccess) e = stf::launch_ntc_train(r->view, step, batch, seed, r->loss, ex_ix, ex_iy, c->stream);
+    if (e == cudaSuccess)
+        e = stf::launch_ntc_train(r->view, step, batch, seed, r->loss, ex_ix, ex_iy, c->num_sms, c->d_status, c->stream);
     float l = 0.0f;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, r->loss, 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -10,7 +10,10 @@ arithmetic:
     neighbouring BF16 value on the GPU (a counted boundary case, like a CDF boundary).
   * shaded values: the GGX condition number with respect to the normal is <= 2/alpha
     = 40 at alpha >= 0.05, giving |df| <= 5e-4 sum|terms| + 1e-6.
-  * gradients: FP32 atomics vs FP64 sums; relative L2 <= 1e-3.
+  * gradients: the tensor-core backward rounds dy, dh2 and dh1 to BF16 as GEMM operands;
+    the oracle's bf16_backward level rounds the same values, so what remains is FP32
+    accumulation (tensor cores, atomics) against FP64 sums, plus the rare operand that
+    rounds to the neighbouring BF16 value: relative L2 <= 1e-3.
 """
 import math
 
@@ -100,7 +103,7 @@ def test_gradients_match_oracle(ctx, net, data):
     loss = ctx.neural_grad(net, step, batch, seed)
     gm = ctx.neural_get(net, "grad_mlp", LAT_TOTAL).astype(np.float64)
     gl = ctx.neural_get(net, "grad_latents", LAT_TOTAL).astype(np.float64)
-    rl, rgm, rgl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True)
+    rl, rgm, rgl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True, bf16_backward=True)
     assert abs(loss - rl) <= 1e-5 * rl
     for got, ref in ((gm, rgm), (gl, rgl)):
         assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
@@ -111,12 +114,31 @@ def test_gradients_match_oracle(ctx, net, data):
     assert np.linalg.norm(gm2 - gm) <= 1e-5 * np.linalg.norm(gm)
 
 
+def test_gradients_many_tiles_per_cta(ctx, net, data):
+    # more tiles than resident CTAs (2 per SM): each CTA accumulates several tiles' weight
+    # gradients in TMEM before adding them once; the last tile is ragged
+    lat, mlp, tg = data
+    step, batch, seed = 1, 2 * 148 * 128 + 12345, 9
+    ix, iy = oracle.ntc_sample_texels(step, batch, seed, R0)
+    loss = ctx.neural_grad(net, step, batch, seed)
+    gm = ctx.neural_get(net, "grad_mlp", LAT_TOTAL).astype(np.float64)
+    gl = ctx.neural_get(net, "grad_latents", LAT_TOTAL).astype(np.float64)
+    rl, rgm, rgl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True, bf16_backward=True)
+    assert abs(loss - rl) <= 1e-5 * rl
+    for got, ref in ((gm, rgm), (gl, rgl)):
+        assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+    # per block: weights and biases of each layer
+    cut = np.cumsum([0, 2048, 64, 4096, 64, 512, 8])
+    for a, b in zip(cut[:-1], cut[1:]):
+        assert np.linalg.norm(gm[a:b] - rgm[a:b]) <= 2e-3 * np.linalg.norm(rgm[a:b]), (a, b)
+
+
 def test_adam_step_matches_oracle(ctx, net, data):
     lat, mlp, tg = data
     lr_l, lr_m, seed, batch = 1e-2, 5e-3, 5, 1024
     ctx.neural_train(net, 1, batch, lr_l, lr_m, seed)
     ix, iy = oracle.ntc_sample_texels(0, batch, seed, R0)
-    _, gm, gl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True)
+    _, gm, gl = oracle.ntc_loss_grad(R0, lat, mlp, tg, ix, iy, round_bf16=True, bf16_backward=True)
     for p0, g, lr, what in ((mlp, gm, lr_m, "mlp"), (np.concatenate([x.ravel() for x in lat]), gl, lr_l, "latents")):
         p = p0.astype(np.float64).copy()
         oracle.adam(p, g, np.zeros_like(p), np.zeros_like(p), 1, lr)

@@ -141,6 +141,32 @@ def test_gradients_match_finite_differences():
     assert np.median(rel) < 1e-3 and np.mean(rel < 1e-3) >= 0.8, rel
 
 
+def test_bf16_backward_rounds_the_gemm_operands():
+    # the tensor-core backward feeds dy, dh2 and dh1 to BF16 GEMMs: the oracle's bf16_backward
+    # level rounds each once where it is formed (relative error <= 2^-9 per operand)
+    lat, mlp, R0 = _small_net(seed=13)
+    mlp[2048:2112] = 0.05
+    m = synth.material_rgba8(R0, 14, octaves=3, base=2, mips=False)
+    targets = synth.ntc_targets(m, 15)
+    rng = np.random.default_rng(7)
+    ix, iy = rng.integers(0, R0, 256), rng.integers(0, R0, 256)
+    l1, g1, d1 = oracle.ntc_loss_grad(R0, lat, mlp, targets, ix, iy, round_bf16=True)
+    l2, g2, d2 = oracle.ntc_loss_grad(R0, lat, mlp, targets, ix, iy, round_bf16=True, bf16_backward=True)
+    assert l1 == l2                                  # the forward is unchanged
+    for a, b in ((g1, g2), (d1, d2)):                # moved, by well under 1e-2 (relative L2)
+        d = np.linalg.norm(a - b) / np.linalg.norm(a)
+        assert 0 < d < 1e-2, d
+    # a zero last layer outputs y = b3 exactly, so db3 is the sum over samples of
+    # BF16(2 (b3 - t / 255) / (8 n)), and dh2 = 0 leaves every earlier gradient at zero
+    mlp0 = mlp.copy()
+    mlp0[6272:6784] = 0.0
+    _, g0, d0 = oracle.ntc_loss_grad(R0, lat, mlp0, targets, ix, iy, round_bf16=True, bf16_backward=True)
+    t = targets[iy, ix].astype(np.float64) / 255.0
+    dy = oracle.round_bf16(2.0 * (mlp0[6784:6792].astype(np.float64) - t) / (8.0 * len(ix)))
+    np.testing.assert_allclose(g0[6784:6792], dy.sum(axis=0), rtol=1e-13, atol=0)
+    assert not np.any(g0[:6272]) and not np.any(d0)
+
+
 def test_adam_first_step_closed_form():
     rng = np.random.default_rng(2)
     p = rng.normal(size=1000)
