@@ -156,10 +156,10 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
         const double f = ap->lr_min_frac, fk = f + (1.0 - f) * 0.5 * (1.0 + std::cos(M_PI * (double)k / (double)steps));
         if (e == cudaSuccess)
             e = stf::launch_adam(r->view.lat32, r->view.dlat, r->m_lat, r->v_lat, r->lat_total,
-                                 (float)(ap->lr_latent * fk), ap->beta1, ap->beta2, ap->eps, t, c->stream);
+                                 (float)(ap->lr_latent * fk), ap->beta1, ap->beta2, ap->eps, t, c->num_sms, c->stream);
         if (e == cudaSuccess)
             e = stf::launch_adam(r->view.mlp32, r->view.grad32, r->m_mlp, r->v_mlp, MLP_N, (float)(ap->lr_mlp * fk),
-                                 ap->beta1, ap->beta2, ap->eps, t, c->stream);
+                                 ap->beta1, ap->beta2, ap->eps, t, c->num_sms, c->stream);
         r->step++;
     }
     if (e == cudaSuccess && losses) e = cudaMemcpyAsync(losses, r->loss, steps * 4, cudaMemcpyDeviceToHost, c->stream);

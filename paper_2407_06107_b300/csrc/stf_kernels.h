@@ -128,7 +128,7 @@ cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch,
                              const int32_t* ex_ix, const int32_t* ex_iy, int num_sms, uint32_t* status,
                              cudaStream_t st);
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
-                        int t, cudaStream_t st);
+                        int t, int num_sms, cudaStream_t st);
 cudaError_t launch_ntc_quantize(const NeuralView& N, uint64_t lat_total, int fmt, unsigned int* amax_scratch,
                                 cudaStream_t st);
 cudaError_t launch_ntc_decode(const NeuralView& N, const NeuralDecodeArgs& a, int num_sms, cudaStream_t st);
