@@ -873,6 +873,34 @@ def run_neural(args):
     ctx.close()
 
 
+def run_train(args):
+    """Neural training workload: the 4096^2 learned material (latent grids 1024^2..128^2 x 8,
+    MLP 32-64-64-8); each step = one batch of --tbatch Philox-drawn texels through the
+    tensor-core forward and backward, then Adam over all 5.6 M latents and the MLP."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    ctx = stf.Context(local)
+    material = synth.material_rgba8(TEX_RES, 102, octaves=6)
+    lat, mlp = synth.ntc_init((1024, 512, 256, 128), 104)
+    net = ctx.neural_create(TEX_RES, lat, mlp, synth.ntc_targets(material, 104))
+    ctx.neural_train(net, args.warmup, args.tbatch, seed=1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = ctx.neural_train(net, args.steps, args.tbatch, seed=2)      # one call: steps + final repack
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "neural training samples/s", "value": args.tbatch / (ms / 1e3),
+                      "unit": "samples/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                      "config": {"workload": f"neural training 4096^2, batch {args.tbatch}"}}), flush=True)
+    ctx.close()
+
+
 def run_ntap(args):
     """N-tap comparator workload: filter-before over the material workload's queries (--queries),
     8 spp, trilinear / bicubic B-spline / Mitchell with all taps of both MIP levels (8 / 32 / 32
@@ -994,7 +1022,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="material",
-                    choices=["material", "volume", "neural", "triplanar", "ntap", "lookup"])
+                    choices=["material", "volume", "neural", "train", "triplanar", "ntap", "lookup"])
     ap.add_argument("--lfilter", default="linear", choices=["linear", "bspline", "catmull_rom", "mitchell", "ewa", "gauss"])
     ap.add_argument("--lmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after", "positivized"])
     ap.add_argument("--lsampler", default="frs", choices=["frs", "fis"])
@@ -1007,6 +1035,7 @@ def main():
     ap.add_argument("--tformat", default="rgba8", choices=["rgba8", "dct6"])
     ap.add_argument("--nfilter", default="bspline", choices=["bspline", "linear", "mitchell"])
     ap.add_argument("--nmode", default="stochastic", choices=["stochastic", "ntap_before", "positivized"])
+    ap.add_argument("--tbatch", type=int, default=1 << 18)
     ap.add_argument("--vfilter", default="bspline", choices=["bspline", "linear"])
     ap.add_argument("--vmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after"])
     ap.add_argument("--width", type=int, default=1920)
@@ -1020,6 +1049,8 @@ def main():
         run_volume(args)
     elif args.workload == "neural":
         run_neural(args)
+    elif args.workload == "train":
+        run_train(args)
     elif args.workload == "triplanar":
         run_triplanar(args)
     elif args.workload == "ntap":
