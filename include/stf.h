@@ -373,6 +373,7 @@ typedef struct {
 typedef struct { float lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac; } stf_adam_params;
 
 typedef enum {
+    STF_LATENT_KEEP = -1,           /* stf_neural_quantize: rebuild in the current format    */
     STF_LATENT_FP16 = 0,            /* inference latents FP16 (round to nearest even)        */
     STF_LATENT_FP8_E4M3 = 1         /* FP8 E4M3 with a per-grid FP32 scale = max|l| / 448   */
 } stf_latent_format;
@@ -399,6 +400,30 @@ stf_status stf_neural_train(stf_ctx ctx, stf_neural net, uint32_t steps, uint32_
  * give the texels.  loss: host float. */
 stf_status stf_neural_grad(stf_ctx ctx, stf_neural net, uint32_t step, uint32_t batch, uint64_t seed,
                            const int32_t* ex_ix, const int32_t* ex_iy, float* loss);
+/* Data-parallel training: one process per GPU, one replica of the network each (created
+ * from the same initial parameters).  Every optimiser step k of a run of `steps`:
+ *   1. each rank calls stf_neural_grad_range for its share [first, first + count) of the
+ *      step's `batch` Philox samples (sample ids are global and the loss is normalised by
+ *      the whole batch, so the ranks' gradients SUM to the batch gradient);
+ *   2. the caller sums the two gradient arrays of stf_neural_grad_buffers over the ranks in
+ *      place (an all-reduce on the context stream), the one exchange step of training;
+ *   3. each rank calls stf_neural_adam_step(k, steps): identical updates keep the replicas
+ *      identical.
+ * Then stf_neural_quantize rebuilds the inference form.  With one rank this is
+ * stf_neural_train.  Both calls are asynchronous on the context stream. */
+/* Replaces the gradient arrays with the gradients of samples [first, first + count) of
+ * the batch of optimiser step `step` (first + count <= batch <= 2^24; count may be 0).
+ * loss: nullable device float to which this part's share of the batch's mean squared
+ * error is added. */
+stf_status stf_neural_grad_range(stf_ctx ctx, stf_neural net, uint32_t step, uint32_t batch, uint32_t first,
+                                 uint32_t count, uint64_t seed, float* loss);
+/* Device addresses and lengths (FP32 elements) of the latent and MLP gradient arrays,
+ * owned by the network and valid until it is destroyed. */
+stf_status stf_neural_grad_buffers(stf_ctx ctx, stf_neural net, float** grad_latents, uint64_t* n_latents,
+                                   float** grad_mlp, uint64_t* n_mlp);
+/* Optimiser step k (0 <= k < steps) of a run of `steps` with the current gradients, which
+ * it consumes (zeroes); the learning-rate schedule is stf_neural_train's. */
+stf_status stf_neural_adam_step(stf_ctx ctx, stf_neural net, const stf_adam_params* adam, uint32_t k, uint32_t steps);
 /* Build the inference form (BF16 weights, FP16 or FP8 latents) from the FP32 masters. */
 stf_status stf_neural_quantize(stf_ctx ctx, stf_neural net, stf_latent_format fmt);
 /* Copy a block to / from host memory; bytes must equal the block size. Synchronous. */

@@ -81,7 +81,7 @@ class _Adam(C.Structure):
 
 
 NEURAL_BLOCKS = {"latents": 0, "mlp": 1, "grad_latents": 2, "grad_mlp": 3, "adam": 4, "scales": 5, "step": 6}
-LATENT_FORMATS = {"fp16": 0, "fp8": 1}
+LATENT_FORMATS = {"fp16": 0, "fp8": 1, "keep": -1}
 MLP_SIZE = 6792
 
 # every entry point declared in include/stf.h, with its ctypes signature
@@ -121,6 +121,9 @@ SIGNATURES = {
     "stf_neural_destroy": ([_P, _U64], _I),
     "stf_neural_train": ([_P, _U64, _U32, _U32, C.POINTER(_Adam), _U64, _P], _I),
     "stf_neural_grad": ([_P, _U64, _U32, _U32, _U64, _P, _P, C.POINTER(C.c_float)], _I),
+    "stf_neural_grad_range": ([_P, _U64, _U32, _U32, _U32, _U32, _U64, _P], _I),
+    "stf_neural_grad_buffers": ([_P, _U64, C.POINTER(_P), C.POINTER(_U64), C.POINTER(_P), C.POINTER(_U64)], _I),
+    "stf_neural_adam_step": ([_P, _U64, C.POINTER(_Adam), _U32, _U32], _I),
     "stf_neural_quantize": ([_P, _U64, _I], _I),
     "stf_neural_get": ([_P, _U64, _I, _P, C.c_size_t], _I),
     "stf_neural_set": ([_P, _U64, _I, _P, C.c_size_t], _I),
@@ -147,6 +150,19 @@ def lib() -> C.CDLL:
             fn.argtypes, fn.restype = args, res
         _lib = L
     return _lib
+
+
+class _CudaArray:
+    """A raw float32 device array, exposed through the CUDA array interface."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def _device_view(ptr: int, n: int, device: int):
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, n), device=torch.device("cuda", device))
 
 
 def _ptr(t) -> int | None:
@@ -440,7 +456,53 @@ class Context:
         return float(loss.value)
 
     def neural_quantize(self, net: int, fmt: str = "fp16"):
+        """fmt: "fp16", "fp8", or "keep" (rebuild in the current latent format)."""
         self._check(lib().stf_neural_quantize(self.h, net, LATENT_FORMATS[fmt]), self.h)
+
+    # data-parallel training: the ranks' gradient shares are summed between grad and Adam
+    def neural_grad_range(self, net: int, step: int, batch: int, first: int, count: int, seed: int = 1,
+                          loss=None):
+        """Gradients of samples [first, first + count) of step's batch (asynchronous); loss:
+        optional float32 cuda tensor (one element) that receives this share of the loss."""
+        self._check(lib().stf_neural_grad_range(self.h, net, step, batch, first, count, seed, _ptr(loss)), self.h)
+
+    def neural_grad_buffers(self, net: int):
+        """Zero-copy float32 cuda tensors over the network's latent and MLP gradient arrays."""
+        pl, nl, pm, nm = _P(), _U64(), _P(), _U64()
+        self._check(lib().stf_neural_grad_buffers(self.h, net, C.byref(pl), C.byref(nl), C.byref(pm), C.byref(nm)),
+                    self.h)
+        return _device_view(pl.value, nl.value, self.device), _device_view(pm.value, nm.value, self.device)
+
+    def neural_adam_step(self, net: int, k: int, steps: int, lr_latent: float = 1e-2, lr_mlp: float = 5e-3,
+                         beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, lr_min_frac: float = 1.0):
+        ap = _Adam(lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac)
+        self._check(lib().stf_neural_adam_step(self.h, net, C.byref(ap), k, steps), self.h)
+
+    def neural_train_dp(self, net: int, steps: int, batch: int, lr_latent: float = 1e-2, lr_mlp: float = 5e-3,
+                        seed: int = 1, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                        lr_min_frac: float = 1.0, group=None) -> np.ndarray:
+        """neural_train as one rank of a data-parallel job (torch.distributed, one process per
+        GPU, the context on the current torch stream): each rank computes its share of every
+        batch, the gradients are all-reduced (summed) in place, and every replica applies the
+        same Adam step.  Without an initialised process group it is a single replica.
+        Returns the per-step losses of the whole batch."""
+        import torch.distributed as dist
+        from .sharding import dp_train
+        torch = self.torch
+        world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+        rank = dist.get_rank(group) if world > 1 else 0
+        step0 = int(self.neural_get(net, "step", 0)[0])
+        dl, dm = self.neural_grad_buffers(net)
+        losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=dl.device)
+        dp_train(steps, batch, rank, world,
+                 lambda k, first, count: self.neural_grad_range(net, step0 + k, batch, first, count, seed,
+                                                                losses[k:k + 1]),
+                 lambda: (dist.all_reduce(dl, group=group), dist.all_reduce(dm, group=group)),
+                 lambda k: self.neural_adam_step(net, k, steps, lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac))
+        if world > 1:
+            dist.all_reduce(losses, group=group)
+        self.neural_quantize(net, "keep")
+        return losses[:steps].cpu().numpy()
 
     def _neural_block_size(self, net: int, what: str, lat_total: int) -> int:
         return {"latents": lat_total, "grad_latents": lat_total, "mlp": MLP_SIZE, "grad_mlp": MLP_SIZE,

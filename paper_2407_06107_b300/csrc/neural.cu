@@ -733,8 +733,8 @@ __device__ __forceinline__ void grad_epilogue(uint32_t taddr, uint2 mask, uint8_
 }
 
 __global__ void __launch_bounds__(TR_ROWS, TR_CTAS_PER_SM)
-k_ntc_train_tc(NeuralView N, uint32_t step, uint32_t batch, RoundKeys K, float* loss_sum, uint32_t use_explicit,
-               const int32_t* ex_ix, const int32_t* ex_iy, uint32_t* status) {
+k_ntc_train_tc(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint32_t count, RoundKeys K,
+               float* loss_sum, uint32_t use_explicit, const int32_t* ex_ix, const int32_t* ex_iy, uint32_t* status) {
     extern __shared__ __align__(1024) uint8_t train_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_raw);
     const int t = threadIdx.x, warp = t >> 5;
@@ -769,11 +769,15 @@ k_ntc_train_tc(NeuralView N, uint32_t step, uint32_t batch, RoundKeys K, float* 
     uint32_t phase = 0;
     bool ok = true, any = false;
     float loss = 0.0f;
-    const uint32_t ntiles = (batch + TR_ROWS - 1) / TR_ROWS;
+    // samples first .. first + count - 1 of the step's batch (global ids: the ranks of a
+    // data-parallel step draw disjoint parts of the same batch); the loss and gradients are
+    // normalised by the whole batch, so the parts' gradients sum to the batch gradient
+    const uint32_t ntiles = (count + TR_ROWS - 1) / TR_ROWS;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const uint32_t acc0 = any ? 1u : 0u;    // accumulators: first tile of this CTA overwrites
-        const uint32_t k = tile * TR_ROWS + t;
-        const bool live = k < batch;
+        const uint32_t j = tile * TR_ROWS + t;
+        const bool live = j < count;
+        const uint32_t k = first + j;
         int ix = 0, iy = 0;
         if (live) {
             if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
@@ -938,14 +942,15 @@ k_ntc_train_tc(NeuralView N, uint32_t step, uint32_t batch, RoundKeys K, float* 
 }
 
 // ------------------------------------------------------------------ launchers
-cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint64_t seed, float* loss_sum,
-                             const int32_t* ex_ix, const int32_t* ex_iy, int num_sms, uint32_t* status,
-                             cudaStream_t st) {
-    const uint32_t tiles = (batch + TR_ROWS - 1) / TR_ROWS;
+cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint32_t first, uint32_t count,
+                             uint64_t seed, float* loss_sum, const int32_t* ex_ix, const int32_t* ex_iy, int num_sms,
+                             uint32_t* status, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const uint32_t tiles = (count + TR_ROWS - 1) / TR_ROWS;
     const uint32_t cap = (uint32_t)num_sms * TR_CTAS_PER_SM;
     const int grid = (int)(tiles < cap ? tiles : cap);
     cudaFuncSetAttribute(k_ntc_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
-    k_ntc_train_tc<<<grid, TR_ROWS, sizeof(TrainSmem), st>>>(N, step, batch, expand_key(seed), loss_sum,
+    k_ntc_train_tc<<<grid, TR_ROWS, sizeof(TrainSmem), st>>>(N, step, batch, first, count, expand_key(seed), loss_sum,
                                                              ex_ix != nullptr, ex_ix, ex_iy, status);
     return cudaGetLastError();
 }

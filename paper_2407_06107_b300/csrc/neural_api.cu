@@ -48,6 +48,27 @@ stf_status quantize(stf_ctx c, NeuralRec& r, int fmt) {
     return STF_OK;
 }
 
+stf_status check_adam(stf_ctx c, const stf_adam_params* ap) {
+    if (!ap) return fail(c, STF_ERR_INVALID_ARG, "adam parameters are required");
+    if (!(ap->lr_min_frac >= 0.0f && ap->lr_min_frac <= 1.0f))
+        return fail(c, STF_ERR_INVALID_ARG, "lr_min_frac must lie in [0, 1]");
+    return STF_OK;
+}
+
+// Optimiser step k of a run of `steps`: Adam on the latents and on the MLP with the
+// half-cosine learning-rate factor (1 when lr_min_frac = 1); consumes the gradients.
+cudaError_t adam_update(stf_ctx c, NeuralRec& r, const stf_adam_params& ap, uint32_t k, uint32_t steps) {
+    const int t = (int)r.step + 1;
+    const double f = ap.lr_min_frac, fk = f + (1.0 - f) * 0.5 * (1.0 + std::cos(M_PI * (double)k / (double)steps));
+    cudaError_t e = stf::launch_adam(r.view.lat32, r.view.dlat, r.m_lat, r.v_lat, r.lat_total,
+                                     (float)(ap.lr_latent * fk), ap.beta1, ap.beta2, ap.eps, t, c->num_sms, c->stream);
+    if (e == cudaSuccess)
+        e = stf::launch_adam(r.view.mlp32, r.view.grad32, r.m_mlp, r.v_mlp, MLP_N, (float)(ap.lr_mlp * fk), ap.beta1,
+                             ap.beta2, ap.eps, t, c->num_sms, c->stream);
+    r.step++;
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -132,11 +153,9 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
-    if (!ap) return fail(c, STF_ERR_INVALID_ARG, "adam parameters are required");
+    if (stf_status s = check_adam(c, ap); s != STF_OK) return s;
     if (!r->trainable) return fail(c, STF_ERR_UNSUPPORTED, "created without targets");
     if (batch < 1 || batch > (1u << 24)) return fail(c, STF_ERR_INVALID_ARG, "batch must be 1..2^24");
-    if (!(ap->lr_min_frac >= 0.0f && ap->lr_min_frac <= 1.0f))
-        return fail(c, STF_ERR_INVALID_ARG, "lr_min_frac must lie in [0, 1]");
     if (steps == 0) return STF_OK;
     CurrentDevice cd(c->device);
     if (r->loss_cap < steps) {
@@ -149,18 +168,9 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.grad32, 0, MLP_N * 4, c->stream) : e;
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.dlat, 0, r->lat_total * 4, c->stream) : e;
     for (uint32_t k = 0; k < steps && e == cudaSuccess; ++k) {
-        e = stf::launch_ntc_train(r->view, r->step, batch, seed, r->loss + k, nullptr, nullptr, c->num_sms,
-                                     c->d_status, c->stream);
-        const int t = (int)r->step + 1;
-        // half-cosine decay over this call's steps (factor 1 when lr_min_frac = 1)
-        const double f = ap->lr_min_frac, fk = f + (1.0 - f) * 0.5 * (1.0 + std::cos(M_PI * (double)k / (double)steps));
-        if (e == cudaSuccess)
-            e = stf::launch_adam(r->view.lat32, r->view.dlat, r->m_lat, r->v_lat, r->lat_total,
-                                 (float)(ap->lr_latent * fk), ap->beta1, ap->beta2, ap->eps, t, c->num_sms, c->stream);
-        if (e == cudaSuccess)
-            e = stf::launch_adam(r->view.mlp32, r->view.grad32, r->m_mlp, r->v_mlp, MLP_N, (float)(ap->lr_mlp * fk),
-                                 ap->beta1, ap->beta2, ap->eps, t, c->num_sms, c->stream);
-        r->step++;
+        e = stf::launch_ntc_train(r->view, r->step, batch, 0, batch, seed, r->loss + k, nullptr, nullptr, c->num_sms,
+                                  c->d_status, c->stream);
+        if (e == cudaSuccess) e = adam_update(c, *r, *ap, k, steps);
     }
     if (e == cudaSuccess && losses) e = cudaMemcpyAsync(losses, r->loss, steps * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "neural train");
@@ -187,7 +197,8 @@ stf_status stf_neural_grad(stf_ctx c, stf_neural h, uint32_t step, uint32_t batc
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.grad32, 0, MLP_N * 4, c->stream) : e;
     e = e == cudaSuccess ? cudaMemsetAsync(r->view.dlat, 0, r->lat_total * 4, c->stream) : e;
     if (e == cudaSuccess)
-        e = stf::launch_ntc_train(r->view, step, batch, seed, r->loss, ex_ix, ex_iy, c->num_sms, c->d_status, c->stream);
+        e = stf::launch_ntc_train(r->view, step, batch, 0, batch, seed, r->loss, ex_ix, ex_iy, c->num_sms, c->d_status,
+                                  c->stream);
     float l = 0.0f;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, r->loss, 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -196,13 +207,62 @@ stf_status stf_neural_grad(stf_ctx c, stf_neural h, uint32_t step, uint32_t batc
     return STF_OK;
 }
 
+stf_status stf_neural_grad_range(stf_ctx c, stf_neural h, uint32_t step, uint32_t batch, uint32_t first,
+                                 uint32_t count, uint64_t seed, float* loss) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    NeuralRec* r = find(c, h);
+    if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
+    if (!r->trainable) return fail(c, STF_ERR_UNSUPPORTED, "created without targets");
+    if (batch < 1 || batch > (1u << 24) || (uint64_t)first + count > batch)
+        return fail(c, STF_ERR_INVALID_ARG, "batch must be 1..2^24 and [first, first + count) inside it");
+    if (loss && ((uintptr_t)loss & 3u)) return fail(c, STF_ERR_INVALID_ARG, "loss must be 4-byte aligned");
+    CurrentDevice cd(c->device);
+    if (!loss && r->loss_cap < 1) {
+        stf_status s = dev_alloc(c, (void**)&r->loss, 4);
+        if (s != STF_OK) return s;
+        r->loss_cap = 1;
+    }
+    cudaError_t e = cudaMemsetAsync(r->view.grad32, 0, MLP_N * 4, c->stream);
+    e = e == cudaSuccess ? cudaMemsetAsync(r->view.dlat, 0, r->lat_total * 4, c->stream) : e;
+    if (e == cudaSuccess)
+        e = stf::launch_ntc_train(r->view, step, batch, first, count, seed, loss ? loss : r->loss, nullptr, nullptr,
+                                  c->num_sms, c->d_status, c->stream);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "neural grad range");
+}
+
+stf_status stf_neural_grad_buffers(stf_ctx c, stf_neural h, float** grad_latents, uint64_t* n_latents,
+                                   float** grad_mlp, uint64_t* n_mlp) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    NeuralRec* r = find(c, h);
+    if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
+    if (!grad_latents || !n_latents || !grad_mlp || !n_mlp) return fail(c, STF_ERR_INVALID_ARG, "null argument");
+    *grad_latents = r->view.dlat;
+    *n_latents = r->lat_total;
+    *grad_mlp = r->view.grad32;
+    *n_mlp = MLP_N;
+    return STF_OK;
+}
+
+stf_status stf_neural_adam_step(stf_ctx c, stf_neural h, const stf_adam_params* ap, uint32_t k, uint32_t steps) {
+    if (!c) return STF_ERR_INVALID_ARG;
+    NeuralRec* r = find(c, h);
+    if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
+    if (stf_status s = check_adam(c, ap); s != STF_OK) return s;
+    if (!r->trainable) return fail(c, STF_ERR_UNSUPPORTED, "created without targets");
+    if (k >= steps) return fail(c, STF_ERR_INVALID_ARG, "k must lie in [0, steps)");
+    CurrentDevice cd(c->device);
+    const cudaError_t e = adam_update(c, *r, *ap, k, steps);
+    return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "neural adam step");
+}
+
 stf_status stf_neural_quantize(stf_ctx c, stf_neural h, stf_latent_format fmt) {
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
-    if (fmt != STF_LATENT_FP16 && fmt != STF_LATENT_FP8_E4M3) return fail(c, STF_ERR_INVALID_ARG, "unknown latent format");
+    if (fmt != STF_LATENT_FP16 && fmt != STF_LATENT_FP8_E4M3 && fmt != STF_LATENT_KEEP)
+        return fail(c, STF_ERR_INVALID_ARG, "unknown latent format");
     CurrentDevice cd(c->device);
-    stf_status s = quantize(c, *r, (int)fmt);
+    stf_status s = quantize(c, *r, fmt == STF_LATENT_KEEP ? r->latent_fmt : (int)fmt);
     if (s != STF_OK) return s;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "neural quantize");

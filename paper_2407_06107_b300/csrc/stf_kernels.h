@@ -124,9 +124,9 @@ struct NeuralDecodeArgs {
     int inject_timeout;         // fault injection: issue no MMA and wait with a short limit
 };
 
-cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint64_t seed, float* loss_sum,
-                             const int32_t* ex_ix, const int32_t* ex_iy, int num_sms, uint32_t* status,
-                             cudaStream_t st);
+cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch, uint32_t first, uint32_t count,
+                             uint64_t seed, float* loss_sum, const int32_t* ex_ix, const int32_t* ex_iy, int num_sms,
+                             uint32_t* status, cudaStream_t st);
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
                         int t, int num_sms, cudaStream_t st);
 cudaError_t launch_ntc_quantize(const NeuralView& N, uint64_t lat_total, int fmt, unsigned int* amax_scratch,

@@ -133,6 +133,56 @@ def test_gradients_many_tiles_per_cta(ctx, net, data):
         assert np.linalg.norm(gm[a:b] - rgm[a:b]) <= 2e-3 * np.linalg.norm(rgm[a:b]), (a, b)
 
 
+def test_gradient_ranges_sum_to_the_batch_gradient(ctx, net, data):
+    # data-parallel shares: the gradients of [0, b) and [b, n) of one step's batch, each
+    # normalised by the whole batch, sum to the batch gradient (FP32 atomics order only);
+    # their losses sum to the batch loss
+    step, batch, seed, b = 4, 1001, 3, 377
+    full = ctx.neural_grad(net, step, batch, seed)
+    gm = ctx.neural_get(net, "grad_mlp", LAT_TOTAL).astype(np.float64)
+    gl = ctx.neural_get(net, "grad_latents", LAT_TOTAL).astype(np.float64)
+    parts_m, parts_l = np.zeros_like(gm), np.zeros_like(gl)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for first, count in ((0, b), (b, batch - b), (batch, 0)):
+        ctx.neural_grad_range(net, step, batch, first, count, seed, loss)
+        dl, dm = ctx.neural_grad_buffers(net)
+        torch.cuda.synchronize()
+        parts_m += dm.cpu().numpy()
+        parts_l += dl.cpu().numpy()
+    assert abs(float(loss) - full) <= 1e-5 * full
+    assert np.linalg.norm(parts_m - gm) <= 1e-5 * np.linalg.norm(gm)
+    assert np.linalg.norm(parts_l - gl) <= 1e-5 * np.linalg.norm(gl)
+    # the gradient views are the blocks stf_neural_get copies
+    dl, dm = ctx.neural_grad_buffers(net)
+    assert dl.numel() == LAT_TOTAL and dm.numel() == 6792
+    import paper_2407_06107_b300 as stf
+    with pytest.raises(stf.StfError) as e:
+        ctx.neural_grad_range(net, step, batch, 1000, 2, seed)
+    assert e.value.status == 1
+
+
+def test_single_replica_data_parallel_loop_matches_train(ctx, data):
+    # neural_train_dp without a process group: grad range + Adam per step, the same updates
+    # as neural_train up to FP32 atomics order
+    lat, mlp, tg = data
+    a, b = ctx.neural_create(R0, lat, mlp, tg), ctx.neural_create(R0, lat, mlp, tg)
+    la = ctx.neural_train(a, 12, 2048, 1e-2, 5e-3, seed=6, lr_min_frac=0.5)
+    lb = ctx.neural_train_dp(b, 12, 2048, 1e-2, 5e-3, seed=6, lr_min_frac=0.5)
+    np.testing.assert_allclose(lb, la, rtol=1e-4)
+    for what in ("latents", "mlp"):
+        pa = ctx.neural_get(a, what, LAT_TOTAL).astype(np.float64)
+        pb = ctx.neural_get(b, what, LAT_TOTAL).astype(np.float64)
+        p0 = (np.concatenate([x.ravel() for x in lat]) if what == "latents" else mlp).astype(np.float64)
+        assert np.linalg.norm(pb - pa) <= 1e-3 * np.linalg.norm(pa - p0), what
+    assert int(ctx.neural_get(b, "step", LAT_TOTAL)[0]) == 12
+    ix, iy = _all_texels()
+    ya = ctx.neural_decode(a, torch.from_numpy(ix).cuda(), torch.from_numpy(iy).cuda()).cpu().numpy()
+    yb = ctx.neural_decode(b, torch.from_numpy(ix).cuda(), torch.from_numpy(iy).cuda()).cpu().numpy()
+    assert np.abs(ya - yb).max() < 1e-2          # the inference form was rebuilt
+    ctx.neural_destroy(a)
+    ctx.neural_destroy(b)
+
+
 def test_adam_step_matches_oracle(ctx, net, data):
     lat, mlp, tg = data
     lr_l, lr_m, seed, batch = 1e-2, 5e-3, 5, 1024
