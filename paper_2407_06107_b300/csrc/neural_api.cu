@@ -74,6 +74,7 @@ cudaError_t adam_update(stf_ctx c, NeuralRec& r, const stf_adam_params& ap, uint
 extern "C" {
 
 stf_status stf_neural_create(stf_ctx c, const stf_neural_desc* d, stf_neural* out) {
+    stfi::NvtxRange nvtx_range("stf_neural_create");
     if (!c || !d || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
     *out = 0;
     if (d->tex_res < 1 || d->tex_res > 16384) return fail(c, STF_ERR_INVALID_ARG, "tex_res must be 1..16384");
@@ -150,6 +151,7 @@ stf_status stf_neural_destroy(stf_ctx c, stf_neural h) {
 
 stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t batch, const stf_adam_params* ap,
                             uint64_t seed, float* losses) {
+    stfi::NvtxRange nvtx_range("stf_neural_train");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
@@ -182,6 +184,7 @@ stf_status stf_neural_train(stf_ctx c, stf_neural h, uint32_t steps, uint32_t ba
 
 stf_status stf_neural_grad(stf_ctx c, stf_neural h, uint32_t step, uint32_t batch, uint64_t seed,
                            const int32_t* ex_ix, const int32_t* ex_iy, float* loss) {
+    stfi::NvtxRange nvtx_range("stf_neural_grad");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
@@ -209,6 +212,7 @@ stf_status stf_neural_grad(stf_ctx c, stf_neural h, uint32_t step, uint32_t batc
 
 stf_status stf_neural_grad_range(stf_ctx c, stf_neural h, uint32_t step, uint32_t batch, uint32_t first,
                                  uint32_t count, uint64_t seed, float* loss) {
+    stfi::NvtxRange nvtx_range("stf_neural_grad_range");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
@@ -244,6 +248,7 @@ stf_status stf_neural_grad_buffers(stf_ctx c, stf_neural h, float** grad_latents
 }
 
 stf_status stf_neural_adam_step(stf_ctx c, stf_neural h, const stf_adam_params* ap, uint32_t k, uint32_t steps) {
+    stfi::NvtxRange nvtx_range("stf_neural_adam_step");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
@@ -256,6 +261,7 @@ stf_status stf_neural_adam_step(stf_ctx c, stf_neural h, const stf_adam_params* 
 }
 
 stf_status stf_neural_quantize(stf_ctx c, stf_neural h, stf_latent_format fmt) {
+    stfi::NvtxRange nvtx_range("stf_neural_quantize");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
@@ -364,6 +370,7 @@ stf_status stf_neural_load(stf_ctx c, stf_neural h, const char* path) {
 }
 
 stf_status stf_neural_decode(stf_ctx c, stf_neural h, uint64_t n, const int32_t* ix, const int32_t* iy, float* y) {
+    stfi::NvtxRange nvtx_range("stf_neural_decode");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");
@@ -382,6 +389,7 @@ stf_status stf_neural_decode(stf_ctx c, stf_neural h, uint64_t n, const int32_t*
 stf_status stf_neural_filter_shade(stf_ctx c, stf_neural h, const stf_queries* q, const stf_derivs* d,
                                    stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
                                    uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_neural_filter_shade");
     if (!c) return STF_ERR_INVALID_ARG;
     NeuralRec* r = find(c, h);
     if (!r) return fail(c, STF_ERR_BAD_HANDLE, "unknown neural handle");

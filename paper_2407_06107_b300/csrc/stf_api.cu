@@ -266,6 +266,7 @@ static stf_status create_dct_texture(stf_ctx c, const stf_texture_desc* d, stf_t
 }
 
 stf_status stf_create_texture(stf_ctx c, const stf_texture_desc* d, stf_tex* out) {
+    stfi::NvtxRange nvtx_range("stf_create_texture");
     if (!c || !d || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
     *out = 0;
     if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
@@ -376,6 +377,7 @@ static stf_status enqueue_filter(stf_ctx c, const TexRec& rec, const stf_queries
 stf_status stf_filter_shade(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
                             stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
                             uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_filter_shade");
     TexRec* rec = nullptr;
     stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, &rec);
     if (s != STF_OK || q->n == 0) return s;
@@ -386,6 +388,7 @@ stf_status stf_filter_shade(stf_ctx c, stf_tex t, const stf_queries* q, const st
 stf_status stf_filter_shade_ex(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
                                const stf_filter_desc* fd, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
                                uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_filter_shade_ex");
     if (!c) return STF_ERR_INVALID_ARG;
     if (!fd) return fail(c, STF_ERR_INVALID_ARG, "null filter descriptor");
     if (fd->sampler != STF_SAMPLER_FRS && fd->sampler != STF_SAMPLER_FIS)
@@ -418,6 +421,7 @@ stf_status stf_filter_shade_ex(stf_ctx c, stf_tex t, const stf_queries* q, const
 stf_status stf_triplanar_shade(stf_ctx c, const stf_tex tex[3], float scale, const stf_tri_queries* q,
                                const stf_tri_derivs* d, stf_filter f, stf_mode m, stf_blend blend, stf_shade sh,
                                uint32_t spp, uint64_t seed, uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_triplanar_shade");
     if (!c) return STF_ERR_INVALID_ARG;
     if (!tex || !q || !out) return fail(c, STF_ERR_INVALID_ARG, "textures, queries and output must be non-null");
     TexRec* rec[3];
@@ -577,12 +581,14 @@ static stf_status host_pipeline(stf_ctx c, stf_tex t, const stf_queries* q, cons
 stf_status stf_filter_shade_host(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
                                  stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
                                  uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_filter_shade_host");
     return host_pipeline(c, t, q, d, f, m, sh, spp, seed, flags, out, false);
 }
 
 stf_status stf_filter_shade_host_async(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
                                        stf_filter f, stf_mode m, stf_shade sh, uint32_t spp, uint64_t seed,
                                        uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_filter_shade_host_async");
     return host_pipeline(c, t, q, d, f, m, sh, spp, seed, flags, out, true);
 }
 
@@ -631,6 +637,7 @@ stf_status stf_destroy_texture_table(stf_ctx c, stf_table t) {
 stf_status stf_filter_shade_table(stf_ctx c, stf_table t, const stf_queries* q, const uint32_t* tex_id,
                                   const stf_derivs* d, stf_filter f, stf_mode m, stf_shade sh, uint32_t spp,
                                   uint64_t seed, uint32_t flags, const stf_output* out) {
+    stfi::NvtxRange nvtx_range("stf_filter_shade_table");
     if (!c) return STF_ERR_INVALID_ARG;
     auto it = c->tables.find(t);
     if (it == c->tables.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown table handle");
@@ -662,6 +669,7 @@ stf_status stf_filter_shade_table(stf_ctx c, stf_table t, const stf_queries* q, 
 // ----------------------------------------------------------------------------- binning
 stf_status stf_bin_queries(stf_ctx c, uint64_t n, const float* u, const float* v, const uint32_t* tex_id,
                            uint32_t ntex, uint32_t tile_log2, uint32_t* order_out) {
+    stfi::NvtxRange nvtx_range("stf_bin_queries");
     if (!c) return STF_ERR_INVALID_ARG;
     if (n == 0) return STF_OK;
     if (!u || !v || !order_out || !aligned4(u) || !aligned4(v) || !aligned4(order_out))
@@ -684,6 +692,7 @@ stf_status stf_bin_queries(stf_ctx c, uint64_t n, const float* u, const float* v
 // --------------------------------------------------------------------------------- volume
 stf_status stf_create_volume(stf_ctx c, uint32_t nx, uint32_t ny, uint32_t nz, stf_format fmt,
                              float sigma_scale, const void* data, int on_device, stf_vol* out) {
+    stfi::NvtxRange nvtx_range("stf_create_volume");
     if (!c || !data || !out) return fail(c, STF_ERR_INVALID_ARG, "null argument");
     *out = 0;
     if (fmt != STF_FMT_R16F) return fail(c, STF_ERR_INVALID_ARG, "volumes are R16F");
@@ -720,6 +729,7 @@ stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t wid
                             uint32_t steps, stf_filter f, stf_mode m, uint32_t spp, uint64_t seed,
                             uint32_t flags, uint64_t pix_begin, uint64_t pix_count, float* out_T,
                             uint32_t* out_picks) {
+    stfi::NvtxRange nvtx_range("stf_march_volume");
     if (!c) return STF_ERR_INVALID_ARG;
     auto it = c->vol.find(v);
     if (it == c->vol.end()) return fail(c, STF_ERR_BAD_HANDLE, "unknown volume handle");

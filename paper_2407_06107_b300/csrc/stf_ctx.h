@@ -5,6 +5,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stf.h"
 #include "stf_kernels.h"
 
@@ -67,6 +69,14 @@ enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2, FAULT_MMA_TIMEOUT = 3 
 stf_status fail(stf_ctx c, stf_status s, const char* msg);
 stf_status cuda_fail(stf_ctx c, cudaError_t e, const char* where);
 stf_status dev_alloc(stf_ctx c, void** p, size_t bytes);
+// Names an entry point's host-side span in a profiler's timeline (NVTX ranges; no cost
+// beyond a function-pointer test unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 struct CurrentDevice {
     int prev = -1;
     explicit CurrentDevice(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }

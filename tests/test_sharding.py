@@ -163,3 +163,42 @@ def test_dp_train_calls_one_collective_per_step():
     dp_train(2, 10, 0, 1, lambda k, f, c: log.append(("g", k, f, c)), lambda: log.append(("r",)),
              lambda k: log.append(("a", k)))
     assert ("r",) not in log and log[0] == ("g", 0, 0, 10)
+
+
+def _dp_leave_worker(rank, world, port, out_dir):
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    from paper_2407_06107_b300.sharding import dp_train
+    g = np.zeros(64)
+
+    def grad(k, first, count):
+        g[:] = k + rank
+
+    def allreduce():
+        dist.all_reduce(torch.from_numpy(g))
+
+    def adam(k):
+        if rank == 1 and k == 1:
+            os._exit(0)          # this rank leaves between steps, with no collective in flight
+    t0 = time.time()
+    try:
+        dp_train(5, 10, rank, world, grad, allreduce, adam)
+        result = "finished"
+    except Exception:            # the surviving rank's next collective fails (closed peer / timeout)
+        result = "error"
+    with open(os.path.join(out_dir, f"rank{rank}"), "w") as f:
+        f.write(f"{result} {time.time() - t0:.3f}")
+    os._exit(0)                  # the group cannot be torn down without its peer
+
+
+@pytest.mark.timeout(180)
+def test_rank_leaving_between_steps_ends_the_others_next_collective(tmp_path):
+    # failure detection on the host: when one data-parallel rank exits after step 1, the other
+    # learns of it at step 2's all-reduce, which raises within the process group's timeout
+    # instead of hanging
+    mp.spawn(_dp_leave_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    result, secs = open(tmp_path / "rank0").read().split()
+    assert result == "error" and float(secs) < 60.0
+    assert not (tmp_path / "rank1").exists()
