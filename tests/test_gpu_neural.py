@@ -281,3 +281,32 @@ def test_cosine_schedule_validation(ctx, net):
     with pytest.raises(stf.StfError) as e:
         ctx.neural_train(net, 2, 64, lr_min_frac=1.5)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "fp8"])
+def test_neural_full_size_sampled(ctx, fmt):
+    """The bench's neural launch: the 4096^2 learned texture (latent grids 1024^2 .. 128^2),
+    2^24 uniform queries without derivatives, stochastic B-spline, 8 spp, GGX, decoded once
+    per sample on the tensor cores; 1500 sampled queries checked one by one against the
+    oracle with their own ids."""
+    grids, R = (1024, 512, 256, 128), 4096
+    lat, mlp = synth.ntc_init(grids, 104)
+    mlp[2048:2112] = 0.02
+    mlp[6784:6792] = 0.5           # outputs around mid-range: upright normals, non-zero shading
+    net = ctx.neural_create(R, lat, mlp)
+    if fmt == "fp8":
+        ctx.neural_quantize(net, "fp8")
+    q = synth.queries_uniform(1 << 24, 9)
+    u, v = torch.from_numpy(q.u).cuda(), torch.from_numpy(q.v).cuda()
+    r, g, b = ctx.neural_filter_shade(net, u, v, None, "bspline", "stochastic", "ggx", spp=8, seed=1)
+    got = torch.stack([r, g, b], 1).cpu().numpy().astype(np.float64)
+    ctx.neural_destroy(net)
+    idx = np.sort(np.random.default_rng(8).choice(q.n, 1500, replace=False))
+    nt = oracle.NeuralTexture.inference_form(R, lat, mlp, fmt)
+    ref = oracle.filter_shade(oracle.Texture(None, neural=nt), q.subset(idx), "bspline", "stochastic", "ggx", 8, 1,
+                              ids=idx)
+    assert (ref.rgb > 0).all(1).mean() > 0.99         # the comparison is not vacuous
+    err = np.abs(got[idx] - ref.rgb)
+    tight = (err <= 5e-4 * ref.mag + 1e-6).all(1)
+    assert tight.mean() >= 0.9, (tight.mean(), float((err / (ref.mag + 1e-9)).max()))
+    assert np.all(err <= 3e-2 * ref.mag + 1e-5), float((err / (ref.mag + 1e-9)).max())
