@@ -1,0 +1,64 @@
+"""Full-size sampled parity of the follow-on rows' bench launches on the 4096^2 material
+with MIPs: DCT6-compressed textures (2^24 material queries, 1 spp, as the DCT block times
+them) and stochastic EWA (2^22 anisotropic queries, 8 spp, as the anisotropic block times
+them).  A seeded sample of queries is re-evaluated by the FP64 oracle one by one with
+their own Philox ids.  The specialised kernels report no picks, so decisions within 1e-6
+of an FP64 boundary are excused by their distance."""
+import numpy as np
+import pytest
+
+import oracle
+import stf_synth as synth
+from gpu_util import assert_values
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+REL_DCT = 3e-5      # the DCT tests' bound: the per-texel inverse DCT adds FP32 roundings
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_06107_b300 as stf
+    c = stf.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def material():
+    return synth.material_rgba8(4096, 102)
+
+
+def _sampled(ctx, h, otex, q, filter, mode, spp, seed, rel, n=1500):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = [t(q.dudx), t(q.dvdx), t(q.dudy), t(q.dvdy)]
+    r, g, b, _ = ctx.filter_shade(h, t(q.u), t(q.v), d, filter, mode, "ggx", spp, seed)
+    idx = np.sort(np.random.default_rng(77).choice(q.n, n, replace=False))
+    rgb = torch.stack([r, g, b], 1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    ref = oracle.filter_shade(otex, q.subset(idx), filter, mode, "ggx", spp, seed, ids=idx)
+    assert (ref.rgb > 0).any(1).mean() > 0.99          # the comparison is not vacuous
+    near = ref.bdist < 1e-6
+    assert near.sum() <= 3
+    assert_values(rgb, ref.rgb, near, rel=rel, scale=ref.mag)
+
+
+@pytest.mark.parametrize("filter", ["linear", "bspline"])
+def test_dct_full_size_sampled(ctx, material, filter):
+    blocks = synth.dct_compress(material)
+    h = ctx.create_texture_dct(blocks, 4096, 4096)
+    otex = oracle.Texture([lv.shape[:2] for lv in material.albedo_rough], dct=blocks)
+    q = synth.queries_uniform(1 << 24, 1, res=4096, lod_range=8.0)
+    _sampled(ctx, h, otex, q, filter, "stochastic", 1, 1, REL_DCT)
+    ctx.destroy_texture(h)
+
+
+def test_ewa_full_size_sampled(ctx, material):
+    h = ctx.create_texture(material.albedo_rough, material.normal)
+    otex = oracle.Texture(material.albedo_rough, material.normal)
+    q = synth.queries_aniso(1 << 22, 44, res=4096, lod_range=3.0, max_aniso=32.0)
+    _sampled(ctx, h, otex, q, "ewa", "stochastic", 8, 7, 1e-5, n=1000)
+    ctx.destroy_texture(h)
