@@ -97,7 +97,7 @@ def lib():
             C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, P, C.c_int, C.c_float]
         L.orc_march.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_float, P, C.c_uint32, C.c_uint32,
                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
-                                C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
+                                C.c_uint64, C.c_uint64, P, P, P, P, P, C.c_int]
         L.orc_triplanar_shade.argtypes = [P, C.c_uint64] + [P] * 13 + [
             C.c_float, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P, C.c_int]
         D = C.c_double
@@ -108,6 +108,7 @@ def lib():
         L.orc_e4m3_value.restype = D
         L.orc_ntc_features.argtypes = [C.POINTER(_NeuralTex), C.c_uint64, P, P, P]
         L.orc_ntc_decode.argtypes = [C.POINTER(_NeuralTex), C.c_uint64, P, P, P, P]
+        L.orc_ntc_decode_exact.argtypes = [C.POINTER(_NeuralTex), C.c_uint64, P, P, P]
         L.orc_ntc_loss_grad.argtypes = [C.POINTER(_NeuralTex)] + [P] * 7 + [C.c_uint64, P, P, C.c_int] + [P] * 7
         L.orc_ntc_loss_grad.restype = D
         L.orc_adam.argtypes = [C.c_uint64, P, P, P, P, C.c_int, D, D, D, D]
@@ -348,8 +349,9 @@ def triplanar_shade(texs, q, scale: float, filter: str, mode: str, blend: str, s
 @dataclass
 class MarchResult:
     T: np.ndarray               # (count,) float64
-    picks: np.ndarray | None    # (count, spp, steps) uint32 (z<<20 | y<<10 | x)
+    picks: np.ndarray | None    # (count, spp, steps) uint32 (z<<20 | y<<10 | x), FP32 decisions (diagnostic)
     bdist: np.ndarray
+    picks64: np.ndarray | None = None  # same, FP64 decisions (the ones the estimate uses)
 
 
 def march(vol: np.ndarray, sigma_scale: float, cam: np.ndarray, width: int, height: int,
@@ -367,13 +369,14 @@ def march(vol: np.ndarray, sigma_scale: float, cam: np.ndarray, width: int, heig
     T = np.zeros(cnt)
     bd = np.zeros(cnt)
     picks = np.zeros((cnt, spp, steps), dtype=np.uint32) if want_picks else None
+    picks64 = np.zeros((cnt, spp, steps), dtype=np.uint32) if want_picks else None
     cam = np.ascontiguousarray(cam, dtype=np.float32)
     rc = lib().orc_march(nx, ny, nz, _p(vol.view(np.uint16)), float(sigma_scale), _p(cam), width,
                          height, steps, FILTERS[filter], MODES[mode], spp, seed, flags, pix_begin,
-                         cnt, _p(pix_ids), _p(T), _p(picks), _p(bd), nthreads or nthreads_default())
+                         cnt, _p(pix_ids), _p(T), _p(picks), _p(picks64), _p(bd), nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("oracle: invalid march arguments")
-    return MarchResult(T, picks, bd)
+    return MarchResult(T, picks, bd, picks64)
 
 
 # ----------------------------------------------------------------------------- learned form
@@ -473,8 +476,8 @@ def ntc_features(nt: NeuralTexture, ix, iy) -> np.ndarray:
 
 def ntc_decode(nt: NeuralTexture, ix, iy):
     """(y [n, 8] float64, rdist [n]): decode, and the smallest rounding margin of its hidden
-    BF16 activations (distance to the rounding midpoint / (sqrt(K) sum|w x|)); a margin
-    below ~4 * 2^-24 can round differently under another FP32 summation order."""
+    BF16 activations (distance to the rounding midpoint / (sqrt(K+1) sum|w x|)); a margin of
+    a fraction of 2^-24 can round differently under another FP32 summation order."""
     ix = np.ascontiguousarray(ix, dtype=np.int32)
     iy = np.ascontiguousarray(iy, dtype=np.int32)
     y = np.zeros((len(ix), 8))
@@ -482,6 +485,21 @@ def ntc_decode(nt: NeuralTexture, ix, iy):
     s = nt._struct()
     lib().orc_ntc_decode(C.byref(s), len(ix), _p(ix), _p(iy), _p(y), _p(rd))
     return y, rd
+
+
+def ntc_decode_exact(tex_res: int, lat32, mlp32, ix, iy) -> np.ndarray:
+    """y [n, 8] float64: the network's exact value at texels (ix, iy) -- FP64 bilinear
+    features of the FP32 master latents and an FP64 forward pass of the FP32 master MLP, with
+    no BF16, FP16 or FP8 rounding anywhere.  The reference the inference forms' decode error
+    is stated against."""
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    nt = NeuralTexture(tex_res, [np.asarray(g, np.float32) for g in lat32],
+                       np.asarray(mlp32, np.float32).astype(np.float64), "fp32")
+    y = np.zeros((len(ix), 8))
+    s = nt._struct()
+    lib().orc_ntc_decode_exact(C.byref(s), len(ix), _p(ix), _p(iy), _p(y))
+    return y
 
 
 def ntc_loss_grad(tex_res: int, lat32, mlp32, targets, ix, iy, round_bf16: bool = True,

@@ -141,6 +141,26 @@ void neural_decode(const NeuralTex& N, int ix, int iy, double y[8], double* rdis
     mlp_forward(*N.mlp, x, h1, h2, y, rdist, true);
 }
 
+// The network's exact value at texel (ix, iy): FP64 bilinear features of the latents as
+// stored in N (the FP32 master values for the exact form) and an FP64 forward pass of the
+// MLP in N with no BF16 rounding anywhere -- the reference the quantised inference forms
+// (BF16 weights and activations, FP16 or FP8 latents) are measured against.
+void neural_decode_exact(const NeuralTex& N, int ix, int iy, double y[8]) {
+    double x[32];
+    for (int g = 0; g < 4; ++g) {
+        const double s = (double)N.res[g] / (double)N.tex_res;
+        const double px = ((double)ix + 0.5) * s - 0.5, py = ((double)iy + 0.5) * s - 0.5;
+        const double fx = std::floor(px), fy = std::floor(py), tx = px - fx, ty = py - fy;
+        const int x0 = wrapi((int)fx, N.res[g]), y0 = wrapi((int)fy, N.res[g]);
+        const int x1 = wrapi((int)fx + 1, N.res[g]), y1 = wrapi((int)fy + 1, N.res[g]);
+        for (int c = 0; c < 8; ++c)
+            x[8 * g + c] = (1 - tx) * (1 - ty) * N.latent(g, x0, y0, c) + tx * (1 - ty) * N.latent(g, x1, y0, c) +
+                           (1 - tx) * ty * N.latent(g, x0, y1, c) + tx * ty * N.latent(g, x1, y1, c);
+    }
+    double h1[64], h2[64];
+    mlp_forward(*N.mlp, x, h1, h2, y, nullptr, false);
+}
+
 }  // namespace orc
 
 // ===================================================================== C entry points
@@ -164,6 +184,11 @@ void orc_ntc_decode(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, cons
         orc::neural_decode(*N, ix[i], iy[i], y + 8 * i, &rd);
         if (rdist) rdist[i] = rd;
     }
+}
+
+// exact FP64 decode of n texels (see neural_decode_exact): y[n*8]
+void orc_ntc_decode_exact(const orc::NeuralTex* N, uint64_t n, const int32_t* ix, const int32_t* iy, double* y) {
+    for (uint64_t i = 0; i < n; ++i) orc::neural_decode_exact(*N, ix[i], iy[i], y + 8 * i);
 }
 
 // Loss and gradients of one training batch.  Latents are FP32 master values (latent_fmt

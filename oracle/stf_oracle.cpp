@@ -137,12 +137,29 @@ double k_bc(double B, double C, double d) {
                 (-12.0 * B - 48.0 * C) * d + (8.0 * B + 24.0 * C)) / 6.0;
     return 0.0;
 }
+// The filters the lookups use, with the signed cubics written as products of their root
+// factors: the same polynomials as k_keys(-1/2) and k_bc(1/3, 1/3), but a value next to a
+// root keeps its relative precision (the expanded outer piece cancels near its double root
+// at |d| = 2, and the ratio of such small weights decides a positivized class choice).
+//   Keys a:   inner (d-1)((a+2) d^2 - d - 1), outer a (d-1)(d-2)^2
+//   BC(B, C): outer (d-2)^2 ((-B-6C) d + 2B + 6C) / 6; for B = C = 1/3, (d-2)^2 (8-7d) / 18;
+//             the inner piece stays above B/6 = 1/18 and keeps its expanded form.
 double kernel64(int f, double d) {
     switch (f) {
         case F_LINEAR: return k_tent(d);
         case F_BSPLINE: return k_bspline(d);
-        case F_CATMULL_ROM: return k_keys(-0.5, d);
-        case F_MITCHELL: return k_bc(1.0 / 3.0, 1.0 / 3.0, d);
+        case F_CATMULL_ROM: {
+            d = std::fabs(d);
+            if (d < 1.0) return (d - 1.0) * (1.5 * d * d - d - 1.0);
+            if (d < 2.0) return -0.5 * (d - 1.0) * (d - 2.0) * (d - 2.0);
+            return 0.0;
+        }
+        case F_MITCHELL: {
+            d = std::fabs(d);
+            if (d < 1.0) return k_bc(1.0 / 3.0, 1.0 / 3.0, d);
+            if (d < 2.0) return (d - 2.0) * (d - 2.0) * (8.0 - 7.0 * d) / 18.0;
+            return 0.0;
+        }
     }
     return 0.0;
 }
@@ -151,31 +168,26 @@ int first_tap(int f) { return f == F_LINEAR ? 0 : -1; }   // offset of tap 0 fro
 bool signed_filter(int f) { return f == F_CATMULL_ROM || f == F_MITCHELL; }
 
 // ------------------------------------------------------------------ FP32 decision weights
-// Per-axis weights in float (the B-spline polynomials of the paper's bicubic/tricubic
-// listings; the cubic kernels evaluated at the four tap distances 1+t, t, 1-t, 2-t), in
-// Horner form with fused multiply-adds -- the listings do not fix contraction, and a
-// single-rounded fmaf is reproducible on any IEEE machine.  Used only to take decisions.
-float k32_cubic(int f, float d) {
-    float c3, c2, c0, q3, q2, q1, q0;
-    if (f == F_CATMULL_ROM) {
-        c3 = 1.5f; c2 = -2.5f; c0 = 1.0f; q3 = -0.5f; q2 = 2.5f; q1 = -4.0f; q0 = 2.0f;
-    } else {   // Mitchell B = C = 1/3
-        c3 = 7.0f / 6.0f; c2 = -2.0f; c0 = 8.0f / 9.0f;
-        q3 = -7.0f / 18.0f; q2 = 2.0f; q1 = -10.0f / 3.0f; q0 = 16.0f / 9.0f;
-    }
-    if (d < 1.0f) { float a = std::fmaf(c3, d, c2); a = a * d; return std::fmaf(a, d, c0); }
-    if (d < 2.0f) { float a = std::fmaf(q3, d, q2); a = std::fmaf(a, d, q1); return std::fmaf(a, d, q0); }
-    return 0.0f;
-}
+// Per-axis weights in float at the four tap distances 1+t, t, 1-t, 2-t (cubic) or 1-t, t
+// (tent), in the forms a float implementation should use: the B-spline polynomials of the
+// paper's bicubic/tricubic listings, and for the two signed cubics the pieces factored at
+// their roots, so that a weight close to zero keeps its relative precision (the expanded
+// outer polynomial loses it near the double root at |x| = 2, and only the ratio of such
+// small weights decides the class choice of a positivized negative sample).  With s = 1-t:
+//   Keys a = -1/2 (Catmull-Rom): outer a (x-1)(x-2)^2, inner (x-1)(3x^2/2 - x - 1)
+//     w0 = -t s^2 / 2, w1 = s (1 + t (1 - 3t/2)), w2 = t (1 + s (1 - 3s/2)), w3 = -s t^2 / 2
+//   Mitchell-Netravali BC(1/3, 1/3): outer (x-2)^2 (8 - 7x) / 18, inner 7x^3/6 - 2x^2 + 8/9
+//     w0 = s^2 (1 - 7t) / 18, w3 = t^2 (7t - 6) / 18, w1, w2 the inner piece at t and s
+//     (it stays above 1/18, so its Horner form loses nothing).
+// Single-rounded fmaf is reproducible on any IEEE machine.  Used only to take decisions.
 int weights32(int f, float t, float w[4]) {
     if (f == F_LINEAR) { w[0] = 1.0f - t; w[1] = t; return 2; }
     if (f == F_BSPLINE) {
         const float s = 1.0f / 6.0f;
-        float t2 = t * t, t3 = t * t2;
+        float t2 = t * t;
         float a;
         // the listing's polynomials in Horner form with fused multiply-adds:
         //   (1-t)^3, t^2 (3t - 6) + 4, t (t (3 - 3t) + 3) + 1, t^3, each times 1/6
-        (void)t3;
         float omt = 1.0f - t;
         w[0] = s * ((omt * omt) * omt);
         a = std::fmaf(3.0f, t, -6.0f); w[1] = s * std::fmaf(t2, a, 4.0f);
@@ -183,8 +195,20 @@ int weights32(int f, float t, float w[4]) {
         w[3] = s * (t2 * t);
         return 4;
     }
-    w[0] = k32_cubic(f, 1.0f + t); w[1] = k32_cubic(f, t);
-    w[2] = k32_cubic(f, 1.0f - t); w[3] = k32_cubic(f, 2.0f - t);
+    const float s = 1.0f - t, t2 = t * t, s2 = s * s;
+    if (f == F_CATMULL_ROM) {
+        w[0] = (-0.5f * t) * s2;
+        w[1] = s * std::fmaf(t, std::fmaf(-1.5f, t, 1.0f), 1.0f);
+        w[2] = t * std::fmaf(s, std::fmaf(-1.5f, s, 1.0f), 1.0f);
+        w[3] = (-0.5f * s) * t2;
+        return 4;
+    }
+    // Mitchell B = C = 1/3
+    const float k18 = 1.0f / 18.0f, c3 = 7.0f / 6.0f, c2 = -2.0f, c0 = 8.0f / 9.0f;
+    w[0] = (s2 * std::fmaf(-7.0f, t, 1.0f)) * k18;
+    w[1] = std::fmaf(std::fmaf(c3, t, c2) * t, t, c0);
+    w[2] = std::fmaf(std::fmaf(c3, s, c2) * s, s, c0);
+    w[3] = (t2 * std::fmaf(7.0f, t, -6.0f)) * k18;
     return 4;
 }
 
@@ -252,6 +276,30 @@ int pick64(const double* w, int n, double xi, int cls, double* bdist) {
         if (k < n - 1) bd = std::min(bd, std::fabs(xi - ck));
         if (!found && xi < ck) { pick = k; found = true; }
     }
+    if (bdist) *bdist = std::min(*bdist, bd);
+    return pick;
+}
+
+// Sample reuse in FP64: the pick of pick64 over all taps, and the uniform remapped into the
+// chosen interval, xi' = (xi - c_{k-1}) / (c_k - c_{k-1}) on the normalised CDF c; *width =
+// c_k - c_{k-1}.  `scale` is the width of the interval the incoming xi was itself remapped
+// from, so scale * |xi - c_j| is the distance of the original uniform to this boundary.
+int pick64_reuse(const double* w, int n, double xi, double* remapped, double* width, double scale,
+                 double* bdist) {
+    double S = 0.0, C[4];
+    for (int k = 0; k < n; ++k) { S += std::fabs(w[k]); C[k] = S; }
+    int pick = n - 1;
+    bool found = false;
+    double lo = 0.0, hi = 1.0, prev = 0.0, bd = 1e30;
+    for (int k = 0; k < n; ++k) {
+        const double ck = k == n - 1 ? 1.0 : C[k] / S;
+        if (k < n - 1) bd = std::min(bd, scale * std::fabs(xi - ck));
+        if (!found && xi < ck) { pick = k; found = true; lo = prev; hi = ck; }
+        prev = ck;
+    }
+    if (!found) { lo = n > 1 ? C[n - 2] / S : 0.0; hi = 1.0; }
+    *width = hi - lo;
+    *remapped = (xi - lo) / (hi - lo);
     if (bdist) *bdist = std::min(*bdist, bd);
     return pick;
 }
@@ -792,6 +840,51 @@ void run_query_gauss(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, in
     if (O.bdist) O.bdist[q] = bd;
 }
 
+// The same decisions as the FP64 estimate, taken in FP32 the way a float implementation
+// takes them (fmaf weights, float CDF sums and compares): diagnostics only.  pk[0] is the
+// positive (or only) pick, pk[1] the negative pick of positivization.
+void picks_fp32(const Tex& T, int filter, int mode, uint32_t flags, float x, float y, int l0, float fr,
+                const float a[5], const float b[5], uint32_t* pk) {
+    const int nt = ntaps(filter), ft = first_tap(filter);
+    const float xl = a[2];
+    float ru = a[2];
+    int lvl = l0 + ((xl < fr) ? 1 : 0);
+    if (flags & FLAG_REUSE) { float r2; lvl = l0 + level_reuse(xl, fr, &r2); ru = r2; }
+    lvl = std::min(lvl, T.levels - 1);
+    const int W = T.width[lvl], H = T.height[lvl];
+    const Axis ax = axis_at(x, W), ay = axis_at(y, H);
+    float wx[4], wy[4];
+    pick_weights32(filter, ax.t, wx);
+    pick_weights32(filter, ay.t, wy);
+    auto pack = [&](int kx, int ky) {
+        return pack2d(lvl, wrapi(ax.i0 + ft + kx, W, T.address), wrapi(ay.i0 + ft + ky, H, T.address));
+    };
+    if (mode == M_STOCHASTIC) {
+        int kx, ky;
+        if (flags & FLAG_REUSE) {
+            float uy, dummy;
+            kx = pick32_reuse(wx, nt, ru, &uy);
+            ky = pick32_reuse(wy, nt, uy, &dummy);
+        } else {
+            kx = pick32(wx, nt, a[3], 0, nullptr);
+            ky = pick32(wy, nt, a[4], 0, nullptr);
+        }
+        pk[0] = pack(kx, ky);
+        return;
+    }
+    float Px, Nx, Py, Ny;
+    pick32(wx, nt, 0.0f, +1, &Px); pick32(wx, nt, 0.0f, -1, &Nx);
+    pick32(wy, nt, 0.0f, +1, &Py); pick32(wy, nt, 0.0f, -1, &Ny);
+    const float Wp = std::fmaf(Nx, Ny, Px * Py);
+    const float Wn = std::fmaf(Nx, Py, Px * Ny);
+    const int cp = (b[0] * Wp < Px * Py) ? +1 : -1;
+    pk[0] = pack(pick32(wx, nt, a[3], cp, nullptr), pick32(wy, nt, a[4], cp, nullptr));
+    if (Wn > 0.0f) {
+        const int cn = (b[3] * Wn < Px * Ny) ? +1 : -1;
+        pk[1] = pack(pick32(wx, nt, b[1], cn, nullptr), pick32(wy, nt, b[2], -cn, nullptr));
+    }
+}
+
 // keep (nullable, [spp]): samples with keep[s] == 0 add nothing (and report no picks) but
 // still count in the mean; the triplanar blend uses it to give each plane its own samples.
 void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filter, int mode, int smode,
@@ -864,12 +957,12 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
         double est[3] = {0, 0, 0};
 
         if (mode == M_NTAP_BEFORE || mode == M_NTAP_AFTER) {
-            // exact sum over both MIP levels and the full 2-D tap grid, FP64 weights
-            double wl[2] = {1.0 - (double)fr, (double)fr};
+            // exact sum over both MIP levels (FP64 lambda) and the full 2-D tap grid, FP64 weights
+            double wl[2] = {1.0 - fr64, fr64};
             Mat fm{}; fm.n = {0, 0, 0};
             double fsum[3] = {0, 0, 0};
             for (int li = 0; li < 2; ++li) {
-                int lvl = l0 + li;
+                int lvl = l0_64 + li;
                 if (wl[li] == 0.0 || lvl >= T.levels) continue;
                 int W = T.width[lvl], H = T.height[lvl];
                 Axis ax = axis_at(x, W), ay = axis_at(y, H);
@@ -902,115 +995,89 @@ void run_query(const Tex& T, const Queries& Q, uint64_t q, uint64_t id, int filt
                 for (int c = 0; c < 3; ++c) est[c] = fsum[c];
             }
         } else {
-            // stochastic MIP level: floor(lambda) + [xi < frac(lambda)] (stochastic lerp)
-            float xl = a[2];
-            float ru = a[2];                       // FLAG_REUSE: one uniform, remapped per decision
-            int lvl = l0 + ((xl < fr) ? 1 : 0);
-            if (flags & FLAG_REUSE) { float r2; lvl = l0 + level_reuse(xl, fr, &r2); ru = r2; }
-            int lvl64 = l0_64 + (((double)xl < fr64) ? 1 : 0);
-            if (lam64 > 0.0 && lam64 < T.levels - 1) bd = std::min(bd, std::fabs((double)xl - fr64));
-            lvl = std::min(lvl, T.levels - 1);
-            lvl64 = std::min(lvl64, T.levels - 1);
-            int W = T.width[lvl], H = T.height[lvl];
-            Axis ax = axis_at(x, W), ay = axis_at(y, H);
-            float wx[4], wy[4];
-            pick_weights32(filter, ax.t, wx);
-            pick_weights32(filter, ay.t, wy);
+            // Stochastic estimate (Eq. stochastic filtering; positivization, Sec. 2.2).  The
+            // FP64 decisions define it: the level floor(lambda) + [xi < frac(lambda)] (the
+            // stochastic lerp), then per axis the first tap whose normalised |w| prefix
+            // exceeds the uniform, all from FP64 weights at the exact texel position.  The
+            // same decisions taken in FP32 (float weights and CDF) are reported as `picks`,
+            // for diagnostics only; the estimate never depends on them.
+            const int L = T.levels;
+            const float xl = a[2];
+            // FLAG_REUSE: the level's uniform, remapped into the chosen interval, drives the
+            // next decision; `scale` maps a distance in the remapped uniform back to the
+            // original one, so `bd` stays a distance of the drawn uniform to a boundary
+            double ru64 = xl, scale = 1.0;
+            int lvl64;
+            if (flags & FLAG_REUSE) {
+                const bool up = (double)xl < fr64;
+                lvl64 = l0_64 + (up ? 1 : 0);
+                ru64 = up ? (double)xl / fr64 : ((double)xl - fr64) / (1.0 - fr64);
+                scale = up ? fr64 : 1.0 - fr64;
+            } else {
+                lvl64 = l0_64 + (((double)xl < fr64) ? 1 : 0);
+            }
+            if (lam64 > 0.0 && lam64 < L - 1) bd = std::min(bd, std::fabs((double)xl - fr64));
+            lvl64 = std::min(lvl64, L - 1);
+            const int W = T.width[lvl64], H = T.height[lvl64];
+            const Axis ax = axis_at(x, W), ay = axis_at(y, H);
             double wx64[4], wy64[4];
             for (int k = 0; k < nt; ++k) {
                 wx64[k] = kernel64(filter, ax.pos - (double)(ax.i0 + ft + k));
                 wy64[k] = kernel64(filter, ay.pos - (double)(ay.i0 + ft + k));
             }
-            // FP64 decisions are evaluated at the FP64 level when it agrees; otherwise the
-            // query is a counted boundary case and only the FP32 picks are reported.
-            auto texel = [&](int lv, int kx, int ky) {
-                int ix = wrapi(ax.i0 + ft + kx, W, T.address), iy = wrapi(ay.i0 + ft + ky, H, T.address);
-                return std::make_pair(ix, iy);
+            auto texel = [&](int kx, int ky) {
+                return std::make_pair(wrapi(ax.i0 + ft + kx, W, T.address), wrapi(ay.i0 + ft + ky, H, T.address));
             };
+            auto value = [&](std::pair<int, int> t, double o[3]) { shade(smode, fetch(T, lvl64, t.first, t.second, &rd), o); };
             if (mode == M_STOCHASTIC) {
-                float Sx, Sy;
-                float ux = a[3], uy = a[4];
                 int kx, ky;
                 if (flags & FLAG_REUSE) {
-                    ux = ru;
-                    kx = pick32_reuse(wx, nt, ux, &uy);
-                    float dummy;
-                    ky = pick32_reuse(wy, nt, uy, &dummy);
-                    pick32(wx, nt, 0.0f, 0, &Sx);
-                    pick32(wy, nt, 0.0f, 0, &Sy);
+                    double s1, s2, r1, r2;
+                    kx = pick64_reuse(wx64, nt, ru64, &r1, &s1, scale, &bd);
+                    ky = pick64_reuse(wy64, nt, r1, &r2, &s2, scale * s1, &bd);
                 } else {
-                    kx = pick32(wx, nt, a[3], 0, &Sx);
-                    ky = pick32(wy, nt, a[4], 0, &Sy);
+                    kx = pick64(wx64, nt, a[3], 0, &bd);
+                    ky = pick64(wy64, nt, a[4], 0, &bd);
                 }
-                int kx64 = pick64(wx64, nt, ux, 0, &bd);
-                int ky64 = pick64(wy64, nt, uy, 0, &bd);
-                auto t = texel(lvl, kx, ky);
-                Mat m = fetch(T, lvl, t.first, t.second, &rd);
+                const auto t = texel(kx, ky);
                 double o[3];
-                shade(smode, m, o);
-                double Wt = 1.0;
+                value(t, o);
+                double Wt = 1.0;     // W = sum |w| with the picked tap's sign (Eq. stochastic-sum)
                 if (sgn) {
                     double sx = 0, sy = 0;
                     for (int k = 0; k < nt; ++k) { sx += std::fabs(wx64[k]); sy += std::fabs(wy64[k]); }
                     Wt = sx * sy * ((wx64[kx] < 0) != (wy64[ky] < 0) ? -1.0 : 1.0);
                 }
                 for (int c = 0; c < 3; ++c) { est[c] = Wt * o[c]; mag[c] += std::fabs(est[c]); }
-                if (pk) pk[0] = pack2d(lvl, t.first, t.second);
-                if (pk64) {
-                    auto t64 = texel(lvl64, kx64, ky64);
-                    pk64[0] = lvl64 == lvl ? pack2d(lvl64, t64.first, t64.second) : NO_PICK - 1;
-                }
+                if (pk64) pk64[0] = pack2d(lvl64, t.first, t.second);
             } else {   // positivization: one sample from each sign set (Sec. 2.2)
-                float Px, Nx, Py, Ny;
-                pick32(wx, nt, 0.0f, +1, &Px); pick32(wx, nt, 0.0f, -1, &Nx);
-                pick32(wy, nt, 0.0f, +1, &Py); pick32(wy, nt, 0.0f, -1, &Ny);
-                float Wp = std::fmaf(Nx, Ny, Px * Py);
-                float Wn = std::fmaf(Nx, Py, Px * Ny);
-                double Px64 = 0, Nx64 = 0, Py64 = 0, Ny64 = 0;
+                double Px = 0, Nx = 0, Py = 0, Ny = 0;
                 for (int k = 0; k < nt; ++k) {
-                    (wx64[k] > 0 ? Px64 : Nx64) += std::fabs(wx64[k]);
-                    (wy64[k] > 0 ? Py64 : Ny64) += std::fabs(wy64[k]);
+                    (wx64[k] > 0 ? Px : Nx) += std::fabs(wx64[k]);
+                    (wy64[k] > 0 ? Py : Ny) += std::fabs(wy64[k]);
                 }
-                double Wp64 = Px64 * Py64 + Nx64 * Ny64, Wn64 = Px64 * Ny64 + Nx64 * Py64;
+                const double Wp = Px * Py + Nx * Ny, Wn = Px * Ny + Nx * Py;
                 // positive set: class (+,+) with probability Px Py / W+, else (-,-)
-                float xc = b[0];
-                int cx = (xc * Wp < Px * Py) ? +1 : -1;
-                int cx64 = ((double)xc < Px64 * Py64 / Wp64) ? +1 : -1;
-                if (Nx64 * Ny64 > 0) bd = std::min(bd, std::fabs((double)xc - Px64 * Py64 / Wp64));
-                int kx = pick32(wx, nt, a[3], cx, nullptr);
-                int ky = pick32(wy, nt, a[4], cx, nullptr);
-                int kx64 = pick64(wx64, nt, a[3], cx64, &bd);
-                int ky64 = pick64(wy64, nt, a[4], cx64, &bd);
-                auto tp = texel(lvl, kx, ky);
+                const double xc = b[0];
+                const int cp = (xc < Px * Py / Wp) ? +1 : -1;
+                if (Nx * Ny > 0) bd = std::min(bd, std::fabs(xc - Px * Py / Wp));
+                const auto tp = texel(pick64(wx64, nt, a[3], cp, &bd), pick64(wy64, nt, a[4], cp, &bd));
                 double o[3];
-                shade(smode, fetch(T, lvl, tp.first, tp.second, &rd), o);
-                for (int c = 0; c < 3; ++c) { est[c] = Wp64 * o[c]; mag[c] += std::fabs(est[c]); }
-                if (pk) pk[0] = pack2d(lvl, tp.first, tp.second);
-                if (pk64) {
-                    auto t64 = texel(lvl64, kx64, ky64);
-                    pk64[0] = lvl64 == lvl ? pack2d(lvl64, t64.first, t64.second) : NO_PICK - 1;
-                }
+                value(tp, o);
+                for (int c = 0; c < 3; ++c) { est[c] = Wp * o[c]; mag[c] += std::fabs(est[c]); }
+                if (pk64) pk64[0] = pack2d(lvl64, tp.first, tp.second);
                 // negative set: class (+,-) with probability Px Ny / W-, else (-,+)
-                if (Wn > 0.0f) {
-                    float xn = b[3];
-                    int nx_cls = (xn * Wn < Px * Ny) ? +1 : -1;
-                    int nx64 = ((double)xn < Px64 * Ny64 / Wn64) ? +1 : -1;
-                    if (Px64 * Ny64 > 0 && Nx64 * Py64 > 0)
-                        bd = std::min(bd, std::fabs((double)xn - Px64 * Ny64 / Wn64));
-                    int qx = pick32(wx, nt, b[1], nx_cls, nullptr);
-                    int qy = pick32(wy, nt, b[2], -nx_cls, nullptr);
-                    int qx64 = pick64(wx64, nt, b[1], nx64, &bd);
-                    int qy64 = pick64(wy64, nt, b[2], -nx64, &bd);
-                    auto tn = texel(lvl, qx, qy);
-                    shade(smode, fetch(T, lvl, tn.first, tn.second, &rd), o);
-                    for (int c = 0; c < 3; ++c) { est[c] -= Wn64 * o[c]; mag[c] += std::fabs(Wn64 * o[c]); }
-                    if (pk) pk[1] = pack2d(lvl, tn.first, tn.second);
-                    if (pk64) {
-                        auto t64 = texel(lvl64, qx64, qy64);
-                        pk64[1] = lvl64 == lvl ? pack2d(lvl64, t64.first, t64.second) : NO_PICK - 1;
-                    }
+                if (Wn > 0) {
+                    const double xn = b[3];
+                    const int cn = (xn < Px * Ny / Wn) ? +1 : -1;
+                    if (Px * Ny > 0 && Nx * Py > 0) bd = std::min(bd, std::fabs(xn - Px * Ny / Wn));
+                    const auto tn = texel(pick64(wx64, nt, b[1], cn, &bd), pick64(wy64, nt, b[2], -cn, &bd));
+                    value(tn, o);
+                    for (int c = 0; c < 3; ++c) { est[c] -= Wn * o[c]; mag[c] += std::fabs(Wn * o[c]); }
+                    if (pk64) pk64[1] = pack2d(lvl64, tn.first, tn.second);
                 }
             }
+            if (pk) picks_fp32(T, filter, mode, flags, x, y, l0, fr, a, b, pk);
         }
         for (int c = 0; c < 3; ++c) acc[c] += est[c];
     }
@@ -1055,11 +1122,11 @@ PlaneQuery plane_query(const TriQueries& Q, uint64_t q, int i, float scale) {
 }
 
 // the filter-before sum of one plane at (x, y): every tap of levels floor(lambda) and
-// floor(lambda) + 1 with FP64 weights, scaled by wb, added into fm
-void ntap_material(const Tex& T, float x, float y, float lam32, int filter, double wb, Mat& fm, double* rd) {
-    const int l0 = (int)std::floor(lam32);
-    const float fr = lam32 - (float)l0;
-    const double wl[2] = {1.0 - (double)fr, (double)fr};
+// floor(lambda) + 1 (FP64 lambda) with FP64 weights, scaled by wb, added into fm
+void ntap_material(const Tex& T, float x, float y, double lam64, int filter, double wb, Mat& fm, double* rd) {
+    const int l0 = (int)std::floor(lam64);
+    const double fr = lam64 - (double)l0;
+    const double wl[2] = {1.0 - fr, fr};
     const int nt = ntaps(filter), ft = first_tap(filter);
     for (int li = 0; li < 2; ++li) {
         const int lvl = l0 + li;
@@ -1142,7 +1209,7 @@ void run_query_triplanar(const Tex* const T[3], const TriQueries& TQ, uint64_t q
                     x = std::fmaf(jy, pq[i].d[2], std::fmaf(jx, pq[i].d[0], x));
                     y = std::fmaf(jy, pq[i].d[3], std::fmaf(jx, pq[i].d[1], y));
                 }
-                ntap_material(*T[i], x, y, lam32, filter, b64[i], fm, &rd);
+                ntap_material(*T[i], x, y, lam64, filter, b64[i], fm, &rd);
             }
             const double ln = std::sqrt(dot(fm.n, fm.n));
             fm.n = ln > 0 ? V3{fm.n.x / ln, fm.n.y / ln, fm.n.z / ln} : V3{0, 0, 1};
@@ -1224,7 +1291,7 @@ inline uint32_t pack3d(int x, int y, int z) { return ((uint32_t)z << 20) | ((uin
 // trilinear or tricubic B-spline, stochastically or with all taps).
 double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint32_t steps,
                     int filter, int mode, uint64_t seed, uint32_t flags, uint32_t spp,
-                    uint64_t pix, uint32_t s, uint32_t* picks, double* bd) {
+                    uint64_t pix, uint32_t s, uint32_t* picks, uint32_t* picks64, double* bd) {
     uint32_t px = (uint32_t)(pix % W), py = (uint32_t)(pix / W);
     float jx, jy;
     if (flags & FLAG_STRATIFIED) {
@@ -1257,6 +1324,7 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
     }
     if (!(tmin < tmax)) {
         if (picks) for (uint32_t k = 0; k < steps; ++k) picks[k] = NO_PICK;
+        if (picks64) for (uint32_t k = 0; k < steps; ++k) picks64[k] = NO_PICK;
         return 1.0;
     }
     float dt = (tmax - tmin) / (float)steps;
@@ -1289,26 +1357,35 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
                 uniforms6(rr, u6);
             }
             const float* uk = u6 + 3 * (k & 1);
-            int kk[3];
-            float ru = uk[0];                      // FLAG_REUSE: x, y, z from one remapped uniform
+            // per axis the first tap whose normalised FP64 |w| prefix exceeds the uniform
+            // (these decisions define the estimate); FLAG_REUSE: x, y, z from one uniform,
+            // remapped into each chosen interval.  The FP32 decisions go to `picks` only.
+            int kk[3], kk64[3];
+            float ru = uk[0];
+            double ru64 = uk[0], scale = 1.0;
             for (int a = 0; a < 3; ++a) {
                 float w[4];
                 double w64[4];
                 pick_weights32(filter, ax[a].t, w);
                 for (int j = 0; j < nt; ++j) w64[j] = kernel64(filter, ax[a].pos - (double)(ax[a].i0 + ft + j));
-                float xi = uk[a];
                 if (flags & FLAG_REUSE) {
-                    xi = ru;
-                    kk[a] = pick32_reuse(w, nt, xi, &ru);
+                    kk[a] = pick32_reuse(w, nt, ru, &ru);
+                    double r, width;
+                    kk64[a] = pick64_reuse(w64, nt, ru64, &r, &width, scale, bd);
+                    ru64 = r;
+                    scale *= width;
                 } else {
-                    kk[a] = pick32(w, nt, xi, 0, nullptr);
+                    kk[a] = pick32(w, nt, uk[a], 0, nullptr);
+                    kk64[a] = pick64(w64, nt, uk[a], 0, bd);
                 }
-                pick64(w64, nt, xi, 0, bd);
             }
-            int ix = ax[0].i0 + ft + kk[0], iy = ax[1].i0 + ft + kk[1], iz = ax[2].i0 + ft + kk[2];
-            sum_sigma += sig * vox(ix, iy, iz);
-            if (picks)
-                picks[k] = pack3d(wrapi(ix, V.nx, ADDR_CLAMP), wrapi(iy, V.ny, ADDR_CLAMP), wrapi(iz, V.nz, ADDR_CLAMP));
+            auto packv = [&](const int* kq) {
+                return pack3d(wrapi(ax[0].i0 + ft + kq[0], V.nx, ADDR_CLAMP), wrapi(ax[1].i0 + ft + kq[1], V.ny, ADDR_CLAMP),
+                              wrapi(ax[2].i0 + ft + kq[2], V.nz, ADDR_CLAMP));
+            };
+            sum_sigma += sig * vox(ax[0].i0 + ft + kk64[0], ax[1].i0 + ft + kk64[1], ax[2].i0 + ft + kk64[2]);
+            if (picks) picks[k] = packv(kk);
+            if (picks64) picks64[k] = packv(kk64);
         } else {
             double fsig = 0.0, favg = 0.0;
             for (int c = 0; c < nt; ++c) {
@@ -1330,6 +1407,7 @@ double march_sample(const Vol& V, const float* cam, uint32_t W, uint32_t H, uint
             sum_sigma += fsig;
             prod *= favg;
             if (picks) picks[k] = NO_PICK;
+            if (picks64) picks64[k] = NO_PICK;
         }
     }
     if (mode == M_NTAP_AFTER) return prod;
@@ -1493,7 +1571,8 @@ int orc_triplanar_shade(const orc_texture* tex, uint64_t n, const float* px, con
 int orc_march(int nx, int ny, int nz, const uint16_t* data, float sigma_scale, const float* cam,
               uint32_t W, uint32_t H, uint32_t steps, int filter, int mode, uint32_t spp,
               uint64_t seed, uint32_t flags, uint64_t pix_begin, uint64_t pix_count,
-              const uint64_t* pix_ids, double* T, uint32_t* picks, double* bdist, int nthreads) {
+              const uint64_t* pix_ids, double* T, uint32_t* picks, uint32_t* picks64, double* bdist,
+              int nthreads) {
     if (!data || !cam || !T || spp == 0 || steps == 0) return 1;
     if (!(filter == F_LINEAR || filter == F_BSPLINE) || mode == M_POSITIVIZED) return 1;
     Vol V{nx, ny, nz, data, sigma_scale};
@@ -1502,7 +1581,8 @@ int orc_march(int nx, int ny, int nz, const uint16_t* data, float sigma_scale, c
         double acc = 0.0, bd = 1e30;
         for (uint32_t s = 0; s < spp; ++s) {
             uint32_t* pk = picks ? picks + (i * spp + s) * steps : nullptr;
-            acc += march_sample(V, cam, W, H, steps, filter, mode, seed, flags, spp, pix, s, pk, &bd);
+            uint32_t* pk64 = picks64 ? picks64 + (i * spp + s) * steps : nullptr;
+            acc += march_sample(V, cam, W, H, steps, filter, mode, seed, flags, spp, pix, s, pk, pk64, &bd);
         }
         T[i] = acc / spp;
         if (bdist) bdist[i] = bd;

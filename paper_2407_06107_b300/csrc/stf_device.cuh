@@ -115,37 +115,27 @@ __device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
 }
 
 // ---------------------------------------------------------------- FP32 decision weights
-// Per-axis weights for the taps at distances 1+t, t, 1-t, 2-t (cubic) or 1-t, t
-// (linear).  The B-spline uses the polynomials of the paper's bicubic listing; the cubic
-// kernels (Keys a=-1/2, Mitchell-Netravali BC(1/3,1/3)) are evaluated in Horner form;
-// multiply-add chains are explicit single-rounded FMAs (__fmaf_rn), nothing else fuses.
+// Per-axis weights for the taps at distances 1+t, t, 1-t, 2-t (cubic) or 1-t, t (linear).
+// The B-spline uses the polynomials of the paper's bicubic listing.  The two signed cubics
+// (Keys a = -1/2, Mitchell-Netravali BC(1/3,1/3)) are evaluated in forms factored at their
+// roots, so a weight near zero keeps its relative precision: the expanded outer polynomial
+// cancels near its double root at |x| = 2, and a positivized negative sample chooses its
+// sign class from the ratio of such small weights.  With s = 1 - t:
+//   Keys: outer a (x-1)(x-2)^2, inner (x-1)(3x^2/2 - x - 1):
+//     w0 = -t s^2/2, w1 = s (1 + t (1 - 3t/2)), w2 = t (1 + s (1 - 3s/2)), w3 = -s t^2/2
+//   Mitchell: outer (x-2)^2 (8 - 7x)/18, inner 7x^3/6 - 2x^2 + 8/9 (>= 1/18, in Horner form):
+//     w0 = s^2 (1 - 7t)/18, w3 = t^2 (7t - 6)/18
+// Multiply-add chains are explicit single-rounded FMAs (__fmaf_rn), nothing else fuses.
 template <int F> struct CubicCoef;
-template <> struct CubicCoef<F_CATMULL_ROM> {
-    static constexpr float c3 = 1.5f, c2 = -2.5f, c0 = 1.0f, q3 = -0.5f, q2 = 2.5f, q1 = -4.0f, q0 = 2.0f;
-};
 template <> struct CubicCoef<F_MITCHELL> {
     static constexpr float c3 = 7.0f / 6.0f, c2 = -2.0f, c0 = 8.0f / 9.0f;
-    static constexpr float q3 = -7.0f / 18.0f, q2 = 2.0f, q1 = -10.0f / 3.0f, q0 = 16.0f / 9.0f;
 };
-// inner piece (|d| < 1) and outer piece (1 <= |d| < 2)
+// Mitchell's inner piece (|d| < 1)
 template <int F>
 __device__ __forceinline__ float k_cubic_inner(float d) {
     using C = CubicCoef<F>;
     const float a = __fmul_rn(__fmaf_rn(C::c3, d, C::c2), d);
     return __fmaf_rn(a, d, C::c0);
-}
-template <int F>
-__device__ __forceinline__ float k_cubic_outer(float d) {
-    using C = CubicCoef<F>;
-    float a = __fmaf_rn(C::q3, d, C::q2);
-    a = __fmaf_rn(a, d, C::q1);
-    return __fmaf_rn(a, d, C::q0);
-}
-template <int F>
-__device__ __forceinline__ float k_cubic(float d) {
-    if (d < 1.0f) return k_cubic_inner<F>(d);
-    if (d < 2.0f) return k_cubic_outer<F>(d);
-    return 0.0f;
 }
 
 template <int F>
@@ -164,17 +154,19 @@ __device__ __forceinline__ void axis_weights(float t, float w[4]) {
         w[2] = __fmul_rn(s, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-3.0f, t, 3.0f), 3.0f), 1.0f));
         w[3] = __fmul_rn(s, __fmul_rn(t2, t));
     } else {
-        // k_cubic at the four distances without its branches: for t in [0, 1] the
-        // distances 1+t and 2-t lie in [1, 2] (outer piece, or 0 where they round to 2)
-        // and t, 1-t in [0, 1] (inner piece, or the outer piece's value at 1 where they
-        // reach 1), so each tap needs one polynomial, a compare and a select; the values
-        // equal k_cubic's bit for bit
-        const float k1 = k_cubic<F>(1.0f);
-        const float d0 = __fadd_rn(1.0f, t), d2 = __fsub_rn(1.0f, t), d3 = __fsub_rn(2.0f, t);
-        w[0] = d0 < 2.0f ? k_cubic_outer<F>(d0) : 0.0f;
-        w[1] = t < 1.0f ? k_cubic_inner<F>(t) : k1;
-        w[2] = d2 < 1.0f ? k_cubic_inner<F>(d2) : k1;
-        w[3] = d3 < 2.0f ? k_cubic_outer<F>(d3) : 0.0f;
+        const float s = __fsub_rn(1.0f, t), t2 = __fmul_rn(t, t), s2 = __fmul_rn(s, s);
+        if constexpr (F == F_CATMULL_ROM) {
+            w[0] = __fmul_rn(__fmul_rn(-0.5f, t), s2);
+            w[1] = __fmul_rn(s, __fmaf_rn(t, __fmaf_rn(-1.5f, t, 1.0f), 1.0f));
+            w[2] = __fmul_rn(t, __fmaf_rn(s, __fmaf_rn(-1.5f, s, 1.0f), 1.0f));
+            w[3] = __fmul_rn(__fmul_rn(-0.5f, s), t2);
+        } else {
+            constexpr float k18 = 1.0f / 18.0f;
+            w[0] = __fmul_rn(__fmul_rn(s2, __fmaf_rn(-7.0f, t, 1.0f)), k18);
+            w[1] = k_cubic_inner<F>(t);
+            w[2] = k_cubic_inner<F>(s);
+            w[3] = __fmul_rn(__fmul_rn(t2, __fmaf_rn(7.0f, t, -6.0f)), k18);
+        }
     }
 }
 

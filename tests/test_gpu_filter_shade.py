@@ -121,6 +121,28 @@ def test_npot_and_extreme_shapes(ctx):
         ctx.destroy_texture(h)
 
 
+@pytest.mark.parametrize("filter,mode", [("mitchell", "positivized"), ("bspline", "stochastic"),
+                                         ("catmull_rom", "ntap_after"), ("linear", "ntap_before")])
+def test_grazing_normals(ctx, filter, mode):
+    # tangent-space normals up to 85 degrees from +z, so n.l and n.v reach down to a few
+    # hundredths and the GGX factors (tan^2 of the Smith terms, 1/(n.v)) are at their worst
+    # conditioned; the per-term FP32 tolerance of the other parity tests must still hold
+    rng = np.random.default_rng(31)
+    dims = [(128 >> i, 128 >> i) for i in range(8)]
+    ar = [rng.integers(0, 256, (a, b, 4), dtype=np.uint8) for a, b in dims]
+    nm = []
+    for a, b in dims:
+        th = np.radians(85.0) * np.sqrt(rng.random((a, b)))
+        ph = 2 * np.pi * rng.random((a, b))
+        xy = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph)], -1)
+        nm.append(np.clip(np.rint((xy + 1) * 127.5), 0, 255).astype(np.uint8))
+    h = ctx.create_texture(ar, nm)
+    otex = oracle.Texture(ar, nm)
+    q = synth.queries_uniform(6000, 32, res=128, lod_range=7.0)
+    _check(ctx, h, otex, q, filter, mode, spp=3, seed=19)
+    ctx.destroy_texture(h)
+
+
 def test_id_base_shards_reproduce_whole(ctx, material):
     # query ids key the Philox counter: two shards with id_base equal one launch
     h, _, q = material
@@ -199,24 +221,34 @@ def test_host_entry_point_chunked(ctx, material, filter, flags):
 
 
 # ---------------------------------------------------------------- full size, sampled
-@pytest.mark.parametrize("filter", ["linear", "bspline", "mitchell"])
-def test_full_size_sampled(ctx, filter):
+@pytest.mark.parametrize("filter,mode", [("linear", "stochastic"), ("bspline", "stochastic"),
+                                         ("mitchell", "stochastic"), ("mitchell", "positivized"),
+                                         ("bspline", "ntap_before"), ("mitchell", "ntap_before"),
+                                         ("linear", "ntap_before")])
+def test_full_size_sampled(ctx, filter, mode):
     # the benchmark workload (4096^2 material with MIPs, 16M queries, 8 spp) in the
-    # launch configuration bench.py times; a seeded sample of queries is re-evaluated by
-    # the oracle with the same Philox ids
+    # launch configuration bench.py times -- the 1-tap estimators and the N-tap filter-before
+    # comparators (8 / 32 / 32 taps over two MIP levels) the equal-RMSE speedups are quoted
+    # against; a seeded sample of queries is re-evaluated by the oracle with the same Philox ids
     m = _full_material()
     h = _full_handle(ctx, m)
-    q = synth.queries_uniform(1 << 24, 1, res=4096, lod_range=8.0)
+    q = _full_queries()
     u, v, d = _dev(q)
-    r, g, b, _ = ctx.filter_shade(h, u, v, d, filter, "stochastic", "ggx", 8, 1)
+    r, g, b, _ = ctx.filter_shade(h, u, v, d, filter, mode, "ggx", 8, 1)
     torch.cuda.synchronize()
     idx = np.sort(np.random.default_rng(99).choice(q.n, 3000, replace=False))
     rgb = torch.stack([r, g, b], 1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
     ref = oracle.filter_shade(oracle.Texture(m.albedo_rough, m.normal), q.subset(idx), filter,
-                              "stochastic", "ggx", 8, 1, ids=idx)
+                              mode, "ggx", 8, 1, ids=idx)
     near = ref.bdist < 1e-6
     assert near.sum() <= 3
     assert_values(rgb, ref.rgb, near, scale=ref.mag)
+
+
+def _full_queries():
+    if "q" not in _FULL:
+        _FULL["q"] = synth.queries_uniform(1 << 24, 1, res=4096, lod_range=8.0)
+    return _FULL["q"]
 
 
 _FULL = {}

@@ -87,20 +87,27 @@ def test_invalid_arguments(ctx, small):
         assert e.value.status == code
 
 
-@pytest.mark.parametrize("filter,mode", [("bspline", "stochastic"), ("bspline", "ntap_before"),
-                                         ("linear", "stochastic")])
-def test_full_size_sampled(ctx, filter, mode):
-    # 512^3 FP16 cloud at 1920x1080, 128 steps: sampled pixels re-evaluated by the oracle
+@pytest.mark.parametrize("filter,mode,spp,flags", [("bspline", "stochastic", 1, 0), ("bspline", "ntap_before", 1, 0),
+                                                   ("linear", "stochastic", 1, 0), ("bspline", "ntap_before", 8, 0),
+                                                   ("bspline", "stochastic", 8, 0),
+                                                   ("bspline", "stochastic", 8, oracle.FLAG_LATTICE),
+                                                   ("linear", "ntap_before", 8, 0)])
+def test_full_size_sampled(ctx, filter, mode, spp, flags):
+    # 512^3 FP16 cloud at 1920x1080, 128 steps, in the launch configurations the benchmark
+    # times (8 spp: the tricubic 64-tap and trilinear 8-tap comparators, the 1-tap estimator
+    # with independent and lattice uniforms): sampled pixels re-evaluated by the oracle
     vol = _full_volume()
     h = _full_handle(ctx, vol)
     cam = synth.camera_pinhole(1920, 1080).as_array()
-    T, _ = ctx.march_volume(h, cam, 1920, 1080, 128, filter, mode, spp=1, seed=1)
+    seed = 1 if spp == 1 else 5
+    T, _ = ctx.march_volume(h, cam, 1920, 1080, 128, filter, mode, spp=spp, seed=seed, flags=flags)
     torch.cuda.synchronize()
     idx = np.sort(np.random.default_rng(5).choice(1920 * 1080, 400, replace=False))
     got = T[torch.from_numpy(idx).cuda()].cpu().numpy()
-    ref = oracle.march(vol, 20.0, cam, 1920, 1080, 128, filter, mode, spp=1, seed=1, pix_ids=idx)
+    ref = oracle.march(vol, 20.0, cam, 1920, 1080, 128, filter, mode, spp=spp, seed=seed, flags=flags,
+                       pix_ids=idx)
     near = ref.bdist < 1e-6
-    assert near.sum() <= 2
+    assert near.sum() <= 2 * spp
     assert_values(got, ref.T, near)
 
 

@@ -9,13 +9,12 @@ import pytest
 
 import oracle
 import stf_synth as synth
-from gpu_util import assert_values
+from gpu_util import REL_DCT, assert_values
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-REL_DCT = 3e-5      # the DCT tests' bound: the per-texel inverse DCT adds FP32 roundings
 
 
 @pytest.fixture(scope="module")

@@ -9,13 +9,12 @@ import pytest
 
 import oracle
 import stf_synth as synth
-from gpu_util import assert_values, compare_picks
+from gpu_util import REL_DCT, assert_values, compare_picks
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-REL_DCT = 3e-5
 
 
 @pytest.fixture(scope="module")

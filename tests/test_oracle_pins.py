@@ -67,8 +67,11 @@ def test_bc_family_identities():
     for d in np.linspace(-2.5, 2.5, 2001):
         assert abs(oracle.kernel_bc(0.0, 0.5, d) - oracle.kernel_keys(-0.5, d)) < 1e-14
         assert abs(oracle.kernel_bc(1.0, 0.0, d) - oracle.kernel("bspline", d)) < 1e-14
-        assert abs(oracle.kernel("catmull_rom", d) - oracle.kernel_keys(-0.5, d)) < 1e-15
-        assert abs(oracle.kernel("mitchell", d) - oracle.kernel_bc(1 / 3, 1 / 3, d)) < 1e-15
+        # the lookups' kernels are the factored forms of the same polynomials; the expanded
+        # forms' own cancellation near the double root at |d| = 2 is ~1e-15 (the factored
+        # forms are checked against exact arithmetic below)
+        assert abs(oracle.kernel("catmull_rom", d) - oracle.kernel_keys(-0.5, d)) < 4e-15
+        assert abs(oracle.kernel("mitchell", d) - oracle.kernel_bc(1 / 3, 1 / 3, d)) < 4e-15
 
 
 def test_bspline_is_fourfold_box_convolution():
@@ -103,6 +106,55 @@ def test_fp32_weights_match_fp64(f):
     for t in np.concatenate([rng.random(2000), [0.0, 0.5, 1.0 - 2 ** -24]]).astype(np.float32):
         w64 = [oracle.kernel(f, float(t) - k) for k in _taps(f)]
         np.testing.assert_allclose(oracle.weights32(f, t), w64, rtol=0, atol=1e-6)
+
+
+def _exact_cubic(f, d):
+    """Keys' a = -1/2 cubic and Mitchell-Netravali BC(1/3, 1/3) at d in exact rational
+    arithmetic, from the published piecewise polynomials (expanded form)."""
+    d = abs(Fraction(d))
+    if f == "catmull_rom":
+        a = Fraction(-1, 2)
+        if d < 1:
+            return (a + 2) * d ** 3 - (a + 3) * d ** 2 + 1
+        return a * d ** 3 - 5 * a * d ** 2 + 8 * a * d - 4 * a if d < 2 else Fraction(0)
+    B = C = Fraction(1, 3)
+    if d < 1:
+        return ((12 - 9 * B - 6 * C) * d ** 3 + (-18 + 12 * B + 6 * C) * d ** 2 + (6 - 2 * B)) / 6
+    if d < 2:
+        return ((-B - 6 * C) * d ** 3 + (6 * B + 30 * C) * d ** 2 + (-12 * B - 48 * C) * d + (8 * B + 24 * C)) / 6
+    return Fraction(0)
+
+
+def _near_root_ts():
+    """FP32 positions t near the signed cubics' roots: t -> 0 and t -> 1 (the double root of
+    the outer piece at |d| = 2 and Keys' root at |d| = 1) and Mitchell's zero crossings of the
+    outer piece at t = 1/7 and 6/7, plus random positions."""
+    ts = [2.0 ** -k for k in range(1, 25)] + [1.0 - 2.0 ** -k for k in range(1, 25)]
+    for c in (1 / 7, 6 / 7):
+        x = np.float32(c)
+        for k in range(-8, 9):
+            ts.append(float(np.nextafter(x, np.float32(2 if k > 0 else -1)) if k else x))
+            x = np.nextafter(x, np.float32(2 if k > 0 else -1)) if k else x
+    ts += list(np.random.default_rng(9).random(500))
+    return np.unique(np.array(ts, dtype=np.float32))
+
+
+@pytest.mark.parametrize("f", ["catmull_rom", "mitchell"])
+def test_signed_weights_keep_relative_precision_near_roots(f):
+    # A positivized sample picks its sign class from the ratio of the small negative-lobe
+    # weights, so both the FP64 definition and the FP32 decision weights must be accurate
+    # RELATIVE to the weight, with the exact sign, also where the weight tends to zero.
+    for t in _near_root_ts():
+        tf = Fraction(float(t))
+        exact = [_exact_cubic(f, tf - k) for k in _taps(f)]
+        w64 = [oracle.kernel(f, float(t) - k) for k in _taps(f)]
+        w32 = oracle.weights32(f, t)
+        for e, a, b in zip(exact, w64, w32):
+            if e == 0:
+                assert a == 0 and b == 0, (t, e, a, b)
+                continue
+            assert abs(Fraction(a) - e) <= abs(e) * Fraction(1, 2 ** 48), (f, float(t), float(e), a)
+            assert abs(Fraction(float(b)) - e) <= abs(e) * Fraction(1, 2 ** 18), (f, float(t), float(e), float(b))
 
 
 # ------------------------------------------------------------------------ picks
@@ -312,16 +364,18 @@ def test_stochastic_expectation_by_enumeration():
 
 
 @pytest.mark.parametrize("f,mode", [("linear", "stochastic"), ("bspline", "stochastic"),
-                                    ("mitchell", "stochastic"), ("mitchell", "positivized")])
+                                    ("mitchell", "stochastic"), ("mitchell", "positivized"),
+                                    ("catmull_rom", "positivized")])
 def test_fp32_decisions_agree_with_fp64_off_boundary(f, mode):
     m = synth.material_rgba8(64, 8, octaves=4, base=4)
     tex = oracle.Texture(m.albedo_rough, m.normal)
-    q = synth.queries_uniform(4000, 77, res=64, lod_range=6.0)
-    r = oracle.filter_shade(tex, q, f, mode, spp=4, seed=9, want_picks=True)
+    q = synth.queries_uniform(20000, 77, res=64, lod_range=6.0)
+    r = oracle.filter_shade(tex, q, f, mode, spp=8, seed=9, want_picks=True)
     diff = np.any(r.picks != r.picks64, axis=(1, 2))
-    # every FP32/FP64 disagreement lies within 1e-6 of an FP64 boundary
+    # every FP32/FP64 disagreement lies within 1e-6 of an FP64 boundary, and they are as rare
+    # as the parity criterion for the kernel's FP32 decisions demands
     assert np.all(r.bdist[diff] < 1e-6)
-    assert diff.mean() < 1e-3
+    assert diff.sum() <= max(1, math.ceil(1e-5 * q.n))
 
 
 # ------------------------------------------------------------------------ volume
@@ -417,7 +471,7 @@ def test_decode_roundtrip_against_encoder():
 
 def _level_hist(tex, q, spp):
     r = oracle.filter_shade(tex, q, "linear", "stochastic", spp=spp, want_picks=True)
-    return (r.picks[..., 0] >> 28).astype(np.int64)
+    return (r.picks64[..., 0] >> 28).astype(np.int64)
 
 
 def test_lod_stochastic_level_frequency_and_aniso_cap():
@@ -479,7 +533,7 @@ def test_lattice_picks_are_stratified():
         tx = px - math.floor(px)
         p = np.array([oracle.kernel("bspline", tx - k) for k in _taps("bspline")])
         ix0 = math.floor(px)
-        xs = (r.picks[i, :, 0] & 0x3FFF).astype(int)
+        xs = (r.picks64[i, :, 0] & 0x3FFF).astype(int)
         counts = np.array([np.sum(xs == (ix0 + k) % 16) for k in _taps("bspline")])
         assert np.all(np.abs(counts - spp * p) <= 1.0 + 1e-9), (counts, spp * p)
 
@@ -632,7 +686,7 @@ def test_ewa_magnification_at_texel_centre_is_point_sample():
         r = oracle.filter_shade(tex, q, "ewa", mode, spp=2, want_picks=True)
         np.testing.assert_allclose(r.rgb[0], want, rtol=1e-12)
         if mode == "stochastic":
-            assert np.all(r.picks[0, :, 0] == ((5 << 14) | 2))
+            assert np.all(r.picks64[0, :, 0] == ((5 << 14) | 2))
 
 
 def test_ewa_constant_texture_reproduced():
@@ -655,7 +709,7 @@ def test_ewa_stochastic_pick_frequencies_follow_weights():
     r = oracle.filter_shade(tex, q, "ewa", "stochastic", spp=spp, seed=9, flags=oracle.FLAG_LOD0, want_picks=True)
     box, w = oracle.ewa_box(q.u[0], q.v[0], q.dudx[0], q.dvdx[0], q.dudy[0], q.dvdy[0], 64, 64)
     s0, s1, t0, t1 = box
-    pk = r.picks[0, :, 0]
+    pk = r.picks64[0, :, 0]
     ix, iy = pk & 0x3FFF, (pk >> 14) & 0x3FFF
     counts = np.zeros_like(w, dtype=np.float64)
     ss = (np.arange(s0, s1 + 1) % 64)
@@ -692,9 +746,9 @@ def test_lod0_flag_uses_the_finest_level_only():
     q = synth.queries_aniso(200, 11, res=32, lod_range=4.0)
     for f in ("bspline", "ewa"):
         r = oracle.filter_shade(tex, q, f, "stochastic", spp=2, flags=oracle.FLAG_LOD0, want_picks=True)
-        assert np.all((r.picks[..., 0] >> 28) == 0)
+        assert np.all((r.picks64[..., 0] >> 28) == 0)
         base = oracle.filter_shade(tex, q, f, "stochastic", spp=2, want_picks=True)
-        assert np.any((base.picks[..., 0] >> 28) > 0)
+        assert np.any((base.picks64[..., 0] >> 28) > 0)
 
 
 # ------------------------------------------------------------------------ DCT texture compression
