@@ -9,10 +9,16 @@ filters (trilinear, bicubic B-spline, Mitchell BC(1/3,1/3) with sign-carried neg
 lobes): 3 x 2^24 x 8 shaded lookups.  Inputs (384 MiB of queries, 171 MiB of texels) are
 larger than L2, so no flush is needed between steps.
 
-value   = shaded lookups/s over all ranks (kernel time, inputs resident in HBM)
-e2e     = the same step through stf_filter_shade_host_async from pinned host buffers
-equal_rmse / volume = N-tap comparators and the equal-RMSE speedups (rank 0, N = 1)
---impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+The LAST stdout line is the headline JSON (a few hundred bytes to ~2 KB):
+  value    = shaded lookups/s over all ranks (kernel time, inputs resident in HBM)
+  e2e      = the same step through stf_filter_shade_host_async from pinned host buffers
+  roofline = the dominant kernel's algorithmic L2 sector throughput against the measured
+             random-sector read rate at L2 (with its HBM and ALU fractions beside it)
+  equal_rmse / neural = the headline ratios of the comparator blocks
+  cpu_baseline = the FP64 oracle on the host cores, on the first 2^20 queries of the workload
+The comparator blocks in full (equal-RMSE curves, volume, anisotropic, DCT, FIS, triplanar,
+bindless table, learned form) go to --extras-out as JSON (rank 0, N = 1).
+--impl reference times the FP64 CPU oracle on the same 2^20-query sample per step.
 """
 from __future__ import annotations
 
@@ -112,25 +118,47 @@ def make_queries(n: int, rank: int):
     return synth.queries_uniform(n, 1 + rank, res=TEX_RES, lod_range=LOD_RANGE)
 
 
-def cpu_baseline(material, seconds: float = 12.0) -> dict:
-    """The FP64 oracle, as it stands, on a bounded sample of the workload (host cores)."""
+CPU_SAMPLE = 1 << 20                # queries per oracle step: the first 2^20 of the workload
+
+
+def oracle_sample(material):
+    """The FP64 oracle's texture and the first 2^20 queries of rank 0's workload, with their
+    Philox ids (0 .. 2^20 - 1): the bounded sample both CPU figures time."""
     import oracle
-    otex = oracle.Texture(material.albedo_rough, material.normal)
+    q = make_queries(1 << 24, 0).subset(slice(0, CPU_SAMPLE))
+    return oracle.Texture(material.albedo_rough, material.normal), q
+
+
+def oracle_step(otex, q, cores):
+    """One oracle step on the sample: stochastic filter+shade at 8 spp with each filter."""
+    import oracle
+    for f in FILTERS:
+        oracle.filter_shade(otex, q, f, "stochastic", "ggx", SPP, 1, nthreads=cores)
+
+
+def oracle_sample_desc(cores):
+    return (f"first {CPU_SAMPLE} queries of the 2^24-query workload x {SPP} spp x {len(FILTERS)} filters "
+            f"per step (FP64 oracle, stochastic, {cores} threads)")
+
+
+def cpu_baseline(material, seconds: float = 12.0) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: steps over the fixed 2^20-query sample
+    until about `seconds` of CPU work (the reference arm times the same step)."""
+    import oracle
+    otex, q = oracle_sample(material)
     cores = oracle.nthreads_default()
-    n = 1 << 10
+    oracle_step(otex, q, cores)                       # warm-up
+    t0 = time.perf_counter()
+    k = 0
     while True:
-        q = make_queries(n, 0)
-        t0 = time.perf_counter()
-        for f in FILTERS:
-            oracle.filter_shade(otex, q, f, "stochastic", "ggx", SPP, 1, nthreads=cores)
+        oracle_step(otex, q, cores)
+        k += 1
         dt = time.perf_counter() - t0
-        if dt > seconds / 2 or n >= (1 << 24):
+        if dt >= seconds or k >= 64:
             break
-        n = min(1 << 24, int(n * max(2.0, seconds / 2 / max(dt, 1e-3))))
-        n = 1 << int(math.log2(n))
-    units = n * SPP * len(FILTERS)
+    units = k * CPU_SAMPLE * SPP * len(FILTERS)
     return {"value": units / dt, "unit": "lookups/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} queries x {SPP} spp x {len(FILTERS)} filters (stochastic, FP64 oracle), {dt:.1f} s"}
+            "sample": f"{k} steps of the " + oracle_sample_desc(cores) + f", {dt:.1f} s"}
 
 
 # ------------------------------------------------------------------------------ our arm
@@ -216,57 +244,92 @@ def run_ours(args):
     e2e = {"value": world * units_step / e2e_s, "unit": "lookups/s",
            "h2d_bytes_per_step": len(FILTERS) * nq * 24, "d2h_bytes_per_step": len(FILTERS) * nq * 12}
 
-    # ---- roofline of the dominant kernel (issue/ALU-bound: see the design notes)
+    # ---- roofline of the dominant kernel.  A stochastic lookup gathers one 8-byte texel from a
+    # random place in a 171 MiB MIP chain whose hot levels sit in L2: the bound is the rate at
+    # which L2 serves random 32-byte sectors, measured here on the same GPU (random sector
+    # reads over a 32 MiB buffer).  Algorithmic sectors per lookup: the texel's sector plus the
+    # 36 bytes of query I/O (24 in, 12 out) shared by the query's spp samples.
     mean = per.mean(0)
     dom = int(np.argmax(mean))
     units_launch = nq * SPP
-    ops = ALG_OPS[FILTERS[dom]]
-    achieved = ops * units_launch / (mean[dom] / 1e3) / 1e12
-    peak = alu_peak_tops()
-    traffic = load_traffic(f"k_filter_shade<{FILTERS[dom]},stochastic>", nq)
-    roof = {"kernel": f"k_filter_shade<{FILTERS[dom]}, stochastic>", "bound": "alu", "achieved": achieved,
-            "peak": peak, "unit": "Tops/s", "frac": achieved / peak, "peak_src":
-            "148 SMs x 128 INT32/FP32 lanes x 2032 MHz (recipe unit counts and max SM clock)",
-            "alg_ops_per_lookup": ops, "traffic": traffic, "ms_per_launch": float(mean[dom]),
-            "alg_bytes_per_launch": units_launch * 8 + nq * (24 + 12),
-            "hbm_frac_of_measured": (units_launch * 8 + nq * 36) / (mean[dom] / 1e3) / 1e9 / peaks()["hbm_gbs"]}
-    # gather roofline: algorithmic 32-byte sectors per lookup (the 8-byte texel lies in one
-    # sector; the 36 bytes of query I/O are shared by the spp samples) against the measured
-    # random-sector read rate at L2 (32 MiB buffer).  Most lookups hit L2, so the DRAM random-
-    # sector rate (1 GiB buffer) is context, not the bound.
     sectors_per_lookup = 1.0 + 36.0 / 32.0 / SPP
     l2_rate, dram_rate = ctx.measure_sector_rate(32 << 20), ctx.measure_sector_rate(1 << 30)
     g_ach = sectors_per_lookup * units_launch / (mean[dom] / 1e3)
-    gather = {"kernel": roof["kernel"], "bound": "l2_sectors", "unit": "sectors/s", "achieved": g_ach,
-              "alg_sectors_per_lookup": sectors_per_lookup, "peak": l2_rate, "frac": g_ach / l2_rate,
-              "peak_src": "measured: random 32-B sector reads at L2, 32 MiB buffer (stf_measure_sector_rate)",
-              "dram_sector_rate": dram_rate}
+    kname = f"k_filter_shade<{FILTERS[dom]},stochastic>"
+    alg_bytes = units_launch * 8 + nq * 36
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clocks.get("sm_max_mhz") or peaks()["sm_max_mhz"]
+    alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12
+    roof = {"kernel": kname, "bound": "l2", "unit": "GB/s",
+            "achieved": g_ach * 32 / 1e9, "peak": l2_rate * 32 / 1e9, "frac": g_ach / l2_rate,
+            "peak_src": "measured random 32-B sector reads at L2 (32 MiB buffer)",
+            "alg_sectors_per_lookup": sectors_per_lookup, "ms_per_launch": float(mean[dom]),
+            "traffic": load_traffic(kname, nq), "alg_bytes_per_launch": alg_bytes,
+            "hbm_frac": alg_bytes / (mean[dom] / 1e3) / 1e9 / peaks()["hbm_gbs"],
+            "dram_sector_rate_gbs": dram_rate * 32 / 1e9,
+            "alu_frac": ALG_OPS[FILTERS[dom]] * units_launch / (mean[dom] / 1e3) / 1e12 / alu_peak,
+            "alu_peak_tops": alu_peak}
 
     line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "2-D mipmapped material: 4096^2 RGBA8+RG8 fBm with MIPs, 2^24 queries/GPU, "
                                    "LOD uniform over 8 levels, stochastic trilinear+bicubic B-spline+Mitchell, 8 spp, GGX",
-                       "queries_per_gpu": nq, "spp": SPP, "filters": list(FILTERS), "l2": "inputs larger than L2 (no flush)",
+                       "queries_per_gpu": nq, "spp": SPP, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"query-sharded x{world}"},
-            "ms_per_launch": {f: float(mean[i]) for i, f in enumerate(FILTERS)},
-            "roofline": roof, "gather_roofline": gather, "e2e": e2e, "gpu_launches": args.steps * len(FILTERS), "clocks": clocks}
+            "ms_per_launch": {f: round(float(mean[i]), 4) for i, f in enumerate(FILTERS)},
+            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * len(FILTERS), "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_extras:
-        line["equal_rmse"] = equal_rmse_2d(ctx, tex, u, v, d, dev)
-        line["aniso"] = aniso_block(ctx, tex, dev)
-        line["dct"] = dct_block(ctx, material, u, v, d, dev)
-        line["fis"] = fis_block(ctx, tex, dev)
-        line["triplanar"] = triplanar_block(ctx, tex, material, dev)
-        line["volume"] = volume_block(ctx, dev, args)
-        line["table"] = table_block(ctx, dev)
-        line["neural"] = neural_block(ctx, dev, material)
+        extras = {"equal_rmse_2d": equal_rmse_2d(ctx, tex, u, v, d, dev),
+                  "volume": volume_block(ctx, dev, args),
+                  "neural": neural_block(ctx, dev, material),
+                  "table": table_block(ctx, dev),
+                  "aniso": aniso_block(ctx, tex, dev),
+                  "dct": dct_block(ctx, material, u, v, d, dev),
+                  "fis": fis_block(ctx, tex, dev),
+                  "triplanar": triplanar_block(ctx, tex, material, dev)}
+        line.update(headline_extras(extras))
+        line["extras"] = os.path.basename(args.extras_out)
+        with open(args.extras_out, "w") as f:
+            json.dump(extras, f, indent=1)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(material)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_rounded(line), separators=(",", ":")), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _rounded(x, digits=5):
+    """Floats to `digits` significant digits, so the headline line stays short."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: _rounded(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_rounded(v, digits) for v in x]
+    return x
+
+
+def headline_extras(ex: dict) -> dict:
+    """The comparator blocks' headline ratios, for the headline line: equal-RMSE speedups of the
+    1-tap path over N-tap filter-before at 8 spp (with the least spp s* that reaches the N-tap
+    RMSE), for the 2-D bicubic filters and the tricubic / trilinear volume, and the learned
+    form's decode rate and 1-tap vs 16-tap ratio."""
+    e2, vol, nn, tb = ex["equal_rmse_2d"], ex["volume"], ex["neural"], ex["table"]
+    pick = lambda d, k_s, k_x: {"s_star": d.get(k_s), "speedup": d.get(k_x)}
+    eq = {"bspline_2d": pick(e2["bspline"], "s_star", "equal_rmse_speedup"),
+          "mitchell_2d_positivized": pick(e2["mitchell"], "s_star_positivized", "equal_rmse_speedup_positivized"),
+          "mitchell_2d_sign": pick(e2["mitchell"], "s_star", "equal_rmse_speedup"),
+          "tricubic_vol_lattice": pick(vol["bspline"], "s_star_lattice", "equal_rmse_speedup_lattice"),
+          "tricubic_vol": pick(vol["bspline"], "s_star", "equal_rmse_speedup"),
+          "trilinear_vol_lattice": pick(vol["linear"], "s_star_lattice", "equal_rmse_speedup_lattice")}
+    return {"equal_rmse": eq,
+            "neural": {"decode_tflops_1tap": nn["stochastic_1tap"]["mlp_tflops"],
+                       "speedup_1tap_vs_16tap": nn["speedup_1tap_vs_16tap"],
+                       "fp8_rmse_vs_fp16_form": nn["fp8"]["rmse_vs_fp16_form"]},
+            "table_lookups_per_s": tb["stochastic"]["lookups_per_s"]}
 
 
 # the sources the 2-D filter kernels are compiled from
@@ -296,10 +359,6 @@ def load_traffic(kernel: str, nq: int):
         return None
     k = d["kernels"][kernel]
     return k["dram_bytes"] * nq / k["queries"]
-
-
-def alu_peak_tops() -> float:
-    return 148 * 128 * 2.032e9 / 1e12
 
 
 def _time_launch(fn, reps=3):
@@ -768,37 +827,34 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
 
 # ------------------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper has no runnable code), as it stands, on
+    the host cores; each step is oracle_step on the fixed 2^20-query sample of the workload.
+    Rank 0 alone runs it."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
     import oracle
     material = synth.material_rgba8(TEX_RES, 102)
-    otex = oracle.Texture(material.albedo_rough, material.normal)
+    otex, q = oracle_sample(material)
     cores = oracle.nthreads_default()
-    n = args.ref_queries
-    q = make_queries(n, 0)
-
-    def step():
-        for f in FILTERS:
-            oracle.filter_shade(otex, q, f, "stochastic", "ggx", SPP, 1, nthreads=cores)
     for _ in range(args.warmup):
-        step()
+        oracle_step(otex, q, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        oracle_step(otex, q, cores)
     dt = (time.perf_counter() - t0) / args.steps
-    units = n * SPP * len(FILTERS)
+    units = CPU_SAMPLE * SPP * len(FILTERS)
     v = units / dt
-    sample = f"{n} queries x {SPP} spp x {len(FILTERS)} filters per step (FP64 oracle, stochastic)"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "lookups/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "2-D mipmapped material: 4096^2 RGBA8+RG8 fBm with MIPs, LOD uniform over 8 levels, "
-                                   "stochastic trilinear+bicubic B-spline+Mitchell, 8 spp, GGX",
-                       "queries_per_step": n, "spp": SPP, "filters": list(FILTERS)},
-            "cpu_baseline": {"value": v, "unit": "lookups/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "config": {"workload": "2-D mipmapped material: 4096^2 RGBA8+RG8 fBm with MIPs, 2^24 queries/GPU, "
+                                   "LOD uniform over 8 levels, stochastic trilinear+bicubic B-spline+Mitchell, 8 spp, GGX",
+                       "queries_per_step": CPU_SAMPLE, "spp": SPP},
+            "cpu_baseline": {"value": v, "unit": "lookups/s", "cores": cores, "kind": "oracle",
+                             "sample": oracle_sample_desc(cores)},
             "e2e": {"value": v, "unit": "lookups/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_rounded(line), separators=(",", ":")), flush=True)
 
 
 def run_volume(args):
@@ -1018,9 +1074,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--queries", type=int, default=1 << 24)
-    ap.add_argument("--ref-queries", type=int, default=1 << 13)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--extras-out", default="bench_extras.json",
+                    help="where the comparator blocks go as JSON (rank 0, N = 1)")
     ap.add_argument("--workload", default="material",
                     choices=["material", "volume", "neural", "train", "triplanar", "ntap", "lookup"])
     ap.add_argument("--lfilter", default="linear", choices=["linear", "bspline", "catmull_rom", "mitchell", "ewa", "gauss"])
