@@ -318,14 +318,18 @@ stf_status stf_bin_queries(stf_ctx ctx, uint64_t n, const float* u, const float*
  * are staged in one fixed device array of the library (a little over 9 MiB, held by every
  * GPU that loads the library until the process exits) instead of context-owned buffers
  * grown with cudaMalloc, so the call allocates nothing.
+ *   - Takes every filter (EWA included), mode, shade and flag (LOD0 included) that
+ *     stf_filter_shade_host takes, with the same checks.
  *   - At most 262144 queries per call (STF_ERR_INVALID_ARG beyond); picks must be NULL
- *     (STF_ERR_UNSUPPORTED otherwise).
+ *     (STF_ERR_UNSUPPORTED otherwise); no execution order (q->order must be NULL).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - All calls share the array: calls that overlap on the GPU (other streams, other
  *     host threads, other contexts on the same device) race and corrupt each other.
  *   - Synchronises the context stream; returns STF_ERR_DEVICE_STATUS if the kernel
- *     flagged its inputs (the results are still written). */
+ *     flagged its inputs (the results are still written).  The call's device status bits
+ *     live in the shared array and are reported by this return value only: they are not
+ *     merged into the context's status word, so stf_get_device_status does not see them. */
 stf_status stf_filter_shade_host_noalloc(stf_ctx ctx, stf_tex tex, const stf_queries* q, const stf_derivs* d,
                                          stf_filter filter, stf_mode mode, stf_shade shade, uint32_t spp,
                                          uint64_t seed, uint32_t flags, const stf_output* out);

@@ -47,41 +47,22 @@ stf_status scratch_address(stf_ctx c, unsigned char** out) {
     return STF_OK;
 }
 
-bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
-
 }  // namespace
 
 extern "C" stf_status stf_filter_shade_host_noalloc(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d,
                                                     stf_filter f, stf_mode m, stf_shade sh, uint32_t spp,
                                                     uint64_t seed, uint32_t flags, const stf_output* out) {
-    if (!c) return STF_ERR_INVALID_ARG;
-    auto it = c->tex.find(t);
-    if (it == c->tex.end()) return stfi::fail(c, STF_ERR_BAD_HANDLE, "unknown texture handle");
-    if (!q || !out) return stfi::fail(c, STF_ERR_INVALID_ARG, "queries and output must be non-null");
-    if (f < 0 || f > 3 || m < 0 || m > 3 || (sh != STF_SHADE_GGX_LAMBERT && sh != STF_SHADE_LINEAR))
-        return stfi::fail(c, STF_ERR_INVALID_ARG, "filter, mode or shade out of range");
-    if (m == STF_MODE_STOCHASTIC_POSITIVIZED && f != STF_FILTER_CATMULL_ROM && f != STF_FILTER_MITCHELL)
-        return stfi::fail(c, STF_ERR_UNSUPPORTED, "positivization needs a filter with negative lobes");
-    if (spp == 0) return stfi::fail(c, STF_ERR_INVALID_ARG, "spp must be >= 1");
-    if ((flags & STF_FLAG_REUSE) && m == STF_MODE_STOCHASTIC_POSITIVIZED)
-        return stfi::fail(c, STF_ERR_UNSUPPORTED, "sample reuse is defined for the 1-tap estimator");
-    if (flags & ~(uint32_t)(STF_FLAG_STRATIFIED | STF_FLAG_LATTICE | STF_FLAG_REUSE)) return stfi::fail(c, STF_ERR_INVALID_ARG, "unknown flag bits");
+    // the same argument checks as stf_filter_shade_host (every filter, mode and flag it takes)
+    TexRec* rec = nullptr;
     int kside = 1;
-    if (flags & STF_FLAG_STRATIFIED) {
-        while ((uint32_t)(kside * kside) < spp) ++kside;
-        if ((uint32_t)(kside * kside) != spp) return stfi::fail(c, STF_ERR_INVALID_ARG, "stratified jitter needs a square spp");
-    }
+    stf_status vs = stfi::validate_filter_args(c, t, q, d, f, m, sh, spp, flags, out, &rec, &kside);
+    if (vs != STF_OK) return vs;
     if (out->picks) return stfi::fail(c, STF_ERR_UNSUPPORTED, "the no-allocation entry point does not report picks");
     if (q->n > NOALLOC_MAX_QUERIES)
         return stfi::fail(c, STF_ERR_INVALID_ARG,
                           "stf_filter_shade_host_noalloc: at most 262144 queries per call (split larger batches)");
     if (q->n == 0) return STF_OK;
     if (q->order) return stfi::fail(c, STF_ERR_UNSUPPORTED, "the host-buffer entry points take no execution order");
-    const void* ptrs[5] = {q->u, q->v, out->r, out->g, out->b};
-    for (const void* p : ptrs)
-        if (!p || !aligned4(p)) return stfi::fail(c, STF_ERR_INVALID_ARG, "query/output pointers must be non-null and 4-byte aligned");
-    if (d && (!d->dudx || !d->dvdx || !d->dudy || !d->dvdy))
-        return stfi::fail(c, STF_ERR_INVALID_ARG, "derivative pointers must be all non-null");
     if (c->fault == stfi::FAULT_LAUNCH) return stfi::fail(c, STF_ERR_CUDA, "injected launch failure (STF_FAULT=launch)");
 
     stfi::CurrentDevice cd(c->device);
@@ -107,7 +88,8 @@ extern "C" stf_status stf_filter_shade_host_noalloc(stf_ctx c, stf_tex t, const 
     a.filter = f; a.mode = m; a.shade = sh; a.spp = spp; a.flags = flags; a.kside = kside;
     a.seed = seed; a.r = arr[6]; a.g = arr[7]; a.b = arr[8]; a.picks = nullptr;
     a.status = status;
-    e = stf::launch_filter_shade(a, it->second.view, c->num_sms, c->stream);
+    a.ewa_lut = c->d_ewa_lut;       // allocated with the context: the call still allocates nothing
+    e = stf::launch_filter_shade(a, rec->view, c->num_sms, c->stream);
     if (e != cudaSuccess) return stfi::cuda_fail(c, e, "filter_shade launch");
     uint32_t st = 0;
     e = cudaMemcpyAsync(out->r, arr[6], n * 4, cudaMemcpyDeviceToHost, c->stream);

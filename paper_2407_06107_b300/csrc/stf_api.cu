@@ -116,6 +116,16 @@ stf_status validate_filter_call(stf_ctx c, stf_tex t, const stf_queries* q, cons
 
 }  // namespace
 
+namespace stfi {
+stf_status validate_filter_args(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d, stf_filter f,
+                                stf_mode m, stf_shade sh, uint32_t spp, uint32_t flags, const stf_output* out,
+                                TexRec** rec, int* kside) {
+    const stf_status s = validate_filter_call(c, t, q, d, f, m, sh, spp, flags, out, rec);
+    if (s == STF_OK && kside) *kside = (flags & STF_FLAG_STRATIFIED) ? square_side(spp) : 1;
+    return s;
+}
+}  // namespace stfi
+
 using stfi::fail;
 using stfi::cuda_fail;
 using stfi::dev_alloc;

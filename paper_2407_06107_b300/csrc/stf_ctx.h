@@ -69,6 +69,12 @@ enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_LAUNCH = 2, FAULT_MMA_TIMEOUT = 3 
 stf_status fail(stf_ctx c, stf_status s, const char* msg);
 stf_status cuda_fail(stf_ctx c, cudaError_t e, const char* where);
 stf_status dev_alloc(stf_ctx c, void** p, size_t bytes);
+// The argument checks of stf_filter_shade and the host-buffer entry points (handles, enums,
+// flags, spp, pointer alignment); *kside = the side of the stratified jitter grid (1 without
+// STF_FLAG_STRATIFIED).  q->n == 0 passes without checking the pointers.
+stf_status validate_filter_args(stf_ctx c, stf_tex t, const stf_queries* q, const stf_derivs* d, stf_filter f,
+                                stf_mode m, stf_shade sh, uint32_t spp, uint32_t flags, const stf_output* out,
+                                TexRec** rec, int* kside);
 // Names an entry point's host-side span in a profiler's timeline (NVTX ranges; no cost
 // beyond a function-pointer test unless a tool is attached).
 struct NvtxRange {

@@ -5,9 +5,15 @@ form (BF16 weights, FP16 or FP8 latents) from them.  Tolerances derived from the
 arithmetic:
   * decoded channels: both sides round the same FP32 features to BF16; the GPU then
     accumulates K <= 64 BF16 products in FP32 (relative error <= 64 * 2^-24 ~ 4e-6 of
-    sum|w h|), so |dy| <= 1e-4 (1 + |y|) bounds it with margin.  Decodes whose hidden
-    activations lie within 2e-5 (relative) of a BF16 rounding boundary may round to the
-    neighbouring BF16 value on the GPU (a counted boundary case, like a CDF boundary).
+    sum|w h|), so |dy| <= 1e-4 (1 + |y|) bounds it with margin.  A hidden activation that
+    lies closer to a BF16 rounding midpoint than the GPU's accumulation error may round to
+    the neighbouring BF16 value there (a counted boundary case, like a CDF boundary).  The
+    oracle reports each decode's smallest such margin in units of sqrt(K+1) 2^-24 S
+    (S = |b| + sum|w h|).  Measured on B300 over every texel of four networks (untrained
+    and oracle-trained, FP16 and FP8 latents; 16,384 decodes), the largest margin at which
+    a unit rounded the other way was 0.044 units; decodes below NEAR = 0.5 units (11x that)
+    are flagged.  At most a quarter of the decodes may be flagged, and every unflagged one
+    must meet the tight bound.
   * shaded values: the GGX condition number with respect to the normal is <= 2/alpha
     = 40 at alpha >= 0.05, giving |df| <= 5e-4 sum|terms| + 1e-6.
   * gradients: the tensor-core backward rounds dy, dh2 and dh1 to BF16 as GEMM operands;
@@ -30,6 +36,7 @@ torch = pytest.importorskip("torch")
 R0 = 64
 GRIDS = (32, 16, 8, 4)
 LAT_TOTAL = sum(r * r * 8 for r in GRIDS)
+NEAR = 0.5 * 2.0 ** -24        # flagged BF16 rounding margin (see the module docstring)
 
 
 @pytest.fixture(scope="module")
@@ -58,6 +65,33 @@ def net(ctx, data):
     ctx.neural_destroy(h)
 
 
+def _oracle_trained(lat, mlp, tg, steps=400, batch=1024, seed=5, lr_lat=1e-2, lr_mlp=5e-3):
+    """The test network after `steps` FP64 Adam steps of the oracle (its loss gradient and its
+    Adam) on Philox-drawn texels: a well-conditioned, trained network whose parameters come
+    from the oracle alone.  Returns FP32 latents and MLP."""
+    L = [np.asarray(g, np.float64).ravel().copy() for g in lat]
+    M = np.asarray(mlp, np.float64).copy()
+    mL, vL = [np.zeros_like(x) for x in L], [np.zeros_like(x) for x in L]
+    mM, vM = np.zeros_like(M), np.zeros_like(M)
+    for step in range(1, steps + 1):
+        ix, iy = oracle.ntc_sample_texels(step, batch, seed, R0)
+        lat32 = [x.astype(np.float32).reshape(g.shape) for x, g in zip(L, lat)]
+        _, gm, gl = oracle.ntc_loss_grad(R0, lat32, M.astype(np.float32), tg, ix, iy, round_bf16=False)
+        gl, off = np.asarray(gl, np.float64), 0
+        for x, m1, m2 in zip(L, mL, vL):
+            oracle.adam(x, np.ascontiguousarray(gl[off:off + x.size]), m1, m2, step, lr_lat)
+            off += x.size
+        oracle.adam(M, np.asarray(gm, np.float64), mM, vM, step, lr_mlp)
+    return [x.astype(np.float32).reshape(g.shape) for x, g in zip(L, lat)], M.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def trained(data):
+    lat, mlp, tg = data
+    tlat, tmlp = _oracle_trained(lat, mlp, tg)
+    return tlat, tmlp, tg
+
+
 def _all_texels():
     ix, iy = np.meshgrid(np.arange(R0, dtype=np.int32), np.arange(R0, dtype=np.int32))
     return ix.ravel(), iy.ravel()
@@ -67,15 +101,14 @@ def _check_decode(ctx, h, nt):
     ix, iy = _all_texels()
     y = ctx.neural_decode(h, torch.from_numpy(ix).cuda(), torch.from_numpy(iy).cuda()).cpu().numpy()
     ref, rd = oracle.ntc_decode(nt, ix, iy)
-    near = rd < 4 * 2.0 ** -24
+    near = rd < NEAR
     err = np.abs(y - ref)
     tol = 1e-4 * (1 + np.abs(ref))
     off = (err > tol).any(1)
-    # the flagged fraction is a property of the network (an untrained one cancels heavily,
-    # which shrinks its margins): enough decodes must remain for the tight check
-    assert near.mean() < 0.8, near.mean()
+    assert near.mean() <= 0.25, near.mean()
     bad = off & ~near
-    assert bad.mean() < 0.01, f"{bad.sum()} unflagged decodes off by up to {err[bad].max():.3g} (flagged {near.mean():.3f})"
+    assert not bad.any(), f"{bad.sum()} unflagged decodes off by up to {err[bad].max():.3g} (flagged {near.mean():.3f})"
+    # a flagged decode is off by at most one BF16 rounding step of a hidden unit
     assert np.all(err <= 3e-2 * (1 + np.abs(ref))), float(err.max())
     return y
 
@@ -94,6 +127,40 @@ def test_decode_fp8_matches_oracle(ctx, net, data):
     # FP8 vs FP16 latents: the error the 8-bit form adds, stated against the FP64 decode
     y16, _ = oracle.ntc_decode(oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp16"), *_all_texels())
     assert np.sqrt(np.mean((y8 - y16) ** 2)) < 0.05
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "fp8"])
+def test_decode_trained_network_matches_oracle(ctx, trained, fmt):
+    lat, mlp, tg = trained
+    h = ctx.neural_create(R0, lat, mlp, tg)
+    if fmt == "fp8":
+        ctx.neural_quantize(h, "fp8")
+    _check_decode(ctx, h, oracle.NeuralTexture.inference_form(R0, lat, mlp, fmt))
+    ctx.neural_destroy(h)
+
+
+def test_decode_error_vs_exact_fp64(ctx, trained):
+    # The error of each inference form (BF16 MLP with FP16 latents, and with FP8 E4M3 latents
+    # and per-grid scales) against the network's exact FP64 value (FP32 master parameters, no
+    # rounding anywhere), on every texel of the oracle-trained network.  The GPU forms' error
+    # is their quantisation error: it equals that of the oracle's own inference forms to a
+    # fraction of a percent, and FP8 latents cost more than FP16 ones.
+    lat, mlp, tg = trained
+    ix, iy = _all_texels()
+    exact = oracle.ntc_decode_exact(R0, lat, mlp, ix, iy)
+    rmse = {}
+    for fmt in ("fp16", "fp8"):
+        h = ctx.neural_create(R0, lat, mlp, tg)
+        if fmt == "fp8":
+            ctx.neural_quantize(h, "fp8")
+        y = ctx.neural_decode(h, torch.from_numpy(ix).cuda(), torch.from_numpy(iy).cuda()).cpu().numpy()
+        ctx.neural_destroy(h)
+        yq, _ = oracle.ntc_decode(oracle.NeuralTexture.inference_form(R0, lat, mlp, fmt), ix, iy)
+        rmse[fmt] = float(np.sqrt(np.mean((y - exact) ** 2)))
+        ref = float(np.sqrt(np.mean((yq - exact) ** 2)))
+        assert abs(rmse[fmt] - ref) <= 0.01 * ref, (fmt, rmse[fmt], ref)
+    print(f"decode RMSE vs exact FP64: BF16+FP16 {rmse['fp16']:.3e}, BF16+FP8 {rmse['fp8']:.3e}")
+    assert rmse["fp16"] < rmse["fp8"] < 0.05
 
 
 def test_gradients_match_oracle(ctx, net, data):
@@ -222,6 +289,8 @@ def test_filter_shade_matches_oracle(ctx, net, data, filter, mode):
     # all queries are held to the one-rounding-step bound, and 90% to the tight one
     err = np.abs(got - ref.rgb)
     tight = (err <= 5e-4 * ref.mag + 1e-6).all(1)
+    near = ref.rdist < NEAR
+    assert tight[~near].all(), float((err[~near] / (ref.mag[~near] + 1e-9)).max())
     assert tight.mean() >= 0.9, (tight.mean(), float((err / (ref.mag + 1e-9)).max()))
     assert np.all(err <= 3e-2 * ref.mag + 1e-5), float((err / (ref.mag + 1e-9)).max())
 
@@ -308,5 +377,7 @@ def test_neural_full_size_sampled(ctx, fmt):
     assert (ref.rgb > 0).all(1).mean() > 0.99         # the comparison is not vacuous
     err = np.abs(got[idx] - ref.rgb)
     tight = (err <= 5e-4 * ref.mag + 1e-6).all(1)
+    near = ref.rdist < NEAR
+    assert tight[~near].all(), float((err[~near] / (ref.mag[~near] + 1e-9)).max())
     assert tight.mean() >= 0.9, (tight.mean(), float((err / (ref.mag + 1e-9)).max()))
     assert np.all(err <= 3e-2 * ref.mag + 1e-5), float((err / (ref.mag + 1e-9)).max())

@@ -54,10 +54,9 @@ def test_features_match_float64_bilinear():
         np.testing.assert_allclose(f[:, 8 * g:8 * g + 8], v, atol=3e-8)
 
 
-def _torch_loss(lat, mlp, targets, ix, iy, R0):
-    """Independent float64 restatement: bilinear features, MLP, MSE (no BF16 rounding)."""
-    L = [torch.tensor(g, dtype=torch.float64, requires_grad=True) for g in lat]
-    M = torch.tensor(mlp, dtype=torch.float64, requires_grad=True)
+def _torch_forward(L, M, ix, iy, R0):
+    """Independent float64 restatement of the decode: bilinear features of the grids L (wrap,
+    at texel centres), MLP M (no BF16 rounding)."""
     W1, b1 = M[:2048].view(64, 32), M[2048:2112]
     W2, b2 = M[2112:6208].view(64, 64), M[6208:6272]
     W3, b3 = M[6272:6784].view(8, 64), M[6784:6792]
@@ -76,11 +75,36 @@ def _torch_loss(lat, mlp, targets, ix, iy, R0):
     x = torch.cat(feats, 1)
     h1 = torch.relu(x @ W1.T + b1)
     h2 = torch.relu(h1 @ W2.T + b2)
-    y = h2 @ W3.T + b3
+    return h2 @ W3.T + b3
+
+
+def _torch_loss(lat, mlp, targets, ix, iy, R0):
+    """Independent float64 restatement: bilinear features, MLP, MSE (no BF16 rounding)."""
+    L = [torch.tensor(g, dtype=torch.float64, requires_grad=True) for g in lat]
+    M = torch.tensor(mlp, dtype=torch.float64, requires_grad=True)
+    y = _torch_forward(L, M, ix, iy, R0)
     t = torch.tensor(targets[iy, ix], dtype=torch.float64) / 255.0
     loss = ((y - t) ** 2).mean()
     loss.backward()
     return float(loss.detach()), M.grad.numpy(), np.concatenate([g.grad.numpy().ravel() for g in L])
+
+
+def test_exact_decode_matches_torch_float64():
+    # the exact FP64 decode (the reference of the inference forms' decode error) against the
+    # independent torch float64 forward, on every texel of a small network
+    lat, mlp, R0 = _small_net()
+    mlp[2048:2112] = 0.05
+    ix, iy = np.meshgrid(np.arange(R0), np.arange(R0))
+    ix, iy = ix.ravel(), iy.ravel()
+    y = oracle.ntc_decode_exact(R0, lat, mlp, ix, iy)
+    with torch.no_grad():
+        t = _torch_forward([torch.tensor(g, dtype=torch.float64) for g in lat],
+                           torch.tensor(np.asarray(mlp, np.float32), dtype=torch.float64), ix, iy, R0).numpy()
+    np.testing.assert_allclose(y, t, rtol=1e-12, atol=1e-13)
+    # the FP16 inference form (BF16 weights and activations, FP16 latents) differs from it by
+    # the quantisation, a few 1e-3 here, not by an error of the decode itself
+    yq, _ = oracle.ntc_decode(oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp16"), ix, iy)
+    assert 1e-5 < np.sqrt(np.mean((yq - y) ** 2)) < 2e-2
 
 
 def test_loss_and_gradients_match_torch_autograd():

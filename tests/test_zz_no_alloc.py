@@ -75,3 +75,15 @@ def test_status_word_is_cleared_per_call(setup):
     assert e.value.status == 6
     q2 = synth.queries_uniform(1000, 74, res=128, lod_range=4.0)
     _compare(ctx, tex, q2, "linear", "stochastic", 1, 1, 0)
+
+
+def test_lod0_and_ewa_match_allocating_entry_point(setup):
+    # the same filters and flags as stf_filter_shade_host: EWA reads the context's weight
+    # table (allocated with the context, so the call still allocates nothing)
+    _, ctx, tex = setup
+    q = synth.queries_aniso(20000, 75, res=128, lod_range=3.0, max_aniso=16.0)
+    u, v, d = _pinned(q)
+    for filter, mode, flags in (("ewa", "stochastic", 0), ("ewa", "ntap_before", 8), ("bspline", "stochastic", 8)):
+        a = ctx.filter_shade_host_noalloc(tex, u, v, d, filter, mode, "ggx", 2, 5, flags)
+        b = ctx.filter_shade_host(tex, u, v, d, filter, mode, "ggx", 2, 5, flags)
+        assert_values(np.stack(a, 1).astype(np.float64), np.stack(b[:3], 1).astype(np.float64))
