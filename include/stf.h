@@ -422,7 +422,9 @@ stf_status stf_neural_grad(stf_ctx ctx, stf_neural net, uint32_t step, uint32_t 
 stf_status stf_neural_grad_range(stf_ctx ctx, stf_neural net, uint32_t step, uint32_t batch, uint32_t first,
                                  uint32_t count, uint64_t seed, float* loss);
 /* Device addresses and lengths (FP32 elements) of the latent and MLP gradient arrays,
- * owned by the network and valid until it is destroyed. */
+ * owned by the network and valid until it is destroyed.  The MLP array follows the latent
+ * array at the next 256-byte boundary, and the gap between them is zero: one all-reduce
+ * (sum) over the FP32 span [grad_latents, grad_mlp + n_mlp) sums both arrays. */
 stf_status stf_neural_grad_buffers(stf_ctx ctx, stf_neural net, float** grad_latents, uint64_t* n_latents,
                                    float** grad_mlp, uint64_t* n_mlp);
 /* Optimiser step k (0 <= k < steps) of a run of `steps` with the current gradients, which

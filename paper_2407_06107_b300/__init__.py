@@ -473,6 +473,17 @@ class Context:
                     self.h)
         return _device_view(pl.value, nl.value, self.device), _device_view(pm.value, nm.value, self.device)
 
+    def neural_grad_bucket(self, net: int):
+        """One float32 cuda tensor over both gradient arrays (latents, the zero gap, MLP): the
+        library lays them out adjacently, so one all-reduce of this view sums both."""
+        pl, nl, pm, nm = _P(), _U64(), _P(), _U64()
+        self._check(lib().stf_neural_grad_buffers(self.h, net, C.byref(pl), C.byref(nl), C.byref(pm), C.byref(nm)),
+                    self.h)
+        gap = pm.value - (pl.value + 4 * nl.value)
+        if not 0 <= gap < 256 or gap % 4:
+            raise StfError(5, "gradient arrays are not adjacent")
+        return _device_view(pl.value, nl.value + gap // 4 + nm.value, self.device)
+
     def neural_adam_step(self, net: int, k: int, steps: int, lr_latent: float = 1e-2, lr_mlp: float = 5e-3,
                          beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, lr_min_frac: float = 1.0):
         ap = _Adam(lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac)
@@ -492,12 +503,12 @@ class Context:
         world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
         rank = dist.get_rank(group) if world > 1 else 0
         step0 = int(self.neural_get(net, "step", 0)[0])
-        dl, dm = self.neural_grad_buffers(net)
-        losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=dl.device)
+        bucket = self.neural_grad_bucket(net)
+        losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=bucket.device)
         dp_train(steps, batch, rank, world,
                  lambda k, first, count: self.neural_grad_range(net, step0 + k, batch, first, count, seed,
                                                                 losses[k:k + 1]),
-                 lambda: (dist.all_reduce(dl, group=group), dist.all_reduce(dm, group=group)),
+                 lambda: dist.all_reduce(bucket, group=group),
                  lambda k: self.neural_adam_step(net, k, steps, lr_latent, lr_mlp, beta1, beta2, eps, lr_min_frac))
         if world > 1:
             dist.all_reduce(losses, group=group)

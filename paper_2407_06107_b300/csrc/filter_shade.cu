@@ -76,7 +76,9 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 const float Wt = wt_next;
                 if (s + 1 < a.spp) raw_next = pick(s + 1, &wt_next);
                 const float3 f = shade(a.shade, decode_raw<TF>(T, raw), SC);
-                acc.x += Wt * f.x; acc.y += Wt * f.y; acc.z += Wt * f.z;
+                acc.x = __fmaf_rn(Wt, f.x, acc.x);
+                acc.y = __fmaf_rn(Wt, f.y, acc.y);
+                acc.z = __fmaf_rn(Wt, f.z, acc.z);
             }
         } else
         for (uint32_t s = 0; s < a.spp; ++s) {

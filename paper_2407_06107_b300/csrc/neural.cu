@@ -23,34 +23,8 @@ namespace stf {
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Packed FP32 pairs (lo, hi) in one 64-bit register pair: the .f32x2 forms of mul, add and
-// fma round each lane to nearest like the scalar instructions, so a pair operation equals
-// two scalar ones bit for bit at half the issue cost.
-__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float2 upk2(uint64_t r) {
-    float2 f;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
-    return f;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
+// Packed FP32 pairs (pk2, upk2, mul2, add2, fma2: .f32x2, one rounding per lane) come from
+// stf_device.cuh.
 // BF16 pair (lo in the low half) of a packed FP32 pair, round to nearest; with RELU,
 // negative values become 0 (ReLU then rounding equals rounding then ReLU)
 template <bool RELU>
@@ -223,7 +197,7 @@ __device__ __forceinline__ void raw_to_pairs(const NeuralView& N, int g, uint4 q
 // `row` of the K-major A tile (same order and rounding as master_features).  The four taps of
 // grid g+1 are loaded before grid g is interpolated, so two grids' gathers are in flight.
 // LF: the latent format (0 FP16, 1 FP8 x scale), fixed per kernel instantiation.
-template <int LF>
+template <int LF, int KA = 32>
 __device__ __forceinline__ void features_to_tile(const NeuralView& N, int ix, int iy, uint8_t* A, int row) {
     LTap tc = latent_taps(N, 0, ix, iy);
     uint4 cur[4];
@@ -251,7 +225,7 @@ __device__ __forceinline__ void features_to_tile(const NeuralView& N, int ix, in
             v = fma2(w01, c[k], v);
             o[k] = bf16x2_of<false>(fma2(w11, d[k], v));
         }
-        *reinterpret_cast<uint4*>(A + kmaj_off(row, 8 * g, 32)) = make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4*>(A + kmaj_off(row, 8 * g, KA)) = make_uint4(o[0], o[1], o[2], o[3]);
         if (g < 3) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
@@ -330,6 +304,42 @@ __global__ void k_pack_mlp(const float* __restrict__ P, __nv_bfloat16* __restric
     }
 }
 
+// Part p (0, 1, 2) of an FP32 value split into three BF16 values whose sum is exact: the
+// rounding h of b, the rounding m of b - h (exact in FP32), and b - h - m (at most 8
+// significant bits, so exactly a BF16 value).
+__device__ __forceinline__ __nv_bfloat16 bf16_part(float b, int p) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(b);
+    const float r1 = __fsub_rn(b, __bfloat162float(h));
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(m));
+    return p == 0 ? h : (p == 1 ? m : __float2bfloat16_rn(r2));
+}
+// MLP master -> BF16 weights with the biases folded in as three extra K columns each (see
+// NeuralView::wext): a GEMM over [x | 1 1 1 | 0..] then adds the FP32 bias exactly, as
+// three exact products inside the FP32 accumulation.
+__global__ void k_pack_mlp_ext(const float* __restrict__ P, __nv_bfloat16* __restrict__ w) {
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 64 * 48 + 64 * 80 + 16 * 80; i += gridDim.x * blockDim.x) {
+        __nv_bfloat16 v = zero;
+        if (i < 64 * 48) {
+            const int o = i / 48, k = i % 48;
+            if (k < 32) v = __float2bfloat16_rn(P[o * 32 + k]);
+            else if (k < 35) v = bf16_part(P[2048 + o], k - 32);
+        } else if (i < 64 * 48 + 64 * 80) {
+            const int j = i - 64 * 48, o = j / 80, k = j % 80;
+            if (k < 64) v = __float2bfloat16_rn(P[2112 + o * 64 + k]);
+            else if (k < 67) v = bf16_part(P[6208 + o], k - 64);
+        } else {
+            const int j = i - 64 * 48 - 64 * 80, o = j / 80, k = j % 80;
+            if (o < 8) {
+                if (k < 64) v = __float2bfloat16_rn(P[6272 + o * 64 + k]);
+                else if (k < 67) v = bf16_part(P[6784 + o], k - 64);
+            }
+        }
+        w[i] = v;
+    }
+}
+
 // ------------------------------------------------------------------ tensor-core decode
 constexpr int NT_ROWS = 128;
 constexpr uint32_t TMEM_COLS = 64;     // the three layers reuse columns 0..63 in turn
@@ -384,7 +394,11 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     if (pair >= npairs) return o;
     uint64_t q;
     uint32_t s;
-    if (npairs <= 0xFFFFFFFFull) {        // 32-bit division (the 64-bit one is a long sequence)
+    if ((a.spp & (a.spp - 1)) == 0u) {    // a power of two: a shift and a mask
+        const int sh = __popc(a.spp - 1);
+        q = pair >> sh;
+        s = (uint32_t)pair & (a.spp - 1);
+    } else if (npairs <= 0xFFFFFFFFull) {   // 32-bit division (the 64-bit one is a long sequence)
         const uint32_t p32 = (uint32_t)pair;
         q = p32 / a.spp;
         s = p32 - (uint32_t)q * a.spp;
@@ -594,6 +608,258 @@ __global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(Neur
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ warp-specialised 1-tap decode
+// The stochastic (one decode per sample) filter + shade of the learned texture as a pipeline
+// per CTA whose stages hand 128-row tiles over through mbarriers instead of block barriers:
+//   warps 0-3, producers: row r of a tile = (query, sample) r -> Philox pick, 16 latent
+//     gathers and FP32 bilinear features -> the BF16 A tile (two buffers, so the next tile is
+//     gathered while this one is in the GEMMs);
+//   warp 8, one lane: the three tcgen05.mma layers of each tile;
+//   warps 4-7, epilogue (TMEM lanes 0-127, one per row): each hidden layer's ReLU and BF16
+//     rounding from TMEM into the H tile, then the 8 channels -> material -> GGX, and each
+//     query's mean over its samples.
+// The biases ride in the GEMMs as three extra K columns (NeuralView::wext, ones in A and H),
+// so an epilogue is a TMEM load, a fused ReLU-and-round and a shared store.  TMEM: layers 1 and
+// 2 accumulate in columns 0-63, layer 3 in 64-79.  Every wait is bounded; a timeout makes every
+// role leave its loop, and the kernel reports DEV_TIMEOUT.
+constexpr int WS_THREADS = 288;
+constexpr int WS_CTAS_PER_SM = 3;
+constexpr uint32_t WS_TMEM_COLS = 128;
+constexpr int WS_K1 = 48, WS_K2 = 80;
+
+struct __align__(128) DecWsSmem {
+    uint8_t A[2][NT_ROWS * WS_K1 * 2];   // features | 1 1 1 | 0 (K-major, no swizzle)
+    uint8_t H[NT_ROWS * WS_K2 * 2];      // hidden activations | 1 1 1 | 0
+    uint8_t W1[64 * WS_K1 * 2];
+    uint8_t W2[64 * WS_K2 * 2];
+    uint8_t W3[16 * WS_K2 * 2];          // rows 8..15 zero
+    long long q[2][NT_ROWS];             // query of each row of an A buffer (-1: idle)
+    float w[2][NT_ROWS];                 // the row's weight (sign * S_x * S_y for a signed filter)
+    uint64_t full_a[2], a_free[2], mma1, mma2, mma3, h1, h2, fin;
+    uint32_t tmem;
+    volatile int abort_flag;
+};
+static_assert(sizeof(DecWsSmem) * WS_CTAS_PER_SM + 3 * 1024 <= 228 * 1024, "three CTAs per SM");
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait that also gives up once any role has given up.
+__device__ __forceinline__ bool ws_wait1(DecWsSmem& S, uint64_t* bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (S.abort_flag || clock64() - t0 > limit) {
+            S.abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// The same for a whole warp: every lane waits, and the decision is the warp's (__all_sync), so
+// a warp whose lanes then run collective instructions (TMEM loads, shuffles) never leaves a
+// loop with some lanes only.
+__device__ __forceinline__ bool ws_wait(DecWsSmem& S, uint64_t* bar, uint32_t parity, long long limit) {
+    return __all_sync(0xFFFFFFFFu, ws_wait1(S, bar, parity, limit));
+}
+// ReLU, then BF16 round-to-nearest, of two FP32 values (lo in the low half)
+__device__ __forceinline__ uint32_t relu_bf16x2(uint32_t lo, uint32_t hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+    return r;
+}
+// one row of a hidden layer: TMEM columns 0..63 of this lane -> ReLU -> BF16 -> row `row` of H
+__device__ __forceinline__ void ws_hidden(uint32_t taddr, uint8_t* H, int row) {
+    uint32_t r[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, r[c]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 8 * c + 2 * i;
+            p[i] = relu_bf16x2(r[k >> 4][k & 15], r[(k + 1) >> 4][(k + 1) & 15]);
+        }
+        *reinterpret_cast<uint4*>(H + kmaj_off(row, 8 * c, WS_K2)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+}
+// the constant columns K0 .. K0+15 of a tile row: 1 1 1 then zeros (bias columns)
+__device__ __forceinline__ void ws_ones(uint8_t* tile, int row, int K0, int K) {
+    *reinterpret_cast<uint4*>(tile + kmaj_off(row, K0, K)) = make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);
+    *reinterpret_cast<uint4*>(tile + kmaj_off(row, K0 + 8, K)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+template <int FILTER, int LF>
+__global__ void __launch_bounds__(WS_THREADS, WS_CTAS_PER_SM)
+k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    DecWsSmem& S = *reinterpret_cast<DecWsSmem*>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const long long limit = a.inject_timeout ? 2000000LL : WAIT_CYCLES;
+
+    stage_weights(S.W1, N.wext, 64, WS_K1);
+    stage_weights(S.W2, N.wext + 64 * WS_K1, 64, WS_K2);
+    stage_weights(S.W3, N.wext + 64 * WS_K1 + 64 * WS_K2, 16, WS_K2);
+    for (int r = t; r < NT_ROWS; r += WS_THREADS) {
+        ws_ones(S.A[0], r, 32, WS_K1);
+        ws_ones(S.A[1], r, 32, WS_K1);
+        ws_ones(S.H, r, 64, WS_K2);
+    }
+    if (t == 0) {
+        mbar_init(&S.full_a[0], NT_ROWS); mbar_init(&S.full_a[1], NT_ROWS);
+        mbar_init(&S.a_free[0], 4); mbar_init(&S.a_free[1], 4);
+        mbar_init(&S.mma1, 1); mbar_init(&S.mma2, 1); mbar_init(&S.mma3, 1); mbar_init(&S.fin, 1);
+        mbar_init(&S.h1, NT_ROWS); mbar_init(&S.h2, NT_ROWS);
+        S.abort_flag = 0;
+    }
+    if (warp == 4) tmem_alloc(&S.tmem, WS_TMEM_COLS);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint64_t nrows = a.nrows;
+    const uint64_t ntiles = (nrows + NT_ROWS - 1) / NT_ROWS;
+
+    if (warp < 4) {
+        // ---------------------------------------------------------------- producers
+        for (uint64_t i = 0;; ++i) {
+            const uint64_t tile = blockIdx.x + i * gridDim.x;
+            if (tile >= ntiles) break;
+            const int b = (int)(i & 1);
+            if (i >= 2 && !ws_wait(S, &S.a_free[b], (uint32_t)(((i >> 1) - 1) & 1), limit)) break;
+            const uint64_t row = tile * NT_ROWS + t;
+            RowOut r{-1, 0, 0, 0.0f};
+            if (row < nrows) r = make_row<FILTER, M_STOCHASTIC>(a, K, row);
+            S.q[b][t] = r.query;
+            S.w[b][t] = r.w;
+            features_to_tile<LF, WS_K1>(N, r.ix, r.iy, S.A[b], t);
+            fence_async_smem();
+            mbar_arrive(&S.full_a[b]);
+        }
+    } else if (warp == 8) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t w1 = smem_u32(S.W1), w2 = smem_u32(S.W2), w3 = smem_u32(S.W3), h = smem_u32(S.H);
+            constexpr uint32_t SB1 = (WS_K1 / 8) * 128, SB2 = (WS_K2 / 8) * 128;
+            for (uint64_t i = 0;; ++i) {
+                const uint64_t tile = blockIdx.x + i * gridDim.x;
+                if (tile >= ntiles) break;
+                const int b = (int)(i & 1);
+                if (!ws_wait1(S, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
+                tc_fence_after();
+                if (!a.inject_timeout) {
+                    const uint32_t aa = smem_u32(S.A[b]);
+#pragma unroll
+                    for (int s = 0; s < WS_K1 / 16; ++s)
+                        mma_bf16(tmem, smem_desc(aa + 256 * s, 128, SB1), smem_desc(w1 + 256 * s, 128, SB1),
+                                 idesc_bf16(128, 64), s > 0);
+                    mma_commit(&S.mma1);
+                }
+                if (!ws_wait1(S, &S.h1, (uint32_t)(i & 1), limit)) break;
+                tc_fence_after();
+                if (!a.inject_timeout) {
+#pragma unroll
+                    for (int s = 0; s < WS_K2 / 16; ++s)
+                        mma_bf16(tmem, smem_desc(h + 256 * s, 128, SB2), smem_desc(w2 + 256 * s, 128, SB2),
+                                 idesc_bf16(128, 64), s > 0);
+                    mma_commit(&S.mma2);
+                }
+                if (!ws_wait1(S, &S.h2, (uint32_t)(i & 1), limit)) break;
+                tc_fence_after();
+                if (!a.inject_timeout) {
+#pragma unroll
+                    for (int s = 0; s < WS_K2 / 16; ++s)
+                        mma_bf16(tmem + 64, smem_desc(h + 256 * s, 128, SB2), smem_desc(w3 + 256 * s, 128, SB2),
+                                 idesc_bf16(128, 16), s > 0);
+                    mma_commit(&S.mma3);
+                }
+            }
+            // every MMA this thread issued has completed before the TMEM is released
+            mma_commit(&S.fin);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&S.fin, 0u) && clock64() - t0 < limit) {}
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int e = t - 128;                                  // TMEM lane = tile row
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const float inv_spp = 1.0f / (float)a.spp;
+        const bool grouped = (32u % a.spp) == 0u;               // a query's samples share a warp
+        for (uint64_t i = 0;; ++i) {
+            const uint64_t tile = blockIdx.x + i * gridDim.x;
+            if (tile >= ntiles) break;
+            const int b = (int)(i & 1);
+            const uint32_t par = (uint32_t)(i & 1);
+            if (!ws_wait(S, &S.mma1, par, limit)) break;
+            // the producers' row data: acquired from their own barrier (its phase for this tile
+            // has completed, and it cannot move on before this warp frees the buffer below)
+            if (!ws_wait(S, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
+            tc_fence_after();
+            const long long q = S.q[b][e];
+            const float w = S.w[b][e];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.a_free[b]);
+            ws_hidden(taddr, S.H, e);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(&S.h1);
+            if (!ws_wait(S, &S.mma2, par, limit)) break;
+            tc_fence_after();
+            ws_hidden(taddr, S.H, e);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(&S.h2);
+            if (!ws_wait(S, &S.mma3, par, limit)) break;
+            tc_fence_after();
+            uint32_t r[16];
+            tmem_ld16(taddr + 64, r);
+            tmem_wait_ld();
+            tc_fence_before();
+            float y[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) y[c] = __uint_as_float(r[c]);
+            float3 est = make_float3(0.f, 0.f, 0.f);
+            if (q >= 0) {
+                const Material m = material_from_channels(y);
+                float3 f;
+                if (a.shade == SH_LINEAR) {
+                    f = m.rho;
+                } else {
+                    float rr, gg, bb;
+                    shade_ggx_t<float>(mat_t(m), rr, gg, bb);
+                    f = make_float3(rr, gg, bb);
+                }
+                est = make_float3(w * f.x, w * f.y, w * f.z);
+            }
+            if (grouped) {
+                // butterfly sum over the query's spp consecutive lanes, then one store
+                for (uint32_t o = 1; o < a.spp; o <<= 1) {
+                    est.x += __shfl_xor_sync(0xFFFFFFFFu, est.x, o);
+                    est.y += __shfl_xor_sync(0xFFFFFFFFu, est.y, o);
+                    est.z += __shfl_xor_sync(0xFFFFFFFFu, est.z, o);
+                }
+                if (q >= 0 && (uint32_t)e % a.spp == 0u) {
+                    a.r[q] = est.x * inv_spp;
+                    a.g[q] = est.y * inv_spp;
+                    a.b[q] = est.z * inv_spp;
+                }
+            } else if (q >= 0) {
+                atomicAdd(a.r + q, est.x * inv_spp);
+                atomicAdd(a.g + q, est.y * inv_spp);
+                atomicAdd(a.b + q, est.z * inv_spp);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0 && S.abort_flag) atomicOr(a.status, DEV_TIMEOUT);
+    tc_fence_after();
+    if (warp == 4) tmem_dealloc(tmem, WS_TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ training (tcgen05)
@@ -966,6 +1232,7 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, uint64_t n, floa
 cudaError_t launch_ntc_quantize(const NeuralView& N, uint64_t lat_total, int fmt, unsigned int* amax_scratch,
                                 cudaStream_t st) {
     k_pack_mlp<<<8, 256, 0, st>>>(N.mlp32, N.wbf, N.bias);
+    k_pack_mlp_ext<<<16, 256, 0, st>>>(N.mlp32, N.wext);
     if (fmt == 0) {
         k_to_fp16<<<1024, 256, 0, st>>>(N.lat32, const_cast<__half*>(N.lat16), lat_total);
     } else {
@@ -990,6 +1257,16 @@ static cudaError_t launch_dec_lf(const NeuralView& N, const NeuralDecodeArgs& a,
     k_ntc_decode_tc<FILTER, MODE, LF><<<grid, NT_ROWS, smem, st>>>(N, a, expand_key(a.seed), make_shade_const());
     return cudaGetLastError();
 }
+template <int FILTER, int LF>
+static cudaError_t launch_dec_ws_lf(const NeuralView& N, const NeuralDecodeArgs& a, int num_sms, cudaStream_t st) {
+    const uint64_t tiles = (a.nrows + NT_ROWS - 1) / NT_ROWS;
+    const uint64_t cap = (uint64_t)num_sms * WS_CTAS_PER_SM;
+    const int grid = (int)(tiles < cap ? (tiles ? tiles : 1) : cap);
+    const size_t smem = sizeof(DecWsSmem);
+    cudaFuncSetAttribute(k_ntc_decode_ws<FILTER, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ntc_decode_ws<FILTER, LF><<<grid, WS_THREADS, smem, st>>>(N, a, expand_key(a.seed));
+    return cudaGetLastError();
+}
 template <int FILTER, int MODE>
 static cudaError_t launch_dec(const NeuralView& N, const NeuralDecodeArgs& a, int grid, cudaStream_t st) {
     return N.latent_fmt == 0 ? launch_dec_lf<FILTER, MODE, 0>(N, a, grid, st) : launch_dec_lf<FILTER, MODE, 1>(N, a, grid, st);
@@ -1005,7 +1282,9 @@ cudaError_t launch_ntc_decode(const NeuralView& N, const NeuralDecodeArgs& a, in
         switch (a.mode) {                                                            \
             case M_NTAP_BEFORE: return launch_dec<F, M_NTAP_BEFORE>(N, a, grid, st); \
             case M_NTAP_AFTER: return launch_dec<F, M_NTAP_AFTER>(N, a, grid, st);   \
-            case M_STOCHASTIC: return launch_dec<F, M_STOCHASTIC>(N, a, grid, st);   \
+            case M_STOCHASTIC:                                                       \
+                return N.latent_fmt == 0 ? launch_dec_ws_lf<F, 0>(N, a, num_sms, st)  \
+                                         : launch_dec_ws_lf<F, 1>(N, a, num_sms, st); \
             default: break;                                                          \
         }                                                                            \
     }

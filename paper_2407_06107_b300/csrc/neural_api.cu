@@ -17,6 +17,7 @@ namespace {
 constexpr uint64_t MLP_N = 6792;              // W1 2048 + b1 64 + W2 4096 + b2 64 + W3 512 + b3 8
 constexpr uint64_t WBF_N = 2048 + 4096 + 1024;
 constexpr uint64_t BIAS_N = 144;
+constexpr uint64_t WEXT_N = 64 * 48 + 64 * 80 + 16 * 80;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -98,10 +99,14 @@ stf_status stf_neural_create(stf_ctx c, const stf_neural_desc* d, stf_neural* ou
     const size_t tgt = d->targets ? (size_t)d->tex_res * d->tex_res * 8 : 0;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-    const size_t o_lat32 = take(T * 4), o_dlat = take(T * 4), o_mlat = take(T * 4), o_vlat = take(T * 4);
+    // the latent and MLP gradients are adjacent (the MLP's start at the next 256-byte boundary;
+    // the gap stays zero), so data-parallel training sums both with one all-reduce
+    const size_t o_lat32 = take(T * 4), o_dlat = take(T * 4), o_grad = take(MLP_N * 4);
+    const size_t o_mlat = take(T * 4), o_vlat = take(T * 4);
     const size_t o_lat16 = take(T * 2), o_lat8 = take(T);
-    const size_t o_mlp = take(MLP_N * 4), o_grad = take(MLP_N * 4), o_mm = take(MLP_N * 4), o_vm = take(MLP_N * 4);
+    const size_t o_mlp = take(MLP_N * 4), o_mm = take(MLP_N * 4), o_vm = take(MLP_N * 4);
     const size_t o_wbf = take(WBF_N * 2), o_bias = take(BIAS_N * 4), o_scale = take(16), o_amax = take(16);
+    const size_t o_wext = take(WEXT_N * 2);
     const size_t o_tgt = take(tgt);
     stf_status s = dev_alloc(c, &r.mem, off);
     if (s != STF_OK) return s;
@@ -114,6 +119,7 @@ stf_status stf_neural_create(stf_ctx c, const stf_neural_desc* d, stf_neural* ou
     r.view.mlp32 = (float*)(b + o_mlp); r.view.grad32 = (float*)(b + o_grad);
     r.m_mlp = (float*)(b + o_mm); r.v_mlp = (float*)(b + o_vm);
     r.view.wbf = (__nv_bfloat16*)(b + o_wbf); r.view.bias = (float*)(b + o_bias);
+    r.view.wext = (__nv_bfloat16*)(b + o_wext);
     r.view.scale_dev = (float*)(b + o_scale); r.amax = (unsigned int*)(b + o_amax);
     r.view.targets = tgt ? (const uint8_t*)(b + o_tgt) : nullptr;
     r.trainable = tgt != 0;

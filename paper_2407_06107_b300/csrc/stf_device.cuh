@@ -13,6 +13,64 @@
 
 namespace stf {
 
+// ---------------------------------------------------------------- scalar / packed FP32 pairs
+// Value arithmetic is written once for T = float (one sample) and T = F2 (two values, one per
+// lane of a 64-bit register pair operated on by the .f32x2 instructions).  Every operation
+// below rounds once, to nearest, per lane.  Each packed instruction returns what the scalar
+// one returns (checked on B300 over 2^25 random operand pairs per operation, with
+// cancellation, subnormals and the byte-decode pattern); a whole kernel built on them agreed
+// with its scalar twin only to an ulp on ~0.1% of results, so the packed forms serve value
+// arithmetic with a tolerance (the learned form's features and epilogues), not the lookup
+// kernels whose specialised and general instantiations must agree bit for bit.
+struct F2 { uint64_t v; };
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t r) {
+    float2 f;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+    return f;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ F2 f2(float lo, float hi) { return F2{pk2(lo, hi)}; }
+__device__ __forceinline__ F2 f2(float x) { return F2{pk2(x, x)}; }
+__device__ __forceinline__ float lo(F2 a) { return upk2(a.v).x; }
+__device__ __forceinline__ float hi(F2 a) { return upk2(a.v).y; }
+__device__ __forceinline__ float lo(float a) { return a; }
+
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) { return F2{mul2(a.v, b.v)}; }
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) { return F2{add2(a.v, b.v)}; }
+// a - b = fma(b, -1, a): one rounding, as __fsub_rn
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) { return F2{fma2(b.v, pk2(-1.0f, -1.0f), a.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2{fma2(a.v, b.v, c.v)}; }
+// a constant of type T
+template <class T> __device__ __forceinline__ T vconst(float x);
+template <> __device__ __forceinline__ float vconst<float>(float x) { return x; }
+template <> __device__ __forceinline__ F2 vconst<F2>(float x) { return f2(x); }
+// per-lane maps
+template <class Fn> __device__ __forceinline__ float vmap(float a, Fn fn) { return fn(a); }
+template <class Fn> __device__ __forceinline__ F2 vmap(F2 a, Fn fn) { const float2 x = upk2(a.v); return f2(fn(x.x), fn(x.y)); }
+
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { SH_GGX = 0, SH_LINEAR = 1 };
 enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u, FLAG_LOD0 = 8u };
@@ -126,66 +184,60 @@ __device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
 //   Mitchell: outer (x-2)^2 (8 - 7x)/18, inner 7x^3/6 - 2x^2 + 8/9 (>= 1/18, in Horner form):
 //     w0 = s^2 (1 - 7t)/18, w3 = t^2 (7t - 6)/18
 // Multiply-add chains are explicit single-rounded FMAs (__fmaf_rn), nothing else fuses.
-template <int F> struct CubicCoef;
-template <> struct CubicCoef<F_MITCHELL> {
-    static constexpr float c3 = 7.0f / 6.0f, c2 = -2.0f, c0 = 8.0f / 9.0f;
-};
-// Mitchell's inner piece (|d| < 1)
-template <int F>
-__device__ __forceinline__ float k_cubic_inner(float d) {
-    using C = CubicCoef<F>;
-    const float a = __fmul_rn(__fmaf_rn(C::c3, d, C::c2), d);
-    return __fmaf_rn(a, d, C::c0);
-}
-
-template <int F>
-__device__ __forceinline__ void axis_weights(float t, float w[4]) {
+// Per-axis weights for T = float (one axis of one sample) or T = F2 (the same axis of two
+// samples, or two axes), in the same operation sequence.
+template <int F, class T>
+__device__ __forceinline__ void axis_weights_t(T t, T w[4]) {
+    const T one = vconst<T>(1.0f);
     if constexpr (F == F_LINEAR) {
-        w[0] = __fsub_rn(1.0f, t);
+        w[0] = vsub(one, t);
         w[1] = t;
     } else if constexpr (F == F_BSPLINE) {
         // the listing's polynomials in Horner form with fused multiply-adds:
         //   (1-t)^3, t^2 (3t - 6) + 4, t (t (3 - 3t) + 3) + 1, t^3, each times 1/6
-        const float s = 1.0f / 6.0f;
-        const float t2 = __fmul_rn(t, t);
-        const float omt = __fsub_rn(1.0f, t);
-        w[0] = __fmul_rn(s, __fmul_rn(__fmul_rn(omt, omt), omt));
-        w[1] = __fmul_rn(s, __fmaf_rn(t2, __fmaf_rn(3.0f, t, -6.0f), 4.0f));
-        w[2] = __fmul_rn(s, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-3.0f, t, 3.0f), 3.0f), 1.0f));
-        w[3] = __fmul_rn(s, __fmul_rn(t2, t));
+        const T k = vconst<T>(1.0f / 6.0f);
+        const T t2 = vmul(t, t);
+        const T omt = vsub(one, t);
+        w[0] = vmul(k, vmul(vmul(omt, omt), omt));
+        w[1] = vmul(k, vfma(t2, vfma(vconst<T>(3.0f), t, vconst<T>(-6.0f)), vconst<T>(4.0f)));
+        w[2] = vmul(k, vfma(t, vfma(t, vfma(vconst<T>(-3.0f), t, vconst<T>(3.0f)), vconst<T>(3.0f)), one));
+        w[3] = vmul(k, vmul(t2, t));
     } else {
-        const float s = __fsub_rn(1.0f, t), t2 = __fmul_rn(t, t), s2 = __fmul_rn(s, s);
+        const T s = vsub(one, t), t2 = vmul(t, t), s2 = vmul(s, s);
         if constexpr (F == F_CATMULL_ROM) {
-            w[0] = __fmul_rn(__fmul_rn(-0.5f, t), s2);
-            w[1] = __fmul_rn(s, __fmaf_rn(t, __fmaf_rn(-1.5f, t, 1.0f), 1.0f));
-            w[2] = __fmul_rn(t, __fmaf_rn(s, __fmaf_rn(-1.5f, s, 1.0f), 1.0f));
-            w[3] = __fmul_rn(__fmul_rn(-0.5f, s), t2);
-        } else {
-            constexpr float k18 = 1.0f / 18.0f;
-            w[0] = __fmul_rn(__fmul_rn(s2, __fmaf_rn(-7.0f, t, 1.0f)), k18);
-            w[1] = k_cubic_inner<F>(t);
-            w[2] = k_cubic_inner<F>(s);
-            w[3] = __fmul_rn(__fmul_rn(t2, __fmaf_rn(7.0f, t, -6.0f)), k18);
+            w[0] = vmul(vmul(vconst<T>(-0.5f), t), s2);
+            w[1] = vmul(s, vfma(t, vfma(vconst<T>(-1.5f), t, one), one));
+            w[2] = vmul(t, vfma(s, vfma(vconst<T>(-1.5f), s, one), one));
+            w[3] = vmul(vmul(vconst<T>(-0.5f), s), t2);
+        } else {   // Mitchell B = C = 1/3; inner piece 7x^3/6 - 2x^2 + 8/9 in Horner form
+            const T k18 = vconst<T>(1.0f / 18.0f), c3 = vconst<T>(7.0f / 6.0f), c2 = vconst<T>(-2.0f);
+            const T c0 = vconst<T>(8.0f / 9.0f);
+            w[0] = vmul(vmul(s2, vfma(vconst<T>(-7.0f), t, one)), k18);
+            w[1] = vfma(vmul(vfma(c3, t, c2), t), t, c0);
+            w[2] = vfma(vmul(vfma(c3, s, c2), s), s, c0);
+            w[3] = vmul(vmul(t2, vfma(vconst<T>(7.0f), t, vconst<T>(-6.0f))), k18);
         }
     }
 }
-
 // Weights for a pick, where only their ratios matter: the B-spline's polynomials without the
 // common factor 1/6 (the CDF pick divides it out; the estimate's weight is 1 for a positive
-// filter), the other filters' weights as axis_weights gives them.
-template <int F>
-__device__ __forceinline__ void axis_pick_weights(float t, float w[4]) {
+// filter), the other filters' weights as axis_weights_t gives them.
+template <int F, class T>
+__device__ __forceinline__ void axis_pick_weights_t(T t, T w[4]) {
     if constexpr (F == F_BSPLINE) {
-        const float t2 = __fmul_rn(t, t);
-        const float omt = __fsub_rn(1.0f, t);
-        w[0] = __fmul_rn(__fmul_rn(omt, omt), omt);
-        w[1] = __fmaf_rn(t2, __fmaf_rn(3.0f, t, -6.0f), 4.0f);
-        w[2] = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-3.0f, t, 3.0f), 3.0f), 1.0f);
-        w[3] = __fmul_rn(t2, t);
+        const T one = vconst<T>(1.0f);
+        const T t2 = vmul(t, t);
+        const T omt = vsub(one, t);
+        w[0] = vmul(vmul(omt, omt), omt);
+        w[1] = vfma(t2, vfma(vconst<T>(3.0f), t, vconst<T>(-6.0f)), vconst<T>(4.0f));
+        w[2] = vfma(t, vfma(t, vfma(vconst<T>(-3.0f), t, vconst<T>(3.0f)), vconst<T>(3.0f)), one);
+        w[3] = vmul(t2, t);
     } else {
-        axis_weights<F>(t, w);
+        axis_weights_t<F, T>(t, w);
     }
 }
+template <int F> __device__ __forceinline__ void axis_weights(float t, float w[4]) { axis_weights_t<F, float>(t, w); }
+template <int F> __device__ __forceinline__ void axis_pick_weights(float t, float w[4]) { axis_pick_weights_t<F, float>(t, w); }
 
 // CDF inversion over one axis: first k with xi*S < prefix_k, S = sum of |w| over the
 // taps of sign class CLS (0: all, +1: w > 0, -1: w < 0).  Returns the tap index.
@@ -297,26 +349,73 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return r;
 }
 
-// f_hat = [rho/pi + D G2 F / (4 nl nv)] nl  (GGX, height-correlated Smith, Schlick)
-__device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst& C) {
-    const float nl = dot3(m.n, C.l), nv = dot3(m.n, C.v);
-    if (!(nl > 0.0f) || !(nv > 0.0f)) return make_float3(0.f, 0.f, 0.f);
-    const float a = fminf(fmaxf(m.rough, 0.05f), 1.0f), a2 = a * a;
-    const float3 nxh = cross3(m.n, C.h);
-    const float nh = dot3(m.n, C.h);
+// The light, view and half vectors and the Fresnel factor as compile-time FP32 constants:
+// l = (0.48, 0.36, 0.80), v = (-0.28, 0, 0.96), h = normalize(l + v) and Fk = F(v.h) / (2 pi)
+// (Schlick, F0 = 0.04, with the constant factors of D G F / 4) evaluated in double and
+// rounded once -- the same values make_shade_const() computes on the host.
+struct GgxK {
+    static constexpr float lx = 0.48f, ly = 0.36f, lz = 0.80f;
+    static constexpr float vx = -0.28f, vz = 0.96f;
+    static constexpr float hx = 0x1.c53674p-4f, hy = 0x1.97e436p-3f, hz = 0x1.f288b4p-1f;
+    static constexpr float Fk = 0x1.a14c3ap-8f;
+};
+
+// A decoded material as scalars (T = float) or as two samples' materials (T = F2).
+template <class T> struct MatT { T rx, ry, rz, rough, nx, ny, nz; };
+
+// f_hat = [rho/pi + D G2 F / (4 nl nv)] nl  (GGX, height-correlated Smith, Schlick), zero
+// where nl <= 0 or nv <= 0.  Every operation is one explicit rounding, so the T = float and
+// T = F2 forms agree bit for bit.
+template <class T>
+__device__ __forceinline__ void shade_ggx_t(const MatT<T>& m, T& r, T& g, T& b) {
+    using K = GgxK;
+    const T nl = vfma(m.nz, vconst<T>(K::lz), vfma(m.ny, vconst<T>(K::ly), vmul(m.nx, vconst<T>(K::lx))));
+    const T nv = vfma(m.nz, vconst<T>(K::vz), vmul(m.nx, vconst<T>(K::vx)));
+    const T a = vmap(m.rough, [](float x) { return fminf(fmaxf(x, 0.05f), 1.0f); });
+    const T a2 = vmul(a, a);
     // |n x h|^2 instead of 1 - (n.h)^2: D = a2 / (pi q^2) is relative to q >= a2 (n.h)^2,
     // so the cancellation of 1 - (n.h)^2 near n = h would show in D
-    const float q = fmaf(a2 * nh, nh, dot3(nxh, nxh));
-    const float rq = rcp_approx(q), rnl = rcp_approx(nl), rnv = rcp_approx(nv);
+    const T cx = vfma(m.ny, vconst<T>(K::hz), vmul(m.nz, vconst<T>(-K::hy)));
+    const T cy = vfma(m.nz, vconst<T>(K::hx), vmul(m.nx, vconst<T>(-K::hz)));
+    const T cz = vfma(m.nx, vconst<T>(K::hy), vmul(m.ny, vconst<T>(-K::hx)));
+    const T nh = vfma(m.nz, vconst<T>(K::hz), vfma(m.ny, vconst<T>(K::hy), vmul(m.nx, vconst<T>(K::hx))));
+    const T q = vfma(vmul(a2, nh), nh, vfma(cz, cz, vfma(cy, cy, vmul(cx, cx))));
+    auto rcp = [](float x) { return rcp_approx(x); };
+    auto rsq = [](float x) { return rsqrt_approx(x); };
+    const T rq = vmap(q, rcp), rnl = vmap(nl, rcp), rnv = vmap(nv, rcp);
     // D = a2 / (pi q^2).  Lambda = (sqrt(1 + a2 tan^2) - 1) / 2 with sin^2 = 1 - (n.w)^2
     // (|n| = 1), so G2 = 1 / (1 + Ll + Lv) = 2 / (sqrt(sl) + sqrt(sv)): a sum of two positive
-    // roots, one reciprocal, no cancellation.  The constants 1/pi, 2 and 1/4 sit in C.Fk.
-    const float xl = a2 * fmaf(-nl, nl, 1.0f) * rnl * rnl, xv = a2 * fmaf(-nv, nv, 1.0f) * rnv * rnv;
-    const float sl = 1.0f + xl, sv = 1.0f + xv;
-    const float rg = rcp_approx(fmaf(sl, rsqrt_approx(sl), sv * rsqrt_approx(sv)));
-    const float spec = a2 * rq * rq * rg * C.Fk * rnv;
-    const float kd = nl * 0.318309886183790672f;
-    return make_float3(fmaf(m.rho.x, kd, spec), fmaf(m.rho.y, kd, spec), fmaf(m.rho.z, kd, spec));
+    // roots, one reciprocal, no cancellation.  The constants 1/pi, 2 and 1/4 sit in Fk.
+    const T one = vconst<T>(1.0f);
+    const T xl = vmul(vmul(vmul(a2, vfma(vmul(nl, vconst<T>(-1.0f)), nl, one)), rnl), rnl);
+    const T xv = vmul(vmul(vmul(a2, vfma(vmul(nv, vconst<T>(-1.0f)), nv, one)), rnv), rnv);
+    const T sl = vadd(one, xl), sv = vadd(one, xv);
+    const T rg = vmap(vfma(sl, vmap(sl, rsq), vmul(sv, vmap(sv, rsq))), rcp);
+    const T spec = vmul(vmul(vmul(vmul(vmul(a2, rq), rq), rg), vconst<T>(K::Fk)), rnv);
+    const T kd = vmul(nl, vconst<T>(0.318309886183790672f));
+    r = vfma(m.rx, kd, spec);
+    g = vfma(m.ry, kd, spec);
+    b = vfma(m.rz, kd, spec);
+    // the lobe exists only above both horizons
+    auto keep = [](float x, float n1, float n2) { return (n1 > 0.0f && n2 > 0.0f) ? x : 0.0f; };
+    if constexpr (sizeof(T) == sizeof(float)) {
+        r = keep(lo(r), lo(nl), lo(nv)); g = keep(lo(g), lo(nl), lo(nv)); b = keep(lo(b), lo(nl), lo(nv));
+    } else {
+        const float2 L = upk2(nl.v), V = upk2(nv.v);
+        const float2 R = upk2(r.v), G = upk2(g.v), B = upk2(b.v);
+        r = f2(keep(R.x, L.x, V.x), keep(R.y, L.y, V.y));
+        g = f2(keep(G.x, L.x, V.x), keep(G.y, L.y, V.y));
+        b = f2(keep(B.x, L.x, V.x), keep(B.y, L.y, V.y));
+    }
+}
+
+__device__ __forceinline__ MatT<float> mat_t(const Material& m) {
+    return {m.rho.x, m.rho.y, m.rho.z, m.rough, m.n.x, m.n.y, m.n.z};
+}
+__device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst&) {
+    float r, g, b;
+    shade_ggx_t<float>(mat_t(m), r, g, b);
+    return make_float3(r, g, b);
 }
 
 __device__ __forceinline__ float3 shade(int sh, const Material& m, const ShadeConst& C) {
@@ -336,25 +435,63 @@ __device__ __forceinline__ float byte_plus_2p23(uint32_t w, uint32_t j) {
 __device__ __forceinline__ float byte_times(uint32_t w, uint32_t j, float k) {
     return __fmaf_rn(byte_plus_2p23(w, j), k, -8388608.0f * k);
 }
-__device__ __forceinline__ float3 decode_normal_rg8(uint32_t xy) {
+// The packed material texel (RGBA8 albedo + roughness in x, RG8 normal in y) of one sample
+// (T = float, t1 ignored) or of two (T = F2: t0 in the low lane, t1 in the high lane).
+//   albedo = byte/255, roughness = 0.05 + 0.95 byte/255;
+//   normal = (X, Y, sqrt R) / 255 with X = 2r - 255, Y = 2g - 255, R = 255^2 - X^2 - Y^2,
+//   exactly unit length when R > 0; otherwise z = 0 and (X, Y) is normalised.
+template <class T>
+__device__ __forceinline__ T bytes_of(uint32_t w0, uint32_t w1, uint32_t j);
+template <> __device__ __forceinline__ float bytes_of<float>(uint32_t w0, uint32_t, uint32_t j) { return byte_plus_2p23(w0, j); }
+template <> __device__ __forceinline__ F2 bytes_of<F2>(uint32_t w0, uint32_t w1, uint32_t j) {
+    return f2(byte_plus_2p23(w0, j), byte_plus_2p23(w1, j));
+}
+template <class T>
+__device__ __forceinline__ MatT<T> decode_rgba8n_t(uint2 t0, uint2 t1 = make_uint2(0u, 0u)) {
+    const float k = 1.0f / 255.0f;
+    MatT<T> m;
+    // byte times k, rounded once: the fused (2^23 + b) k - 2^23 k is exactly b k
+    const T kk = vconst<T>(k), off = vconst<T>(-8388608.0f * k);
+    m.rx = vfma(bytes_of<T>(t0.x, t1.x, 0), kk, off);
+    m.ry = vfma(bytes_of<T>(t0.x, t1.x, 1), kk, off);
+    m.rz = vfma(bytes_of<T>(t0.x, t1.x, 2), kk, off);
+    m.rough = vfma(vconst<T>(0.95f), vfma(bytes_of<T>(t0.x, t1.x, 3), kk, off), vconst<T>(0.05f));
     // 2b - 255 exactly: (2^23 + b) - (2^23 + 127) = b - 127, then 2 (b - 127) - 1
-    const float X = __fmaf_rn(2.0f, __fsub_rn(byte_plus_2p23(xy, 0), 8388735.0f), -1.0f);
-    const float Y = __fmaf_rn(2.0f, __fsub_rn(byte_plus_2p23(xy, 1), 8388735.0f), -1.0f);
-    const float R = 65025.0f - X * X - Y * Y;                        // exact integer radicand
-    // R > 0: |(X, Y, sqrt R)| = 255 exactly; otherwise z = 0 and (X, Y) is normalised
-    if (R > 0.0f) {
-        const float k = 1.0f / 255.0f;
-        return make_float3(X * k, Y * k, R * rsqrt_approx(R) * k);
+    const T X = vfma(vconst<T>(2.0f), vsub(bytes_of<T>(t0.y, t1.y, 0), vconst<T>(8388735.0f)), vconst<T>(-1.0f));
+    const T Y = vfma(vconst<T>(2.0f), vsub(bytes_of<T>(t0.y, t1.y, 1), vconst<T>(8388735.0f)), vconst<T>(-1.0f));
+    const T XY = vfma(Y, Y, vmul(X, X));                              // exact integer
+    const T R = vsub(vconst<T>(65025.0f), XY);                        // exact integer radicand
+    // R > 0: scale 1/255 and z = sqrt(R)/255; otherwise scale 1/|(X, Y)| and z = 0
+    auto sc = [](float r, float xy) { return r > 0.0f ? 1.0f / 255.0f : rsqrt_approx(xy); };
+    auto zz = [](float r) { return r > 0.0f ? __fmul_rn(__fmul_rn(r, rsqrt_approx(r)), 1.0f / 255.0f) : 0.0f; };
+    T scale, z;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        scale = sc(lo(R), lo(XY));
+        z = zz(lo(R));
+    } else {
+        const float2 r = upk2(R.v), xy = upk2(XY.v);
+        scale = f2(sc(r.x, xy.x), sc(r.y, xy.y));
+        z = f2(zz(r.x), zz(r.y));
     }
-    const float inv = rsqrt_approx(X * X + Y * Y);
-    return make_float3(X * inv, Y * inv, 0.0f);
+    m.nx = vmul(X, scale);
+    m.ny = vmul(Y, scale);
+    m.nz = z;
+    return m;
+}
+__device__ __forceinline__ Material mat_of(const MatT<float>& m) {
+    Material r;
+    r.rho = make_float3(m.rx, m.ry, m.rz);
+    r.rough = m.rough;
+    r.n = make_float3(m.nx, m.ny, m.nz);
+    return r;
 }
 __device__ __forceinline__ Material decode_rgba8(uint2 t, bool has_normal) {
+    if (has_normal) return mat_of(decode_rgba8n_t<float>(t));
     Material m;
     const float k = 1.0f / 255.0f;
     m.rho = make_float3(byte_times(t.x, 0, k), byte_times(t.x, 1, k), byte_times(t.x, 2, k));
-    m.rough = fmaf(0.95f, byte_times(t.x, 3, k), 0.05f);
-    m.n = has_normal ? decode_normal_rg8(t.y) : make_float3(0.f, 0.f, 1.f);
+    m.rough = __fmaf_rn(0.95f, byte_times(t.x, 3, k), 0.05f);
+    m.n = make_float3(0.f, 0.f, 1.f);
     return m;
 }
 // Decoded channels (albedo RGB, roughness, normal X and Y, each in [0,1] up to decoding

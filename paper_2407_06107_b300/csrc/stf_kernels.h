@@ -105,6 +105,9 @@ struct NeuralView {
     float* grad32;              // gradients, same layout
     __nv_bfloat16* wbf;         // inference weights: W1 | W2 | W3 padded to 16 rows
     float* bias;                // inference biases: b1 | b2 | b3 padded to 16
+    // inference weights with the biases as extra columns, each FP32 bias split exactly into
+    // three BF16 parts (row-major): W1 | b1 [64][48], W2 | b2 [64][80], W3 | b3 [16][80]
+    __nv_bfloat16* wext;
     const uint8_t* targets;     // explicit 8-channel texture [tex_res][tex_res][8]
 };
 

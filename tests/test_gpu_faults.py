@@ -67,3 +67,20 @@ def test_decode_wait_times_out_and_reports(stf):
     y = ok.neural_decode(net, ix, ix)
     assert torch.isfinite(y).all() and ok.device_status() == 0
     ok.close()
+
+
+def test_stochastic_decode_pipeline_times_out_and_reports(stf):
+    # the 1-tap neural filter's pipelined kernel: with no MMA issued, its epilogue's bounded
+    # wait runs out, every role leaves its loop, and the status reports the timeout
+    ctx = _ctx(stf, "mma_timeout")
+    lat, mlp = synth.ntc_init((8, 4, 2, 1), 3)
+    net = ctx.neural_create(16, lat, mlp, None)
+    u = torch.rand(500, device="cuda")
+    ctx.neural_filter_shade(net, u, u, None, "bspline", "stochastic", "ggx", 4, 1)
+    assert ctx.device_status() & stf.DEV_TIMEOUT
+    ctx.close()
+    ok = stf.Context(0)
+    net = ok.neural_create(16, lat, mlp, None)
+    r, g, b = ok.neural_filter_shade(net, u, u, None, "bspline", "stochastic", "ggx", 4, 1)
+    assert torch.isfinite(r).all() and ok.device_status() == 0
+    ok.close()
