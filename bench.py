@@ -781,6 +781,19 @@ def neural_block(ctx, dev, material, steps=1 << 14, batch=1 << 12, nq=1 << 24, s
                                                        out=out), 2)
     res["fp8"] = {"mse_vs_targets": float(((y8 - tg) ** 2).mean()), "rmse_vs_fp16_form": float(np.sqrt(((y8 - y16) ** 2).mean())),
                   "ms_stochastic_1tap": ms8, "latent_bytes": lat_bytes_fp16 // 2}
+    # the precision / batching stress of the learned form: FP8 E4M3 latents with per-grid
+    # scales and the BF16 MLP, bicubic Mitchell (sign-carried) at 4 spp over 2^26 uniform queries
+    del u, v, out
+    n5 = 1 << 26
+    q5 = synth.queries_uniform(n5, 10)
+    u5, v5 = torch.from_numpy(q5.u).to(dev), torch.from_numpy(q5.v).to(dev)
+    del q5
+    out5 = [torch.empty(n5, dtype=torch.float32, device=dev) for _ in range(3)]
+    ms5 = _time_launch(lambda: ctx.neural_filter_shade(net, u5, v5, None, "mitchell", "stochastic", "ggx", 4, 1,
+                                                       out=out5), 2)
+    res["fp8"]["mitchell_4spp_2p26"] = {"ms": ms5, "lookups_per_s": n5 * 4 / (ms5 / 1e3),
+                                        "mlp_tflops": n5 * 4 * flop_per_decode / (ms5 / 1e3) / 1e12}
+    del u5, v5, out5
     ctx.neural_destroy(net)
     return res
 

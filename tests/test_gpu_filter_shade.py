@@ -245,6 +245,31 @@ def test_full_size_sampled(ctx, filter, mode):
     assert_values(rgb, ref.rgb, near, scale=ref.mag)
 
 
+@pytest.mark.parametrize("filter", ["bspline", "mitchell"])
+def test_rmse_reference_matches_oracle(ctx, filter):
+    # The bench's equal-RMSE reference is the GPU's exact filter-after pass with 16 x 16
+    # stratified footprint samples on the first 2^16 queries of the workload (the bench may not
+    # run the oracle).  Pin it to the FP64 oracle on a sample of those queries, value by value,
+    # and check that an 8-spp stochastic estimate's RMSE against the GPU reference equals its
+    # RMSE against the oracle's to 1e-3 relative.
+    m = _full_material()
+    h = _full_handle(ctx, m)
+    q = _full_queries()
+    idx = np.sort(np.random.default_rng(17).choice(1 << 16, 256, replace=False))
+    qs = q.subset(idx)
+    u, v, d = _dev(qs)
+    r, g, b, _ = ctx.filter_shade(h, u, v, d, filter, "ntap_after", "ggx", 256, 1, oracle.FLAG_STRATIFIED)
+    R = torch.stack([r, g, b], 1).cpu().numpy().astype(np.float64)
+    ref = oracle.filter_shade(oracle.Texture(m.albedo_rough, m.normal), qs, filter, "ntap_after", "ggx", 256, 1,
+                              oracle.FLAG_STRATIFIED)
+    assert_values(R, ref.rgb, scale=ref.mag)
+    r, g, b, _ = ctx.filter_shade(h, u, v, d, filter, "stochastic", "ggx", 8, 7, 0)
+    S = torch.stack([r, g, b], 1).cpu().numpy().astype(np.float64)
+    rmse_gpu = np.sqrt(np.mean((S - R) ** 2))
+    rmse_oracle = np.sqrt(np.mean((S - ref.rgb) ** 2))
+    assert abs(rmse_gpu - rmse_oracle) <= 1e-3 * rmse_oracle, (rmse_gpu, rmse_oracle)
+
+
 def _full_queries():
     if "q" not in _FULL:
         _FULL["q"] = synth.queries_uniform(1 << 24, 1, res=4096, lod_range=8.0)
