@@ -250,6 +250,235 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
     }
 }
 
+// ---------------------------------------------------------------- TMA-staged tricubic N-tap
+// The 64-tap comparators (tricubic filter-before / filter-after) with no flags: at every
+// march step the 32 rays of a warp (an 8 x 4 pixel tile) read 4 x 4 x 4 voxel windows that
+// mostly overlap.  One lane copies the box that holds all of them into the warp's shared
+// memory with one 3-D TMA copy (cp.async.bulk.tensor, completion on an mbarrier); the lanes
+// then read their windows from there, in the same order and with the same arithmetic as
+// k_march, so the results are identical.  The box is 24 x 8 x 8 voxels and starts at an x that
+// is a multiple of 8 (a 16-byte boundary); a step whose windows do not fit in it, or that
+// needs clamping at a face of the volume, reads from global memory as k_march does.
+// Every lane of a warp runs every (sample, step) in lockstep (rays that miss the volume sit
+// idle), so the box and the copy are the warp's; waits are bounded, and a copy that times out
+// sets DEV_TIMEOUT and sends the rest of the warp's steps to global memory.
+constexpr int SB_X = 24, SB_Y = 8, SB_Z = 8, SB_ELEMS = SB_X * SB_Y * SB_Z;
+constexpr long long SB_WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* tmap, int x, int y, int z, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"((uint32_t)(SB_ELEMS * 2))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool sb_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > SB_WAIT_CYCLES) return false;
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_march_staged(MarchArgs a, const __grid_constant__ CUtensorMap tmap, RoundKeys K) {
+    constexpr int NT = 4, T0 = -1;
+    __shared__ __align__(128) __half box[4][SB_ELEMS];
+    __shared__ __align__(8) uint64_t bar[4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) mbar_init(&bar[warp], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+    uint32_t phase = 0;
+    bool staging = true;            // false after a copy timed out (this warp's steps then read global memory)
+    const float res[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < a.pix_count;
+    uint64_t o = i;
+    if (a.tiled) {
+        const uint64_t tile = i >> 5;
+        const uint32_t ln = (uint32_t)i & 31u, tpr = a.width >> 3;
+        o = (tile / tpr * 4u + (ln >> 3)) * (uint64_t)a.width + (tile % tpr) * 8u + (ln & 7u);
+    }
+    const uint64_t pix = a.pix_begin + o;
+    const uint32_t px = (uint32_t)(pix % a.width), py = (uint32_t)(pix / a.width);
+    const uint32_t id_lo = (uint32_t)pix, id_hi = (uint32_t)(pix >> 32);
+    const __half* bx = box[warp];
+    float acc = 0.0f;
+    for (uint32_t s = 0; s < a.spp; ++s) {
+        float d[3] = {0.f, 0.f, 0.f}, e[3] = {0.f, 0.f, 0.f};
+        float tmin = 0.0f, tmax = -1.0f;
+        if (valid) {
+            const uint4 r = philox(id_lo, id_hi, s, 0u, K);
+            const float jx = unif(r.x), jy = unif(r.y);
+            const float sx = __fmaf_rn(__fadd_rn((float)px, jx), __fdiv_rn(2.0f, (float)a.width), -1.0f);
+            const float sy = __fmaf_rn(-__fadd_rn((float)py, jy), __fdiv_rn(2.0f, (float)a.height), 1.0f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                e[c] = a.cam[c];
+                d[c] = __fmaf_rn(sy, a.cam[9 + c], __fmaf_rn(sx, a.cam[6 + c], a.cam[3 + c]));
+            }
+            const float l2 = __fmaf_rn(d[2], d[2], __fmaf_rn(d[1], d[1], __fmul_rn(d[0], d[0])));
+            const float inv = __fdiv_rn(1.0f, __fsqrt_rn(l2));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d[c] = __fmul_rn(d[c], inv);
+            tmax = __int_as_float(0x7f800000);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (d[c] != 0.0f) {
+                    const float id = __fdiv_rn(1.0f, d[c]);
+                    const float t1 = __fmul_rn(__fsub_rn(0.0f, e[c]), id), t2 = __fmul_rn(__fsub_rn(1.0f, e[c]), id);
+                    tmin = fmaxf(tmin, fminf(t1, t2));
+                    tmax = fminf(tmax, fmaxf(t1, t2));
+                } else if (e[c] < 0.0f || e[c] > 1.0f) {
+                    tmax = -1.0f;
+                }
+            }
+        }
+        const bool hit = valid && tmin < tmax;
+        if (!__any_sync(0xFFFFFFFFu, hit)) {       // the whole warp misses the volume
+            if (valid) acc += 1.0f;
+            continue;
+        }
+        const float dt = hit ? __fdiv_rn(__fsub_rn(tmax, tmin), (float)a.steps) : 0.0f;
+        const float sdt = a.sigma_scale * dt;
+        float Ssum = 0.0f, Scomp = 0.0f;   // before: compensated sum of filtered sigma / scale
+        float P = 1.0f, Pe = 0.0f;         // after: compensated product
+        for (uint32_t k = 0; k < a.steps; ++k) {
+            AxisPos ap[3] = {{0, 0.0f}, {0, 0.0f}, {0, 0.0f}};
+            float w[3][4];
+            if (hit) {
+                const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ap[c] = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) axis_weights<F_BSPLINE>(ap[c].t, w[c]);
+            }
+            const int x0 = ap[0].i0 + T0, y0 = ap[1].i0 + T0, z0 = ap[2].i0 + T0;
+            // the box of the warp's windows (rays that miss take no part)
+            const int BIG = 1 << 30;
+            const int xmn = __reduce_min_sync(0xFFFFFFFFu, hit ? x0 : BIG), xmx = __reduce_max_sync(0xFFFFFFFFu, hit ? x0 : -BIG);
+            const int ymn = __reduce_min_sync(0xFFFFFFFFu, hit ? y0 : BIG), ymx = __reduce_max_sync(0xFFFFFFFFu, hit ? y0 : -BIG);
+            const int zmn = __reduce_min_sync(0xFFFFFFFFu, hit ? z0 : BIG), zmx = __reduce_max_sync(0xFFFFFFFFu, hit ? z0 : -BIG);
+            const int xs = xmn & ~7;
+            // staged: every window inside the volume (no clamping) and inside the box, with 4
+            // voxels of slack after the last window in x for the 8-byte row reads below
+            bool staged = staging && xmn >= 0 && ymn >= 0 && zmn >= 0 && xmx + 8 <= a.nx && ymx + NT <= a.ny &&
+                          zmx + NT <= a.nz && xmx + 8 - xs <= SB_X && ymx + NT - ymn <= SB_Y && zmx + NT - zmn <= SB_Z;
+            if (staged) {
+                if (lane == 0) tma_load_box(box[warp], &tmap, xs, ymn, zmn, &bar[warp]);
+                const bool ok = __all_sync(0xFFFFFFFFu, sb_wait(&bar[warp], phase));
+                phase ^= 1u;
+                if (!ok) {
+                    staging = staged = false;
+                    if (lane == 0) atomicOr(a.status, DEV_TIMEOUT);
+                }
+            }
+            if (hit) {
+                float fsig = 0.0f, fab = 0.0f;   // sum w d, sum w (1 - exp(-sigma dt))
+                auto tap = [&](float ww, float dv) {
+                    if (MODE == M_NTAP_BEFORE) {
+                        fsig = fmaf(ww, dv, fsig);
+                    } else if (dv != 0.0f) {
+                        fab = fmaf(ww, -expm1f(-sdt * dv), fab);
+                    }
+                };
+                const int xa = x0 & ~3;   // 8-byte aligned start of the row segment
+                const bool rows = staged || ((a.nx & 3) == 0 && x0 >= 0 && xa + 8 <= a.nx && y0 >= 0 && y0 + NT <= a.ny &&
+                                             z0 >= 0 && z0 + NT <= a.nz);
+                if (rows) {
+                    // each row's 4 voxels from two aligned 8-byte reads, realigned with funnel shifts
+                    const int off = x0 - xa;          // 0..3
+                    const bool hi_pair = (off & 2) != 0, odd = (off & 1) != 0;
+#pragma unroll
+                    for (int cz = 0; cz < NT; ++cz) {
+#pragma unroll
+                        for (int cy = 0; cy < NT; ++cy) {
+                            const float wyz = w[2][cz] * w[1][cy];
+                            uint2 lo2, hi2;
+                            if (staged) {
+                                const uint2* row = reinterpret_cast<const uint2*>(
+                                    bx + ((z0 + cz - zmn) * SB_Y + (y0 + cy - ymn)) * SB_X + (xa - xs));
+                                lo2 = row[0]; hi2 = row[1];
+                            } else {
+                                const uint2* row = reinterpret_cast<const uint2*>(
+                                    a.vox + ((size_t)(z0 + cz) * a.ny + (size_t)(y0 + cy)) * a.nx + xa);
+                                lo2 = __ldg(row); hi2 = __ldg(row + 1);
+                            }
+                            const uint32_t q0 = hi_pair ? lo2.y : lo2.x, q1 = hi_pair ? hi2.x : lo2.y,
+                                           q2 = hi_pair ? hi2.y : hi2.x;
+                            const uint32_t p0 = odd ? __funnelshift_r(q0, q1, 16) : q0;
+                            const uint32_t p1 = odd ? __funnelshift_r(q1, q2, 16) : q1;
+                            const float2 f01 = __half22float2(*reinterpret_cast<const __half2*>(&p0));
+                            const float2 f23 = __half22float2(*reinterpret_cast<const __half2*>(&p1));
+                            tap(wyz * w[0][0], f01.x);
+                            tap(wyz * w[0][1], f01.y);
+                            tap(wyz * w[0][2], f23.x);
+                            tap(wyz * w[0][3], f23.y);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int cz = 0; cz < NT; ++cz) {
+#pragma unroll
+                        for (int cy = 0; cy < NT; ++cy) {
+                            const float wyz = w[2][cz] * w[1][cy];
+#pragma unroll
+                            for (int cx = 0; cx < NT; ++cx) tap(wyz * w[0][cx], vox(a, x0 + cx, y0 + cy, z0 + cz));
+                        }
+                    }
+                }
+                if (MODE == M_NTAP_BEFORE) {
+                    const float t = Ssum + fsig;   // Neumaier compensated summation
+                    Scomp += (fabsf(Ssum) >= fabsf(fsig)) ? (Ssum - t) + fsig : (fsig - t) + Ssum;
+                    Ssum = t;
+                } else if (fab != 0.0f) {
+                    const float f = 1.0f - fab;
+                    const float p = P * f;
+                    Pe = fmaf(Pe, f, fmaf(P, f, -p));   // exact error of P*f, carried
+                    P = p;
+                }
+            }
+            __syncwarp();   // every lane has read the box before the next copy overwrites it
+        }
+        if (hit) acc += (MODE == M_NTAP_BEFORE) ? expf(-sdt * (Ssum + Scomp)) : P + Pe;
+        else if (valid) acc += 1.0f;
+    }
+    if (valid) a.T[o] = acc / (float)a.spp;
+    if (!staging && lane == 0) {
+        // a copy that timed out may still be in flight: give it one more bounded wait before the
+        // block's shared memory is released
+        sb_wait(&bar[warp], phase ^ 1u);
+    }
+}
+
+// The volume as a 3-D FP16 tensor for the staged march: dims (nx, ny, nz), x fastest, box
+// 24 x 8 x 8.  Needs 16-byte row and slice strides (nx a multiple of 8); false otherwise or if
+// the driver cannot encode it.
+bool encode_volume_tmap(CUtensorMap* out, const void* vox, int nx, int ny, int nz) {
+    if (nx % 8 != 0 || nx < SB_X || ny < SB_Y || nz < SB_Z) return false;
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * ny * 2};
+    const cuuint32_t boxd[3] = {SB_X, SB_Y, SB_Z}, estr[3] = {1, 1, 1};
+    return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(vox), dims, strides, boxd, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // One block per 128 pixels: rays cost very different amounts (a ray that misses the
 // volume takes no steps), and the hardware block scheduler balances them as blocks retire.
 // Measured at 1920x1080 x 8 spp, this beats a one-wave grid-stride launch by 17-24 % for
@@ -280,8 +509,22 @@ static cudaError_t launch_f(const MarchArgs& a, cudaStream_t st) {
     }
 }
 
-cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st) {
+cudaError_t launch_march(const MarchArgs& a, const CUtensorMap* tmap, int num_sms, cudaStream_t st) {
     (void)num_sms;
+    if (tmap && a.filter == F_BSPLINE && (a.mode == M_NTAP_BEFORE || a.mode == M_NTAP_AFTER) && a.flags == 0 &&
+        a.picks == nullptr) {
+        // staged: 8 x 4 pixel tiles per warp where the range allows, so a warp's windows share a box
+        MarchArgs b = a;
+        const uint64_t band = 4ull * a.width;
+        b.tiled = (a.width % 8 == 0 && a.pix_begin % band == 0 && a.pix_count % band == 0) ? 1 : 0;
+        const uint64_t need = (a.pix_count + 127) / 128;
+        if (need > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+        if (a.mode == M_NTAP_BEFORE)
+            k_march_staged<M_NTAP_BEFORE><<<(int)(need ? need : 1), 128, 0, st>>>(b, *tmap, expand_key(a.seed));
+        else
+            k_march_staged<M_NTAP_AFTER><<<(int)(need ? need : 1), 128, 0, st>>>(b, *tmap, expand_key(a.seed));
+        return cudaGetLastError();
+    }
     if (a.filter == F_LINEAR) return launch_f<F_LINEAR>(a, st);
     if (a.filter == F_BSPLINE) return launch_f<F_BSPLINE>(a, st);
     return cudaErrorInvalidValue;

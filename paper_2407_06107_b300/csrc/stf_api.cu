@@ -718,6 +718,7 @@ stf_status stf_create_volume(stf_ctx c, uint32_t nx, uint32_t ny, uint32_t nz, s
     cudaError_t e = cudaMemcpyAsync(rec.mem, data, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { cudaFree(rec.mem); return cuda_fail(c, e, "volume upload"); }
+    rec.tmap_ok = stf::encode_volume_tmap(&rec.tmap, rec.mem, (int)nx, (int)ny, (int)nz);
     const uint64_t h = c->next_handle++;
     c->vol[h] = rec;
     *out = h;
@@ -769,7 +770,7 @@ stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t wid
     const uint64_t band = 4ull * width;
     a.tiled = (m != STF_MODE_NTAP_BEFORE && width % 8 == 0 && pix_begin % band == 0 && pix_count % band == 0) ? 1 : 0;
     a.T = out_T; a.picks = out_picks; a.status = c->d_status;
-    cudaError_t e = stf::launch_march(a, c->num_sms, c->stream);
+    cudaError_t e = stf::launch_march(a, it->second.tmap_ok ? &it->second.tmap : nullptr, c->num_sms, c->stream);
     return e == cudaSuccess ? STF_OK : cuda_fail(c, e, "march launch");
 }
 

@@ -20,6 +20,8 @@ struct VolRec {
     void* mem = nullptr;
     uint32_t nx = 0, ny = 0, nz = 0;
     float sigma_scale = 1.0f;
+    CUtensorMap tmap{};             // the voxels as a TMA tensor (valid when tmap_ok)
+    bool tmap_ok = false;
 };
 struct NeuralRec {
     void* mem = nullptr;           // one allocation for every array below

@@ -71,6 +71,23 @@ template <> __device__ __forceinline__ F2 vconst<F2>(float x) { return f2(x); }
 template <class Fn> __device__ __forceinline__ float vmap(float a, Fn fn) { return fn(a); }
 template <class Fn> __device__ __forceinline__ F2 vmap(F2 a, Fn fn) { const float2 x = upk2(a.v); return f2(fn(x.x), fn(x.y)); }
 
+// ---------------------------------------------------------------- shared memory and mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 enum { M_NTAP_BEFORE = 0, M_NTAP_AFTER = 1, M_STOCHASTIC = 2, M_POSITIVIZED = 3 };
 enum { SH_GGX = 0, SH_LINEAR = 1 };
 enum { FLAG_STRATIFIED = 1u, FLAG_LATTICE = 2u, FLAG_REUSE = 4u, FLAG_LOD0 = 8u };

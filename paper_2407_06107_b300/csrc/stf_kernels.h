@@ -1,6 +1,7 @@
 // Internal launch interface between the C-ABI layer (stf_api.cu) and the kernels.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -145,7 +146,10 @@ cudaError_t launch_filter_shade_table(const FilterShadeArgs& a, const FetchCtx* 
                                       const uint32_t* tex_id, unsigned long long* counter, int num_sms,
                                       cudaStream_t st);
 cudaError_t launch_triplanar(const TriplanarArgs& a, const TexView tv[3], cudaStream_t st);
-cudaError_t launch_march(const MarchArgs& a, int num_sms, cudaStream_t st);
+// tmap: the volume as a 3-D FP16 tensor map with a 24 x 8 x 8 box (encode_volume_tmap), or
+// null; with it, the tricubic N-tap marches stage each warp's voxels in shared memory by TMA.
+cudaError_t launch_march(const MarchArgs& a, const CUtensorMap* tmap, int num_sms, cudaStream_t st);
+bool encode_volume_tmap(CUtensorMap* out, const void* vox, int nx, int ny, int nz);
 cudaError_t launch_bin_queries(uint64_t n, const float* u, const float* v, const uint32_t* tex_id, uint32_t ntex,
                                uint32_t tile_log2, uint32_t* order, uint32_t* scratch, uint64_t nbins,
                                cudaStream_t st);

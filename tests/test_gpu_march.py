@@ -166,3 +166,25 @@ def test_tiled_and_row_order_agree(ctx, small, mode):
     rows = torch.cat([a, b]).cpu().numpy()
     assert np.array_equal(full.cpu().numpy(), rows)
     assert np.array_equal(pk_full.cpu().numpy(), torch.cat([pk_a, pk_b]).cpu().numpy())
+
+
+@pytest.mark.parametrize("mode", ["ntap_before", "ntap_after"])
+@pytest.mark.parametrize("w,h", [(160, 96), (40, 24), (37, 23)])
+def test_staged_tricubic_equals_unstaged(ctx, small, mode, w, h):
+    # the tricubic N-tap march without flags stages each warp's voxel box in shared memory by
+    # TMA (8 x 4 pixel tiles when the range allows, row order otherwise; steps whose windows do
+    # not fit the box or need clamping read global memory).  With pick output the unstaged
+    # kernel runs.  Same voxels, same order: identical results, and both match the oracle.
+    hnd, vol = small
+    cam = synth.camera_pinhole(w, h).as_array()
+    staged, _ = ctx.march_volume(hnd, cam, w, h, 96, "bspline", mode, spp=2, seed=7)
+    plain, pk = ctx.march_volume(hnd, cam, w, h, 96, "bspline", mode, spp=2, seed=7, want_picks=True)
+    torch.cuda.synchronize()
+    assert torch.equal(staged, plain)
+    ref = oracle.march(vol, 20.0, cam, w, h, 96, "bspline", mode, spp=2, seed=7)
+    assert_values(staged.cpu().numpy(), ref.T)
+    # a sub-range of whole 4-row bands and one that is not
+    for begin, cnt in ((4 * w, 8 * w), (5, 3 * w + 1)):
+        part, _ = ctx.march_volume(hnd, cam, w, h, 96, "bspline", mode, spp=2, seed=7, pix_begin=begin, pix_count=cnt)
+        torch.cuda.synchronize()
+        assert torch.equal(part, plain[begin:begin + cnt])
