@@ -310,11 +310,18 @@ def test_binned_order_is_permutation_and_results_identical(ctx, material):
     fv = np.mod(q.v.astype(np.float64), 1.0)
     tile = (np.minimum((fv * 16).astype(int), 15) << 4) | np.minimum((fu * 16).astype(int), 15)
     assert np.all(np.diff(tile[o]) >= 0)
+    _, otex, _ = material
     for f, mode in (("bspline", "stochastic"), ("mitchell", "positivized"), ("linear", "ntap_before")):
         a = ctx.filter_shade(h, u, v, d, f, mode, "ggx", 3, 4, want_picks=True)
         b = ctx.filter_shade(h, u, v, d, f, mode, "ggx", 3, 4, want_picks=True, order=order)
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+        # and the binned run against the oracle itself (each query keeps its id)
+        torch.cuda.synchronize()
+        ref = oracle.filter_shade(otex, q, f, mode, "ggx", 3, 4, want_picks=True)
+        mism = compare_picks(b[3].cpu().numpy().view(np.uint32), ref, q.n)
+        rgb = torch.stack(b[:3], 1).cpu().numpy().astype(np.float64)
+        assert_values(rgb, ref.rgb, mism, scale=ref.mag)
     # one sample, no picks: the two-queries-per-thread kernel follows the order too
     a = ctx.filter_shade(h, u, v, d, "bspline", "stochastic", "ggx", 1, 4)
     b = ctx.filter_shade(h, u, v, d, "bspline", "stochastic", "ggx", 1, 4, order=order)
