@@ -114,36 +114,18 @@ __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, 
     return t;
 }
 
-// 8 FP32 master latent channels of one grid texel as 4 packed pairs
+// 8 FP32 master latent channels of one grid texel (32 bytes, one sector) as 4 packed pairs:
+// one 256-bit load, read-only during the kernel and not kept in L1 (random texels have no
+// reuse within an SM; L1 stays for the registers a thread spills)
 __device__ __forceinline__ void load_master8(const NeuralView& N, int g, int x, int y, uint64_t v[4]) {
-    const float4* p = reinterpret_cast<const float4*>(N.lat32 + N.lat_off[g] + ((size_t)y * N.res[g] + x) * 8);
-    const float4 a = p[0], b = p[1];
-    v[0] = pk2(a.x, a.y); v[1] = pk2(a.z, a.w); v[2] = pk2(b.x, b.y); v[3] = pk2(b.z, b.w);
+    const float* p = N.lat32 + N.lat_off[g] + ((size_t)y * N.res[g] + x) * 8;
+    float a[8];
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+                 : "l"(p));
+    v[0] = pk2(a[0], a[1]); v[1] = pk2(a[2], a[3]); v[2] = pk2(a[4], a[5]); v[3] = pk2(a[6], a[7]);
 }
 
-// The 32 features of a training sample from the FP32 master latents, as 16 packed pairs:
-// per grid and channel, w00 a + w10 b + w01 c + w11 d in this order, each step one
-// rounding (the oracle's order).  No stores in between, so all 16 gathers can be in flight.
-__device__ __forceinline__ void master_features(const NeuralView& N, int ix, int iy, uint64_t f[16]) {
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const LTap t = latent_taps(N, g, ix, iy);
-        uint64_t a[4], b[4], c[4], d[4];
-        load_master8(N, g, t.x0, t.y0, a);
-        load_master8(N, g, t.x1, t.y0, b);
-        load_master8(N, g, t.x0, t.y1, c);
-        load_master8(N, g, t.x1, t.y1, d);
-        const uint64_t w00 = pk2(t.w00, t.w00), w10 = pk2(t.w10, t.w10);
-        const uint64_t w01 = pk2(t.w01, t.w01), w11 = pk2(t.w11, t.w11);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint64_t v = mul2(w00, a[k]);
-            v = fma2(w10, b[k], v);
-            v = fma2(w01, c[k], v);
-            f[4 * g + k] = fma2(w11, d[k], v);
-        }
-    }
-}
 // Inference form (FP16 or FP8 latents): the four taps of a grid as raw 16-byte (FP16) or
 // 8-byte (FP8, in .x .y) texels, and their conversion to packed FP32 pairs.
 template <int LF>
@@ -632,11 +614,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Bounded wait that also gives up once any role has given up.
-__device__ __forceinline__ bool ws_wait1(DecWsSmem& S, uint64_t* bar, uint32_t parity, long long limit) {
+__device__ __forceinline__ bool ws_wait1(volatile int* abort_flag, uint64_t* bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (S.abort_flag || clock64() - t0 > limit) {
-            S.abort_flag = 1;
+        if (*abort_flag || clock64() - t0 > limit) {
+            *abort_flag = 1;
             return false;
         }
     }
@@ -645,8 +627,8 @@ __device__ __forceinline__ bool ws_wait1(DecWsSmem& S, uint64_t* bar, uint32_t p
 // The same for a whole warp: every lane waits, and the decision is the warp's (__all_sync), so
 // a warp whose lanes then run collective instructions (TMEM loads, shuffles) never leaves a
 // loop with some lanes only.
-__device__ __forceinline__ bool ws_wait(DecWsSmem& S, uint64_t* bar, uint32_t parity, long long limit) {
-    return __all_sync(0xFFFFFFFFu, ws_wait1(S, bar, parity, limit));
+__device__ __forceinline__ bool ws_wait(volatile int* abort_flag, uint64_t* bar, uint32_t parity, long long limit) {
+    return __all_sync(0xFFFFFFFFu, ws_wait1(abort_flag, bar, parity, limit));
 }
 // ReLU, then BF16 round-to-nearest, of two FP32 values (lo in the low half)
 __device__ __forceinline__ uint32_t relu_bf16x2(uint32_t lo, uint32_t hi) {
@@ -716,7 +698,7 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
             const uint64_t tile = blockIdx.x + i * gridDim.x;
             if (tile >= ntiles) break;
             const int b = (int)(i & 1);
-            if (i >= 2 && !ws_wait(S, &S.a_free[b], (uint32_t)(((i >> 1) - 1) & 1), limit)) break;
+            if (i >= 2 && !ws_wait(&S.abort_flag, &S.a_free[b], (uint32_t)(((i >> 1) - 1) & 1), limit)) break;
             const uint64_t row = tile * NT_ROWS + t;
             RowOut r{-1, 0, 0, 0.0f};
             if (row < nrows) r = make_row<FILTER, M_STOCHASTIC>(a, K, row);
@@ -735,7 +717,7 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
                 const uint64_t tile = blockIdx.x + i * gridDim.x;
                 if (tile >= ntiles) break;
                 const int b = (int)(i & 1);
-                if (!ws_wait1(S, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
+                if (!ws_wait1(&S.abort_flag, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
                 tc_fence_after();
                 if (!a.inject_timeout) {
                     const uint32_t aa = smem_u32(S.A[b]);
@@ -745,7 +727,7 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
                                  idesc_bf16(128, 64), s > 0);
                     mma_commit(&S.mma1);
                 }
-                if (!ws_wait1(S, &S.h1, (uint32_t)(i & 1), limit)) break;
+                if (!ws_wait1(&S.abort_flag, &S.h1, (uint32_t)(i & 1), limit)) break;
                 tc_fence_after();
                 if (!a.inject_timeout) {
 #pragma unroll
@@ -754,7 +736,7 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
                                  idesc_bf16(128, 64), s > 0);
                     mma_commit(&S.mma2);
                 }
-                if (!ws_wait1(S, &S.h2, (uint32_t)(i & 1), limit)) break;
+                if (!ws_wait1(&S.abort_flag, &S.h2, (uint32_t)(i & 1), limit)) break;
                 tc_fence_after();
                 if (!a.inject_timeout) {
 #pragma unroll
@@ -780,10 +762,10 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
             if (tile >= ntiles) break;
             const int b = (int)(i & 1);
             const uint32_t par = (uint32_t)(i & 1);
-            if (!ws_wait(S, &S.mma1, par, limit)) break;
+            if (!ws_wait(&S.abort_flag, &S.mma1, par, limit)) break;
             // the producers' row data: acquired from their own barrier (its phase for this tile
             // has completed, and it cannot move on before this warp frees the buffer below)
-            if (!ws_wait(S, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
+            if (!ws_wait(&S.abort_flag, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
             tc_fence_after();
             const long long q = S.q[b][e];
             const float w = S.w[b][e];
@@ -793,13 +775,13 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
             fence_async_smem();
             tc_fence_before();
             mbar_arrive(&S.h1);
-            if (!ws_wait(S, &S.mma2, par, limit)) break;
+            if (!ws_wait(&S.abort_flag, &S.mma2, par, limit)) break;
             tc_fence_after();
             ws_hidden(taddr, S.H, e);
             fence_async_smem();
             tc_fence_before();
             mbar_arrive(&S.h2);
-            if (!ws_wait(S, &S.mma3, par, limit)) break;
+            if (!ws_wait(&S.abort_flag, &S.mma3, par, limit)) break;
             tc_fence_after();
             uint32_t r[16];
             tmem_ld16(taddr + 64, r);
@@ -848,8 +830,8 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
 }
 
 // ------------------------------------------------------------------ training (tcgen05)
-// One CTA of 128 threads; one training sample (one row) per thread in each 128-sample tile.
-// Forward: the decode's three GEMMs on BF16 operands.  Backward, per tile:
+// One training sample (one row) per thread of a 128-sample tile.  Forward: the decode's three
+// GEMMs on BF16 operands.  Backward, per tile:
 //   dH2 = dY W3            (A dY, K-major;  B W3 read MN-major)          -> TMEM scratch
 //   dW3^T += [H2 | 1]^T dY (A the H2 tile read MN-major; B dY MN-major)  -> TMEM accumulator
 //   dH1 = dZ2 W2,  dW2 += dZ2^T [H1 | 1]
@@ -861,46 +843,77 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
 // weight-gradient GEMMs read the same bytes with features along M or N and samples along K;
 // the weights, stored K-major for the forward, are read MN-major as the backward's B.
 // A block of ones after the features of X, H1 and H2 makes each bias gradient one more
-// column (or lane) of a weight-gradient accumulator.  The weight-gradient GEMMs run at
-// M = 128 with 64 (H2: 80) meaningful rows; the rows beyond read the next tiles of the
-// shared-memory struct, and their lanes are never read.  The accumulators sum over
-// all tiles of a CTA and are added to the global gradient once, at the end.
+// column (or lane) of a weight-gradient accumulator.  dZ2 is written over H2 once the
+// layer-3 GEMMs have read H2, and dZ1 over H1 once the layer-2 GEMMs have read H1; both keep
+// the ones block of the tile they replace.
+//
+// The weight-gradient GEMMs run at M = 128 with 64 (H2: 80) meaningful rows, so their
+// accumulators take 144 TMEM columns of which half the lanes are never read.  Rather than
+// one tile per CTA, waiting on every GEMM round, a CTA (one per SM, all 512 TMEM columns)
+// keeps TRW_GROUPS tiles in flight: each group of four warps owns one tile at a time
+// (gathers, epilogues, loss, latent-gradient scatter) with its own 64 scratch columns, and
+// one MMA thread serves the groups in whatever order their stages become ready.  Only that
+// thread issues MMAs, so the weight-gradient GEMMs of all groups accumulate into one set of
+// accumulators in issue order.  Hand-over per stage: the group's 128 threads arrive on
+// ready[g] after writing their rows (generic-proxy writes fenced to the async proxy); the
+// MMA thread issues the stage and commits to done[g]; the group waits on done[g].  Every
+// wait is bounded; a role that gives up sets abort_flag, which ends every other wait.
+// The M = 128 reads past the 64 (80) features of an H tile land in the next tile of the
+// group (H1 -> H2, H2 -> dY), whose lanes are never read.
 constexpr int TR_ROWS = 128;
-constexpr int TR_CTAS_PER_SM = 2;              // 2 x 256 TMEM columns = 512
-constexpr uint32_t TR_TMEM_COLS = 256;
-constexpr uint32_t TC_DW2 = 64, TC_DW1 = 144, TC_DW3 = 192;   // accumulator columns (80, 48, 16)
-constexpr int FX = 48, FH = 80, FZ2 = 64, FY = 16;            // row lengths of the tiles (elements)
+constexpr int TRW_GROUPS = 3;
+constexpr int TRW_THREADS = TRW_GROUPS * TR_ROWS + 32;
+constexpr uint32_t TRW_TMEM_COLS = 512;
+constexpr uint32_t TW_DW2 = 0, TW_DW1 = 80, TW_DW3 = 128;   // accumulator columns (80, 48, 16)
+constexpr uint32_t TW_SCRATCH = 256;                          // group g: columns 256 + 64 g ..
+constexpr int FX = 48, FH = 80, FY = 16;                      // row lengths of the tiles (elements)
 constexpr uint32_t IDESC_A_MN = 1u << 15, IDESC_B_MN = 1u << 16;
 
-struct TrainSmem {
+struct TrwGroup {
     uint8_t X[TR_ROWS * FX * 2];      // 32 latent features | 16 ones
-    uint8_t H1[TR_ROWS * FH * 2];     // 64 activations | 16 ones
-    uint8_t H2[TR_ROWS * FH * 2];     // 64 activations | 16 ones; later dZ1 | 16 ones
-    uint8_t dZ2[TR_ROWS * FZ2 * 2];
+    uint8_t H1[TR_ROWS * FH * 2];     // 64 activations | 16 ones; later dZ1 | 16 ones
+    uint8_t H2[TR_ROWS * FH * 2];     // 64 activations | 16 ones; later dZ2 | 16 ones
     uint8_t dY[TR_ROWS * FY * 2];     // 8 output gradients | 8 zeros
-    uint8_t W1[64 * 32 * 2], W2[64 * 64 * 2], W3[16 * 64 * 2];
-    float bias[144];
-    uint64_t bar;
-    uint32_t tmem;
-    int abort_flag;
-    float red[4];
 };
-// The M = 128 reads past the 64 (80) features of dZ2, H2 and dZ1 land in the next tiles of
-// the struct (at most 70,656 B from its start); W3 ends last, at 88,064 B.
-static_assert(sizeof(TrainSmem) * 3 > 228 * 1024, "at most 2 CTAs (2 x 256 TMEM columns) per SM");
+struct __align__(128) TrainWsSmem {
+    TrwGroup grp[TRW_GROUPS];
+    // BF16 weights with the biases folded in (K-major): W1 | b1 [64][48], W2 | b2 [64][80],
+    // W3 | b3 [16][80] (rows 8..15 zero); the bias columns meet the ones blocks of X, H1, H2
+    uint8_t W1[64 * FX * 2], W2[64 * FH * 2], W3[16 * FH * 2];
+    uint64_t ready[TRW_GROUPS], done[TRW_GROUPS], fin;
+    uint32_t tmem;
+    volatile int abort_flag;
+    int acc_valid;
+    float red[TRW_GROUPS * 4];
+};
+static_assert(TW_SCRATCH + 64 * TRW_GROUPS <= TRW_TMEM_COLS, "scratch columns of every group");
+static_assert(TW_DW3 + 16 <= TW_SCRATCH, "accumulators below the scratch columns");
+// 15 row groups x 1,280 B + 16 feature groups x 128 B: the last byte an M = 128 read of an H
+// tile touches lies inside the next tile of the same group
+static_assert(15 * FH * 16 + 16 * 128 <= TR_ROWS * FH * 2 + TR_ROWS * FY * 2, "M = 128 reads stay in the group");
+static_assert(2 * sizeof(TrainWsSmem) > 228 * 1024, "one CTA per SM: it allocates all 512 TMEM columns");
+static_assert(sizeof(TrainWsSmem) + 1024 <= 227 * 1024, "shared memory of one CTA");
 
-// FP32 master weights [rows][K] (rows >= present are zero) -> BF16, K-major tile
-__device__ __forceinline__ void stage_weights_f32(uint8_t* dst, const float* src, int rows, int K, int present) {
-    const int chunks = rows * K / 8;
+// FP32 master weights W [rows][Kw] and bias b [rows] (rows >= present are zero) -> BF16
+// K-major tile [rows][Kt]: W, then the bias as three exact BF16 parts, then zeros.  Against
+// a ones block in the activation tile the three parts add the FP32 bias inside the GEMM.
+__device__ __forceinline__ void stage_weights_ext(uint8_t* dst, const float* W, const float* b, int rows, int Kw,
+                                                  int Kt, int present) {
+    const int chunks = rows * Kt / 8;
     for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-        const int row = c / (K / 8), kc = c % (K / 8);
+        const int row = c / (Kt / 8), kc = c % (Kt / 8);
         uint32_t p[4] = {0u, 0u, 0u, 0u};
         if (row < present) {
-            const float* s = src + (size_t)row * K + kc * 8;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) p[i] = bf16x2_of<false>(pk2(s[2 * i], s[2 * i + 1]));
+            for (int i = 0; i < 8; ++i) {
+                const int k = 8 * kc + i;
+                __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+                if (k < Kw) v = __float2bfloat16_rn(W[(size_t)row * Kw + k]);
+                else if (k < Kw + 3) v = bf16_part(b[row], k - Kw);
+                p[i >> 1] |= (uint32_t)__bfloat16_as_ushort(v) << (16 * (i & 1));
+            }
         }
-        *reinterpret_cast<uint4*>(dst + kmaj_off(row, kc * 8, K)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, kc * 8, Kt)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
 }
 
@@ -912,284 +925,395 @@ __device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t mn_stride, 
     return smem_desc(saddr, k_stride, mn_stride);
 }
 
-// All threads: publish this thread's shared-memory writes to the tensor core and meet;
-// thread 0 issues the MMAs and waits (bounded) for their completion; all meet again.
-template <class Issue>
-__device__ __forceinline__ bool tc_round(TrainSmem& S, uint32_t& phase, Issue issue) {
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc_fence_after();
-        issue();
-        mma_commit(&S.bar);
-        if (!mbar_wait_bounded(&S.bar, phase, WAIT_CYCLES)) S.abort_flag = 1;
-    }
-    phase ^= 1u;
-    __syncthreads();
-    tc_fence_after();
-    return S.abort_flag == 0;
-}
-
-// Hidden layer epilogue: 64 pre-activations from TMEM + bias -> ReLU -> BF16 row of a tile
-// with F columns; returns the mask [z > 0] (bit j = feature j)
-template <int F>
-__device__ __forceinline__ uint2 hidden_epilogue(uint32_t taddr, const float* bias, uint8_t* dst, int row) {
-    uint32_t r[4][16];
+// The 32 features of a training sample from the FP32 master latents -> BF16 row `row` of the
+// X tile: per grid and channel, w00 a + w10 b + w01 c + w11 d in this order, each step one
+// rounding (the oracle's order).  Two grids' gathers (16 loads, 64 registers) are in flight
+// at a time, so a 128-register thread does not spill.
+__device__ __forceinline__ void master_features_to_tile(const NeuralView& N, int ix, int iy, uint8_t* X, int row) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, r[c]);
-    tmem_wait_ld();
-    const ulonglong2* bias2 = reinterpret_cast<const ulonglong2*>(bias);
-    uint32_t m[2] = {0u, 0u};
+    for (int h = 0; h < 2; ++h) {
+        LTap t[2];
+        uint64_t a[2][4], b[2][4], c[2][4], d[2][4];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const ulonglong2 ba = bias2[2 * c], bb = bias2[2 * c + 1];
-        const uint64_t bv[4] = {ba.x, ba.y, bb.x, bb.y};
-        uint32_t p[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int j = 8 * c + 2 * i;
-            const uint64_t z = add2(pk2(__uint_as_float(r[j >> 4][j & 15]), __uint_as_float(r[(j + 1) >> 4][(j + 1) & 15])),
-                                    bv[i]);
-            const float2 zf = upk2(z);
-            m[j >> 5] |= (zf.x > 0.0f ? 1u : 0u) << (j & 31);
-            m[j >> 5] |= (zf.y > 0.0f ? 1u : 0u) << ((j + 1) & 31);
-            p[i] = bf16x2_of<true>(z);
+        for (int q = 0; q < 2; ++q) {
+            t[q] = latent_taps(N, 2 * h + q, ix, iy);
+            load_master8(N, 2 * h + q, t[q].x0, t[q].y0, a[q]);
+            load_master8(N, 2 * h + q, t[q].x1, t[q].y0, b[q]);
+            load_master8(N, 2 * h + q, t[q].x0, t[q].y1, c[q]);
+            load_master8(N, 2 * h + q, t[q].x1, t[q].y1, d[q]);
         }
-        *reinterpret_cast<uint4*>(dst + kmaj_off(row, 8 * c, F)) = make_uint4(p[0], p[1], p[2], p[3]);
-    }
-    return make_uint2(m[0], m[1]);
-}
-
-// Gradient epilogue: 64 values from TMEM, masked by [z > 0], as a BF16 row of a tile
-template <int F>
-__device__ __forceinline__ void grad_epilogue(uint32_t taddr, uint2 mask, uint8_t* dst, int row) {
-    uint32_t r[4][16];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, r[c]);
-    tmem_wait_ld();
-    const uint32_t m[2] = {mask.x, mask.y};
+        for (int q = 0; q < 2; ++q) {
+            const uint64_t w00 = pk2(t[q].w00, t[q].w00), w10 = pk2(t[q].w10, t[q].w10);
+            const uint64_t w01 = pk2(t[q].w01, t[q].w01), w11 = pk2(t[q].w11, t[q].w11);
+            uint32_t p[4];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        uint32_t p[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int j = 8 * c + 2 * i;
-            const float a = (m[j >> 5] >> (j & 31)) & 1u ? __uint_as_float(r[j >> 4][j & 15]) : 0.0f;
-            const float b = (m[j >> 5] >> ((j + 1) & 31)) & 1u ? __uint_as_float(r[(j + 1) >> 4][(j + 1) & 15]) : 0.0f;
-            p[i] = bf16x2_of<false>(pk2(a, b));
+            for (int k = 0; k < 4; ++k) {
+                uint64_t v = mul2(w00, a[q][k]);
+                v = fma2(w10, b[q][k], v);
+                v = fma2(w01, c[q][k], v);
+                p[k] = bf16x2_of<false>(fma2(w11, d[q][k], v));
+            }
+            *reinterpret_cast<uint4*>(X + kmaj_off(row, 8 * (2 * h + q), FX)) = make_uint4(p[0], p[1], p[2], p[3]);
         }
-        *reinterpret_cast<uint4*>(dst + kmaj_off(row, 8 * c, F)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
 }
 
-__global__ void __launch_bounds__(TR_ROWS, TR_CTAS_PER_SM)
-k_ntc_train_tc(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint32_t count, RoundKeys K,
+// Non-blocking test of an mbarrier phase (the MMA thread polls several barriers in turn).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Hidden layer epilogue: 64 pre-activations z (bias included) from TMEM -> ReLU -> BF16 row
+// of a tile with F columns, 32 columns at a time
+template <int F>
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, uint8_t* dst, int row) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t r[2][16];
+        tmem_ld16(taddr + 32 * h, r[0]);
+        tmem_ld16(taddr + 32 * h + 16, r[1]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = 8 * c + 2 * i;         // column within this half
+                p[i] = relu_bf16x2(r[j >> 4][j & 15], r[(j + 1) >> 4][(j + 1) & 15]);
+            }
+            *reinterpret_cast<uint4*>(dst + kmaj_off(row, 32 * h + 8 * c, F)) = make_uint4(p[0], p[1], p[2], p[3]);
+        }
+    }
+}
+
+// 0xFFFF in each half of a BF16 pair that is > 0
+__device__ __forceinline__ uint32_t positive_mask(uint32_t h) {
+    __nv_bfloat162 v;
+    memcpy(&v, &h, 4);
+    return __hgt2_mask(v, __float2bfloat162_rn(0.0f));
+}
+
+// Gradient epilogue: 64 values dH from TMEM -> dZ = dH (.) [z > 0], BF16, written over the
+// same row of `tile` (F columns), which holds the layer's ReLU outputs: a ReLU output is
+// nonzero exactly where z > 0 (BF16 keeps FP32's exponent range, so a positive FP32 z rounds
+// to zero only below 2^-133).  dZ in BF16 is the rounded dH, or 0.
+template <int F>
+__device__ __forceinline__ void grad_epilogue(uint32_t taddr, uint8_t* tile, int row) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t r[2][16];
+        tmem_ld16(taddr + 32 * h, r[0]);
+        tmem_ld16(taddr + 32 * h + 16, r[1]);
+        uint4 hv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) hv[c] = *reinterpret_cast<const uint4*>(tile + kmaj_off(row, 32 * h + 8 * c, F));
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t hw[4] = {hv[c].x, hv[c].y, hv[c].z, hv[c].w};
+            uint32_t p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = 8 * c + 2 * i;
+                const uint32_t d = bf16x2_of<false>(pk2(__uint_as_float(r[j >> 4][j & 15]),
+                                                        __uint_as_float(r[(j + 1) >> 4][(j + 1) & 15])));
+                p[i] = d & positive_mask(hw[i]);
+            }
+            *reinterpret_cast<uint4*>(tile + kmaj_off(row, 32 * h + 8 * c, F)) = make_uint4(p[0], p[1], p[2], p[3]);
+        }
+    }
+}
+
+// The GEMMs of one stage of a group's tile (issued by the MMA thread).  fresh_*: the first
+// accumulation into that weight-gradient accumulator in this CTA overwrites it.
+__device__ __forceinline__ void train_stage(TrainWsSmem& S, int g, int stage, uint32_t tmem, bool& fresh3,
+                                            bool& fresh2, bool& fresh1) {
+    const TrwGroup& G = S.grp[g];
+    const uint32_t scr = tmem + TW_SCRATCH + 64u * (uint32_t)g;
+    const uint32_t sX = smem_u32(G.X), sH1 = smem_u32(G.H1), sH2 = smem_u32(G.H2), sY = smem_u32(G.dY);
+    const uint32_t sW1 = smem_u32(S.W1), sW2 = smem_u32(S.W2), sW3 = smem_u32(S.W3);
+    switch (stage) {
+    case 0:     // Z1 = [X | 1] [W1 | b1]^T
+        for (int s = 0; s < FX / 16; ++s)
+            mma_bf16(scr, smem_desc(sX + 256 * s, 128, FX * 16), smem_desc(sW1 + 256 * s, 128, FX * 16),
+                     idesc_bf16(128, 64), s > 0);
+        break;
+    case 1:     // Z2 = [H1 | 1] [W2 | b2]^T
+        for (int s = 0; s < FH / 16; ++s)
+            mma_bf16(scr, smem_desc(sH1 + 256 * s, 128, FH * 16), smem_desc(sW2 + 256 * s, 128, FH * 16),
+                     idesc_bf16(128, 64), s > 0);
+        break;
+    case 2:     // Y = [H2 | 1] [W3 | b3]^T (8 outputs and 8 zero rows)
+        for (int s = 0; s < FH / 16; ++s)
+            mma_bf16(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), smem_desc(sW3 + 256 * s, 128, FH * 16),
+                     idesc_bf16(128, 16), s > 0);
+        break;
+    case 3:     // dH2 = dY W3;  dW3^T | db3 += [H2 | 1]^T dY
+        mma_bf16(scr, smem_desc(sY, 128, FY * 16), mn_desc(sW3, 128, FH * 16), idesc_bf16(128, 64) | IDESC_B_MN, 0);
+        for (int s = 0; s < 8; ++s)
+            mma_bf16(tmem + TW_DW3, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
+                     mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16), idesc_bf16(128, 16) | IDESC_A_MN | IDESC_B_MN,
+                     (fresh3 && s == 0) ? 0u : 1u);
+        fresh3 = false;
+        break;
+    case 4:     // dH1 = dZ2 W2;  dW2 | db2 += dZ2^T [H1 | 1]   (dZ2 in the H2 tile)
+        for (int s = 0; s < 4; ++s)
+            mma_bf16(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), mn_desc(sW2 + 2 * FH * 16 * s, 128, FH * 16),
+                     idesc_bf16(128, 64) | IDESC_B_MN, s > 0);
+        for (int s = 0; s < 8; ++s)
+            mma_bf16(tmem + TW_DW2, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
+                     mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(128, 80) | IDESC_A_MN | IDESC_B_MN,
+                     (fresh2 && s == 0) ? 0u : 1u);
+        fresh2 = false;
+        break;
+    default:    // dX = dZ1 W1;  dW1 | db1 += dZ1^T [X | 1]   (dZ1 in the H1 tile)
+        for (int s = 0; s < 4; ++s)
+            mma_bf16(scr, smem_desc(sH1 + 256 * s, 128, FH * 16), mn_desc(sW1 + 2 * FX * 16 * s, 128, FX * 16),
+                     idesc_bf16(128, 32) | IDESC_B_MN, s > 0);
+        for (int s = 0; s < 8; ++s)
+            mma_bf16(tmem + TW_DW1, mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16),
+                     mn_desc(sX + 2 * FX * 16 * s, 128, FX * 16), idesc_bf16(128, 48) | IDESC_A_MN | IDESC_B_MN,
+                     (fresh1 && s == 0) ? 0u : 1u);
+        fresh1 = false;
+        break;
+    }
+}
+
+constexpr int TRAIN_STAGES = 6;
+
+__global__ void __launch_bounds__(TRW_THREADS, 1)
+k_ntc_train_ws(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint32_t count, RoundKeys K,
                float* loss_sum, uint32_t use_explicit, const int32_t* ex_ix, const int32_t* ex_iy, uint32_t* status) {
     extern __shared__ __align__(1024) uint8_t train_raw[];
-    TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_raw);
-    const int t = threadIdx.x, warp = t >> 5;
+    TrainWsSmem& S = *reinterpret_cast<TrainWsSmem*>(train_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int grp = warp >> 2;                  // tile group; grp == TRW_GROUPS: the MMA warp
+    const int e = t - TR_ROWS * grp;            // row of the group's tile = its TMEM lane
     const float* P = N.mlp32;       // W1 [64][32], b1, W2 [64][64], b2, W3 [8][64], b3
-    stage_weights_f32(S.W1, P, 64, 32, 64);
-    stage_weights_f32(S.W2, P + 2112, 64, 64, 64);
-    stage_weights_f32(S.W3, P + 6272, 16, 64, 8);
-    for (int i = t; i < 64; i += TR_ROWS) { S.bias[i] = P[2048 + i]; S.bias[64 + i] = P[6208 + i]; }
-    if (t < 16) S.bias[128 + t] = t < 8 ? P[6784 + t] : 0.0f;
-    {   // constant blocks of this thread's rows: ones after the features, zeros after dY
+    stage_weights_ext(S.W1, P, P + 2048, 64, 32, FX, 64);
+    stage_weights_ext(S.W2, P + 2112, P + 6208, 64, 64, FH, 64);
+    stage_weights_ext(S.W3, P + 6272, P + 6784, 16, 64, FH, 8);
+    if (grp < TRW_GROUPS) {   // constant blocks of this thread's rows: ones after the features, zeros after dY
+        TrwGroup& G = S.grp[grp];
         const uint4 one = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
         const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            *reinterpret_cast<uint4*>(S.X + kmaj_off(t, 32 + 8 * h, FX)) = one;
-            *reinterpret_cast<uint4*>(S.H1 + kmaj_off(t, 64 + 8 * h, FH)) = one;
-            *reinterpret_cast<uint4*>(S.H2 + kmaj_off(t, 64 + 8 * h, FH)) = one;
+            *reinterpret_cast<uint4*>(G.X + kmaj_off(e, 32 + 8 * h, FX)) = one;
+            *reinterpret_cast<uint4*>(G.H1 + kmaj_off(e, 64 + 8 * h, FH)) = one;
+            *reinterpret_cast<uint4*>(G.H2 + kmaj_off(e, 64 + 8 * h, FH)) = one;
         }
-        *reinterpret_cast<uint4*>(S.dY + kmaj_off(t, 8, FY)) = zero;
+        *reinterpret_cast<uint4*>(G.dY + kmaj_off(e, 8, FY)) = zero;
     }
-    if (t == 0) { mbar_init(&S.bar, 1); S.abort_flag = 0; }
-    if (warp == 0) tmem_alloc(&S.tmem, TR_TMEM_COLS);
+    if (t == 0) {
+        for (int g = 0; g < TRW_GROUPS; ++g) { mbar_init(&S.ready[g], TR_ROWS); mbar_init(&S.done[g], 1); }
+        mbar_init(&S.fin, 1);
+        S.abort_flag = 0;
+        S.acc_valid = 0;
+    }
+    if (warp == 0) tmem_alloc(&S.tmem, TRW_TMEM_COLS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const uint32_t sX = smem_u32(S.X), sH1 = smem_u32(S.H1), sH2 = smem_u32(S.H2), sZ2 = smem_u32(S.dZ2);
-    const uint32_t sY = smem_u32(S.dY), sW1 = smem_u32(S.W1), sW2 = smem_u32(S.W2), sW3 = smem_u32(S.W3);
-    const float inv = 1.0f / (8.0f * (float)batch);
-    uint32_t phase = 0;
-    bool ok = true, any = false;
-    float loss = 0.0f;
-    // samples first .. first + count - 1 of the step's batch (global ids: the ranks of a
-    // data-parallel step draw disjoint parts of the same batch); the loss and gradients are
-    // normalised by the whole batch, so the parts' gradients sum to the batch gradient
     const uint32_t ntiles = (count + TR_ROWS - 1) / TR_ROWS;
-    for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const uint32_t acc0 = any ? 1u : 0u;    // accumulators: first tile of this CTA overwrites
-        const uint32_t j = tile * TR_ROWS + t;
-        const bool live = j < count;
-        const uint32_t k = first + j;
-        int ix = 0, iy = 0;
-        if (live) {
-            if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
-            else {
-                const uint4 w = philox(k, step, 0u, 0x4E54u, K);
-                ix = (int)__umulhi(w.x, (uint32_t)N.tex_res);
-                iy = (int)__umulhi(w.y, (uint32_t)N.tex_res);
-            }
-        }
-        {   // latent features (FP32 master latents) -> BF16 row of X
-            uint64_t f[16];
-            master_features(N, ix, iy, f);
-#pragma unroll
-            for (int g = 0; g < 4; ++g)
-                *reinterpret_cast<uint4*>(S.X + kmaj_off(t, 8 * g, FX)) =
-                    make_uint4(bf16x2_of<false>(f[4 * g]), bf16x2_of<false>(f[4 * g + 1]),
-                               bf16x2_of<false>(f[4 * g + 2]), bf16x2_of<false>(f[4 * g + 3]));
-        }
-        // ---- forward
-        ok = tc_round(S, phase, [&] {
-            for (int s = 0; s < 2; ++s)
-                mma_bf16(tmem, smem_desc(sX + 256 * s, 128, FX * 16), smem_desc(sW1 + 256 * s, 128, 512),
-                         idesc_bf16(128, 64), s > 0);
-        });
-        if (!ok) break;
-        const uint2 mask1 = hidden_epilogue<FH>(tmem + lane_base, S.bias, S.H1, t);
-        ok = tc_round(S, phase, [&] {
-            for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem, smem_desc(sH1 + 256 * s, 128, FH * 16), smem_desc(sW2 + 256 * s, 128, 1024),
-                         idesc_bf16(128, 64), s > 0);
-        });
-        if (!ok) break;
-        const uint2 mask2 = hidden_epilogue<FH>(tmem + lane_base, S.bias + 64, S.H2, t);
-        ok = tc_round(S, phase, [&] {
-            for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem, smem_desc(sH2 + 256 * s, 128, FH * 16), smem_desc(sW3 + 256 * s, 128, 1024),
-                         idesc_bf16(128, 16), s > 0);
-        });
-        if (!ok) break;
-        {   // outputs -> MSE loss and dY (BF16 row of the dY tile)
-            uint32_t r[16];
-            tmem_ld16(tmem + lane_base, r);
-            tmem_wait_ld();
-            float dy[8];
-            const uint8_t* tg = N.targets + ((size_t)iy * N.tex_res + ix) * 8;
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const float y = __uint_as_float(r[o]) + S.bias[128 + o];
-                const float e = live ? y - (float)tg[o] * (1.0f / 255.0f) : 0.0f;
-                loss = fmaf(e * e, inv, loss);
-                dy[o] = 2.0f * e * inv;
-            }
-            *reinterpret_cast<uint4*>(S.dY + kmaj_off(t, 0, FY)) =
-                make_uint4(bf16x2_of<false>(pk2(dy[0], dy[1])), bf16x2_of<false>(pk2(dy[2], dy[3])),
-                           bf16x2_of<false>(pk2(dy[4], dy[5])), bf16x2_of<false>(pk2(dy[6], dy[7])));
-        }
-        // ---- backward, layer 3: dH2 = dY W3;  dW3^T | db3 += [H2 | 1]^T dY
-        ok = tc_round(S, phase, [&] {
-            mma_bf16(tmem, smem_desc(sY, 128, FY * 16), mn_desc(sW3, 128, 1024), idesc_bf16(128, 64) | IDESC_B_MN, 0);
-            for (int s = 0; s < 8; ++s)
-                mma_bf16(tmem + TC_DW3, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
-                         mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16), idesc_bf16(128, 16) | IDESC_A_MN | IDESC_B_MN,
-                         acc0 | (s > 0));
-        });
-        if (!ok) break;
-        grad_epilogue<FZ2>(tmem + lane_base, mask2, S.dZ2, t);
-        // ---- layer 2: dH1 = dZ2 W2;  dW2 | db2 += dZ2^T [H1 | 1]
-        ok = tc_round(S, phase, [&] {
-            for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem, smem_desc(sZ2 + 256 * s, 128, FZ2 * 16), mn_desc(sW2 + 2048 * s, 128, 1024),
-                         idesc_bf16(128, 64) | IDESC_B_MN, s > 0);
-            for (int s = 0; s < 8; ++s)
-                mma_bf16(tmem + TC_DW2, mn_desc(sZ2 + 2 * FZ2 * 16 * s, 128, FZ2 * 16),
-                         mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(128, 80) | IDESC_A_MN | IDESC_B_MN,
-                         acc0 | (s > 0));
-        });
-        if (!ok) break;
-        grad_epilogue<FH>(tmem + lane_base, mask1, S.H2, t);      // dZ1 replaces H2 (same layout)
-        // ---- layer 1: dX = dZ1 W1;  dW1 | db1 += dZ1^T [X | 1]
-        ok = tc_round(S, phase, [&] {
-            for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem, smem_desc(sH2 + 256 * s, 128, FH * 16), mn_desc(sW1 + 1024 * s, 128, 512),
-                         idesc_bf16(128, 32) | IDESC_B_MN, s > 0);
-            for (int s = 0; s < 8; ++s)
-                mma_bf16(tmem + TC_DW1, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
-                         mn_desc(sX + 2 * FX * 16 * s, 128, FX * 16), idesc_bf16(128, 48) | IDESC_A_MN | IDESC_B_MN,
-                         acc0 | (s > 0));
-        });
-        if (!ok) break;
-        any = true;
-        {   // dX -> latent gradients, spread over each grid's 4 taps with the bilinear weights
-            uint32_t r0[16], r1[16];
-            tmem_ld16(tmem + lane_base, r0);
-            tmem_ld16(tmem + lane_base + 16, r1);
-            tmem_wait_ld();
+    const uint32_t tstride = gridDim.x * TRW_GROUPS;
+    float loss = 0.0f;
+
+    if (grp < TRW_GROUPS) {
+        // ---------------------------------------------------------------- tile groups
+        TrwGroup& G = S.grp[grp];
+        const uint32_t scr = tmem + TW_SCRATCH + 64u * (uint32_t)grp + ((uint32_t)((warp & 3) * 32) << 16);
+        const float inv = 1.0f / (8.0f * (float)batch);
+        uint32_t handed = 0;     // stages handed over so far (the parity of ready and done)
+        // publish this stage's rows to the MMA thread, then wait for its GEMMs
+        auto hand_over = [&]() -> bool {
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(&S.ready[grp]);
+            const bool ok = ws_wait(&S.abort_flag, &S.done[grp], handed & 1u, WAIT_CYCLES);
+            ++handed;
+            tc_fence_after();
+            return ok;
+        };
+        // samples first .. first + count - 1 of the step's batch (global ids: the ranks of a
+        // data-parallel step draw disjoint parts of the same batch); the loss and gradients are
+        // normalised by the whole batch, so the parts' gradients sum to the batch gradient
+        for (uint32_t tile = grp * gridDim.x + blockIdx.x; tile < ntiles; tile += tstride) {
+            const uint32_t j = tile * TR_ROWS + e;
+            const bool live = j < count;
+            const uint32_t k = first + j;
+            int ix = 0, iy = 0;
+            uint2 tgt = make_uint2(0u, 0u);     // the sample's 8 target channels (bytes)
             if (live) {
+                if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
+                else {
+                    const uint4 w = philox(k, step, 0u, 0x4E54u, K);
+                    ix = (int)__umulhi(w.x, (uint32_t)N.tex_res);
+                    iy = (int)__umulhi(w.y, (uint32_t)N.tex_res);
+                }
+                asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+                             : "=r"(tgt.x), "=r"(tgt.y)
+                             : "l"(N.targets + ((size_t)iy * N.tex_res + ix) * 8));
+            }
+            master_features_to_tile(N, ix, iy, G.X, e);     // FP32 master latents -> BF16 row of X
+            if (!hand_over()) break;                                          // Z1
+            hidden_epilogue<FH>(scr, G.H1, e);
+            if (!hand_over()) break;                                          // Z2
+            hidden_epilogue<FH>(scr, G.H2, e);
+            if (!hand_over()) break;                                          // Y
+            {   // outputs -> MSE loss and dY (BF16 row of the dY tile)
+                uint32_t r[16];
+                tmem_ld16(scr, r);
+                tmem_wait_ld();
+                float dy[8];
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const LTap tp = latent_taps(N, g, ix, iy);
-                    float dx[8];
+                for (int o = 0; o < 8; ++o) {
+                    const float y = __uint_as_float(r[o]);
+                    const uint32_t byte = ((o < 4 ? tgt.x : tgt.y) >> (8 * (o & 3))) & 0xFFu;
+                    const float d = live ? y - (float)byte * (1.0f / 255.0f) : 0.0f;
+                    loss = fmaf(d * d, inv, loss);
+                    dy[o] = 2.0f * d * inv;
+                }
+                *reinterpret_cast<uint4*>(G.dY + kmaj_off(e, 0, FY)) =
+                    make_uint4(bf16x2_of<false>(pk2(dy[0], dy[1])), bf16x2_of<false>(pk2(dy[2], dy[3])),
+                               bf16x2_of<false>(pk2(dy[4], dy[5])), bf16x2_of<false>(pk2(dy[6], dy[7])));
+            }
+            if (!hand_over()) break;                                          // dH2, dW3
+            grad_epilogue<FH>(scr, G.H2, e);                                  // dZ2 replaces H2
+            if (!hand_over()) break;                                          // dH1, dW2
+            grad_epilogue<FH>(scr, G.H1, e);                                  // dZ1 replaces H1
+            if (!hand_over()) break;                                          // dX, dW1
+            {   // dX -> latent gradients, spread over each grid's 4 taps with the bilinear weights
+                uint32_t r0[16], r1[16];
+                tmem_ld16(scr, r0);
+                tmem_ld16(scr + 16, r1);
+                tmem_wait_ld();
+                tc_fence_before();
+                if (live) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) dx[c] = __uint_as_float(g < 2 ? r0[8 * g + c] : r1[8 * (g - 2) + c]);
-                    float* dl = N.dlat + N.lat_off[g];
-                    const int R = N.res[g];
-                    const int xs[4] = {tp.x0, tp.x1, tp.x0, tp.x1}, ys[4] = {tp.y0, tp.y0, tp.y1, tp.y1};
-                    const float ws[4] = {tp.w00, tp.w10, tp.w01, tp.w11};
+                    for (int gi = 0; gi < 4; ++gi) {
+                        const LTap tp = latent_taps(N, gi, ix, iy);
+                        float dx[8];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float4* p = reinterpret_cast<float4*>(dl + ((size_t)ys[q] * R + xs[q]) * 8);
-                        atomicAdd(p, make_float4(ws[q] * dx[0], ws[q] * dx[1], ws[q] * dx[2], ws[q] * dx[3]));
-                        atomicAdd(p + 1, make_float4(ws[q] * dx[4], ws[q] * dx[5], ws[q] * dx[6], ws[q] * dx[7]));
+                        for (int c = 0; c < 8; ++c)
+                            dx[c] = __uint_as_float(gi < 2 ? r0[8 * gi + c] : r1[8 * (gi - 2) + c]);
+                        float* dl = N.dlat + N.lat_off[gi];
+                        const int R = N.res[gi];
+                        const int xs[4] = {tp.x0, tp.x1, tp.x0, tp.x1}, ys[4] = {tp.y0, tp.y0, tp.y1, tp.y1};
+                        const float ws[4] = {tp.w00, tp.w10, tp.w01, tp.w11};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float4* p = reinterpret_cast<float4*>(dl + ((size_t)ys[q] * R + xs[q]) * 8);
+                            atomicAdd(p, make_float4(ws[q] * dx[0], ws[q] * dx[1], ws[q] * dx[2], ws[q] * dx[3]));
+                            atomicAdd(p + 1, make_float4(ws[q] * dx[4], ws[q] * dx[5], ws[q] * dx[6], ws[q] * dx[7]));
+                        }
                     }
                 }
             }
         }
+    } else if (lane == 0) {
+        // ---------------------------------------------------------------- MMA thread
+        uint32_t left[TRW_GROUPS], stage[TRW_GROUPS], par[TRW_GROUPS];
+        uint32_t remaining = 0;
+#pragma unroll
+        for (int g = 0; g < TRW_GROUPS; ++g) {
+            const uint32_t t0 = g * gridDim.x + blockIdx.x;      // the group's first tile
+            left[g] = t0 < ntiles ? ((ntiles - 1 - t0) / tstride + 1) * TRAIN_STAGES : 0u;
+            stage[g] = 0u;
+            par[g] = 0u;
+            remaining += left[g];
+        }
+        bool fresh3 = true, fresh2 = true, fresh1 = true;
+        long long since = clock64();
+        while (remaining) {
+            bool progress = false;
+#pragma unroll
+            for (int g = 0; g < TRW_GROUPS; ++g) {
+                if (left[g] == 0u || !mbar_test_wait(&S.ready[g], par[g])) continue;
+                tc_fence_after();
+                train_stage(S, g, (int)stage[g], tmem, fresh3, fresh2, fresh1);
+                mma_commit(&S.done[g]);
+                stage[g] = stage[g] + 1u == (uint32_t)TRAIN_STAGES ? 0u : stage[g] + 1u;
+                par[g] ^= 1u;
+                --left[g];
+                --remaining;
+                progress = true;
+            }
+            if (progress) since = clock64();
+            else if (S.abort_flag || clock64() - since > WAIT_CYCLES) { S.abort_flag = 1; break; }
+        }
+        // every MMA this thread issued has completed before the accumulators are read
+        mma_commit(&S.fin);
+        const long long t1 = clock64();
+        bool fin = false;
+        while (!(fin = mbar_try_wait(&S.fin, 0u)) && clock64() - t1 < WAIT_CYCLES) {}
+        if (!fin) S.abort_flag = 1;
+        S.acc_valid = (!fresh1 && remaining == 0u) ? 1 : 0;
         tc_fence_before();
-        __syncthreads();    // the next tile's features overwrite X only after every dX read
     }
     // loss of this CTA's samples
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
-    if ((t & 31) == 0) S.red[warp] = loss;
+    if (lane == 0 && grp < TRW_GROUPS) S.red[warp] = loss;
     __syncthreads();
-    if (t == 0) atomicAdd(loss_sum, (S.red[0] + S.red[1]) + (S.red[2] + S.red[3]));
-    // accumulators -> global gradients (lane = output feature; lane 64 of dW3^T = db3)
-    if (ok && any) {
-        tc_fence_after();
-        float* G = N.grad32;
+    tc_fence_after();
+    const bool ok = S.abort_flag == 0;
+    if (t == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < TRW_GROUPS * 4; ++w) s += S.red[w];
+        atomicAdd(loss_sum, s);
+    }
+    // accumulators -> global gradients (lane = output feature; lane 64 of dW3^T = db3),
+    // read by the first group's warps (TMEM lanes 0..127)
+    if (ok && S.acc_valid && warp < 4) {
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float* Gg = N.grad32;
         uint32_t r[16];
 #pragma unroll 1
         for (int c = 0; c < 5; ++c) {            // dW2 [64][64] | db2
-            tmem_ld16(tmem + lane_base + TC_DW2 + 16 * c, r);
+            tmem_ld16(tmem + lane_base + TW_DW2 + 16 * c, r);
             tmem_wait_ld();
             if (t < 64)
                 for (int j = 0; j < 16; ++j) {
                     const int col = 16 * c + j;
-                    if (col < 64) atomicAdd(G + 2112 + t * 64 + col, __uint_as_float(r[j]));
-                    else if (col == 64) atomicAdd(G + 6208 + t, __uint_as_float(r[j]));
+                    if (col < 64) atomicAdd(Gg + 2112 + t * 64 + col, __uint_as_float(r[j]));
+                    else if (col == 64) atomicAdd(Gg + 6208 + t, __uint_as_float(r[j]));
                 }
         }
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {            // dW1 [64][32] | db1
-            tmem_ld16(tmem + lane_base + TC_DW1 + 16 * c, r);
+            tmem_ld16(tmem + lane_base + TW_DW1 + 16 * c, r);
             tmem_wait_ld();
             if (t < 64)
                 for (int j = 0; j < 16; ++j) {
                     const int col = 16 * c + j;
-                    if (col < 32) atomicAdd(G + t * 32 + col, __uint_as_float(r[j]));
-                    else if (col == 32) atomicAdd(G + 2048 + t, __uint_as_float(r[j]));
+                    if (col < 32) atomicAdd(Gg + t * 32 + col, __uint_as_float(r[j]));
+                    else if (col == 32) atomicAdd(Gg + 2048 + t, __uint_as_float(r[j]));
                 }
         }
-        tmem_ld16(tmem + lane_base + TC_DW3, r);   // dW3^T [64][8] | db3
+        tmem_ld16(tmem + lane_base + TW_DW3, r);   // dW3^T [64][8] | db3
         tmem_wait_ld();
         if (t < 64)
-            for (int o = 0; o < 8; ++o) atomicAdd(G + 6272 + o * 64 + t, __uint_as_float(r[o]));
+            for (int o = 0; o < 8; ++o) atomicAdd(Gg + 6272 + o * 64 + t, __uint_as_float(r[o]));
         else if (t == 64)
-            for (int o = 0; o < 8; ++o) atomicAdd(G + 6784 + o, __uint_as_float(r[o]));
+            for (int o = 0; o < 8; ++o) atomicAdd(Gg + 6784 + o, __uint_as_float(r[o]));
     }
     if (!ok && t == 0) atomicOr(status, DEV_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TR_TMEM_COLS);
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, TRW_TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1197,12 +1321,14 @@ cudaError_t launch_ntc_train(const NeuralView& N, uint32_t step, uint32_t batch,
                              uint64_t seed, float* loss_sum, const int32_t* ex_ix, const int32_t* ex_iy, int num_sms,
                              uint32_t* status, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
+    // tile i goes to group i / grid of CTA i % grid (cyclically beyond grid x groups): a small
+    // batch spreads over one tile per SM before a CTA's second group takes one
     const uint32_t tiles = (count + TR_ROWS - 1) / TR_ROWS;
-    const uint32_t cap = (uint32_t)num_sms * TR_CTAS_PER_SM;
+    const uint32_t cap = (uint32_t)num_sms;
     const int grid = (int)(tiles < cap ? tiles : cap);
-    cudaFuncSetAttribute(k_ntc_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
-    k_ntc_train_tc<<<grid, TR_ROWS, sizeof(TrainSmem), st>>>(N, step, batch, first, count, expand_key(seed), loss_sum,
-                                                             ex_ix != nullptr, ex_ix, ex_iy, status);
+    cudaFuncSetAttribute(k_ntc_train_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainWsSmem));
+    k_ntc_train_ws<<<grid, TRW_THREADS, sizeof(TrainWsSmem), st>>>(N, step, batch, first, count, expand_key(seed),
+                                                                   loss_sum, ex_ix != nullptr, ex_ix, ex_iy, status);
     return cudaGetLastError();
 }
 

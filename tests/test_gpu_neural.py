@@ -182,10 +182,11 @@ def test_gradients_match_oracle(ctx, net, data):
 
 
 def test_gradients_many_tiles_per_cta(ctx, net, data):
-    # more tiles than resident CTAs (2 per SM): each CTA accumulates several tiles' weight
-    # gradients in TMEM before adding them once; the last tile is ragged
+    # more tiles than the tile groups of all CTAs (one CTA per SM, three groups each): each
+    # CTA accumulates several tiles' weight gradients, from all its groups, in one set of TMEM
+    # accumulators before adding them once; the last tile is ragged
     lat, mlp, tg = data
-    step, batch, seed = 1, 2 * 148 * 128 + 12345, 9
+    step, batch, seed = 1, 2 * 3 * 148 * 128 + 12345, 9
     ix, iy = oracle.ntc_sample_texels(step, batch, seed, R0)
     loss = ctx.neural_grad(net, step, batch, seed)
     gm = ctx.neural_get(net, "grad_mlp", LAT_TOTAL).astype(np.float64)
