@@ -831,40 +831,40 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
 
 // ------------------------------------------------------------------ training (tcgen05)
 // One training sample (one row) per thread of a 128-sample tile.  Forward: the decode's three
-// GEMMs on BF16 operands.  Backward, per tile:
+// GEMMs on BF16 operands, the biases folded in.  Backward, per tile:
 //   dH2 = dY W3            (A dY, K-major;  B W3 read MN-major)          -> TMEM scratch
-//   dW3^T += [H2 | 1]^T dY (A the H2 tile read MN-major; B dY MN-major)  -> TMEM accumulator
-//   dH1 = dZ2 W2,  dW2 += dZ2^T [H1 | 1]
-//   dX  = dZ1 W1,  dW1 += dZ1^T [X | 1]
+//   dW3 | db3 += dY^T [H2 | 1]  (A the dY tile read MN-major; B the H2 tile MN-major)
+//   dH1 = dZ2 W2,  dW2 | db2 += dZ2^T [H1 | 1]
+//   dX  = dZ1 W1,  dW1 | db1 += dZ1^T [X | 1]
 // with dZ = dH (.) [Z > 0] and dY = 2 (y - target) / (8 batch), each rounded to BF16 as a
 // GEMM operand.  The activation tiles are written once, row = sample, in the K-major layout
 // of the forward GEMMs.  A K-major core matrix (8 samples x 8 features) is also an MN-major
 // core matrix of the transposed tile (8 features contiguous, 8 samples), so the
 // weight-gradient GEMMs read the same bytes with features along M or N and samples along K;
 // the weights, stored K-major for the forward, are read MN-major as the backward's B.
-// A block of ones after the features of X, H1 and H2 makes each bias gradient one more
-// column (or lane) of a weight-gradient accumulator.  dZ2 is written over H2 once the
-// layer-3 GEMMs have read H2, and dZ1 over H1 once the layer-2 GEMMs have read H1; both keep
-// the ones block of the tile they replace.
+// A block of ones after the features of X, H1 and H2 adds the bias in the forward GEMMs and
+// makes each bias gradient one more column of a weight-gradient accumulator.  dZ2 is written
+// over H2 once the layer-3 GEMMs have read H2, and dZ1 over H1 once the layer-2 GEMMs have
+// read H1; both keep the ones block of the tile they replace.
 //
-// The weight-gradient GEMMs run at M = 128 with 64 (H2: 80) meaningful rows, so their
-// accumulators take 144 TMEM columns of which half the lanes are never read.  Rather than
-// one tile per CTA, waiting on every GEMM round, a CTA (one per SM, all 512 TMEM columns)
-// keeps TRW_GROUPS tiles in flight: each group of four warps owns one tile at a time
-// (gathers, epilogues, loss, latent-gradient scatter) with its own 64 scratch columns, and
-// one MMA thread serves the groups in whatever order their stages become ready.  Only that
-// thread issues MMAs, so the weight-gradient GEMMs of all groups accumulate into one set of
-// accumulators in issue order.  Hand-over per stage: the group's 128 threads arrive on
-// ready[g] after writing their rows (generic-proxy writes fenced to the async proxy); the
-// MMA thread issues the stage and commits to done[g]; the group waits on done[g].  Every
-// wait is bounded; a role that gives up sets abort_flag, which ends every other wait.
-// The M = 128 reads past the 64 (80) features of an H tile land in the next tile of the
-// group (H1 -> H2, H2 -> dY), whose lanes are never read.
+// The weight-gradient GEMMs run at M = 64 (the 64 output features of a layer; dY's 8 and
+// padding), K = the tile's 128 samples; their accumulators (80 + 48 + 80 columns) sum over
+// every tile of the CTA.  An M = 64 accumulator keeps row r in TMEM lane 32 (r / 16) + r % 16:
+// lanes 0..15 of each 32-lane quarter.  Rather than one tile per CTA, waiting on every GEMM
+// round, a CTA (one per SM, all 512 TMEM columns) keeps TRW_GROUPS tiles in flight: each
+// group of four warps owns one tile at a time (gathers, epilogues, loss, latent-gradient
+// scatter) with its own 64 scratch columns, and one MMA thread serves the groups in whatever
+// order their stages become ready.  Only that thread issues MMAs, so the weight-gradient
+// GEMMs of all groups accumulate into one set of accumulators in issue order.  Hand-over per
+// stage: the group's 128 threads arrive on ready[g] after writing their rows (generic-proxy
+// writes fenced to the async proxy); the MMA thread issues the stage and commits to done[g];
+// the group waits on done[g].  Every wait is bounded; a role that gives up sets abort_flag,
+// which ends every other wait.
 constexpr int TR_ROWS = 128;
 constexpr int TRW_GROUPS = 3;
 constexpr int TRW_THREADS = TRW_GROUPS * TR_ROWS + 32;
 constexpr uint32_t TRW_TMEM_COLS = 512;
-constexpr uint32_t TW_DW2 = 0, TW_DW1 = 80, TW_DW3 = 128;   // accumulator columns (80, 48, 16)
+constexpr uint32_t TW_DW2 = 0, TW_DW1 = 80, TW_DW3 = 128;   // accumulator columns (80, 48, 80)
 constexpr uint32_t TW_SCRATCH = 256;                          // group g: columns 256 + 64 g ..
 constexpr int FX = 48, FH = 80, FY = 16;                      // row lengths of the tiles (elements)
 constexpr uint32_t IDESC_A_MN = 1u << 15, IDESC_B_MN = 1u << 16;
@@ -887,10 +887,11 @@ struct __align__(128) TrainWsSmem {
     float red[TRW_GROUPS * 4];
 };
 static_assert(TW_SCRATCH + 64 * TRW_GROUPS <= TRW_TMEM_COLS, "scratch columns of every group");
-static_assert(TW_DW3 + 16 <= TW_SCRATCH, "accumulators below the scratch columns");
-// 15 row groups x 1,280 B + 16 feature groups x 128 B: the last byte an M = 128 read of an H
-// tile touches lies inside the next tile of the same group
-static_assert(15 * FH * 16 + 16 * 128 <= TR_ROWS * FH * 2 + TR_ROWS * FY * 2, "M = 128 reads stay in the group");
+static_assert(TW_DW3 + 80 <= TW_SCRATCH, "accumulators below the scratch columns");
+// The M = 64 read of dY (16 columns) as 64 features runs past the dY tile by at most
+// 15 x 256 + 8 x 128 - 4,096 = 768 B, into the next group's X tile or, after the last
+// group, into W1 (rows >= 8 of that accumulator are never read)
+static_assert(15 * FY * 16 + 8 * 128 - TR_ROWS * FY * 2 <= 64 * FX * 2, "dY over-read stays in the struct");
 static_assert(2 * sizeof(TrainWsSmem) > 228 * 1024, "one CTA per SM: it allocates all 512 TMEM columns");
 static_assert(sizeof(TrainWsSmem) + 1024 <= 227 * 1024, "shared memory of one CTA");
 
@@ -1057,11 +1058,11 @@ __device__ __forceinline__ void train_stage(TrainWsSmem& S, int g, int stage, ui
             mma_bf16(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), smem_desc(sW3 + 256 * s, 128, FH * 16),
                      idesc_bf16(128, 16), s > 0);
         break;
-    case 3:     // dH2 = dY W3;  dW3^T | db3 += [H2 | 1]^T dY
+    case 3:     // dH2 = dY W3;  dW3 | db3 += dY^T [H2 | 1]
         mma_bf16(scr, smem_desc(sY, 128, FY * 16), mn_desc(sW3, 128, FH * 16), idesc_bf16(128, 64) | IDESC_B_MN, 0);
         for (int s = 0; s < 8; ++s)
-            mma_bf16(tmem + TW_DW3, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
-                     mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16), idesc_bf16(128, 16) | IDESC_A_MN | IDESC_B_MN,
+            mma_bf16(tmem + TW_DW3, mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16),
+                     mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(64, 80) | IDESC_A_MN | IDESC_B_MN,
                      (fresh3 && s == 0) ? 0u : 1u);
         fresh3 = false;
         break;
@@ -1071,7 +1072,7 @@ __device__ __forceinline__ void train_stage(TrainWsSmem& S, int g, int stage, ui
                      idesc_bf16(128, 64) | IDESC_B_MN, s > 0);
         for (int s = 0; s < 8; ++s)
             mma_bf16(tmem + TW_DW2, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
-                     mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(128, 80) | IDESC_A_MN | IDESC_B_MN,
+                     mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(64, 80) | IDESC_A_MN | IDESC_B_MN,
                      (fresh2 && s == 0) ? 0u : 1u);
         fresh2 = false;
         break;
@@ -1081,7 +1082,7 @@ __device__ __forceinline__ void train_stage(TrainWsSmem& S, int g, int stage, ui
                      idesc_bf16(128, 32) | IDESC_B_MN, s > 0);
         for (int s = 0; s < 8; ++s)
             mma_bf16(tmem + TW_DW1, mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16),
-                     mn_desc(sX + 2 * FX * 16 * s, 128, FX * 16), idesc_bf16(128, 48) | IDESC_A_MN | IDESC_B_MN,
+                     mn_desc(sX + 2 * FX * 16 * s, 128, FX * 16), idesc_bf16(64, 48) | IDESC_A_MN | IDESC_B_MN,
                      (fresh1 && s == 0) ? 0u : 1u);
         fresh1 = false;
         break;
@@ -1274,40 +1275,47 @@ k_ntc_train_ws(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint
         for (int w = 0; w < TRW_GROUPS * 4; ++w) s += S.red[w];
         atomicAdd(loss_sum, s);
     }
-    // accumulators -> global gradients (lane = output feature; lane 64 of dW3^T = db3),
-    // read by the first group's warps (TMEM lanes 0..127)
+    // accumulators -> global gradients, read by the first group's warps: lanes 0..15 of warp
+    // w hold rows 16 w .. 16 w + 15 (the output features; dW3's rows 0..7)
     if (ok && S.acc_valid && warp < 4) {
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int row = 16 * warp + lane;
+        const bool has = lane < 16;
         float* Gg = N.grad32;
         uint32_t r[16];
 #pragma unroll 1
         for (int c = 0; c < 5; ++c) {            // dW2 [64][64] | db2
             tmem_ld16(tmem + lane_base + TW_DW2 + 16 * c, r);
             tmem_wait_ld();
-            if (t < 64)
+            if (has)
                 for (int j = 0; j < 16; ++j) {
                     const int col = 16 * c + j;
-                    if (col < 64) atomicAdd(Gg + 2112 + t * 64 + col, __uint_as_float(r[j]));
-                    else if (col == 64) atomicAdd(Gg + 6208 + t, __uint_as_float(r[j]));
+                    if (col < 64) atomicAdd(Gg + 2112 + row * 64 + col, __uint_as_float(r[j]));
+                    else if (col == 64) atomicAdd(Gg + 6208 + row, __uint_as_float(r[j]));
                 }
         }
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {            // dW1 [64][32] | db1
             tmem_ld16(tmem + lane_base + TW_DW1 + 16 * c, r);
             tmem_wait_ld();
-            if (t < 64)
+            if (has)
                 for (int j = 0; j < 16; ++j) {
                     const int col = 16 * c + j;
-                    if (col < 32) atomicAdd(Gg + t * 32 + col, __uint_as_float(r[j]));
-                    else if (col == 32) atomicAdd(Gg + 2048 + t, __uint_as_float(r[j]));
+                    if (col < 32) atomicAdd(Gg + row * 32 + col, __uint_as_float(r[j]));
+                    else if (col == 32) atomicAdd(Gg + 2048 + row, __uint_as_float(r[j]));
                 }
         }
-        tmem_ld16(tmem + lane_base + TW_DW3, r);   // dW3^T [64][8] | db3
-        tmem_wait_ld();
-        if (t < 64)
-            for (int o = 0; o < 8; ++o) atomicAdd(Gg + 6272 + o * 64 + t, __uint_as_float(r[o]));
-        else if (t == 64)
-            for (int o = 0; o < 8; ++o) atomicAdd(Gg + 6784 + o, __uint_as_float(r[o]));
+#pragma unroll 1
+        for (int c = 0; c < 5; ++c) {            // dW3 [8][64] | db3
+            tmem_ld16(tmem + lane_base + TW_DW3 + 16 * c, r);
+            tmem_wait_ld();
+            if (has && row < 8)
+                for (int j = 0; j < 16; ++j) {
+                    const int col = 16 * c + j;
+                    if (col < 64) atomicAdd(Gg + 6272 + row * 64 + col, __uint_as_float(r[j]));
+                    else if (col == 64) atomicAdd(Gg + 6784 + row, __uint_as_float(r[j]));
+                }
+        }
     }
     if (!ok && t == 0) atomicOr(status, DEV_TIMEOUT);
     tc_fence_before();
