@@ -945,7 +945,7 @@ def run_neural(args):
 def run_train(args):
     """Neural training workload: the 4096^2 learned material (latent grids 1024^2..128^2 x 8,
     MLP 32-64-64-8); each step = one batch of --tbatch Philox-drawn texels through the
-    tensor-core forward and backward, then Adam over all 5.6 M latents and the MLP."""
+    tensor-core forward and backward, then Adam over all 11.1 M latent values and the MLP."""
     import torch
 
     import paper_2407_06107_b300 as stf
