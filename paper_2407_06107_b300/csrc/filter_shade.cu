@@ -48,11 +48,13 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             if (MODE == M_POSITIVIZED) LB = ints5(philox(id_lo, id_hi, 0xFFFFFFFFu, 1u, K));
         }
 
+        // stream 0 of the query: (jitter x, jitter y, level, pick x, pick y) per sample
+        const PhiloxS R0(id_lo, id_hi, 0u, K);
         if constexpr (MODE == M_STOCHASTIC) {
             // Software-pipelined: sample s+1 is picked and its texel load issued before
             // sample s is decoded and shaded, so the gather latency hides behind shading.
             auto pick = [&](uint32_t s, float* wt) -> typename RawOf<TF>::type {
-                U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+                U5 A = uniforms5(R0(s, K));
                 if (lat) {
                     const uint32_t lshift = lattice_shift(s, a.spp, 24);
 #pragma unroll
@@ -75,15 +77,14 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 const typename RawOf<TF>::type raw = raw_next;
                 const float Wt = wt_next;
                 if (s + 1 < a.spp) raw_next = pick(s + 1, &wt_next);
-                const float3 f = shade(a.shade, decode_raw<TF>(T, raw), SC);
+                const float3 f = shade<clamp_rough<TF>()>(a.shade, decode_raw<TF>(T, raw), SC);
                 acc.x = __fmaf_rn(Wt, f.x, acc.x);
                 acc.y = __fmaf_rn(Wt, f.y, acc.y);
                 acc.z = __fmaf_rn(Wt, f.z, acc.z);
             }
         } else
         for (uint32_t s = 0; s < a.spp; ++s) {
-            // stream 0: (jitter x, jitter y, level, pick x, pick y)
-            U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            U5 A = uniforms5(R0(s, K));
             const uint32_t lshift = lat ? lattice_shift(s, a.spp, 24) : 0u;
             if (lat) {
 #pragma unroll
@@ -256,7 +257,7 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
             uint32_t pk = NO_PICK;
             if (any) {
                 const int ix = wrap_index(ps, W), iy = wrap_index(pt, H);
-                est = shade(a.shade, fetch_t<TF>(T, lvl, ix, iy), SC);
+                est = shade<clamp_rough<TF>()>(a.shade, fetch_t<TF>(T, lvl, ix, iy), SC);
                 pk = pack_pick(lvl, ix, iy);
             }
             if (picks) {
@@ -300,7 +301,7 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
                             mb.n.y = fmaf(w, m.n.y, mb.n.y);
                             mb.n.z = fmaf(w, m.n.z, mb.n.z);
                         } else {
-                            const float3 f = shade(a.shade, m, SC);
+                            const float3 f = shade<clamp_rough<TF>()>(a.shade, m, SC);
                             ma.x = fmaf(w, f.x, ma.x);
                             ma.y = fmaf(w, f.y, ma.y);
                             ma.z = fmaf(w, f.z, ma.z);
@@ -420,7 +421,7 @@ __device__ __forceinline__ void gauss_query(const FilterShadeArgs& a, const Fetc
                 iy = (int)floorf(__fmaf_rn(y, (float)H, oy));
             }
             const int wx_ = wrap_index(ix, W), wy_ = wrap_index(iy, H);
-            est = shade(a.shade, fetch_t<TF>(T, lvl, wx_, wy_), SC);
+            est = shade<clamp_rough<TF>()>(a.shade, fetch_t<TF>(T, lvl, wx_, wy_), SC);
             if (picks) {
                 uint32_t* p2 = picks + (q * a.spp + s) * 2;
                 p2[0] = pack_pick(lvl, wx_, wy_);
@@ -466,7 +467,7 @@ __device__ __forceinline__ void gauss_query(const FilterShadeArgs& a, const Fetc
                             fm.n.y = fmaf(w, m.n.y, fm.n.y);
                             fm.n.z = fmaf(w, m.n.z, fm.n.z);
                         } else {
-                            const float3 f = shade(a.shade, m, SC);
+                            const float3 f = shade<clamp_rough<TF>()>(a.shade, m, SC);
                             est.x = fmaf(w, f.x, est.x);
                             est.y = fmaf(w, f.y, est.y);
                             est.z = fmaf(w, f.z, est.z);
@@ -570,10 +571,10 @@ k_filter_shade_1spp_pair(FilterShadeArgs a, const __grid_constant__ FetchCtx T, 
     const Pending1<TF> r0 = pick_1spp<FILTER, TF>(a, T, K, q0);
     Pending1<TF> r1{};
     if (two) r1 = pick_1spp<FILTER, TF>(a, T, K, q1);
-    const float3 f0 = shade(a.shade, decode_raw<TF>(T, r0.raw), SC);
+    const float3 f0 = shade<clamp_rough<TF>()>(a.shade, decode_raw<TF>(T, r0.raw), SC);
     a.r[q0] = r0.wt * f0.x; a.g[q0] = r0.wt * f0.y; a.b[q0] = r0.wt * f0.z;
     if (two) {
-        const float3 f1 = shade(a.shade, decode_raw<TF>(T, r1.raw), SC);
+        const float3 f1 = shade<clamp_rough<TF>()>(a.shade, decode_raw<TF>(T, r1.raw), SC);
         a.r[q1] = r1.wt * f1.x; a.g[q1] = r1.wt * f1.y; a.b[q1] = r1.wt * f1.z;
     }
 }

@@ -99,10 +99,8 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const AxisPos ap = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
-                        float w[4];
-                        axis_pick_weights<FILTER>(ap.t, w);
                         const int n = c == 0 ? a.nx : (c == 1 ? a.ny : a.nz);
-                        idx[c] = clamp_index(ap.i0 + T0 + cdf_pick<NT>(w, uk[c], 0, nullptr), n);
+                        idx[c] = clamp_index(ap.i0 + T0 + pick_positive<FILTER>(ap.t, uk[c]), n);
                     }
                     // at most 1024^3 voxels: the index fits 32 bits
                     return ((uint32_t)idx[2] * (uint32_t)a.ny + (uint32_t)idx[1]) * (uint32_t)a.nx + (uint32_t)idx[0];
@@ -117,10 +115,10 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                         uniforms3_of6(rw, odd, u);
                     }
                 };
-                const uint32_t sidx = V == KV_LATTICE ? 0xFFFFFFFFu : s;
+                const PhiloxT R(id_lo, id_hi, V == KV_LATTICE ? 0xFFFFFFFFu : s, K);
                 uint32_t k = 0;
                 for (; k + 1 < a.steps; k += 2) {
-                    const uint4 rw = philox(id_lo, id_hi, sidx, (k >> 1) + 1u, K);
+                    const uint4 rw = R((k >> 1) + 1u, K);
                     float u0[3], u1[3];
                     step_uniforms(rw, 0, u0);
                     step_uniforms(rw, 1, u1);
@@ -130,7 +128,7 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                 }
                 if (k < a.steps) {
                     float u0[3];
-                    step_uniforms(philox(id_lo, id_hi, sidx, (k >> 1) + 1u, K), 0, u0);
+                    step_uniforms(R((k >> 1) + 1u, K), 0, u0);
                     fixed_sum += (uint64_t)(__half2float(a.vox[voxel(k, u0)]) * 16777216.0f);
                 }
             } else
@@ -165,9 +163,9 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                         ky = cdf_pick_reuse<NT>(w[1], r1, &r2);
                         kz = cdf_pick_reuse<NT>(w[2], r2, &r3);
                     } else {
-                        kx = cdf_pick<NT>(w[0], uk[0], 0, nullptr);
-                        ky = cdf_pick<NT>(w[1], uk[1], 0, nullptr);
-                        kz = cdf_pick<NT>(w[2], uk[2], 0, nullptr);
+                        kx = pick_positive<FILTER>(ap[0].t, uk[0]);
+                        ky = pick_positive<FILTER>(ap[1].t, uk[1]);
+                        kz = pick_positive<FILTER>(ap[2].t, uk[2]);
                     }
                     const int ix = clamp_index(ap[0].i0 + T0 + kx, a.nx);
                     const int iy = clamp_index(ap[1].i0 + T0 + ky, a.ny);

@@ -386,21 +386,28 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
     const AxisPos ax = axis_pos(x, (float)R), ay = axis_pos(y, (float)R);
     float wx[4], wy[4];
     if constexpr (MODE == M_STOCHASTIC) {
-        axis_pick_weights<FILTER>(ax.t, wx);
-        axis_pick_weights<FILTER>(ay.t, wy);
+        if constexpr (is_signed(FILTER)) {
+            axis_pick_weights<FILTER>(ax.t, wx);
+            axis_pick_weights<FILTER>(ay.t, wy);
+        }
     } else {
         axis_weights<FILTER>(ax.t, wx);
         axis_weights<FILTER>(ay.t, wy);
     }
     o.query = (long long)q;
     if (MODE == M_STOCHASTIC) {
-        float Sx, Sy;
-        bool nx = false, ny = false;
-        const int kx = cdf_pick_sign<NT>(wx, A.u[3], &Sx, &nx);
-        const int ky = cdf_pick_sign<NT>(wy, A.u[4], &Sy, &ny);
-        float W = 1.0f;
-        if (is_signed(FILTER)) W = (nx != ny) ? -Sx * Sy : Sx * Sy;
-        o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R); o.w = W;
+        if constexpr (is_signed(FILTER)) {
+            float Sx, Sy;
+            bool nx = false, ny = false;
+            const int kx = cdf_pick_sign<NT, true>(wx, A.u[3], &Sx, &nx);
+            const int ky = cdf_pick_sign<NT, true>(wy, A.u[4], &Sy, &ny);
+            o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R);
+            o.w = (nx != ny) ? -Sx * Sy : Sx * Sy;
+        } else {   // a positive filter: the CDF in closed form, weight 1
+            o.ix = wrap_index(ax.i0 + T0 + pick_positive<FILTER>(ax.t, A.u[3]), R);
+            o.iy = wrap_index(ay.i0 + T0 + pick_positive<FILTER>(ay.t, A.u[4]), R);
+            o.w = 1.0f;
+        }
     } else if (MODE == M_POSITIVIZED) {
         float Px, Nx, Py, Ny;
         cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
@@ -551,12 +558,12 @@ __global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(Neur
                     float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     for (int r = t; r < t + NR; ++r)
                         for (int i = 0; i < 8; ++i) c[i] = fmaf(S.wt[r], S.ch[r][i], c[i]);
-                    const float3 f3 = shade(a.shade, material_from_channels(c), SC);
+                    const float3 f3 = shade<false>(a.shade, material_from_channels(c), SC);
                     est[0] = f3.x; est[1] = f3.y; est[2] = f3.z;
                 } else {
                     for (int r = t; r < t + NR; ++r) {
                         if (S.wt[r] == 0.0f) continue;
-                        const float3 f3 = shade(a.shade, material_from_channels(S.ch[r]), SC);
+                        const float3 f3 = shade<false>(a.shade, material_from_channels(S.ch[r]), SC);
                         est[0] = fmaf(S.wt[r], f3.x, est[0]);
                         est[1] = fmaf(S.wt[r], f3.y, est[1]);
                         est[2] = fmaf(S.wt[r], f3.z, est[2]);
@@ -798,7 +805,7 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
                     f = m.rho;
                 } else {
                     float rr, gg, bb;
-                    shade_ggx_t<float>(mat_t(m), rr, gg, bb);
+                    shade_ggx_t<float, false>(mat_t(m), rr, gg, bb);
                     f = make_float3(rr, gg, bb);
                 }
                 est = make_float3(w * f.x, w * f.y, w * f.z);

@@ -124,19 +124,80 @@ inline RoundKeys expand_key(uint64_t seed) {
     return r;
 }
 
-__device__ __forceinline__ uint4 philox(uint32_t id_lo, uint32_t id_hi, uint32_t sample,
-                                        uint32_t stream, const RoundKeys& K) {
-    uint32_t x0 = id_lo, x1 = id_hi, x2 = sample, x3 = stream;
+constexpr uint32_t PHILOX_M0 = 0xD2511F53u, PHILOX_M1 = 0xCD9E8D57u;   // round multipliers
+
+// rounds FIRST..9 on the state (x0, x1, x2, x3)
+template <int FIRST>
+__host__ __device__ __forceinline__ void philox_rounds(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                                       const RoundKeys& K) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * x0, p1 = (uint64_t)0xCD9E8D57u * x2;
+    for (int r = FIRST; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * x0, p1 = (uint64_t)PHILOX_M1 * x2;
         x0 = (uint32_t)(p1 >> 32) ^ x1 ^ K.k[2 * r];
         x1 = (uint32_t)p1;
         x2 = (uint32_t)(p0 >> 32) ^ x3 ^ K.k[2 * r + 1];
         x3 = (uint32_t)p0;
     }
+}
+
+__host__ __device__ __forceinline__ uint4 philox(uint32_t id_lo, uint32_t id_hi, uint32_t sample,
+                                                 uint32_t stream, const RoundKeys& K) {
+    uint32_t x0 = id_lo, x1 = id_hi, x2 = sample, x3 = stream;
+    philox_rounds<0>(x0, x1, x2, x3, K);
     return make_uint4(x0, x1, x2, x3);
 }
+
+// The same generator with the counter words that stay fixed across a loop hoisted out of it.
+// A round multiplies counter words 0 and 2; where a product depends on fixed words only, it
+// and the XORs that use it are computed once, before the loop.  Both return exactly
+// philox() of the same counter.
+//   PhiloxS: counter (id_lo, id_hi, s, stream), only the sample s varying -- the first two
+//            rounds cost two multiplies and three XORs instead of four and four;
+//   PhiloxT: counter (id_lo, id_hi, s, t), only the last word t varying -- the first three
+//            rounds cost two multiplies and four XORs instead of six and six.
+struct PhiloxS {
+    uint32_t c0, c1, l1, c2;
+    __host__ __device__ __forceinline__ PhiloxS(uint32_t id_lo, uint32_t id_hi, uint32_t stream, const RoundKeys& K) {
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * id_lo;                 // round 0, word 0
+        const uint32_t x2 = (uint32_t)(p0 >> 32) ^ stream ^ K.k[1];      // word 2 after round 0
+        c0 = id_hi ^ K.k[0];
+        const uint64_t q = (uint64_t)PHILOX_M1 * x2;                     // round 1, word 2
+        c1 = (uint32_t)(q >> 32) ^ K.k[2];
+        l1 = (uint32_t)q;                                                // word 1 after round 1
+        c2 = (uint32_t)p0 ^ K.k[3];
+    }
+    __host__ __device__ __forceinline__ uint4 operator()(uint32_t s, const RoundKeys& K) const {
+        const uint64_t p1 = (uint64_t)PHILOX_M1 * s;                     // round 0, word 2
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ c0, y1 = (uint32_t)p1;
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * y0;                    // round 1, word 0
+        uint32_t x0 = y1 ^ c1, x1 = l1, x2 = (uint32_t)(p0 >> 32) ^ c2, x3 = (uint32_t)p0;
+        philox_rounds<2>(x0, x1, x2, x3, K);
+        return make_uint4(x0, x1, x2, x3);
+    }
+};
+struct PhiloxT {
+    uint32_t d0, d1, d2, e1, d3;
+    __host__ __device__ __forceinline__ PhiloxT(uint32_t id_lo, uint32_t id_hi, uint32_t s, const RoundKeys& K) {
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * id_lo, p1 = (uint64_t)PHILOX_M1 * s;   // round 0
+        const uint32_t g0 = (uint32_t)(p1 >> 32) ^ id_hi ^ K.k[0];
+        d0 = (uint32_t)(p0 >> 32) ^ K.k[1];                              // word 2 after round 0: d0 ^ t
+        d1 = (uint32_t)p1 ^ K.k[2];
+        const uint64_t r0 = (uint64_t)PHILOX_M0 * g0;                    // round 1, word 0
+        const uint32_t e2 = (uint32_t)(r0 >> 32) ^ (uint32_t)p0 ^ K.k[3];
+        const uint64_t r2 = (uint64_t)PHILOX_M1 * e2;                    // round 2, word 2
+        d2 = (uint32_t)(r2 >> 32) ^ K.k[4];
+        e1 = (uint32_t)r2;                                               // word 1 after round 2
+        d3 = (uint32_t)r0 ^ K.k[5];
+    }
+    __host__ __device__ __forceinline__ uint4 operator()(uint32_t t, const RoundKeys& K) const {
+        const uint64_t p1 = (uint64_t)PHILOX_M1 * (d0 ^ t);              // round 1, word 2
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ d1, y1 = (uint32_t)p1;
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * y0;                    // round 2, word 0
+        uint32_t x0 = y1 ^ d2, x1 = e1, x2 = (uint32_t)(p0 >> 32) ^ d3, x3 = (uint32_t)p0;
+        philox_rounds<3>(x0, x1, x2, x3, K);
+        return make_uint4(x0, x1, x2, x3);
+    }
+};
 // top 24 bits scaled by 2^-24: exact in FP32
 __device__ __forceinline__ float unif(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-8f; }
 
@@ -277,8 +338,10 @@ __device__ __forceinline__ int cdf_pick(const float w[4], float xi, int cls, flo
 }
 
 // cdf_pick over all taps (class 0) that also reports whether the picked weight is negative,
-// selected in the same compare chain as the index
-template <int N>
+// selected in the same compare chain as the index.  INNER_POS: the two inner weights of a
+// 4-tap filter are known to be positive (Keys and Mitchell-Netravali: at least 1/2 (1-t) and
+// 1/18 on [0, 1)), so only the outer taps can carry a minus sign.
+template <int N, bool INNER_POS = false>
 __device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* total, bool* neg) {
     float c[N];
     float acc = 0.0f;
@@ -286,6 +349,11 @@ __device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* 
     for (int k = 0; k < N; ++k) { acc = __fadd_rn(acc, fabsf(w[k])); c[k] = acc; }
     *total = acc;
     const float target = __fmul_rn(xi, acc);
+    if constexpr (INNER_POS && N == 4) {
+        const bool h0 = target < c[0], h1 = target < c[1], h2 = target < c[2];
+        *neg = h0 ? (w[0] < 0.0f) : (!h2 && w[3] < 0.0f);
+        return h0 ? 0 : (h1 ? 1 : (h2 ? 2 : 3));
+    }
     int k = N - 1;
     bool ng = w[N - 1] < 0.0f;
 #pragma unroll
@@ -296,6 +364,26 @@ __device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* 
     }
     *neg = ng;
     return k;
+}
+
+// The tap a positive filter picks on one axis for the uniform xi, the first k with xi < C_k,
+// from the CDF's closed form (the weights sum to one): tent C_0 = 1 - t; cubic B-spline
+// 6 C_0 = (1-t)^3, 6 C_1 = 5 - 3t - 3t^2 + 2t^3, 6 C_2 = 6 - t^3 (prefix sums of the
+// polynomials of the bicubic listing).  In FP32 each boundary lies within ~1e-7 of its exact
+// value, inside the 1e-6 band around a boundary where a pick may differ from the exact one.
+template <int F>
+__device__ __forceinline__ int pick_positive(float t, float xi) {
+    static_assert(F == F_LINEAR || F == F_BSPLINE, "positive filters only");
+    if constexpr (F == F_LINEAR) {
+        return xi < __fsub_rn(1.0f, t) ? 0 : 1;
+    } else {
+        const float s = __fsub_rn(1.0f, t);
+        const float c0 = __fmul_rn(__fmul_rn(s, s), s);
+        const float c1 = __fmaf_rn(__fmaf_rn(__fmaf_rn(2.0f, t, -3.0f), t, -3.0f), t, 5.0f);
+        const float c2 = __fmaf_rn(-__fmul_rn(t, t), t, 6.0f);
+        const float x6 = __fmul_rn(xi, 6.0f);
+        return x6 < c0 ? 0 : (x6 < c1 ? 1 : (x6 < c2 ? 2 : 3));
+    }
 }
 
 // Sample reuse: the same pick, and the uniform remapped into the chosen interval,
@@ -340,8 +428,9 @@ __device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0),
 // ---------------------------------------------------------------- shading (FP32)
 struct Material { float3 rho; float rough; float3 n; };
 
-// Fixed light / view directions (unit in exact arithmetic) and the derived half vector,
-// F(v.h) and 1/pi.  The half vector is FP32-rounded normalize(l+v).
+// Fixed light / view directions (unit in exact arithmetic), the derived half vector (FP32-rounded
+// normalize(l+v)) and F(v.h) / (2 pi), as the host evaluates them; the shading kernels take
+// the same directions as compile-time constants (GgxK).
 struct ShadeConst {
     float3 l, v, h;
     float Fk;   // F / (2 pi): Schlick Fresnel at v.h (F0 = 0.04) with the constant factors of D G F / 4
@@ -366,29 +455,40 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return r;
 }
 
-// The light, view and half vectors and the Fresnel factor as compile-time FP32 constants:
-// l = (0.48, 0.36, 0.80), v = (-0.28, 0, 0.96), h = normalize(l + v) and Fk = F(v.h) / (2 pi)
-// (Schlick, F0 = 0.04, with the constant factors of D G F / 4) evaluated in double and
-// rounded once -- the same values make_shade_const() computes on the host.
+// The light, view and half vectors as compile-time FP32 constants: l = (0.48, 0.36, 0.80),
+// v = (-0.28, 0, 0.96) (unit in exact arithmetic) and h = normalize(l + v), stored scaled by
+// kappa = Fk^(-1/4), where Fk = F(v.h) / (2 pi) is the Schlick Fresnel at v.h (F0 = 0.04) with
+// the constant factors of D G F / 4.  h enters only n.h and |n x h|^2, so the scaled vector
+// gives q' = kappa^2 q for the denominator q = a2 (n.h)^2 + |n x h|^2 of D, and a2 / q'^2 is
+// Fk a2 / q^2: the constant factor costs no multiply.  Each constant is evaluated in double
+// and rounded once to FP32.
 struct GgxK {
     static constexpr float lx = 0.48f, ly = 0.36f, lz = 0.80f;
     static constexpr float vx = -0.28f, vz = 0.96f;
-    static constexpr float hx = 0x1.c53674p-4f, hy = 0x1.97e436p-3f, hz = 0x1.f288b4p-1f;
-    static constexpr float Fk = 0x1.a14c3ap-8f;
+    static constexpr float hx = 0x1.91191ap-2f, hy = 0x1.68fcfep-1f, hz = 0x1.b93536p+1f;   // kappa h
 };
 
 // A decoded material as scalars (T = float) or as two samples' materials (T = F2).
 template <class T> struct MatT { T rx, ry, rz, rough, nx, ny, nz; };
 
+// x where both n.l > 0 and n.v > 0, else 0, per lane
+__device__ __forceinline__ float above(float x, float nl, float nv) { return (nl > 0.0f && nv > 0.0f) ? x : 0.0f; }
+__device__ __forceinline__ F2 above(F2 x, F2 nl, F2 nv) {
+    const float2 X = upk2(x.v), L = upk2(nl.v), V = upk2(nv.v);
+    return f2(above(X.x, L.x, V.x), above(X.y, L.y, V.y));
+}
+
 // f_hat = [rho/pi + D G2 F / (4 nl nv)] nl  (GGX, height-correlated Smith, Schlick), zero
 // where nl <= 0 or nv <= 0.  Every operation is one explicit rounding, so the T = float and
-// T = F2 forms agree bit for bit.
-template <class T>
+// T = F2 forms agree bit for bit.  CLAMP: clamp the roughness to [0.05, 1] first; a caller
+// whose decoded roughness lies in that range already (0.05 + 0.95 x with x in [0, 1]) skips it.
+template <class T, bool CLAMP = true>
 __device__ __forceinline__ void shade_ggx_t(const MatT<T>& m, T& r, T& g, T& b) {
     using K = GgxK;
     const T nl = vfma(m.nz, vconst<T>(K::lz), vfma(m.ny, vconst<T>(K::ly), vmul(m.nx, vconst<T>(K::lx))));
     const T nv = vfma(m.nz, vconst<T>(K::vz), vmul(m.nx, vconst<T>(K::vx)));
-    const T a = vmap(m.rough, [](float x) { return fminf(fmaxf(x, 0.05f), 1.0f); });
+    T a = m.rough;
+    if constexpr (CLAMP) a = vmap(m.rough, [](float x) { return fminf(fmaxf(x, 0.05f), 1.0f); });
     const T a2 = vmul(a, a);
     // |n x h|^2 instead of 1 - (n.h)^2: D = a2 / (pi q^2) is relative to q >= a2 (n.h)^2,
     // so the cancellation of 1 - (n.h)^2 near n = h would show in D
@@ -400,44 +500,37 @@ __device__ __forceinline__ void shade_ggx_t(const MatT<T>& m, T& r, T& g, T& b) 
     auto rcp = [](float x) { return rcp_approx(x); };
     auto rsq = [](float x) { return rsqrt_approx(x); };
     const T rq = vmap(q, rcp), rnl = vmap(nl, rcp), rnv = vmap(nv, rcp);
-    // D = a2 / (pi q^2).  Lambda = (sqrt(1 + a2 tan^2) - 1) / 2 with sin^2 = 1 - (n.w)^2
+    // D = a2 / (pi q^2).  Lambda = (sqrt(1 + a2 tan^2) - 1) / 2 with tan^2 = 1/(n.w)^2 - 1
     // (|n| = 1), so G2 = 1 / (1 + Ll + Lv) = 2 / (sqrt(sl) + sqrt(sv)): a sum of two positive
-    // roots, one reciprocal, no cancellation.  The constants 1/pi, 2 and 1/4 sit in Fk.
-    const T one = vconst<T>(1.0f);
-    const T xl = vmul(vmul(vmul(a2, vfma(vmul(nl, vconst<T>(-1.0f)), nl, one)), rnl), rnl);
-    const T xv = vmul(vmul(vmul(a2, vfma(vmul(nv, vconst<T>(-1.0f)), nv, one)), rnv), rnv);
-    const T sl = vadd(one, xl), sv = vadd(one, xv);
+    // roots, one reciprocal, no cancellation.  The constants 1/pi, 2, 1/4 and F ride in kappa.
+    const T one = vconst<T>(1.0f), mone = vconst<T>(-1.0f);
+    const T sl = vfma(a2, vfma(rnl, rnl, mone), one);
+    const T sv = vfma(a2, vfma(rnv, rnv, mone), one);
     const T rg = vmap(vfma(sl, vmap(sl, rsq), vmul(sv, vmap(sv, rsq))), rcp);
-    const T spec = vmul(vmul(vmul(vmul(vmul(a2, rq), rq), rg), vconst<T>(K::Fk)), rnv);
-    const T kd = vmul(nl, vconst<T>(0.318309886183790672f));
+    // the lobe exists only above both horizons
+    const T spec = above(vmul(vmul(vmul(vmul(a2, rq), rq), rg), rnv), nl, nv);
+    const T kd = above(vmul(nl, vconst<T>(0.318309886183790672f)), nl, nv);
     r = vfma(m.rx, kd, spec);
     g = vfma(m.ry, kd, spec);
     b = vfma(m.rz, kd, spec);
-    // the lobe exists only above both horizons
-    auto keep = [](float x, float n1, float n2) { return (n1 > 0.0f && n2 > 0.0f) ? x : 0.0f; };
-    if constexpr (sizeof(T) == sizeof(float)) {
-        r = keep(lo(r), lo(nl), lo(nv)); g = keep(lo(g), lo(nl), lo(nv)); b = keep(lo(b), lo(nl), lo(nv));
-    } else {
-        const float2 L = upk2(nl.v), V = upk2(nv.v);
-        const float2 R = upk2(r.v), G = upk2(g.v), B = upk2(b.v);
-        r = f2(keep(R.x, L.x, V.x), keep(R.y, L.y, V.y));
-        g = f2(keep(G.x, L.x, V.x), keep(G.y, L.y, V.y));
-        b = f2(keep(B.x, L.x, V.x), keep(B.y, L.y, V.y));
-    }
 }
 
 __device__ __forceinline__ MatT<float> mat_t(const Material& m) {
     return {m.rho.x, m.rho.y, m.rho.z, m.rough, m.n.x, m.n.y, m.n.z};
 }
+template <bool CLAMP = true>
 __device__ __forceinline__ float3 shade_ggx(const Material& m, const ShadeConst&) {
     float r, g, b;
-    shade_ggx_t<float>(mat_t(m), r, g, b);
+    shade_ggx_t<float, CLAMP>(mat_t(m), r, g, b);
     return make_float3(r, g, b);
 }
 
+// CLAMP = false: the caller's roughness is in [0.05, 1] already (a decoded texel of an RGBA8,
+// DCT or learned texture); the clamp would return it unchanged.
+template <bool CLAMP = true>
 __device__ __forceinline__ float3 shade(int sh, const Material& m, const ShadeConst& C) {
     if (sh == SH_LINEAR) return m.rho;
-    return shade_ggx(m, C);
+    return shade_ggx<CLAMP>(m, C);
 }
 
 // ---------------------------------------------------------------- texel decode

@@ -36,6 +36,10 @@ template <int TF> struct RawOf { using type = uint4; };
 template <> struct RawOf<TF_DCT> { using type = DctRaw; };
 template <> struct RawOf<TF_RGBA8N> { using type = uint2; };
 
+// Whether a decoded texel's roughness needs clamping to [0.05, 1] before shading: an RGBA32F
+// texel holds any value; the other formats decode to 0.05 + 0.95 x with x in [0, 1].
+template <int TF> constexpr bool clamp_rough() { return TF == TF_BASIC; }
+
 // the family a texture's kernels may use: RGBA8N for RGBA8 textures with a normal map
 inline int texture_family(const FetchCtx& T) {
     return T.fmt == FMT_DCT ? TF_DCT : (T.fmt == FMT_RGBA8 && T.has_normal) ? TF_RGBA8N : TF_BASIC;
@@ -125,6 +129,16 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
     lvl = min(lvl, T.levels - 1);
     const int W = T.w[lvl], H = T.h[lvl];
     const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+    Pick1 p;
+    p.lvl = lvl;
+    p.wt = 1.0f;
+    if constexpr (!is_signed(FILTER)) {
+        if (!reuse) {   // a positive filter's pick needs no weights: its CDF in closed form
+            p.ix = wrap_index(ax.i0 + T0 + pick_positive<FILTER>(ax.t, A.u[3]), W);
+            p.iy = wrap_index(ay.i0 + T0 + pick_positive<FILTER>(ay.t, A.u[4]), H);
+            return p;
+        }
+    }
     float wx[4], wy[4];
     axis_pick_weights<FILTER>(ax.t, wx);
     axis_pick_weights<FILTER>(ay.t, wy);
@@ -145,17 +159,14 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
             }
         }
     } else if (is_signed(FILTER)) {
-        kx = cdf_pick_sign<NT>(wx, A.u[3], &Sx, &nx);
-        ky = cdf_pick_sign<NT>(wy, A.u[4], &Sy, &ny);
+        kx = cdf_pick_sign<NT, true>(wx, A.u[3], &Sx, &nx);
+        ky = cdf_pick_sign<NT, true>(wy, A.u[4], &Sy, &ny);
     } else {
         kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
         ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
     }
-    Pick1 p;
-    p.lvl = lvl;
     p.ix = wrap_index(ax.i0 + T0 + kx, W);
     p.iy = wrap_index(ay.i0 + T0 + ky, H);
-    p.wt = 1.0f;
     if (is_signed(FILTER)) {
         p.wt = Sx * Sy;
         if (nx != ny) p.wt = -p.wt;
@@ -198,10 +209,10 @@ __device__ __forceinline__ float3 positivized_sample(const FetchCtx& T, float x,
         raw_n = load_raw<TF>(T, lvl, jx, jy);
         negpick = pack_pick(lvl, jx, jy);
     }
-    const float3 f = shade(shade_mode, decode_raw<TF>(T, raw_p), SC);
+    const float3 f = shade<clamp_rough<TF>()>(shade_mode, decode_raw<TF>(T, raw_p), SC);
     float3 est = make_float3(Wp * f.x, Wp * f.y, Wp * f.z);
     if (Wn > 0.0f) {
-        const float3 g = shade(shade_mode, decode_raw<TF>(T, raw_n), SC);
+        const float3 g = shade<clamp_rough<TF>()>(shade_mode, decode_raw<TF>(T, raw_n), SC);
         est.x = fmaf(-Wn, g.x, est.x);
         est.y = fmaf(-Wn, g.y, est.y);
         est.z = fmaf(-Wn, g.z, est.z);
@@ -259,7 +270,7 @@ __device__ __forceinline__ void ntap_accumulate(const FetchCtx& T, float x, floa
                     fm.n.y = fmaf(w, m.n.y, fm.n.y);
                     fm.n.z = fmaf(w, m.n.z, fm.n.z);
                 } else {
-                    const float3 f = shade(shade_mode, m, SC);
+                    const float3 f = shade<clamp_rough<TF>()>(shade_mode, m, SC);
                     fsum.x = fmaf(w, f.x, fsum.x);
                     fsum.y = fmaf(w, f.y, fsum.y);
                     fsum.z = fmaf(w, f.z, fsum.z);

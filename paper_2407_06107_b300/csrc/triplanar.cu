@@ -66,7 +66,7 @@ __device__ __forceinline__ float3 plane_sample(const FetchCtx& T, const PlaneQ& 
     if (has_d) jitter(s, kside, flags, A, p.dudx, p.dvdx, p.dudy, p.dvdy, &x, &y);
     if constexpr (MODE == M_STOCHASTIC) {
         const Pick1 k = pick_1tap<FILTER>(T, x, y, p.l0, p.fr, A, false);
-        const float3 f = shade(shade_mode, fetch_t<TF>(T, k.lvl, k.ix, k.iy), SC);
+        const float3 f = shade<clamp_rough<TF>()>(shade_mode, fetch_t<TF>(T, k.lvl, k.ix, k.iy), SC);
         if (pk) { pk[0] = pack_pick(k.lvl, k.ix, k.iy); pk[1] = NO_PICK; }
         const float w = scale * k.wt;
         return make_float3(w * f.x, w * f.y, w * f.z);
@@ -219,7 +219,7 @@ __device__ __forceinline__ TriPick<TF> tri_pick_1spp(const TriplanarArgs& a, con
 template <int TF>
 __device__ __forceinline__ void tri_finish_1spp(const TriplanarArgs& a, const TriTex& TT, const ShadeConst& SC,
                                                 const TriPick<TF>& r, uint64_t q) {
-    const float3 f = shade(a.shade, decode_raw<TF>(TT.t[r.plane], r.raw), SC);
+    const float3 f = shade<clamp_rough<TF>()>(a.shade, decode_raw<TF>(TT.t[r.plane], r.raw), SC);
     a.r[q] = r.wt * f.x;
     a.g[q] = r.wt * f.y;
     a.b[q] = r.wt * f.z;
