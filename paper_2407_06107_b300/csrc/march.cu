@@ -22,8 +22,13 @@ __device__ __forceinline__ float vox(const MarchArgs& a, int x, int y, int z) {
 
 // V: the kernel variant (KV_*).  The specialised ones (no picks; no flags, or the lattice
 // flag alone) run the stochastic steps in pairs, see below.
+// Resident 128-thread blocks per SM the register budget is set for: 10 (<= 48 registers) for
+// the specialised 1-tap marches, no bound for the others.
+template <int MODE, int V>
+constexpr int march_min_blocks() { return (MODE == M_STOCHASTIC && V != KV_GENERAL) ? 10 : 1; }
+
 template <int FILTER, int MODE, int V>
-__global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
+__global__ void __launch_bounds__(128, march_min_blocks<MODE, V>()) k_march(MarchArgs a, RoundKeys K) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
     const float res[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
     const uint32_t flags = V == KV_GENERAL ? a.flags : variant_flags(V);
@@ -93,44 +98,57 @@ __global__ void __launch_bounds__(128) k_march(MarchArgs a, RoundKeys K) {
                 // are made and both voxel loads issued before either density is added, so
                 // two gathers are in flight per thread.  LATTICE: the call is the per-pixel
                 // offset (sample index 0xFFFFFFFF), shifted per sample.
-                auto voxel = [&](uint32_t k, const float uk[3]) -> uint32_t {
-                    const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
+                // kh = k + 1/2, the step's midpoint in steps, kept as an exact float; the pick
+                // uniforms come pre-scaled for pick_positive_scaled
+                auto voxel = [&](float kh, const float uk[3]) -> int {
+                    const float tk = __fmaf_rn(kh, dt, tmin);
                     int idx[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const AxisPos ap = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
-                        const int n = c == 0 ? a.nx : (c == 1 ? a.ny : a.nz);
-                        idx[c] = clamp_index(ap.i0 + T0 + pick_positive<FILTER>(ap.t, uk[c]), n);
+                        idx[c] = ap.i0 + T0 + pick_positive_scaled<FILTER>(ap.t, uk[c]);
                     }
-                    // at most 1024^3 voxels: the index fits 32 bits
-                    return ((uint32_t)idx[2] * (uint32_t)a.ny + (uint32_t)idx[1]) * (uint32_t)a.nx + (uint32_t)idx[0];
+                    // A sample point lies inside the box, so a picked index is in [-2, n + 1] and
+                    // the bordered copy holds its clamped voxel: no clamping here.  At most
+                    // 1028^2 x 1032 voxels: the offset fits 32 bits.
+                    return idx[2] * a.pxy + idx[1] * a.px + idx[0];
                 };
+                constexpr float US = pick_scale<FILTER>();
                 auto step_uniforms = [&](const uint4& rw, int odd, float u[3]) {
                     if constexpr (V == KV_LATTICE) {
                         uint32_t f[3];
                         ints3_of6(rw, odd, f);
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) u[c] = lattice(f[c], lshift, 21);
+                        for (int c = 0; c < 3; ++c) u[c] = lattice(f[c], lshift, 21, US);
                     } else {
-                        uniforms3_of6(rw, odd, u);
+                        uniforms3_of6(rw, odd, u, US);
                     }
                 };
                 const PhiloxT R(id_lo, id_hi, V == KV_LATTICE ? 0xFFFFFFFFu : s, K);
-                uint32_t k = 0;
-                for (; k + 1 < a.steps; k += 2) {
-                    const uint4 rw = R((k >> 1) + 1u, K);
-                    float u0[3], u1[3];
-                    step_uniforms(rw, 0, u0);
-                    step_uniforms(rw, 1, u1);
-                    const uint32_t v0 = voxel(k, u0), v1 = voxel(k + 1, u1);
-                    const float d0 = __half2float(a.vox[v0]), d1 = __half2float(a.vox[v1]);
-                    fixed_sum += (uint64_t)(d0 * 16777216.0f) + (uint64_t)(d1 * 16777216.0f);
-                }
-                if (k < a.steps) {
-                    float u0[3];
-                    step_uniforms(R((k >> 1) + 1u, K), 0, u0);
-                    fixed_sum += (uint64_t)(__half2float(a.vox[voxel(k, u0)]) * 16777216.0f);
-                }
+                // The sum in an accumulator of type Acc.  32 bits hold it exactly when steps x
+                // (largest density) < 256, each term d 2^24 then below 2^32 / steps (a.fixed32).
+                auto march = [&](auto zero) -> uint64_t {
+                    using Acc = decltype(zero);
+                    Acc sum = zero;
+                    uint32_t k = 0;
+                    float kh = 0.5f;
+                    for (; k + 1 < a.steps; k += 2, kh = __fadd_rn(kh, 2.0f)) {
+                        const uint4 rw = R((k >> 1) + 1u, K);
+                        float u0[3], u1[3];
+                        step_uniforms(rw, 0, u0);
+                        step_uniforms(rw, 1, u1);
+                        const int v0 = voxel(kh, u0), v1 = voxel(__fadd_rn(kh, 1.0f), u1);
+                        const float d0 = __half2float(a.vpad[v0]), d1 = __half2float(a.vpad[v1]);
+                        sum += (Acc)(d0 * 16777216.0f) + (Acc)(d1 * 16777216.0f);
+                    }
+                    if (k < a.steps) {
+                        float u0[3];
+                        step_uniforms(R((k >> 1) + 1u, K), 0, u0);
+                        sum += (Acc)(__half2float(a.vpad[voxel(kh, u0)]) * 16777216.0f);
+                    }
+                    return (uint64_t)sum;
+                };
+                fixed_sum = a.fixed32 ? march(uint32_t{0}) : march(uint64_t{0});
             } else
             for (uint32_t k = 0; k < a.steps; ++k) {
                 const float tk = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, tmin);
@@ -453,6 +471,44 @@ __global__ void __launch_bounds__(128) k_march_staged(MarchArgs a, const __grid_
 // The volume as a 3-D FP16 tensor for the staged march: dims (nx, ny, nz), x fastest, box
 // 24 x 8 x 8.  Needs 16-byte row and slice strides (nx a multiple of 8); false otherwise or if
 // the driver cannot encode it.
+// Largest density of a volume as FP16 bits (non-negative FP16 values order like their bit
+// patterns; negative densities count as 0, NaN and infinity above every finite value).
+__global__ void k_vol_max_bits(const uint16_t* __restrict__ v, uint64_t n, unsigned int* out) {
+    unsigned int m = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned int b = v[i];
+        m = max(m, (b & 0x8000u) ? 0u : b);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+cudaError_t launch_vol_max_bits(const void* vox, uint64_t n, unsigned int* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const uint64_t g = (n + 255) / 256;
+    k_vol_max_bits<<<(int)(g < 2048 ? (g ? g : 1) : 2048), 256, 0, st>>>((const uint16_t*)vox, n, out);
+    return cudaGetLastError();
+}
+
+// The clamped border copy of a volume (clamp-to-edge addressing written out): every voxel of
+// the padded grid takes the voxel at its coordinates clamped to the volume.
+__global__ void k_pad_volume(const __half* __restrict__ src, int nx, int ny, int nz, __half* __restrict__ dst,
+                             int px, int py, int pz) {
+    const uint64_t n = (uint64_t)px * py * pz;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % (uint64_t)px), y = (int)(i / (uint64_t)px % (uint64_t)py), z = (int)(i / ((uint64_t)px * py));
+        const int sx = clamp_index(x - VOL_PAD, nx), sy = clamp_index(y - VOL_PAD, ny), sz = clamp_index(z - VOL_PAD, nz);
+        dst[i] = src[((size_t)sz * ny + sy) * nx + sx];
+    }
+}
+cudaError_t launch_pad_volume(const void* src, int nx, int ny, int nz, void* dst, cudaStream_t st) {
+    const int px = (int)vol_pad_pitch((uint32_t)nx), py = ny + 2 * VOL_PAD, pz = nz + 2 * VOL_PAD;
+    const uint64_t g = ((uint64_t)px * py * pz + 255) / 256;
+    k_pad_volume<<<(int)(g < 8192 ? (g ? g : 1) : 8192), 256, 0, st>>>((const __half*)src, nx, ny, nz, (__half*)dst,
+                                                                       px, py, pz);
+    return cudaGetLastError();
+}
+
 bool encode_volume_tmap(CUtensorMap* out, const void* vox, int nx, int ny, int nz) {
     if (nx % 8 != 0 || nx < SB_X || ny < SB_Y || nz < SB_Z) return false;
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -190,7 +190,7 @@ stf_status stf_destroy(stf_ctx c) {
     cudaStreamSynchronize(c->stream);
     drain_lanes(c);
     for (auto& kv : c->tex) cudaFree(kv.second.mem);
-    for (auto& kv : c->vol) cudaFree(kv.second.mem);
+    for (auto& kv : c->vol) { cudaFree(kv.second.mem); cudaFree(kv.second.pad); }
     for (auto& kv : c->tables) cudaFree(kv.second.mem);
     for (auto& kv : c->neural) { cudaFree(kv.second.mem); if (kv.second.loss) cudaFree(kv.second.loss); }
     for (int i = 0; i < STF_LANES; ++i) {
@@ -715,9 +715,23 @@ stf_status stf_create_volume(stf_ctx c, uint32_t nx, uint32_t ny, uint32_t nz, s
     const size_t bytes = (size_t)nx * ny * nz * 2;
     stf_status s = dev_alloc(c, &rec.mem, bytes);
     if (s != STF_OK) return s;
+    const size_t pbytes = (size_t)stf::vol_pad_pitch(nx) * (ny + 2 * stf::VOL_PAD) * (nz + 2 * stf::VOL_PAD) * 2;
+    s = dev_alloc(c, &rec.pad, pbytes);
+    if (s != STF_OK) { cudaFree(rec.mem); return s; }
+    unsigned int* d_max = nullptr;
+    s = dev_alloc(c, (void**)&d_max, sizeof(unsigned int));
+    if (s != STF_OK) { cudaFree(rec.mem); cudaFree(rec.pad); return s; }
+    unsigned int max_bits = 0x7C00u;
     cudaError_t e = cudaMemcpyAsync(rec.mem, data, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = stf::launch_pad_volume(rec.mem, (int)nx, (int)ny, (int)nz, rec.pad, c->stream);
+    if (e == cudaSuccess) e = stf::launch_vol_max_bits(rec.mem, bytes / 2, d_max, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&max_bits, d_max, sizeof(max_bits), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) { cudaFree(rec.mem); return cuda_fail(c, e, "volume upload"); }
+    cudaFree(d_max);
+    if (e != cudaSuccess) { cudaFree(rec.mem); cudaFree(rec.pad); return cuda_fail(c, e, "volume upload"); }
+    __half_raw hr;
+    hr.x = (unsigned short)max_bits;
+    rec.dmax = max_bits >= 0x7C00u ? INFINITY : __half2float(__half(hr));
     rec.tmap_ok = stf::encode_volume_tmap(&rec.tmap, rec.mem, (int)nx, (int)ny, (int)nz);
     const uint64_t h = c->next_handle++;
     c->vol[h] = rec;
@@ -732,6 +746,7 @@ stf_status stf_destroy_volume(stf_ctx c, stf_vol v) {
     CurrentDevice cd(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(it->second.mem);
+    cudaFree(it->second.pad);
     c->vol.erase(it);
     return STF_OK;
 }
@@ -759,6 +774,10 @@ stf_status stf_march_volume(stf_ctx c, stf_vol v, const float* cam, uint32_t wid
     stf::MarchArgs a{};
     a.vox = (const __half*)it->second.mem;
     a.nx = (int)it->second.nx; a.ny = (int)it->second.ny; a.nz = (int)it->second.nz;
+    a.px = (int)stf::vol_pad_pitch(it->second.nx);
+    a.pxy = a.px * (a.ny + 2 * stf::VOL_PAD);
+    a.vpad = (const __half*)it->second.pad + (size_t)stf::VOL_PAD * ((size_t)a.pxy + a.px + 1);
+    a.fixed32 = (double)steps * it->second.dmax < 256.0 ? 1 : 0;
     a.sigma_scale = it->second.sigma_scale;
     for (int i = 0; i < 12; ++i) a.cam[i] = cam[i];
     a.width = width; a.height = height; a.steps = steps; a.spp = spp; a.flags = flags;

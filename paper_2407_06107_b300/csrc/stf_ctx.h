@@ -18,8 +18,10 @@ struct TexRec {
 };
 struct VolRec {
     void* mem = nullptr;
+    void* pad = nullptr;            // the voxels with a clamped two-voxel border (launch_pad_volume)
     uint32_t nx = 0, ny = 0, nz = 0;
     float sigma_scale = 1.0f;
+    float dmax = 0.0f;              // largest density (0 for none; infinite for inf or NaN voxels)
     CUtensorMap tmap{};             // the voxels as a TMA tensor (valid when tmap_ok)
     bool tmap_ok = false;
 };

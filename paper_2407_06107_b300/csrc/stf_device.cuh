@@ -216,8 +216,9 @@ __device__ __forceinline__ U5 uniforms5(uint4 w) {
 __device__ __forceinline__ uint32_t lattice_shift(uint32_t s, uint32_t spp, int bits) {
     return (uint32_t)(((uint64_t)s << bits) / spp);          // floor(s 2^bits / spp), once per sample
 }
-__device__ __forceinline__ float lattice(uint32_t phi, uint32_t shift, int bits) {
-    return __uint2float_rn((phi + shift) & ((1u << bits) - 1u)) * __int_as_float((127 - bits) << 23);
+// (times `scale`, a small integer: the product is the one rounding)
+__device__ __forceinline__ float lattice(uint32_t phi, uint32_t shift, int bits, float scale = 1.0f) {
+    return __uint2float_rn((phi + shift) & ((1u << bits) - 1u)) * (__int_as_float((127 - bits) << 23) * scale);
 }
 // integer numerators of uniforms5
 struct I5 { uint32_t f[5]; };
@@ -237,9 +238,10 @@ __device__ __forceinline__ void ints3_of6(uint4 w, int odd, uint32_t f[3]) {
     }
 }
 
-// six 21-bit uniforms per Philox output: three for each of two volume march steps
-__device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3]) {
-    const float k = 4.76837158203125e-7f;
+// six 21-bit uniforms per Philox output: three for each of two volume march steps, each
+// times `scale` (a power of two times a small integer: the product is the one rounding)
+__device__ __forceinline__ void uniforms3_of6(uint4 w, int odd, float u[3], float scale = 1.0f) {
+    const float k = 4.76837158203125e-7f * scale;
     if (!odd) {
         u[0] = __uint2float_rn(w.x >> 11) * k; u[1] = __uint2float_rn(w.y >> 11) * k;
         u[2] = __uint2float_rn(w.z >> 11) * k;
@@ -371,19 +373,26 @@ __device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* 
 // 6 C_0 = (1-t)^3, 6 C_1 = 5 - 3t - 3t^2 + 2t^3, 6 C_2 = 6 - t^3 (prefix sums of the
 // polynomials of the bicubic listing).  In FP32 each boundary lies within ~1e-7 of its exact
 // value, inside the 1e-6 band around a boundary where a pick may differ from the exact one.
+// pick_positive_scaled takes xs = pick_scale<F>() * xi; a caller that forms xi = n * 2^-b
+// from an integer n < 2^b can fold the scale into that multiply (n * (6 * 2^-b) rounds to
+// the same value as (n * 2^-b) * 6).
+template <int F> __host__ __device__ constexpr float pick_scale() { return F == F_BSPLINE ? 6.0f : 1.0f; }
 template <int F>
-__device__ __forceinline__ int pick_positive(float t, float xi) {
+__device__ __forceinline__ int pick_positive_scaled(float t, float xs) {
     static_assert(F == F_LINEAR || F == F_BSPLINE, "positive filters only");
     if constexpr (F == F_LINEAR) {
-        return xi < __fsub_rn(1.0f, t) ? 0 : 1;
+        return xs < __fsub_rn(1.0f, t) ? 0 : 1;
     } else {
         const float s = __fsub_rn(1.0f, t);
         const float c0 = __fmul_rn(__fmul_rn(s, s), s);
         const float c1 = __fmaf_rn(__fmaf_rn(__fmaf_rn(2.0f, t, -3.0f), t, -3.0f), t, 5.0f);
         const float c2 = __fmaf_rn(-__fmul_rn(t, t), t, 6.0f);
-        const float x6 = __fmul_rn(xi, 6.0f);
-        return x6 < c0 ? 0 : (x6 < c1 ? 1 : (x6 < c2 ? 2 : 3));
+        return xs < c0 ? 0 : (xs < c1 ? 1 : (xs < c2 ? 2 : 3));
     }
+}
+template <int F>
+__device__ __forceinline__ int pick_positive(float t, float xi) {
+    return pick_positive_scaled<F>(t, F == F_BSPLINE ? __fmul_rn(xi, 6.0f) : xi);
 }
 
 // Sample reuse: the same pick, and the uniform remapped into the chosen interval,

@@ -77,6 +77,11 @@ struct TriplanarArgs {
 struct MarchArgs {
     const __half* vox;    // nz*ny*nx FP16
     int nx, ny, nz;
+    // the same voxels with a border of two replicated (clamped) voxels on every face: voxel
+    // (x, y, z), each coordinate in [-2, n + 1], at vpad[z * pxy + y * px + x]
+    const __half* vpad;
+    int px, pxy;
+    int fixed32;          // steps x (largest density) < 256: the 1-tap sum fits 32 bits
     float sigma_scale;
     float cam[12];
     uint32_t width, height, steps, spp, flags;
@@ -150,6 +155,12 @@ cudaError_t launch_triplanar(const TriplanarArgs& a, const TexView tv[3], cudaSt
 // null; with it, the tricubic N-tap marches stage each warp's voxels in shared memory by TMA.
 cudaError_t launch_march(const MarchArgs& a, const CUtensorMap* tmap, int num_sms, cudaStream_t st);
 bool encode_volume_tmap(CUtensorMap* out, const void* vox, int nx, int ny, int nz);
+// the clamped border copy: dst holds (nx + 4 rounded up to 8) x (ny + 4) x (nz + 4) voxels
+constexpr int VOL_PAD = 2;
+inline uint32_t vol_pad_pitch(uint32_t nx) { return (nx + 2 * VOL_PAD + 7u) & ~7u; }
+cudaError_t launch_pad_volume(const void* src, int nx, int ny, int nz, void* dst, cudaStream_t st);
+// the largest non-negative density of n FP16 voxels, as FP16 bits, into *out (device)
+cudaError_t launch_vol_max_bits(const void* vox, uint64_t n, unsigned int* out, cudaStream_t st);
 cudaError_t launch_bin_queries(uint64_t n, const float* u, const float* v, const uint32_t* tex_id, uint32_t ntex,
                                uint32_t tile_log2, uint32_t* order, uint32_t* scratch, uint64_t nbins,
                                cudaStream_t st);

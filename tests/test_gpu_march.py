@@ -60,6 +60,28 @@ def test_specialised_path_equals_general_path(ctx, small, filter, steps, flags):
     assert torch.equal(T1, T2)
 
 
+@pytest.mark.parametrize("scale,steps", [(16.0, 97), (1.0, 97), (1.9, 128), (2.0, 128)])
+@pytest.mark.parametrize("filter", ["linear", "bspline"])
+def test_density_sum_widths_and_odd_shapes(ctx, filter, scale, steps):
+    # The 1-tap march sums the picked densities as exact d * 2^24 fixed point, in 32 bits when
+    # steps x (largest density) < 256 and in 64 bits otherwise (scale 16 and 2 x 128 steps);
+    # either way it equals the general path bit for bit and the oracle within tolerance.  The
+    # volume is not a cube and its x size is no multiple of 8, so the bordered copy the 1-tap
+    # march reads has a padded row pitch.
+    base = synth.volume_cloud(24, 107, zero_frac=0.7, octaves=3, base=2)[:, :19, :13]
+    vol = np.ascontiguousarray((base.astype(np.float32) * scale).astype(np.float16))
+    h = ctx.create_volume(vol, 1.5)
+    cam = synth.camera_pinhole(W, H).as_array()
+    T1, pk = ctx.march_volume(h, cam, W, H, steps, filter, "stochastic", spp=2, seed=6, want_picks=True)
+    T2, _ = ctx.march_volume(h, cam, W, H, steps, filter, "stochastic", spp=2, seed=6)
+    torch.cuda.synchronize()
+    assert torch.equal(T1, T2)
+    ref = oracle.march(vol, 1.5, cam, W, H, steps, filter, "stochastic", spp=2, seed=6, want_picks=True)
+    mism = compare_picks(pk.cpu().numpy().view(np.uint32), ref, W * H)
+    assert_values(T1.cpu().numpy(), ref.T, mism)
+    ctx.destroy_volume(h)
+
+
 def test_stratified_and_pixel_ranges(ctx, small):
     h, vol = small
     cam = synth.camera_pinhole(W, H).as_array()
