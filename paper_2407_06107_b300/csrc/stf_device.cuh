@@ -352,9 +352,12 @@ __device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* 
     *total = acc;
     const float target = __fmul_rn(xi, acc);
     if constexpr (INNER_POS && N == 4) {
-        const bool h0 = target < c[0], h1 = target < c[1], h2 = target < c[2];
-        *neg = h0 ? (w[0] < 0.0f) : (!h2 && w[3] < 0.0f);
-        return h0 ? 0 : (h1 ? 1 : (h2 ? 2 : 3));
+        // binary search: the middle boundary first, then the one on its side; only the
+        // outer taps 0 and 3 carry a sign
+        const bool hi = target >= c[1];
+        const bool up = target >= (hi ? c[2] : c[0]);
+        *neg = hi ? (up && w[3] < 0.0f) : (!up && w[0] < 0.0f);
+        return (hi ? 2 : 0) + (up ? 1 : 0);
     }
     int k = N - 1;
     bool ng = w[N - 1] < 0.0f;
@@ -387,7 +390,9 @@ __device__ __forceinline__ int pick_positive_scaled(float t, float xs) {
         const float c0 = __fmul_rn(__fmul_rn(s, s), s);
         const float c1 = __fmaf_rn(__fmaf_rn(__fmaf_rn(2.0f, t, -3.0f), t, -3.0f), t, 5.0f);
         const float c2 = __fmaf_rn(-__fmul_rn(t, t), t, 6.0f);
-        return xs < c0 ? 0 : (xs < c1 ? 1 : (xs < c2 ? 2 : 3));
+        // binary search: the middle boundary first, then the one on its side
+        const bool hi = xs >= c1;
+        return (hi ? 2 : 0) + ((xs >= (hi ? c2 : c0)) ? 1 : 0);
     }
 }
 template <int F>
