@@ -352,12 +352,9 @@ __device__ __forceinline__ int cdf_pick_sign(const float w[4], float xi, float* 
     *total = acc;
     const float target = __fmul_rn(xi, acc);
     if constexpr (INNER_POS && N == 4) {
-        // binary search: the middle boundary first, then the one on its side; only the
-        // outer taps 0 and 3 carry a sign
-        const bool hi = target >= c[1];
-        const bool up = target >= (hi ? c[2] : c[0]);
-        *neg = hi ? (up && w[3] < 0.0f) : (!up && w[0] < 0.0f);
-        return (hi ? 2 : 0) + (up ? 1 : 0);
+        const bool h0 = target < c[0], h1 = target < c[1], h2 = target < c[2];
+        *neg = h0 ? (w[0] < 0.0f) : (!h2 && w[3] < 0.0f);
+        return h0 ? 0 : (h1 ? 1 : (h2 ? 2 : 3));
     }
     int k = N - 1;
     bool ng = w[N - 1] < 0.0f;
