@@ -62,7 +62,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 }
                 float x = u, y = v;
                 if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
-                const Pick1 p = pick_1tap<FILTER>(T, x, y, l0, fr, A, (flags & FLAG_REUSE) != 0);
+                const Pick1 p = pick_1tap<FILTER, TF>(T, x, y, l0, fr, A, (flags & FLAG_REUSE) != 0);
                 *wt = p.wt;
                 if (picks) {
                     uint32_t* pk = picks + (q * a.spp + s) * 2;
@@ -554,7 +554,7 @@ __device__ __forceinline__ Pending1<TF> pick_1spp(const FilterShadeArgs& a, cons
     const U5 A = uniforms5(philox((uint32_t)id, (uint32_t)(id >> 32), 0u, 0u, K));
     float x = u, y = v;
     if (a.has_derivs) jitter(0u, 1, 0u, A, dudx, dvdx, dudy, dvdy, &x, &y);
-    const Pick1 p = pick_1tap<FILTER>(T, x, y, l0, fr, A, false);
+    const Pick1 p = pick_1tap<FILTER, TF>(T, x, y, l0, fr, A, false);
     return {load_raw<TF>(T, p.lvl, p.ix, p.iy), p.wt};
 }
 

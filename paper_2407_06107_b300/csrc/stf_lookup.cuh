@@ -40,9 +40,22 @@ template <> struct RawOf<TF_RGBA8N> { using type = uint2; };
 // texel holds any value; the other formats decode to 0.05 + 0.95 x with x in [0, 1].
 template <int TF> constexpr bool clamp_rough() { return TF == TF_BASIC; }
 
-// the family a texture's kernels may use: RGBA8N for RGBA8 textures with a normal map
+// the family a texture's kernels may use: RGBA8N for RGBA8 textures with a normal map whose
+// levels all have power-of-two sides (wrap addressing is then a mask)
 inline int texture_family(const FetchCtx& T) {
-    return T.fmt == FMT_DCT ? TF_DCT : (T.fmt == FMT_RGBA8 && T.has_normal) ? TF_RGBA8N : TF_BASIC;
+    if (T.fmt == FMT_DCT) return TF_DCT;
+    if (T.fmt != FMT_RGBA8 || !T.has_normal) return TF_BASIC;
+    for (int l = 0; l < T.levels; ++l)
+        if ((T.w[l] & (T.w[l] - 1)) != 0 || (T.h[l] & (T.h[l] - 1)) != 0) return TF_BASIC;
+    return TF_RGBA8N;
+}
+
+// wrap addressing of index i on an axis of n texels: a mask for the RGBA8N family's
+// power-of-two levels, the general modulo otherwise
+template <int TF>
+__device__ __forceinline__ int wrap_t(int i, int n) {
+    if constexpr (TF == TF_RGBA8N) return i & (n - 1);
+    else return wrap_index(i, n);
 }
 
 template <int TF>
@@ -115,7 +128,7 @@ __device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, co
 // stochastic-sum).  reuse: one uniform drives the level and both axes, remapped per decision.
 struct Pick1 { int lvl, ix, iy; float wt; };
 
-template <int FILTER>
+template <int FILTER, int TF = TF_BASIC>
 __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, int l0, float fr, const U5& A,
                                            bool reuse) {
     constexpr int NT = ntaps(FILTER), T0 = tap0(FILTER);
@@ -134,8 +147,8 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
     p.wt = 1.0f;
     if constexpr (!is_signed(FILTER)) {
         if (!reuse) {   // a positive filter's pick needs no weights: its CDF in closed form
-            p.ix = wrap_index(ax.i0 + T0 + pick_positive<FILTER>(ax.t, A.u[3]), W);
-            p.iy = wrap_index(ay.i0 + T0 + pick_positive<FILTER>(ay.t, A.u[4]), H);
+            p.ix = wrap_t<TF>(ax.i0 + T0 + pick_positive<FILTER>(ax.t, A.u[3]), W);
+            p.iy = wrap_t<TF>(ay.i0 + T0 + pick_positive<FILTER>(ay.t, A.u[4]), H);
             return p;
         }
     }
@@ -165,8 +178,8 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
         kx = cdf_pick<NT>(wx, A.u[3], 0, &Sx);
         ky = cdf_pick<NT>(wy, A.u[4], 0, &Sy);
     }
-    p.ix = wrap_index(ax.i0 + T0 + kx, W);
-    p.iy = wrap_index(ay.i0 + T0 + ky, H);
+    p.ix = wrap_t<TF>(ax.i0 + T0 + kx, W);
+    p.iy = wrap_t<TF>(ay.i0 + T0 + ky, H);
     if (is_signed(FILTER)) {
         p.wt = Sx * Sy;
         if (nx != ny) p.wt = -p.wt;
@@ -197,7 +210,7 @@ __device__ __forceinline__ float3 positivized_sample(const FetchCtx& T, float x,
     const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
     const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
     const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
-    const int ix = wrap_index(ax.i0 + T0 + kx, W), iy = wrap_index(ay.i0 + T0 + ky, H);
+    const int ix = wrap_t<TF>(ax.i0 + T0 + kx, W), iy = wrap_t<TF>(ay.i0 + T0 + ky, H);
     const typename RawOf<TF>::type raw_p = load_raw<TF>(T, lvl, ix, iy);
     uint32_t negpick = NO_PICK;
     typename RawOf<TF>::type raw_n{};
@@ -205,7 +218,7 @@ __device__ __forceinline__ float3 positivized_sample(const FetchCtx& T, float x,
         const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
         const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
         const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
-        const int jx = wrap_index(ax.i0 + T0 + qx, W), jy = wrap_index(ay.i0 + T0 + qy, H);
+        const int jx = wrap_t<TF>(ax.i0 + T0 + qx, W), jy = wrap_t<TF>(ay.i0 + T0 + qy, H);
         raw_n = load_raw<TF>(T, lvl, jx, jy);
         negpick = pack_pick(lvl, jx, jy);
     }
@@ -242,8 +255,8 @@ __device__ __forceinline__ void ntap_accumulate(const FetchCtx& T, float x, floa
         axis_weights<FILTER>(ay.t, wy);
         // the window's wrapped columns and rows: one full wrap per axis, then +1 steps
         int cx[4], ry[4];
-        cx[0] = wrap_index(ax.i0 + T0, W);
-        ry[0] = wrap_index(ay.i0 + T0, H);
+        cx[0] = wrap_t<TF>(ax.i0 + T0, W);
+        ry[0] = wrap_t<TF>(ay.i0 + T0, H);
 #pragma unroll
         for (int k = 1; k < NT; ++k) {
             cx[k] = cx[k - 1] + 1 == W ? 0 : cx[k - 1] + 1;

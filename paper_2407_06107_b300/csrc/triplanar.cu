@@ -65,7 +65,7 @@ __device__ __forceinline__ float3 plane_sample(const FetchCtx& T, const PlaneQ& 
     float x = p.u, y = p.v;
     if (has_d) jitter(s, kside, flags, A, p.dudx, p.dvdx, p.dudy, p.dvdy, &x, &y);
     if constexpr (MODE == M_STOCHASTIC) {
-        const Pick1 k = pick_1tap<FILTER>(T, x, y, p.l0, p.fr, A, false);
+        const Pick1 k = pick_1tap<FILTER, TF>(T, x, y, p.l0, p.fr, A, false);
         const float3 f = shade<clamp_rough<TF>()>(shade_mode, fetch_t<TF>(T, k.lvl, k.ix, k.iy), SC);
         if (pk) { pk[0] = pack_pick(k.lvl, k.ix, k.iy); pk[1] = NO_PICK; }
         const float w = scale * k.wt;
@@ -210,7 +210,7 @@ __device__ __forceinline__ TriPick<TF> tri_pick_1spp(const TriplanarArgs& a, con
     const PlaneQ p = plane_query(r.plane, P, DX, DY, has_d, a.scale, T, 0u);
     float x = p.u, y = p.v;
     if (has_d) jitter(0u, 1, 0u, A, p.dudx, p.dvdx, p.dudy, p.dvdy, &x, &y);
-    const Pick1 k = pick_1tap<FILTER>(T, x, y, p.l0, p.fr, A, false);
+    const Pick1 k = pick_1tap<FILTER, TF>(T, x, y, p.l0, p.fr, A, false);
     r.raw = load_raw<TF>(T, k.lvl, k.ix, k.iy);
     r.wt = k.wt;
     return r;
