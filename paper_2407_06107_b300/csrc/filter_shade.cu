@@ -60,8 +60,9 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
 #pragma unroll
                     for (int k = 2; k < 5; ++k) A.u[k] = lattice(LA.f[k], lshift, 24);
                 }
+                // without derivatives they are 0 and the jitter leaves (u, v) as it is
                 float x = u, y = v;
-                if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
+                jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
                 const Pick1 p = pick_1tap<FILTER, TF>(T, x, y, l0, fr, A, (flags & FLAG_REUSE) != 0);
                 *wt = p.wt;
                 if (picks) {
@@ -73,15 +74,19 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             };
             float wt_next;
             typename RawOf<TF>::type raw_next = pick(0, &wt_next);
-            for (uint32_t s = 0; s < a.spp; ++s) {
-                const typename RawOf<TF>::type raw = raw_next;
-                const float Wt = wt_next;
-                if (s + 1 < a.spp) raw_next = pick(s + 1, &wt_next);
+            auto add = [&](const typename RawOf<TF>::type& raw, float Wt) {
                 const float3 f = shade<clamp_rough<TF>()>(a.shade, decode_raw<TF>(T, raw), SC);
                 acc.x = __fmaf_rn(Wt, f.x, acc.x);
                 acc.y = __fmaf_rn(Wt, f.y, acc.y);
                 acc.z = __fmaf_rn(Wt, f.z, acc.z);
+            };
+            for (uint32_t s = 0; s + 1 < a.spp; ++s) {
+                const typename RawOf<TF>::type raw = raw_next;
+                const float Wt = wt_next;
+                raw_next = pick(s + 1, &wt_next);
+                add(raw, Wt);
             }
+            add(raw_next, wt_next);
         } else
         for (uint32_t s = 0; s < a.spp; ++s) {
             U5 A = uniforms5(R0(s, K));
@@ -552,8 +557,8 @@ __device__ __forceinline__ Pending1<TF> pick_1spp(const FilterShadeArgs& a, cons
     const float fr = __fsub_rn(lam, (float)l0);
     const uint64_t id = a.id_base + q;
     const U5 A = uniforms5(philox((uint32_t)id, (uint32_t)(id >> 32), 0u, 0u, K));
-    float x = u, y = v;
-    if (a.has_derivs) jitter(0u, 1, 0u, A, dudx, dvdx, dudy, dvdy, &x, &y);
+    float x = u, y = v;     // without derivatives they are 0 and the jitter leaves (u, v) as it is
+    jitter(0u, 1, 0u, A, dudx, dvdx, dudy, dvdy, &x, &y);
     const Pick1 p = pick_1tap<FILTER, TF>(T, x, y, l0, fr, A, false);
     return {load_raw<TF>(T, p.lvl, p.ix, p.iy), p.wt};
 }
