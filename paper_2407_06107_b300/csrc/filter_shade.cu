@@ -80,13 +80,24 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
                 acc.y = __fmaf_rn(Wt, f.y, acc.y);
                 acc.z = __fmaf_rn(Wt, f.z, acc.z);
             };
-            for (uint32_t s = 0; s + 1 < a.spp; ++s) {
-                const typename RawOf<TF>::type raw = raw_next;
-                const float Wt = wt_next;
-                raw_next = pick(s + 1, &wt_next);
-                add(raw, Wt);
+            if constexpr (TF == TF_RGBA8N) {
+                // the last sample's shade peeled off: no per-sample test for a next sample
+                for (uint32_t s = 0; s + 1 < a.spp; ++s) {
+                    const typename RawOf<TF>::type raw = raw_next;
+                    const float Wt = wt_next;
+                    raw_next = pick(s + 1, &wt_next);
+                    add(raw, Wt);
+                }
+                add(raw_next, wt_next);
+            } else {
+                // one copy of the shade (fewer registers for the other families and the table)
+                for (uint32_t s = 0; s < a.spp; ++s) {
+                    const typename RawOf<TF>::type raw = raw_next;
+                    const float Wt = wt_next;
+                    if (s + 1 < a.spp) raw_next = pick(s + 1, &wt_next);
+                    add(raw, Wt);
+                }
             }
-            add(raw_next, wt_next);
         } else
         for (uint32_t s = 0; s < a.spp; ++s) {
             U5 A = uniforms5(R0(s, K));
