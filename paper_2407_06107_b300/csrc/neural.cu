@@ -107,7 +107,10 @@ __device__ __forceinline__ LTap latent_taps(const NeuralView& N, int g, int ix, 
     const float ux = __fsub_rn(1.0f, tx), uy = __fsub_rn(1.0f, ty);
     LTap t;
     const int R = N.res[g];
-    t.x0 = wrap_index((int)fx, R); t.y0 = wrap_index((int)fy, R);
+    // ix, iy lie in [0, tex_res), so p lies in [-1/2, R - 1/2) and floor(p) in [-1, R - 1]: the
+    // wrap is -1 -> R - 1 alone, a select
+    const int ix0 = (int)fx, iy0 = (int)fy;
+    t.x0 = ix0 < 0 ? R - 1 : ix0; t.y0 = iy0 < 0 ? R - 1 : iy0;
     t.x1 = t.x0 + 1 == R ? 0 : t.x0 + 1;     // the next texel, wrapped
     t.y1 = t.y0 + 1 == R ? 0 : t.y0 + 1;
     t.w00 = __fmul_rn(ux, uy); t.w10 = __fmul_rn(tx, uy); t.w01 = __fmul_rn(ux, ty); t.w11 = __fmul_rn(tx, ty);
@@ -470,7 +473,9 @@ __global__ void __launch_bounds__(NT_ROWS, DEC_CTAS_PER_SM) k_ntc_decode_tc(Neur
         float w = 0.0f;
         if (row < nrows) {
             if constexpr (MODE < 0) {
-                ix = a.ex_ix[row]; iy = a.ex_iy[row]; pr = (long long)row; w = 1.0f;
+                // explicit texels wrap into [0, tex_res) (latent_taps relies on that range)
+                ix = wrap_index(a.ex_ix[row], a.tex_res); iy = wrap_index(a.ex_iy[row], a.tex_res);
+                pr = (long long)row; w = 1.0f;
             } else {
                 const RowOut r = make_row<FILTER, MODE>(a, K, row);
                 ix = r.ix; iy = r.iy; pr = r.query; w = r.w;
@@ -1165,7 +1170,9 @@ k_ntc_train_ws(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint
             int ix = 0, iy = 0;
             uint2 tgt = make_uint2(0u, 0u);     // the sample's 8 target channels (bytes)
             if (live) {
-                if (use_explicit) { ix = ex_ix[k]; iy = ex_iy[k]; }
+                if (use_explicit) {   // wrapped into [0, tex_res), the range latent_taps relies on
+                    ix = wrap_index(ex_ix[k], (int)N.tex_res); iy = wrap_index(ex_iy[k], (int)N.tex_res);
+                }
                 else {
                     const uint4 w = philox(k, step, 0u, 0x4E54u, K);
                     ix = (int)__umulhi(w.x, (uint32_t)N.tex_res);
