@@ -118,6 +118,17 @@ def test_decode_fp16_matches_oracle(ctx, net, data):
     _check_decode(ctx, net, oracle.NeuralTexture.inference_form(R0, lat, mlp, "fp16"))
 
 
+def test_explicit_texels_wrap(ctx, net):
+    # explicit texel coordinates outside [0, R0) wrap into it: the decode of (x + k R0, y - m R0)
+    # is the decode of (x, y), bit for bit
+    ix, iy = _all_texels()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+    y0 = ctx.neural_decode(net, dev(ix), dev(iy))
+    k = np.random.default_rng(3).integers(-3, 4, (2, ix.size))
+    y1 = ctx.neural_decode(net, dev(ix + k[0] * R0), dev(iy - k[1] * R0))
+    assert torch.equal(y0, y1)
+
+
 def test_decode_fp8_matches_oracle(ctx, net, data):
     lat, mlp, _ = data
     ctx.neural_quantize(net, "fp8")
