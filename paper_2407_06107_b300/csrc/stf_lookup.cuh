@@ -147,8 +147,15 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
     p.wt = 1.0f;
     if constexpr (!is_signed(FILTER)) {
         if (!reuse) {   // a positive filter's pick needs no weights: its CDF in closed form
-            p.ix = wrap_t<TF>(ax.i0 + T0 + pick_positive<FILTER>(ax.t, A.u[3]), W);
-            p.iy = wrap_t<TF>(ay.i0 + T0 + pick_positive<FILTER>(ay.t, A.u[4]), H);
+            int kx, ky;
+            if constexpr (TF == TF_RGBA8N) {
+                pick_positive2<FILTER>(ax.t, ay.t, A.u[3], A.u[4], &kx, &ky);
+            } else {
+                kx = pick_positive<FILTER>(ax.t, A.u[3]);
+                ky = pick_positive<FILTER>(ay.t, A.u[4]);
+            }
+            p.ix = wrap_t<TF>(ax.i0 + T0 + kx, W);
+            p.iy = wrap_t<TF>(ay.i0 + T0 + ky, H);
             return p;
         }
     }
