@@ -417,6 +417,30 @@ __device__ __forceinline__ void pick_positive2(float tx, float ty, float xi_x, f
     }
 }
 
+// Positivization's per-axis sums and picks for a 4-tap filter whose inner taps are positive
+// (Keys, Mitchell-Netravali): the positive class is {tap 0 if w0 > 0, 1, 2, tap 3 if w3 > 0},
+// the negative class {tap 0 if w0 < 0, tap 3 if w3 < 0}.  The prefix sums are cdf_pick's for
+// classes +1 and -1, in the same order (a skipped tap adds an exact zero), so the sums and the
+// picks equal cdf_pick's.
+struct SignedAxis4 { float c0, c1, c2, P, n0, N; };
+__device__ __forceinline__ SignedAxis4 signed_axis4(const float w[4]) {
+    SignedAxis4 a;
+    a.c0 = w[0] > 0.0f ? w[0] : 0.0f;
+    a.c1 = __fadd_rn(a.c0, w[1]);
+    a.c2 = __fadd_rn(a.c1, w[2]);
+    a.P = __fadd_rn(a.c2, w[3] > 0.0f ? w[3] : 0.0f);
+    a.n0 = w[0] < 0.0f ? -w[0] : 0.0f;
+    a.N = __fadd_rn(a.n0, w[3] < 0.0f ? -w[3] : 0.0f);
+    return a;
+}
+// the tap of class cls (+1 or -1) for the uniform xi
+__device__ __forceinline__ int signed_pick4(const SignedAxis4& a, float xi, int cls) {
+    const float tp = __fmul_rn(xi, a.P), tn = __fmul_rn(xi, a.N);
+    const int kp = tp < a.c0 ? 0 : (tp < a.c1 ? 1 : (tp < a.c2 ? 2 : 3));
+    const int kn = tn < a.n0 ? 0 : 3;
+    return cls > 0 ? kp : kn;
+}
+
 // Sample reuse: the same pick, and the uniform remapped into the chosen interval,
 // u' = (xi S - C_{k-1}) / (C_k - C_{k-1}) (Eq. uniform-sample-reuse on a sampling array).
 template <int N>

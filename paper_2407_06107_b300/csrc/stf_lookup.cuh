@@ -209,22 +209,35 @@ __device__ __forceinline__ float3 positivized_sample(const FetchCtx& T, float x,
     float wx[4], wy[4];
     axis_weights<FILTER>(ax.t, wx);
     axis_weights<FILTER>(ay.t, wy);
+    // the 4-tap signed filters' class sums and picks from their sign structure (signed_axis4),
+    // the others' from the class CDFs; the values are the same either way
+    constexpr bool S4 = NT == 4 && is_signed(FILTER);
+    SignedAxis4 sx{}, sy{};
     float Px, Nx, Py, Ny;
-    cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
-    cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
+    if constexpr (S4) {
+        sx = signed_axis4(wx); sy = signed_axis4(wy);
+        Px = sx.P; Nx = sx.N; Py = sy.P; Ny = sy.N;
+    } else {
+        cdf_pick<NT>(wx, 0.0f, +1, &Px); cdf_pick<NT>(wx, 0.0f, -1, &Nx);
+        cdf_pick<NT>(wy, 0.0f, +1, &Py); cdf_pick<NT>(wy, 0.0f, -1, &Ny);
+    }
+    auto pick = [&](const float w[4], const SignedAxis4& sa, float xi, int cls) {
+        if constexpr (S4) return signed_pick4(sa, xi, cls);
+        else return cdf_pick<NT>(w, xi, cls, nullptr);
+    };
     const float Wp = __fmaf_rn(Nx, Ny, __fmul_rn(Px, Py));
     const float Wn = __fmaf_rn(Nx, Py, __fmul_rn(Px, Ny));
     const int cp = (__fmul_rn(B.u[0], Wp) < __fmul_rn(Px, Py)) ? +1 : -1;
-    const int kx = cdf_pick<NT>(wx, A.u[3], cp, nullptr);
-    const int ky = cdf_pick<NT>(wy, A.u[4], cp, nullptr);
+    const int kx = pick(wx, sx, A.u[3], cp);
+    const int ky = pick(wy, sy, A.u[4], cp);
     const int ix = wrap_t<TF>(ax.i0 + T0 + kx, W), iy = wrap_t<TF>(ay.i0 + T0 + ky, H);
     const typename RawOf<TF>::type raw_p = load_raw<TF>(T, lvl, ix, iy);
     uint32_t negpick = NO_PICK;
     typename RawOf<TF>::type raw_n{};
     if (Wn > 0.0f) {
         const int cn = (__fmul_rn(B.u[3], Wn) < __fmul_rn(Px, Ny)) ? +1 : -1;
-        const int qx = cdf_pick<NT>(wx, B.u[1], cn, nullptr);
-        const int qy = cdf_pick<NT>(wy, B.u[2], -cn, nullptr);
+        const int qx = pick(wx, sx, B.u[1], cn);
+        const int qy = pick(wy, sy, B.u[2], -cn);
         const int jx = wrap_t<TF>(ax.i0 + T0 + qx, W), jy = wrap_t<TF>(ay.i0 + T0 + qy, H);
         raw_n = load_raw<TF>(T, lvl, jx, jy);
         negpick = pack_pick(lvl, jx, jy);
