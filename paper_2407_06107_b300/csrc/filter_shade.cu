@@ -48,8 +48,9 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             if (MODE == M_POSITIVIZED) LB = ints5(philox(id_lo, id_hi, 0xFFFFFFFFu, 1u, K));
         }
 
-        // stream 0 of the query: (jitter x, jitter y, level, pick x, pick y) per sample
-        const PhiloxS R0(id_lo, id_hi, 0u, K);
+        // stream 0 of the query: (jitter x, jitter y, level, pick x, pick y) per sample;
+        // stream 1 (positivization): (positive class, negative pick x, negative pick y, negative class)
+        const PhiloxS R0(id_lo, id_hi, 0u, K), R1(id_lo, id_hi, 1u, K);
         if constexpr (MODE == M_STOCHASTIC) {
             // Software-pipelined: sample s+1 is picked and its texel load issued before
             // sample s is decoded and shaded, so the gather latency hides behind shading.
@@ -110,8 +111,7 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             if (a.has_derivs) jitter(s, kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
             float3 est;
             if (MODE == M_POSITIVIZED) {
-                // stream 1: (positive class, negative pick x, negative pick y, negative class)
-                U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                U5 B = uniforms5(R1(s, K));
                 if (lat) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) B.u[k] = lattice(LB.f[k], lshift, 24);
@@ -248,10 +248,11 @@ __device__ __forceinline__ void ewa_query(const FilterShadeArgs& a, const FetchC
     const uint64_t id = a.id_base + q;
     const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
     float3 acc = make_float3(0.f, 0.f, 0.f);
+    const PhiloxS R0(id_lo, id_hi, 0u, K);
     for (uint32_t s = 0; s < a.spp; ++s) {
         float3 est = make_float3(0.f, 0.f, 0.f);
         if constexpr (MODE == M_STOCHASTIC) {
-            const U5 A5 = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+            const U5 A5 = uniforms5(R0(s, K));
             const int lvl = min(l0 + ((A5.u[2] < fr) ? 1 : 0), T.levels - 1);
             const int W = T.w[lvl], H = T.h[lvl];
             const EwaBox e = ewa_setup(u, v, dudx, dvdx, dudy, dvdy, W, H);
@@ -397,8 +398,9 @@ __device__ __forceinline__ void gauss_query(const FilterShadeArgs& a, const Fetc
     const uint64_t id = a.id_base + q;
     const uint32_t id_lo = (uint32_t)id, id_hi = (uint32_t)(id >> 32);
     float3 acc = make_float3(0.f, 0.f, 0.f);
+    const PhiloxS R0(id_lo, id_hi, 0u, K), R1(id_lo, id_hi, 1u, K);
     for (uint32_t s = 0; s < a.spp; ++s) {
-        const U5 A = uniforms5(philox(id_lo, id_hi, s, 0u, K));
+        const U5 A = uniforms5(R0(s, K));
         float x = u, y = v;
         if (a.has_derivs) jitter(s, a.kside, flags, A, dudx, dvdx, dudy, dvdy, &x, &y);
         float3 est = make_float3(0.f, 0.f, 0.f);
@@ -423,7 +425,7 @@ __device__ __forceinline__ void gauss_query(const FilterShadeArgs& a, const Fetc
                     ox = __fsub_rn(A.u[3], 0.5f);
                     oy = __fsub_rn(A.u[4], 0.5f);
                 } else if constexpr (FILTER == F_FIS_BSPLINE) {
-                    const U5 B = uniforms5(philox(id_lo, id_hi, s, 1u, K));
+                    const U5 B = uniforms5(R1(s, K));
                     ox = __fsub_rn(__fadd_rn(__fadd_rn(A.u[3], B.u[0]), B.u[1]), 1.5f);
                     oy = __fsub_rn(__fadd_rn(__fadd_rn(A.u[4], B.u[2]), B.u[3]), 1.5f);
                 } else {
