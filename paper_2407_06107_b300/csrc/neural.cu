@@ -625,16 +625,18 @@ static_assert(sizeof(DecWsSmem) * WS_CTAS_PER_SM + 3 * 1024 <= 228 * 1024, "thre
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait that also gives up once any role has given up.
+// Bounded wait that also gives up once any role has given up.  The abort flag and the clock
+// are read on every 8th poll only, so a waiting warp spends fewer issue slots polling.
 __device__ __forceinline__ bool ws_wait1(volatile int* abort_flag, uint64_t* bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort_flag || clock64() - t0 > limit) {
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 7u) == 0u && (*abort_flag || clock64() - t0 > limit)) {
             *abort_flag = 1;
             return false;
         }
     }
-    return true;
 }
 // The same for a whole warp: every lane waits, and the decision is the warp's (__all_sync), so
 // a warp whose lanes then run collective instructions (TMEM loads, shuffles) never leaves a
