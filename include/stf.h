@@ -335,7 +335,12 @@ stf_status stf_filter_shade_host_noalloc(stf_ctx ctx, stf_tex tex, const stf_que
                                          uint64_t seed, uint32_t flags, const stf_output* out);
 
 /* ---- 3-D volume march (Sec. 5 "Offline rendering", transmittance exp(-sigma dt)) ------- */
-/* data: nz*ny*nx FP16 densities (x fastest); sigma = sigma_scale * density. */
+/* data: nz*ny*nx FP16 densities (x fastest); sigma = sigma_scale * density.  The library keeps
+ * two device copies: the grid itself (read by the N-tap marches and the TMA-staged comparator)
+ * and a copy with a clamped two-voxel border on every face, rows padded to a multiple of 8
+ * voxels, which the 1-tap march reads without clamping its picks (about 2.1x the grid's bytes in
+ * all).  It also records the grid's largest density: where steps x that maximum is below 256,
+ * the 1-tap march sums its fixed-point densities in 32 bits.  Synchronises the context stream. */
 stf_status stf_create_volume(stf_ctx ctx, uint32_t nx, uint32_t ny, uint32_t nz, stf_format format,
                              float sigma_scale, const void* data, int data_on_device, stf_vol* out);
 stf_status stf_destroy_volume(stf_ctx ctx, stf_vol vol);
