@@ -103,10 +103,17 @@ __global__ void __launch_bounds__(128, march_min_blocks<MODE, V>()) k_march(Marc
                 auto voxel = [&](float kh, const float uk[3]) -> int {
                     const float tk = __fmaf_rn(kh, dt, tmin);
                     int idx[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const AxisPos ap = axis_pos(__fmaf_rn(tk, d[c], e[c]), res[c]);
-                        idx[c] = ap.i0 + T0 + pick_positive_scaled<FILTER>(ap.t, uk[c]);
+                    {   // x and y in packed FP32 pairs (one rounding per lane, as axis_pos), z alone
+                        const float2 p = upk2(vfma(vfma(f2(tk), f2(d[0], d[1]), f2(e[0], e[1])),
+                                                   f2(res[0], res[1]), vconst<F2>(-0.5f)).v);
+                        const float fx = floorf(p.x), fy = floorf(p.y);
+                        const F2 t = vsub(f2(p.x, p.y), f2(fx, fy));
+                        int kx, ky;
+                        pick_positive2_scaled<FILTER>(t, uk[0], uk[1], &kx, &ky);
+                        idx[0] = (int)fx + T0 + kx;
+                        idx[1] = (int)fy + T0 + ky;
+                        const AxisPos ap = axis_pos(__fmaf_rn(tk, d[2], e[2]), res[2]);
+                        idx[2] = ap.i0 + T0 + pick_positive_scaled<FILTER>(ap.t, uk[2]);
                     }
                     // A sample point lies inside the box, so a picked index is in [-2, n + 1] and
                     // the bordered copy holds its clamped voxel: no clamping here.  At most

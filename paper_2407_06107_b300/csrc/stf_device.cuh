@@ -397,23 +397,33 @@ __device__ __forceinline__ int pick_positive(float t, float xi) {
     return pick_positive_scaled<F>(t, F == F_BSPLINE ? __fmul_rn(xi, 6.0f) : xi);
 }
 // The same for two axes at once (x, y), the B-spline boundaries in packed FP32 pairs (one
-// rounding per lane: the values equal pick_positive's)
+// rounding per lane: the values equal pick_positive's); the _scaled form takes pre-scaled
+// uniforms as pick_positive_scaled does
+template <int F>
+__device__ __forceinline__ void pick_positive2_scaled(F2 t, float xs_x, float xs_y, int* kx, int* ky) {
+    if constexpr (F == F_LINEAR) {
+        const float2 tt = upk2(t.v);
+        *kx = pick_positive_scaled<F>(tt.x, xs_x);
+        *ky = pick_positive_scaled<F>(tt.y, xs_y);
+    } else {
+        const F2 s = vsub(vconst<F2>(1.0f), t);
+        const float2 c0 = upk2(vmul(vmul(s, s), s).v);
+        const float2 c1 = upk2(vfma(vfma(vfma(vconst<F2>(2.0f), t, vconst<F2>(-3.0f)), t, vconst<F2>(-3.0f)), t,
+                                    vconst<F2>(5.0f)).v);
+        const float2 c2 = upk2(vfma(vmul(vmul(t, t), vconst<F2>(-1.0f)), t, vconst<F2>(6.0f)).v);
+        const bool hx = xs_x >= c1.x, hy = xs_y >= c1.y;
+        *kx = (hx ? 2 : 0) + ((xs_x >= (hx ? c2.x : c0.x)) ? 1 : 0);
+        *ky = (hy ? 2 : 0) + ((xs_y >= (hy ? c2.y : c0.y)) ? 1 : 0);
+    }
+}
 template <int F>
 __device__ __forceinline__ void pick_positive2(float tx, float ty, float xi_x, float xi_y, int* kx, int* ky) {
     if constexpr (F == F_LINEAR) {
         *kx = pick_positive<F>(tx, xi_x);
         *ky = pick_positive<F>(ty, xi_y);
     } else {
-        const F2 t = f2(tx, ty);
-        const F2 s = vsub(vconst<F2>(1.0f), t);
-        const float2 c0 = upk2(vmul(vmul(s, s), s).v);
-        const float2 c1 = upk2(vfma(vfma(vfma(vconst<F2>(2.0f), t, vconst<F2>(-3.0f)), t, vconst<F2>(-3.0f)), t,
-                                    vconst<F2>(5.0f)).v);
-        const float2 c2 = upk2(vfma(vmul(vmul(t, t), vconst<F2>(-1.0f)), t, vconst<F2>(6.0f)).v);
         const float2 xs = upk2(vmul(f2(xi_x, xi_y), vconst<F2>(6.0f)).v);
-        const bool hx = xs.x >= c1.x, hy = xs.y >= c1.y;
-        *kx = (hx ? 2 : 0) + ((xs.x >= (hx ? c2.x : c0.x)) ? 1 : 0);
-        *ky = (hy ? 2 : 0) + ((xs.y >= (hy ? c2.y : c0.y)) ? 1 : 0);
+        pick_positive2_scaled<F>(f2(tx, ty), xs.x, xs.y, kx, ky);
     }
 }
 
