@@ -118,6 +118,16 @@ __device__ __forceinline__ void jitter(uint32_t s, int kside, uint32_t flags, co
 }
 
 
+// Both axes' raster positions at once in packed FP32 pairs: the same values as axis_pos on x
+// and on y (one rounding per lane)
+__device__ __forceinline__ void axis_pos2(float x, float y, float W, float H, AxisPos* ax, AxisPos* ay) {
+    const float2 p = upk2(vfma(f2(x, y), f2(W, H), vconst<F2>(-0.5f)).v);
+    const float fx = floorf(p.x), fy = floorf(p.y);
+    const float2 t = upk2(vsub(f2(p.x, p.y), f2(fx, fy)).v);
+    *ax = {(int)fx, t.x};
+    *ay = {(int)fy, t.y};
+}
+
 // ---------------------------------------------------------------- per-sample filters
 // Each takes the (jittered) position (x, y) in texture coordinates, the query's level floor
 // l0 and fraction fr, and the sample's uniforms.
@@ -141,7 +151,13 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
     }
     lvl = min(lvl, T.levels - 1);
     const int W = T.w[lvl], H = T.h[lvl];
-    const AxisPos ax = axis_pos(x, (float)W), ay = axis_pos(y, (float)H);
+    AxisPos ax, ay;
+    if constexpr (TF == TF_RGBA8N && !is_signed(FILTER)) {   // packed: faster for the positive filters
+        axis_pos2(x, y, (float)W, (float)H, &ax, &ay);
+    } else {
+        ax = axis_pos(x, (float)W);
+        ay = axis_pos(y, (float)H);
+    }
     Pick1 p;
     p.lvl = lvl;
     p.wt = 1.0f;
