@@ -405,7 +405,8 @@ __device__ __forceinline__ RowOut make_row(const NeuralDecodeArgs& a, const Roun
             const int kx = cdf_pick_sign<NT, true>(wx, A.u[3], &Sx, &nx);
             const int ky = cdf_pick_sign<NT, true>(wy, A.u[4], &Sy, &ny);
             o.ix = wrap_index(ax.i0 + T0 + kx, R); o.iy = wrap_index(ay.i0 + T0 + ky, R);
-            const float W = __fmul_rn(__fmul_rn(Sx, Sy), pick_weight_scale<FILTER>());
+            float W = Sx * Sy;
+            if constexpr (pick_weight_scale<FILTER>() != 1.0f) W = __fmul_rn(W, pick_weight_scale<FILTER>());
             o.w = (nx != ny) ? -W : W;
         } else {   // a positive filter: the CDF in closed form, weight 1
             o.ix = wrap_index(ax.i0 + T0 + pick_positive<FILTER>(ax.t, A.u[3]), R);

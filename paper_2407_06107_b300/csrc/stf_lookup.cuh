@@ -204,7 +204,8 @@ __device__ __forceinline__ Pick1 pick_1tap(const FetchCtx& T, float x, float y, 
     p.ix = wrap_t<TF>(ax.i0 + T0 + kx, W);
     p.iy = wrap_t<TF>(ay.i0 + T0 + ky, H);
     if (is_signed(FILTER)) {
-        p.wt = __fmul_rn(__fmul_rn(Sx, Sy), pick_weight_scale<FILTER>());
+        p.wt = Sx * Sy;
+        if constexpr (pick_weight_scale<FILTER>() != 1.0f) p.wt = __fmul_rn(p.wt, pick_weight_scale<FILTER>());
         if (nx != ny) p.wt = -p.wt;
     }
     return p;
