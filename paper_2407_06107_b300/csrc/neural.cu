@@ -79,6 +79,25 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
+// The same two, executed by a whole warp: elect.sync picks one lane (the lowest, the same on
+// every call with the full mask) to issue, so the warp's control flow and operands stay uniform.
+__device__ __forceinline__ void mma_bf16_warp(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_warp(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+        ::"r"(smem_u32(bar))
+        : "memory");
+}
 // 16 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
@@ -627,6 +646,7 @@ static_assert(sizeof(DecWsSmem) * WS_CTAS_PER_SM + 3 * 1024 <= 228 * 1024, "thre
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+
 // Bounded wait that also gives up once any role has given up.  The abort flag and the clock
 // are read on every 8th poll only, so a waiting warp spends fewer issue slots polling.
 __device__ __forceinline__ bool ws_wait1(volatile int* abort_flag, uint64_t* bar, uint32_t parity, long long limit) {
@@ -726,47 +746,47 @@ k_ntc_decode_ws(NeuralView N, NeuralDecodeArgs a, RoundKeys K) {
         }
     } else if (warp == 8) {
         // ---------------------------------------------------------------- MMA issue
-        if (lane == 0) {
-            const uint32_t w1 = smem_u32(S.W1), w2 = smem_u32(S.W2), w3 = smem_u32(S.W3), h = smem_u32(S.H);
-            constexpr uint32_t SB1 = (WS_K1 / 8) * 128, SB2 = (WS_K2 / 8) * 128;
-            for (uint64_t i = 0;; ++i) {
-                const uint64_t tile = blockIdx.x + i * gridDim.x;
-                if (tile >= ntiles) break;
-                const int b = (int)(i & 1);
-                if (!ws_wait1(&S.abort_flag, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
-                tc_fence_after();
-                if (!a.inject_timeout) {
-                    const uint32_t aa = smem_u32(S.A[b]);
+        // The whole warp runs the loop and the waits, with warp-uniform control flow and
+        // operands; one elected lane (the same every time) issues the MMAs and their commits.
+        const uint32_t w1 = smem_u32(S.W1), w2 = smem_u32(S.W2), w3 = smem_u32(S.W3), h = smem_u32(S.H);
+        constexpr uint32_t SB1 = (WS_K1 / 8) * 128, SB2 = (WS_K2 / 8) * 128;
+        for (uint64_t i = 0;; ++i) {
+            const uint64_t tile = blockIdx.x + i * gridDim.x;
+            if (tile >= ntiles) break;
+            const int b = (int)(i & 1);
+            if (!ws_wait(&S.abort_flag, &S.full_a[b], (uint32_t)((i >> 1) & 1), limit)) break;
+            tc_fence_after();
+            if (!a.inject_timeout) {
+                const uint32_t aa = smem_u32(S.A[b]);
 #pragma unroll
-                    for (int s = 0; s < WS_K1 / 16; ++s)
-                        mma_bf16(tmem, smem_desc(aa + 256 * s, 128, SB1), smem_desc(w1 + 256 * s, 128, SB1),
-                                 idesc_bf16(128, 64), s > 0);
-                    mma_commit(&S.mma1);
-                }
-                if (!ws_wait1(&S.abort_flag, &S.h1, (uint32_t)(i & 1), limit)) break;
-                tc_fence_after();
-                if (!a.inject_timeout) {
-#pragma unroll
-                    for (int s = 0; s < WS_K2 / 16; ++s)
-                        mma_bf16(tmem, smem_desc(h + 256 * s, 128, SB2), smem_desc(w2 + 256 * s, 128, SB2),
-                                 idesc_bf16(128, 64), s > 0);
-                    mma_commit(&S.mma2);
-                }
-                if (!ws_wait1(&S.abort_flag, &S.h2, (uint32_t)(i & 1), limit)) break;
-                tc_fence_after();
-                if (!a.inject_timeout) {
-#pragma unroll
-                    for (int s = 0; s < WS_K2 / 16; ++s)
-                        mma_bf16(tmem + 64, smem_desc(h + 256 * s, 128, SB2), smem_desc(w3 + 256 * s, 128, SB2),
-                                 idesc_bf16(128, 16), s > 0);
-                    mma_commit(&S.mma3);
-                }
+                for (int s = 0; s < WS_K1 / 16; ++s)
+                    mma_bf16_warp(tmem, smem_desc(aa + 256 * s, 128, SB1), smem_desc(w1 + 256 * s, 128, SB1),
+                                  idesc_bf16(128, 64), s > 0);
+                mma_commit_warp(&S.mma1);
             }
-            // every MMA this thread issued has completed before the TMEM is released
-            mma_commit(&S.fin);
-            const long long t0 = clock64();
-            while (!mbar_try_wait(&S.fin, 0u) && clock64() - t0 < limit) {}
+            if (!ws_wait(&S.abort_flag, &S.h1, (uint32_t)(i & 1), limit)) break;
+            tc_fence_after();
+            if (!a.inject_timeout) {
+#pragma unroll
+                for (int s = 0; s < WS_K2 / 16; ++s)
+                    mma_bf16_warp(tmem, smem_desc(h + 256 * s, 128, SB2), smem_desc(w2 + 256 * s, 128, SB2),
+                                  idesc_bf16(128, 64), s > 0);
+                mma_commit_warp(&S.mma2);
+            }
+            if (!ws_wait(&S.abort_flag, &S.h2, (uint32_t)(i & 1), limit)) break;
+            tc_fence_after();
+            if (!a.inject_timeout) {
+#pragma unroll
+                for (int s = 0; s < WS_K2 / 16; ++s)
+                    mma_bf16_warp(tmem + 64, smem_desc(h + 256 * s, 128, SB2), smem_desc(w3 + 256 * s, 128, SB2),
+                                  idesc_bf16(128, 16), s > 0);
+                mma_commit_warp(&S.mma3);
+            }
         }
+        // every MMA the elected lane issued has completed before the TMEM is released
+        mma_commit_warp(&S.fin);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&S.fin, 0u) && clock64() - t0 < limit) {}
     } else {
         // ---------------------------------------------------------------- epilogue
         const int e = t - 128;                                  // TMEM lane = tile row
