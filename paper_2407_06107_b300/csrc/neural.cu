@@ -1070,7 +1070,7 @@ __device__ __forceinline__ void grad_epilogue(uint32_t taddr, uint8_t* tile, int
     }
 }
 
-// The GEMMs of one stage of a group's tile (issued by the MMA thread).  fresh_*: the first
+// The GEMMs of one stage of a group's tile (issued by the MMA warp's elected lane).  fresh_*: the first
 // accumulation into that weight-gradient accumulator in this CTA overwrites it.
 __device__ __forceinline__ void train_stage(TrainWsSmem& S, int g, int stage, uint32_t tmem, bool& fresh3,
                                             bool& fresh2, bool& fresh1) {
@@ -1081,43 +1081,43 @@ __device__ __forceinline__ void train_stage(TrainWsSmem& S, int g, int stage, ui
     switch (stage) {
     case 0:     // Z1 = [X | 1] [W1 | b1]^T
         for (int s = 0; s < FX / 16; ++s)
-            mma_bf16(scr, smem_desc(sX + 256 * s, 128, FX * 16), smem_desc(sW1 + 256 * s, 128, FX * 16),
+            mma_bf16_warp(scr, smem_desc(sX + 256 * s, 128, FX * 16), smem_desc(sW1 + 256 * s, 128, FX * 16),
                      idesc_bf16(128, 64), s > 0);
         break;
     case 1:     // Z2 = [H1 | 1] [W2 | b2]^T
         for (int s = 0; s < FH / 16; ++s)
-            mma_bf16(scr, smem_desc(sH1 + 256 * s, 128, FH * 16), smem_desc(sW2 + 256 * s, 128, FH * 16),
+            mma_bf16_warp(scr, smem_desc(sH1 + 256 * s, 128, FH * 16), smem_desc(sW2 + 256 * s, 128, FH * 16),
                      idesc_bf16(128, 64), s > 0);
         break;
     case 2:     // Y = [H2 | 1] [W3 | b3]^T (8 outputs and 8 zero rows)
         for (int s = 0; s < FH / 16; ++s)
-            mma_bf16(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), smem_desc(sW3 + 256 * s, 128, FH * 16),
+            mma_bf16_warp(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), smem_desc(sW3 + 256 * s, 128, FH * 16),
                      idesc_bf16(128, 16), s > 0);
         break;
     case 3:     // dH2 = dY W3;  dW3 | db3 += dY^T [H2 | 1]
-        mma_bf16(scr, smem_desc(sY, 128, FY * 16), mn_desc(sW3, 128, FH * 16), idesc_bf16(128, 64) | IDESC_B_MN, 0);
+        mma_bf16_warp(scr, smem_desc(sY, 128, FY * 16), mn_desc(sW3, 128, FH * 16), idesc_bf16(128, 64) | IDESC_B_MN, 0);
         for (int s = 0; s < 8; ++s)
-            mma_bf16(tmem + TW_DW3, mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16),
+            mma_bf16_warp(tmem + TW_DW3, mn_desc(sY + 2 * FY * 16 * s, 128, FY * 16),
                      mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(64, 80) | IDESC_A_MN | IDESC_B_MN,
                      (fresh3 && s == 0) ? 0u : 1u);
         fresh3 = false;
         break;
     case 4:     // dH1 = dZ2 W2;  dW2 | db2 += dZ2^T [H1 | 1]   (dZ2 in the H2 tile)
         for (int s = 0; s < 4; ++s)
-            mma_bf16(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), mn_desc(sW2 + 2 * FH * 16 * s, 128, FH * 16),
+            mma_bf16_warp(scr, smem_desc(sH2 + 256 * s, 128, FH * 16), mn_desc(sW2 + 2 * FH * 16 * s, 128, FH * 16),
                      idesc_bf16(128, 64) | IDESC_B_MN, s > 0);
         for (int s = 0; s < 8; ++s)
-            mma_bf16(tmem + TW_DW2, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
+            mma_bf16_warp(tmem + TW_DW2, mn_desc(sH2 + 2 * FH * 16 * s, 128, FH * 16),
                      mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16), idesc_bf16(64, 80) | IDESC_A_MN | IDESC_B_MN,
                      (fresh2 && s == 0) ? 0u : 1u);
         fresh2 = false;
         break;
     default:    // dX = dZ1 W1;  dW1 | db1 += dZ1^T [X | 1]   (dZ1 in the H1 tile)
         for (int s = 0; s < 4; ++s)
-            mma_bf16(scr, smem_desc(sH1 + 256 * s, 128, FH * 16), mn_desc(sW1 + 2 * FX * 16 * s, 128, FX * 16),
+            mma_bf16_warp(scr, smem_desc(sH1 + 256 * s, 128, FH * 16), mn_desc(sW1 + 2 * FX * 16 * s, 128, FX * 16),
                      idesc_bf16(128, 32) | IDESC_B_MN, s > 0);
         for (int s = 0; s < 8; ++s)
-            mma_bf16(tmem + TW_DW1, mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16),
+            mma_bf16_warp(tmem + TW_DW1, mn_desc(sH1 + 2 * FH * 16 * s, 128, FH * 16),
                      mn_desc(sX + 2 * FX * 16 * s, 128, FX * 16), idesc_bf16(64, 48) | IDESC_A_MN | IDESC_B_MN,
                      (fresh1 && s == 0) ? 0u : 1u);
         fresh1 = false;
@@ -1262,8 +1262,10 @@ k_ntc_train_ws(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint
                 }
             }
         }
-    } else if (lane == 0) {
-        // ---------------------------------------------------------------- MMA thread
+    } else {
+        // ---------------------------------------------------------------- MMA warp
+        // The whole warp runs the scheduler with warp-uniform decisions and operands; one lane
+        // elected inside the issue instructions (elect.sync) issues the MMAs and commits.
         uint32_t left[TRW_GROUPS], stage[TRW_GROUPS], par[TRW_GROUPS];
         uint32_t remaining = 0;
 #pragma unroll
@@ -1280,10 +1282,10 @@ k_ntc_train_ws(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint
             bool progress = false;
 #pragma unroll
             for (int g = 0; g < TRW_GROUPS; ++g) {
-                if (left[g] == 0u || !mbar_test_wait(&S.ready[g], par[g])) continue;
+                if (left[g] == 0u || !__all_sync(0xFFFFFFFFu, mbar_test_wait(&S.ready[g], par[g]))) continue;
                 tc_fence_after();
                 train_stage(S, g, (int)stage[g], tmem, fresh3, fresh2, fresh1);
-                mma_commit(&S.done[g]);
+                mma_commit_warp(&S.done[g]);
                 stage[g] = stage[g] + 1u == (uint32_t)TRAIN_STAGES ? 0u : stage[g] + 1u;
                 par[g] ^= 1u;
                 --left[g];
@@ -1291,14 +1293,14 @@ k_ntc_train_ws(NeuralView N, uint32_t step, uint32_t batch, uint32_t first, uint
                 progress = true;
             }
             if (progress) since = clock64();
-            else if (S.abort_flag || clock64() - since > WAIT_CYCLES) { S.abort_flag = 1; break; }
+            else if (__any_sync(0xFFFFFFFFu, S.abort_flag || clock64() - since > WAIT_CYCLES)) { S.abort_flag = 1; break; }
         }
-        // every MMA this thread issued has completed before the accumulators are read
-        mma_commit(&S.fin);
+        // every MMA the elected lane issued has completed before the accumulators are read
+        mma_commit_warp(&S.fin);
         const long long t1 = clock64();
         bool fin = false;
         while (!(fin = mbar_try_wait(&S.fin, 0u)) && clock64() - t1 < WAIT_CYCLES) {}
-        if (!fin) S.abort_flag = 1;
+        if (!__all_sync(0xFFFFFFFFu, fin)) S.abort_flag = 1;
         S.acc_valid = (!fresh1 && remaining == 0u) ? 1 : 0;
         tc_fence_before();
     }
