@@ -129,6 +129,27 @@ def test_explicit_texels_wrap(ctx, net):
     assert torch.equal(y0, y1)
 
 
+@pytest.mark.parametrize("n", [0, 1, 129, 4095])
+def test_decode_ragged_and_empty(ctx, net, n):
+    # a decode does not depend on the rest of its batch: an empty batch, a single row and
+    # ragged last tiles give the rows of the full-batch decode (checked against the oracle
+    # above) bit for bit
+    ix, iy = _all_texels()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+    sel = np.random.default_rng(n).permutation(ix.size)[:n]
+    y_all = ctx.neural_decode(net, dev(ix), dev(iy))
+    y = ctx.neural_decode(net, dev(ix[sel]), dev(iy[sel]))
+    torch.cuda.synchronize()
+    assert tuple(y.shape) == (n, 8)
+    assert torch.equal(y, y_all[torch.from_numpy(sel).cuda()])
+
+
+def test_filter_shade_empty_batch(ctx, net):
+    e = torch.empty(0, device="cuda")
+    r, g, b = ctx.neural_filter_shade(net, e, e, None, "bspline", "stochastic", "ggx", 4, 1)
+    assert r.numel() == 0 and g.numel() == 0 and b.numel() == 0
+
+
 def test_decode_fp8_matches_oracle(ctx, net, data):
     lat, mlp, _ = data
     ctx.neural_quantize(net, "fp8")

@@ -60,6 +60,19 @@ def test_other_filters_table(ctx):
         _check_table(ctx, texs, 5000, f, mode, 2, 5)
 
 
+def test_empty_batch_is_noop(ctx):
+    texs = synth.texture_table_rgba8(3, 2, 64, seed=107, fbm_below=64)
+    handles = [ctx.create_texture([t]) for t in texs]
+    table = ctx.create_texture_table(handles)
+    e = torch.empty(0, device="cuda")
+    tid = torch.empty(0, dtype=torch.int32, device="cuda")
+    r, _, _, _ = ctx.filter_shade_table(table, e, e, tid, None, "mitchell", "stochastic", "ggx", 4, 1)
+    assert r.numel() == 0
+    ctx.destroy_texture_table(table)
+    for h in handles:
+        ctx.destroy_texture(h)
+
+
 def test_large_table_sampled(ctx):
     # 256 textures, sides 64..1024 log-uniform, 4M mixed queries, Mitchell at 4 spp
     texs = synth.texture_table_rgba8(256, 64, 1024, seed=107)
