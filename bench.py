@@ -329,7 +329,8 @@ def headline_extras(ex: dict) -> dict:
             "neural": {"decode_tflops_1tap": nn["stochastic_1tap"]["mlp_tflops"],
                        "speedup_1tap_vs_16tap": nn["speedup_1tap_vs_16tap"],
                        "fp8_rmse_vs_fp16_form": nn["fp8"]["rmse_vs_fp16_form"]},
-            "table_lookups_per_s": tb["stochastic"]["lookups_per_s"]}
+            "table_lookups_per_s": tb["stochastic"]["lookups_per_s"],
+            "table_frac_of_dram_floor": tb["stochastic"]["frac_of_dram_floor"]}
 
 
 # the sources the 2-D filter kernels are compiled from
@@ -820,6 +821,16 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
     texs = synth.texture_table_rgba8(ntex, 64, 4096, seed=105)
     handles = [ctx.create_texture([t]) for t in texs]
     tbytes = sum(t.nbytes for t in texs)
+    # The DRAM floor.  A query picks a texture uniformly and a texel uniformly within it, so
+    # the bytes of a texture with T texels are each read with density 1 / (ntex T).  An L2 that
+    # held exactly the hottest bytes (the smallest textures, 8 B per texel on the device) would
+    # still miss on the rest, and those misses at the measured random DRAM sector rate bound
+    # the launch time from below.
+    texels = np.sort(np.array([t.shape[0] * t.shape[1] for t in texs], dtype=np.float64))
+    l2_bytes = float(torch.cuda.get_device_properties(dev).L2_cache_size)
+    cum = np.cumsum(texels * 8.0)
+    k = int(np.searchsorted(cum, l2_bytes))
+    hit = 1.0 if k >= ntex else (k + (l2_bytes - (cum[k - 1] if k else 0.0)) / (texels[k] * 8.0)) / ntex
     del texs
     table = ctx.create_texture_table(handles)
     rng = np.random.default_rng(5)
@@ -839,14 +850,17 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
         msb = _time_launch(lambda: ctx.filter_shade_table(table, u, v, tid, None, "mitchell", mode, "ggx", 4, 1,
                                                           out=out, order=order), 2)
         fetches = 1 if mode == "stochastic" else 2
-        # one 32-B sector per 4-B texel fetch, plus 24 B of query I/O shared by the 4 samples
+        # one 32-B sector per 8-B texel fetch, plus 24 B of query I/O shared by the 4 samples
         sectors = (fetches + 24.0 / 32.0 / 4) * nq * 4 / (ms / 1e3)
+        floor_ms = (1.0 - hit) * fetches * nq * 4 / dram_rate * 1e3
         res[mode] = {"ms": ms, "lookups_per_s": nq * 4 / (ms / 1e3),
                      "texel_fetches_per_lookup": fetches,
                      "alg_sectors_per_s": sectors, "frac_of_l2_sector_rate": sectors / l2_rate,
+                     "dram_floor_ms": floor_ms, "frac_of_dram_floor": floor_ms / ms,
                      "binned_ms": msb, "binned_lookups_per_s": nq * 4 / (msb / 1e3)}
     res["bin_ms"] = ms_bin
     res["l2_sector_rate"], res["dram_sector_rate"] = l2_rate, dram_rate
+    res["l2_hit_bound"] = hit
     ctx.destroy_texture_table(table)
     for h in handles:
         ctx.destroy_texture(h)
@@ -1095,6 +1109,24 @@ def run_triplanar(args):
     ctx.close()
 
 
+def run_table(args):
+    """Bindless-table workload: the table block alone (256 RGBA8 textures, ~2 GiB, 2^26
+    queries, Mitchell 1-tap and positivized at 4 spp; single GPU)."""
+    import torch
+
+    import paper_2407_06107_b300 as stf
+    _, _, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = stf.Context(local)
+    res = table_block(ctx, dev)
+    print(json.dumps({"metric": "bindless table lookups/s", "value": res["stochastic"]["lookups_per_s"],
+                      "unit": "lookups/s", "ms_per_step": res["stochastic"]["ms"], "table": res,
+                      "config": {"workload": "bindless table, 256 RGBA8 textures (~2 GiB), 2^26 queries, "
+                                             "Mitchell at 4 spp"}}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1107,7 +1139,7 @@ def main():
     ap.add_argument("--extras-out", default="bench_extras.json",
                     help="where the comparator blocks go as JSON (rank 0, N = 1)")
     ap.add_argument("--workload", default="material",
-                    choices=["material", "volume", "neural", "train", "triplanar", "ntap", "lookup"])
+                    choices=["material", "volume", "neural", "train", "triplanar", "ntap", "lookup", "table"])
     ap.add_argument("--lfilter", default="linear", choices=["linear", "bspline", "catmull_rom", "mitchell", "ewa", "gauss"])
     ap.add_argument("--lmode", default="stochastic", choices=["stochastic", "ntap_before", "ntap_after", "positivized"])
     ap.add_argument("--lsampler", default="frs", choices=["frs", "fis"])
@@ -1142,6 +1174,8 @@ def main():
         run_ntap(args)
     elif args.workload == "lookup":
         run_lookup(args)
+    elif args.workload == "table":
+        run_table(args)
     else:
         run_ours(args)
 
