@@ -26,11 +26,13 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
     const uint32_t flags = V == KV_GENERAL ? a.flags : variant_flags(V);
     uint32_t* const picks = V == KV_GENERAL ? a.picks : nullptr;
     {
-        const float u = a.u[q], v = a.v[q];
+        // the query and result streams are touched once: loaded and stored evict-first, so
+        // they do not push texels out of L2
+        const float u = __ldcs(a.u + q), v = __ldcs(a.v + q);
         float dudx = 0.f, dvdx = 0.f, dudy = 0.f, dvdy = 0.f;
         float lam = 0.0f;
         if (a.has_derivs) {
-            dudx = a.dudx[q]; dvdx = a.dvdx[q]; dudy = a.dudy[q]; dvdy = a.dvdy[q];
+            dudx = __ldcs(a.dudx + q); dvdx = __ldcs(a.dvdx + q); dudy = __ldcs(a.dudy + q); dvdy = __ldcs(a.dvdy + q);
             if (T.levels > 1) lam = lod_aniso(dudx, dvdx, dudy, dvdy, (float)T.w[0], (float)T.h[0], T.levels);
         }
         if (flags & FLAG_LOD0) lam = 0.0f;      // finest level only
@@ -145,9 +147,9 @@ __device__ __forceinline__ void query_body(const FilterShadeArgs& a, const Fetch
             }
             acc.x += est.x; acc.y += est.y; acc.z += est.z;
         }
-        a.r[q] = acc.x * inv_spp;
-        a.g[q] = acc.y * inv_spp;
-        a.b[q] = acc.z * inv_spp;
+        __stcs(a.r + q, acc.x * inv_spp);
+        __stcs(a.g + q, acc.y * inv_spp);
+        __stcs(a.b + q, acc.z * inv_spp);
     }
 }
 
@@ -624,7 +626,7 @@ k_filter_shade_table(FilterShadeArgs a, const FetchCtx* __restrict__ table, uint
         const uint64_t i = base + threadIdx.x;
         if (i < a.n) {
             const uint64_t q = a.order ? (uint64_t)__ldg(a.order + i) : i;
-            const uint32_t t = __ldg(tex_id + q);
+            const uint32_t t = __ldcs(tex_id + q);
             if (t < ntex) {
                 query_body<FILTER, MODE, V>(a, table[t], SC, K, q);
             } else {
