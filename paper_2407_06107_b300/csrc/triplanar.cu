@@ -99,12 +99,13 @@ k_triplanar(TriplanarArgs a, const __grid_constant__ TriTex TT, ShadeConst SC, R
     const uint32_t flags = V == KV_GENERAL ? a.flags : variant_flags(V);
     uint32_t* const picks = V == KV_GENERAL ? a.picks : nullptr;
     const bool has_d = a.has_derivs != 0;
-    const float3 P = make_float3(a.px[q], a.py[q], a.pz[q]);
-    const float3 N = make_float3(a.nx[q], a.ny[q], a.nz[q]);
+    // the point and result streams are touched once: loaded and stored evict-first
+    const float3 P = make_float3(__ldcs(a.px + q), __ldcs(a.py + q), __ldcs(a.pz + q));
+    const float3 N = make_float3(__ldcs(a.nx + q), __ldcs(a.ny + q), __ldcs(a.nz + q));
     float3 DX = make_float3(0.f, 0.f, 0.f), DY = DX;
     if (has_d) {
-        DX = make_float3(a.dxx[q], a.dxy[q], a.dxz[q]);
-        DY = make_float3(a.dyx[q], a.dyy[q], a.dyz[q]);
+        DX = make_float3(__ldcs(a.dxx + q), __ldcs(a.dxy + q), __ldcs(a.dxz + q));
+        DY = make_float3(__ldcs(a.dyx + q), __ldcs(a.dyy + q), __ldcs(a.dyz + q));
     }
     if (isnan(P.x) || isnan(P.y) || isnan(P.z) || isnan(N.x) || isnan(N.y) || isnan(N.z) || isnan(DX.x) ||
         isnan(DX.y) || isnan(DX.z) || isnan(DY.x) || isnan(DY.y) || isnan(DY.z))
@@ -173,9 +174,9 @@ k_triplanar(TriplanarArgs a, const __grid_constant__ TriTex TT, ShadeConst SC, R
         acc.x += est.x; acc.y += est.y; acc.z += est.z;
     }
     const float inv_spp = 1.0f / (float)a.spp;
-    a.r[q] = acc.x * inv_spp;
-    a.g[q] = acc.y * inv_spp;
-    a.b[q] = acc.z * inv_spp;
+    __stcs(a.r + q, acc.x * inv_spp);
+    __stcs(a.g + q, acc.y * inv_spp);
+    __stcs(a.b + q, acc.z * inv_spp);
 }
 
 // The fully stochastic lookup at one sample per point with no flags, split at the texel
@@ -188,12 +189,13 @@ template <int FILTER, int TF>
 __device__ __forceinline__ TriPick<TF> tri_pick_1spp(const TriplanarArgs& a, const TriTex& TT, const RoundKeys& K,
                                                      uint64_t q) {
     const bool has_d = a.has_derivs != 0;
-    const float3 P = make_float3(a.px[q], a.py[q], a.pz[q]);
-    const float3 N = make_float3(a.nx[q], a.ny[q], a.nz[q]);
+    // the point and result streams are touched once: loaded and stored evict-first
+    const float3 P = make_float3(__ldcs(a.px + q), __ldcs(a.py + q), __ldcs(a.pz + q));
+    const float3 N = make_float3(__ldcs(a.nx + q), __ldcs(a.ny + q), __ldcs(a.nz + q));
     float3 DX = make_float3(0.f, 0.f, 0.f), DY = DX;
     if (has_d) {
-        DX = make_float3(a.dxx[q], a.dxy[q], a.dxz[q]);
-        DY = make_float3(a.dyx[q], a.dyy[q], a.dyz[q]);
+        DX = make_float3(__ldcs(a.dxx + q), __ldcs(a.dxy + q), __ldcs(a.dxz + q));
+        DY = make_float3(__ldcs(a.dyx + q), __ldcs(a.dyy + q), __ldcs(a.dyz + q));
     }
     if (isnan(P.x) || isnan(P.y) || isnan(P.z) || isnan(N.x) || isnan(N.y) || isnan(N.z) || isnan(DX.x) ||
         isnan(DX.y) || isnan(DX.z) || isnan(DY.x) || isnan(DY.y) || isnan(DY.z))
@@ -220,9 +222,9 @@ template <int TF>
 __device__ __forceinline__ void tri_finish_1spp(const TriplanarArgs& a, const TriTex& TT, const ShadeConst& SC,
                                                 const TriPick<TF>& r, uint64_t q) {
     const float3 f = shade<clamp_rough<TF>()>(a.shade, decode_raw<TF>(TT.t[r.plane], r.raw), SC);
-    a.r[q] = r.wt * f.x;
-    a.g[q] = r.wt * f.y;
-    a.b[q] = r.wt * f.z;
+    __stcs(a.r + q, r.wt * f.x);
+    __stcs(a.g + q, r.wt * f.y);
+    __stcs(a.b + q, r.wt * f.z);
 }
 
 template <int FILTER, int TF>
