@@ -814,6 +814,20 @@ def neural_block(ctx, dev, material, steps=1 << 14, batch=1 << 12, nq=1 << 24, s
     return res
 
 
+def ideal_l2_hit(texels, l2_bytes: float, texel_bytes: float = 8.0) -> float:
+    """Hit fraction of an L2 of l2_bytes that holds exactly the most-read bytes, when a query
+    picks one of the textures uniformly and a texel uniformly within it.  A texel of a texture
+    with T texels is then read with probability 1 / (n T): the smallest textures are the
+    hottest, so the cache holds them whole in order of size, and a part of the next one."""
+    t = np.sort(np.asarray(texels, dtype=np.float64))
+    n = t.size
+    cum = np.cumsum(t * texel_bytes)
+    k = int(np.searchsorted(cum, l2_bytes))
+    if k >= n:
+        return 1.0
+    return (k + (l2_bytes - (cum[k - 1] if k else 0.0)) / (t[k] * texel_bytes)) / n
+
+
 def table_block(ctx, dev, ntex=256, nq=1 << 26):
     """Bindless table: 256 RGBA8 textures with sides log-uniform in [64, 4096] (~2 GiB), 2^26
     mixed queries (texture id uniform), one persistent launch, Mitchell at 4 spp."""
@@ -821,16 +835,10 @@ def table_block(ctx, dev, ntex=256, nq=1 << 26):
     texs = synth.texture_table_rgba8(ntex, 64, 4096, seed=105)
     handles = [ctx.create_texture([t]) for t in texs]
     tbytes = sum(t.nbytes for t in texs)
-    # The DRAM floor.  A query picks a texture uniformly and a texel uniformly within it, so
-    # the bytes of a texture with T texels are each read with density 1 / (ntex T).  An L2 that
-    # held exactly the hottest bytes (the smallest textures, 8 B per texel on the device) would
-    # still miss on the rest, and those misses at the measured random DRAM sector rate bound
-    # the launch time from below.
-    texels = np.sort(np.array([t.shape[0] * t.shape[1] for t in texs], dtype=np.float64))
-    l2_bytes = float(torch.cuda.get_device_properties(dev).L2_cache_size)
-    cum = np.cumsum(texels * 8.0)
-    k = int(np.searchsorted(cum, l2_bytes))
-    hit = 1.0 if k >= ntex else (k + (l2_bytes - (cum[k - 1] if k else 0.0)) / (texels[k] * 8.0)) / ntex
+    # The DRAM floor: the picks that miss even an ideal L2 (ideal_l2_hit), at the measured
+    # random DRAM sector rate, bound the launch time from below.
+    hit = ideal_l2_hit([t.shape[0] * t.shape[1] for t in texs],
+                       float(torch.cuda.get_device_properties(dev).L2_cache_size))
     del texs
     table = ctx.create_texture_table(handles)
     rng = np.random.default_rng(5)
